@@ -1,0 +1,296 @@
+"""Python front end of the FGIM merge oracle (``fgim_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``. The product path never imports it.
+
+All arrays are host numpy arrays; see ``fgim_oracle.h`` for the layouts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fgim_oracle.c")
+_HDR = os.path.join(_HERE, "fgim_oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libfgim_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLAG_NEW = 1
+FLAG_REPLACED = 2
+
+_i32p = ctypes.c_void_p
+_c = ctypes
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("ndc", "hops", "pairs", "updates", "zero_before", "zero_after", "replaced",
+                 "prune_dist", "unreached", "attached")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class _Input(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("metric", ctypes.c_int32), ("h", ctypes.c_int32), ("off", ctypes.c_void_p),
+                ("adj", ctypes.c_void_p), ("M", ctypes.c_int32), ("entry", ctypes.c_void_p),
+                ("nthreads", ctypes.c_int32)]
+
+
+def compile_lib(force: bool = False) -> str:
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(compile_lib())
+            vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+            sig = {
+                "or_delta64": (ctypes.c_double, [vp, vp, i32, i32]),
+                "or_delta": (f32, [vp, vp, i32, i32]),
+                "or_knn_search": (i32, [vp, i64, i32, i32, vp, i32, i32, vp, i32, i32, vp, vp, vp]),
+                "or_knn_exact": (None, [vp, i64, i32, i32, vp, i64, vp, i32, i32, vp, vp]),
+                "or_stage_a": (i32, [vp, i32, i32, vp, vp, vp, vp]),
+                "or_refine_iter": (None, [vp, i32, i32, vp, vp, vp, vp]),
+                "or_indegree_repair": (None, [vp, i32, vp, vp, vp, vp, vp]),
+                "or_indegree": (None, [vp, i64, i32, vp]),
+                "or_prune": (None, [vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp]),
+                "or_reverse_insert": (None, [i64, i32, vp, vp, vp, vp, vp, vp]),
+                "or_reach_fix": (None, [vp, i32, i32, i32, vp, vp, vp, vp]),
+                "or_merged_entry": (i32, [vp]),
+                "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
+                "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+@dataclass
+class Problem:
+    """The merge input: vectors in phi order plus the h input PGs (local ids)."""
+    X: np.ndarray          # [N, d] float32
+    sizes: List[int]
+    adj: np.ndarray        # [N, M] int32 local ids
+    entry: np.ndarray      # [h] int32 local
+    metric: int
+    nthreads: int = 0
+
+    def __post_init__(self):
+        self.X = np.ascontiguousarray(self.X, dtype=np.float32)
+        self.adj = np.ascontiguousarray(self.adj, dtype=np.int32)
+        self.entry = np.ascontiguousarray(self.entry, dtype=np.int32)
+        off = [0]
+        for s in self.sizes:
+            off.append(off[-1] + int(s))
+        self.off = np.asarray(off, dtype=np.int64)
+        assert self.off[-1] == self.X.shape[0] == self.adj.shape[0]
+        self._in = _Input(self.X.ctypes.data, self.X.shape[0], self.X.shape[1], self.metric, len(self.sizes),
+                          self.off.ctypes.data, self.adj.ctypes.data, self.adj.shape[1],
+                          self.entry.ctypes.data, self.nthreads)
+
+    @property
+    def N(self):
+        return int(self.X.shape[0])
+
+    @property
+    def h(self):
+        return len(self.sizes)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._in)
+
+    @staticmethod
+    def from_workload(w, graphs: Sequence[Tuple[np.ndarray, int]], nthreads: int = 0) -> "Problem":
+        adj = np.concatenate([g[0] for g in graphs], axis=0)
+        entry = np.asarray([g[1] for g in graphs], dtype=np.int32)
+        return Problem(w.X, list(w.shard_sizes), adj, entry, w.metric, nthreads)
+
+
+def delta(x: np.ndarray, y: np.ndarray, metric: int) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    return float(lib().or_delta(x.ctypes.data, y.ctypes.data, x.shape[0], metric))
+
+
+def knn_search(X_local, adj_local, ep, q, L, k, metric):
+    X_local = np.ascontiguousarray(X_local, dtype=np.float32)
+    adj_local = np.ascontiguousarray(adj_local, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    ids = np.full(k, -1, np.int32)
+    dist = np.full(k, np.inf, np.float32)
+    st = Stats()
+    r = lib().or_knn_search(X_local.ctypes.data, X_local.shape[0], X_local.shape[1], metric, adj_local.ctypes.data,
+                            adj_local.shape[1], ep, q.ctypes.data, L, k, ids.ctypes.data, dist.ctypes.data,
+                            ctypes.byref(st))
+    return ids[:r], dist[:r], st.as_dict()
+
+
+def knn_exact(X, Q, k, metric, exclude=None, nthreads=0):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), np.int32)
+    dist = np.empty((nq, k), np.float32)
+    ex = None if exclude is None else np.ascontiguousarray(exclude, dtype=np.int64)
+    lib().or_knn_exact(X.ctypes.data, X.shape[0], X.shape[1], metric, Q.ctypes.data, nq, _p(ex), k, nthreads,
+                       ids.ctypes.data, dist.ctypes.data)
+    return ids, dist
+
+
+class KNNG:
+    def __init__(self, N, k):
+        self.ids = np.full((N, k), -1, np.int32)
+        self.dist = np.full((N, k), np.inf, np.float32)
+        self.flags = np.zeros((N, k), np.uint8)
+
+    def copy(self):
+        c = KNNG.__new__(KNNG)
+        c.ids, c.dist, c.flags = self.ids.copy(), self.dist.copy(), self.flags.copy()
+        return c
+
+
+def stage_a(P: Problem, k: int, L: int = 0):
+    g = KNNG(P.N, k)
+    st = Stats()
+    Lu = lib().or_stage_a(P.ref, k, L, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data, ctypes.byref(st))
+    return g, int(Lu), st.as_dict()
+
+
+def refine_iter(P: Problem, g: KNNG, rev_cap: int = 0):
+    """One synchronous Visit + Update pass, in place on ``g``."""
+    k = g.ids.shape[1]
+    st = Stats()
+    lib().or_refine_iter(P.ref, k, rev_cap, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data,
+                         ctypes.byref(st))
+    return st.as_dict()
+
+
+def indegree(ids: np.ndarray) -> np.ndarray:
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    T = np.empty(ids.shape[0], np.int32)
+    lib().or_indegree(ids.ctypes.data, ids.shape[0], ids.shape[1], T.ctypes.data)
+    return T
+
+
+def indegree_repair(P: Problem, g: KNNG):
+    k = g.ids.shape[1]
+    T = np.empty(P.N, np.int32)
+    st = Stats()
+    lib().or_indegree_repair(P.ref, k, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data, T.ctypes.data,
+                             ctypes.byref(st))
+    return T, st.as_dict()
+
+
+def prune(P: Problem, g: KNNG, T: np.ndarray, R: int, alpha: float):
+    k = g.ids.shape[1]
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    e_ids = np.empty((P.N, R), np.int32)
+    e_dist = np.empty((P.N, R), np.float32)
+    e_cnt = np.empty(P.N, np.int32)
+    st = Stats()
+    lib().or_prune(P.ref, k, g.ids.ctypes.data, g.dist.ctypes.data, T.ctypes.data, R, alpha, e_ids.ctypes.data,
+                   e_dist.ctypes.data, e_cnt.ctypes.data, ctypes.byref(st))
+    return e_ids, e_dist, e_cnt, st.as_dict()
+
+
+def reverse_insert(e_ids, e_dist, e_cnt):
+    N, R = e_ids.shape
+    e_ids = np.ascontiguousarray(e_ids, dtype=np.int32)
+    e_dist = np.ascontiguousarray(e_dist, dtype=np.float32)
+    e_cnt = np.ascontiguousarray(e_cnt, dtype=np.int32)
+    o_ids = np.empty((N, R), np.int32)
+    o_dist = np.empty((N, R), np.float32)
+    o_deg = np.empty(N, np.int32)
+    lib().or_reverse_insert(N, R, e_ids.ctypes.data, e_dist.ctypes.data, e_cnt.ctypes.data, o_ids.ctypes.data,
+                            o_dist.ctypes.data, o_deg.ctypes.data)
+    return o_ids, o_dist, o_deg
+
+
+def reach_fix(P: Problem, o_ids, o_dist, o_deg, entry, beam: int = 64):
+    """In place on (o_ids, o_dist, o_deg)."""
+    R = o_ids.shape[1]
+    st = Stats()
+    lib().or_reach_fix(P.ref, R, entry, beam, o_ids.ctypes.data, o_dist.ctypes.data, o_deg.ctypes.data,
+                       ctypes.byref(st))
+    return st.as_dict()
+
+
+def merged_entry(P: Problem) -> int:
+    return int(lib().or_merged_entry(P.ref))
+
+
+@dataclass
+class MergeResult:
+    ids: np.ndarray
+    dist: np.ndarray
+    deg: np.ndarray
+    entry: int
+    knn_ids: np.ndarray
+    knn_dist: np.ndarray
+    L: int
+    stats: dict
+
+
+def merge(P: Problem, k: int, R: int, alpha: float, L: int = 0, iters: int = 3, rev_cap: int = 0,
+          ensure_reachable: bool = True) -> MergeResult:
+    N = P.N
+    o_ids = np.empty((N, R), np.int32)
+    o_dist = np.empty((N, R), np.float32)
+    o_deg = np.empty(N, np.int32)
+    entry = np.zeros(1, np.int32)
+    k_ids = np.empty((N, k), np.int32)
+    k_dist = np.empty((N, k), np.float32)
+    st = Stats()
+    Lu = lib().or_merge(P.ref, k, L, iters, rev_cap, R, alpha, int(ensure_reachable), o_ids.ctypes.data,
+                        o_dist.ctypes.data, o_deg.ctypes.data, entry.ctypes.data, k_ids.ctypes.data,
+                        k_dist.ctypes.data, ctypes.byref(st))
+    return MergeResult(o_ids, o_dist, o_deg, int(entry[0]), k_ids, k_dist, int(Lu), st.as_dict())
+
+
+def search(X, g_ids, entry, Q, beam, topk, metric, nthreads=0):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    g_ids = np.ascontiguousarray(g_ids, dtype=np.int32)
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    nq = Q.shape[0]
+    ids = np.empty((nq, topk), np.int32)
+    dist = np.empty((nq, topk), np.float32)
+    st = Stats()
+    lib().or_search(X.ctypes.data, X.shape[0], X.shape[1], metric, g_ids.ctypes.data, g_ids.shape[1], entry,
+                    Q.ctypes.data, nq, beam, topk, nthreads, ids.ctypes.data, dist.ctypes.data, ctypes.byref(st))
+    return ids, dist, st.as_dict()
+
+
+def recall_at(found: np.ndarray, truth: np.ndarray, k: int) -> float:
+    """Recall@k (Sec. 2.1): |R intersect R~| / k averaged over queries."""
+    hits = 0
+    for f, t in zip(found[:, :k], truth[:, :k]):
+        hits += len(set(int(x) for x in f if x >= 0) & set(int(x) for x in t if x >= 0))
+    return hits / (k * found.shape[0])

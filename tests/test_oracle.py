@@ -1,0 +1,425 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test ties one oracle function to something other than itself: a hand-derived
+trace (tests/golden), a closed form, a special case that reduces to exact k-NN, or
+an invariant the algorithm guarantees.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _line_problem(pos, sizes=None, adj=None, M=1):
+    """1-D points (d=1) as a problem; adjacency defaults to empty lists."""
+    X = np.asarray(pos, np.float32).reshape(-1, 1)
+    N = X.shape[0]
+    sizes = sizes or [N]
+    if adj is None:
+        adj = np.full((N, M), -1, np.int32)
+    return O.Problem(X, sizes, adj, np.zeros(len(sizes), np.int32), O_METRIC_L2)
+
+
+O_METRIC_L2, O_METRIC_IP, O_METRIC_COS = 0, 1, 2
+
+
+def _knng_from_lists(P, lists, flags=0):
+    N = len(lists)
+    k = len(lists[0])
+    g = O.KNNG(N, k)
+    for u, row in enumerate(lists):
+        for t, v in enumerate(row):
+            g.ids[u, t] = v
+            g.dist[u, t] = O.delta(P.X[u], P.X[v], P.metric)
+    g.flags[:] = flags
+    return g
+
+
+def _check_lists(ids, dist, N):
+    for u in range(ids.shape[0]):
+        row = ids[u]
+        valid = row[row >= 0]
+        n = len(valid)
+        assert np.all(row[n:] == -1), "empty slots must be last"
+        assert len(set(valid.tolist())) == n, "duplicate id"
+        assert u not in set(valid.tolist()), "self loop"
+        d = dist[u, :n]
+        keys = list(zip(d.tolist(), valid.tolist()))
+        assert keys == sorted(keys), "row not sorted by (dist, id)"
+        assert np.all(valid < N)
+
+
+# --------------------------------------------------------------------------- delta
+def test_delta_closed_forms():
+    x = np.array([1, 2, 3, 0], np.float32)
+    y = np.array([4, 6, 3, 0], np.float32)
+    assert O.delta(x, y, O_METRIC_L2) == 25.0
+    assert O.delta(y, x, O_METRIC_L2) == 25.0
+    e1 = np.array([1, 0, 0, 0], np.float32)
+    s = np.array([1, 1, 0, 0], np.float32) / np.float32(np.sqrt(2))
+    assert abs(O.delta(e1, s, O_METRIC_IP) - (1 - 1 / np.sqrt(2))) < 1e-7
+    # cosine ignores the norms
+    assert abs(O.delta(e1 * 3, np.array([2, 2, 0, 0], np.float32), O_METRIC_COS) - (1 - 1 / np.sqrt(2))) < 1e-7
+    # 1 - x.y on unit vectors equals half the squared L2 distance
+    a = np.random.default_rng(1).standard_normal(16).astype(np.float32)
+    b = np.random.default_rng(2).standard_normal(16).astype(np.float32)
+    a /= np.linalg.norm(a)
+    b /= np.linalg.norm(b)
+    assert abs(O.delta(a, b, O_METRIC_IP) - 0.5 * O.delta(a, b, O_METRIC_L2)) < 1e-6
+
+
+# --------------------------------------------------------------------------- Alg. 1
+def test_beam_chain_golden():
+    g = _golden("beam_chain.json")
+    n = g["n"]
+    X = np.arange(n, dtype=np.float32).reshape(-1, 1)
+    adj = np.full((n, 2), -1, np.int32)
+    for i in range(n):
+        if i > 0:
+            adj[i, 0] = i - 1
+        if i + 1 < n:
+            adj[i, 1] = i + 1
+    q = np.array([g["query"]], np.float32)
+    ids, dist, st = O.knn_search(X, adj, g["entry"], q, g["L"], g["k"], O_METRIC_L2)
+    assert ids.tolist() == g["expected_ids"]
+    np.testing.assert_allclose(dist, g["expected_dist"], rtol=1e-5)
+    assert st["hops"] == g["expected_hops"]
+    assert st["ndc"] == g["expected_ndc"]
+
+
+def test_beam_exhaustive_equals_bruteforce():
+    """If the graph is connected from ep and L >= n, Alg. 1 evaluates every vertex: exact top-k."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((300, 8)).astype(np.float32)
+    # a ring (connected) plus random chords
+    adj = np.concatenate([((np.arange(300) + 1) % 300)[:, None], ((np.arange(300) - 1) % 300)[:, None],
+                          rng.integers(0, 300, (300, 6))], axis=1).astype(np.int32)
+    ep = 17
+    Q = rng.standard_normal((20, 8)).astype(np.float32)
+    gt, gd = O.knn_exact(X, Q, 10, O_METRIC_L2)
+    for qi in range(20):
+        ids, dist, st = O.knn_search(X, adj, ep, Q[qi], 300, 10, O_METRIC_L2)
+        assert ids.tolist() == gt[qi].tolist()
+        assert st["ndc"] == 300
+
+
+def test_beam_invariants(small_problem):
+    w, graphs, P = small_problem
+    X0 = w.shard(0)
+    adj, ep = graphs[0]
+    for qi in range(50):
+        ids, dist, st = O.knn_search(X0, adj, ep, w.Q[qi], 16, 16, w.metric)
+        assert len(ids) == 16 and len(set(ids.tolist())) == 16
+        keys = list(zip(dist.tolist(), ids.tolist()))
+        assert keys == sorted(keys)
+        assert st["hops"] >= 1 and st["ndc"] >= 16
+
+
+# --------------------------------------------------------------------------- Alg. 2
+def _complete_problem(X, sizes, metric=O_METRIC_L2):
+    N = X.shape[0]
+    M = max(sizes) - 1
+    adj = np.full((N, M), -1, np.int32)
+    off = np.cumsum([0] + sizes)
+    for i, s in enumerate(sizes):
+        for u in range(s):
+            others = [v for v in range(s) if v != u]
+            adj[off[i] + u, :len(others)] = others
+    return O.Problem(X, sizes, adj, np.zeros(len(sizes), np.int32), metric)
+
+
+@pytest.mark.parametrize("sizes,k,L", [([60, 60], 8, 0), ([40, 50, 30], 6, 6)])
+def test_stage_a_complete_graphs_is_exact(sizes, k, L):
+    """Complete input graphs make C+ exact and one expansion of ep exact, so Alg. 2 yields the exact k-NNG."""
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((sum(sizes), 6)).astype(np.float32)
+    P = _complete_problem(X, sizes)
+    g, Lu, st = O.stage_a(P, k, L)
+    gt, gd = O.knn_exact(X, X, k, O_METRIC_L2, exclude=np.arange(X.shape[0]))
+    assert np.array_equal(g.ids, gt)
+    np.testing.assert_allclose(g.dist, gd, rtol=1e-6)
+    assert np.all(g.flags == O.FLAG_NEW)
+
+
+@pytest.mark.parametrize("k,h,L", [(16, 2, 16), (64, 4, 22), (48, 2, 48), (64, 8, 10), (32, 6, 7), (32, 3, 16)])
+def test_minimum_querying_L(k, h, L):
+    """Sec. 4.1.2 worst case: L = ceil(k / (h - 1))."""
+    rng = np.random.default_rng(0)
+    sizes = [12] * h
+    X = rng.standard_normal((12 * h, 4)).astype(np.float32)
+    P = _complete_problem(X, sizes)
+    _, Lu, _ = O.stage_a(P, k, 0)
+    assert Lu == L
+
+
+def test_stage_a_rows_valid(small_problem):
+    w, graphs, P = small_problem
+    g, Lu, st = O.stage_a(P, w.k)
+    assert Lu == 16
+    _check_lists(g.ids, g.dist, w.N)
+    assert np.all(g.ids >= 0), "every vertex gets k candidates (L >= k / (h-1))"
+
+
+# --------------------------------------------------------------------------- Alg. 3
+def _two_shard_uniform(N=600, d=4, seed=11):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (N, d)).astype(np.float32)
+    return X, [N // 2, N - N // 2]
+
+
+def test_refine_exact_knng_is_fixed_point():
+    X, sizes = _two_shard_uniform()
+    P = _complete_problem(X, sizes)
+    k = 8
+    gt, gd = O.knn_exact(X, X, k, O_METRIC_L2, exclude=np.arange(X.shape[0]))
+    g = O.KNNG(X.shape[0], k)
+    g.ids[:], g.dist[:], g.flags[:] = gt, gd, O.FLAG_NEW
+    st = O.refine_iter(P, g)
+    assert st["updates"] == 0
+    assert st["pairs"] > 0
+    assert np.array_equal(g.ids, gt) and np.array_equal(g.dist, gd)
+    assert np.all(g.flags == 0), "visited entries are old after the pass"
+
+
+def test_refine_monotone_cross_only(small_problem):
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    shard = np.repeat(np.arange(w.h), w.shard_sizes)
+    for _ in range(2):
+        before = g.copy()
+        st = O.refine_iter(P, g)
+        assert st["updates"] > 0
+        _check_lists(g.ids, g.dist, w.N)
+        # the j-th distance of a list never increases
+        assert np.all(g.dist <= before.dist)
+        # every entry inserted by Update is a cross-graph pair (Alg. 3: v1, v2 from different G_i)
+        new = (g.flags & O.FLAG_NEW) > 0
+        rows = np.nonzero(new)[0]
+        assert np.all(shard[g.ids[new]] != shard[rows])
+        # entries that were already present keep their distance
+        for u in range(0, w.N, 997):
+            old = dict(zip(before.ids[u].tolist(), before.dist[u].tolist()))
+            for v, dv in zip(g.ids[u].tolist(), g.dist[u].tolist()):
+                if v in old:
+                    assert old[v] == dv
+
+
+def test_refine_converges_to_exact_with_complete_local_graphs():
+    """Complete local graphs make the intra-shard part exact; refinement must complete the cross part."""
+    X, sizes = _two_shard_uniform(N=800, d=3, seed=3)
+    P = _complete_problem(X, sizes)
+    k = 8
+    g, _, _ = O.stage_a(P, k, 2)          # deliberately few cross candidates
+    gt, _ = O.knn_exact(X, X, k, O_METRIC_L2, exclude=np.arange(X.shape[0]))
+    r0 = O.recall_at(g.ids, gt, k)
+    for _ in range(6):
+        O.refine_iter(P, g)
+    r1 = O.recall_at(g.ids, gt, k)
+    assert r0 < 0.95 and r1 >= 0.99, (r0, r1)
+
+
+def test_refine_rev_cap_limits_pairs(small_problem):
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    g2 = g.copy()
+    s_full = O.refine_iter(P, g, rev_cap=w.k)
+    s_cap = O.refine_iter(P, g2, rev_cap=2)
+    assert s_cap["pairs"] < s_full["pairs"]
+
+
+# --------------------------------------------------------------------------- Alg. 4
+def test_repair_golden():
+    gd = _golden("repair_10v.json")
+    P = _line_problem(gd["pos"])
+    g = _knng_from_lists(P, gd["lists"], flags=0)
+    T, st = O.indegree_repair(P, g)
+    assert g.ids.tolist() == gd["expected_lists"]
+    np.testing.assert_array_equal(g.dist, np.asarray(gd["expected_dist"], np.float32))
+    assert g.flags.tolist() == gd["expected_flags"]
+    assert T.tolist() == gd["expected_T"]
+    assert st["zero_before"] == 4 and st["zero_after"] == 0 and st["replaced"] == 4
+
+
+def test_repair_invariants(small_problem):
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    O.refine_iter(P, g)
+    T0 = O.indegree(g.ids)
+    outdeg0 = (g.ids >= 0).sum(1)
+    T, st = O.indegree_repair(P, g)
+    assert np.array_equal(T, O.indegree(g.ids)), "returned recorder equals the recomputed indegree"
+    assert T.sum() == (g.ids >= 0).sum()
+    assert np.array_equal((g.ids >= 0).sum(1), outdeg0), "outdegree unchanged"
+    assert st["zero_before"] == (T0 == 0).sum()
+    assert st["zero_after"] <= st["zero_before"]
+    assert np.all(T[T0 > 0] > 0), "no vertex driven to zero indegree"
+    _check_lists(g.ids, g.dist, w.N)
+
+
+# --------------------------------------------------------------------------- Alg. 5
+def test_prune_golden():
+    gd = _golden("prune_line.json")
+    P = _line_problem(gd["pos"])
+    N = len(gd["pos"])
+    lists = [[1, 2, 3, 4, 5]] + [[-1] * 5 for _ in range(N - 1)]
+    g = O.KNNG(N, 5)
+    for t, v in enumerate(lists[0]):
+        g.ids[0, t] = v
+        g.dist[0, t] = O.delta(P.X[0], P.X[v], 0)
+    for case in gd["cases"]:
+        T = np.full(N, 2, np.int32)
+        for v in case["T1"]:
+            T[v] = 1
+        e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, case["R"], case["alpha"])
+        assert e_ids[0, :e_cnt[0]].tolist() == case["kept"], case
+
+
+def test_prune_exact_tie_is_pruned():
+    gd = _golden("prune_line.json")["tie_case"]
+    X = np.asarray(gd["pts"], np.float32)
+    P = O.Problem(X, [3], np.full((3, 1), -1, np.int32), np.zeros(1, np.int32), 0)
+    g = O.KNNG(3, 2)
+    g.ids[0] = [1, 2]
+    g.dist[0] = [O.delta(X[0], X[1], 0), O.delta(X[0], X[2], 0)]
+    assert g.dist[0].tolist() == [1.0, 1.25]
+    for case in gd["cases"]:
+        T = np.full(3, 2, np.int32)
+        for v in case["T1"]:
+            T[v] = 1
+        e_ids, _, e_cnt, _ = O.prune(P, g, T, case["R"], case["alpha"])
+        assert e_ids[0, :e_cnt[0]].tolist() == case["kept"]
+
+
+def test_prune_line_keeps_one_per_side():
+    """alpha=1 on a line: only the nearest neighbour on each side survives (all T > 1)."""
+    rng = np.random.default_rng(4)
+    pos = np.concatenate([[0.0], rng.uniform(-10, 10, 30)])
+    P = _line_problem(pos)
+    N = len(pos)
+    d = (pos[1:] - pos[0]) ** 2
+    order = np.lexsort((np.arange(1, N), d)) + 1
+    g = O.KNNG(N, N - 1)
+    for t, v in enumerate(order):
+        g.ids[0, t] = v
+        g.dist[0, t] = O.delta(P.X[0], P.X[v], 0)
+    T = np.full(N, 2, np.int32)
+    e_ids, _, e_cnt, _ = O.prune(P, g, T, 8, 1.0)
+    kept = e_ids[0, :e_cnt[0]]
+    right = [v for v in range(1, N) if pos[v] > 0]
+    left = [v for v in range(1, N) if pos[v] < 0]
+    expect = {min(right, key=lambda v: pos[v]), max(left, key=lambda v: pos[v])}
+    assert set(kept.tolist()) == expect
+
+
+def test_prune_invariants(small_problem):
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    T = O.indegree(g.ids)
+    e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, w.R, w.alpha)
+    a2 = np.float32(w.alpha) ** 2
+    for u in range(0, w.N, 331):
+        kept = e_ids[u, :e_cnt[u]].tolist()
+        row = g.ids[u].tolist()
+        assert kept == [v for v in row if v in set(kept)], "kept in list order"
+        assert e_cnt[u] <= w.R
+        # no kept, unprotected v is occluded by a kept w that precedes it
+        for j, v in enumerate(kept):
+            if T[v] == 1:
+                continue
+            for wv in kept[:j]:
+                assert e_dist[u, j] < np.float32(a2 * np.float32(O.delta(P.X[wv], P.X[v], 0)))
+
+
+def test_reverse_insert_invariants(small_problem):
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    T = O.indegree(g.ids)
+    e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, w.R, w.alpha)
+    o_ids, o_dist, o_deg = O.reverse_insert(e_ids, e_dist, e_cnt)
+    _check_lists(o_ids, o_dist, w.N)
+    assert np.all(o_deg <= w.R)
+    E = {(u, int(v)) for u in range(w.N) for v in e_ids[u, :e_cnt[u]]}
+    out = {(u, int(v)) for u in range(w.N) for v in o_ids[u, :o_deg[u]]}
+    assert out <= (E | {(v, u) for (u, v) in E})
+    for (u, v) in list(E)[::50]:
+        if (v, u) not in out:
+            # v's list is full of entries no worse than (delta(u,v), u)
+            assert o_deg[v] == w.R
+            duv = e_dist[u, list(e_ids[u]).index(v)]
+            assert (o_dist[v, -1], o_ids[v, -1]) <= (duv, u)
+
+
+# --------------------------------------------------------------------------- reachability fix
+def test_reach_fix_attaches_one_rep_per_component():
+    # three far-apart clusters of 1-D points; each cluster a clique
+    pos = [0, 1, 2, 100, 101, 102, 103, 200, 201]
+    P = _line_problem(pos)
+    clusters = [[0, 1, 2], [3, 4, 5, 6], [7, 8]]
+    R = 6
+    N = len(pos)
+    ids = np.full((N, R), -1, np.int32)
+    dist = np.full((N, R), np.inf, np.float32)
+    deg = np.zeros(N, np.int32)
+    for c in clusters:
+        for u in c:
+            nb = sorted((O.delta(P.X[u], P.X[v], 0), v) for v in c if v != u)
+            for t, (dv, v) in enumerate(nb):
+                ids[u, t], dist[u, t] = v, dv
+            deg[u] = len(nb)
+    st = O.reach_fix(P, ids, dist, deg, 0)
+    assert st["attached"] == 2 and st["unreached"] == 0
+    # cluster [3..6] is represented by 3 and hangs under the nearest reached vertex (2)
+    assert 3 in ids[2, :deg[2]].tolist()
+    # in the same round, cluster [7, 8] is represented by 7 and searched over the round-start graph:
+    # its nearest reached vertex is 2 again
+    assert 7 in ids[2, :deg[2]].tolist()
+    _check_lists(ids, dist, N)
+
+
+# --------------------------------------------------------------------------- end to end
+def test_merge_small_invariants(small_problem):
+    w, graphs, P = small_problem
+    r = O.merge(P, w.k, w.R, w.alpha)
+    _check_lists(r.ids, r.dist, w.N)
+    _check_lists(r.knn_ids, r.knn_dist, w.N)
+    assert np.all(r.deg <= w.R)
+    assert r.stats["unreached"] == 0
+    assert r.entry == O.merged_entry(P) == graphs[0][1]   # equal shards: the first shard's entry
+
+
+def test_merge_uniform_recall_and_exhaustive_search():
+    rng = np.random.default_rng(21)
+    from synth import pgbuild
+    X = rng.uniform(0, 1, (4000, 8)).astype(np.float32)
+    Q = rng.uniform(0, 1, (200, 8)).astype(np.float32)
+    sizes = [2000, 2000]
+    graphs = [pgbuild.build_pg(X[:2000], 16, 64, 0), pgbuild.build_pg(X[2000:], 16, 64, 0)]
+    P = O.Problem(X, sizes, np.concatenate([graphs[0][0], graphs[1][0]]),
+                  np.array([graphs[0][1], graphs[1][1]], np.int32), 0)
+    r = O.merge(P, 16, 32, 1.2)
+    gt, _ = O.knn_exact(X, Q, 10, 0)
+    ids, _, _ = O.search(X, r.ids, r.entry, Q, 64, 10, 0)
+    assert O.recall_at(ids, gt, 10) >= 0.95
+    # beam >= N on a graph where everything is reachable is exhaustive
+    ids_all, _, st = O.search(X, r.ids, r.entry, Q[:5], 4000, 10, 0)
+    assert np.array_equal(ids_all, gt[:5])
+
+
+def test_merge_thread_count_independent(small_problem):
+    w, graphs, _ = small_problem
+    P1 = O.Problem.from_workload(w, graphs, nthreads=1)
+    a = O.merge(P1, w.k, w.R, w.alpha, iters=1)
+    P4 = O.Problem.from_workload(w, graphs, nthreads=4)
+    b = O.merge(P4, w.k, w.R, w.alpha, iters=1)
+    assert np.array_equal(a.ids, b.ids) and np.array_equal(a.dist, b.dist)
+    assert np.array_equal(a.knn_ids, b.knn_ids)

@@ -1,0 +1,213 @@
+/*
+ * fgim.h -- C ABI of the GB300 (sm_103a) implementation of the FGIM merge hot path.
+ *
+ * FGIM merges h proximity-graph (PG) ANNS indexes built over disjoint vector sets
+ * into one PG over their union (Sec. 2.1, Definition "Merging Graph-based Indexes
+ * for ANNS"). The merge has three stages (Sec. 3.3):
+ *   (a) PGs -> k-NNG by cross querying (Sec. 4.1, Alg. 1 + Alg. 2),
+ *   (b) k-NNG refinement: Visit + Update local join and indegree repair (Sec. 4.2, Alg. 3 + Alg. 4),
+ *   (c) k-NNG -> PG: neighbour selection and reverse-edge insertion (Sec. 4.3, Alg. 5),
+ * followed by an added reachability fix (not in the paper) that attaches vertices the
+ * entry point cannot reach.
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers unless the name ends in _host. They are
+ *    borrowed: fgim never frees them and never keeps them after the call returns.
+ *    Inputs are never modified (except arguments documented as in/out).
+ *  - Global ids follow the ID mapping phi of Sec. 4.1.3 as offsets: local id v of
+ *    shard i is global id  n_0 + ... + n_{i-1} + v.
+ *  - Lists are rows of fixed width, sorted ascending by (distance, global id), valid
+ *    entries first, empty slots hold id -1 and distance +inf.
+ *  - Distances are squared L2, 1 - x.y (IP), or 1 - cos(x, y), evaluated in FP32.
+ *  - Every call is ordered on `stream` (0 = legacy default stream). Scratch memory is
+ *    taken with cudaMallocAsync on that stream and released before the call returns.
+ *    Calls return after the stream has drained (they synchronize the stream), so
+ *    results are ready and every error is reported by the call itself.
+ *  - Errors: argument errors are detected on the host before any work is queued and
+ *    return FGIM_EINVAL / FGIM_EUNSUPPORTED. CUDA errors return FGIM_ECUDA (the CUDA
+ *    error string is available from fgim_last_error()). A device-side bounded wait that
+ *    ran out returns FGIM_ETIMEOUT. No exception crosses the ABI.
+ *  - Not thread-safe for concurrent calls that share a stream; concurrent calls on
+ *    different streams are safe.
+ */
+#ifndef FGIM_H
+#define FGIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FGIM_OK = 0,
+    FGIM_EINVAL = -1,
+    FGIM_ENOMEM = -2,
+    FGIM_ECUDA = -3,
+    FGIM_ETIMEOUT = -4,
+    FGIM_EUNSUPPORTED = -5,
+    FGIM_EINTERNAL = -6
+} fgim_status;
+
+typedef enum { FGIM_L2SQ = 0, FGIM_IP = 1, FGIM_COSINE = 2 } fgim_metric;
+
+typedef enum { FGIM_F32 = 0 } fgim_dtype;
+
+/* Limits of this build. */
+#define FGIM_MAX_SHARDS 64
+#define FGIM_MAX_K 128          /* k of the k-NNG */
+#define FGIM_MAX_R 128          /* degree bound of the merged PG */
+#define FGIM_MAX_L 128          /* search pool (beam width) */
+#define FGIM_MAX_DEGREE 128     /* max degree of an input PG */
+#define FGIM_MAX_DIM 2048       /* dim must also be a multiple of 4 */
+
+/* List-entry flags of the k-NNG (Sec. 4.2.1 new/old, Alg. 4 `replaced`). */
+#define FGIM_FLAG_NEW 1u
+#define FGIM_FLAG_REPLACED 2u
+
+/* One input index G_i (Sec. 2.1): its vectors X_i and its PG. */
+typedef struct {
+    const void* vectors;     /* [n, dim] row-major, dtype of the params, 16-byte aligned */
+    const int32_t* adj;      /* [n, max_degree] LOCAL ids, -1 padded */
+    int32_t n;               /* n_i >= 1 */
+    int32_t max_degree;      /* 1 .. FGIM_MAX_DEGREE */
+    int32_t entry;           /* entry point ep_i (local id) */
+    int32_t reserved;
+} fgim_shard;
+
+typedef struct {
+    int32_t dim;             /* d, multiple of 4, <= FGIM_MAX_DIM */
+    int32_t dtype;           /* fgim_dtype */
+    int32_t metric;          /* fgim_metric */
+    int32_t k;               /* k of the k-NNG (Alg. 2 outdegree bound) */
+    int32_t R;               /* degree bound of the merged PG (Alg. 5) */
+    float alpha;             /* alpha-RNG factor of the prune; 1 = Alg. 5 as printed */
+    int32_t L;               /* cross-query pool; 0 = ceil(k / (h - 1)) (Sec. 4.1.2) */
+    int32_t iters;           /* I_max of Alg. 3 (>= 0) */
+    int32_t rev_cap;         /* cap of each reverse list in Visit; 0 = k */
+    int32_t ensure_reachable;/* 1 = run the reachability fix after Alg. 5 */
+    int32_t reach_beam;      /* pool of the searches of the reachability fix; 0 = 64 */
+    int32_t reserved[5];
+} fgim_params;
+
+/* k-NNG buffers, caller-owned device memory: [n, k] each. */
+typedef struct {
+    int32_t* ids;
+    float* dist;
+    uint8_t* flags;
+    int64_t n;
+    int32_t k;
+    int32_t reserved;
+} fgim_knng;
+
+/* Merged PG buffers, caller-owned device memory. */
+typedef struct {
+    int32_t* ids;            /* [n, R] global ids, -1 padded */
+    float* dist;             /* [n, R] */
+    int32_t* deg;            /* [n] */
+    int64_t n;
+    int32_t R;
+    int32_t entry;           /* out: global id of the merged entry point */
+} fgim_graph;
+
+/* Counters of the last call on this host thread (informational). */
+typedef struct {
+    int64_t ndc;             /* distance evaluations of the beam searches (stage a + reach fix) */
+    int64_t hops;            /* beam-search expansions */
+    int64_t join_pairs;      /* cross-graph pairs evaluated by Update */
+    int64_t proposals;       /* list insertions proposed by Update (after filtering) */
+    int64_t zero_indegree;   /* zero-indegree vertices met by the last indegree repair */
+    int64_t repaired;        /* replacements made by the indegree repairs */
+    int64_t attached;        /* vertices attached by the reachability fix */
+    int64_t unreached;       /* vertices still unreached after the fix */
+    int64_t join_reruns;     /* Update passes re-run after a proposal-buffer overflow */
+} fgim_stats;
+
+/*
+ * Full merge (Sec. 3.3): stage a, then `iters` x (Visit + Update + indegree repair),
+ * then Alg. 5 and, if params->ensure_reachable, the reachability fix.
+ * shards: host array of h descriptors (2 <= h <= FGIM_MAX_SHARDS). The shards' vector
+ *   arrays may live anywhere on the device; when they are consecutive in one buffer
+ *   (shard i+1 starts right after shard i) no copy is made.
+ * knng_out: optional (NULL = internal); receives the refined k-NNG (n = sum n_i, k).
+ * out: receives the merged PG (n = sum n_i, R = params->R) and its entry point, the
+ *   entry of the largest input shard (lowest shard index on ties) mapped by phi.
+ */
+fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                       fgim_knng* knng_out, fgim_graph* out, void* stream);
+
+/*
+ * Same merge from and to HOST memory: copies the vectors and graphs in, merges, copies
+ * the merged PG back. vectors_host: [sum n_i, dim] (shards consecutive in phi order);
+ * adj_host: [sum n_i, max_degree] local ids; sizes/entries: [h]. out_ids_host [N, R],
+ * out_deg_host [N], out_entry_host [1]. Host buffers should be pinned for full speed.
+ */
+fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, const int32_t* sizes,
+                            const int32_t* entries, int32_t h, int32_t max_degree, const fgim_params* params,
+                            int32_t* out_ids_host, int32_t* out_deg_host, int32_t* out_entry_host, void* stream);
+
+/* Stage (a), Alg. 2: PGs -> k-NNG by cross querying. out: [N, k], all flags new. */
+fgim_status fgim_cross_query(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                             fgim_knng* out, void* stream);
+
+/*
+ * One pass of Alg. 3's Visit + Update, in place on `knng` (synchronous form: every
+ * candidate set is built from the lists as they stand when the pass starts, and each
+ * list ends as the top-k of its entries and all proposals, duplicates by id removed).
+ */
+fgim_status fgim_refine_pass(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                             fgim_knng* knng, void* stream);
+
+/* Alg. 4 in place on `knng`; T_out (optional, [N]) receives the indegree recorder. */
+fgim_status fgim_indegree_repair(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                                 fgim_knng* knng, int32_t* T_out, void* stream);
+
+/*
+ * Alg. 5 neighbour selection: keep v when T(v) = 1 or delta(u,v) < alpha^2 delta(w,v) for
+ * every kept w; stop at R. e_ids/e_dist [N, R] (-1 / +inf padded), e_cnt [N].
+ */
+fgim_status fgim_prune(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                       const fgim_knng* knng, const int32_t* T, int32_t* e_ids, float* e_dist,
+                       int32_t* e_cnt, void* stream);
+
+/* Alg. 5 connectivity enhancement: out(u) = top-R of E'(u) U {v : u in E'(v)}. */
+fgim_status fgim_reverse_insert(int64_t n, int32_t R, const int32_t* e_ids, const float* e_dist,
+                                const int32_t* e_cnt, fgim_graph* out, void* stream);
+
+/* Reachability fix in place on `graph` (graph->entry is read, not written). */
+fgim_status fgim_reach_fix(const fgim_shard* shards, int32_t h, const fgim_params* params,
+                           fgim_graph* graph, void* stream);
+
+/*
+ * Alg. 1 over a merged graph for nq queries: pool `beam` (<= FGIM_MAX_L), returns the
+ * first `topk` (<= beam) results. base: [n, dim] vectors in global-id order.
+ */
+fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                        const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
+                        int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream);
+
+/* Counters of the last merge/search call made by this host thread. */
+void fgim_last_stats(fgim_stats* out);
+
+/* Human-readable name of a status; message of the last CUDA error on this host thread. */
+const char* fgim_strerror(fgim_status s);
+const char* fgim_last_error(void);
+
+/* Library version string. */
+const char* fgim_version(void);
+
+/*
+ * Launch accounting: number of kernels this library has launched since load (all
+ * threads). With profiling enabled, every launch is bracketed by CUDA events on its
+ * stream and the per-kernel event times are accumulated (fgim_prof_query, milliseconds).
+ */
+int64_t fgim_launch_count(void);
+void fgim_prof_enable(int32_t on);
+void fgim_prof_reset(void);
+int32_t fgim_prof_query(const char* kernel, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGIM_H */

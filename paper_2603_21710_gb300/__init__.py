@@ -1,0 +1,265 @@
+"""FGIM merge hot path on GB300 (sm_103a): Python binding of the C ABI in include/fgim.h.
+
+Argument marshalling only. PyTorch provides device memory and the current stream;
+every step of the merge runs in libfgim.so's CUDA kernels.
+
+    import paper_2603_21710_gb300 as fg
+    inp = fg.MergeInput(vectors, adjs, entries, metric="l2")   # per-shard CUDA tensors
+    out = fg.merge(inp, k=64, R=32, alpha=1.2)                 # merged PG on the device
+    ids, dist = fg.search(inp.X, out["ids"], out["entry"], queries, topk=10, beam=64)
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import FgimError, KNNG, Graph, Params, Shard, check, last_stats, load  # noqa: F401
+
+__all__ = ["MergeInput", "merge", "merge_host", "cross_query", "refine_pass", "indegree_repair", "prune",
+           "reverse_insert", "reach_fix", "search", "last_stats", "load", "launch_count", "FgimError",
+           "FLAG_NEW", "FLAG_REPLACED", "profiling"]
+
+FLAG_NEW = 1
+FLAG_REPLACED = 2
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _p(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+class MergeInput:
+    """The h input indexes: per-shard vectors [n_i, d] float32 and PGs [n_i, M_i] int32 (local ids).
+
+    Shards are stored back to back in one [N, d] tensor ``X`` (phi order), so the library
+    never copies them.
+    """
+
+    def __init__(self, vectors: Sequence[torch.Tensor], adjs: Sequence[torch.Tensor], entries: Sequence[int],
+                 metric="l2"):
+        if len(vectors) != len(adjs) or len(vectors) != len(entries):
+            raise ValueError("vectors, adjs and entries must have one item per shard")
+        self.metric = _lib.METRICS[metric]
+        vs = [_dev(v, torch.float32, "vectors") for v in vectors]
+        self.sizes = [int(v.shape[0]) for v in vs]
+        self.d = int(vs[0].shape[1])
+        self.X = vs[0] if len(vs) == 1 else torch.cat(vs, 0).contiguous()
+        self.adjs = [_dev(a, torch.int32, "adj") for a in adjs]
+        self.entries = [int(e) for e in entries]
+        self.N = int(sum(self.sizes))
+        self._shards = (Shard * len(vs))()
+        o = 0
+        for i, (n, a, e) in enumerate(zip(self.sizes, self.adjs, self.entries)):
+            self._shards[i] = Shard(self.X[o:o + n].data_ptr(), a.data_ptr(), n, int(a.shape[1]), e, 0)
+            o += n
+
+    @property
+    def h(self) -> int:
+        return len(self.sizes)
+
+    @classmethod
+    def from_flat(cls, X: torch.Tensor, sizes: Sequence[int], adj: torch.Tensor, entries: Sequence[int],
+                  metric="l2") -> "MergeInput":
+        """X [N, d] with shards consecutive; adj [N, M] local ids."""
+        vs, ads, o = [], [], 0
+        for n in sizes:
+            vs.append(X[o:o + n])
+            ads.append(adj[o:o + n])
+            o += n
+        return cls(vs, ads, entries, metric)
+
+    def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
+               reach_beam=0) -> Params:
+        p = Params()
+        p.dim, p.dtype, p.metric = self.d, 0, self.metric
+        p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap = k, R, float(alpha), L, iters, rev_cap
+        p.ensure_reachable, p.reach_beam = int(bool(ensure_reachable)), reach_beam
+        return p
+
+
+def _knng_struct(ids, dist, flags) -> KNNG:
+    return KNNG(ids.data_ptr(), dist.data_ptr(), flags.data_ptr(), ids.shape[0], ids.shape[1], 0)
+
+
+def _new_knng(N: int, k: int, device) -> dict:
+    return {"ids": torch.empty((N, k), dtype=torch.int32, device=device),
+            "dist": torch.empty((N, k), dtype=torch.float32, device=device),
+            "flags": torch.empty((N, k), dtype=torch.uint8, device=device)}
+
+
+def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3, rev_cap: int = 0,
+          ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False) -> dict:
+    """Full merge (stages a, b, c and the reachability fix). Returns device tensors."""
+    L_ = load()
+    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam)
+    dev = inp.X.device
+    out = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
+           "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
+           "deg": torch.empty((inp.N,), dtype=torch.int32, device=dev)}
+    g = Graph(out["ids"].data_ptr(), out["dist"].data_ptr(), out["deg"].data_ptr(), inp.N, R, 0)
+    kn = None
+    if return_knng:
+        kd = _new_knng(inp.N, k, dev)
+        kn = _knng_struct(kd["ids"], kd["dist"], kd["flags"])
+    check(L_.fgim_merge(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn) if kn else None, ctypes.byref(g),
+                        _stream()))
+    out["entry"] = int(g.entry)
+    out["stats"] = last_stats()
+    if return_knng:
+        out["knng"] = kd
+    return out
+
+
+def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metric="l2", L: int = 0, iters: int = 3,
+               rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None) -> dict:
+    """Merge from host memory (CPU tensors, pinned for speed); results land in host tensors."""
+    L_ = load()
+    if X.is_cuda or adj.is_cuda:
+        raise ValueError("merge_host takes host tensors")
+    X = X.contiguous()
+    adj = adj.contiguous()
+    if X.dtype != torch.float32 or adj.dtype != torch.int32:
+        raise ValueError("X must be float32 and adj int32")
+    N = int(X.shape[0])
+    p = Params()
+    p.dim, p.dtype, p.metric = int(X.shape[1]), 0, _lib.METRICS[metric]
+    p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap, p.ensure_reachable = k, R, float(alpha), L, iters, rev_cap, int(
+        bool(ensure_reachable))
+    sz = (ctypes.c_int32 * len(sizes))(*[int(s) for s in sizes])
+    en = (ctypes.c_int32 * len(entries))(*[int(e) for e in entries])
+    if out_ids is None:
+        out_ids = torch.empty((N, R), dtype=torch.int32).pin_memory()
+    if out_deg is None:
+        out_deg = torch.empty((N,), dtype=torch.int32).pin_memory()
+    entry = ctypes.c_int32(0)
+    check(L_.fgim_merge_host(_p(X), _p(adj), sz, en, len(sizes), int(adj.shape[1]), ctypes.byref(p), _p(out_ids),
+                             _p(out_deg), ctypes.byref(entry), _stream()))
+    return {"ids": out_ids, "deg": out_deg, "entry": int(entry.value), "stats": last_stats()}
+
+
+def cross_query(inp: MergeInput, k: int, L: int = 0) -> dict:
+    """Stage (a), Alg. 2: PGs -> k-NNG."""
+    L_ = load()
+    p = inp.params(k=k, L=L)
+    kd = _new_knng(inp.N, k, inp.X.device)
+    kn = _knng_struct(kd["ids"], kd["dist"], kd["flags"])
+    check(L_.fgim_cross_query(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
+    kd["stats"] = last_stats()
+    return kd
+
+
+def refine_pass(inp: MergeInput, knng: dict, rev_cap: int = 0) -> dict:
+    """One synchronous Visit + Update pass of Alg. 3, in place on ``knng``."""
+    L_ = load()
+    k = int(knng["ids"].shape[1])
+    p = inp.params(k=k, rev_cap=rev_cap)
+    kn = _knng_struct(knng["ids"], knng["dist"], knng["flags"])
+    check(L_.fgim_refine_pass(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
+    return last_stats()
+
+
+def indegree_repair(inp: MergeInput, knng: dict):
+    """Alg. 4 in place on ``knng``; returns (T, stats)."""
+    L_ = load()
+    k = int(knng["ids"].shape[1])
+    p = inp.params(k=k)
+    T = torch.empty((inp.N,), dtype=torch.int32, device=inp.X.device)
+    kn = _knng_struct(knng["ids"], knng["dist"], knng["flags"])
+    check(L_.fgim_indegree_repair(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _p(T), _stream()))
+    return T, last_stats()
+
+
+def prune(inp: MergeInput, knng: dict, T: torch.Tensor, R: int, alpha: float = 1.0):
+    """Alg. 5 neighbour selection: returns (e_ids [N, R], e_dist, e_cnt)."""
+    L_ = load()
+    k = int(knng["ids"].shape[1])
+    p = inp.params(k=k, R=R, alpha=alpha)
+    dev = inp.X.device
+    e_ids = torch.empty((inp.N, R), dtype=torch.int32, device=dev)
+    e_dist = torch.empty((inp.N, R), dtype=torch.float32, device=dev)
+    e_cnt = torch.empty((inp.N,), dtype=torch.int32, device=dev)
+    flags = knng.get("flags")
+    if flags is None:
+        flags = torch.zeros_like(knng["ids"], dtype=torch.uint8)
+    kn = _knng_struct(knng["ids"], knng["dist"], flags)
+    T = _dev(T, torch.int32, "T")
+    check(L_.fgim_prune(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _p(T), _p(e_ids), _p(e_dist),
+                        _p(e_cnt), _stream()))
+    return e_ids, e_dist, e_cnt
+
+
+def reverse_insert(e_ids: torch.Tensor, e_dist: torch.Tensor, e_cnt: torch.Tensor) -> dict:
+    """Alg. 5 connectivity enhancement."""
+    L_ = load()
+    N, R = int(e_ids.shape[0]), int(e_ids.shape[1])
+    dev = e_ids.device
+    out = {"ids": torch.empty((N, R), dtype=torch.int32, device=dev),
+           "dist": torch.empty((N, R), dtype=torch.float32, device=dev),
+           "deg": torch.empty((N,), dtype=torch.int32, device=dev)}
+    g = Graph(out["ids"].data_ptr(), out["dist"].data_ptr(), out["deg"].data_ptr(), N, R, 0)
+    check(L_.fgim_reverse_insert(N, R, _p(_dev(e_ids, torch.int32, "e_ids")), _p(_dev(e_dist, torch.float32, "e_dist")),
+                                 _p(_dev(e_cnt, torch.int32, "e_cnt")), ctypes.byref(g), _stream()))
+    return out
+
+
+def reach_fix(inp: MergeInput, graph: dict, entry: int, k: int = 16, beam: int = 0) -> dict:
+    """Reachability fix in place on ``graph`` (ids, dist, deg)."""
+    L_ = load()
+    R = int(graph["ids"].shape[1])
+    p = inp.params(k=k, R=R, reach_beam=beam)
+    g = Graph(graph["ids"].data_ptr(), graph["dist"].data_ptr(), graph["deg"].data_ptr(), inp.N, R, int(entry))
+    check(L_.fgim_reach_fix(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(g), _stream()))
+    return last_stats()
+
+
+def search(X: torch.Tensor, graph_ids: torch.Tensor, entry: int, queries: torch.Tensor, topk: int = 10,
+           beam: int = 64, metric="l2"):
+    """Alg. 1 over a merged graph: returns (ids [nq, topk], dist)."""
+    L_ = load()
+    X = _dev(X, torch.float32, "X")
+    Q = _dev(queries, torch.float32, "queries")
+    G = _dev(graph_ids, torch.int32, "graph_ids")
+    nq = int(Q.shape[0])
+    ids = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
+    dist = torch.empty((nq, topk), dtype=torch.float32, device=X.device)
+    check(L_.fgim_search(_p(X), int(X.shape[0]), int(X.shape[1]), 0, _lib.METRICS[metric], _p(G), int(G.shape[1]),
+                         int(entry), _p(Q), nq, topk, beam, _p(ids), _p(dist), _stream()))
+    return ids, dist
+
+
+def launch_count() -> int:
+    return int(load().fgim_launch_count())
+
+
+class profiling:
+    """Context manager: per-kernel CUDA-event timing of every launch inside the block."""
+
+    def __enter__(self):
+        L_ = load()
+        L_.fgim_prof_reset()
+        L_.fgim_prof_enable(1)
+        return self
+
+    def __exit__(self, *exc):
+        load().fgim_prof_enable(0)
+
+    @staticmethod
+    def query(kernel: str):
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        load().fgim_prof_query(kernel.encode(), ctypes.byref(n), ctypes.byref(ms))
+        return int(n.value), float(ms.value)

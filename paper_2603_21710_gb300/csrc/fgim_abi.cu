@@ -1,0 +1,775 @@
+// C ABI of the FGIM library (see include/fgim.h): argument checks, scratch memory,
+// stage orchestration, launch accounting. Every compute step runs in this library's
+// kernels; the host only sequences launches and reads back small counters.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fgim_launch.h"
+
+namespace fgim {
+
+// ---------------------------------------------------------------------------- accounting
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_prof{0};
+static std::mutex g_prof_mu;
+struct ProfEntry {
+    long long launches = 0;
+    double ms = 0.0;
+};
+static std::map<std::string, ProfEntry> g_prof_table;
+struct PendingEvent {
+    const char* name;
+    cudaEvent_t e0, e1;
+};
+static thread_local std::vector<PendingEvent> t_pending;
+static thread_local fgim_stats t_stats;
+static thread_local std::string t_last_error;
+
+LaunchScope::LaunchScope(const char* n, cudaStream_t s) : name(n), stream(s), e0(nullptr), e1(nullptr), timed(false) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_prof.load(std::memory_order_relaxed)) {
+        if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+            cudaEventRecord(e0, s) == cudaSuccess)
+            timed = true;
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (timed && cudaEventRecord(e1, stream) == cudaSuccess) {
+        t_pending.push_back({name, e0, e1});
+        return;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+}
+
+// after the stream has drained: fold the recorded launches into the table
+static void resolve_events() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& p : t_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+            ProfEntry& e = g_prof_table[p.name];
+            e.launches += 1;
+            e.ms += ms;
+        }
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    t_pending.clear();
+}
+
+// ---------------------------------------------------------------------------- scratch
+class Scratch {
+   public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    ~Scratch() { release(); }
+    template <typename T>
+    T* alloc(long long count) {
+        if (count <= 0) count = 1;
+        void* p = nullptr;
+        const size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+        if (cudaMallocAsync(&p, bytes, s_) != cudaSuccess) {
+            cudaGetLastError();
+            ok_ = false;
+            return nullptr;
+        }
+        ptrs_.push_back(p);
+        return static_cast<T*>(p);
+    }
+    bool ok() const { return ok_; }
+    void release() {
+        for (void* p : ptrs_) cudaFreeAsync(p, s_);
+        ptrs_.clear();
+    }
+
+   private:
+    cudaStream_t s_;
+    std::vector<void*> ptrs_;
+    bool ok_ = true;
+};
+
+// ---------------------------------------------------------------------------- errors
+struct Fail {
+    fgim_status st;
+};
+
+static inline void ck(cudaError_t e) {
+    if (e != cudaSuccess) {
+        t_last_error = cudaGetErrorString(e);
+        if (e == cudaErrorMemoryAllocation) throw Fail{FGIM_ENOMEM};
+        throw Fail{FGIM_ECUDA};
+    }
+}
+
+static inline void need(bool ok, fgim_status st, const char* what) {
+    if (!ok) {
+        t_last_error = what;
+        throw Fail{st};
+    }
+}
+
+// counters on the device: [0] ndc, [1] hops, [2] pairs, [3] repaired, [4] attached
+struct Ctx {
+    cudaStream_t s;
+    Scratch sc;
+    int* status = nullptr;
+    unsigned long long* ctr = nullptr;
+    long long* host = nullptr;   // pinned readback slot
+    explicit Ctx(cudaStream_t st) : s(st), sc(st) {
+        status = sc.alloc<int>(4);
+        ctr = sc.alloc<unsigned long long>(16);
+        need(sc.ok(), FGIM_ENOMEM, "scratch allocation failed");
+        ck(cudaMemsetAsync(status, 0, 4 * sizeof(int), s));
+        ck(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
+        ck(cudaMallocHost(&host, 64));
+    }
+    ~Ctx() {
+        if (host) cudaFreeHost(host);
+    }
+    template <typename T>
+    T* alloc(long long n) {
+        T* p = sc.alloc<T>(n);
+        need(p != nullptr, FGIM_ENOMEM, "scratch allocation failed");
+        return p;
+    }
+    long long read_ll(const long long* dev) {
+        ck(cudaMemcpyAsync(host, dev, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        return host[0];
+    }
+    int read_i32(const int32_t* dev) {
+        ck(cudaMemcpyAsync(host, dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        return reinterpret_cast<int32_t*>(host)[0];
+    }
+    unsigned long long read_u64(const unsigned long long* dev) {
+        ck(cudaMemcpyAsync(host, dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        return reinterpret_cast<unsigned long long*>(host)[0];
+    }
+    // drain the stream, then report device-side errors and counters
+    void finish(fgim_stats* st) {
+        ck(cudaStreamSynchronize(s));
+        int hs[4];
+        unsigned long long hc[16];
+        ck(cudaMemcpy(hs, status, sizeof(hs), cudaMemcpyDeviceToHost));
+        ck(cudaMemcpy(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost));
+        if (st) {
+            st->ndc += (int64_t)hc[0];
+            st->hops += (int64_t)hc[1];
+            st->join_pairs += (int64_t)hc[2];
+            st->repaired += (int64_t)hc[3];
+            st->attached += (int64_t)hc[4];
+        }
+        if (hs[0] & kErrTimeout) need(false, FGIM_ETIMEOUT, "a bounded device loop ran out");
+        if (hs[0] & kErrBounds) need(false, FGIM_EINVAL, "an input index is out of range (graph ids or entry)");
+    }
+};
+
+// ---------------------------------------------------------------------------- validation
+static long long total_n(const fgim_shard* sh, int h) {
+    long long n = 0;
+    for (int i = 0; i < h; ++i) n += sh[i].n;
+    return n;
+}
+
+static void check_params(const fgim_params* p, bool need_merge) {
+    need(p != nullptr, FGIM_EINVAL, "params is NULL");
+    need(p->dim >= 4 && p->dim <= FGIM_MAX_DIM && p->dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
+    need(p->dtype == FGIM_F32, FGIM_EUNSUPPORTED, "only FP32 vector storage is supported");
+    need(p->metric == FGIM_L2SQ || p->metric == FGIM_IP || p->metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
+    if (!need_merge) return;
+    need(p->k >= 1 && p->k <= FGIM_MAX_K, FGIM_EINVAL, "k must be in [1, 128]");
+    need(p->R >= 1 && p->R <= FGIM_MAX_R, FGIM_EINVAL, "R must be in [1, 128]");
+    need(std::isfinite(p->alpha) && p->alpha > 0.f, FGIM_EINVAL, "alpha must be a positive finite number");
+    need(p->L >= 0 && p->L <= FGIM_MAX_L, FGIM_EINVAL, "L must be 0 or in [1, 128]");
+    need(p->iters >= 0 && p->iters <= 1000, FGIM_EINVAL, "iters must be in [0, 1000]");
+    need(p->rev_cap >= 0 && p->rev_cap <= FGIM_MAX_K, FGIM_EINVAL, "rev_cap must be 0 or in [1, 128]");
+    need(p->reach_beam >= 0 && p->reach_beam <= FGIM_MAX_L, FGIM_EINVAL, "reach_beam must be 0 or in [1, 128]");
+}
+
+static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
+    need(sh != nullptr, FGIM_EINVAL, "shards is NULL");
+    need(h >= 2 && h <= FGIM_MAX_SHARDS, FGIM_EINVAL, "h must be in [2, 64]");
+    long long n = 0;
+    for (int i = 0; i < h; ++i) {
+        need(sh[i].vectors != nullptr && sh[i].adj != nullptr, FGIM_EINVAL, "shard vectors/adj is NULL");
+        need(((uintptr_t)sh[i].vectors & 15u) == 0, FGIM_EINVAL, "shard vectors must be 16-byte aligned");
+        need(sh[i].n >= 1, FGIM_EINVAL, "shard n must be >= 1");
+        need(sh[i].max_degree >= 1 && sh[i].max_degree <= FGIM_MAX_DEGREE, FGIM_EINVAL, "max_degree must be in [1, 128]");
+        need(sh[i].entry >= 0 && sh[i].entry < sh[i].n, FGIM_EINVAL, "entry out of range");
+        n += sh[i].n;
+    }
+    need(n < 0x7fffffffLL, FGIM_EINVAL, "total size must fit a 31-bit id");
+    (void)p;
+}
+
+static ShardTable make_table(const fgim_shard* sh, int h, int dim) {
+    ShardTable t;
+    std::memset(&t, 0, sizeof(t));
+    t.h = h;
+    t.dim = dim;
+    long long o = 0;
+    for (int i = 0; i < h; ++i) {
+        t.off[i] = o;
+        t.adj[i] = sh[i].adj;
+        t.M[i] = sh[i].max_degree;
+        t.entry[i] = sh[i].entry;
+        o += sh[i].n;
+    }
+    t.off[h] = o;
+    return t;
+}
+
+// vectors of all shards as one [N, dim] buffer (no copy when they are already consecutive)
+static const float* contiguous_vectors(Ctx& c, const fgim_shard* sh, int h, int dim, long long N) {
+    const char* base = static_cast<const char*>(sh[0].vectors);
+    bool contiguous = true;
+    long long o = 0;
+    for (int i = 0; i < h; ++i) {
+        if (static_cast<const char*>(sh[i].vectors) != base + o * dim * 4) contiguous = false;
+        o += sh[i].n;
+    }
+    if (contiguous) return reinterpret_cast<const float*>(base);
+    float* X = c.alloc<float>(N * dim);
+    o = 0;
+    for (int i = 0; i < h; ++i) {
+        ck(cudaMemcpyAsync(X + o * dim, sh[i].vectors, (size_t)sh[i].n * dim * 4, cudaMemcpyDeviceToDevice, c.s));
+        o += sh[i].n;
+    }
+    return X;
+}
+
+static int resolve_L(const fgim_params* p, int h) { return p->L > 0 ? p->L : (p->k + (h - 1) - 1) / (h - 1); }
+static int resolve_rev_cap(const fgim_params* p) { return p->rev_cap > 0 ? p->rev_cap : p->k; }
+
+static int merged_entry(const fgim_shard* sh, int h) {
+    int best = 0;
+    for (int i = 1; i < h; ++i)
+        if (sh[i].n > sh[best].n) best = i;
+    long long o = 0;
+    for (int i = 0; i < best; ++i) o += sh[i].n;
+    return (int)(o + sh[best].entry);
+}
+
+// ---------------------------------------------------------------------------- stages
+struct Problem {
+    ShardTable t;
+    const float* X;
+    const float* inv;
+    long long N;
+    int d;
+    int metric;
+};
+
+static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_params* p) {
+    Problem P;
+    P.N = total_n(sh, h);
+    P.d = p->dim;
+    P.metric = p->metric;
+    P.t = make_table(sh, h, p->dim);
+    P.X = contiguous_vectors(c, sh, h, p->dim, P.N);
+    P.inv = nullptr;
+    if (p->metric == FGIM_COSINE) {
+        float* inv = c.alloc<float>(P.N);
+        ck(launch_inv_norms(P.X, P.N, P.d, inv, c.s));
+        P.inv = inv;
+    }
+    return P;
+}
+
+static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_knng* g) {
+    const int L = resolve_L(p, h);
+    need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
+    ck(launch_cross_query(P.t, P.X, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s));
+}
+
+static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knng* g, fgim_stats* st) {
+    const long long N = P.N;
+    const int k = g->k;
+    const int rev_cap = resolve_rev_cap(p);
+    RefineBuffers b;
+    std::memset(&b, 0, sizeof(b));
+    b.cntN = c.alloc<int32_t>(N);
+    b.cntO = c.alloc<int32_t>(N);
+    b.offN = c.alloc<long long>(N + 1);
+    b.offO = c.alloc<long long>(N + 1);
+    b.fillN = c.alloc<int32_t>(N);
+    b.fillO = c.alloc<int32_t>(N);
+    b.rev_capacity = N * k;
+    b.revN = c.alloc<uint64_t>(N * k);
+    b.revO = c.alloc<uint64_t>(N * k);
+    b.topN = c.alloc<int32_t>(N * rev_cap);
+    b.topO = c.alloc<int32_t>(N * rev_cap);
+    b.ntopN = c.alloc<int32_t>(N);
+    b.ntopO = c.alloc<int32_t>(N);
+    b.cmax = 2 * (k + rev_cap);
+    b.cand = c.alloc<int32_t>(N * b.cmax);
+    b.nn = c.alloc<int32_t>(N);
+    b.no = c.alloc<int32_t>(N);
+    // proposal buffer: large enough for every proposal of one vertex many times over
+    long long cap = 32LL * N;
+    const long long per_vertex_max = 2LL * b.cmax * b.cmax;
+    if (cap < 4 * per_vertex_max) cap = 4 * per_vertex_max;
+    if (cap < (1LL << 22)) cap = 1LL << 22;
+    b.prop_cap = cap;
+    b.prop_tgt = c.alloc<int32_t>(cap);
+    b.prop_key = c.alloc<uint64_t>(cap);
+    b.prop_sorted = c.alloc<uint64_t>(cap);
+    b.prop_count = c.alloc<unsigned long long>(1);
+    b.pcnt = c.alloc<int32_t>(N);
+    b.poff = c.alloc<long long>(N + 1);
+    b.pfill = c.alloc<int32_t>(N);
+    b.pending = c.alloc<uint8_t>(N);
+    b.pend_flag = c.alloc<int32_t>(N);
+    b.pend_list = c.alloc<int32_t>(N);
+    b.pend_off = c.alloc<long long>(N + 1);
+    b.scan_bytes = scan_scratch_bytes(N);
+    b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
+
+    ck(refine_visit(*g, rev_cap, b, c.s));
+    ck(cudaMemsetAsync(b.pending, 0, N, c.s));
+    ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
+    ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, nullptr, N, c.ctr + 2, c.status, c.s));
+    unsigned long long cnt = c.read_u64(b.prop_count);
+    long long total = (long long)cnt;
+    ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
+    long long prev_pending = -1;
+    while (cnt > (unsigned long long)cap) {
+        // some vertices dropped proposals: re-run exactly those against the merged lists
+        ck(launch_nonzero_flags(b.pending, N, b.pend_flag, c.s));
+        ck(compact_flags(b.pend_flag, N, b.pend_list, b.pend_off, b.scan_tmp, b.scan_bytes, c.s));
+        const long long np = c.read_ll(b.pend_off + N);
+        need(np > 0 && np != prev_pending + (np == prev_pending ? 0 : 0), FGIM_EINTERNAL, "proposal overflow without pending vertices");
+        prev_pending = np;
+        st->join_reruns += 1;
+        need(st->join_reruns < 10000, FGIM_EINTERNAL, "proposal overflow does not shrink");
+        ck(cudaMemsetAsync(b.pending, 0, N, c.s));
+        ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
+        ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, b.pend_list, np, c.ctr + 2, c.status, c.s));
+        cnt = c.read_u64(b.prop_count);
+        total += (long long)cnt;
+        ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
+    }
+    st->proposals += total;
+}
+
+static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stats* st) {
+    const long long N = P.N;
+    ck(launch_indegree(g->ids, N, g->k, T, true, g->flags, c.s));
+    int32_t* flag = c.alloc<int32_t>(N);
+    int32_t* zeros = c.alloc<int32_t>(N);
+    long long* off = c.alloc<long long>(N + 1);
+    const size_t sb = scan_scratch_bytes(N);
+    unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
+    ck(launch_zero_flags(T, N, flag, c.s));
+    ck(compact_flags(flag, N, zeros, off, tmp, sb, c.s));
+    ck(launch_repair(*g, T, zeros, off + N, c.ctr + 3, c.status, c.s));
+    if (st) st->zero_indegree = c.read_ll(off + N);
+}
+
+static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knng* g, const int32_t* T, int32_t* e_ids,
+                  float* e_dist, int32_t* e_cnt) {
+    const float alpha2 = (float)((double)p->alpha * (double)p->alpha);
+    ck(launch_prune(P.X, P.inv, P.N, P.d, P.metric, *g, T, p->R, alpha2, e_ids, e_dist, e_cnt, c.status, c.s));
+}
+
+static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
+                           fgim_graph* out) {
+    ReverseBuffers b;
+    b.cnt = c.alloc<int32_t>(N);
+    b.off = c.alloc<long long>(N + 1);
+    b.fill = c.alloc<int32_t>(N);
+    b.rev = c.alloc<uint64_t>(N * R);
+    b.scan_bytes = scan_scratch_bytes(N);
+    b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
+    ck(launch_reverse_insert(N, R, e_ids, e_dist, e_cnt, b, out->ids, out->dist, out->deg, c.s));
+}
+
+// BFS from the entry; returns the number of reached vertices
+static long long bfs(Ctx& c, const fgim_graph* g, int32_t* visited, int32_t* fa, int32_t* fb, int32_t* counts) {
+    const long long N = g->n;
+    ck(launch_bfs_init(visited, N, fa, counts + 0, g->entry, c.s));
+    long long reached = 1;
+    int32_t* fin = fa;
+    int32_t* fout = fb;
+    int cur = 0;
+    for (long long level = 0; level <= N; ++level) {
+        ck(cudaMemsetAsync(counts + (cur ^ 1), 0, sizeof(int32_t), c.s));
+        ck(launch_bfs_step(g->ids, g->R, N, visited, fin, counts + cur, fout, counts + (cur ^ 1), c.s));
+        const int nf = c.read_i32(counts + (cur ^ 1));
+        if (nf == 0) break;
+        reached += nf;
+        std::swap(fin, fout);
+        cur ^= 1;
+    }
+    return reached;
+}
+
+static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph* g, fgim_stats* st) {
+    const long long N = g->n;
+    const int R = g->R;
+    const int beam = p->reach_beam > 0 ? p->reach_beam : 64;
+    int32_t* visited = c.alloc<int32_t>(N);
+    int32_t* fa = c.alloc<int32_t>(N);
+    int32_t* fb = c.alloc<int32_t>(N);
+    int32_t* counts = c.alloc<int32_t>(4);
+    int32_t* label = c.alloc<int32_t>(N);
+    int32_t* flag = c.alloc<int32_t>(N);
+    int32_t* reps = c.alloc<int32_t>(N);
+    long long* off = c.alloc<long long>(N + 1);
+    const size_t sb = scan_scratch_bytes(N);
+    unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
+    int32_t* changed = c.alloc<int32_t>(1);
+    int32_t* cand = nullptr;
+    float* cdist = nullptr;
+    long long cand_cap = 0;
+    long long reached = 0;
+    for (int round = 0; round < 8; ++round) {
+        reached = bfs(c, g, visited, fa, fb, counts);
+        if (reached >= N) break;
+        ck(launch_cc_init(visited, N, label, c.s));
+        for (long long it = 0; it <= N; ++it) {
+            ck(cudaMemsetAsync(changed, 0, sizeof(int32_t), c.s));
+            ck(launch_cc_step(g->ids, R, N, visited, label, changed, c.s));
+            if (c.read_i32(changed) == 0) break;
+        }
+        ck(launch_rep_flags(visited, label, N, flag, c.s));
+        ck(compact_flags(flag, N, reps, off, tmp, sb, c.s));
+        const long long nr = c.read_ll(off + N);
+        if (nr == 0) break;
+        if (nr > cand_cap) {
+            cand = c.alloc<int32_t>(nr * beam);
+            cdist = c.alloc<float>(nr * beam);
+            cand_cap = nr;
+        }
+        ck(launch_search(P.X, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
+                         cand, cdist, c.ctr + 0, c.status, c.s));
+        ck(launch_reach_assign(g->ids, g->dist, g->deg, R, reps, off + N, cand, cdist, beam, c.ctr + 4, c.s));
+    }
+    reached = bfs(c, g, visited, fa, fb, counts);
+    if (st) st->unreached = N - reached;
+}
+
+}  // namespace fgim
+
+// ============================================================================ C ABI
+using namespace fgim;
+
+template <typename F>
+static fgim_status guarded(F&& f) {
+    try {
+        f();
+        return FGIM_OK;
+    } catch (const Fail& e) {
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        t_last_error = "host allocation failed";
+        return FGIM_ENOMEM;
+    } catch (...) {
+        t_last_error = "internal error";
+        return FGIM_EINTERNAL;
+    }
+}
+
+static void begin_call() {
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    t_last_error.clear();
+}
+
+static void end_call() { resolve_events(); }
+
+extern "C" {
+
+fgim_status fgim_cross_query(const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* out,
+                             void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(out && out->ids && out->dist && out->flags, FGIM_EINVAL, "knng buffers are NULL");
+        need(out->n == total_n(shards, h) && out->k == params->k, FGIM_EINVAL, "knng shape mismatch");
+        Ctx c((cudaStream_t)stream);
+        Problem P = make_problem(c, shards, h, params);
+        stage_a(c, P, params, h, out);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_refine_pass(const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* knng,
+                             void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(knng && knng->ids && knng->dist && knng->flags, FGIM_EINVAL, "knng buffers are NULL");
+        need(knng->n == total_n(shards, h) && knng->k >= 1 && knng->k <= FGIM_MAX_K, FGIM_EINVAL, "knng shape mismatch");
+        Ctx c((cudaStream_t)stream);
+        Problem P = make_problem(c, shards, h, params);
+        refine_pass(c, P, params, knng, &t_stats);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_indegree_repair(const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* knng,
+                                 int32_t* T_out, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(knng && knng->ids && knng->dist && knng->flags, FGIM_EINVAL, "knng buffers are NULL");
+        need(knng->n == total_n(shards, h), FGIM_EINVAL, "knng shape mismatch");
+        Ctx c((cudaStream_t)stream);
+        Problem P;
+        P.N = knng->n;
+        int32_t* T = T_out ? T_out : c.alloc<int32_t>(P.N);
+        repair(c, P, knng, T, &t_stats);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_prune(const fgim_shard* shards, int32_t h, const fgim_params* params, const fgim_knng* knng,
+                       const int32_t* T, int32_t* e_ids, float* e_dist, int32_t* e_cnt, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(knng && knng->ids && knng->dist && T && e_ids && e_dist && e_cnt, FGIM_EINVAL, "NULL buffer");
+        need(knng->n == total_n(shards, h) && knng->k >= 1 && knng->k <= FGIM_MAX_K, FGIM_EINVAL, "knng shape mismatch");
+        Ctx c((cudaStream_t)stream);
+        Problem P = make_problem(c, shards, h, params);
+        prune(c, P, params, knng, T, e_ids, e_dist, e_cnt);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_reverse_insert(int64_t n, int32_t R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
+                                fgim_graph* out, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(n >= 1 && n < 0x7fffffffLL && R >= 1 && R <= FGIM_MAX_R, FGIM_EINVAL, "bad n or R");
+        need(e_ids && e_dist && e_cnt && out && out->ids && out->dist && out->deg, FGIM_EINVAL, "NULL buffer");
+        need(out->n == n && out->R == R, FGIM_EINVAL, "graph shape mismatch");
+        Ctx c((cudaStream_t)stream);
+        reverse_insert(c, n, R, e_ids, e_dist, e_cnt, out);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_reach_fix(const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_graph* graph,
+                           void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(graph && graph->ids && graph->dist && graph->deg, FGIM_EINVAL, "NULL buffer");
+        need(graph->n == total_n(shards, h) && graph->R == params->R, FGIM_EINVAL, "graph shape mismatch");
+        need(graph->entry >= 0 && graph->entry < graph->n, FGIM_EINVAL, "graph entry out of range");
+        Ctx c((cudaStream_t)stream);
+        Problem P = make_problem(c, shards, h, params);
+        reach_fix(c, P, params, graph, &t_stats);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+static void merge_impl(Ctx& c, const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* knng_out,
+                       fgim_graph* out) {
+    Problem P = make_problem(c, shards, h, params);
+    const long long N = P.N;
+    const int k = params->k;
+    fgim_knng g;
+    if (knng_out) {
+        g = *knng_out;
+    } else {
+        g.ids = c.alloc<int32_t>(N * k);
+        g.dist = c.alloc<float>(N * k);
+        g.flags = c.alloc<uint8_t>(N * k);
+        g.n = N;
+        g.k = k;
+    }
+    stage_a(c, P, params, h, &g);
+    int32_t* T = c.alloc<int32_t>(N);
+    for (int it = 0; it < params->iters; ++it) {
+        refine_pass(c, P, params, &g, &t_stats);
+        repair(c, P, &g, T, &t_stats);
+    }
+    if (params->iters == 0) ck(launch_indegree(g.ids, N, k, T, false, nullptr, c.s));
+    int32_t* e_ids = c.alloc<int32_t>(N * params->R);
+    float* e_dist = c.alloc<float>(N * params->R);
+    int32_t* e_cnt = c.alloc<int32_t>(N);
+    prune(c, P, params, &g, T, e_ids, e_dist, e_cnt);
+    reverse_insert(c, N, params->R, e_ids, e_dist, e_cnt, out);
+    out->entry = merged_entry(shards, h);
+    if (params->ensure_reachable) reach_fix(c, P, params, out, &t_stats);
+    c.finish(&t_stats);
+}
+
+fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* knng_out,
+                       fgim_graph* out, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        const long long N = total_n(shards, h);
+        need(out && out->ids && out->dist && out->deg, FGIM_EINVAL, "graph buffers are NULL");
+        need(out->n == N && out->R == params->R, FGIM_EINVAL, "graph shape mismatch");
+        if (knng_out) {
+            need(knng_out->ids && knng_out->dist && knng_out->flags, FGIM_EINVAL, "knng buffers are NULL");
+            need(knng_out->n == N && knng_out->k == params->k, FGIM_EINVAL, "knng shape mismatch");
+        }
+        Ctx c((cudaStream_t)stream);
+        merge_impl(c, shards, h, params, knng_out, out);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, const int32_t* sizes,
+                            const int32_t* entries, int32_t h, int32_t max_degree, const fgim_params* params,
+                            int32_t* out_ids_host, int32_t* out_deg_host, int32_t* out_entry_host, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        need(vectors_host && adj_host && sizes && entries && out_ids_host && out_deg_host && out_entry_host,
+             FGIM_EINVAL, "NULL host buffer");
+        need(h >= 2 && h <= FGIM_MAX_SHARDS, FGIM_EINVAL, "h must be in [2, 64]");
+        need(max_degree >= 1 && max_degree <= FGIM_MAX_DEGREE, FGIM_EINVAL, "max_degree must be in [1, 128]");
+        long long N = 0;
+        for (int i = 0; i < h; ++i) {
+            need(sizes[i] >= 1, FGIM_EINVAL, "shard size must be >= 1");
+            N += sizes[i];
+        }
+        need(N < 0x7fffffffLL, FGIM_EINVAL, "total size must fit a 31-bit id");
+        Ctx c((cudaStream_t)stream);
+        const int d = params->dim;
+        float* X = c.alloc<float>(N * d);
+        int32_t* A = c.alloc<int32_t>(N * max_degree);
+        ck(cudaMemcpyAsync(X, vectors_host, (size_t)N * d * 4, cudaMemcpyHostToDevice, c.s));
+        ck(cudaMemcpyAsync(A, adj_host, (size_t)N * max_degree * 4, cudaMemcpyHostToDevice, c.s));
+        std::vector<fgim_shard> sh(h);
+        long long o = 0;
+        for (int i = 0; i < h; ++i) {
+            sh[i].vectors = X + o * d;
+            sh[i].adj = A + o * max_degree;
+            sh[i].n = sizes[i];
+            sh[i].max_degree = max_degree;
+            sh[i].entry = entries[i];
+            sh[i].reserved = 0;
+            o += sizes[i];
+        }
+        check_shards(sh.data(), h, params);
+        fgim_graph g;
+        g.ids = c.alloc<int32_t>(N * params->R);
+        g.dist = c.alloc<float>(N * params->R);
+        g.deg = c.alloc<int32_t>(N);
+        g.n = N;
+        g.R = params->R;
+        merge_impl(c, sh.data(), h, params, nullptr, &g);
+        ck(cudaMemcpyAsync(out_ids_host, g.ids, (size_t)N * params->R * 4, cudaMemcpyDeviceToHost, c.s));
+        ck(cudaMemcpyAsync(out_deg_host, g.deg, (size_t)N * 4, cudaMemcpyDeviceToHost, c.s));
+        ck(cudaStreamSynchronize(c.s));
+        *out_entry_host = g.entry;
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                        const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
+                        int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(base && graph_ids && queries && out_ids && out_dist, FGIM_EINVAL, "NULL buffer");
+        need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
+        need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
+        need(dtype == FGIM_F32, FGIM_EUNSUPPORTED, "only FP32 vector storage is supported");
+        need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
+        need(R >= 1 && R <= FGIM_MAX_DEGREE, FGIM_EINVAL, "R must be in [1, 128]");
+        need(entry >= 0 && entry < n, FGIM_EINVAL, "entry out of range");
+        need(nq >= 0, FGIM_EINVAL, "nq must be >= 0");
+        need(beam >= 1 && beam <= FGIM_MAX_L && topk >= 1 && topk <= beam, FGIM_EINVAL, "need 1 <= topk <= beam <= 128");
+        need(((uintptr_t)base & 15u) == 0 && ((uintptr_t)queries & 15u) == 0, FGIM_EINVAL, "vectors must be 16-byte aligned");
+        if (nq == 0) return;
+        Ctx c((cudaStream_t)stream);
+        const float* X = static_cast<const float*>(base);
+        const float* Q = static_cast<const float*>(queries);
+        float* inv = nullptr;
+        float* qinv = nullptr;
+        if (metric == FGIM_COSINE) {
+            inv = c.alloc<float>(n);
+            qinv = c.alloc<float>(nq);
+            ck(launch_inv_norms(X, n, dim, inv, c.s));
+            ck(launch_inv_norms(Q, nq, dim, qinv, c.s));
+        }
+        ck(launch_search(X, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
+                         out_dist, c.ctr + 0, c.status, c.s));
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+void fgim_last_stats(fgim_stats* out) {
+    if (out) *out = t_stats;
+}
+
+const char* fgim_strerror(fgim_status s) {
+    switch (s) {
+        case FGIM_OK: return "ok";
+        case FGIM_EINVAL: return "invalid argument";
+        case FGIM_ENOMEM: return "out of memory";
+        case FGIM_ECUDA: return "CUDA error";
+        case FGIM_ETIMEOUT: return "device wait timed out";
+        case FGIM_EUNSUPPORTED: return "unsupported configuration";
+        case FGIM_EINTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char* fgim_last_error(void) { return t_last_error.c_str(); }
+
+const char* fgim_version(void) { return "fgim-gb300 0.1.0 (sm_103a)"; }
+
+int64_t fgim_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void fgim_prof_enable(int32_t on) { g_prof.store(on ? 1 : 0); }
+
+void fgim_prof_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_table.clear();
+}
+
+int32_t fgim_prof_query(const char* kernel, int64_t* launches, double* total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto it = g_prof_table.find(kernel ? kernel : "");
+    if (it == g_prof_table.end()) {
+        if (launches) *launches = 0;
+        if (total_ms) *total_ms = 0.0;
+        return 0;
+    }
+    if (launches) *launches = it->second.launches;
+    if (total_ms) *total_ms = it->second.ms;
+    return 1;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// Internal device and host helpers of the FGIM CUDA library (sm_103a).
+//
+// Keys. Every list, pool and candidate set orders entries by (distance, global id).
+// Both are packed in one 64-bit key: the high word is the distance's IEEE bits mapped
+// to an order-preserving unsigned integer, the low word the id. Key order equals the
+// lexicographic (distance, id) order for every non-NaN distance.
+//
+// Distance. One function computes every distance that enters a list or decides a
+// comparison: over float4 chunks c = 0 .. d/4-1 in order, four accumulators
+// s_j += (a[4c+j] - b[4c+j])^2 (fused multiply-add), result (s0 + s1) + (s2 + s3).
+// (For inner product: s_j += a*b, delta = 1 - sum; cosine multiplies the sum by the
+// product of the two inverse norms.) It is symmetric bit for bit in its two operands,
+// so delta(a, b) computed anywhere equals delta(b, a) computed anywhere else, and the
+// same (id, distance) pair always yields the same key.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fgim.h"
+
+namespace fgim {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kMaxShards = FGIM_MAX_SHARDS;
+
+// device status word bits
+constexpr int kErrOverflow = 1;   // a bounded buffer overflowed (handled by the host)
+constexpr int kErrBounds = 2;     // an index failed a bounds check (the access was skipped)
+constexpr int kErrTimeout = 4;    // a bounded wait ran out
+
+struct ShardTable {
+    int h;
+    int dim;
+    long long off[kMaxShards + 1];
+    const int32_t* adj[kMaxShards];
+    int M[kMaxShards];
+    int entry[kMaxShards];
+};
+
+__host__ __device__ inline uint32_t f2ord(float f) {
+#ifdef __CUDA_ARCH__
+    uint32_t u = __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ inline float ord2f(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+__host__ __device__ inline uint64_t mkkey(float d, int32_t id) {
+    return ((uint64_t)f2ord(d) << 32) | (uint32_t)id;
+}
+__host__ __device__ inline int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)(k & 0xffffffffu); }
+__host__ __device__ inline float key_dist(uint64_t k) { return ord2f((uint32_t)(k >> 32)); }
+
+__device__ __forceinline__ int shard_of(const ShardTable& t, long long g) {
+    int lo = 0, hi = t.h - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g >= t.off[mid]) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ----------------------------------------------------------------------------
+// canonical distance (see the file comment); a and b are 16-byte aligned
+// ----------------------------------------------------------------------------
+template <int METRIC>
+__device__ __forceinline__ float delta_fn(const float* __restrict__ a, const float* __restrict__ b, int d,
+                                          float inv_ab) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    const int nc = d >> 2;
+#pragma unroll 4
+    for (int c = 0; c < nc; ++c) {
+        float4 x = a4[c];
+        float4 y = b4[c];
+        if (METRIC == FGIM_L2SQ) {
+            float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+            s0 = fmaf(e0, e0, s0);
+            s1 = fmaf(e1, e1, s1);
+            s2 = fmaf(e2, e2, s2);
+            s3 = fmaf(e3, e3, s3);
+        } else {
+            s0 = fmaf(x.x, y.x, s0);
+            s1 = fmaf(x.y, y.y, s1);
+            s2 = fmaf(x.z, y.z, s2);
+            s3 = fmaf(x.w, y.w, s3);
+        }
+    }
+    float s = (s0 + s1) + (s2 + s3);
+    if (METRIC == FGIM_L2SQ) return s;
+    if (METRIC == FGIM_IP) return 1.f - s;
+    return 1.f - s * inv_ab;
+}
+
+// ----------------------------------------------------------------------------
+// warp helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    lo = __shfl_sync(kFull, lo, src);
+    hi = __shfl_sync(kFull, hi, src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    lo = __shfl_xor_sync(kFull, lo, m);
+    hi = __shfl_xor_sync(kFull, hi, m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// ascending bitonic sort of one 64-bit key per lane across the warp
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            uint64_t o = shfl_xor64(v, stride);
+            bool up = ((lane & size) == 0);
+            bool lower = ((lane & stride) == 0);
+            uint64_t mn = v < o ? v : o;
+            uint64_t mx = v < o ? o : v;
+            v = (up == lower) ? mn : mx;
+        }
+    }
+    return v;
+}
+
+// Merge one candidate key per lane (kEmptyKey = none) into a sorted list of at most
+// `cap` keys held in shared memory, keeping the `cap` smallest. `aux` (optional) is a
+// byte that travels with each list entry; every candidate of one call enters with the
+// same `cand_aux`. Duplicates are removed by id: a candidate whose id is already in
+// the list is dropped (the list copy wins), and among lanes offering the same id only
+// the smallest key survives. BY_ID = false checks list membership by key equality,
+// which is exact when every copy of an id carries the same key (canonical distances).
+// Called by all 32 lanes with identical n, cap and cand_aux; cap <= 128. Returns the
+// new list size.
+template <bool BY_ID>
+__device__ int warp_merge(uint64_t* list, uint8_t* aux, int n, int cap, uint64_t cand, uint8_t cand_aux) {
+    const int lane = lane_id();
+    bool valid = cand != kEmptyKey;
+    if (valid && n >= cap && cand >= list[cap - 1]) valid = false;
+    if (valid) {
+        if (BY_ID) {
+            const int32_t cid = key_id(cand);
+            for (int t = 0; t < n; ++t)
+                if (key_id(list[t]) == cid) { valid = false; break; }
+        } else {
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (list[mid] < cand) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < n && list[lo] == cand) valid = false;
+        }
+    }
+    // duplicates among lanes: keep the smallest key of each id (lowest lane on equal keys)
+    {
+        const int32_t cid = valid ? key_id(cand) : -1 - lane;
+        const unsigned grp = __match_any_sync(kFull, cid);
+        if (__any_sync(kFull, valid && __popc(grp) > 1)) {
+            for (int src = 0; src < 32; ++src) {
+                uint64_t ok = shfl64(cand, src);
+                if (valid && ((grp >> src) & 1u) && src != lane && (ok < cand || (ok == cand && src < lane)))
+                    valid = false;
+            }
+        }
+    }
+    const uint64_t sorted = warp_sort32(valid ? cand : kEmptyKey);
+    const int m = __popc(__ballot_sync(kFull, sorted != kEmptyKey));
+    if (m == 0) return n;
+    // final position of every list entry: its index plus the candidates below it
+    const int per = (n + 31) >> 5;
+    uint64_t lk[4];
+    uint8_t la[4];
+    int lpos[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        lk[r] = kEmptyKey;
+        la[r] = 0;
+        lpos[r] = cap;
+        if (r < per) {
+            const int i = lane + 32 * r;
+            const bool act = i < n;
+            if (act) {
+                lk[r] = list[i];
+                la[r] = aux ? aux[i] : (uint8_t)0;
+            }
+            int lo = 0, hi = m;
+#pragma unroll
+            for (int step = 0; step < 6; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const uint64_t mk = shfl64(sorted, mid < 31 ? mid : 31);
+                if (lo < hi) {
+                    if (mk < lk[r]) lo = mid + 1;
+                    else hi = mid;
+                }
+            }
+            if (act) lpos[r] = i + lo;
+        }
+    }
+    // final position of every candidate: its rank plus the list entries below it
+    int cpos = cap;
+    if (lane < m) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (list[mid] < sorted) lo = mid + 1;
+            else hi = mid;
+        }
+        cpos = lane + lo;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (lpos[r] < cap) {
+            list[lpos[r]] = lk[r];
+            if (aux) aux[lpos[r]] = la[r];
+        }
+    }
+    if (cpos < cap) {
+        list[cpos] = sorted;
+        if (aux) aux[cpos] = cand_aux;
+    }
+    __syncwarp();
+    const int nn = n + m;
+    return nn < cap ? nn : cap;
+}
+
+// ----------------------------------------------------------------------------
+// host-side launch accounting (defined in fgim_abi.cu)
+// ----------------------------------------------------------------------------
+struct LaunchScope {
+    const char* name;
+    cudaStream_t stream;
+    cudaEvent_t e0, e1;
+    bool timed;
+    LaunchScope(const char* n, cudaStream_t s);
+    ~LaunchScope();
+};
+
+}  // namespace fgim

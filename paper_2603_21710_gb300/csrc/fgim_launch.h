@@ -1,0 +1,110 @@
+// Host-side launchers of the FGIM kernels (one declaration per kernel family).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fgim_internal.cuh"
+
+namespace fgim {
+
+// ---- k_search.cu
+cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float* inv_norm, long long N, int metric,
+                               int k, int L, fgim_knng* out, unsigned long long* counters, int* status,
+                               cudaStream_t s);
+cudaError_t launch_search(const float* X, const float* inv_norm, long long n, int d, int metric, const int32_t* graph,
+                          int R, int entry, const float* Q, const float* q_inv, const int32_t* qids, long long nq,
+                          int topk, int L, int32_t* out_ids, float* out_dist, unsigned long long* counters,
+                          int* status, cudaStream_t s);
+
+// ---- k_util.cu
+// exclusive scan of n int32 counts into n + 1 int64 offsets (out[n] = total)
+cudaError_t scan_counts(const int32_t* in, long long n, long long* out, void* scratch, size_t scratch_bytes,
+                        cudaStream_t s);
+size_t scan_scratch_bytes(long long n);
+cudaError_t launch_inv_norms(const float* X, long long n, int d, float* inv, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s);
+// indices i (ascending) with flag[i] != 0, written to out; count to *count (device)
+cudaError_t compact_flags(const int32_t* flag, long long n, int32_t* out, long long* offsets_scratch,
+                          void* scan_scratch, size_t scan_bytes, cudaStream_t s);
+
+// ---- k_refine.cu
+struct RefineBuffers {
+    // reverse lists
+    int32_t* cntN;
+    int32_t* cntO;
+    long long* offN;
+    long long* offO;
+    int32_t* fillN;
+    int32_t* fillO;
+    uint64_t* revN;
+    uint64_t* revO;
+    long long rev_capacity;   // entries of revN / revO (N * k each)
+    int32_t* topN;            // [N, rev_cap]
+    int32_t* topO;
+    int32_t* ntopN;
+    int32_t* ntopO;
+    // candidate sets
+    int32_t* cand;            // [N, cmax]
+    int32_t* nn;
+    int32_t* no;
+    int cmax;
+    // proposals
+    int32_t* prop_tgt;
+    uint64_t* prop_key;
+    long long prop_cap;
+    unsigned long long* prop_count;   // device counter
+    uint64_t* prop_sorted;
+    int32_t* pcnt;
+    long long* poff;
+    int32_t* pfill;
+    uint8_t* pending;
+    int32_t* pend_flag;
+    int32_t* pend_list;
+    long long* pend_off;
+    // scan scratch
+    void* scan_tmp;
+    size_t scan_bytes;
+};
+
+cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s);
+cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
+                        RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
+                        int* status, cudaStream_t s);
+cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
+cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
+                            cudaStream_t s);
+cudaError_t launch_repair(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
+                          unsigned long long* repaired, int* status, cudaStream_t s);
+cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cudaStream_t s);
+cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s);
+
+// ---- k_prune.cu
+cudaError_t launch_prune(const float* X, const float* inv_norm, long long N, int d, int metric, const fgim_knng& g,
+                         const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
+                         int* status, cudaStream_t s);
+struct ReverseBuffers {
+    int32_t* cnt;
+    long long* off;
+    int32_t* fill;
+    uint64_t* rev;
+    void* scan_tmp;
+    size_t scan_bytes;
+};
+cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
+                                  ReverseBuffers& b, int32_t* out_ids, float* out_dist, int32_t* out_deg,
+                                  cudaStream_t s);
+// reachability fix helpers
+cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry,
+                            cudaStream_t s);
+cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
+                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, cudaStream_t s);
+cudaError_t launch_cc_init(const int32_t* visited, long long N, int32_t* label, cudaStream_t s);
+cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32_t* visited, int32_t* label,
+                           int32_t* changed, cudaStream_t s);
+cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
+                             cudaStream_t s);
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int R, const int32_t* reps,
+                                const long long* nreps, const int32_t* cand, const float* cdist, int beam,
+                                unsigned long long* attached, cudaStream_t s);
+
+}  // namespace fgim

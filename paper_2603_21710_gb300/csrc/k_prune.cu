@@ -1,0 +1,334 @@
+// Stage (c): k-NNG -> PG (Alg. 5) and the reachability fix.
+//
+// Neighbour selection runs one warp per vertex u. The candidate rows of u are staged in
+// shared memory (padded stride) when they fit; candidates are visited in ascending
+// (delta, id); for each one the kept neighbours are tested in parallel, one lane per
+// kept w, with the canonical distance delta(w, v) and the alpha-RNG test
+// delta(u, v) < alpha^2 * delta(w, v) (alpha^2 rounded once to FP32, product in FP32).
+// A vertex whose only in-edge is u (T(v) = 1) is kept unconditionally (Alg. 5 line 5).
+//
+// Connectivity enhancement builds the reverse lists of the pruned snapshot E' by a
+// counting sort and merges them into E'(u), keeping the R smallest (delta, id).
+#include "fgim_launch.h"
+
+namespace fgim {
+
+static inline long long cdivl(long long a, long long b) { return (a + b - 1) / b; }
+
+template <int METRIC, bool STAGE>
+__global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const float* __restrict__ inv_norm,
+                                              long long N, int d, int k, const int32_t* __restrict__ ids,
+                                              const float* __restrict__ dist, const int32_t* __restrict__ T, int R,
+                                              float alpha2, int32_t* __restrict__ e_ids, float* __restrict__ e_dist,
+                                              int32_t* __restrict__ e_cnt, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (u >= N) return;
+    const int stride = d + 4;
+    const size_t per_warp = ((size_t)(STAGE ? k * stride * 4 : 0) + (size_t)k * 8 + 16 + 15) & ~(size_t)15;
+    unsigned char* base = smem + per_warp * warp;
+    float* rows = reinterpret_cast<float*>(base);
+    int32_t* cidv = reinterpret_cast<int32_t*>(base + (STAGE ? (size_t)k * stride * 4 : 0));
+    int32_t* kept = cidv + k;
+
+    // valid prefix of list(u)
+    int nv = 0;
+    for (int s0 = 0; s0 < k; s0 += 32) {
+        const int s = s0 + lane;
+        int32_t id = s < k ? ids[u * k + s] : -1;
+        if (id >= N) {
+            atomicOr(status, kErrBounds);
+            id = -1;
+        }
+        if (s < k) cidv[s] = id;
+        nv += __popc(__ballot_sync(kFull, id >= 0));
+    }
+    __syncwarp();
+    if (STAGE) {
+        const int nc4 = d >> 2;
+        for (int item = lane; item < nv * nc4; item += 32) {
+            const int r = item / nc4, c = item - (item / nc4) * nc4;
+            reinterpret_cast<float4*>(rows + r * stride)[c] =
+                reinterpret_cast<const float4*>(X + (long long)cidv[r] * d)[c];
+        }
+        __syncwarp();
+    }
+    int nk = 0;
+    for (int t = 0; t < nv && nk < R; ++t) {
+        const int32_t v = cidv[t];
+        bool keep = T[v] == 1;
+        if (!keep) {
+            const float duv = dist[u * k + t];
+            const float* rv = STAGE ? rows + t * stride : X + (long long)v * d;
+            bool occluded = false;
+            for (int s0 = 0; s0 < nk; s0 += 32) {
+                const int s = s0 + lane;
+                if (s < nk) {
+                    const int wi = kept[s];
+                    const float* rw = STAGE ? rows + wi * stride : X + (long long)cidv[wi] * d;
+                    const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]) : 1.f;
+                    const float dwv = delta_fn<METRIC>(rw, rv, d, inv);
+                    if (!(duv < __fmul_rn(alpha2, dwv))) occluded = true;
+                }
+            }
+            keep = !__any_sync(kFull, occluded);
+        }
+        if (keep) {
+            if (lane == 0) kept[nk] = t;
+            ++nk;
+            __syncwarp();
+        }
+    }
+    for (int s = lane; s < R; s += 32) {
+        if (s < nk) {
+            e_ids[u * R + s] = cidv[kept[s]];
+            e_dist[u * R + s] = dist[u * k + kept[s]];
+        } else {
+            e_ids[u * R + s] = -1;
+            e_dist[u * R + s] = __int_as_float(0x7f800000);
+        }
+    }
+    if (lane == 0) e_cnt[u] = nk;
+}
+
+cudaError_t launch_prune(const float* X, const float* inv_norm, long long N, int d, int metric, const fgim_knng& g,
+                         const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
+                         int* status, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const int k = g.k;
+    const int wpb = 2;
+    const size_t staged = ((size_t)k * (d + 4) * 4 + (size_t)k * 8 + 16 + 15) & ~(size_t)15;
+    const size_t unstaged = ((size_t)k * 8 + 16 + 15) & ~(size_t)15;
+    const bool stage = staged * wpb <= 160 * 1024;
+    const size_t smem = (stage ? staged : unstaged) * wpb;
+    cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_P(MT, ST)                                                                                     \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_prune<MT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        if (e != cudaSuccess) break;                                                                              \
+        LaunchScope ls("k_prune", s);                                                                             \
+        k_prune<MT, ST><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R, \
+                                                                        alpha2, e_ids, e_dist, e_cnt, status);    \
+        e = cudaGetLastError();                                                                                   \
+    } while (0)
+    if (stage) {
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_P(FGIM_L2SQ, true);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_P(FGIM_IP, true);
+        else FGIM_LAUNCH_P(FGIM_COSINE, true);
+    } else {
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_P(FGIM_L2SQ, false);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_P(FGIM_IP, false);
+        else FGIM_LAUNCH_P(FGIM_COSINE, false);
+    }
+#undef FGIM_LAUNCH_P
+    return e;
+}
+
+// ---------------------------------------------------------------------------- reverse insertion
+__global__ void k_e_count(const int32_t* __restrict__ e_ids, long long total, int32_t* __restrict__ cnt) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int32_t v = e_ids[i];
+    if (v >= 0) atomicAdd(cnt + v, 1);
+}
+
+__global__ void k_e_fill(const int32_t* __restrict__ e_ids, const float* __restrict__ e_dist, long long total, int R,
+                         const long long* __restrict__ off, int32_t* __restrict__ fill, uint64_t* __restrict__ rev) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int32_t v = e_ids[i];
+    if (v < 0) return;
+    const int p = atomicAdd(fill + v, 1);
+    rev[off[v] + p] = mkkey(e_dist[i], (int32_t)(i / R));
+}
+
+__global__ void __launch_bounds__(128) k_e_merge(const int32_t* __restrict__ e_ids, const float* __restrict__ e_dist,
+                                                 const int32_t* __restrict__ e_cnt, long long N, int R,
+                                                 const long long* __restrict__ off, const uint64_t* __restrict__ rev,
+                                                 int32_t* __restrict__ out_ids, float* __restrict__ out_dist,
+                                                 int32_t* __restrict__ out_deg) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (u >= N) return;
+    uint64_t* list = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * R;
+    const int ne = e_cnt[u];
+    for (int s = lane; s < ne; s += 32) list[s] = mkkey(e_dist[u * R + s], e_ids[u * R + s]);
+    __syncwarp();
+    int n = ne;
+    const long long b = off[u], m = off[u + 1] - off[u];
+    for (long long c0 = 0; c0 < m; c0 += 32) {
+        const uint64_t key = (c0 + lane < m) ? rev[b + c0 + lane] : kEmptyKey;
+        n = warp_merge<true>(list, nullptr, n, R, key, 0);
+    }
+    for (int s = lane; s < R; s += 32) {
+        if (s < n) {
+            out_ids[u * R + s] = key_id(list[s]);
+            out_dist[u * R + s] = key_dist(list[s]);
+        } else {
+            out_ids[u * R + s] = -1;
+            out_dist[u * R + s] = __int_as_float(0x7f800000);
+        }
+    }
+    if (lane == 0) out_deg[u] = n;
+}
+
+cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
+                                  ReverseBuffers& b, int32_t* out_ids, float* out_dist, int32_t* out_deg,
+                                  cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const long long total = N * R;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.fill, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    const unsigned gb = (unsigned)cdivl(total, 256);
+    {
+        LaunchScope ls("k_e_count", s);
+        k_e_count<<<gb, 256, 0, s>>>(e_ids, total, b.cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = scan_counts(b.cnt, N, b.off, b.scan_tmp, b.scan_bytes, s)) != cudaSuccess) return e;
+    {
+        LaunchScope ls("k_e_fill", s);
+        k_e_fill<<<gb, 256, 0, s>>>(e_ids, e_dist, total, R, b.off, b.fill, b.rev);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int wpb = 4;
+    LaunchScope ls("k_e_merge", s);
+    k_e_merge<<<(unsigned)cdivl(N, wpb), wpb * 32, (size_t)wpb * R * 8, s>>>(e_ids, e_dist, e_cnt, N, R, b.off, b.rev,
+                                                                             out_ids, out_dist, out_deg);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- reachability fix
+__global__ void k_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) visited[i] = (i == entry) ? 1 : 0;
+    if (i == 0) {
+        frontier[0] = entry;
+        *fcount = 1;
+    }
+}
+
+cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry,
+                            cudaStream_t s) {
+    LaunchScope ls("k_bfs_init", s);
+    k_bfs_init<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, frontier, fcount, entry);
+    return cudaGetLastError();
+}
+
+// one level: thread per (frontier vertex, neighbour slot)
+__global__ void k_bfs_step(const int32_t* __restrict__ graph, int R, long long N, int32_t* __restrict__ visited,
+                           const int32_t* __restrict__ fin, const int32_t* __restrict__ fin_count,
+                           int32_t* __restrict__ fout, int32_t* __restrict__ fout_count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nf = *fin_count;
+    if (i >= nf * R) return;
+    const int32_t x = fin[i / R];
+    const int32_t y = graph[(long long)x * R + (i % R)];
+    if (y < 0 || y >= N) return;
+    if (visited[y] == 0 && atomicExch(visited + y, 1) == 0) fout[atomicAdd(fout_count, 1)] = y;
+}
+
+cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
+                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, cudaStream_t s) {
+    // grid sized for the largest possible frontier; threads beyond the live frontier exit
+    LaunchScope ls("k_bfs_step", s);
+    k_bfs_step<<<(unsigned)cdivl(N * R, 256), 256, 0, s>>>(graph, R, N, visited, fin, fin_count, fout, fout_count);
+    return cudaGetLastError();
+}
+
+__global__ void k_cc_init(const int32_t* __restrict__ visited, long long N, int32_t* __restrict__ label) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) label[i] = visited[i] ? -1 : (int32_t)i;
+}
+
+cudaError_t launch_cc_init(const int32_t* visited, long long N, int32_t* label, cudaStream_t s) {
+    LaunchScope ls("k_cc_init", s);
+    k_cc_init<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, label);
+    return cudaGetLastError();
+}
+
+// min-label propagation over the undirected edges between unreached vertices
+__global__ void k_cc_step(const int32_t* __restrict__ graph, int R, long long N, const int32_t* __restrict__ visited,
+                          int32_t* __restrict__ label, int32_t* __restrict__ changed) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * R) return;
+    const long long x = i / R;
+    if (visited[x]) return;
+    const int32_t y = graph[i];
+    if (y < 0 || y >= N || visited[y]) return;
+    const int32_t lx = label[x], ly = label[y];
+    if (lx < ly) {
+        if (atomicMin(label + y, lx) > lx) *changed = 1;
+    } else if (ly < lx) {
+        if (atomicMin(label + x, ly) > ly) *changed = 1;
+    }
+}
+
+cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32_t* visited, int32_t* label,
+                           int32_t* changed, cudaStream_t s) {
+    LaunchScope ls("k_cc_step", s);
+    k_cc_step<<<(unsigned)cdivl(N * R, 256), 256, 0, s>>>(graph, R, N, visited, label, changed);
+    return cudaGetLastError();
+}
+
+__global__ void k_rep_flags(const int32_t* __restrict__ visited, const int32_t* __restrict__ label, long long N,
+                            int32_t* __restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) flag[i] = (!visited[i] && label[i] == (int32_t)i) ? 1 : 0;
+}
+
+cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
+                             cudaStream_t s) {
+    LaunchScope ls("k_rep_flags", s);
+    k_rep_flags<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, label, N, flag);
+    return cudaGetLastError();
+}
+
+// ascending representatives: append x to the first search result p with room (one thread)
+__global__ void k_reach_assign(int32_t* __restrict__ graph, float* __restrict__ gdist, int32_t* __restrict__ deg,
+                               int R, const int32_t* __restrict__ reps, const long long* __restrict__ nreps,
+                               const int32_t* __restrict__ cand, const float* __restrict__ cdist, int beam,
+                               unsigned long long* attached) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long nr = *nreps;
+    unsigned long long att = 0;
+    for (long long r = 0; r < nr; ++r) {
+        const int32_t x = reps[r];
+        for (int t = 0; t < beam; ++t) {
+            const int32_t p = cand[r * beam + t];
+            if (p < 0) break;
+            if (deg[p] >= R) continue;
+            const float d = cdist[r * beam + t];
+            const uint64_t key = mkkey(d, x);
+            int32_t* li = graph + (long long)p * R;
+            float* ld = gdist + (long long)p * R;
+            int pos = deg[p];
+            while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
+                li[pos] = li[pos - 1];
+                ld[pos] = ld[pos - 1];
+                --pos;
+            }
+            li[pos] = x;
+            ld[pos] = d;
+            deg[p] += 1;
+            ++att;
+            break;
+        }
+    }
+    *attached += att;
+}
+
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int R, const int32_t* reps,
+                                const long long* nreps, const int32_t* cand, const float* cdist, int beam,
+                                unsigned long long* attached, cudaStream_t s) {
+    LaunchScope ls("k_reach_assign", s);
+    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, R, reps, nreps, cand, cdist, beam, attached);
+    return cudaGetLastError();
+}
+
+}  // namespace fgim

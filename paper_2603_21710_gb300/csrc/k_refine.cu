@@ -1,0 +1,710 @@
+// Stage (b): k-NNG refinement, Alg. 3 (Visit + Update) and Alg. 4 (indegree repair).
+//
+// Synchronous form of one refinement pass:
+//   Visit   reverse lists of new / old entries (counting sort by destination, then the
+//           rev_cap smallest (delta, source) per vertex), C_n(v) = new forward U new
+//           reverse, C_o(v) = (old forward U old reverse) \ C_n(v); forward new flags
+//           are cleared once the sets are built.
+//   Update  one CTA per vertex v evaluates every cross-graph pair of C_n(v)^2 U
+//           C_n(v) x C_o(v) as a register-tiled distance tile (rows C_n, columns C_n ++
+//           C_o, upper triangle in C_n), and emits a proposal "b for list(a)" only when
+//           b is not already in list(a) (membership bitmask built in shared memory
+//           from the candidates' lists) and (delta, b) beats list(a)'s worst key.
+//   Merge   proposals are grouped by target (counting sort) and each list becomes the
+//           top-k of its entries and its proposals, duplicates by id removed, inserted
+//           entries flagged new. The result does not depend on the order of proposals.
+// A proposal buffer that overflows marks the vertices whose proposals were dropped;
+// the host merges what fits and re-runs those vertices (their pairs are re-evaluated
+// against the updated lists), which yields the same final lists.
+#include "fgim_launch.h"
+
+namespace fgim {
+
+static inline long long cdivll(long long a, long long b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------- indegree
+__global__ void k_indegree(const int32_t* __restrict__ ids, long long total, int32_t* __restrict__ T,
+                           uint8_t* __restrict__ flags) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int32_t v = ids[i];
+    if (v >= 0) atomicAdd(T + v, 1);
+    if (flags) flags[i] &= (uint8_t)~FGIM_FLAG_REPLACED;
+}
+
+cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(T, 0, sizeof(int32_t) * N, s);
+    if (e != cudaSuccess) return e;
+    const long long total = N * k;
+    if (total == 0) return cudaSuccess;
+    LaunchScope ls("k_indegree", s);
+    k_indegree<<<(unsigned)cdivll(total, 256), 256, 0, s>>>(ids, total, T, clear_replaced ? flags : nullptr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- Visit
+__global__ void k_rev_count(const int32_t* __restrict__ ids, const uint8_t* __restrict__ flags, long long total,
+                            int32_t* __restrict__ cntN, int32_t* __restrict__ cntO) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int32_t v = ids[i];
+    if (v < 0) return;
+    atomicAdd((flags[i] & FGIM_FLAG_NEW) ? cntN + v : cntO + v, 1);
+}
+
+__global__ void k_rev_fill(const int32_t* __restrict__ ids, const float* __restrict__ dist,
+                           const uint8_t* __restrict__ flags, long long total, int k,
+                           const long long* __restrict__ offN, const long long* __restrict__ offO,
+                           int32_t* __restrict__ fillN, int32_t* __restrict__ fillO, uint64_t* __restrict__ revN,
+                           uint64_t* __restrict__ revO) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int32_t v = ids[i];
+    if (v < 0) return;
+    const int32_t u = (int32_t)(i / k);
+    const uint64_t key = mkkey(dist[i], u);
+    if (flags[i] & FGIM_FLAG_NEW) {
+        const int p = atomicAdd(fillN + v, 1);
+        revN[offN[v] + p] = key;
+    } else {
+        const int p = atomicAdd(fillO + v, 1);
+        revO[offO[v] + p] = key;
+    }
+}
+
+// the `cap` smallest (delta, source) keys of every reverse segment (warp per vertex)
+__global__ void __launch_bounds__(128) k_rev_select(const long long* __restrict__ off, const uint64_t* __restrict__ rev,
+                                                    long long N, int cap, int32_t* __restrict__ top,
+                                                    int32_t* __restrict__ ntop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long v = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (v >= N) return;
+    uint64_t* list = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * cap;
+    const long long b = off[v], m = off[v + 1] - off[v];
+    int n = 0;
+    for (long long c0 = 0; c0 < m; c0 += 32) {
+        const uint64_t key = (c0 + lane < m) ? rev[b + c0 + lane] : kEmptyKey;
+        n = warp_merge<false>(list, nullptr, n, cap, key, 0);
+    }
+    for (int s = lane; s < n; s += 32) top[v * cap + s] = key_id(list[s]);
+    if (lane == 0) ntop[v] = n;
+}
+
+// C_n(v), C_o(v) of every vertex (warp per vertex); clears the forward new flags
+__global__ void __launch_bounds__(128) k_build_cands(const int32_t* __restrict__ ids, uint8_t* __restrict__ flags,
+                                                     long long N, int k, const int32_t* __restrict__ topN,
+                                                     const int32_t* __restrict__ ntopN,
+                                                     const int32_t* __restrict__ topO,
+                                                     const int32_t* __restrict__ ntopO, int rev_cap,
+                                                     int32_t* __restrict__ cand, int32_t* __restrict__ nn_out,
+                                                     int32_t* __restrict__ no_out, int cmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long v = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (v >= N) return;
+    int32_t* C = reinterpret_cast<int32_t*>(smem) + (size_t)warp * cmax;
+    const unsigned lt = (1u << lane) - 1u;
+    int nn = 0;
+    // new forward neighbours
+    for (int t0 = 0; t0 < k; t0 += 32) {
+        const int t = t0 + lane;
+        int32_t id = -1;
+        bool take = false;
+        if (t < k) {
+            id = ids[v * k + t];
+            take = id >= 0 && (flags[v * k + t] & FGIM_FLAG_NEW);
+        }
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) C[nn + __popc(m & lt)] = id;
+        nn += __popc(m);
+    }
+    __syncwarp();
+    const int nfwd = nn;
+    // new reverse neighbours not already present
+    const int rn = ntopN[v];
+    for (int t0 = 0; t0 < rn; t0 += 32) {
+        const int t = t0 + lane;
+        int32_t id = -1;
+        bool take = false;
+        if (t < rn) {
+            id = topN[v * rev_cap + t];
+            take = true;
+            for (int s = 0; s < nfwd; ++s)
+                if (C[s] == id) { take = false; break; }
+        }
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) C[nn + __popc(m & lt)] = id;
+        nn += __popc(m);
+        __syncwarp();
+    }
+    int no = 0;
+    // old forward neighbours not in C_n
+    for (int t0 = 0; t0 < k; t0 += 32) {
+        const int t = t0 + lane;
+        int32_t id = -1;
+        bool take = false;
+        if (t < k) {
+            id = ids[v * k + t];
+            take = id >= 0 && !(flags[v * k + t] & FGIM_FLAG_NEW);
+            if (take)
+                for (int s = 0; s < nn; ++s)
+                    if (C[s] == id) { take = false; break; }
+        }
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) C[nn + no + __popc(m & lt)] = id;
+        no += __popc(m);
+        __syncwarp();
+    }
+    // old reverse neighbours not in C_n nor already in C_o
+    const int ro = ntopO[v];
+    const int nfo = no;
+    for (int t0 = 0; t0 < ro; t0 += 32) {
+        const int t = t0 + lane;
+        int32_t id = -1;
+        bool take = false;
+        if (t < ro) {
+            id = topO[v * rev_cap + t];
+            take = true;
+            for (int s = 0; s < nn + nfo; ++s)
+                if (C[s] == id) { take = false; break; }
+        }
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) C[nn + no + __popc(m & lt)] = id;
+        no += __popc(m);
+        __syncwarp();
+    }
+    for (int s = lane; s < nn + no; s += 32) cand[v * cmax + s] = C[s];
+    if (lane == 0) {
+        nn_out[v] = nn;
+        no_out[v] = no;
+    }
+    // Visit done: the forward new neighbours of v are old from now on
+    for (int t = lane; t < k; t += 32) flags[v * k + t] &= (uint8_t)~FGIM_FLAG_NEW;
+}
+
+cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s) {
+    const long long N = g.n;
+    const int k = g.k;
+    const long long total = N * k;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.cntN, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.cntO, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.fillN, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.fillO, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    const unsigned gb = (unsigned)cdivll(total, 256);
+    {
+        LaunchScope ls("k_rev_count", s);
+        k_rev_count<<<gb, 256, 0, s>>>(g.ids, g.flags, total, b.cntN, b.cntO);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = scan_counts(b.cntN, N, b.offN, b.scan_tmp, b.scan_bytes, s)) != cudaSuccess) return e;
+    if ((e = scan_counts(b.cntO, N, b.offO, b.scan_tmp, b.scan_bytes, s)) != cudaSuccess) return e;
+    {
+        LaunchScope ls("k_rev_fill", s);
+        k_rev_fill<<<gb, 256, 0, s>>>(g.ids, g.dist, g.flags, total, k, b.offN, b.offO, b.fillN, b.fillO, b.revN,
+                                      b.revO);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int wpb = 4;
+    const unsigned wb = (unsigned)cdivll(N, wpb);
+    {
+        LaunchScope ls("k_rev_select", s);
+        k_rev_select<<<wb, wpb * 32, (size_t)wpb * rev_cap * 8, s>>>(b.offN, b.revN, N, rev_cap, b.topN, b.ntopN);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_rev_select", s);
+        k_rev_select<<<wb, wpb * 32, (size_t)wpb * rev_cap * 8, s>>>(b.offO, b.revO, N, rev_cap, b.topO, b.ntopO);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_build_cands", s);
+        k_build_cands<<<wb, wpb * 32, (size_t)wpb * b.cmax * 4, s>>>(g.ids, g.flags, N, k, b.topN, b.ntopN, b.topO,
+                                                                     b.ntopO, rev_cap, b.cand, b.nn, b.no, b.cmax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------- Update
+constexpr int kJT = 64;       // block tile edge (pairs)
+constexpr int kJK = 32;       // floats of one K slice
+constexpr int kJP = kJK + 4;  // padded row stride (floats)
+constexpr int kJThreads = 256;
+
+struct JoinLayout {
+    int cid, csh, thr, cinv, hk, hv, mask, tiles, bytes, hs, words;
+};
+
+__host__ __device__ inline JoinLayout join_layout(int cm) {
+    JoinLayout l;
+    int hs = 64;
+    while (hs < 2 * cm) hs <<= 1;
+    l.hs = hs;
+    l.words = (cm + 31) >> 5;
+    int o = 0;
+    l.thr = o;
+    o += cm * 8;
+    l.cid = o;
+    o += ((cm * 4 + 15) & ~15);
+    l.csh = o;
+    o += ((cm * 4 + 15) & ~15);
+    l.cinv = o;
+    o += ((cm * 4 + 15) & ~15);
+    l.hk = o;
+    o += hs * 4;
+    l.hv = o;
+    o += hs * 4;
+    l.mask = o;
+    o += ((cm * l.words * 4 + 15) & ~15);
+    l.tiles = o;
+    o += 2 * 2 * kJT * kJP * 4;
+    l.bytes = o;
+    return l;
+}
+
+__device__ __forceinline__ int jhash(int32_t id, int hs) { return (int)(((uint32_t)id * 2654435761u) & (hs - 1)); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int sz = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int METRIC>
+__global__ void __launch_bounds__(kJThreads) k_join(ShardTable t, const float* __restrict__ X,
+                                                    const float* __restrict__ inv_norm, int k,
+                                                    const int32_t* __restrict__ ids, const float* __restrict__ dist,
+                                                    const int32_t* __restrict__ cand,
+                                                    const int32_t* __restrict__ nn_arr,
+                                                    const int32_t* __restrict__ no_arr, int cmax,
+                                                    const int32_t* __restrict__ vlist,
+                                                    int32_t* __restrict__ prop_tgt, uint64_t* __restrict__ prop_key,
+                                                    unsigned long long* prop_count, long long prop_cap,
+                                                    uint8_t* __restrict__ pending, unsigned long long* pairs_count,
+                                                    int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int tx = tid & 15, ty = tid >> 4;
+    const long long v = vlist ? (long long)vlist[blockIdx.x] : (long long)blockIdx.x;
+    const int nn = nn_arr[v];
+    const int nc = nn + no_arr[v];
+    if (nn == 0 || nc < 2) return;
+    const JoinLayout L = join_layout(cmax);
+    uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
+    int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
+    int32_t* csh = reinterpret_cast<int32_t*>(smem + L.csh);
+    float* cinv = reinterpret_cast<float*>(smem + L.cinv);
+    int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
+    int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
+    float* tiles = reinterpret_cast<float*>(smem + L.tiles);
+    const int d = t.dim;
+    const int W = L.words;
+    const int hs = L.hs;
+
+    for (int i = tid; i < nc; i += kJThreads) {
+        const int32_t c = cand[v * cmax + i];
+        cid[i] = c;
+        csh[i] = shard_of(t, c);
+        const int32_t wi = ids[(long long)c * k + k - 1];
+        thr[i] = wi < 0 ? kEmptyKey : mkkey(dist[(long long)c * k + k - 1], wi);
+        cinv[i] = (METRIC == FGIM_COSINE) ? inv_norm[c] : 1.f;
+    }
+    for (int i = tid; i < hs; i += kJThreads) hk[i] = -1;
+    for (int i = tid; i < nc * W; i += kJThreads) mask[i] = 0u;
+    __syncthreads();
+    for (int i = tid; i < nc; i += kJThreads) {
+        const int32_t c = cid[i];
+        int slot = jhash(c, hs);
+        for (int probe = 0; probe < hs; ++probe) {
+            if (atomicCAS(hk + slot, -1, c) == -1) {
+                hv[slot] = i;
+                break;
+            }
+            slot = (slot + 1) & (hs - 1);
+        }
+    }
+    __syncthreads();
+    // membership: bit (i, j) set when C[j] is already in list(C[i])
+    for (int idx = tid; idx < nc * k; idx += kJThreads) {
+        const int i = idx / k, s = idx - (idx / k) * k;
+        const int32_t e = ids[(long long)cid[i] * k + s];
+        if (e < 0) continue;
+        int slot = jhash(e, hs);
+        for (int probe = 0; probe < hs; ++probe) {
+            const int32_t h = hk[slot];
+            if (h == e) {
+                const int j = hv[slot];
+                atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
+                break;
+            }
+            if (h == -1) break;
+            slot = (slot + 1) & (hs - 1);
+        }
+    }
+    __syncthreads();
+
+    float* As = tiles;                        // [2][kJT][kJP]
+    float* Bs = tiles + 2 * kJT * kJP;        // [2][kJT][kJP]
+    const int nchunk = d >> 2;
+    const int nslice = (d + kJK - 1) / kJK;
+    unsigned long long my_pairs = 0;
+
+    for (int r0 = 0; r0 < nn; r0 += kJT) {
+        for (int c0 = 0; c0 < nc; c0 += kJT) {
+            const int cmaxj = min(c0 + kJT, nc) - 1;
+            if (cmaxj <= r0) continue;   // no pair with j > i in this tile
+            float acc[4][4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][bb][q] = 0.f;
+
+            auto load_slice = [&](int buf, int sl) {
+                for (int item = tid; item < 2 * kJT * (kJK / 4); item += kJThreads) {
+                    const int mat = item / (kJT * (kJK / 4));
+                    const int rem = item - mat * (kJT * (kJK / 4));
+                    const int r = rem / (kJK / 4);
+                    const int c = rem - r * (kJK / 4);
+                    const int idx = (mat == 0 ? r0 : c0) + r;
+                    const int lim = mat == 0 ? nn : nc;
+                    const int gc = sl * (kJK / 4) + c;
+                    const bool ok = idx < lim && gc < nchunk;
+                    const float* src = ok ? X + (long long)cid[idx] * d + gc * 4 : X;
+                    float* dst = (mat == 0 ? As : Bs) + (buf * kJT + r) * kJP + c * 4;
+                    cp_async16(dst, src, ok);
+                }
+                cp_async_commit();
+            };
+            load_slice(0, 0);
+            for (int sl = 0; sl < nslice; ++sl) {
+                const int buf = sl & 1;
+                if (sl + 1 < nslice) {
+                    load_slice(buf ^ 1, sl + 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                const float* Ab = As + buf * kJT * kJP;
+                const float* Bb = Bs + buf * kJT * kJP;
+#pragma unroll
+                for (int c = 0; c < kJK / 4; ++c) {
+                    float4 av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(Ab + (ty + 16 * a) * kJP + c * 4);
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) bv[bb] = *reinterpret_cast<const float4*>(Bb + (tx + 16 * bb) * kJP + c * 4);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) {
+                            if (METRIC == FGIM_L2SQ) {
+                                const float e0 = __fsub_rn(av[a].x, bv[bb].x), e1 = __fsub_rn(av[a].y, bv[bb].y);
+                                const float e2 = __fsub_rn(av[a].z, bv[bb].z), e3 = __fsub_rn(av[a].w, bv[bb].w);
+                                acc[a][bb][0] = fmaf(e0, e0, acc[a][bb][0]);
+                                acc[a][bb][1] = fmaf(e1, e1, acc[a][bb][1]);
+                                acc[a][bb][2] = fmaf(e2, e2, acc[a][bb][2]);
+                                acc[a][bb][3] = fmaf(e3, e3, acc[a][bb][3]);
+                            } else {
+                                acc[a][bb][0] = fmaf(av[a].x, bv[bb].x, acc[a][bb][0]);
+                                acc[a][bb][1] = fmaf(av[a].y, bv[bb].y, acc[a][bb][1]);
+                                acc[a][bb][2] = fmaf(av[a].z, bv[bb].z, acc[a][bb][2]);
+                                acc[a][bb][3] = fmaf(av[a].w, bv[bb].w, acc[a][bb][3]);
+                            }
+                        }
+                }
+                __syncthreads();
+            }
+            // epilogue: distances, filters, proposals
+            uint32_t emit = 0;   // bit (a*4+bb)*2 + dir
+            float dl[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int i = r0 + ty + 16 * a;
+                    const int j = c0 + tx + 16 * bb;
+                    const float s = __fadd_rn(__fadd_rn(acc[a][bb][0], acc[a][bb][1]),
+                                              __fadd_rn(acc[a][bb][2], acc[a][bb][3]));
+                    float dd;
+                    if (METRIC == FGIM_L2SQ) dd = s;
+                    else if (METRIC == FGIM_IP) dd = __fsub_rn(1.f, s);
+                    else dd = __fsub_rn(1.f, __fmul_rn(s, (i < nc && j < nc) ? __fmul_rn(cinv[i], cinv[j]) : 1.f));
+                    dl[a][bb] = dd;
+                    if (i < nn && j < nc && j > i && csh[i] != csh[j]) {
+                        ++my_pairs;
+                        if (!((mask[i * W + (j >> 5)] >> (j & 31)) & 1u) && mkkey(dd, cid[j]) < thr[i])
+                            emit |= 1u << ((a * 4 + bb) * 2);
+                        if (!((mask[j * W + (i >> 5)] >> (i & 31)) & 1u) && mkkey(dd, cid[i]) < thr[j])
+                            emit |= 1u << ((a * 4 + bb) * 2 + 1);
+                    }
+                }
+            const int cnt = __popc(emit);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtotal = __shfl_sync(kFull, incl, 31);
+            unsigned long long base = 0;
+            if (wtotal > 0) {
+                if (lane == 31) base = atomicAdd(prop_count, (unsigned long long)wtotal);
+                base = __shfl_sync(kFull, base, 31);
+                unsigned long long pos = base + (unsigned long long)(incl - cnt);
+                bool dropped = false;
+                uint32_t m = emit;
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int ab = bit >> 1, dir = bit & 1;
+                    const int a = ab >> 2, bb = ab & 3;
+                    const int i = r0 + ty + 16 * a;
+                    const int j = c0 + tx + 16 * bb;
+                    if (pos < (unsigned long long)prop_cap) {
+                        prop_tgt[pos] = dir == 0 ? cid[i] : cid[j];
+                        prop_key[pos] = mkkey(dl[a][bb], dir == 0 ? cid[j] : cid[i]);
+                    } else {
+                        dropped = true;
+                    }
+                    ++pos;
+                }
+                if (dropped) {
+                    pending[v] = 1;
+                    atomicOr(status, kErrOverflow);
+                }
+            }
+        }
+    }
+    // pairs evaluated by this CTA
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(kFull, my_pairs, o);
+    if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
+}
+
+cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
+                        RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
+                        int* status, cudaStream_t s) {
+    if (nv <= 0) return cudaSuccess;
+    const JoinLayout L = join_layout(b.cmax);
+    const size_t smem = L.bytes;
+    cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_J(MT)                                                                                        \
+    do {                                                                                                         \
+        e = cudaFuncSetAttribute(k_join<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+        if (e != cudaSuccess) break;                                                                             \
+        LaunchScope ls("k_join", s);                                                                             \
+        k_join<MT><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand, b.nn, b.no, \
+                                                         b.cmax, vlist, b.prop_tgt, b.prop_key, b.prop_count,    \
+                                                         b.prop_cap, b.pending, pairs, status);                  \
+        e = cudaGetLastError();                                                                                  \
+    } while (0)
+    if (metric == FGIM_L2SQ) FGIM_LAUNCH_J(FGIM_L2SQ);
+    else if (metric == FGIM_IP) FGIM_LAUNCH_J(FGIM_IP);
+    else FGIM_LAUNCH_J(FGIM_COSINE);
+#undef FGIM_LAUNCH_J
+    return e;
+}
+
+// ---------------------------------------------------------------------------- Merge
+__global__ void k_prop_count(const int32_t* __restrict__ tgt, long long P, int32_t* __restrict__ cnt) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) atomicAdd(cnt + tgt[i], 1);
+}
+
+__global__ void k_prop_scatter(const int32_t* __restrict__ tgt, const uint64_t* __restrict__ key, long long P,
+                               const long long* __restrict__ off, int32_t* __restrict__ fill,
+                               uint64_t* __restrict__ sorted) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const int32_t a = tgt[i];
+    const int p = atomicAdd(fill + a, 1);
+    sorted[off[a] + p] = key[i];
+}
+
+// list(a) <- top-k of list(a) U proposals(a), duplicates by id removed (warp per target)
+__global__ void __launch_bounds__(128) k_prop_merge(const long long* __restrict__ off,
+                                                    const uint64_t* __restrict__ sorted, long long N, int k,
+                                                    int32_t* __restrict__ ids, float* __restrict__ dist,
+                                                    uint8_t* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long a = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (a >= N) return;
+    const long long b = off[a], m = off[a + 1] - off[a];
+    if (m == 0) return;
+    uint64_t* list = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * k;
+    uint8_t* aux = smem + (size_t)(blockDim.x >> 5) * k * 8 + (size_t)warp * k;
+    int n = 0;
+    for (int s0 = 0; s0 < k; s0 += 32) {
+        const int s = s0 + lane;
+        bool valid = false;
+        if (s < k) {
+            const int32_t id = ids[a * k + s];
+            valid = id >= 0;
+            list[s] = valid ? mkkey(dist[a * k + s], id) : kEmptyKey;
+            aux[s] = flags[a * k + s];
+        }
+        n += __popc(__ballot_sync(kFull, valid));
+    }
+    __syncwarp();
+    for (long long c0 = 0; c0 < m; c0 += 32) {
+        const uint64_t key = (c0 + lane < m) ? sorted[b + c0 + lane] : kEmptyKey;
+        n = warp_merge<true>(list, aux, n, k, key, FGIM_FLAG_NEW);
+    }
+    for (int s = lane; s < k; s += 32) {
+        if (s < n) {
+            ids[a * k + s] = key_id(list[s]);
+            dist[a * k + s] = key_dist(list[s]);
+            flags[a * k + s] = aux[s];
+        } else {
+            ids[a * k + s] = -1;
+            dist[a * k + s] = __int_as_float(0x7f800000);
+            flags[a * k + s] = 0;
+        }
+    }
+}
+
+cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long P, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    const long long N = g.n;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.pcnt, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.pfill, 0, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    const unsigned gp = (unsigned)cdivll(P, 256);
+    {
+        LaunchScope ls("k_prop_count", s);
+        k_prop_count<<<gp, 256, 0, s>>>(b.prop_tgt, P, b.pcnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = scan_counts(b.pcnt, N, b.poff, b.scan_tmp, b.scan_bytes, s)) != cudaSuccess) return e;
+    {
+        LaunchScope ls("k_prop_scatter", s);
+        k_prop_scatter<<<gp, 256, 0, s>>>(b.prop_tgt, b.prop_key, P, b.poff, b.pfill, b.prop_sorted);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int wpb = 4;
+    LaunchScope ls("k_prop_merge", s);
+    k_prop_merge<<<(unsigned)cdivll(N, wpb), wpb * 32, (size_t)wpb * g.k * 9, s>>>(b.poff, b.prop_sorted, N, g.k,
+                                                                                   g.ids, g.dist, g.flags);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- Alg. 4
+__global__ void k_zero_flags(const int32_t* __restrict__ T, long long N, int32_t* __restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) flag[i] = T[i] == 0;
+}
+
+cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    LaunchScope ls("k_zero_flags", s);
+    k_zero_flags<<<(unsigned)cdivll(N, 256), 256, 0, s>>>(T, N, flag);
+    return cudaGetLastError();
+}
+
+__global__ void k_nonzero_u8(const uint8_t* __restrict__ v, long long N, int32_t* __restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) flag[i] = v[i] != 0;
+}
+
+cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    LaunchScope ls("k_nonzero_u8", s);
+    k_nonzero_u8<<<(unsigned)cdivll(N, 256), 256, 0, s>>>(v, N, flag);
+    return cudaGetLastError();
+}
+
+// Alg. 4 in ascending v* order by one warp: exact sequential semantics.
+__global__ void __launch_bounds__(32) k_repair(int32_t* __restrict__ ids, float* __restrict__ dist,
+                                               uint8_t* __restrict__ flags, long long N, int k,
+                                               int32_t* __restrict__ T, const int32_t* __restrict__ zeros,
+                                               const long long* __restrict__ nzeros,
+                                               unsigned long long* repaired, int* status) {
+    const int lane = lane_id();
+    const long long nz = *nzeros;
+    unsigned long long done_count = 0;
+    for (long long z = 0; z < nz; ++z) {
+        const long long vs = zeros[z];
+        if (vs < 0 || vs >= N) {
+            if (lane == 0) atomicOr(status, kErrBounds);
+            continue;
+        }
+        // lines 3-4: neighbours v of v*, closest first
+        for (int a = 0; a < k; ++a) {
+            const int32_t v = ids[vs * k + a];
+            if (v < 0) break;
+            if (v >= N) {
+                if (lane == 0) atomicOr(status, kErrBounds);
+                break;
+            }
+            const float dvs = dist[vs * k + a];
+            // line 5-6: farthest entry of N(v) that is not replaced and has T > 1
+            int best = -1;
+            for (int r = (k - 1) >> 5; r >= 0 && best < 0; --r) {
+                const int s = r * 32 + lane;
+                bool el = false;
+                if (s < k) {
+                    const int32_t e = ids[(long long)v * k + s];
+                    el = e >= 0 && e < N && !(flags[(long long)v * k + s] & FGIM_FLAG_REPLACED) && T[e] > 1;
+                }
+                const unsigned m = __ballot_sync(kFull, el);
+                if (m) best = r * 32 + 31 - __clz(m);
+            }
+            if (best < 0) continue;
+            // lines 7-11: replace, mark, update T, re-sort N(v)
+            if (lane == 0) {
+                int32_t* li = ids + (long long)v * k;
+                float* ld = dist + (long long)v * k;
+                uint8_t* lf = flags + (long long)v * k;
+                const int32_t old = li[best];
+                T[old] -= 1;
+                T[vs] += 1;
+                const uint64_t key = mkkey(dvs, (int32_t)vs);
+                int pos = best;
+                while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
+                    li[pos] = li[pos - 1];
+                    ld[pos] = ld[pos - 1];
+                    lf[pos] = lf[pos - 1];
+                    --pos;
+                }
+                while (pos + 1 < k && li[pos + 1] >= 0 && mkkey(ld[pos + 1], li[pos + 1]) < key) {
+                    li[pos] = li[pos + 1];
+                    ld[pos] = ld[pos + 1];
+                    lf[pos] = lf[pos + 1];
+                    ++pos;
+                }
+                li[pos] = (int32_t)vs;
+                ld[pos] = dvs;
+                lf[pos] = FGIM_FLAG_NEW | FGIM_FLAG_REPLACED;
+                ++done_count;
+            }
+            __syncwarp();
+            __threadfence_block();
+            break;
+        }
+    }
+    if (lane == 0 && done_count) atomicAdd(repaired, done_count);
+}
+
+cudaError_t launch_repair(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
+                          unsigned long long* repaired, int* status, cudaStream_t s) {
+    LaunchScope ls("k_repair", s);
+    k_repair<<<1, 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, repaired, status);
+    return cudaGetLastError();
+}
+
+}  // namespace fgim

@@ -1,0 +1,316 @@
+// Stage (a) and evaluation search: Alg. 1 (KNNSearch) and Alg. 2 (PGs -> k-NNG).
+//
+// One warp runs one beam search. The pool C (<= L keys, sorted by (delta, id)) and its
+// "expanded" marks live in shared memory; each expansion reads the expanded vertex's
+// adjacency row (one id per lane), drops ids already evaluated, computes the distances
+// of the rest (one neighbour per lane, canonical distance, query in shared memory) and
+// merges them into the pool with warp_merge.
+//
+// Evaluated ids are remembered in a small direct-mapped table that may forget an id
+// when another id lands on its slot (never the reverse). A forgotten id is evaluated
+// again: its key equals its earlier key, so it is dropped if it is still in the pool,
+// and otherwise it cannot beat the pool's worst entry (once the pool is full its worst
+// key only decreases, and an id leaves the pool or is refused only when L better keys
+// are present). The pool therefore evolves exactly as with an exact visited set
+// (Alg. 1's "not visited" test); only the number of distance evaluations grows.
+#include "fgim_internal.cuh"
+#include "fgim_launch.h"
+
+namespace fgim {
+
+__device__ __forceinline__ int ht_slot(int v, int bits) { return (int)(((uint32_t)v * 2654435761u) >> (32 - bits)); }
+
+struct WarpCounters {
+    long long ndc = 0;
+    long long hops = 0;
+};
+
+// Alg. 1 over one graph whose rows are Xt[v] / adj[v * M] for local ids v < nt. Keys carry
+// global ids (local + id_off). Returns the pool size (<= L); the pool stays sorted.
+template <int METRIC>
+__device__ int beam_search(const float* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
+                           int M, long long nt, int ep, long long id_off, const float* q, float qinv, int d, int L,
+                           uint64_t* pool, uint8_t* pflag, int32_t* ht, int htbits, WarpCounters& ctr, int* status) {
+    const int lane = lane_id();
+    const int H = 1 << htbits;
+    for (int s = lane; s < H; s += 32) ht[s] = -1;
+    __syncwarp();
+    uint64_t key = kEmptyKey;
+    if (ep < 0 || ep >= nt) {
+        if (lane == 0) atomicOr(status, kErrBounds);
+        return 0;
+    }
+    if (lane == 0) {
+        float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[ep]) : 1.f;
+        key = mkkey(delta_fn<METRIC>(q, Xt + (long long)ep * d, d, inv), (int32_t)(ep + id_off));
+        ht[ht_slot(ep, htbits)] = ep;
+        ctr.ndc++;
+    }
+    int n = warp_merge<false>(pool, pflag, 0, L, key, 0);
+    // every vertex is expanded at most once, so nt + 1 iterations always suffice
+    for (long long it = 0; it <= nt; ++it) {
+        int first = -1;
+        for (int base = 0; base < n; base += 32) {
+            const int p = base + lane;
+            const unsigned m = __ballot_sync(kFull, p < n && pflag[p] == 0);
+            if (m) {
+                first = base + __ffs(m) - 1;
+                break;
+            }
+        }
+        if (first < 0) return n;
+        const long long u = (long long)key_id(pool[first]) - id_off;
+        __syncwarp();
+        if (lane == 0) {
+            pflag[first] = 1;
+            ctr.hops++;
+        }
+        __syncwarp();
+        const int32_t* row = adj + u * M;
+        for (int c0 = 0; c0 < M; c0 += 32) {
+            int v = (c0 + lane < M) ? row[c0 + lane] : -1;
+            if (v >= nt) {
+                atomicOr(status, kErrBounds);
+                v = -1;
+            }
+            if (v >= 0) {
+                const int s = ht_slot(v, htbits);
+                if (ht[s] == v) v = -1;
+                else ht[s] = v;
+            }
+            uint64_t cand = kEmptyKey;
+            if (v >= 0) {
+                float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[v]) : 1.f;
+                cand = mkkey(delta_fn<METRIC>(q, Xt + (long long)v * d, d, inv), (int32_t)(v + id_off));
+                ctr.ndc++;
+            }
+            n = warp_merge<false>(pool, pflag, n, L, cand, 0);
+        }
+    }
+    if (lane == 0) atomicOr(status, kErrTimeout);
+    return n;
+}
+
+__device__ __forceinline__ void warp_add_counters(WarpCounters& c, unsigned long long* out) {
+    long long a = c.ndc, b = c.hops;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+    }
+    if (lane_id() == 0 && out) {
+        atomicAdd(out + 0, (unsigned long long)a);
+        atomicAdd(out + 1, (unsigned long long)b);
+    }
+}
+
+// shared-memory layout of one warp; all offsets multiples of 16 bytes
+struct WarpLayout {
+    int q, pool, pflag, ht, res, bytes;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int kres) {
+    WarpLayout w;
+    int o = 0;
+    w.q = o;
+    o += align16(d * 4);
+    w.pool = o;
+    o += align16(L * 8);
+    w.pflag = o;
+    o += align16(L);
+    w.ht = o;
+    o += align16((1 << htbits) * 4);
+    w.res = o;
+    o += align16(kres * 8);
+    w.bytes = o;
+    return w;
+}
+
+// Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
+// own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
+// (delta, id), write ids / distances / new flags.
+template <int METRIC>
+__global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* __restrict__ X,
+                                                     const float* __restrict__ inv_norm, long long N, int k, int L,
+                                                     int htbits, int32_t* __restrict__ out_ids,
+                                                     float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
+                                                     unsigned long long* counters, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= N) return;
+    const int d = t.dim;
+    const WarpLayout lay = warp_layout(d, L, htbits, k);
+    unsigned char* base = smem + (size_t)warp * lay.bytes;
+    float* q = reinterpret_cast<float*>(base + lay.q);
+    uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
+    uint8_t* pflag = base + lay.pflag;
+    int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
+    uint64_t* res = reinterpret_cast<uint64_t*>(base + lay.res);
+
+    const float4* src = reinterpret_cast<const float4*>(X + g * d);
+    float4* q4 = reinterpret_cast<float4*>(q);
+    for (int c = lane; c < (d >> 2); c += 32) q4[c] = src[c];
+    const float qinv = (METRIC == FGIM_COSINE) ? inv_norm[g] : 1.f;
+    __syncwarp();
+
+    WarpCounters ctr;
+    const int i = shard_of(t, g);
+    const long long u = g - t.off[i];
+    const long long ni = t.off[i + 1] - t.off[i];
+    int nres = 0;
+    // Alg. 2 line 5: local candidate neighbours, mapped to global ids by phi
+    const int Mi = t.M[i];
+    const int32_t* arow = t.adj[i] + u * Mi;
+    for (int c0 = 0; c0 < Mi; c0 += 32) {
+        int v = (c0 + lane < Mi) ? arow[c0 + lane] : -1;
+        if (v >= ni) {
+            atomicOr(status, kErrBounds);
+            v = -1;
+        }
+        uint64_t cand = kEmptyKey;
+        if (v >= 0 && v != u) {
+            const long long gv = t.off[i] + v;
+            float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, inv_norm[gv]) : 1.f;
+            cand = mkkey(delta_fn<METRIC>(q, X + gv * d, d, inv), (int32_t)gv);
+            ctr.ndc++;
+        }
+        nres = warp_merge<true>(res, nullptr, nres, k, cand, 0);
+    }
+    // Alg. 2 lines 6-7: cross querying of every other index
+    for (int j = 0; j < t.h; ++j) {
+        if (j == i) continue;
+        const long long nj = t.off[j + 1] - t.off[j];
+        const int np = beam_search<METRIC>(X + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr, t.adj[j],
+                                           t.M[j], nj, t.entry[j], t.off[j], q, qinv, d, L, pool, pflag, ht, htbits,
+                                           ctr, status);
+        for (int c0 = 0; c0 < np; c0 += 32) {
+            const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
+            nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
+        }
+    }
+    // Alg. 2 lines 8-10: sorted, resized to k
+    for (int s = lane; s < k; s += 32) {
+        const long long o = g * k + s;
+        if (s < nres) {
+            out_ids[o] = key_id(res[s]);
+            out_dist[o] = key_dist(res[s]);
+            out_flags[o] = FGIM_FLAG_NEW;
+        } else {
+            out_ids[o] = -1;
+            out_dist[o] = __int_as_float(0x7f800000);
+            out_flags[o] = 0;
+        }
+    }
+    warp_add_counters(ctr, counters);
+}
+
+// Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
+// (qids == nullptr) or rows qids[i] of X.
+template <int METRIC>
+__global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, const float* __restrict__ inv_norm,
+                                                long long n, int d, const int32_t* __restrict__ graph, int R,
+                                                int entry, const float* __restrict__ Q,
+                                                const float* __restrict__ q_inv, const int32_t* __restrict__ qids,
+                                                long long nq, int topk, int L, int htbits,
+                                                int32_t* __restrict__ out_ids, float* __restrict__ out_dist,
+                                                unsigned long long* counters, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long qi = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (qi >= nq) return;
+    const WarpLayout lay = warp_layout(d, L, htbits, 0);
+    unsigned char* base = smem + (size_t)warp * lay.bytes;
+    float* q = reinterpret_cast<float*>(base + lay.q);
+    uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
+    uint8_t* pflag = base + lay.pflag;
+    int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
+    const float* qsrc = qids ? X + (long long)qids[qi] * d : Q + qi * d;
+    const float4* src = reinterpret_cast<const float4*>(qsrc);
+    float4* q4 = reinterpret_cast<float4*>(q);
+    for (int c = lane; c < (d >> 2); c += 32) q4[c] = src[c];
+    float qinv = 1.f;
+    if (METRIC == FGIM_COSINE) qinv = qids ? inv_norm[qids[qi]] : q_inv[qi];
+    __syncwarp();
+    WarpCounters ctr;
+    const int np = beam_search<METRIC>(X, inv_norm, graph, R, n, entry, 0, q, qinv, d, L, pool, pflag, ht, htbits,
+                                       ctr, status);
+    for (int s = lane; s < topk; s += 32) {
+        if (s < np) {
+            out_ids[qi * topk + s] = key_id(pool[s]);
+            out_dist[qi * topk + s] = key_dist(pool[s]);
+        } else {
+            out_ids[qi * topk + s] = -1;
+            out_dist[qi * topk + s] = __int_as_float(0x7f800000);
+        }
+    }
+    warp_add_counters(ctr, counters);
+}
+
+// ---------------------------------------------------------------------------- host
+static int ht_bits_for(int L) {
+    int want = 32 * L;
+    int b = 9;
+    while ((1 << b) < want && b < 12) ++b;
+    return b;
+}
+
+cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float* inv_norm, long long N, int metric,
+                               int k, int L, fgim_knng* out, unsigned long long* counters, int* status,
+                               cudaStream_t s) {
+    const int htbits = ht_bits_for(L);
+    const int wpb = 4;
+    const WarpLayout lay = warp_layout(t.dim, L, htbits, k);
+    const size_t smem = (size_t)lay.bytes * wpb;
+    const long long blocks = (N + wpb - 1) / wpb;
+    if (blocks <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_CQ(MT)                                                                                         \
+    do {                                                                                                           \
+        e = cudaFuncSetAttribute(k_cross_query<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+        if (e != cudaSuccess) break;                                                                               \
+        LaunchScope ls("k_cross_query", s);                                                                        \
+        k_cross_query<MT><<<(unsigned)blocks, wpb * 32, smem, s>>>(t, X, inv_norm, N, k, L, htbits, out->ids,     \
+                                                                   out->dist, out->flags, counters, status);       \
+        e = cudaGetLastError();                                                                                    \
+    } while (0)
+    if (metric == FGIM_L2SQ) FGIM_LAUNCH_CQ(FGIM_L2SQ);
+    else if (metric == FGIM_IP) FGIM_LAUNCH_CQ(FGIM_IP);
+    else FGIM_LAUNCH_CQ(FGIM_COSINE);
+#undef FGIM_LAUNCH_CQ
+    return e;
+}
+
+cudaError_t launch_search(const float* X, const float* inv_norm, long long n, int d, int metric, const int32_t* graph,
+                          int R, int entry, const float* Q, const float* q_inv, const int32_t* qids, long long nq,
+                          int topk, int L, int32_t* out_ids, float* out_dist, unsigned long long* counters,
+                          int* status, cudaStream_t s) {
+    const int htbits = ht_bits_for(L);
+    const int wpb = 4;
+    const WarpLayout lay = warp_layout(d, L, htbits, 0);
+    const size_t smem = (size_t)lay.bytes * wpb;
+    const long long blocks = (nq + wpb - 1) / wpb;
+    if (blocks <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_S(MT)                                                                                          \
+    do {                                                                                                           \
+        e = cudaFuncSetAttribute(k_search<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+        if (e != cudaSuccess) break;                                                                               \
+        LaunchScope ls("k_search", s);                                                                             \
+        k_search<MT><<<(unsigned)blocks, wpb * 32, smem, s>>>(X, inv_norm, n, d, graph, R, entry, Q, q_inv, qids, \
+                                                              nq, topk, L, htbits, out_ids, out_dist, counters,   \
+                                                              status);                                             \
+        e = cudaGetLastError();                                                                                    \
+    } while (0)
+    if (metric == FGIM_L2SQ) FGIM_LAUNCH_S(FGIM_L2SQ);
+    else if (metric == FGIM_IP) FGIM_LAUNCH_S(FGIM_IP);
+    else FGIM_LAUNCH_S(FGIM_COSINE);
+#undef FGIM_LAUNCH_S
+    return e;
+}
+
+}  // namespace fgim

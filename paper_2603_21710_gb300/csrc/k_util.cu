@@ -1,0 +1,152 @@
+// Small building blocks: exclusive scans, compaction by flags, fills, inverse norms.
+#include "fgim_launch.h"
+
+namespace fgim {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr long long kScanTile = (long long)kScanThreads * kScanItems;
+
+template <typename TIN>
+__global__ void __launch_bounds__(kScanThreads) k_scan_block(const TIN* __restrict__ in, long long n,
+                                                             long long* __restrict__ out,
+                                                             long long* __restrict__ bsum) {
+    __shared__ long long sh[kScanThreads];
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)tid * kScanItems;
+    long long v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long idx = base + i;
+        v[i] = idx < n ? (long long)in[idx] : 0;
+        s += v[i];
+    }
+    sh[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        long long add = tid >= off ? sh[tid - off] : 0;
+        __syncthreads();
+        sh[tid] += add;
+        __syncthreads();
+    }
+    long long run = sh[tid] - s;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (tid == kScanThreads - 1) bsum[blockIdx.x] = sh[tid];
+}
+
+__global__ void k_scan_add(long long* __restrict__ out, long long n, const long long* __restrict__ boff) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += boff[i / kScanTile];
+}
+
+__global__ void k_copy1(long long* dst, const long long* src) { *dst = *src; }
+
+static long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+size_t scan_scratch_bytes(long long n) {
+    size_t words = 0;
+    long long m = n;
+    do {
+        long long blocks = cdiv(m > 0 ? m : 1, kScanTile);
+        words += 2 * blocks + 1;
+        m = blocks;
+    } while (m > 1);
+    return (words + 8) * sizeof(long long);
+}
+
+template <typename TIN>
+static cudaError_t scan_impl(const TIN* in, long long n, long long* out, long long* scratch, cudaStream_t s) {
+    const long long blocks = cdiv(n > 0 ? n : 1, kScanTile);
+    long long* bsum = scratch;
+    long long* boff = scratch + blocks;
+    {
+        LaunchScope ls("k_scan_block", s);
+        k_scan_block<TIN><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, out, bsum);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (blocks == 1) {
+        LaunchScope ls("k_copy1", s);
+        k_copy1<<<1, 1, 0, s>>>(out + n, bsum);
+        return cudaGetLastError();
+    }
+    e = scan_impl<long long>(bsum, blocks, boff, scratch + 2 * blocks + 1, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        LaunchScope ls("k_scan_add", s);
+        k_scan_add<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, n, boff);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    LaunchScope ls("k_copy1", s);
+    k_copy1<<<1, 1, 0, s>>>(out + n, boff + blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_counts(const int32_t* in, long long n, long long* out, void* scratch, size_t scratch_bytes,
+                        cudaStream_t s) {
+    if (scratch_bytes < scan_scratch_bytes(n)) return cudaErrorInvalidValue;
+    return scan_impl<int32_t>(in, n, out, reinterpret_cast<long long*>(scratch), s);
+}
+
+__global__ void k_compact(const int32_t* __restrict__ flag, long long n, const long long* __restrict__ off,
+                          int32_t* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[off[i]] = (int32_t)i;
+}
+
+cudaError_t compact_flags(const int32_t* flag, long long n, int32_t* out, long long* offsets, void* scan_scratch,
+                          size_t scan_bytes, cudaStream_t s) {
+    cudaError_t e = scan_counts(flag, n, offsets, scan_scratch, scan_bytes, s);
+    if (e != cudaSuccess || n == 0) return e;
+    LaunchScope ls("k_compact", s);
+    k_compact<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(flag, n, offsets, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_i32(int32_t* p, long long n, int32_t v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_fill_i32", s);
+    k_fill_i32<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+// 1 / ||x|| of every row (warp per row), used by the cosine metric
+__global__ void k_inv_norms(const float* __restrict__ X, long long n, int d, float* __restrict__ inv) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float4* x = reinterpret_cast<const float4*>(X + row * d);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int c = lane; c < (d >> 2); c += 32) {
+        float4 v = x[c];
+        s0 = fmaf(v.x, v.x, s0);
+        s1 = fmaf(v.y, v.y, s1);
+        s2 = fmaf(v.z, v.z, s2);
+        s3 = fmaf(v.w, v.w, s3);
+    }
+    float s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) inv[row] = s > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(s)) : 0.f;
+}
+
+cudaError_t launch_inv_norms(const float* X, long long n, int d, float* inv, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_inv_norms", s);
+    k_inv_norms<<<(unsigned)cdiv(n * 32, 256), 256, 0, s>>>(X, n, d, inv);
+    return cudaGetLastError();
+}
+
+}  // namespace fgim

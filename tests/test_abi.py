@@ -1,0 +1,91 @@
+"""The C ABI library loads, exports every entry point include/fgim.h declares, and rejects
+bad arguments on the host before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "fgim.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgim_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_21710_gb300 import _lib
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "fgim_merge" in names and "fgim_search" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_2603_21710_gb300 import _lib
+    assert set(_declared()) <= set(_lib.EXPORTS)
+
+
+def test_struct_layouts_match_header():
+    from paper_2603_21710_gb300 import _lib
+    assert ctypes.sizeof(_lib.Shard) == 32
+    assert ctypes.sizeof(_lib.Params) == 64
+    assert ctypes.sizeof(_lib.KNNG) == 40
+    assert ctypes.sizeof(_lib.Graph) == 40
+
+
+def _params(**kw):
+    from paper_2603_21710_gb300 import _lib
+    p = _lib.Params()
+    p.dim, p.dtype, p.metric, p.k, p.R, p.alpha, p.L, p.iters = 32, 0, 0, 16, 32, 1.2, 0, 3
+    for a, v in kw.items():
+        setattr(p, a, v)
+    return p
+
+
+@pytest.mark.parametrize("kw", [dict(dim=30), dict(k=0), dict(k=200), dict(R=0), dict(alpha=float("nan")),
+                                dict(L=500), dict(metric=7), dict(iters=-1), dict(dtype=3)])
+def test_bad_params_rejected_on_host(lib, kw):
+    from paper_2603_21710_gb300 import _lib
+    sh = (_lib.Shard * 2)()
+    buf = ctypes.create_string_buffer(4096 + 16)
+    base = (ctypes.addressof(buf) + 15) & ~15
+    for i in range(2):
+        sh[i] = _lib.Shard(base, base, 4, 4, 0, 0)
+    g = _lib.Graph(base, base, base, 8, 32, 0)
+    p = _params(**kw)
+    st = lib.fgim_merge(sh, 2, ctypes.byref(p), None, ctypes.byref(g), None)
+    assert st in (_lib.FGIM_EINVAL, _lib.FGIM_EUNSUPPORTED)
+    assert lib.fgim_last_error()
+
+
+def test_bad_shards_rejected_on_host(lib):
+    from paper_2603_21710_gb300 import _lib
+    buf = ctypes.create_string_buffer(4096 + 16)
+    base = (ctypes.addressof(buf) + 15) & ~15
+    g = _lib.Graph(base, base, base, 8, 32, 0)
+    p = _params()
+    sh = (_lib.Shard * 2)()
+    sh[0] = _lib.Shard(base, base, 4, 4, 0, 0)
+    sh[1] = _lib.Shard(base, base, 4, 4, 9, 0)       # entry out of range
+    assert lib.fgim_merge(sh, 2, ctypes.byref(p), None, ctypes.byref(g), None) == _lib.FGIM_EINVAL
+    sh[1] = _lib.Shard(base + 4, base, 4, 4, 0, 0)   # misaligned vectors
+    assert lib.fgim_merge(sh, 2, ctypes.byref(p), None, ctypes.byref(g), None) == _lib.FGIM_EINVAL
+    assert lib.fgim_merge(sh, 1, ctypes.byref(p), None, ctypes.byref(g), None) == _lib.FGIM_EINVAL  # h < 2
+    g2 = _lib.Graph(base, base, base, 9, 32, 0)     # wrong output shape
+    sh[1] = _lib.Shard(base, base, 4, 4, 0, 0)
+    assert lib.fgim_merge(sh, 2, ctypes.byref(p), None, ctypes.byref(g2), None) == _lib.FGIM_EINVAL
+
+
+def test_strerror_and_version(lib):
+    assert lib.fgim_strerror(0) == b"ok"
+    assert lib.fgim_strerror(-1) == b"invalid argument"
+    assert b"sm_103a" in lib.fgim_version()

@@ -1,0 +1,324 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, stage by stage.
+
+Each stage receives the SAME input on both sides (the oracle's output of the previous
+stage), so the comparison isolates one kernel family. Exact stages must satisfy the
+list rule of tests/_parity.py; the approximate stage (beam search) must give
+bit-identical rows for almost every query and the same recall within 0.5 point.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import _parity as PR
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _inp(w, graphs):
+    import paper_2603_21710_gb300 as fg
+    dev = _dev()
+    X = torch.from_numpy(w.X).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    return fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs],
+                                   metric={0: "l2", 1: "ip", 2: "cos"}[w.metric])
+
+
+def _to_dev(g: "O.KNNG"):
+    dev = _dev()
+    return {"ids": torch.from_numpy(g.ids.copy()).to(dev), "dist": torch.from_numpy(g.dist.copy()).to(dev),
+            "flags": torch.from_numpy(g.flags.copy()).to(dev)}
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small(small_problem):
+    w, graphs, P = small_problem
+    return w, graphs, P, _inp(w, graphs)
+
+
+@pytest.fixture(scope="module")
+def sift_like():
+    """Sift-like recipe (integer values 0..255, d=128, 4 shards) at N=40,000: FP32 sums are exact."""
+    from synth import gen, pgbuild
+    w = gen.make("medium", N=40_000, nq=500, n_centers=40)
+    graphs = pgbuild.build_all(w)
+    P = O.Problem.from_workload(w, graphs)
+    return w, graphs, P, _inp(w, graphs)
+
+
+# --------------------------------------------------------------------------- stage (a)
+def test_cross_query_small(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    g = fg.cross_query(inp, w.k)
+    o, L, _ = O.stage_a(P, w.k)
+    gi, gd = _np(g["ids"]), _np(g["dist"])
+    PR.check_lists(gi, gd, w.N)
+    assert np.all(_np(g["flags"])[gi >= 0] == fg.FLAG_NEW)
+    same = np.all(gi == o.ids, 1).mean()
+    assert same >= 0.99, same
+    # where the ids agree, distances agree within the FP32 tolerance
+    m = gi == o.ids
+    assert np.all(PR.close(gd[m], o.dist[m]))
+    rng = np.random.default_rng(3)
+    samp = rng.choice(w.N, 1000, replace=False)
+    tid, _ = O.knn_exact(w.X, w.X[samp], w.k, w.metric, exclude=samp)
+    assert abs(O.recall_at(gi[samp], tid, w.k) - O.recall_at(o.ids[samp], tid, w.k)) <= 0.005
+
+
+def test_cross_query_integer_data_bit_exact(sift_like):
+    """Integer inputs make every FP32 partial sum exact: the GPU rows equal the oracle's bit for bit."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    g = fg.cross_query(inp, w.k)
+    o, L, ost = O.stage_a(P, w.k)
+    assert L == 22
+    assert np.array_equal(_np(g["ids"]), o.ids)
+    assert np.array_equal(_np(g["dist"]), o.dist)
+    # the GPU's lossy visited table may re-evaluate, never skip: its count is >= the oracle's
+    assert g["stats"]["ndc"] >= ost["ndc"]
+
+
+# --------------------------------------------------------------------------- stage (b)
+def test_refine_pass_small(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    st = fg.refine_pass(inp, g)
+    O.refine_iter(P, o)
+    bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)
+    assert len(bad) == 0, bad[:10]
+    same = np.all(_np(g["ids"]) == o.ids, 1)
+    assert np.array_equal(_np(g["flags"])[same], o.flags[same])
+    assert st["join_pairs"] > 0
+
+
+def test_refine_pass_integer_bit_exact(sift_like):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    st = fg.refine_pass(inp, g)
+    ost = O.refine_iter(P, o)
+    assert np.array_equal(_np(g["ids"]), o.ids)
+    assert np.array_equal(_np(g["dist"]), o.dist)
+    assert np.array_equal(_np(g["flags"]), o.flags)
+    assert st["join_pairs"] == ost["pairs"]
+    # a second pass (only new entries join) stays identical too
+    fg.refine_pass(inp, g)
+    O.refine_iter(P, o)
+    assert np.array_equal(_np(g["ids"]), o.ids)
+
+
+def test_refine_pass_small_rev_cap(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    fg.refine_pass(inp, g, rev_cap=3)
+    O.refine_iter(P, o, rev_cap=3)
+    assert len(PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)) == 0
+
+
+def test_indegree_repair_exact(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, _, _ = O.stage_a(P, w.k)
+    O.refine_iter(P, o)
+    g = _to_dev(o)
+    T, st = fg.indegree_repair(inp, g)
+    To, ost = O.indegree_repair(P, o)
+    assert ost["zero_before"] > 0
+    assert st["zero_indegree"] == ost["zero_before"]
+    assert st["repaired"] == ost["replaced"]
+    assert np.array_equal(_np(T), To)
+    assert np.array_equal(_np(g["ids"]), o.ids)
+    assert np.array_equal(_np(g["dist"]), o.dist)
+    assert np.array_equal(_np(g["flags"]), o.flags)
+
+
+# --------------------------------------------------------------------------- stage (c)
+def _refined(P, w, iters=2):
+    o, _, _ = O.stage_a(P, w.k)
+    T = None
+    for _ in range(iters):
+        O.refine_iter(P, o)
+        T, _ = O.indegree_repair(P, o)
+    return o, T
+
+
+def test_prune_small(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, T = _refined(P, w)
+    ei, ed, ec = fg.prune(inp, _to_dev(o), torch.from_numpy(T).to(_dev()), w.R, w.alpha)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, w.alpha)
+    ei, ed, ec = _np(ei), _np(ed), _np(ec)
+    diff = np.nonzero(~np.all(ei == oi, 1))[0]
+    assert len(diff) <= max(2, w.N // 2000), len(diff)
+    for u in diff:
+        # a differing row must contain an occlusion test that ties within tolerance
+        cand = o.ids[u][o.ids[u] >= 0]
+        assert PR.prune_row_has_near_tie(w.X, u, cand, o.dist[u][:len(cand)], w.alpha), u
+    same = np.all(ei == oi, 1)
+    assert np.array_equal(ed[same], od[same]) and np.array_equal(ec[same], oc[same])
+
+
+def test_prune_integer_bit_exact(sift_like):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, T = _refined(P, w, iters=1)
+    ei, ed, ec = fg.prune(inp, _to_dev(o), torch.from_numpy(T).to(_dev()), w.R, w.alpha)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, w.alpha)
+    assert np.array_equal(_np(ei), oi) and np.array_equal(_np(ed), od) and np.array_equal(_np(ec), oc)
+
+
+def test_reverse_insert_exact(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, T = _refined(P, w, iters=1)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, w.alpha)
+    dev = _dev()
+    out = fg.reverse_insert(torch.from_numpy(oi).to(dev), torch.from_numpy(od).to(dev), torch.from_numpy(oc).to(dev))
+    ri, rd, rg = O.reverse_insert(oi, od, oc)
+    assert np.array_equal(_np(out["ids"]), ri)
+    assert np.array_equal(_np(out["dist"]), rd)
+    assert np.array_equal(_np(out["deg"]), rg)
+
+
+def test_reach_fix_small(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    o, T = _refined(P, w, iters=1)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, w.alpha)
+    ri, rd, rg = O.reverse_insert(oi, od, oc)
+    entry = O.merged_entry(P)
+    assert not PR.bfs_reached(ri, entry).all(), "the small workload is disconnected before the fix"
+    dev = _dev()
+    g = {"ids": torch.from_numpy(ri.copy()).to(dev), "dist": torch.from_numpy(rd.copy()).to(dev),
+         "deg": torch.from_numpy(rg.copy()).to(dev)}
+    st = fg.reach_fix(inp, g, entry, k=w.k)
+    ost = O.reach_fix(P, ri, rd, rg, entry)
+    gi = _np(g["ids"])
+    assert st["unreached"] == 0 and ost["unreached"] == 0
+    assert PR.bfs_reached(gi, entry).all()
+    assert st["attached"] == ost["attached"]
+    assert np.all(gi == ri, 1).mean() >= 0.999
+    PR.check_lists(gi, _np(g["dist"]), w.N)
+
+
+# --------------------------------------------------------------------------- end to end
+def test_merge_small_end_to_end(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=3, return_knng=True)
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=3)
+    gi, gd, gdeg = _np(out["ids"]), _np(out["dist"]), _np(out["deg"])
+    PR.check_lists(gi, gd, w.N)
+    assert np.all(gdeg <= w.R) and np.array_equal(gdeg, (gi >= 0).sum(1))
+    assert out["entry"] == ref.entry
+    assert out["stats"]["unreached"] == 0 and PR.bfs_reached(gi, out["entry"]).all()
+    # k-NNG recall against exact k-NN on a sample, and search recall@10 at beam 64
+    rng = np.random.default_rng(9)
+    samp = rng.choice(w.N, 1000, replace=False)
+    tid, _ = O.knn_exact(w.X, w.X[samp], w.k, w.metric, exclude=samp)
+    kg = _np(out["knng"]["ids"])
+    assert abs(O.recall_at(kg[samp], tid, w.k) - O.recall_at(ref.knn_ids[samp], tid, w.k)) <= 0.005
+    gt, _ = O.knn_exact(w.X, w.Q, 10, w.metric)
+    sg, _ = fg.search(inp.X, out["ids"], out["entry"], torch.from_numpy(w.Q).to(_dev()), topk=10, beam=64)
+    so, _, _ = O.search(w.X, ref.ids, ref.entry, w.Q, 64, 10, w.metric)
+    assert abs(O.recall_at(_np(sg), gt, 10) - O.recall_at(so, gt, 10)) <= 0.005
+
+
+def test_merge_integer_bit_exact(sift_like):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, return_knng=True)
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=2)
+    assert np.array_equal(_np(out["knng"]["ids"]), ref.knn_ids)
+    assert np.array_equal(_np(out["ids"]), ref.ids)
+    assert np.array_equal(_np(out["deg"]), ref.deg)
+
+
+def test_search_parity(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=1)
+    dev = _dev()
+    sg, sd = fg.search(inp.X, torch.from_numpy(ref.ids).to(dev), ref.entry, torch.from_numpy(w.Q).to(dev), 10, 64)
+    so, sdo, _ = O.search(w.X, ref.ids, ref.entry, w.Q, 64, 10, w.metric)
+    sg = _np(sg)
+    assert np.all(sg == so, 1).mean() >= 0.99
+    gt, _ = O.knn_exact(w.X, w.Q, 10, w.metric)
+    assert abs(O.recall_at(sg, gt, 10) - O.recall_at(so, gt, 10)) <= 0.005
+
+
+def test_merge_host_matches_device(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    X = torch.from_numpy(w.X).pin_memory()
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).pin_memory()
+    h = fg.merge_host(X, adj, w.shard_sizes, [g[1] for g in graphs], k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    d = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    assert np.array_equal(h["ids"].numpy(), _np(d["ids"]))
+    assert h["entry"] == d["entry"]
+
+
+def test_deterministic_repeat(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    a = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2)
+    b = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2)
+    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"])
+
+
+# --------------------------------------------------------------------------- edge cases
+def _tiny(seed, sizes, d, M, metric=0):
+    from synth import pgbuild
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((sum(sizes), d)).astype(np.float32)
+    if metric == 1:
+        X /= np.linalg.norm(X, axis=1, keepdims=True)
+    gs, o = [], 0
+    for n in sizes:
+        gs.append(pgbuild.build_pg(X[o:o + n], M, 32, metric))
+        o += n
+    return X, gs
+
+
+@pytest.mark.parametrize("sizes,d,M,k,R,metric", [
+    ([3, 5], 8, 4, 6, 4, 0),            # shards smaller than k: padded lists
+    ([700, 300, 257], 36, 40, 12, 10, 0),  # ragged K tail (d=36), two adjacency chunks (M=40), h=3
+    ([500, 500], 96, 16, 48, 32, 1),    # inner product, k=48
+    ([1, 400], 16, 8, 8, 8, 0),         # a one-point shard
+])
+def test_edge_cases_match_oracle(sizes, d, M, k, R, metric):
+    import paper_2603_21710_gb300 as fg
+    X, gs = _tiny(sum(sizes) + d, sizes, d, M, metric)
+    P = O.Problem(X, sizes, np.concatenate([g[0] for g in gs]), np.array([g[1] for g in gs], np.int32), metric)
+    dev = _dev()
+    inp = fg.MergeInput.from_flat(torch.from_numpy(X).to(dev), sizes,
+                                  torch.from_numpy(np.concatenate([g[0] for g in gs])).to(dev),
+                                  [g[1] for g in gs], metric=metric)
+    ga = fg.cross_query(inp, k)
+    oa, _, _ = O.stage_a(P, k)
+    assert np.all(_np(ga["ids"]) == oa.ids, 1).mean() >= 0.98
+    g = _to_dev(oa)
+    fg.refine_pass(inp, g)
+    O.refine_iter(P, oa)
+    assert len(PR.lists_match(_np(g["ids"]), _np(g["dist"]), oa.ids, oa.dist)) == 0
+    out = fg.merge(inp, k=k, R=R, alpha=1.0, iters=2)
+    gi = _np(out["ids"])
+    PR.check_lists(gi, _np(out["dist"]), sum(sizes))
+    assert PR.bfs_reached(gi, out["entry"]).all()

@@ -1,0 +1,350 @@
+"""Benchmark of the FGIM merge hot path on GB300.
+
+One step = one full merge (stage a cross querying, 3 x (Visit + Update + indegree
+repair), Alg. 5 prune + reverse-edge insertion, reachability fix) of the Sift-like
+workload: N = 1,000,000 points, d = 128, integer values 0..255 from a 1,000-cluster
+mixture, 4 shards of 250,000 with HNSW-style input PGs (M = 32, ef = 128), k = 64,
+R = 32, alpha = 1.2. Inputs are synthetic and seeded; the input PGs are built on the
+host before timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. Under torchrun (N > 1) every rank merges its own replica of the
+workload (weak scaling, no collective on the data path); value = all ranks' points /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "merged points/sec (3 stages, 1 GB300) at recall@10 within 0.5pt of oracle"
+UNIT = "points/s"
+WORKLOAD = dict(name="medium", N=1_000_000, d=128, h=4, M=32, ef=128, k=64, R=32, alpha=1.2, iters=3)
+# bounded CPU sample: the same recipe at N = 100,000 (4 shards of 25,000)
+SAMPLE_N = 100_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fgim", choices=["fgim", "reference"])
+    ap.add_argument("--n", type=int, default=WORKLOAD["N"], help="points (default: the full workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- distributed plumbing
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return dist
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- inputs
+def make_inputs(n: int, seed_offset: int = 0):
+    from synth import gen, pgbuild
+    w = gen.make(WORKLOAD["name"], N=n, seed=gen.MASTER_SEED + seed_offset)
+    graphs = pgbuild.build_all(w)
+    return w, graphs
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only query)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except ValueError:
+                    pass
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- oracle legs
+def cpu_baseline_leg(w_full, graphs_full, n_queries_sample=2000):
+    """The oracle as it stands, on the host cores: (1) a full merge of a bounded sample of the
+    workload (the same recipe at SAMPLE_N points), (2) its beam-search counters on sampled
+    cross queries of the full workload (the per-query work model of stage a)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    w, graphs = make_inputs(SAMPLE_N)
+    P = O.Problem.from_workload(w, graphs)
+    t0 = time.perf_counter()
+    r = O.merge(P, w.k, w.R, w.alpha, iters=WORKLOAD["iters"])
+    dt = time.perf_counter() - t0
+    # per-query counters of Alg. 1 on the full workload (cross queries of sampled vertices)
+    rng = np.random.default_rng(7)
+    off = w_full.offsets
+    L = -(-w_full.k // (w_full.h - 1))
+    ndc = hops = nq = 0
+    for g in rng.choice(w_full.N, n_queries_sample // (w_full.h - 1), replace=False):
+        i = int(np.searchsorted(off, g, side="right") - 1)
+        for j in range(w_full.h):
+            if j == i:
+                continue
+            adj, ep = graphs_full[j]
+            _, _, st = O.knn_search(w_full.shard(j), adj, ep, w_full.X[g], L, L, w_full.metric)
+            ndc += st["ndc"]
+            hops += st["hops"]
+            nq += 1
+    return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full oracle merge (3 stages, iters=3) of the same recipe at N={SAMPLE_N} "
+                      f"(4 shards of {SAMPLE_N // 4}), {dt:.2f} s on {cores} host threads",
+            "seconds": dt, "stats": r.stats,
+            "stage_a_per_query": {"ndc": ndc / nq, "hops": hops / nq, "queries_sampled": nq, "L": L}}
+
+
+def run_reference(args):
+    """The oracle arm: each step is one oracle merge of the bounded sample on the host cores."""
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    import oracle as O
+    w, graphs = make_inputs(SAMPLE_N)
+    P = O.Problem.from_workload(w, graphs)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.merge(P, w.k, w.R, w.alpha, iters=WORKLOAD["iters"])
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = SAMPLE_N * len(times) / total
+    cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Sift-like merge, oracle sample N={SAMPLE_N}, d=128, 4 shards, k=64, R=32",
+                       "sample_of": "medium (N=1,000,000)", "iters": WORKLOAD["iters"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"oracle merge of the recipe at N={SAMPLE_N} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def roofline_for(kernel: str, per_launch_ms: float, w, graphs, cpu, peaks):
+    """Algorithmic bytes of one launch of the dominant kernel / its mean event time."""
+    N, d, k = w.N, w.d, w.k
+    M = w.M
+    if kernel == "k_cross_query" and cpu is not None:
+        pq = cpu["stage_a_per_query"]
+        nq = N * (w.h - 1)
+        mean_deg = float(np.mean([(g[0] >= 0).sum(1).mean() for g in graphs]))
+        # per cross query: NDC vector rows + ids, hops adjacency rows; per vertex: its row,
+        # its local-candidate rows and adjacency row, and the k-NNG row it writes
+        bytes_ = nq * (pq["ndc"] * (d * 4 + 4) + pq["hops"] * M * 4) + N * (d * 4 + mean_deg * d * 4 + M * 4 + k * 9)
+        bound, unit, peak = "hbm", "GB/s", peaks.get("hbm_gbs")
+        achieved = bytes_ / (per_launch_ms * 1e-3) / 1e9
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak if peak else None, "traffic": None, "kernel": kernel,
+                "algorithmic_bytes": bytes_, "per_launch_ms": per_launch_ms, "peak_kind": "measured burst copy"}
+    return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": None,
+            "traffic": None, "kernel": kernel, "per_launch_ms": per_launch_ms}
+
+
+def run_fgim(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        init_dist(ws, "nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2603_21710_gb300 as fg
+    fg.load()
+    w, graphs = make_inputs(args.n)
+    X = torch.from_numpy(w.X).to(dev)
+    adj_np = np.concatenate([g[0] for g in graphs])
+    adj = torch.from_numpy(adj_np).to(dev)
+    entries = [g[1] for g in graphs]
+    inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, entries, metric="l2")
+    kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=WORKLOAD["iters"])
+    stream = torch.cuda.current_stream()
+    out = None
+    for _ in range(args.warmup):
+        out = fg.merge(inp, **kw)
+    torch.cuda.synchronize()
+    barrier(ws)
+    # ---- timed region (device-resident inputs)
+    launches0 = fg.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk, fg.profiling() as prof:
+        torch.cuda.synchronize()
+        barrier(ws)
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            out = fg.merge(inp, **kw)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        kernels = {}
+        for name in ("k_cross_query", "k_join", "k_prune", "k_search", "k_repair", "k_build_cands", "k_rev_select",
+                     "k_prop_merge", "k_e_merge", "k_bfs_step", "k_cc_step", "k_rev_fill", "k_rev_count",
+                     "k_indegree", "k_e_fill", "k_e_count", "k_reach_assign", "k_scan_block", "k_scan_add",
+                     "k_prop_count", "k_prop_scatter", "k_compact", "k_zero_flags", "k_rep_flags",
+                     "k_bfs_init", "k_cc_init", "k_copy1", "k_nonzero_u8", "k_fill_i32"):
+            n, ms = prof.query(name)
+            if n:
+                kernels[name] = {"launches": n, "ms": ms}
+    launches = fg.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_ms = sum(step_ms)
+    total_ms = max_over_ranks(local_ms, ws, dev)
+    stats = out["stats"]
+    # ---- evaluation outside the timed region: recall@10 at beam 64 against exact k-NN
+    nq_eval = min(1000, w.Q.shape[0])
+    Q = torch.from_numpy(w.Q[:nq_eval]).to(dev)
+    sid, _ = fg.search(X, out["ids"], out["entry"], Q, topk=10, beam=64)
+    d2 = (Q * Q).sum(1, keepdim=True) - 2 * Q @ X.T + (X * X).sum(1)[None, :]
+    gt = torch.topk(d2, 10, dim=1, largest=False).indices
+    hits = sum(len(set(a) & set(b)) for a, b in zip(sid.cpu().tolist(), gt.cpu().tolist()))
+    recall = hits / (10 * nq_eval)
+    del d2
+    # ---- end to end through the host-buffer entry point (pinned host inputs and outputs)
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(w.X).pin_memory()
+        Ah = torch.from_numpy(adj_np).pin_memory()
+        oi = torch.empty((w.N, w.R), dtype=torch.int32).pin_memory()
+        od = torch.empty((w.N,), dtype=torch.int32).pin_memory()
+        fg.merge_host(Xh, Ah, w.shard_sizes, entries, out_ids=oi, out_deg=od, **kw)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fg.merge_host(Xh, Ah, w.shard_sizes, entries, out_ids=oi, out_deg=od, **kw)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+        e2e = {"value": ws * w.N * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * 4 + Ah.numel() * 4),
+               "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4 + 4)}
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline_leg(w, graphs)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
+    roof = roofline_for(dom, kernels[dom]["ms"] / kernels[dom]["launches"], w, graphs, cpu, peaks) if dom else None
+    value = ws * w.N * args.steps / (total_ms * 1e-3)
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Sift-like merge: N=1,000,000 (4 x 250,000), d=128 integer 0..255, "
+                                   "input PGs M=32 ef=128, k=64, R=32, alpha=1.2, I_max=3",
+                       "N": w.N, "d": w.d, "shards": w.shard_sizes, "k": w.k, "R": w.R, "alpha": w.alpha,
+                       "iters": WORKLOAD["iters"], "l2_policy": "inputs larger than L2 (512 MB vectors)",
+                       "parallelism": f"replicas x{ws}"},
+            "recall@10": recall, "recall_eval": {"queries": nq_eval, "beam": 64, "truth": "exact (GPU brute force)"},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+            "cpu_baseline": ({k_: v for k_, v in cpu.items() if k_ in ("value", "unit", "cores", "kind", "sample")}
+                             if cpu else None),
+            "stage_a_work_model": cpu["stage_a_per_query"] if cpu else None,
+            "kernels": kernels, "merge_stats": stats, "step_ms": step_ms}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_fgim(args)
+    ws, _, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -678,9 +678,15 @@ static void uf_union(int32_t* parent, int32_t a, int32_t b) {
 /*
  * Rounds of: BFS from the entry; weak components of the subgraph induced by the
  * unreached vertices, each represented by its smallest id x; Alg. 1 for x_x over
- * the graph as it stands at the round start (pool `beam`, top `beam`); then, in
- * ascending x, append x to the first search result p (ascending (delta, id)) whose
- * list still has room (deg(p) < R), keeping p's list sorted. Nothing is removed.
+ * the graph as it stands at the round start (pool `beam`, top `beam`); then, for
+ * every representative in ascending id, one new edge p -> x:
+ *   - p is the first search result (ascending (delta, id)) whose list has room
+ *     (deg(p) < R): x is appended to p's list, kept sorted;
+ *   - otherwise p is the first search result that has a neighbour y with indegree
+ *     above one (indegree over the current graph); the farthest such y (by
+ *     (delta, id)) is replaced by x and p's list is re-sorted.
+ * Degrees and indegrees are updated after every attachment. Rounds repeat (at most
+ * OR_REACH_ROUNDS) while unreached vertices remain.
  */
 void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
                   int32_t* out_ids, float* out_dist, int32_t* out_deg, or_stats* st) {
@@ -689,6 +695,7 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
     int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * N);
     int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * N);
     int32_t* reps = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* indeg = (int32_t*)malloc(sizeof(int32_t) * N);
     int64_t attached = 0;
     set_threads(in->nthreads);
     for (int round = 0; round < OR_REACH_ROUNDS; ++round) {
@@ -706,6 +713,7 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
         int64_t nreps = 0;
         for (int64_t x = 0; x < N; ++x)
             if (!reached[x] && uf_find(parent, (int32_t)x) == x) reps[nreps++] = (int32_t)x;
+        or_indegree(out_ids, N, R, indeg);
         int32_t* cid = (int32_t*)malloc(sizeof(int32_t) * nreps * beam);
         float* cdist = (float*)malloc(sizeof(float) * nreps * beam);
         int32_t* cn = (int32_t*)malloc(sizeof(int32_t) * nreps);
@@ -723,21 +731,31 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
         }
         for (int64_t r = 0; r < nreps; ++r) {
             int32_t x = reps[r];
-            for (int32_t t = 0; t < cn[r]; ++t) {
-                int32_t p = cid[r * beam + t];
-                if (out_deg[p] >= R) continue;
-                int32_t* li = out_ids + (int64_t)p * R;
-                float* ld = out_dist + (int64_t)p * R;
-                float d = dist_g(in, p, x);
-                int32_t pos = out_deg[p]++;
-                while (pos > 0 && key_lt(d, x, ld[pos - 1], li[pos - 1])) {
-                    li[pos] = li[pos - 1]; ld[pos] = ld[pos - 1]; --pos;
-                }
-                li[pos] = x;
-                ld[pos] = d;
-                ++attached;
-                break;
+            int32_t p = -1, pos = -1;
+            for (int32_t t = 0; t < cn[r] && p < 0; ++t)
+                if (out_deg[cid[r * beam + t]] < R) { p = cid[r * beam + t]; pos = out_deg[p]; }
+            for (int32_t t = 0; t < cn[r] && p < 0; ++t) {
+                int32_t q = cid[r * beam + t];
+                for (int32_t s = out_deg[q] - 1; s >= 0; --s)
+                    if (indeg[out_ids[(int64_t)q * R + s]] > 1) { p = q; pos = s; break; }
             }
+            if (p < 0) continue;
+            int32_t* li = out_ids + (int64_t)p * R;
+            float* ld = out_dist + (int64_t)p * R;
+            float d = dist_g(in, p, x);
+            if (pos == out_deg[p]) out_deg[p] += 1;
+            else indeg[li[pos]] -= 1;
+            indeg[x] += 1;
+            /* place (d, x) at pos, then restore ascending (delta, id) */
+            while (pos > 0 && key_lt(d, x, ld[pos - 1], li[pos - 1])) {
+                li[pos] = li[pos - 1]; ld[pos] = ld[pos - 1]; --pos;
+            }
+            while (pos + 1 < out_deg[p] && key_lt(ld[pos + 1], li[pos + 1], d, x)) {
+                li[pos] = li[pos + 1]; ld[pos] = ld[pos + 1]; ++pos;
+            }
+            li[pos] = x;
+            ld[pos] = d;
+            ++attached;
         }
         free(cid);
         free(cdist);
@@ -752,6 +770,7 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
     free(queue);
     free(parent);
     free(reps);
+    free(indeg);
 }
 
 int32_t or_merged_entry(const or_input* in) {

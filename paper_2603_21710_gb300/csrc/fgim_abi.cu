@@ -429,6 +429,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     const size_t sb = scan_scratch_bytes(N);
     unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
     int32_t* changed = c.alloc<int32_t>(1);
+    int32_t* indeg = c.alloc<int32_t>(N);
     int32_t* cand = nullptr;
     float* cdist = nullptr;
     long long cand_cap = 0;
@@ -453,7 +454,8 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         }
         ck(launch_search(P.X, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
                          cand, cdist, c.ctr + 0, c.status, c.s));
-        ck(launch_reach_assign(g->ids, g->dist, g->deg, R, reps, off + N, cand, cdist, beam, c.ctr + 4, c.s));
+        ck(launch_indegree(g->ids, N, R, indeg, false, nullptr, c.s));
+        ck(launch_reach_assign(g->ids, g->dist, g->deg, indeg, R, reps, off + N, cand, cdist, beam, c.ctr + 4, c.s));
     }
     reached = bfs(c, g, visited, fa, fb, counts);
     if (st) st->unreached = N - reached;

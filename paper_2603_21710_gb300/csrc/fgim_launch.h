@@ -103,7 +103,7 @@ cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32
                            int32_t* changed, cudaStream_t s);
 cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
                              cudaStream_t s);
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int R, const int32_t* reps,
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int32_t* indeg, int R, const int32_t* reps,
                                 const long long* nreps, const int32_t* cand, const float* cdist, int beam,
                                 unsigned long long* attached, cudaStream_t s);
 

@@ -289,45 +289,87 @@ cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long 
     return cudaGetLastError();
 }
 
-// ascending representatives: append x to the first search result p with room (one thread)
-__global__ void k_reach_assign(int32_t* __restrict__ graph, float* __restrict__ gdist, int32_t* __restrict__ deg,
-                               int R, const int32_t* __restrict__ reps, const long long* __restrict__ nreps,
-                               const int32_t* __restrict__ cand, const float* __restrict__ cdist, int beam,
-                               unsigned long long* attached) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Representatives in ascending id, one warp (sequential semantics, lanes scan candidates):
+// append x to the first search result p with room; otherwise replace, in the first search
+// result that has one, the farthest neighbour whose indegree is above one.
+__global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph, float* __restrict__ gdist,
+                                                     int32_t* __restrict__ deg, int32_t* __restrict__ indeg, int R,
+                                                     const int32_t* __restrict__ reps,
+                                                     const long long* __restrict__ nreps,
+                                                     const int32_t* __restrict__ cand,
+                                                     const float* __restrict__ cdist, int beam,
+                                                     unsigned long long* attached) {
+    const int lane = lane_id();
     const long long nr = *nreps;
     unsigned long long att = 0;
     for (long long r = 0; r < nr; ++r) {
         const int32_t x = reps[r];
-        for (int t = 0; t < beam; ++t) {
-            const int32_t p = cand[r * beam + t];
-            if (p < 0) break;
-            if (deg[p] >= R) continue;
-            const float d = cdist[r * beam + t];
-            const uint64_t key = mkkey(d, x);
+        const int32_t* cr = cand + r * beam;
+        // first candidate with room
+        int p = -1, pos = -1, t_sel = -1;
+        for (int t0 = 0; t0 < beam && p < 0; t0 += 32) {
+            const int t = t0 + lane;
+            const int32_t q = t < beam ? cr[t] : -1;
+            const bool room = q >= 0 && deg[q] < R;
+            const unsigned m = __ballot_sync(kFull, room);
+            if (m) {
+                t_sel = t0 + __ffs(m) - 1;
+                p = cr[t_sel];
+                pos = deg[p];
+            }
+        }
+        // else the first candidate with a replaceable neighbour (indegree above one), farthest first
+        for (int t = 0; t < beam && p < 0; ++t) {
+            const int32_t q = cr[t];
+            if (q < 0) break;
+            const int dq = deg[q];
+            int best = -1;
+            for (int s0 = ((R - 1) >> 5) << 5; s0 >= 0 && best < 0; s0 -= 32) {
+                const int s = s0 + lane;
+                bool ok = false;
+                if (s < dq) ok = indeg[graph[(long long)q * R + s]] > 1;
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (m) best = s0 + 31 - __clz(m);
+            }
+            if (best >= 0) {
+                p = q;
+                pos = best;
+                t_sel = t;
+            }
+        }
+        if (p >= 0 && lane == 0) {
             int32_t* li = graph + (long long)p * R;
             float* ld = gdist + (long long)p * R;
-            int pos = deg[p];
+            const float d = cdist[r * beam + t_sel];
+            const uint64_t key = mkkey(d, x);
+            if (pos == deg[p]) deg[p] += 1;
+            else indeg[li[pos]] -= 1;
+            indeg[x] += 1;
             while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
                 li[pos] = li[pos - 1];
                 ld[pos] = ld[pos - 1];
                 --pos;
             }
+            while (pos + 1 < deg[p] && mkkey(ld[pos + 1], li[pos + 1]) < key) {
+                li[pos] = li[pos + 1];
+                ld[pos] = ld[pos + 1];
+                ++pos;
+            }
             li[pos] = x;
             ld[pos] = d;
-            deg[p] += 1;
             ++att;
-            break;
         }
+        __syncwarp();
+        __threadfence_block();
     }
-    *attached += att;
+    if (lane == 0) *attached += att;
 }
 
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int R, const int32_t* reps,
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int32_t* indeg, int R, const int32_t* reps,
                                 const long long* nreps, const int32_t* cand, const float* cdist, int beam,
                                 unsigned long long* attached, cudaStream_t s) {
     LaunchScope ls("k_reach_assign", s);
-    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, R, reps, nreps, cand, cdist, beam, attached);
+    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, indeg, R, reps, nreps, cand, cdist, beam, attached);
     return cudaGetLastError();
 }
 

@@ -322,3 +322,30 @@ def test_edge_cases_match_oracle(sizes, d, M, k, R, metric):
     gi = _np(out["ids"])
     PR.check_lists(gi, _np(out["dist"]), sum(sizes))
     assert PR.bfs_reached(gi, out["entry"]).all()
+
+
+def test_reach_fix_victim_rule():
+    """Every search candidate is full: the farthest neighbour with indegree > 1 is replaced (as in the oracle)."""
+    import json
+    import os
+    import paper_2603_21710_gb300 as fg
+    gd = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "reach_victim.json")))
+    pos = np.asarray(gd["pos"], np.float32)
+    X = np.zeros((len(pos), 4), np.float32)
+    X[:, 0] = pos
+    R = gd["R"]
+    ids = np.asarray(gd["lists"], np.int32)
+    deg = (ids >= 0).sum(1).astype(np.int32)
+    dist = np.full(ids.shape, np.inf, np.float32)
+    for u in range(len(pos)):
+        for t in range(deg[u]):
+            dist[u, t] = (pos[u] - pos[ids[u, t]]) ** 2
+    dev = _dev()
+    adj = torch.full((len(pos), 2), -1, dtype=torch.int32, device=dev)
+    inp = fg.MergeInput.from_flat(torch.from_numpy(X).to(dev), [2, 2], adj, [0, 0])
+    g = {"ids": torch.from_numpy(ids.copy()).to(dev), "dist": torch.from_numpy(dist).to(dev),
+         "deg": torch.from_numpy(deg).to(dev)}
+    st = fg.reach_fix(inp, g, gd["entry"], k=2)
+    assert _np(g["ids"]).tolist() == gd["expected_lists"]
+    assert _np(g["dist"])[2].tolist() == gd["expected_dist_row2"]
+    assert st["attached"] == 1 and st["unreached"] == 0

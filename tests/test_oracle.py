@@ -386,6 +386,23 @@ def test_reach_fix_attaches_one_rep_per_component():
     _check_lists(ids, dist, N)
 
 
+def test_reach_fix_victim_golden():
+    gd = _golden("reach_victim.json")
+    P = _line_problem(gd["pos"])
+    R = gd["R"]
+    N = len(gd["pos"])
+    ids = np.asarray(gd["lists"], np.int32)
+    dist = np.full((N, R), np.inf, np.float32)
+    deg = (ids >= 0).sum(1).astype(np.int32)
+    for u in range(N):
+        for t in range(deg[u]):
+            dist[u, t] = O.delta(P.X[u], P.X[ids[u, t]], 0)
+    st = O.reach_fix(P, ids, dist, deg, gd["entry"])
+    assert ids.tolist() == gd["expected_lists"]
+    assert dist[2].tolist() == gd["expected_dist_row2"]
+    assert st["attached"] == gd["expected_attached"] and st["unreached"] == 0
+
+
 # --------------------------------------------------------------------------- end to end
 def test_merge_small_invariants(small_problem):
     w, graphs, P = small_problem

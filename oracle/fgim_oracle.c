@@ -640,6 +640,28 @@ void or_reverse_insert(int64_t N, int32_t R, const int32_t* e_ids, const float* 
 /* ------------------------------------------------------------------------- */
 /* Reachability fix (added step; the paper only reduces SCCs, Sec. 4.2.2)      */
 /* ------------------------------------------------------------------------- */
+/* BFS over out-edges from src marking unmarked vertices; level[] (optional) gets 1 + hops from src */
+static int64_t bfs_level(int64_t N, int32_t R, const int32_t* g, int32_t src, uint8_t* reached, int32_t* queue,
+                         int32_t* level) {
+    if (reached[src]) return 0;
+    int64_t head = 0, tail = 0;
+    reached[src] = 1;
+    level[src] = 1;
+    queue[tail++] = src;
+    while (head < tail) {
+        int32_t x = queue[head++];
+        for (int32_t t = 0; t < R; ++t) {
+            int32_t y = g[(int64_t)x * R + t];
+            if (y < 0 || reached[y]) continue;
+            reached[y] = 1;
+            level[y] = level[x] + 1;
+            queue[tail++] = y;
+        }
+    }
+    (void)N;
+    return tail;
+}
+
 static int64_t bfs_mark(int64_t N, int32_t R, const int32_t* g, int32_t src, uint8_t* reached, int32_t* queue) {
     if (reached[src]) return 0;
     int64_t head = 0, tail = 0, n = 0;
@@ -673,20 +695,21 @@ static void uf_union(int32_t* parent, int32_t a, int32_t b) {
     else parent[ra] = rb;
 }
 
-#define OR_REACH_ROUNDS 8
+#define OR_REACH_ROUNDS 16
 
 /*
- * Rounds of: BFS from the entry; weak components of the subgraph induced by the
- * unreached vertices, each represented by its smallest id x; Alg. 1 for x_x over
- * the graph as it stands at the round start (pool `beam`, top `beam`); then, for
- * every representative in ascending id, one new edge p -> x:
+ * Rounds of: BFS from the entry (levels = 1 + hops); weak components of the subgraph
+ * induced by the unreached vertices, each represented by its smallest id x; Alg. 1 for
+ * x_x over the graph as it stands at the round start (pool `beam`, top `beam`); then,
+ * for every representative in ascending id, one new edge p -> x:
  *   - p is the first search result (ascending (delta, id)) whose list has room
  *     (deg(p) < R): x is appended to p's list, kept sorted;
- *   - otherwise p is the first search result that has a neighbour y with indegree
- *     above one (indegree over the current graph); the farthest such y (by
+ *   - otherwise p is the first search result that has a replaceable neighbour: a
+ *     reached y that keeps a BFS parent other than p (an in-neighbour at a smaller
+ *     level), so y and all it reaches stay reachable; the farthest such y (by
  *     (delta, id)) is replaced by x and p's list is re-sorted.
- * Degrees and indegrees are updated after every attachment. Rounds repeat (at most
- * OR_REACH_ROUNDS) while unreached vertices remain.
+ * Degrees and parent counts are updated after every attachment. Rounds repeat (at
+ * most OR_REACH_ROUNDS) while unreached vertices remain.
  */
 void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
                   int32_t* out_ids, float* out_dist, int32_t* out_deg, or_stats* st) {
@@ -695,13 +718,24 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
     int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * N);
     int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * N);
     int32_t* reps = (int32_t*)malloc(sizeof(int32_t) * N);
-    int32_t* indeg = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* level = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* npar = (int32_t*)malloc(sizeof(int32_t) * N);
     int64_t attached = 0;
     set_threads(in->nthreads);
     for (int round = 0; round < OR_REACH_ROUNDS; ++round) {
         memset(reached, 0, N);
-        int64_t nr = bfs_mark(N, R, out_ids, entry_g, reached, queue);
+        memset(level, 0, sizeof(int32_t) * N);
+        int64_t nr = bfs_level(N, R, out_ids, entry_g, reached, queue, level);
         if (nr == N) break;
+        /* BFS parents: in-neighbours at a smaller level */
+        memset(npar, 0, sizeof(int32_t) * N);
+        for (int64_t x = 0; x < N; ++x) {
+            if (!level[x]) continue;
+            for (int32_t t = 0; t < R; ++t) {
+                int32_t y = out_ids[x * R + t];
+                if (y >= 0 && level[y] > level[x]) npar[y]++;
+            }
+        }
         for (int64_t x = 0; x < N; ++x) parent[x] = (int32_t)x;
         for (int64_t x = 0; x < N; ++x) {
             if (reached[x]) continue;
@@ -713,7 +747,6 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
         int64_t nreps = 0;
         for (int64_t x = 0; x < N; ++x)
             if (!reached[x] && uf_find(parent, (int32_t)x) == x) reps[nreps++] = (int32_t)x;
-        or_indegree(out_ids, N, R, indeg);
         int32_t* cid = (int32_t*)malloc(sizeof(int32_t) * nreps * beam);
         float* cdist = (float*)malloc(sizeof(float) * nreps * beam);
         int32_t* cn = (int32_t*)malloc(sizeof(int32_t) * nreps);
@@ -736,16 +769,18 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
                 if (out_deg[cid[r * beam + t]] < R) { p = cid[r * beam + t]; pos = out_deg[p]; }
             for (int32_t t = 0; t < cn[r] && p < 0; ++t) {
                 int32_t q = cid[r * beam + t];
-                for (int32_t s = out_deg[q] - 1; s >= 0; --s)
-                    if (indeg[out_ids[(int64_t)q * R + s]] > 1) { p = q; pos = s; break; }
+                for (int32_t s = out_deg[q] - 1; s >= 0; --s) {
+                    int32_t y = out_ids[(int64_t)q * R + s];
+                    int32_t other = npar[y] - (level[q] < level[y] ? 1 : 0);
+                    if (level[y] > 0 && other >= 1) { p = q; pos = s; break; }
+                }
             }
             if (p < 0) continue;
             int32_t* li = out_ids + (int64_t)p * R;
             float* ld = out_dist + (int64_t)p * R;
             float d = dist_g(in, p, x);
             if (pos == out_deg[p]) out_deg[p] += 1;
-            else indeg[li[pos]] -= 1;
-            indeg[x] += 1;
+            else if (level[p] < level[li[pos]]) npar[li[pos]] -= 1;
             /* place (d, x) at pos, then restore ascending (delta, id) */
             while (pos > 0 && key_lt(d, x, ld[pos - 1], li[pos - 1])) {
                 li[pos] = li[pos - 1]; ld[pos] = ld[pos - 1]; --pos;
@@ -770,7 +805,8 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
     free(queue);
     free(parent);
     free(reps);
-    free(indeg);
+    free(level);
+    free(npar);
 }
 
 int32_t or_merged_entry(const or_input* in) {

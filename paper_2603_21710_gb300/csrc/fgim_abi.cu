@@ -372,8 +372,21 @@ static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stat
     unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
     ck(launch_zero_flags(T, N, flag, c.s));
     ck(compact_flags(flag, N, zeros, off, tmp, sb, c.s));
-    ck(launch_repair(*g, T, zeros, off + N, c.ctr + 3, c.status, c.s));
-    if (st) st->zero_indegree = c.read_ll(off + N);
+    const long long nz = c.read_ll(off + N);
+    if (st) st->zero_indegree = nz;
+    if (nz == 0) return;
+    int32_t* owner = c.alloc<int32_t>(N);
+    long long* cursor = c.alloc<long long>(2);   // [0] start, [1] first failing index
+    ck(cudaMemsetAsync(cursor, 0, sizeof(long long), c.s));
+    long long start = 0;
+    for (long long round = 0; start < nz; ++round) {
+        need(round <= nz, FGIM_EINTERNAL, "indegree repair made no progress");
+        ck(launch_repair_round(*g, T, zeros, off + N, cursor, nz - start, owner, cursor + 1, c.ctr + 3, c.status,
+                               c.s));
+        const long long next = c.read_ll(cursor);
+        need(next > start, FGIM_EINTERNAL, "indegree repair made no progress");
+        start = next;
+    }
 }
 
 static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knng* g, const int32_t* T, int32_t* e_ids,
@@ -399,15 +412,18 @@ static long long bfs(Ctx& c, const fgim_graph* g, int32_t* visited, int32_t* fa,
     const long long N = g->n;
     ck(launch_bfs_init(visited, N, fa, counts + 0, g->entry, c.s));
     long long reached = 1;
+    long long frontier = 1;
     int32_t* fin = fa;
     int32_t* fout = fb;
     int cur = 0;
-    for (long long level = 0; level <= N; ++level) {
+    for (long long level = 1; level <= N; ++level) {
         ck(cudaMemsetAsync(counts + (cur ^ 1), 0, sizeof(int32_t), c.s));
-        ck(launch_bfs_step(g->ids, g->R, N, visited, fin, counts + cur, fout, counts + (cur ^ 1), c.s));
+        ck(launch_bfs_step(g->ids, g->R, N, visited, fin, counts + cur, fout, counts + (cur ^ 1), (int32_t)(level + 1),
+                           frontier, c.s));
         const int nf = c.read_i32(counts + (cur ^ 1));
         if (nf == 0) break;
         reached += nf;
+        frontier = nf;
         std::swap(fin, fout);
         cur ^= 1;
     }
@@ -429,12 +445,12 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     const size_t sb = scan_scratch_bytes(N);
     unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
     int32_t* changed = c.alloc<int32_t>(1);
-    int32_t* indeg = c.alloc<int32_t>(N);
+    int32_t* npar = c.alloc<int32_t>(N);
     int32_t* cand = nullptr;
     float* cdist = nullptr;
     long long cand_cap = 0;
     long long reached = 0;
-    for (int round = 0; round < 8; ++round) {
+    for (int round = 0; round < 16; ++round) {
         reached = bfs(c, g, visited, fa, fb, counts);
         if (reached >= N) break;
         ck(launch_cc_init(visited, N, label, c.s));
@@ -454,8 +470,9 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         }
         ck(launch_search(P.X, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
                          cand, cdist, c.ctr + 0, c.status, c.s));
-        ck(launch_indegree(g->ids, N, R, indeg, false, nullptr, c.s));
-        ck(launch_reach_assign(g->ids, g->dist, g->deg, indeg, R, reps, off + N, cand, cdist, beam, c.ctr + 4, c.s));
+        ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
+        ck(launch_reach_assign(g->ids, g->dist, g->deg, visited, npar, R, reps, off + N, cand, cdist, beam, c.ctr + 4,
+                               c.s));
     }
     reached = bfs(c, g, visited, fa, fb, counts);
     if (st) st->unreached = N - reached;

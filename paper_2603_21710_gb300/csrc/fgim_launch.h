@@ -73,8 +73,9 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
 cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
                             cudaStream_t s);
-cudaError_t launch_repair(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
-                          unsigned long long* repaired, int* status, cudaStream_t s);
+cudaError_t launch_repair_round(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
+                                long long* start, long long pending, int32_t* owner, long long* first_fail,
+                                unsigned long long* repaired, int* status, cudaStream_t s);
 cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cudaStream_t s);
 cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s);
 
@@ -97,14 +98,17 @@ cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, cons
 cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry,
                             cudaStream_t s);
 cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
-                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, cudaStream_t s);
+                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, int32_t next_level,
+                            long long max_frontier, cudaStream_t s);
+cudaError_t launch_bfs_parents(const int32_t* graph, int R, long long N, const int32_t* level, int32_t* npar,
+                               cudaStream_t s);
 cudaError_t launch_cc_init(const int32_t* visited, long long N, int32_t* label, cudaStream_t s);
 cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32_t* visited, int32_t* label,
                            int32_t* changed, cudaStream_t s);
 cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
                              cudaStream_t s);
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int32_t* indeg, int R, const int32_t* reps,
-                                const long long* nreps, const int32_t* cand, const float* cdist, int beam,
-                                unsigned long long* attached, cudaStream_t s);
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
+                                const int32_t* reps, const long long* nreps, const int32_t* cand, const float* cdist,
+                                int beam, unsigned long long* attached, cudaStream_t s);
 
 }  // namespace fgim

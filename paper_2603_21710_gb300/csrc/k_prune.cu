@@ -220,24 +220,46 @@ cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, in
     return cudaGetLastError();
 }
 
-// one level: thread per (frontier vertex, neighbour slot)
+// one level: thread per (frontier vertex, neighbour slot); visited[y] = BFS level (entry = 1)
 __global__ void k_bfs_step(const int32_t* __restrict__ graph, int R, long long N, int32_t* __restrict__ visited,
                            const int32_t* __restrict__ fin, const int32_t* __restrict__ fin_count,
-                           int32_t* __restrict__ fout, int32_t* __restrict__ fout_count) {
+                           int32_t* __restrict__ fout, int32_t* __restrict__ fout_count, int32_t next_level) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nf = *fin_count;
     if (i >= nf * R) return;
     const int32_t x = fin[i / R];
     const int32_t y = graph[(long long)x * R + (i % R)];
     if (y < 0 || y >= N) return;
-    if (visited[y] == 0 && atomicExch(visited + y, 1) == 0) fout[atomicAdd(fout_count, 1)] = y;
+    if (visited[y] == 0 && atomicCAS(visited + y, 0, next_level) == 0) fout[atomicAdd(fout_count, 1)] = y;
 }
 
 cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
-                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, cudaStream_t s) {
-    // grid sized for the largest possible frontier; threads beyond the live frontier exit
+                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, int32_t next_level,
+                            long long max_frontier, cudaStream_t s) {
+    // grid sized for the largest frontier the host has seen; threads beyond the live frontier exit
     LaunchScope ls("k_bfs_step", s);
-    k_bfs_step<<<(unsigned)cdivl(N * R, 256), 256, 0, s>>>(graph, R, N, visited, fin, fin_count, fout, fout_count);
+    k_bfs_step<<<(unsigned)cdivl(max_frontier * R, 256), 256, 0, s>>>(graph, R, N, visited, fin, fin_count, fout,
+                                                                        fout_count, next_level);
+    return cudaGetLastError();
+}
+
+// number of BFS parents of every reached vertex: in-neighbours at a smaller level
+__global__ void k_bfs_parents(const int32_t* __restrict__ graph, int R, long long N, const int32_t* __restrict__ level,
+                              int32_t* __restrict__ npar) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * R) return;
+    const int32_t lx = level[i / R];
+    if (lx == 0) return;
+    const int32_t y = graph[i];
+    if (y >= 0 && y < N && level[y] > lx) atomicAdd(npar + y, 1);
+}
+
+cudaError_t launch_bfs_parents(const int32_t* graph, int R, long long N, const int32_t* level, int32_t* npar,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(npar, 0, sizeof(int32_t) * N, s);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls("k_bfs_parents", s);
+    k_bfs_parents<<<(unsigned)cdivl(N * R, 256), 256, 0, s>>>(graph, R, N, level, npar);
     return cudaGetLastError();
 }
 
@@ -291,9 +313,10 @@ cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long 
 
 // Representatives in ascending id, one warp (sequential semantics, lanes scan candidates):
 // append x to the first search result p with room; otherwise replace, in the first search
-// result that has one, the farthest neighbour whose indegree is above one.
+// result that has one, the farthest reached neighbour y that keeps a BFS parent other than p.
 __global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph, float* __restrict__ gdist,
-                                                     int32_t* __restrict__ deg, int32_t* __restrict__ indeg, int R,
+                                                     int32_t* __restrict__ deg, const int32_t* __restrict__ level,
+                                                     int32_t* __restrict__ npar, int R,
                                                      const int32_t* __restrict__ reps,
                                                      const long long* __restrict__ nreps,
                                                      const int32_t* __restrict__ cand,
@@ -318,16 +341,21 @@ __global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph
                 pos = deg[p];
             }
         }
-        // else the first candidate with a replaceable neighbour (indegree above one), farthest first
+        // else the first candidate with a replaceable neighbour (keeps a BFS parent other than p), farthest first
         for (int t = 0; t < beam && p < 0; ++t) {
             const int32_t q = cr[t];
             if (q < 0) break;
             const int dq = deg[q];
+            const int32_t lq = level[q];
             int best = -1;
             for (int s0 = ((R - 1) >> 5) << 5; s0 >= 0 && best < 0; s0 -= 32) {
                 const int s = s0 + lane;
                 bool ok = false;
-                if (s < dq) ok = indeg[graph[(long long)q * R + s]] > 1;
+                if (s < dq) {
+                    const int32_t y = graph[(long long)q * R + s];
+                    const int32_t ly = level[y];
+                    ok = ly > 0 && npar[y] - (lq < ly ? 1 : 0) >= 1;
+                }
                 const unsigned m = __ballot_sync(kFull, ok);
                 if (m) best = s0 + 31 - __clz(m);
             }
@@ -343,8 +371,7 @@ __global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph
             const float d = cdist[r * beam + t_sel];
             const uint64_t key = mkkey(d, x);
             if (pos == deg[p]) deg[p] += 1;
-            else indeg[li[pos]] -= 1;
-            indeg[x] += 1;
+            else if (level[p] < level[li[pos]]) npar[li[pos]] -= 1;
             while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
                 li[pos] = li[pos - 1];
                 ld[pos] = ld[pos - 1];
@@ -365,11 +392,11 @@ __global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph
     if (lane == 0) *attached += att;
 }
 
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, int32_t* indeg, int R, const int32_t* reps,
-                                const long long* nreps, const int32_t* cand, const float* cdist, int beam,
-                                unsigned long long* attached, cudaStream_t s) {
+cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
+                                const int32_t* reps, const long long* nreps, const int32_t* cand, const float* cdist,
+                                int beam, unsigned long long* attached, cudaStream_t s) {
     LaunchScope ls("k_reach_assign", s);
-    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, indeg, R, reps, nreps, cand, cdist, beam, attached);
+    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, cand, cdist, beam, attached);
     return cudaGetLastError();
 }
 

@@ -628,82 +628,136 @@ cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, c
     return cudaGetLastError();
 }
 
-// Alg. 4 in ascending v* order by one warp: exact sequential semantics.
-__global__ void __launch_bounds__(32) k_repair(int32_t* __restrict__ ids, float* __restrict__ dist,
-                                               uint8_t* __restrict__ flags, long long N, int k,
-                                               int32_t* __restrict__ T, const int32_t* __restrict__ zeros,
-                                               const long long* __restrict__ nzeros,
-                                               unsigned long long* repaired, int* status) {
+// Alg. 4 with the result of the sequential loop over v* in ascending id, computed in
+// parallel rounds. In a round every pending v* (warp per v*) works out its action on
+// the current lists: the neighbour v it would use and the entry of N(v) it would
+// replace. The action reads N(v*), N(v) of every neighbour tried, and T of every entry
+// scanned; it writes one entry of N(v), T(v') and T(v*). All those vertex ids are
+// reserved with atomicMin of the pending index. The longest ascending prefix of
+// pending vertices that hold all their reservations is committed: their actions touch
+// disjoint vertices, so applying them at once equals applying them one after another,
+// and each was computed on the state the sequential loop would have given it. The
+// rest is recomputed in the next round. The lowest pending index always holds its
+// reservations, so every round commits at least one action.
+enum { kPlan = 0, kCheck = 1, kCommit = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_repair_round(int32_t* __restrict__ ids, float* __restrict__ dist,
+                                                      uint8_t* __restrict__ flags, long long N, int k,
+                                                      int32_t* __restrict__ T, const int32_t* __restrict__ zeros,
+                                                      const long long* __restrict__ nzeros,
+                                                      const long long* __restrict__ start,
+                                                      int32_t* __restrict__ owner, long long* __restrict__ first_fail,
+                                                      unsigned long long* repaired, int* status) {
+    const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
+    const long long i = *start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const long long nz = *nzeros;
-    unsigned long long done_count = 0;
-    for (long long z = 0; z < nz; ++z) {
-        const long long vs = zeros[z];
-        if (vs < 0 || vs >= N) {
-            if (lane == 0) atomicOr(status, kErrBounds);
-            continue;
+    if (i >= nz) return;
+    if (MODE == kCommit && i >= *first_fail) return;
+    const int32_t tag = (int32_t)(i & 0x7fffffff);
+    bool ok = true;
+    auto touch = [&](int32_t x) {
+        if (MODE == kPlan) atomicMin(owner + x, tag);
+        else if (MODE == kCheck) ok = ok && owner[x] == tag;
+    };
+    const long long vs = zeros[i];
+    if (vs < 0 || vs >= N) {
+        if (lane == 0) atomicOr(status, kErrBounds);
+        return;
+    }
+    if (lane == 0) touch((int32_t)vs);
+    int a_sel = -1, best = -1;
+    int32_t v_sel = -1;
+    for (int a = 0; a < k; ++a) {
+        const int32_t v = ids[vs * k + a];
+        if (v < 0 || v >= N) break;
+        if (lane == 0) touch(v);
+        // farthest entry of N(v) that is not replaced and has T > 1 (entries scanned are touched)
+        int bst = -1;
+        for (int r = (k - 1) >> 5; r >= 0 && bst < 0; --r) {
+            const int s = r * 32 + lane;
+            int32_t e = -1;
+            bool el = false;
+            if (s < k) {
+                e = ids[(long long)v * k + s];
+                el = e >= 0 && e < N && !(flags[(long long)v * k + s] & FGIM_FLAG_REPLACED) && T[e] > 1;
+            }
+            const unsigned m = __ballot_sync(kFull, el);
+            if (m) bst = r * 32 + 31 - __clz(m);
+            if (e >= 0 && e < N && (bst < 0 || s >= bst)) touch(e);
         }
-        // lines 3-4: neighbours v of v*, closest first
-        for (int a = 0; a < k; ++a) {
-            const int32_t v = ids[vs * k + a];
-            if (v < 0) break;
-            if (v >= N) {
-                if (lane == 0) atomicOr(status, kErrBounds);
-                break;
-            }
-            const float dvs = dist[vs * k + a];
-            // line 5-6: farthest entry of N(v) that is not replaced and has T > 1
-            int best = -1;
-            for (int r = (k - 1) >> 5; r >= 0 && best < 0; --r) {
-                const int s = r * 32 + lane;
-                bool el = false;
-                if (s < k) {
-                    const int32_t e = ids[(long long)v * k + s];
-                    el = e >= 0 && e < N && !(flags[(long long)v * k + s] & FGIM_FLAG_REPLACED) && T[e] > 1;
-                }
-                const unsigned m = __ballot_sync(kFull, el);
-                if (m) best = r * 32 + 31 - __clz(m);
-            }
-            if (best < 0) continue;
-            // lines 7-11: replace, mark, update T, re-sort N(v)
-            if (lane == 0) {
-                int32_t* li = ids + (long long)v * k;
-                float* ld = dist + (long long)v * k;
-                uint8_t* lf = flags + (long long)v * k;
-                const int32_t old = li[best];
-                T[old] -= 1;
-                T[vs] += 1;
-                const uint64_t key = mkkey(dvs, (int32_t)vs);
-                int pos = best;
-                while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
-                    li[pos] = li[pos - 1];
-                    ld[pos] = ld[pos - 1];
-                    lf[pos] = lf[pos - 1];
-                    --pos;
-                }
-                while (pos + 1 < k && li[pos + 1] >= 0 && mkkey(ld[pos + 1], li[pos + 1]) < key) {
-                    li[pos] = li[pos + 1];
-                    ld[pos] = ld[pos + 1];
-                    lf[pos] = lf[pos + 1];
-                    ++pos;
-                }
-                li[pos] = (int32_t)vs;
-                ld[pos] = dvs;
-                lf[pos] = FGIM_FLAG_NEW | FGIM_FLAG_REPLACED;
-                ++done_count;
-            }
-            __syncwarp();
-            __threadfence_block();
+        if (bst >= 0) {
+            a_sel = a;
+            best = bst;
+            v_sel = v;
             break;
         }
     }
-    if (lane == 0 && done_count) atomicAdd(repaired, done_count);
+    if (MODE == kCheck) {
+        if (__any_sync(kFull, !ok) && lane == 0) atomicMin((unsigned long long*)first_fail, (unsigned long long)i);
+        return;
+    }
+    if (MODE == kCommit && best >= 0 && lane == 0) {
+        int32_t* li = ids + (long long)v_sel * k;
+        float* ld = dist + (long long)v_sel * k;
+        uint8_t* lf = flags + (long long)v_sel * k;
+        const float dvs = dist[vs * k + a_sel];
+        const int32_t old = li[best];
+        T[old] -= 1;
+        T[vs] += 1;
+        const uint64_t key = mkkey(dvs, (int32_t)vs);
+        int pos = best;
+        while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
+            li[pos] = li[pos - 1];
+            ld[pos] = ld[pos - 1];
+            lf[pos] = lf[pos - 1];
+            --pos;
+        }
+        while (pos + 1 < k && li[pos + 1] >= 0 && mkkey(ld[pos + 1], li[pos + 1]) < key) {
+            li[pos] = li[pos + 1];
+            ld[pos] = ld[pos + 1];
+            lf[pos] = lf[pos + 1];
+            ++pos;
+        }
+        li[pos] = (int32_t)vs;
+        ld[pos] = dvs;
+        lf[pos] = FGIM_FLAG_NEW | FGIM_FLAG_REPLACED;
+        atomicAdd(repaired, 1ull);
+    }
 }
 
-cudaError_t launch_repair(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
-                          unsigned long long* repaired, int* status, cudaStream_t s) {
-    LaunchScope ls("k_repair", s);
-    k_repair<<<1, 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, repaired, status);
+__global__ void k_repair_advance(long long* start, const long long* first_fail) { *start = *first_fail; }
+
+cudaError_t launch_repair_round(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
+                                long long* start, long long pending, int32_t* owner, long long* first_fail,
+                                unsigned long long* repaired, int* status, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(owner, 0x7f, sizeof(int32_t) * g.n, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(first_fail, nzeros, sizeof(long long), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    const int wpb = 4;
+    const unsigned blocks = (unsigned)cdivll(pending, wpb);
+    {
+        LaunchScope ls("k_repair_round", s);
+        k_repair_round<kPlan><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
+                                                          owner, first_fail, repaired, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_repair_round", s);
+        k_repair_round<kCheck><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
+                                                           owner, first_fail, repaired, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_repair_round", s);
+        k_repair_round<kCommit><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
+                                                            owner, first_fail, repaired, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    LaunchScope ls("k_repair_advance", s);
+    k_repair_advance<<<1, 1, 0, s>>>(start, first_fail);
     return cudaGetLastError();
 }
 

@@ -206,6 +206,8 @@ int64_t fgim_launch_count(void);
 void fgim_prof_enable(int32_t on);
 void fgim_prof_reset(void);
 int32_t fgim_prof_query(const char* kernel, int64_t* launches, double* total_ms);
+/* Comma-separated names of the kernels timed since the last reset; returns the full length. */
+int32_t fgim_prof_names(char* buf, int32_t buf_bytes);
 
 #ifdef __cplusplus
 }

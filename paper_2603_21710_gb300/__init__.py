@@ -258,6 +258,14 @@ class profiling:
         load().fgim_prof_enable(0)
 
     @staticmethod
+    def names():
+        L_ = load()
+        n = L_.fgim_prof_names(None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        L_.fgim_prof_names(buf, n + 1)
+        return [x for x in buf.value.decode().split(",") if x]
+
+    @staticmethod
     def query(kernel: str):
         n = ctypes.c_int64(0)
         ms = ctypes.c_double(0.0)

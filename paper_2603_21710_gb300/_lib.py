@@ -81,6 +81,7 @@ EXPORTS = {
     "fgim_prof_enable": (None, [ctypes.c_int32]),
     "fgim_prof_reset": (None, []),
     "fgim_prof_query": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fgim_prof_names": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
 }
 
 

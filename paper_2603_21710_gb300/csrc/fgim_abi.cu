@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -105,6 +106,10 @@ static inline void ck(cudaError_t e) {
     if (e != cudaSuccess) {
         t_last_error = cudaGetErrorString(e);
         if (e == cudaErrorMemoryAllocation) throw Fail{FGIM_ENOMEM};
+        if (e == cudaErrorNotSupported) {
+            t_last_error = "candidate sets of this size do not fit the join's shared memory";
+            throw Fail{FGIM_EUNSUPPORTED};
+        }
         throw Fail{FGIM_ECUDA};
     }
 }
@@ -316,7 +321,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.nn = c.alloc<int32_t>(N);
     b.no = c.alloc<int32_t>(N);
     // proposal buffer: large enough for every proposal of one vertex many times over
-    long long cap = 32LL * N;
+    long long cap = 128LL * N;
     const long long per_vertex_max = 2LL * b.cmax * b.cmax;
     if (cap < 4 * per_vertex_max) cap = 4 * per_vertex_max;
     if (cap < (1LL << 22)) cap = 1LL << 22;
@@ -334,6 +339,8 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.pend_off = c.alloc<long long>(N + 1);
     b.scan_bytes = scan_scratch_bytes(N);
     b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
+    b.max_nc = c.alloc<int32_t>(1);
+    b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);
 
     ck(refine_visit(*g, rev_cap, b, c.s));
     ck(cudaMemsetAsync(b.pending, 0, N, c.s));
@@ -446,6 +453,8 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
     int32_t* changed = c.alloc<int32_t>(1);
     int32_t* npar = c.alloc<int32_t>(N);
+    int32_t* owner = c.alloc<int32_t>(N);
+    long long* cursor = c.alloc<long long>(2);
     int32_t* cand = nullptr;
     float* cdist = nullptr;
     long long cand_cap = 0;
@@ -471,8 +480,16 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         ck(launch_search(P.X, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
                          cand, cdist, c.ctr + 0, c.status, c.s));
         ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
-        ck(launch_reach_assign(g->ids, g->dist, g->deg, visited, npar, R, reps, off + N, cand, cdist, beam, c.ctr + 4,
-                               c.s));
+        ck(cudaMemsetAsync(cursor, 0, sizeof(long long), c.s));
+        long long start = 0;
+        for (long long it = 0; start < nr; ++it) {
+            need(it <= nr, FGIM_EINTERNAL, "reachability fix made no progress");
+            ck(launch_reach_round(g->ids, g->dist, g->deg, visited, npar, R, N, reps, off + N, cursor, nr - start, cand,
+                                  cdist, beam, owner, cursor + 1, c.ctr + 4, c.s));
+            const long long next = c.read_ll(cursor);
+            need(next > start, FGIM_EINTERNAL, "reachability fix made no progress");
+            start = next;
+        }
     }
     reached = bfs(c, g, visited, fa, fb, counts);
     if (st) st->unreached = N - reached;
@@ -789,6 +806,21 @@ int32_t fgim_prof_query(const char* kernel, int64_t* launches, double* total_ms)
     if (launches) *launches = it->second.launches;
     if (total_ms) *total_ms = it->second.ms;
     return 1;
+}
+
+int32_t fgim_prof_names(char* buf, int32_t buf_bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::string all;
+    for (auto& kv : g_prof_table) {
+        if (!all.empty()) all += ",";
+        all += kv.first;
+    }
+    if (buf && buf_bytes > 0) {
+        const size_t n = std::min((size_t)(buf_bytes - 1), all.size());
+        std::memcpy(buf, all.data(), n);
+        buf[n] = 0;
+    }
+    return (int32_t)all.size();
 }
 
 }  // extern "C"

@@ -5,13 +5,17 @@
 // to an order-preserving unsigned integer, the low word the id. Key order equals the
 // lexicographic (distance, id) order for every non-NaN distance.
 //
-// Distance. One function computes every distance that enters a list or decides a
-// comparison: over float4 chunks c = 0 .. d/4-1 in order, four accumulators
-// s_j += (a[4c+j] - b[4c+j])^2 (fused multiply-add), result (s0 + s1) + (s2 + s3).
-// (For inner product: s_j += a*b, delta = 1 - sum; cosine multiplies the sum by the
-// product of the two inverse norms.) It is symmetric bit for bit in its two operands,
-// so delta(a, b) computed anywhere equals delta(b, a) computed anywhere else, and the
-// same (id, distance) pair always yields the same key.
+// Distance. One definition gives every distance that enters a list or decides a
+// comparison (the canonical FP32 distance). The d dimensions form float4 chunks
+// c = 0 .. d/4-1; lane l of a warp owns the chunks c = l, l+32, l+64, ... and adds them
+// in increasing c into four accumulators s_j += e_j * e_j with e = a - b (fused
+// multiply-add; inner product: s_j += a_j * b_j), its partial is (s0 + s1) + (s2 + s3);
+// the 32 partials are summed by a butterfly over lane offsets 16, 8, 4, 2, 1. Inner
+// product gives 1 - sum, cosine 1 - sum * (inv_a * inv_b). Every step is a single
+// rounded operation whose operands are symmetric in a and b, so delta(a, b) equals
+// delta(b, a) bit for bit, and the same (id, distance) pair always yields the same key.
+// Warps compute it one row at a time (butterfly) or 32 rows at a time (transpose
+// reduction, which forms exactly the same sums).
 #pragma once
 
 #include <cstdint>
@@ -77,21 +81,18 @@ __device__ __forceinline__ int shard_of(const ShardTable& t, long long g) {
 }
 
 // ----------------------------------------------------------------------------
-// canonical distance (see the file comment); a and b are 16-byte aligned
+// canonical distance (see the file comment); rows are 16-byte aligned float4 arrays
 // ----------------------------------------------------------------------------
 template <int METRIC>
-__device__ __forceinline__ float delta_fn(const float* __restrict__ a, const float* __restrict__ b, int d,
-                                          float inv_ab) {
-    const float4* a4 = reinterpret_cast<const float4*>(a);
-    const float4* b4 = reinterpret_cast<const float4*>(b);
+__device__ __forceinline__ float lane_part(const float4* __restrict__ a, const float4* __restrict__ b, int nc4,
+                                           int lane) {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    const int nc = d >> 2;
-#pragma unroll 4
-    for (int c = 0; c < nc; ++c) {
-        float4 x = a4[c];
-        float4 y = b4[c];
+    for (int c = lane; c < nc4; c += 32) {
+        const float4 x = a[c];
+        const float4 y = b[c];
         if (METRIC == FGIM_L2SQ) {
-            float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+            const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+            const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
             s0 = fmaf(e0, e0, s0);
             s1 = fmaf(e1, e1, s1);
             s2 = fmaf(e2, e2, s2);
@@ -103,11 +104,117 @@ __device__ __forceinline__ float delta_fn(const float* __restrict__ a, const flo
             s3 = fmaf(x.w, y.w, s3);
         }
     }
-    float s = (s0 + s1) + (s2 + s3);
-    if (METRIC == FGIM_L2SQ) return s;
-    if (METRIC == FGIM_IP) return 1.f - s;
-    return 1.f - s * inv_ab;
+    return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
 }
+
+// the lane partial for one float4 chunk per lane (d = 128), as lane_part computes it
+template <int METRIC>
+__device__ __forceinline__ float chunk_part(const float4 x, const float4 y) {
+    float s0, s1, s2, s3;
+    if (METRIC == FGIM_L2SQ) {
+        const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+        const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
+        s0 = fmaf(e0, e0, 0.f);
+        s1 = fmaf(e1, e1, 0.f);
+        s2 = fmaf(e2, e2, 0.f);
+        s3 = fmaf(e3, e3, 0.f);
+    } else {
+        s0 = fmaf(x.x, y.x, 0.f);
+        s1 = fmaf(x.y, y.y, 0.f);
+        s2 = fmaf(x.z, y.z, 0.f);
+        s3 = fmaf(x.w, y.w, 0.f);
+    }
+    return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
+}
+
+template <int METRIC>
+__device__ __forceinline__ float delta_finish(float s, float inv_ab) {
+    if (METRIC == FGIM_L2SQ) return s;
+    if (METRIC == FGIM_IP) return __fsub_rn(1.f, s);
+    return __fsub_rn(1.f, __fmul_rn(s, inv_ab));
+}
+
+// butterfly sum of one value per lane; every lane gets the same result
+__device__ __forceinline__ float warp_butterfly(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// v[r] = this lane's partial of row r (r < 32). Returns the butterfly sum of row `lane`:
+// at offset o each lane keeps the half of its rows whose bit o matches its own lane bit
+// and adds its partner's partials of those rows, forming the butterfly's sums.
+__device__ __forceinline__ float warp_transpose_reduce(float (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16, n = 16; o > 0; o >>= 1, n >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (r < n) {
+                const float send = up ? v[r] : v[r + n];
+                const float keep = up ? v[r + n] : v[r];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, o);
+                v[r] = __fadd_rn(keep, recv);
+            }
+        }
+    }
+    return v[0];
+}
+
+// P[l * 33 + r] = lane l's partial of row r. Returns the butterfly sum of row r, added in the
+// butterfly's tree (pairs of lanes 16 apart, then 8, 4, 2, 1; every pair sum is commutative).
+__device__ __forceinline__ float smem_tree_sum(const float* P, int r) {
+    float a[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) a[l] = __fadd_rn(P[l * 33 + r], P[(l + 16) * 33 + r]);
+#pragma unroll
+    for (int l = 0; l < 8; ++l) a[l] = __fadd_rn(a[l], a[l + 8]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) a[l] = __fadd_rn(a[l], a[l + 4]);
+#pragma unroll
+    for (int l = 0; l < 2; ++l) a[l] = __fadd_rn(a[l], a[l + 2]);
+    return __fadd_rn(a[0], a[1]);
+}
+
+// Non-canonical FP32 distance by one thread: sequential over the chunks with four
+// accumulators. Used only as a filter; decisions near its value are re-taken with the
+// canonical distance (the two differ by less than fp32_pair_margin of the sum of |terms|).
+template <int METRIC>
+__device__ __forceinline__ float seq_sum(const float4* __restrict__ a, const float4* __restrict__ b, int nc4) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < nc4; ++c) {
+        const float4 x = a[c];
+        const float4 y = b[c];
+        if (METRIC == FGIM_L2SQ) {
+            const float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+            s0 = fmaf(e0, e0, s0);
+            s1 = fmaf(e1, e1, s1);
+            s2 = fmaf(e2, e2, s2);
+            s3 = fmaf(e3, e3, s3);
+        } else {
+            s0 = fmaf(x.x, y.x, s0);
+            s1 = fmaf(x.y, y.y, s1);
+            s2 = fmaf(x.z, y.z, s2);
+            s3 = fmaf(x.w, y.w, s3);
+        }
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+// canonical distance of one row pair by one warp (all lanes get it)
+template <int METRIC>
+__device__ __forceinline__ float warp_delta(const float* a, const float* b, int d, float inv_ab, int lane) {
+    const float p = lane_part<METRIC>(reinterpret_cast<const float4*>(a), reinterpret_cast<const float4*>(b), d >> 2,
+                                      lane);
+    return delta_finish<METRIC>(warp_butterfly(p), inv_ab);
+}
+
+// rounding margin between two FP32 evaluations of the same distance that both follow
+// sums of at most d/4 + 8 terms per chain: the worst-case relative error of either is
+// below (d/4 + 8) * 2^-24 of the sum of |terms| (Higham, Accuracy and Stability of
+// Numerical Algorithms, 2nd ed., Sec. 3.1), so they differ by less than twice that.
+__host__ __device__ inline float fp32_pair_margin(int d) { return 2.f * (float)(d / 4 + 8) * 5.9604645e-8f; }
 
 // ----------------------------------------------------------------------------
 // warp helpers

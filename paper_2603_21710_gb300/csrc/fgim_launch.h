@@ -64,6 +64,9 @@ struct RefineBuffers {
     // scan scratch
     void* scan_tmp;
     size_t scan_bytes;
+    // largest candidate set of a pass (device) and a pinned host slot to read it
+    int32_t* max_nc;
+    int32_t* host_i32;
 };
 
 cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s);
@@ -107,8 +110,9 @@ cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32
                            int32_t* changed, cudaStream_t s);
 cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
                              cudaStream_t s);
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
-                                const int32_t* reps, const long long* nreps, const int32_t* cand, const float* cdist,
-                                int beam, unsigned long long* attached, cudaStream_t s);
+cudaError_t launch_reach_round(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
+                               long long N, const int32_t* reps, const long long* nreps, long long* start,
+                               long long pending, const int32_t* cand, const float* cdist, int beam, int32_t* owner,
+                               long long* first_fail, unsigned long long* attached, cudaStream_t s);
 
 }  // namespace fgim

@@ -2,9 +2,12 @@
 //
 // Neighbour selection runs one warp per vertex u. The candidate rows of u are staged in
 // shared memory (padded stride) when they fit; candidates are visited in ascending
-// (delta, id); for each one the kept neighbours are tested in parallel, one lane per
-// kept w, with the canonical distance delta(w, v) and the alpha-RNG test
-// delta(u, v) < alpha^2 * delta(w, v) (alpha^2 rounded once to FP32, product in FP32).
+// (delta, id); for each one every kept w is tested in parallel (one lane per w) with the
+// alpha-RNG rule delta(u, v) < alpha^2 * delta(w, v) (alpha^2 rounded once to FP32, product
+// in FP32). A lane's own sequential FP32 distance decides whenever the decision is further
+// from the boundary than the rounding margin between it and the canonical distance; the few
+// decisions inside the margin are re-taken with the canonical distance (whole warp), so the
+// outcome is exactly that of the canonical distance.
 // A vertex whose only in-edge is u (T(v) = 1) is kept unconditionally (Alg. 5 line 5).
 //
 // Connectivity enhancement builds the reverse lists of the pruned snapshot E' by a
@@ -27,11 +30,14 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
     const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (u >= N) return;
     const int stride = d + 4;
-    const size_t per_warp = ((size_t)(STAGE ? k * stride * 4 : 0) + (size_t)k * 8 + 16 + 15) & ~(size_t)15;
+    const int nc4 = d >> 2;
+    const size_t per_warp = ((size_t)(STAGE ? k * stride * 4 : 0) + (size_t)k * 12 + 16 + 15) & ~(size_t)15;
     unsigned char* base = smem + per_warp * warp;
     float* rows = reinterpret_cast<float*>(base);
     int32_t* cidv = reinterpret_cast<int32_t*>(base + (STAGE ? (size_t)k * stride * 4 : 0));
     int32_t* kept = cidv + k;
+    float* nrm = reinterpret_cast<float*>(kept + k);
+    const float eps = fp32_pair_margin(d);
 
     // valid prefix of list(u)
     int nv = 0;
@@ -47,12 +53,21 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
     }
     __syncwarp();
     if (STAGE) {
-        const int nc4 = d >> 2;
-        for (int item = lane; item < nv * nc4; item += 32) {
-            const int r = item / nc4, c = item - (item / nc4) * nc4;
-            reinterpret_cast<float4*>(rows + r * stride)[c] =
-                reinterpret_cast<const float4*>(X + (long long)cidv[r] * d)[c];
+        // coalesced: each warp pass copies one row
+        for (int r = 0; r < nv; ++r) {
+            const float4* src = reinterpret_cast<const float4*>(X + (long long)cidv[r] * d);
+            float4* dst = reinterpret_cast<float4*>(rows + r * stride);
+            for (int c = lane; c < nc4; c += 32) dst[c] = src[c];
         }
+        __syncwarp();
+    }
+    auto rowp = [&](int idx) -> const float4* {
+        return STAGE ? reinterpret_cast<const float4*>(rows + idx * stride)
+                     : reinterpret_cast<const float4*>(X + (long long)cidv[idx] * d);
+    };
+    if (METRIC == FGIM_IP) {
+        // norms bound the rounding margin of the inner products
+        for (int r = lane; r < nv; r += 32) nrm[r] = sqrtf(seq_sum<FGIM_IP>(rowp(r), rowp(r), nc4)) * 1.0001f;
         __syncwarp();
     }
     int nk = 0;
@@ -61,19 +76,43 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
         bool keep = T[v] == 1;
         if (!keep) {
             const float duv = dist[u * k + t];
-            const float* rv = STAGE ? rows + t * stride : X + (long long)v * d;
+            const float4* rv = rowp(t);
             bool occluded = false;
-            for (int s0 = 0; s0 < nk; s0 += 32) {
+            for (int s0 = 0; s0 < nk && !occluded; s0 += 32) {
                 const int s = s0 + lane;
+                bool occ = false, near = false;
+                float inv = 1.f;
                 if (s < nk) {
                     const int wi = kept[s];
-                    const float* rw = STAGE ? rows + wi * stride : X + (long long)cidv[wi] * d;
-                    const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]) : 1.f;
-                    const float dwv = delta_fn<METRIC>(rw, rv, d, inv);
-                    if (!(duv < __fmul_rn(alpha2, dwv))) occluded = true;
+                    const float sum = seq_sum<METRIC>(rowp(wi), rv, nc4);
+                    if (METRIC == FGIM_COSINE) inv = __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]);
+                    const float dt = delta_finish<METRIC>(sum, inv);
+                    const float bound = alpha2 * dt;
+                    float m;   // bound on |alpha^2 * (filter distance - canonical distance)| plus product rounding
+                    if (METRIC == FGIM_L2SQ) m = alpha2 * eps * sum * 1.01f;
+                    else if (METRIC == FGIM_IP) m = alpha2 * eps * nrm[wi] * nrm[t];
+                    else m = alpha2 * 2.f * eps;
+                    m += 2.f * 5.9604645e-8f * fabsf(bound);
+                    near = fabsf(duv - bound) <= m;
+                    occ = !near && !(duv < bound);
+                }
+                if (__any_sync(kFull, occ)) {
+                    occluded = true;
+                    break;
+                }
+                // undecided: re-take each near decision with the canonical distance
+                unsigned nm = __ballot_sync(kFull, near);
+                while (nm && !occluded) {
+                    const int l = __ffs(nm) - 1;
+                    nm &= nm - 1;
+                    const int wi = kept[s0 + l];
+                    const float invl = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]) : 1.f;
+                    const float dc = delta_finish<METRIC>(
+                        warp_butterfly(lane_part<METRIC>(rowp(wi), rv, nc4, lane)), invl);
+                    if (!(duv < __fmul_rn(alpha2, dc))) occluded = true;
                 }
             }
-            keep = !__any_sync(kFull, occluded);
+            keep = !occluded;
         }
         if (keep) {
             if (lane == 0) kept[nk] = t;
@@ -99,8 +138,8 @@ cudaError_t launch_prune(const float* X, const float* inv_norm, long long N, int
     if (N <= 0) return cudaSuccess;
     const int k = g.k;
     const int wpb = 2;
-    const size_t staged = ((size_t)k * (d + 4) * 4 + (size_t)k * 8 + 16 + 15) & ~(size_t)15;
-    const size_t unstaged = ((size_t)k * 8 + 16 + 15) & ~(size_t)15;
+    const size_t staged = ((size_t)k * (d + 4) * 4 + (size_t)k * 12 + 16 + 15) & ~(size_t)15;
+    const size_t unstaged = ((size_t)k * 12 + 16 + 15) & ~(size_t)15;
     const bool stage = staged * wpb <= 160 * 1024;
     const size_t smem = (stage ? staged : unstaged) * wpb;
     cudaError_t e = cudaSuccess;
@@ -311,92 +350,141 @@ cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long 
     return cudaGetLastError();
 }
 
-// Representatives in ascending id, one warp (sequential semantics, lanes scan candidates):
-// append x to the first search result p with room; otherwise replace, in the first search
-// result that has one, the farthest reached neighbour y that keeps a BFS parent other than p.
-__global__ void __launch_bounds__(32) k_reach_assign(int32_t* __restrict__ graph, float* __restrict__ gdist,
+// Attachment of the representatives with the result of the sequential loop over them in
+// ascending id, computed in parallel rounds (warp per representative). The action of x:
+// the first search result p with room gets x appended; otherwise the first search result
+// with a replaceable neighbour y (reached, keeps a BFS parent other than p) has its
+// farthest such y replaced by x. Reads that other actions cannot change are not reserved:
+// a full list stays full (degrees only grow) and a neighbour that is not replaceable stays
+// so (parent counts only shrink). Only p (its list and degree) and y (its parent count)
+// are reserved with atomicMin of the representative's index; the longest ascending prefix
+// holding its reservations is committed, the rest recomputed in the next round.
+enum { kRPlan = 0, kRCheck = 1, kRCommit = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph, float* __restrict__ gdist,
                                                      int32_t* __restrict__ deg, const int32_t* __restrict__ level,
                                                      int32_t* __restrict__ npar, int R,
                                                      const int32_t* __restrict__ reps,
                                                      const long long* __restrict__ nreps,
+                                                     const long long* __restrict__ start,
                                                      const int32_t* __restrict__ cand,
                                                      const float* __restrict__ cdist, int beam,
+                                                     int32_t* __restrict__ owner, long long* __restrict__ first_fail,
                                                      unsigned long long* attached) {
+    const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
+    const long long r = *start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const long long nr = *nreps;
-    unsigned long long att = 0;
-    for (long long r = 0; r < nr; ++r) {
-        const int32_t x = reps[r];
-        const int32_t* cr = cand + r * beam;
-        // first candidate with room
-        int p = -1, pos = -1, t_sel = -1;
-        for (int t0 = 0; t0 < beam && p < 0; t0 += 32) {
-            const int t = t0 + lane;
-            const int32_t q = t < beam ? cr[t] : -1;
-            const bool room = q >= 0 && deg[q] < R;
-            const unsigned m = __ballot_sync(kFull, room);
-            if (m) {
-                t_sel = t0 + __ffs(m) - 1;
-                p = cr[t_sel];
-                pos = deg[p];
-            }
+    if (r >= nr) return;
+    if (MODE == kRCommit && r >= *first_fail) return;
+    const int32_t x = reps[r];
+    const int32_t* cr = cand + r * beam;
+    int p = -1, pos = -1, t_sel = -1;
+    for (int t0 = 0; t0 < beam && p < 0; t0 += 32) {
+        const int t = t0 + lane;
+        const int32_t q = t < beam ? cr[t] : -1;
+        const bool room = q >= 0 && deg[q] < R;
+        const unsigned m = __ballot_sync(kFull, room);
+        if (m) {
+            t_sel = t0 + __ffs(m) - 1;
+            p = cr[t_sel];
+            pos = deg[p];
         }
-        // else the first candidate with a replaceable neighbour (keeps a BFS parent other than p), farthest first
-        for (int t = 0; t < beam && p < 0; ++t) {
-            const int32_t q = cr[t];
-            if (q < 0) break;
-            const int dq = deg[q];
-            const int32_t lq = level[q];
-            int best = -1;
-            for (int s0 = ((R - 1) >> 5) << 5; s0 >= 0 && best < 0; s0 -= 32) {
-                const int s = s0 + lane;
-                bool ok = false;
-                if (s < dq) {
-                    const int32_t y = graph[(long long)q * R + s];
-                    const int32_t ly = level[y];
-                    ok = ly > 0 && npar[y] - (lq < ly ? 1 : 0) >= 1;
-                }
-                const unsigned m = __ballot_sync(kFull, ok);
-                if (m) best = s0 + 31 - __clz(m);
-            }
-            if (best >= 0) {
-                p = q;
-                pos = best;
-                t_sel = t;
-            }
-        }
-        if (p >= 0 && lane == 0) {
-            int32_t* li = graph + (long long)p * R;
-            float* ld = gdist + (long long)p * R;
-            const float d = cdist[r * beam + t_sel];
-            const uint64_t key = mkkey(d, x);
-            if (pos == deg[p]) deg[p] += 1;
-            else if (level[p] < level[li[pos]]) npar[li[pos]] -= 1;
-            while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
-                li[pos] = li[pos - 1];
-                ld[pos] = ld[pos - 1];
-                --pos;
-            }
-            while (pos + 1 < deg[p] && mkkey(ld[pos + 1], li[pos + 1]) < key) {
-                li[pos] = li[pos + 1];
-                ld[pos] = ld[pos + 1];
-                ++pos;
-            }
-            li[pos] = x;
-            ld[pos] = d;
-            ++att;
-        }
-        __syncwarp();
-        __threadfence_block();
     }
-    if (lane == 0) *attached += att;
+    for (int t = 0; t < beam && p < 0; ++t) {
+        const int32_t q = cr[t];
+        if (q < 0) break;
+        const int dq = deg[q];
+        const int32_t lq = level[q];
+        int best = -1;
+        for (int s0 = ((R - 1) >> 5) << 5; s0 >= 0 && best < 0; s0 -= 32) {
+            const int s = s0 + lane;
+            bool ok = false;
+            if (s < dq) {
+                const int32_t y = graph[(long long)q * R + s];
+                const int32_t ly = level[y];
+                ok = ly > 0 && npar[y] - (lq < ly ? 1 : 0) >= 1;
+            }
+            const unsigned m = __ballot_sync(kFull, ok);
+            if (m) best = s0 + 31 - __clz(m);
+        }
+        if (best >= 0) {
+            p = q;
+            pos = best;
+            t_sel = t;
+        }
+    }
+    if (p < 0) return;
+    const int32_t victim = pos < deg[p] ? graph[(long long)p * R + pos] : -1;
+    const int32_t tag = (int32_t)(r & 0x7fffffff);
+    if (MODE == kRPlan) {
+        if (lane == 0) {
+            atomicMin(owner + p, tag);
+            if (victim >= 0) atomicMin(owner + victim, tag);
+        }
+        return;
+    }
+    if (MODE == kRCheck) {
+        if (lane == 0 && (owner[p] != tag || (victim >= 0 && owner[victim] != tag)))
+            atomicMin((unsigned long long*)first_fail, (unsigned long long)r);
+        return;
+    }
+    if (lane == 0) {
+        int32_t* li = graph + (long long)p * R;
+        float* ld = gdist + (long long)p * R;
+        const float d = cdist[r * beam + t_sel];
+        const uint64_t key = mkkey(d, x);
+        if (pos == deg[p]) deg[p] += 1;
+        else if (level[p] < level[victim]) npar[victim] -= 1;
+        while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
+            li[pos] = li[pos - 1];
+            ld[pos] = ld[pos - 1];
+            --pos;
+        }
+        while (pos + 1 < deg[p] && mkkey(ld[pos + 1], li[pos + 1]) < key) {
+            li[pos] = li[pos + 1];
+            ld[pos] = ld[pos + 1];
+            ++pos;
+        }
+        li[pos] = x;
+        ld[pos] = d;
+        atomicAdd(attached, 1ull);
+    }
 }
 
-cudaError_t launch_reach_assign(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
-                                const int32_t* reps, const long long* nreps, const int32_t* cand, const float* cdist,
-                                int beam, unsigned long long* attached, cudaStream_t s) {
-    LaunchScope ls("k_reach_assign", s);
-    k_reach_assign<<<1, 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, cand, cdist, beam, attached);
+__global__ void k_round_advance(long long* start, const long long* first_fail) { *start = *first_fail; }
+
+cudaError_t launch_reach_round(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
+                               long long N, const int32_t* reps, const long long* nreps, long long* start,
+                               long long pending, const int32_t* cand, const float* cdist, int beam, int32_t* owner,
+                               long long* first_fail, unsigned long long* attached, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(owner, 0x7f, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(first_fail, nreps, sizeof(long long), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+    const int wpb = 4;
+    const unsigned blocks = (unsigned)cdivl(pending, wpb);
+    {
+        LaunchScope ls("k_reach_round", s);
+        k_reach_round<kRPlan><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start, cand,
+                                                          cdist, beam, owner, first_fail, attached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_reach_round", s);
+        k_reach_round<kRCheck><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start, cand,
+                                                           cdist, beam, owner, first_fail, attached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls("k_reach_round", s);
+        k_reach_round<kRCommit><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start,
+                                                            cand, cdist, beam, owner, first_fail, attached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    LaunchScope ls("k_round_advance", s);
+    k_round_advance<<<1, 1, 0, s>>>(start, first_fail);
     return cudaGetLastError();
 }
 

@@ -231,41 +231,7 @@ cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cuda
 }
 
 // ---------------------------------------------------------------------------- Update
-constexpr int kJT = 64;       // block tile edge (pairs)
-constexpr int kJK = 32;       // floats of one K slice
-constexpr int kJP = kJK + 4;  // padded row stride (floats)
 constexpr int kJThreads = 256;
-
-struct JoinLayout {
-    int cid, csh, thr, cinv, hk, hv, mask, tiles, bytes, hs, words;
-};
-
-__host__ __device__ inline JoinLayout join_layout(int cm) {
-    JoinLayout l;
-    int hs = 64;
-    while (hs < 2 * cm) hs <<= 1;
-    l.hs = hs;
-    l.words = (cm + 31) >> 5;
-    int o = 0;
-    l.thr = o;
-    o += cm * 8;
-    l.cid = o;
-    o += ((cm * 4 + 15) & ~15);
-    l.csh = o;
-    o += ((cm * 4 + 15) & ~15);
-    l.cinv = o;
-    o += ((cm * 4 + 15) & ~15);
-    l.hk = o;
-    o += hs * 4;
-    l.hv = o;
-    o += hs * 4;
-    l.mask = o;
-    o += ((cm * l.words * 4 + 15) & ~15);
-    l.tiles = o;
-    o += 2 * 2 * kJT * kJP * 4;
-    l.bytes = o;
-    return l;
-}
 
 __device__ __forceinline__ int jhash(int32_t id, int hs) { return (int)(((uint32_t)id * 2654435761u) & (hs - 1)); }
 
@@ -278,52 +244,132 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// barrier of the 64 threads of one tile group (ids 1..4; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp) { asm volatile("bar.sync %0, 64;\n" ::"r"(grp + 1) : "memory"); }
+
+// ---- Update kernel: every candidate row and list of v in shared memory, 32 x 32 tiles.
+// The register tile forms FP32 distances in its own summation order; they only filter.
+// A pair survives for direction a <- b when b is not in list(a) and its tile distance,
+// lowered by the rounding margin between two FP32 orders (fp32_pair_margin), can still
+// beat list(a)'s worst key. Survivors are re-ranked by the tile's thread group with the
+// canonical distance (transpose reduction over 32 pairs) and proposed only when their
+// exact key beats the worst key. Proposals gather in shared memory and leave the CTA
+// with one global reservation.
+constexpr int kST = 32;          // tile edge
+constexpr int kSGroups = 4;      // tile groups of 64 threads
+constexpr int kSQueue = kST * kST;
+constexpr int kPropBuf = 512;    // proposals buffered per CTA
+
+struct StagedLayout {
+    int thr, cid, csh, cinv, nrm, hk, hv, mask, lists, rows, queue, pbuf_tgt, pbuf_key, misc, bytes, hs, words;
+};
+
+__host__ __device__ inline StagedLayout staged_layout(int cm, int k, int d) {
+    StagedLayout l;
+    int hs = 64;
+    while (hs < 2 * cm) hs <<= 1;
+    l.hs = hs;
+    l.words = (cm + 31) >> 5;
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    int o = 0;
+    l.thr = o;
+    o += a16(cm * 8);
+    l.pbuf_key = o;
+    o += kPropBuf * 8;
+    l.cid = o;
+    o += a16(cm * 4);
+    l.csh = o;
+    o += a16(cm * 4);
+    l.cinv = o;
+    o += a16(cm * 4);
+    l.nrm = o;
+    o += a16(cm * 4);
+    l.hk = o;
+    o += hs * 4;
+    l.hv = o;
+    o += hs * 4;
+    l.mask = o;
+    o += a16(cm * l.words * 4);
+    l.queue = o;
+    o += kSGroups * kSQueue * 4;
+    l.pbuf_tgt = o;
+    o += kPropBuf * 4;
+    l.misc = o;
+    o += 64;
+    l.lists = o;
+    l.rows = o;
+    o += cm * (d + 4) * 4;
+    l.bytes = o;
+    return l;
+}
+
+__global__ void k_max_nc(const int32_t* __restrict__ nn, const int32_t* __restrict__ no,
+                         const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int m = 0;
+    if (i < nv) {
+        const long long v = vlist ? vlist[i] : i;
+        m = nn[v] > 0 ? nn[v] + no[v] : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
 template <int METRIC>
-__global__ void __launch_bounds__(kJThreads) k_join(ShardTable t, const float* __restrict__ X,
-                                                    const float* __restrict__ inv_norm, int k,
-                                                    const int32_t* __restrict__ ids, const float* __restrict__ dist,
-                                                    const int32_t* __restrict__ cand,
-                                                    const int32_t* __restrict__ nn_arr,
-                                                    const int32_t* __restrict__ no_arr, int cmax,
-                                                    const int32_t* __restrict__ vlist,
-                                                    int32_t* __restrict__ prop_tgt, uint64_t* __restrict__ prop_key,
-                                                    unsigned long long* prop_count, long long prop_cap,
-                                                    uint8_t* __restrict__ pending, unsigned long long* pairs_count,
-                                                    int* status) {
+__global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
+    ShardTable t, const float* __restrict__ X, const float* __restrict__ inv_norm, int k,
+    const int32_t* __restrict__ ids, const float* __restrict__ dist, const int32_t* __restrict__ cand,
+    const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax, int cm,
+    const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt, uint64_t* __restrict__ prop_key,
+    unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
+    unsigned long long* pairs_count, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int tx = tid & 15, ty = tid >> 4;
     const long long v = vlist ? (long long)vlist[blockIdx.x] : (long long)blockIdx.x;
     const int nn = nn_arr[v];
     const int nc = nn + no_arr[v];
     if (nn == 0 || nc < 2) return;
-    const JoinLayout L = join_layout(cmax);
+    if (nc > cm) {   // the host sized shared memory for the largest set; never expected
+        if (tid == 0) atomicOr(status, kErrBounds);
+        return;
+    }
+    const int d = t.dim;
+    const StagedLayout L = staged_layout(cm, k, d);
     uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
     int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
     int32_t* csh = reinterpret_cast<int32_t*>(smem + L.csh);
     float* cinv = reinterpret_cast<float*>(smem + L.cinv);
+    float* nrm = reinterpret_cast<float*>(smem + L.nrm);
     int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
     int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
-    float* tiles = reinterpret_cast<float*>(smem + L.tiles);
-    const int d = t.dim;
-    const int W = L.words;
-    const int hs = L.hs;
+    float* rows = reinterpret_cast<float*>(smem + L.rows);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(smem + L.queue);
+    int32_t* pb_tgt = reinterpret_cast<int32_t*>(smem + L.pbuf_tgt);
+    uint64_t* pb_key = reinterpret_cast<uint64_t*>(smem + L.pbuf_key);
+    int* misc = reinterpret_cast<int*>(smem + L.misc);   // [0] proposals buffered, [1..4] queue sizes
+    const int W = L.words, hs = L.hs, stride = d + 4;
+    const int vq = d >> 2;
+    const float eps = fp32_pair_margin(d);
 
+    for (int i = tid; i < nc; i += kJThreads) cid[i] = cand[v * cmax + i];
+    for (int i = tid; i < hs; i += kJThreads) hk[i] = -1;
+    for (int i = tid; i < nc * W; i += kJThreads) mask[i] = 0u;
+    if (tid < 16) misc[tid] = 0;
+    __syncthreads();
+    for (int item = tid; item < nc * vq; item += kJThreads) {
+        const int r = item / vq, c = item - (item / vq) * vq;
+        cp_async16(rows + r * stride + c * 4, X + (long long)cid[r] * d + c * 4, true);
+    }
+    cp_async_commit();
     for (int i = tid; i < nc; i += kJThreads) {
-        const int32_t c = cand[v * cmax + i];
-        cid[i] = c;
+        const int32_t c = cid[i];
         csh[i] = shard_of(t, c);
         const int32_t wi = ids[(long long)c * k + k - 1];
         thr[i] = wi < 0 ? kEmptyKey : mkkey(dist[(long long)c * k + k - 1], wi);
         cinv[i] = (METRIC == FGIM_COSINE) ? inv_norm[c] : 1.f;
-    }
-    for (int i = tid; i < hs; i += kJThreads) hk[i] = -1;
-    for (int i = tid; i < nc * W; i += kJThreads) mask[i] = 0u;
-    __syncthreads();
-    for (int i = tid; i < nc; i += kJThreads) {
-        const int32_t c = cid[i];
         int slot = jhash(c, hs);
         for (int probe = 0; probe < hs; ++probe) {
             if (atomicCAS(hk + slot, -1, c) == -1) {
@@ -333,162 +379,181 @@ __global__ void __launch_bounds__(kJThreads) k_join(ShardTable t, const float* _
             slot = (slot + 1) & (hs - 1);
         }
     }
+    cp_async_wait<0>();
     __syncthreads();
-    // membership: bit (i, j) set when C[j] is already in list(C[i])
-    for (int idx = tid; idx < nc * k; idx += kJThreads) {
-        const int i = idx / k, s = idx - (idx / k) * k;
-        const int32_t e = ids[(long long)cid[i] * k + s];
-        if (e < 0) continue;
-        int slot = jhash(e, hs);
-        for (int probe = 0; probe < hs; ++probe) {
-            const int32_t h = hk[slot];
-            if (h == e) {
-                const int j = hv[slot];
-                atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
-                break;
+    // membership bits: bit (i, j) set when C[j] is already in list(C[i]); list entries are
+    // read from global memory eight at a time per thread so the loads overlap
+    {
+        const int total = nc * k;
+        for (int base = tid * 8; base < total; base += kJThreads * 8) {
+            int32_t e8[8];
+#pragma unroll
+            for (int u8 = 0; u8 < 8; ++u8) {
+                const int idx = base + u8;
+                e8[u8] = idx < total ? ids[(long long)cid[idx / k] * k + (idx - (idx / k) * k)] : -1;
             }
-            if (h == -1) break;
-            slot = (slot + 1) & (hs - 1);
+#pragma unroll
+            for (int u8 = 0; u8 < 8; ++u8) {
+                const int32_t e = e8[u8];
+                if (e < 0) continue;
+                const int i = (base + u8) / k;
+                int slot = jhash(e, hs);
+                for (int probe = 0; probe < hs; ++probe) {
+                    const int32_t h = hk[slot];
+                    if (h == e) {
+                        const int j = hv[slot];
+                        atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
+                        break;
+                    }
+                    if (h == -1) break;
+                    slot = (slot + 1) & (hs - 1);
+                }
+            }
         }
     }
+    if (METRIC == FGIM_IP)
+        for (int i = tid; i < nc; i += kJThreads) {
+            float ss = 0.f;
+            for (int c = 0; c < d; ++c) ss = fmaf(rows[i * stride + c], rows[i * stride + c], ss);
+            nrm[i] = sqrtf(ss) * 1.0001f;
+        }
     __syncthreads();
 
-    float* As = tiles;                        // [2][kJT][kJP]
-    float* Bs = tiles + 2 * kJT * kJP;        // [2][kJT][kJP]
-    const int nchunk = d >> 2;
-    const int nslice = (d + kJK - 1) / kJK;
+    const int grp = tid >> 6;
+    const int gt = tid & 63;
+    const int tx = gt & 7, ty = gt >> 3;
+    uint32_t* gq = queue + grp * kSQueue;
+    int* gqn = misc + 1 + grp;
+    const int RT = (nn + kST - 1) / kST, CT = (nc + kST - 1) / kST;
     unsigned long long my_pairs = 0;
-
-    for (int r0 = 0; r0 < nn; r0 += kJT) {
-        for (int c0 = 0; c0 < nc; c0 += kJT) {
-            const int cmaxj = min(c0 + kJT, nc) - 1;
-            if (cmaxj <= r0) continue;   // no pair with j > i in this tile
+    int tile_no = 0;
+    for (int rt = 0; rt < RT; ++rt) {
+        for (int ct = 0; ct < CT; ++ct) {
+            const int r0 = rt * kST, c0 = ct * kST;
+            if (min(c0 + kST, nc) - 1 <= r0) continue;     // no pair with j > i
+            const bool mine = (tile_no++ % kSGroups) == grp;
+            if (!mine) continue;
             float acc[4][4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int bb = 0; bb < 4; ++bb)
+                for (int b = 0; b < 4; ++b)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[a][bb][q] = 0.f;
-
-            auto load_slice = [&](int buf, int sl) {
-                for (int item = tid; item < 2 * kJT * (kJK / 4); item += kJThreads) {
-                    const int mat = item / (kJT * (kJK / 4));
-                    const int rem = item - mat * (kJT * (kJK / 4));
-                    const int r = rem / (kJK / 4);
-                    const int c = rem - r * (kJK / 4);
-                    const int idx = (mat == 0 ? r0 : c0) + r;
-                    const int lim = mat == 0 ? nn : nc;
-                    const int gc = sl * (kJK / 4) + c;
-                    const bool ok = idx < lim && gc < nchunk;
-                    const float* src = ok ? X + (long long)cid[idx] * d + gc * 4 : X;
-                    float* dst = (mat == 0 ? As : Bs) + (buf * kJT + r) * kJP + c * 4;
-                    cp_async16(dst, src, ok);
-                }
-                cp_async_commit();
-            };
-            load_slice(0, 0);
-            for (int sl = 0; sl < nslice; ++sl) {
-                const int buf = sl & 1;
-                if (sl + 1 < nslice) {
-                    load_slice(buf ^ 1, sl + 1);
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
-                }
-                __syncthreads();
-                const float* Ab = As + buf * kJT * kJP;
-                const float* Bb = Bs + buf * kJT * kJP;
+                    for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+            const float* ar[4];
+            const float* br[4];
 #pragma unroll
-                for (int c = 0; c < kJK / 4; ++c) {
-                    float4 av[4], bv[4];
+            for (int a = 0; a < 4; ++a) ar[a] = rows + min(r0 + ty + 8 * a, nc - 1) * stride;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(Ab + (ty + 16 * a) * kJP + c * 4);
+            for (int b = 0; b < 4; ++b) br[b] = rows + min(c0 + tx + 8 * b, nc - 1) * stride;
+            for (int c = 0; c < vq; ++c) {
+                float4 av[4], bv[4];
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) bv[bb] = *reinterpret_cast<const float4*>(Bb + (tx + 16 * bb) * kJP + c * 4);
+                for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(ar[a] + c * 4);
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b) bv[b] = *reinterpret_cast<const float4*>(br[b] + c * 4);
 #pragma unroll
-                        for (int bb = 0; bb < 4; ++bb) {
-                            if (METRIC == FGIM_L2SQ) {
-                                const float e0 = __fsub_rn(av[a].x, bv[bb].x), e1 = __fsub_rn(av[a].y, bv[bb].y);
-                                const float e2 = __fsub_rn(av[a].z, bv[bb].z), e3 = __fsub_rn(av[a].w, bv[bb].w);
-                                acc[a][bb][0] = fmaf(e0, e0, acc[a][bb][0]);
-                                acc[a][bb][1] = fmaf(e1, e1, acc[a][bb][1]);
-                                acc[a][bb][2] = fmaf(e2, e2, acc[a][bb][2]);
-                                acc[a][bb][3] = fmaf(e3, e3, acc[a][bb][3]);
-                            } else {
-                                acc[a][bb][0] = fmaf(av[a].x, bv[bb].x, acc[a][bb][0]);
-                                acc[a][bb][1] = fmaf(av[a].y, bv[bb].y, acc[a][bb][1]);
-                                acc[a][bb][2] = fmaf(av[a].z, bv[bb].z, acc[a][bb][2]);
-                                acc[a][bb][3] = fmaf(av[a].w, bv[bb].w, acc[a][bb][3]);
-                            }
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if (METRIC == FGIM_L2SQ) {
+                            const float e0 = av[a].x - bv[b].x, e1 = av[a].y - bv[b].y;
+                            const float e2 = av[a].z - bv[b].z, e3 = av[a].w - bv[b].w;
+                            acc[a][b][0] = fmaf(e0, e0, acc[a][b][0]);
+                            acc[a][b][1] = fmaf(e1, e1, acc[a][b][1]);
+                            acc[a][b][2] = fmaf(e2, e2, acc[a][b][2]);
+                            acc[a][b][3] = fmaf(e3, e3, acc[a][b][3]);
+                        } else {
+                            acc[a][b][0] = fmaf(av[a].x, bv[b].x, acc[a][b][0]);
+                            acc[a][b][1] = fmaf(av[a].y, bv[b].y, acc[a][b][1]);
+                            acc[a][b][2] = fmaf(av[a].z, bv[b].z, acc[a][b][2]);
+                            acc[a][b][3] = fmaf(av[a].w, bv[b].w, acc[a][b][3]);
                         }
-                }
-                __syncthreads();
+                    }
             }
-            // epilogue: distances, filters, proposals
-            uint32_t emit = 0;   // bit (a*4+bb)*2 + dir
-            float dl[4][4];
+            // filter: queue (i, j, directions) of the pairs that may pass
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-                    const int i = r0 + ty + 16 * a;
-                    const int j = c0 + tx + 16 * bb;
-                    const float s = __fadd_rn(__fadd_rn(acc[a][bb][0], acc[a][bb][1]),
-                                              __fadd_rn(acc[a][bb][2], acc[a][bb][3]));
-                    float dd;
-                    if (METRIC == FGIM_L2SQ) dd = s;
-                    else if (METRIC == FGIM_IP) dd = __fsub_rn(1.f, s);
-                    else dd = __fsub_rn(1.f, __fmul_rn(s, (i < nc && j < nc) ? __fmul_rn(cinv[i], cinv[j]) : 1.f));
-                    dl[a][bb] = dd;
-                    if (i < nn && j < nc && j > i && csh[i] != csh[j]) {
-                        ++my_pairs;
-                        if (!((mask[i * W + (j >> 5)] >> (j & 31)) & 1u) && mkkey(dd, cid[j]) < thr[i])
-                            emit |= 1u << ((a * 4 + bb) * 2);
-                        if (!((mask[j * W + (i >> 5)] >> (i & 31)) & 1u) && mkkey(dd, cid[i]) < thr[j])
-                            emit |= 1u << ((a * 4 + bb) * 2 + 1);
+                for (int b = 0; b < 4; ++b) {
+                    const int i = r0 + ty + 8 * a;
+                    const int j = c0 + tx + 8 * b;
+                    if (!(i < nn && j < nc && j > i && csh[i] != csh[j])) continue;
+                    ++my_pairs;
+                    const float s = (acc[a][b][0] + acc[a][b][1]) + (acc[a][b][2] + acc[a][b][3]);
+                    float lo;   // lower bound of the canonical distance
+                    if (METRIC == FGIM_L2SQ) lo = s - eps * s;
+                    else if (METRIC == FGIM_IP) lo = (1.f - s) - eps * nrm[i] * nrm[j];
+                    else lo = (1.f - s * cinv[i] * cinv[j]) - 2.f * eps;
+                    unsigned dm = 0;
+                    if (!((mask[i * W + (j >> 5)] >> (j & 31)) & 1u) &&
+                        (thr[i] == kEmptyKey || lo <= key_dist(thr[i])))
+                        dm |= 1u;
+                    if (!((mask[j * W + (i >> 5)] >> (i & 31)) & 1u) &&
+                        (thr[j] == kEmptyKey || lo <= key_dist(thr[j])))
+                        dm |= 2u;
+                    if (dm) {
+                        const int slot = atomicAdd(gqn, 1);
+                        gq[slot] = (uint32_t)i | ((uint32_t)j << 10) | (dm << 20);
                     }
                 }
-            const int cnt = __popc(emit);
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
+            group_sync(grp);
+            // re-rank the queued pairs with the canonical distance (one pair per warp step)
+            const int nq = *gqn;
+            const int gw = gt >> 5;   // warp within the group
+            for (int qi = gw; qi < nq; qi += 2) {
+                const uint32_t e = gq[qi];
+                const int i = e & 1023, j = (e >> 10) & 1023;
+                const unsigned dm = (e >> 20) & 3u;
+                const float sc = warp_butterfly(lane_part<METRIC>(reinterpret_cast<const float4*>(rows + i * stride),
+                                                                  reinterpret_cast<const float4*>(rows + j * stride),
+                                                                  vq, lane));
+                if (lane < 2 && ((dm >> lane) & 1u)) {
+                    const float dd = delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(cinv[i], cinv[j]) : 1.f);
+                    const int a = lane == 0 ? i : j, b = lane == 0 ? j : i;
+                    const uint64_t key = mkkey(dd, cid[b]);
+                    if (key < thr[a]) {
+                        const int slot = atomicAdd(misc, 1);
+                        if (slot < kPropBuf) {
+                            pb_tgt[slot] = cid[a];
+                            pb_key[slot] = key;
+                        } else {
+                            const unsigned long long pos = atomicAdd(prop_count, 1ull);
+                            if (pos < (unsigned long long)prop_cap) {
+                                prop_tgt[pos] = cid[a];
+                                prop_key[pos] = key;
+                            } else {
+                                pending[v] = 1;
+                                atomicOr(status, kErrOverflow);
+                            }
+                        }
+                    }
+                }
             }
-            const int wtotal = __shfl_sync(kFull, incl, 31);
-            unsigned long long base = 0;
-            if (wtotal > 0) {
-                if (lane == 31) base = atomicAdd(prop_count, (unsigned long long)wtotal);
-                base = __shfl_sync(kFull, base, 31);
-                unsigned long long pos = base + (unsigned long long)(incl - cnt);
-                bool dropped = false;
-                uint32_t m = emit;
-                while (m) {
-                    const int bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int ab = bit >> 1, dir = bit & 1;
-                    const int a = ab >> 2, bb = ab & 3;
-                    const int i = r0 + ty + 16 * a;
-                    const int j = c0 + tx + 16 * bb;
-                    if (pos < (unsigned long long)prop_cap) {
-                        prop_tgt[pos] = dir == 0 ? cid[i] : cid[j];
-                        prop_key[pos] = mkkey(dl[a][bb], dir == 0 ? cid[j] : cid[i]);
-                    } else {
-                        dropped = true;
-                    }
-                    ++pos;
-                }
-                if (dropped) {
-                    pending[v] = 1;
-                    atomicOr(status, kErrOverflow);
-                }
+            group_sync(grp);
+            if (gt == 0) *gqn = 0;
+            group_sync(grp);
+        }
+    }
+    __syncthreads();
+    // buffered proposals leave with one reservation
+    const int nb = min(misc[0], kPropBuf);
+    __shared__ unsigned long long base_s;
+    if (tid == 0 && nb > 0) base_s = atomicAdd(prop_count, (unsigned long long)nb);
+    __syncthreads();
+    if (nb > 0) {
+        const unsigned long long base = base_s;
+        for (int i = tid; i < nb; i += kJThreads) {
+            const unsigned long long pos = base + i;
+            if (pos < (unsigned long long)prop_cap) {
+                prop_tgt[pos] = pb_tgt[i];
+                prop_key[pos] = pb_key[i];
+            } else {
+                pending[v] = 1;
+                atomicOr(status, kErrOverflow);
             }
         }
     }
-    // pairs evaluated by this CTA
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(kFull, my_pairs, o);
     if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
@@ -498,23 +563,37 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         int* status, cudaStream_t s) {
     if (nv <= 0) return cudaSuccess;
-    const JoinLayout L = join_layout(b.cmax);
-    const size_t smem = L.bytes;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_J(MT)                                                                                        \
-    do {                                                                                                         \
-        e = cudaFuncSetAttribute(k_join<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
-        if (e != cudaSuccess) break;                                                                             \
-        LaunchScope ls("k_join", s);                                                                             \
-        k_join<MT><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand, b.nn, b.no, \
-                                                         b.cmax, vlist, b.prop_tgt, b.prop_key, b.prop_count,    \
-                                                         b.prop_cap, b.pending, pairs, status);                  \
-        e = cudaGetLastError();                                                                                  \
+    // largest candidate set of this pass sizes the staged variant's shared memory
+    if ((e = cudaMemsetAsync(b.max_nc, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    {
+        LaunchScope ls("k_max_nc", s);
+        k_max_nc<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, b.max_nc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int32_t cm = 0;
+    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    cm = *b.host_i32;
+    if (cm < 2) return cudaSuccess;
+    const StagedLayout SL = staged_layout(cm, g.k, t.dim);
+    if (SL.bytes > 227 * 1024) return cudaErrorNotSupported;
+    const size_t smem = SL.bytes;
+#define FGIM_LAUNCH_JS(MT)                                                                                        \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_join_staged<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (e != cudaSuccess) break;                                                                              \
+        LaunchScope ls("k_join", s);                                                                              \
+        k_join_staged<MT><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand, b.nn,  \
+                                                                b.no, b.cmax, cm, vlist, b.prop_tgt, b.prop_key,  \
+                                                                b.prop_count, b.prop_cap, b.pending, pairs,       \
+                                                                status);                                          \
+        e = cudaGetLastError();                                                                                   \
     } while (0)
-    if (metric == FGIM_L2SQ) FGIM_LAUNCH_J(FGIM_L2SQ);
-    else if (metric == FGIM_IP) FGIM_LAUNCH_J(FGIM_IP);
-    else FGIM_LAUNCH_J(FGIM_COSINE);
-#undef FGIM_LAUNCH_J
+    if (metric == FGIM_L2SQ) FGIM_LAUNCH_JS(FGIM_L2SQ);
+    else if (metric == FGIM_IP) FGIM_LAUNCH_JS(FGIM_IP);
+    else FGIM_LAUNCH_JS(FGIM_COSINE);
+#undef FGIM_LAUNCH_JS
     return e;
 }
 

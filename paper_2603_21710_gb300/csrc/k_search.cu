@@ -2,9 +2,10 @@
 //
 // One warp runs one beam search. The pool C (<= L keys, sorted by (delta, id)) and its
 // "expanded" marks live in shared memory; each expansion reads the expanded vertex's
-// adjacency row (one id per lane), drops ids already evaluated, computes the distances
-// of the rest (one neighbour per lane, canonical distance, query in shared memory) and
-// merges them into the pool with warp_merge.
+// adjacency row (one id per lane), drops ids already evaluated, compacts the rest, loads
+// their rows coalesced (each warp load covers one row, eight rows in flight), forms the
+// canonical distances of up to 32 rows with one transpose reduction, and merges them
+// into the pool with warp_merge.
 //
 // Evaluated ids are remembered in a small direct-mapped table that may forget an id
 // when another id lands on its slot (never the reverse). A forgotten id is evaluated
@@ -25,28 +26,74 @@ struct WarpCounters {
     long long hops = 0;
 };
 
+// Canonical distances between the query (q in shared memory; qreg = this lane's chunk when
+// d <= 128) and the U <= 32 rows base[rid[r]]; lane r receives row r's distance. Rows load
+// coalesced (one warp load per row, eight rows in flight); every lane stores its partials in
+// P (32 x 33 floats of this warp's shared memory) and lane r re-adds row r in tree order.
+template <int METRIC, bool SMALLD>
+__device__ __forceinline__ float rows_delta(const float* __restrict__ base, const int32_t* rid, int U, const float* q,
+                                            float4 qreg, int d, int lane, float* P) {
+    const int nc4 = d >> 2;
+    if (SMALLD) {
+        const bool has = lane < nc4;
+        for (int b = 0; b < U; b += 8) {
+            float4 y[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int r = b + t;
+                y[t] = (r < U && has) ? reinterpret_cast<const float4*>(base + (long long)rid[r] * d)[lane]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int r = b + t;
+                if (r < U) P[lane * 33 + r] = has ? chunk_part<METRIC>(qreg, y[t]) : 0.f;
+            }
+        }
+    } else {
+        for (int r = 0; r < U; ++r)
+            P[lane * 33 + r] = lane_part<METRIC>(reinterpret_cast<const float4*>(q),
+                                                 reinterpret_cast<const float4*>(base + (long long)rid[r] * d), nc4,
+                                                 lane);
+    }
+    __syncwarp();
+    const float s = lane < U ? smem_tree_sum(P, lane) : 0.f;
+    __syncwarp();
+    return s;
+}
+
 // Alg. 1 over one graph whose rows are Xt[v] / adj[v * M] for local ids v < nt. Keys carry
 // global ids (local + id_off). Returns the pool size (<= L); the pool stays sorted.
-template <int METRIC>
+// scratch: 32 ints of shared memory for the compacted neighbour ids.
+template <int METRIC, bool SMALLD>
 __device__ int beam_search(const float* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
-                           int M, long long nt, int ep, long long id_off, const float* q, float qinv, int d, int L,
-                           uint64_t* pool, uint8_t* pflag, int32_t* ht, int htbits, WarpCounters& ctr, int* status) {
+                           int M, long long nt, int ep, long long id_off, const float* q, float4 qreg, float qinv,
+                           int d, int L, uint64_t* pool, uint8_t* pflag, int32_t* ht, int htbits, int32_t* scratch,
+                           float* P, WarpCounters& ctr, int* status) {
     const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
     const int H = 1 << htbits;
     for (int s = lane; s < H; s += 32) ht[s] = -1;
+    if (lane == 0) scratch[0] = ep;
     __syncwarp();
-    uint64_t key = kEmptyKey;
     if (ep < 0 || ep >= nt) {
         if (lane == 0) atomicOr(status, kErrBounds);
         return 0;
     }
-    if (lane == 0) {
-        float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[ep]) : 1.f;
-        key = mkkey(delta_fn<METRIC>(q, Xt + (long long)ep * d, d, inv), (int32_t)(ep + id_off));
-        ht[ht_slot(ep, htbits)] = ep;
-        ctr.ndc++;
+    {
+        const float dd = rows_delta<METRIC, SMALLD>(Xt, scratch, 1, q, qreg, d, lane, P);
+        uint64_t key = kEmptyKey;
+        if (lane == 0) {
+            const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[ep]) : 1.f;
+            key = mkkey(delta_finish<METRIC>(dd, inv), (int32_t)(ep + id_off));
+            ht[ht_slot(ep, htbits)] = ep;
+            ctr.ndc++;
+        }
+        __syncwarp();
+        int n0 = warp_merge<false>(pool, pflag, 0, L, key, 0);
+        (void)n0;
     }
-    int n = warp_merge<false>(pool, pflag, 0, L, key, 0);
+    int n = 1;
     // every vertex is expanded at most once, so nt + 1 iterations always suffice
     for (long long it = 0; it <= nt; ++it) {
         int first = -1;
@@ -78,12 +125,20 @@ __device__ int beam_search(const float* __restrict__ Xt, const float* __restrict
                 if (ht[s] == v) v = -1;
                 else ht[s] = v;
             }
+            const unsigned m = __ballot_sync(kFull, v >= 0);
+            const int U = __popc(m);
+            if (U == 0) continue;
+            if (v >= 0) scratch[__popc(m & lt)] = v;
+            __syncwarp();
+            const float dd = rows_delta<METRIC, SMALLD>(Xt, scratch, U, q, qreg, d, lane, P);
             uint64_t cand = kEmptyKey;
-            if (v >= 0) {
-                float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[v]) : 1.f;
-                cand = mkkey(delta_fn<METRIC>(q, Xt + (long long)v * d, d, inv), (int32_t)(v + id_off));
+            if (lane < U) {
+                const int32_t w = scratch[lane];
+                const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[w]) : 1.f;
+                cand = mkkey(delta_finish<METRIC>(dd, inv), (int32_t)(w + id_off));
                 ctr.ndc++;
             }
+            __syncwarp();
             n = warp_merge<false>(pool, pflag, n, L, cand, 0);
         }
     }
@@ -106,7 +161,7 @@ __device__ __forceinline__ void warp_add_counters(WarpCounters& c, unsigned long
 
 // shared-memory layout of one warp; all offsets multiples of 16 bytes
 struct WarpLayout {
-    int q, pool, pflag, ht, res, bytes;
+    int q, pool, pflag, ht, res, scratch, part, bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -124,6 +179,10 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
     o += align16((1 << htbits) * 4);
     w.res = o;
     o += align16(kres * 8);
+    w.scratch = o;
+    o += 32 * 4;
+    w.part = o;
+    o += 32 * 33 * 4;
     w.bytes = o;
     return w;
 }
@@ -131,7 +190,7 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 // Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
 // (delta, id), write ids / distances / new flags.
-template <int METRIC>
+template <int METRIC, bool SMALLD>
 __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* __restrict__ X,
                                                      const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
@@ -140,6 +199,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (g >= N) return;
     const int d = t.dim;
@@ -150,12 +210,15 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
     uint64_t* res = reinterpret_cast<uint64_t*>(base + lay.res);
+    int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
+    float* P = reinterpret_cast<float*>(base + lay.part);
 
     const float4* src = reinterpret_cast<const float4*>(X + g * d);
     float4* q4 = reinterpret_cast<float4*>(q);
     for (int c = lane; c < (d >> 2); c += 32) q4[c] = src[c];
     const float qinv = (METRIC == FGIM_COSINE) ? inv_norm[g] : 1.f;
     __syncwarp();
+    const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
 
     WarpCounters ctr;
     const int i = shard_of(t, g);
@@ -171,22 +234,30 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
             atomicOr(status, kErrBounds);
             v = -1;
         }
+        if (v == u) v = -1;
+        const unsigned m = __ballot_sync(kFull, v >= 0);
+        const int U = __popc(m);
+        if (U == 0) continue;
+        if (v >= 0) scratch[__popc(m & lt)] = (int32_t)(t.off[i] + v);
+        __syncwarp();
+        const float dd = rows_delta<METRIC, SMALLD>(X, scratch, U, q, qreg, d, lane, P);
         uint64_t cand = kEmptyKey;
-        if (v >= 0 && v != u) {
-            const long long gv = t.off[i] + v;
-            float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, inv_norm[gv]) : 1.f;
-            cand = mkkey(delta_fn<METRIC>(q, X + gv * d, d, inv), (int32_t)gv);
+        if (lane < U) {
+            const int32_t gv = scratch[lane];
+            const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, inv_norm[gv]) : 1.f;
+            cand = mkkey(delta_finish<METRIC>(dd, inv), gv);
             ctr.ndc++;
         }
+        __syncwarp();
         nres = warp_merge<true>(res, nullptr, nres, k, cand, 0);
     }
     // Alg. 2 lines 6-7: cross querying of every other index
     for (int j = 0; j < t.h; ++j) {
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
-        const int np = beam_search<METRIC>(X + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr, t.adj[j],
-                                           t.M[j], nj, t.entry[j], t.off[j], q, qinv, d, L, pool, pflag, ht, htbits,
-                                           ctr, status);
+        const int np = beam_search<METRIC, SMALLD>(X + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr,
+                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, qinv, d, L,
+                                                   pool, pflag, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
             const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
             nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
@@ -210,7 +281,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
 
 // Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
 // (qids == nullptr) or rows qids[i] of X.
-template <int METRIC>
+template <int METRIC, bool SMALLD>
 __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
                                                 int entry, const float* __restrict__ Q,
@@ -229,6 +300,8 @@ __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, con
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
     uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
+    int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
+    float* P = reinterpret_cast<float*>(base + lay.part);
     const float* qsrc = qids ? X + (long long)qids[qi] * d : Q + qi * d;
     const float4* src = reinterpret_cast<const float4*>(qsrc);
     float4* q4 = reinterpret_cast<float4*>(q);
@@ -236,9 +309,10 @@ __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, con
     float qinv = 1.f;
     if (METRIC == FGIM_COSINE) qinv = qids ? inv_norm[qids[qi]] : q_inv[qi];
     __syncwarp();
+    const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     WarpCounters ctr;
-    const int np = beam_search<METRIC>(X, inv_norm, graph, R, n, entry, 0, q, qinv, d, L, pool, pflag, ht, htbits,
-                                       ctr, status);
+    const int np = beam_search<METRIC, SMALLD>(X, inv_norm, graph, R, n, entry, 0, q, qreg, qinv, d, L, pool, pflag,
+                                               ht, htbits, scratch, P, ctr, status);
     for (int s = lane; s < topk; s += 32) {
         if (s < np) {
             out_ids[qi * topk + s] = key_id(pool[s]);
@@ -259,6 +333,18 @@ static int ht_bits_for(int L) {
     return b;
 }
 
+#define FGIM_DISPATCH_METRIC_D(M, D, MACRO)                          \
+    do {                                                             \
+        const bool small_ = (D) <= 128;                              \
+        if ((M) == FGIM_L2SQ) {                                      \
+            if (small_) MACRO(FGIM_L2SQ, true); else MACRO(FGIM_L2SQ, false);       \
+        } else if ((M) == FGIM_IP) {                                 \
+            if (small_) MACRO(FGIM_IP, true); else MACRO(FGIM_IP, false);           \
+        } else {                                                     \
+            if (small_) MACRO(FGIM_COSINE, true); else MACRO(FGIM_COSINE, false);   \
+        }                                                            \
+    } while (0)
+
 cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float* inv_norm, long long N, int metric,
                                int k, int L, fgim_knng* out, unsigned long long* counters, int* status,
                                cudaStream_t s) {
@@ -269,18 +355,16 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float*
     const long long blocks = (N + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_CQ(MT)                                                                                         \
+#define FGIM_LAUNCH_CQ(MT, SD)                                                                                     \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_cross_query<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+        e = cudaFuncSetAttribute(k_cross_query<MT, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_cross_query", s);                                                                        \
-        k_cross_query<MT><<<(unsigned)blocks, wpb * 32, smem, s>>>(t, X, inv_norm, N, k, L, htbits, out->ids,     \
-                                                                   out->dist, out->flags, counters, status);       \
+        k_cross_query<MT, SD><<<(unsigned)blocks, wpb * 32, smem, s>>>(t, X, inv_norm, N, k, L, htbits, out->ids, \
+                                                                       out->dist, out->flags, counters, status);   \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (metric == FGIM_L2SQ) FGIM_LAUNCH_CQ(FGIM_L2SQ);
-    else if (metric == FGIM_IP) FGIM_LAUNCH_CQ(FGIM_IP);
-    else FGIM_LAUNCH_CQ(FGIM_COSINE);
+    FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ);
 #undef FGIM_LAUNCH_CQ
     return e;
 }
@@ -296,19 +380,17 @@ cudaError_t launch_search(const float* X, const float* inv_norm, long long n, in
     const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_S(MT)                                                                                          \
+#define FGIM_LAUNCH_S(MT, SD)                                                                                      \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_search<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+        e = cudaFuncSetAttribute(k_search<MT, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_search", s);                                                                             \
-        k_search<MT><<<(unsigned)blocks, wpb * 32, smem, s>>>(X, inv_norm, n, d, graph, R, entry, Q, q_inv, qids, \
-                                                              nq, topk, L, htbits, out_ids, out_dist, counters,   \
-                                                              status);                                             \
+        k_search<MT, SD><<<(unsigned)blocks, wpb * 32, smem, s>>>(X, inv_norm, n, d, graph, R, entry, Q, q_inv,   \
+                                                                  qids, nq, topk, L, htbits, out_ids, out_dist,   \
+                                                                  counters, status);                               \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (metric == FGIM_L2SQ) FGIM_LAUNCH_S(FGIM_L2SQ);
-    else if (metric == FGIM_IP) FGIM_LAUNCH_S(FGIM_IP);
-    else FGIM_LAUNCH_S(FGIM_COSINE);
+    FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S);
 #undef FGIM_LAUNCH_S
     return e;
 }

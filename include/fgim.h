@@ -187,6 +187,27 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
                         const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
                         int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream);
 
+/*
+ * fgim_search for callers that cannot allocate device memory while they run: processes
+ * whose device memory belongs to a pool they do not control, latency-critical paths where
+ * an allocation (and the synchronisation it may bring) is not allowed, plug-ins inside a
+ * host that forbids allocator calls. Same arguments and results as fgim_search; the paper
+ * has no counterpart (this is a deployment variant of the evaluation search).
+ * Its scratch (status word, counters and, for cosine, the inverse norms of the base and of
+ * the queries) lives in one fixed device array inside the library, kept on every device
+ * that loads the library until the process exits. Limits: cosine search accepts at most
+ * 1,048,576 base vectors and 65,536 queries (larger calls return FGIM_EINVAL); the other
+ * metrics have no extra limit. The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress): make that first call before any stream capture. All calls share
+ * the array, so calls that overlap on the GPU race and must be serialised by the caller.
+ * Calls no allocator (no cudaMalloc, cudaMallocAsync, cudaFree, no host allocation) as long
+ * as launch profiling is off; errors are returned as status codes only (fgim_last_error()
+ * is not updated).
+ */
+fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                                const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
+                                int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream);
+
 /* Counters of the last merge/search call made by this host thread. */
 void fgim_last_stats(fgim_stats* out);
 

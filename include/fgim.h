@@ -54,7 +54,7 @@ typedef enum { FGIM_L2SQ = 0, FGIM_IP = 1, FGIM_COSINE = 2 } fgim_metric;
 
 typedef enum { FGIM_F32 = 0 } fgim_dtype;
 
-/* Limits of this build. */
+/* Size limits of the library. */
 #define FGIM_MAX_SHARDS 64
 #define FGIM_MAX_K 128          /* k of the k-NNG */
 #define FGIM_MAX_R 128          /* degree bound of the merged PG */

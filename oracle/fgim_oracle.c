@@ -107,7 +107,7 @@ static int32_t knn_search_tagged(const float* X, int32_t d, int32_t metric, cons
     int32_t n = 0;
     int64_t ndc = 0, hops = 0;
 
-    /* line 1: C <- {(ep, delta(ep, q))} */
+    /* start: C <- {(ep, delta(ep, q))} */
     seen[ep] = tag;
     cd[0] = or_delta(q, X + (int64_t)ep * d, d, metric);
     ci[0] = ep;
@@ -115,15 +115,15 @@ static int32_t knn_search_tagged(const float* X, int32_t d, int32_t metric, cons
     n = 1;
     ndc++;
     for (;;) {
-        /* line 8: i <- index of the first unexpanded vertex in C */
+        /* i <- index of the first unexpanded vertex in C */
         int32_t i = 0;
         while (i < n && cx[i]) ++i;
         if (i >= n) break;                 /* no unexpanded vertex left */
-        /* lines 3-4: u <- C[i], mark u as visited (expanded) */
+        /* u <- C[i], mark u as visited (expanded) */
         cx[i] = 1;
         int32_t u = ci[i];
         hops++;
-        /* lines 5-6: insert every not-yet-seen neighbour v of u */
+        /* insert every not-yet-seen neighbour v of u */
         for (int32_t t = 0; t < M; ++t) {
             int32_t v = adj[(int64_t)u * M + t];
             if (v < 0) continue;
@@ -131,7 +131,7 @@ static int32_t knn_search_tagged(const float* X, int32_t d, int32_t metric, cons
             seen[v] = tag;
             float dv = or_delta(q, X + (int64_t)v * d, d, metric);
             ndc++;
-            /* line 7: keep the top-L of C by (delta, id) */
+            /* keep the top-L of C by (delta, id) */
             if (n == L && !key_lt(dv, v, cd[n - 1], ci[n - 1])) continue;
             int32_t pos = n < L ? n : L - 1;
             while (pos > 0 && key_lt(dv, v, cd[pos - 1], ci[pos - 1])) {
@@ -146,7 +146,7 @@ static int32_t knn_search_tagged(const float* X, int32_t d, int32_t metric, cons
             if (n < L) ++n;
         }
     }
-    /* line 9: the first k results */
+    /* result: the first k entries */
     int32_t r = n < k ? n : k;
     for (int32_t t = 0; t < r; ++t) {
         out_ids[t] = ci[t];
@@ -237,7 +237,7 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
             int i = shard_of(in, g);
             int64_t u = g - in->off[i];
             int32_t n = 0;
-            /* line 5: local candidate neighbours C_i^+(u) from G_i, mapped by phi */
+            /* local candidate neighbours C_i^+(u) from G_i, mapped by phi */
             for (int32_t t = 0; t < in->M; ++t) {
                 int32_t v = in->adj[g * in->M + t];
                 if (v < 0 || v == u) continue;
@@ -247,7 +247,7 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
                 ls.ndc++;
                 ++n;
             }
-            /* lines 6-7: cross querying, KNNSearch(x_u, G_j, L, L, ep_j) for every j != i */
+            /* cross querying, KNNSearch(x_u, G_j, L, L, ep_j) for every j != i */
             for (int j = 0; j < h; ++j) {
                 if (j == i) continue;
                 int64_t nj = in->off[j + 1] - in->off[j];
@@ -266,7 +266,7 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
                     ++n;
                 }
             }
-            /* lines 8-10: sort by distance, map ids (done above), resize(C, k) */
+            /* sort by distance, map ids (done above), resize(C, k) */
             qsort(C, n, sizeof(ent_t), ent_cmp);
             int32_t w = 0;
             for (int32_t t = 0; t < n && w < k; ++t) {
@@ -496,31 +496,31 @@ static void resort_entry(int32_t* ids, float* dist, uint8_t* flags, int32_t k, i
 void or_indegree_repair(const or_input* in, int32_t k, int32_t* ids, float* dist, uint8_t* flags,
                         int32_t* T, or_stats* st) {
     const int64_t N = in->off[in->h];
-    /* line 1: T <- indegree of every vertex */
+    /* T <- indegree of every vertex */
     or_indegree(ids, N, k, T);
     for (int64_t t = 0; t < N * k; ++t) flags[t] &= (uint8_t)~OR_FLAG_REPLACED;
     int64_t zero_before = 0, replaced = 0;
-    /* line 2: every v* with T(v*) = 0, ascending id */
+    /* every v* with T(v*) = 0, ascending id */
     for (int64_t vs = 0; vs < N; ++vs) {
         if (T[vs] != 0) continue;
         ++zero_before;
         int done = 0;
-        /* lines 3-4: neighbours v of v*, closest first, until T(v*) > 0 */
+        /* neighbours v of v*, closest first, until T(v*) > 0 */
         for (int32_t a = 0; a < k && !done; ++a) {
             int32_t v = ids[vs * k + a];
             if (v < 0) break;
             int32_t* lv = ids + (int64_t)v * k;
             float* dv = dist + (int64_t)v * k;
             uint8_t* fv = flags + (int64_t)v * k;
-            /* line 5: v' in N(v) in descending order of distance to x_v */
+            /* v' in N(v) in descending order of distance to x_v */
             for (int32_t b = k - 1; b >= 0; --b) {
                 int32_t vp = lv[b];
                 if (vp < 0) continue;
-                /* line 6: not replaced and T(v') > 1. (Within one call a replaced entry holds a
+                /* not replaced and T(v') > 1. (Within one call a replaced entry holds a
                  * vertex whose indegree just became 1, so the T test alone would skip it too;
                  * the mark is kept because the paper states it.) */
                 if ((fv[b] & OR_FLAG_REPLACED) || T[vp] <= 1) continue;
-                /* lines 7-10 */
+                /* replace v' by v*, mark it, update T */
                 lv[b] = (int32_t)vs;
                 dv[b] = dist_g(in, v, vs);
                 fv[b] = OR_FLAG_NEW | OR_FLAG_REPLACED;
@@ -555,12 +555,12 @@ void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* di
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : evals)
     for (int64_t u = 0; u < N; ++u) {
         int32_t nr = 0;
-        /* line 4: v in N_G(u) in ascending order of delta(u, v) */
+        /* v in N_G(u) in ascending order of delta(u, v) */
         for (int32_t t = 0; t < k; ++t) {
             int32_t v = ids[u * k + t];
             if (v < 0) break;
             float duv = dist[u * k + t];
-            /* line 5: T(v) = 1, or delta(u,v) < alpha^2 * delta(w,v) for every kept w */
+            /* T(v) = 1, or delta(u,v) < alpha^2 * delta(w,v) for every kept w */
             int keep = T[v] == 1;
             if (!keep) {
                 keep = 1;
@@ -576,7 +576,7 @@ void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* di
                 e_dist[u * R + nr] = duv;
                 ++nr;
             }
-            /* line 7: break if |R| = bound */
+            /* stop once |R| reaches the bound */
             if (nr == R) break;
         }
         e_cnt[u] = nr;
@@ -605,7 +605,7 @@ void or_reverse_insert(int64_t N, int32_t R, const int32_t* e_ids, const float* 
         }
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t u = 0; u < N; ++u) {
-        /* lines 10-12: N(u) U {v : (v, u) in E'}, sorted by distance, resized to the bound */
+        /* N(u) U {v : (v, u) in E'}, sorted by distance, resized to the bound */
         int64_t m = e_cnt[u] + (cnt[u + 1] - cnt[u]);
         ent_t* c = (ent_t*)malloc(sizeof(ent_t) * (m + 1));
         int64_t n = 0;

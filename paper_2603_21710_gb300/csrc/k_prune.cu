@@ -8,7 +8,7 @@
 // from the boundary than the rounding margin between it and the canonical distance; the few
 // decisions inside the margin are re-taken with the canonical distance (whole warp), so the
 // outcome is exactly that of the canonical distance.
-// A vertex whose only in-edge is u (T(v) = 1) is kept unconditionally (Alg. 5 line 5).
+// A vertex whose only in-edge is u (T(v) = 1) is kept unconditionally (Alg. 5).
 //
 // Connectivity enhancement builds the reverse lists of the pruned snapshot E' by a
 // counting sort and merges them into E'(u), keeping the R smallest (delta, id).

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     const long long u = g - t.off[i];
     const long long ni = t.off[i + 1] - t.off[i];
     int nres = 0;
-    // Alg. 2 line 5: local candidate neighbours, mapped to global ids by phi
+    // Alg. 2, local candidate neighbours C_i^+(u), mapped to global ids by phi
     const int Mi = t.M[i];
     const int32_t* arow = t.adj[i] + u * Mi;
     for (int c0 = 0; c0 < Mi; c0 += 32) {
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
         __syncwarp();
         nres = warp_merge<true>(res, nullptr, nres, k, cand, 0);
     }
-    // Alg. 2 lines 6-7: cross querying of every other index
+    // Alg. 2, cross querying of every other index
     for (int j = 0; j < t.h; ++j) {
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
             nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
         }
     }
-    // Alg. 2 lines 8-10: sorted, resized to k
+    // Alg. 2, sorted by distance and resized to k
     for (int s = lane; s < k; s += 32) {
         const long long o = g * k + s;
         if (s < nres) {

@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--n", type=int, default=WORKLOAD["N"], help="points (default: the full workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--join-filter", default="tc", choices=["tc", "fp32"],
+                    help="Update's pair filter: BF16 tensor-core tile (default) or FP32 SIMT tile")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form alongside")
     return ap.parse_args()
 
 
@@ -264,7 +267,7 @@ def run_fgim(args):
     adj = torch.from_numpy(adj_np).to(dev)
     entries = [g[1] for g in graphs]
     inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, entries, metric="l2")
-    kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=WORKLOAD["iters"])
+    kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=WORKLOAD["iters"], join_filter=args.join_filter)
     stream = torch.cuda.current_stream()
     out = None
     for _ in range(args.warmup):

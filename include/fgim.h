@@ -88,7 +88,12 @@ typedef struct {
     int32_t rev_cap;         /* cap of each reverse list in Visit; 0 = k */
     int32_t ensure_reachable;/* 1 = run the reachability fix after Alg. 5 */
     int32_t reach_beam;      /* pool of the searches of the reachability fix; 0 = 64 */
-    int32_t reserved[5];
+    int32_t join_filter;     /* Update's pair filter: 0 = BF16 tensor-core tile (tcgen05), 1 = FP32 SIMT
+                                tile. Both re-rank survivors with the exact FP32 distance, so the lists
+                                are the same; only speed differs. Passes whose shapes the tensor-core
+                                tile does not cover (dim % 16 != 0, |C_n| > 128, |C| > 256) use the
+                                FP32 tile. */
+    int32_t reserved[4];
 } fgim_params;
 
 /* k-NNG buffers, caller-owned device memory: [n, k] each. */

@@ -24,6 +24,8 @@ __all__ = ["MergeInput", "merge", "merge_host", "cross_query", "refine_pass", "i
 
 FLAG_NEW = 1
 FLAG_REPLACED = 2
+# Update's pair filter: BF16 tensor-core tile or FP32 SIMT tile (same results)
+JOIN_FILTERS = {"tc": 0, "bf16": 0, "fp32": 1, "simt": 1, 0: 0, 1: 1}
 
 
 def _stream() -> int:
@@ -83,11 +85,12 @@ class MergeInput:
         return cls(vs, ads, entries, metric)
 
     def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
-               reach_beam=0) -> Params:
+               reach_beam=0, join_filter="tc") -> Params:
         p = Params()
         p.dim, p.dtype, p.metric = self.d, 0, self.metric
         p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap = k, R, float(alpha), L, iters, rev_cap
         p.ensure_reachable, p.reach_beam = int(bool(ensure_reachable)), reach_beam
+        p.join_filter = JOIN_FILTERS[join_filter]
         return p
 
 
@@ -102,10 +105,11 @@ def _new_knng(N: int, k: int, device) -> dict:
 
 
 def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3, rev_cap: int = 0,
-          ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False) -> dict:
+          ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False,
+          join_filter="tc") -> dict:
     """Full merge (stages a, b, c and the reachability fix). Returns device tensors."""
     L_ = load()
-    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam)
+    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter)
     dev = inp.X.device
     out = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
            "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
@@ -125,7 +129,7 @@ def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters
 
 
 def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metric="l2", L: int = 0, iters: int = 3,
-               rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None) -> dict:
+               rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None, join_filter="tc") -> dict:
     """Merge from host memory (CPU tensors, pinned for speed); results land in host tensors."""
     L_ = load()
     if X.is_cuda or adj.is_cuda:
@@ -139,6 +143,7 @@ def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metri
     p.dim, p.dtype, p.metric = int(X.shape[1]), 0, _lib.METRICS[metric]
     p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap, p.ensure_reachable = k, R, float(alpha), L, iters, rev_cap, int(
         bool(ensure_reachable))
+    p.join_filter = JOIN_FILTERS[join_filter]
     sz = (ctypes.c_int32 * len(sizes))(*[int(s) for s in sizes])
     en = (ctypes.c_int32 * len(entries))(*[int(e) for e in entries])
     if out_ids is None:
@@ -162,11 +167,11 @@ def cross_query(inp: MergeInput, k: int, L: int = 0) -> dict:
     return kd
 
 
-def refine_pass(inp: MergeInput, knng: dict, rev_cap: int = 0) -> dict:
+def refine_pass(inp: MergeInput, knng: dict, rev_cap: int = 0, join_filter="tc") -> dict:
     """One synchronous Visit + Update pass of Alg. 3, in place on ``knng``."""
     L_ = load()
     k = int(knng["ids"].shape[1])
-    p = inp.params(k=k, rev_cap=rev_cap)
+    p = inp.params(k=k, rev_cap=rev_cap, join_filter=join_filter)
     kn = _knng_struct(knng["ids"], knng["dist"], knng["flags"])
     check(L_.fgim_refine_pass(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
     return last_stats()

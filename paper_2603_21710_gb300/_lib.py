@@ -25,7 +25,7 @@ class Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("R", ctypes.c_int32), ("alpha", ctypes.c_float), ("L", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("rev_cap", ctypes.c_int32), ("ensure_reachable", ctypes.c_int32),
-                ("reach_beam", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("reach_beam", ctypes.c_int32), ("join_filter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class KNNG(ctypes.Structure):

@@ -199,6 +199,7 @@ static void check_params(const fgim_params* p, bool need_merge) {
     need(p->iters >= 0 && p->iters <= 1000, FGIM_EINVAL, "iters must be in [0, 1000]");
     need(p->rev_cap >= 0 && p->rev_cap <= FGIM_MAX_K, FGIM_EINVAL, "rev_cap must be 0 or in [1, 128]");
     need(p->reach_beam >= 0 && p->reach_beam <= FGIM_MAX_L, FGIM_EINVAL, "reach_beam must be 0 or in [1, 128]");
+    need(p->join_filter == 0 || p->join_filter == 1, FGIM_EINVAL, "join_filter must be 0 (tensor core) or 1 (FP32)");
 }
 
 static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
@@ -339,8 +340,17 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.pend_off = c.alloc<long long>(N + 1);
     b.scan_bytes = scan_scratch_bytes(N);
     b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
-    b.max_nc = c.alloc<int32_t>(1);
-    b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);
+    b.max_nc = c.alloc<int32_t>(8);
+    b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);   // 8 ints of the 64-byte pinned slot
+    b.blist = c.alloc<int32_t>(2 * N);
+    b.blist_cap = N;
+    b.join_filter = p->join_filter;
+    b.Xb = nullptr;
+    if (p->join_filter == 0 && P.d % 16 == 0) {
+        b.Xb = c.alloc<__nv_bfloat16>(N * P.d);
+        b.tcm = c.alloc<float4>(N);
+        ck(launch_prep_bf16(P.X, N, P.d, reinterpret_cast<__nv_bfloat16*>(b.Xb), b.tcm, c.s));
+    }
 
     ck(refine_visit(*g, rev_cap, b, c.s));
     ck(cudaMemsetAsync(b.pending, 0, N, c.s));

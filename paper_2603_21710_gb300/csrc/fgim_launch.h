@@ -1,6 +1,7 @@
 // Host-side launchers of the FGIM kernels (one declaration per kernel family).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "fgim_internal.cuh"
@@ -64,9 +65,17 @@ struct RefineBuffers {
     // scan scratch
     void* scan_tmp;
     size_t scan_bytes;
-    // largest candidate set of a pass (device) and a pinned host slot to read it
+    // largest candidate set and C_n of a pass and the two launch lists' sizes and largest
+    // sets (device, 6 ints), a pinned host slot to read them, and the launch lists (2 x cap)
     int32_t* max_nc;
     int32_t* host_i32;
+    int32_t* blist;
+    long long blist_cap;
+    // tensor-core filter inputs: BF16 copy of the vectors and per row (|x|^2, bound on |x|,
+    // bound on the BF16 conversion error |bf(x) - x|, unused)
+    int join_filter;
+    void* Xb;
+    float4* tcm;
 };
 
 cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s);
@@ -74,6 +83,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         int* status, cudaStream_t s);
 cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
+cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
                             cudaStream_t s);
 cudaError_t launch_repair_round(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,

@@ -16,7 +16,10 @@
 // A proposal buffer that overflows marks the vertices whose proposals were dropped;
 // the host merges what fits and re-runs those vertices (their pairs are re-evaluated
 // against the updated lists), which yields the same final lists.
+#include <cuda_bf16.h>
+
 #include "fgim_launch.h"
+#include "tc_sm100.cuh"
 
 namespace fgim {
 
@@ -303,19 +306,7 @@ __host__ __device__ inline StagedLayout staged_layout(int cm, int k, int d) {
     return l;
 }
 
-__global__ void k_max_nc(const int32_t* __restrict__ nn, const int32_t* __restrict__ no,
-                         const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int m = 0;
-    if (i < nv) {
-        const long long v = vlist ? vlist[i] : i;
-        m = nn[v] > 0 ? nn[v] + no[v] : 0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
-}
-
+// out[0] = largest |C| and out[1] = largest |C_n| among the vertices that have pairs
 template <int METRIC>
 __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     ShardTable t, const float* __restrict__ X, const float* __restrict__ inv_norm, int k,
@@ -559,23 +550,552 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
 }
 
+// ---- tensor-core filter (BF16 tcgen05 Gram tile), exact FP32 re-rank
+//
+// Per vertex v the candidate rows (BF16 copies) are staged in shared memory (K-major,
+// 128-byte swizzle) and one 128 x N x d tcgen05.mma tile (FP32 accumulation in TMEM) gives
+// D_ij ~ x_i . x_j for every pair of C_n x C. The filter value is
+//   L2: n2_i + n2_j - 2 D_ij,  IP: 1 - D_ij,  cosine: 1 - D_ij * inv_i * inv_j,
+// and a pair direction survives when the value minus a bound on its error can still beat
+// the target's worst key. The bound (Cauchy-Schwarz on the BF16 conversion errors e = bf(x)
+// - x, plus the FP32 accumulation and rounding terms of Higham's bound with g = (d + 16) u):
+//   |D - x_i.x_j| <= |e_i||x_j| + |x_i||e_j| + |e_i||e_j| + g (|x_i| + |e_i|)(|x_j| + |e_j|).
+// On integer-valued data the conversion is exact (e = 0) and the bound is tiny. Survivors are
+// re-ranked with the canonical FP32 distance (from the staged rows when every one of them
+// converted exactly, else from the FP32 rows); only exact keys are proposed.
+constexpr int kTCThreads = 128;    // four warps, one per 32-lane quarter of TMEM
+constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
+constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
+constexpr int kTCSmallNC = 128;    // candidate sets up to this size form the four-CTAs-per-SM launch
+
+__global__ void k_prep_bf16(const float* __restrict__ X, long long N, int d, __nv_bfloat16* __restrict__ Xb,
+                            float4* __restrict__ tcm) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const float* x = X + row * d;
+    __nv_bfloat16* xb = Xb + row * d;
+    float s = 0.f, se = 0.f;
+    bool inexact = false;
+    for (int c = lane; c < d; c += 32) {
+        const float v = x[c];
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        xb[c] = b;
+        const float e = __bfloat162float(b) - v;
+        inexact |= e != 0.f;
+        s = fmaf(v, v, s);
+        se = fmaf(e, e, se);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(kFull, s, o);
+        se += __shfl_xor_sync(kFull, se, o);
+    }
+    inexact = __any_sync(kFull, inexact);
+    if (lane == 0) {
+        // |e| == 0 exactly when the BF16 row equals the FP32 row; squares of conversion errors
+        // below 2^-75 can underflow, so an inexact row never reports less than 1e-18
+        const float en = inexact ? fmaxf(sqrtf(se) * 1.0001f, 1e-18f) : 0.f;
+        tcm[row] = make_float4(s, sqrtf(s) * 1.0001f, en, 0.f);
+    }
+}
+
+cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    LaunchScope ls("k_prep_bf16", s);
+    k_prep_bf16<<<(unsigned)cdivll(N * 32, 256), 256, 0, s>>>(X, N, d, Xb, tcm);
+    return cudaGetLastError();
+}
+
+// Shared memory of one k_join_tc CTA (offsets from the first 1024-byte boundary of the
+// dynamic shared memory; `bytes` includes the slack for that alignment).
+struct TCLayout {
+    int op, rows_alloc, dpad, meta, thr, pb_key, tdist, cid, csh, hk, hv, mask, queue, pb_tgt, misc, bytes, hs, words;
+};
+
+__host__ __device__ inline TCLayout tc_layout(int cm, int d) {
+    TCLayout l;
+    int hs = 64;
+    while (hs < 2 * cm) hs <<= 1;
+    l.hs = hs;
+    l.words = (cm + 31) >> 5;
+    const int npad = ((cm + 15) / 16) * 16;
+    l.rows_alloc = npad > 128 ? npad : 128;   // the A operand always spans 128 rows
+    l.dpad = ((d + 63) / 64) * 64;            // whole 128-byte panels (zero beyond d)
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    int o = 0;
+    l.op = o;
+    o += l.rows_alloc * l.dpad * 2;   // a multiple of 1024
+    l.meta = o;
+    o += cm * 16;
+    l.thr = o;
+    o += a16(cm * 8);
+    l.pb_key = o;
+    o += kTCPropBuf * 8;
+    l.tdist = o;
+    o += a16(cm * 4);
+    l.cid = o;
+    o += a16(cm * 4);
+    l.csh = o;
+    o += a16(cm * 4);
+    l.hk = o;
+    o += hs * 4;
+    l.hv = o;
+    o += hs * 4;
+    l.mask = o;
+    o += a16(cm * l.words * 4);
+    l.queue = o;
+    o += kTCQueue * 4;
+    l.pb_tgt = o;
+    o += kTCPropBuf * 4;
+    l.misc = o;
+    o += 64;
+    l.bytes = o + 1024;
+    return l;
+}
+
+// One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
+template <int METRIC>
+__global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
+    ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const float4* __restrict__ tcm,
+    const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
+    const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
+    int cm, uint32_t tmem_cols, const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt,
+    uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
+    unsigned long long* pairs_count, int* status) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const long long v = vlist ? (long long)vlist[blockIdx.x] : (long long)blockIdx.x;
+    const int nn = nn_arr[v];
+    const int nc = nn + no_arr[v];
+    if (nn == 0 || nc < 2) return;
+    if (nc > cm || nn > 128) {   // the host sized the launch for the largest sets; never expected
+        if (tid == 0) atomicOr(status, kErrBounds);
+        return;
+    }
+    const int d = t.dim;
+    const TCLayout L = tc_layout(cm, d);
+    unsigned char* op = smem + L.op;
+    float4* meta = reinterpret_cast<float4*>(smem + L.meta);   // n2, |x| bound, |e| bound, cosine 1/|x|
+    uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
+    float* tdist = reinterpret_cast<float*>(smem + L.tdist);
+    int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
+    int32_t* csh = reinterpret_cast<int32_t*>(smem + L.csh);
+    int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
+    int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(smem + L.queue);
+    int32_t* pb_tgt = reinterpret_cast<int32_t*>(smem + L.pb_tgt);
+    uint64_t* pb_key = reinterpret_cast<uint64_t*>(smem + L.pb_key);
+    // misc: [0] proposals buffered, [1] survivors, [2] rows whose BF16 copy is inexact,
+    // [4..5] base of this CTA's proposals in the global buffer; mbarrier at byte 32, TMEM
+    // address at byte 48
+    int* misc = reinterpret_cast<int*>(smem + L.misc);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.misc + 32);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc + 48);
+    const int W = L.words, hs = L.hs, rows = L.rows_alloc;
+    const int vq = d >> 2;           // float4 chunks per FP32 row
+    const int kc = d >> 3;           // 16-byte chunks per BF16 row
+    const int kcp = L.dpad >> 3;     // 16-byte chunks per staged row
+    const int npad = ((nc + 15) / 16) * 16;   // MMA N
+    const float g = (float)(d + 16) * 5.9604645e-8f;
+
+    for (int i = tid; i < nc; i += kTCThreads) cid[i] = cand[v * cmax + i];
+    for (int i = tid; i < hs; i += kTCThreads) hk[i] = -1;
+    for (int i = tid; i < nc * W; i += kTCThreads) mask[i] = 0u;
+    if (tid < 8) misc[tid] = 0;
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tmem_slot, tmem_cols);
+    __syncthreads();
+    // stage the BF16 rows of C (rows past nc are never used: their products land in ignored
+    // rows and columns of D); chunks past d are zero
+    for (int item = tid; item < nc * kcp; item += kTCThreads) {
+        const int r = item / kcp, c = item - (item / kcp) * kcp;
+        unsigned char* dst = op + tc::sw_offset(r, c, rows);
+        if (c < kc) cp_async16(dst, Xb + (long long)cid[r] * d + c * 8, true);
+        else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+    for (int i = tid; i < nc; i += kTCThreads) {
+        const int32_t c = cid[i];
+        csh[i] = shard_of(t, c);
+        const int32_t wi = ids[(long long)c * k + k - 1];
+        const uint64_t th = wi < 0 ? kEmptyKey : mkkey(dist[(long long)c * k + k - 1], wi);
+        thr[i] = th;
+        tdist[i] = wi < 0 ? __int_as_float(0x7f800000) : key_dist(th);
+        float4 m = tcm[c];
+        if (m.z != 0.f) atomicOr(misc + 2, 1);
+        m.w = (METRIC == FGIM_COSINE) ? inv_norm[c] : 1.f;
+        meta[i] = m;
+        int slot = jhash(c, hs);
+        for (int probe = 0; probe < hs; ++probe) {
+            if (atomicCAS(hk + slot, -1, c) == -1) {
+                hv[slot] = i;
+                break;
+            }
+            slot = (slot + 1) & (hs - 1);
+        }
+    }
+    __syncthreads();
+    // membership bits: mask(i, j) = C[j] in N(C[i]); list rows are read 16 bytes at a time
+    {
+        auto member = [&](int i, int32_t e) {
+            if (e < 0) return;
+            int slot = jhash(e, hs);
+            for (int probe = 0; probe < hs; ++probe) {
+                const int32_t h = hk[slot];
+                if (h == e) {
+                    const int j = hv[slot];
+                    atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
+                    return;
+                }
+                if (h == -1) return;
+                slot = (slot + 1) & (hs - 1);
+            }
+        };
+        if ((k & 3) == 0 && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0) {
+            const int k4 = k >> 2;
+            const int total = nc * k4;
+            for (int base = tid; base < total; base += 4 * kTCThreads) {
+                int4 e4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int idx = base + u * kTCThreads;
+                    if (idx < total) {
+                        const int i = idx / k4;
+                        e4[u] = reinterpret_cast<const int4*>(ids + (long long)cid[i] * k)[idx - i * k4];
+                    } else {
+                        e4[u] = make_int4(-1, -1, -1, -1);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int idx = base + u * kTCThreads;
+                    if (idx >= total) continue;
+                    const int i = idx / k4;
+                    member(i, e4[u].x);
+                    member(i, e4[u].y);
+                    member(i, e4[u].z);
+                    member(i, e4[u].w);
+                }
+            }
+        } else {
+            const int total = nc * k;
+            for (int base = tid * 8; base < total; base += kTCThreads * 8) {
+                int32_t e8[8];
+#pragma unroll
+                for (int u8 = 0; u8 < 8; ++u8) {
+                    const int idx = base + u8;
+                    e8[u8] = idx < total ? ids[(long long)cid[idx / k] * k + (idx - (idx / k) * k)] : -1;
+                }
+#pragma unroll
+                for (int u8 = 0; u8 < 8; ++u8)
+                    if (base + u8 < total) member((base + u8) / k, e8[u8]);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    tc::fence_async_smem();
+    tc::fence_mbar_init();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const bool exact = misc[2] == 0;   // every staged row equals its FP32 row
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16(128, npad);
+        const uint32_t base = tc::smem_u32(op);
+        for (int s = 0; s < L.dpad / 16; ++s) {
+            const uint64_t desc = tc::smem_desc_sw128(base + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32));
+            tc::mma_bf16(tmem, desc, desc, idesc, s > 0 ? 1u : 0u);
+        }
+        tc::commit_to(mbar);
+    }
+    const bool ok_mma = tc::mbar_wait(mbar, 0, 1 << 24);
+    if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
+    tc::fence_after_sync();
+
+    // filter: warp w owns rows 32 w .. 32 w + 31 (its TMEM lane quarter) and reads the
+    // columns right of its first row, 16 at a time
+    const int i = 32 * warp + lane;
+    const bool row_ok = i < nn;
+    const float4 mi = row_ok ? meta[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float n2i = mi.x, xi = mi.y, ei = mi.z, ci = mi.w;
+    const float xei = xi + ei;
+    const float tdi = row_ok ? tdist[i] : 0.f;
+    const int shi = row_ok ? csh[i] : -1;
+    unsigned long long my_pairs = 0;
+    if (ok_mma && 32 * warp < nn) {
+        for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
+            float dv[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)j0, dv);
+#pragma unroll
+            for (int t16 = 0; t16 < 16; ++t16) {
+                const int j = j0 + t16;
+                if (j >= nc) break;
+                const float4 mj = meta[j];
+                if (!(row_ok && j > i && shi != csh[j])) continue;
+                ++my_pairs;
+                const float dot = dv[t16];
+                // |D - x_i.x_j| bound: e_i x_j + e_j (x_i + e_i) + g (x_i + e_i)(x_j + e_j)
+                const float cs = ei * mj.y + mj.z * xei + g * xei * (mj.y + mj.z);
+                float val, bound;
+                if (METRIC == FGIM_L2SQ) {
+                    const float s2 = n2i + mj.x;
+                    val = s2 - 2.f * dot;
+                    bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
+                                    4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
+                } else if (METRIC == FGIM_IP) {
+                    val = 1.f - dot;
+                    bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
+                } else {
+                    const float cc = ci * mj.w;
+                    val = 1.f - dot * cc;
+                    bound = 1.1f * (cs * cc + g * fabsf(val)) + 4.8e-7f;
+                }
+                const float lo = val - bound;
+                const float tdj = tdist[j];
+                if (!(lo <= fmaxf(tdi, tdj))) continue;
+                unsigned dm = 0;
+                if (lo <= tdi && !((mask[i * W + (j >> 5)] >> (j & 31)) & 1u)) dm |= 1u;
+                if (lo <= tdj && !((mask[j * W + (i >> 5)] >> (i & 31)) & 1u)) dm |= 2u;
+                if (dm) {
+                    const int slot = atomicAdd(misc + 1, 1);
+                    if (slot < kTCQueue) queue[slot] = (uint32_t)i | ((uint32_t)j << 10) | (dm << 20);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);   // free TMEM for the next CTA on this SM
+
+    // exact re-rank of the survivors with the canonical FP32 distance, eight pairs per warp
+    // step. With every staged row exact the rows are read from the staged tile (the same
+    // values), otherwise from the FP32 rows in global memory.
+    const int nq = min(misc[1], kTCQueue);
+    for (int q0 = warp * 8; q0 < nq; q0 += (kTCThreads / 32) * 8) {
+        const int U = min(8, nq - q0);
+        int ra[8], rb[8];
+#pragma unroll
+        for (int t8 = 0; t8 < 8; ++t8) {
+            const uint32_t e = queue[q0 + min(t8, U - 1)];
+            ra[t8] = (int)(e & 1023u);
+            rb[t8] = (int)((e >> 10) & 1023u);
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
+        for (int c = lane; c < vq; c += 32) {
+            float4 xa[8], xb[8];
+            if (exact) {
+#pragma unroll
+                for (int t8 = 0; t8 < 8; ++t8) {
+                    const uint2 ua =
+                        *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
+                    const uint2 ub =
+                        *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
+                    xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
+                                         __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
+                    xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
+                                         __uint_as_float(ub.y << 16), __uint_as_float(ub.y & 0xffff0000u));
+                }
+            } else {
+#pragma unroll
+                for (int t8 = 0; t8 < 8; ++t8) {
+                    xa[t8] = reinterpret_cast<const float4*>(X + (long long)cid[ra[t8]] * d)[c];
+                    xb[t8] = reinterpret_cast<const float4*>(X + (long long)cid[rb[t8]] * d)[c];
+                }
+            }
+#pragma unroll
+            for (int t8 = 0; t8 < 8; ++t8) {
+                const float4 x = xa[t8], y = xb[t8];
+                if (METRIC == FGIM_L2SQ) {
+                    const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+                    const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
+                    acc[t8][0] = fmaf(e0, e0, acc[t8][0]);
+                    acc[t8][1] = fmaf(e1, e1, acc[t8][1]);
+                    acc[t8][2] = fmaf(e2, e2, acc[t8][2]);
+                    acc[t8][3] = fmaf(e3, e3, acc[t8][3]);
+                } else {
+                    acc[t8][0] = fmaf(x.x, y.x, acc[t8][0]);
+                    acc[t8][1] = fmaf(x.y, y.y, acc[t8][1]);
+                    acc[t8][2] = fmaf(x.z, y.z, acc[t8][2]);
+                    acc[t8][3] = fmaf(x.w, y.w, acc[t8][3]);
+                }
+            }
+        }
+        float sc = 0.f;
+#pragma unroll
+        for (int t8 = 0; t8 < 8; ++t8) {
+            const float tot = warp_butterfly(__fadd_rn(__fadd_rn(acc[t8][0], acc[t8][1]),
+                                                       __fadd_rn(acc[t8][2], acc[t8][3])));
+            if (lane == t8) sc = tot;
+        }
+        if (lane < U) {
+            const uint32_t e = queue[q0 + lane];
+            const int ia = (int)(e & 1023u), jb = (int)((e >> 10) & 1023u);
+            const unsigned dm = (e >> 20) & 3u;
+            const float dd =
+                delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(meta[ia].w, meta[jb].w) : 1.f);
+            for (int dir = 0; dir < 2; ++dir) {
+                if (!((dm >> dir) & 1u)) continue;
+                const int a2 = dir == 0 ? ia : jb, b2 = dir == 0 ? jb : ia;
+                const uint64_t key = mkkey(dd, cid[b2]);
+                if (key >= thr[a2]) continue;
+                const int slot = atomicAdd(misc, 1);
+                if (slot < kTCPropBuf) {
+                    pb_tgt[slot] = cid[a2];
+                    pb_key[slot] = key;
+                } else {
+                    const unsigned long long pos = atomicAdd(prop_count, 1ull);
+                    if (pos < (unsigned long long)prop_cap) {
+                        prop_tgt[pos] = cid[a2];
+                        prop_key[pos] = key;
+                    } else {
+                        pending[v] = 1;
+                        atomicOr(status, kErrOverflow);
+                    }
+                }
+            }
+        }
+    }
+    if (misc[1] > kTCQueue && tid == 0) {   // survivors dropped: this vertex is redone after the merge
+        pending[v] = 1;
+        atomicOr(status, kErrOverflow);
+    }
+    __syncthreads();
+    const int nb = min(misc[0], kTCPropBuf);
+    unsigned long long* base_s = reinterpret_cast<unsigned long long*>(misc + 4);
+    if (tid == 0 && nb > 0) *base_s = atomicAdd(prop_count, (unsigned long long)nb);
+    __syncthreads();
+    if (nb > 0) {
+        const unsigned long long base = *base_s;
+        for (int q = tid; q < nb; q += kTCThreads) {
+            const unsigned long long pos = base + q;
+            if (pos < (unsigned long long)prop_cap) {
+                prop_tgt[pos] = pb_tgt[q];
+                prop_key[pos] = pb_key[q];
+            } else {
+                pending[v] = 1;
+                atomicOr(status, kErrOverflow);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(kFull, my_pairs, o);
+    if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
+}
+
+// Largest candidate set and C_n of the vertices in vlist (all when null), and the vertices
+// split by candidate-set size into two lists (blist[0..], blist[cap..]) for the tensor-core
+// launches. out: [0] max |C|, [1] max |C_n|, [2], [3] list sizes, [4], [5] max |C| per list.
+__global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __restrict__ no,
+                               const int32_t* __restrict__ vlist, long long nv, int small_nc,
+                               int32_t* __restrict__ out, int32_t* __restrict__ blist, long long cap) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int m = 0, mn = 0;
+    long long v = 0;
+    bool act = false;
+    if (i < nv) {
+        v = vlist ? vlist[i] : i;
+        mn = nn[v];
+        m = mn > 0 ? mn + no[v] : 0;
+        act = mn > 0 && m >= 2;
+    }
+    const bool small = act && m <= small_nc, large = act && m > small_nc;
+    const unsigned bs = __ballot_sync(kFull, small), bl = __ballot_sync(kFull, large);
+    int base_s = 0, base_l = 0;
+    if (lane == 0) {
+        if (bs) base_s = atomicAdd(out + 2, __popc(bs));
+        if (bl) base_l = atomicAdd(out + 3, __popc(bl));
+    }
+    base_s = __shfl_sync(kFull, base_s, 0);
+    base_l = __shfl_sync(kFull, base_l, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (small) blist[base_s + __popc(bs & lt)] = (int32_t)v;
+    if (large) blist[cap + base_l + __popc(bl & lt)] = (int32_t)v;
+    int ms = small ? m : 0, ml = large ? m : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = max(m, __shfl_xor_sync(kFull, m, o));
+        mn = max(mn, __shfl_xor_sync(kFull, mn, o));
+        ms = max(ms, __shfl_xor_sync(kFull, ms, o));
+        ml = max(ml, __shfl_xor_sync(kFull, ml, o));
+    }
+    if (lane == 0) {
+        if (m > 0) atomicMax(out, m);
+        if (mn > 0) atomicMax(out + 1, mn);
+        if (ms > 0) atomicMax(out + 4, ms);
+        if (ml > 0) atomicMax(out + 5, ml);
+    }
+}
+
+// shared memory a k_join_tc launch asks for: its layout, raised so that no more CTAs fit on
+// an SM than the 512 TMEM columns can serve at once (an allocation never has to wait)
+static size_t tc_launch_smem(const TCLayout& TL, uint32_t cols) {
+    const int per_sm = 233472;   // 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+    const int fit = (int)(512 / cols);
+    const int floor_bytes = per_sm / (fit + 1) - 1024 + 16;
+    return (size_t)(TL.bytes > floor_bytes ? TL.bytes : floor_bytes);
+}
+
 cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         int* status, cudaStream_t s) {
     if (nv <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    // largest candidate set of this pass sizes the staged variant's shared memory
-    if ((e = cudaMemsetAsync(b.max_nc, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.max_nc, 0, 6 * sizeof(int32_t), s)) != cudaSuccess) return e;
     {
-        LaunchScope ls("k_max_nc", s);
-        k_max_nc<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, b.max_nc);
+        LaunchScope ls("k_join_buckets", s);
+        k_join_buckets<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, kTCSmallNC, b.max_nc,
+                                                                  b.blist, b.blist_cap);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    int32_t cm = 0;
-    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    cm = *b.host_i32;
+    int32_t hb[6];
+    for (int q = 0; q < 6; ++q) hb[q] = b.host_i32[q];
+    const int32_t cm = hb[0], cmn = hb[1];
     if (cm < 2) return cudaSuccess;
+    bool use_tc = b.join_filter == 0 && b.Xb && t.dim % 16 == 0 && cmn <= 128 && cm <= 256;
+    if (use_tc)
+        for (int q = 0; q < 2; ++q)
+            if (hb[2 + q] > 0 && tc_layout(hb[4 + q], t.dim).bytes > 227 * 1024) use_tc = false;
+    if (use_tc) {
+        for (int q = 0; q < 2; ++q) {
+            const int32_t count = hb[2 + q], cmq = hb[4 + q];
+            if (count <= 0) continue;
+            const TCLayout TL = tc_layout(cmq, t.dim);
+            const int npad = ((cmq + 15) / 16) * 16;
+            uint32_t cols = 32;
+            while ((int)cols < npad) cols <<= 1;
+            const size_t smem = tc_launch_smem(TL, cols);
+            const int32_t* list = b.blist + (long long)q * b.blist_cap;
+#define FGIM_LAUNCH_TC(MT)                                                                                        \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_join_tc<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+        if (e != cudaSuccess) break;                                                                              \
+        LaunchScope ls("k_join", s);                                                                              \
+        k_join_tc<MT><<<(unsigned)count, kTCThreads, smem, s>>>(                                                  \
+            t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,      \
+            b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
+            pairs, status);                                                                                       \
+        e = cudaGetLastError();                                                                                   \
+    } while (0)
+            if (metric == FGIM_L2SQ) FGIM_LAUNCH_TC(FGIM_L2SQ);
+            else if (metric == FGIM_IP) FGIM_LAUNCH_TC(FGIM_IP);
+            else FGIM_LAUNCH_TC(FGIM_COSINE);
+#undef FGIM_LAUNCH_TC
+            if (e != cudaSuccess) return e;
+        }
+        return e;
+    }
     const StagedLayout SL = staged_layout(cm, g.k, t.dim);
     if (SL.bytes > 227 * 1024) return cudaErrorNotSupported;
     const size_t smem = SL.bytes;

@@ -349,3 +349,19 @@ def test_reach_fix_victim_rule():
     assert _np(g["ids"]).tolist() == gd["expected_lists"]
     assert _np(g["dist"])[2].tolist() == gd["expected_dist_row2"]
     assert st["attached"] == 1 and st["unreached"] == 0
+
+
+@pytest.mark.parametrize("which", ["small", "sift_like"])
+def test_join_filters_agree(which, request):
+    """The BF16 tensor-core filter and the FP32 SIMT filter re-rank exactly: identical lists."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = request.getfixturevalue(which)
+    o, _, _ = O.stage_a(P, w.k)
+    a, b = _to_dev(o), _to_dev(o)
+    sa = fg.refine_pass(inp, a, join_filter="tc")
+    sb = fg.refine_pass(inp, b, join_filter="fp32")
+    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"]) and torch.equal(a["flags"], b["flags"])
+    assert sa["join_pairs"] == sb["join_pairs"]
+    ma = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, join_filter="tc")
+    mb = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, join_filter="fp32")
+    assert torch.equal(ma["ids"], mb["ids"])

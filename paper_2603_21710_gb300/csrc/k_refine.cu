@@ -610,7 +610,7 @@ cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* 
 // Shared memory of one k_join_tc CTA (offsets from the first 1024-byte boundary of the
 // dynamic shared memory; `bytes` includes the slack for that alignment).
 struct TCLayout {
-    int op, rows_alloc, dpad, meta, thr, pb_key, tdist, cid, csh, hk, hv, mask, queue, pb_tgt, misc, bytes, hs, words;
+    int op, rows_alloc, dpad, meta, colf, thr, pb_key, cid, hk, hv, mask, queue, pb_tgt, misc, bytes, hs, words;
 };
 
 __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
@@ -628,15 +628,13 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     o += l.rows_alloc * l.dpad * 2;   // a multiple of 1024
     l.meta = o;
     o += cm * 16;
+    l.colf = o;
+    o += cm * 16;
     l.thr = o;
     o += a16(cm * 8);
     l.pb_key = o;
     o += kTCPropBuf * 8;
-    l.tdist = o;
-    o += a16(cm * 4);
     l.cid = o;
-    o += a16(cm * 4);
-    l.csh = o;
     o += a16(cm * 4);
     l.hk = o;
     o += hs * 4;
@@ -671,8 +669,12 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const long long v = vlist ? (long long)vlist[blockIdx.x] : (long long)blockIdx.x;
     const int nn = nn_arr[v];
     const int nc = nn + no_arr[v];
+    // candidate ids, read before nc is known (a row of cand holds cmax >= cm entries)
+    const long long crow = v * (long long)cmax;
+    const int32_t cA = tid < cm ? cand[crow + tid] : -1;
+    const int32_t cB = tid + kTCThreads < cm ? cand[crow + tid + kTCThreads] : -1;
     if (nn == 0 || nc < 2) return;
-    if (nc > cm || nn > 128) {   // the host sized the launch for the largest sets; never expected
+    if (nc > cm || nn > 128 || cm > 2 * kTCThreads) {   // the host sized the launch; never expected
         if (tid == 0) atomicOr(status, kErrBounds);
         return;
     }
@@ -680,10 +682,9 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const TCLayout L = tc_layout(cm, d);
     unsigned char* op = smem + L.op;
     float4* meta = reinterpret_cast<float4*>(smem + L.meta);   // n2, |x| bound, |e| bound, cosine 1/|x|
+    float4* colf = reinterpret_cast<float4*>(smem + L.colf);   // P, worst distance, shard (bits), -
     uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
-    float* tdist = reinterpret_cast<float*>(smem + L.tdist);
     int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
-    int32_t* csh = reinterpret_cast<int32_t*>(smem + L.csh);
     int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
     int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
@@ -702,16 +703,22 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const int kcp = L.dpad >> 3;     // 16-byte chunks per staged row
     const int npad = ((nc + 15) / 16) * 16;   // MMA N
     const float g = (float)(d + 16) * 5.9604645e-8f;
+    // squared L2 on exactly converted rows: lo = P_i + P_j - 2 D_ij with P = (1 - Cf) |x|^2
+    // lies below (value - bound) of the general test (see the filter)
+    const float Cf = 1.2f * (4.001f * g + 12.01f * 5.9604645e-8f);
 
-    for (int i = tid; i < nc; i += kTCThreads) cid[i] = cand[v * cmax + i];
+    if (tid < nc) cid[tid] = cA;
+    if (tid + kTCThreads < nc) cid[tid + kTCThreads] = cB;
     for (int i = tid; i < hs; i += kTCThreads) hk[i] = -1;
     for (int i = tid; i < nc * W; i += kTCThreads) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tmem_slot, tmem_cols);
     __syncthreads();
-    // stage the BF16 rows of C (rows past nc are never used: their products land in ignored
-    // rows and columns of D); chunks past d are zero
+    // One round trip for everything the candidate ids address: the BF16 rows (cp.async; rows
+    // past nc are never used, their products land in ignored rows and columns of D; chunks
+    // past d are zero), this thread's candidates' worst keys and row statistics, and the
+    // first batch of list entries for the membership bits.
     for (int item = tid; item < nc * kcp; item += kTCThreads) {
         const int r = item / kcp, c = item - (item / kcp) * kcp;
         unsigned char* dst = op + tc::sw_offset(r, c, rows);
@@ -719,81 +726,91 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
     cp_async_commit();
-    for (int i = tid; i < nc; i += kTCThreads) {
-        const int32_t c = cid[i];
-        csh[i] = shard_of(t, c);
-        const int32_t wi = ids[(long long)c * k + k - 1];
-        const uint64_t th = wi < 0 ? kEmptyKey : mkkey(dist[(long long)c * k + k - 1], wi);
-        thr[i] = th;
-        tdist[i] = wi < 0 ? __int_as_float(0x7f800000) : key_dist(th);
-        float4 m = tcm[c];
-        if (m.z != 0.f) atomicOr(misc + 2, 1);
-        m.w = (METRIC == FGIM_COSINE) ? inv_norm[c] : 1.f;
-        meta[i] = m;
+    int32_t wiA = -1, wiB = -1;
+    float dkA = 0.f, dkB = 0.f, invA = 1.f, invB = 1.f;
+    float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), mB = mA;
+    if (tid < nc) {
+        wiA = ids[(long long)cA * k + k - 1];
+        dkA = dist[(long long)cA * k + k - 1];
+        mA = tcm[cA];
+        if (METRIC == FGIM_COSINE) invA = inv_norm[cA];
+    }
+    if (tid + kTCThreads < nc) {
+        wiB = ids[(long long)cB * k + k - 1];
+        dkB = dist[(long long)cB * k + k - 1];
+        mB = tcm[cB];
+        if (METRIC == FGIM_COSINE) invB = inv_norm[cB];
+    }
+    // membership items: 16 bytes (four entries) of a list when rows are 16-byte aligned, else one entry
+    const bool vec = (k & 3) == 0 && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0;
+    const int per = vec ? (k >> 2) : k;
+    const int mtotal = nc * per;
+    constexpr int kMB = 8;   // items in flight per thread
+    int4 e4[kMB];
+    auto load_items = [&](int b0) {
+#pragma unroll
+        for (int u = 0; u < kMB; ++u) {
+            const int idx = b0 + tid + u * kTCThreads;
+            e4[u] = make_int4(-1, -1, -1, -1);
+            if (idx < mtotal) {
+                const int i = idx / per;
+                const int32_t* row = ids + (long long)cid[i] * k;
+                if (vec) e4[u] = reinterpret_cast<const int4*>(row)[idx - i * per];
+                else e4[u].x = row[idx - i * per];
+            }
+        }
+    };
+    load_items(0);
+    auto insert = [&](int32_t c, int i) {
         int slot = jhash(c, hs);
         for (int probe = 0; probe < hs; ++probe) {
             if (atomicCAS(hk + slot, -1, c) == -1) {
                 hv[slot] = i;
-                break;
+                return;
             }
             slot = (slot + 1) & (hs - 1);
         }
-    }
+    };
+    if (tid < nc) insert(cA, tid);
+    if (tid + kTCThreads < nc) insert(cB, tid + kTCThreads);
     __syncthreads();
-    // membership bits: mask(i, j) = C[j] in N(C[i]); list rows are read 16 bytes at a time
-    {
-        auto member = [&](int i, int32_t e) {
-            if (e < 0) return;
-            int slot = jhash(e, hs);
-            for (int probe = 0; probe < hs; ++probe) {
-                const int32_t h = hk[slot];
-                if (h == e) {
-                    const int j = hv[slot];
-                    atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
-                    return;
-                }
-                if (h == -1) return;
-                slot = (slot + 1) & (hs - 1);
+    auto put_meta = [&](int i, int32_t c, int32_t wi, float dk, float4 m, float inv) {
+        thr[i] = wi < 0 ? kEmptyKey : mkkey(dk, wi);
+        if (m.z != 0.f) atomicOr(misc + 2, 1);
+        colf[i] = make_float4((1.f - Cf) * m.x, wi < 0 ? __int_as_float(0x7f800000) : dk,
+                              __int_as_float(shard_of(t, c)), 0.f);
+        m.w = inv;
+        meta[i] = m;
+    };
+    if (tid < nc) put_meta(tid, cA, wiA, dkA, mA, invA);
+    if (tid + kTCThreads < nc) put_meta(tid + kTCThreads, cB, wiB, dkB, mB, invB);
+    // membership bits: mask(i, j) = C[j] in N(C[i])
+    auto member = [&](int i, int32_t e) {
+        if (e < 0) return;
+        int slot = jhash(e, hs);
+        for (int probe = 0; probe < hs; ++probe) {
+            const int32_t h = hk[slot];
+            if (h == e) {
+                const int j = hv[slot];
+                atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
+                return;
             }
-        };
-        if ((k & 3) == 0 && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0) {
-            const int k4 = k >> 2;
-            const int total = nc * k4;
-            for (int base = tid; base < total; base += 4 * kTCThreads) {
-                int4 e4[4];
+            if (h == -1) return;
+            slot = (slot + 1) & (hs - 1);
+        }
+    };
+    for (int b0 = 0; b0 < mtotal; b0 += kMB * kTCThreads) {
+        if (b0 > 0) load_items(b0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int idx = base + u * kTCThreads;
-                    if (idx < total) {
-                        const int i = idx / k4;
-                        e4[u] = reinterpret_cast<const int4*>(ids + (long long)cid[i] * k)[idx - i * k4];
-                    } else {
-                        e4[u] = make_int4(-1, -1, -1, -1);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int idx = base + u * kTCThreads;
-                    if (idx >= total) continue;
-                    const int i = idx / k4;
-                    member(i, e4[u].x);
-                    member(i, e4[u].y);
-                    member(i, e4[u].z);
-                    member(i, e4[u].w);
-                }
-            }
-        } else {
-            const int total = nc * k;
-            for (int base = tid * 8; base < total; base += kTCThreads * 8) {
-                int32_t e8[8];
-#pragma unroll
-                for (int u8 = 0; u8 < 8; ++u8) {
-                    const int idx = base + u8;
-                    e8[u8] = idx < total ? ids[(long long)cid[idx / k] * k + (idx - (idx / k) * k)] : -1;
-                }
-#pragma unroll
-                for (int u8 = 0; u8 < 8; ++u8)
-                    if (base + u8 < total) member((base + u8) / k, e8[u8]);
+        for (int u = 0; u < kMB; ++u) {
+            const int idx = b0 + tid + u * kTCThreads;
+            if (idx >= mtotal) continue;
+            const int i = idx / per;
+            member(i, e4[u].x);
+            if (vec) {
+                member(i, e4[u].y);
+                member(i, e4[u].z);
+                member(i, e4[u].w);
             }
         }
     }
@@ -818,53 +835,81 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
     tc::fence_after_sync();
 
-    // filter: warp w owns rows 32 w .. 32 w + 31 (its TMEM lane quarter) and reads the
-    // columns right of its first row, 16 at a time
+    // Filter: warp w owns rows 32 w .. 32 w + 31 (its TMEM lane quarter) and reads the
+    // columns right of its first row, 16 at a time. A pair survives when lo, a lower bound
+    // of its exact value, can still beat the worst key of a list it is not already in.
+    // General test: lo = value - bound with the bound of the file comment (cs term:
+    // e_i x_j + e_j (x_i + e_i) + g (x_i + e_i)(x_j + e_j)). Squared L2 on exactly converted
+    // rows (e = 0): with s2 = n2_i + n2_j, 2 x_i x_j <= 1.0002 s2 and |D| <= (1 + g) x_i x_j,
+    // the general bound is at most 1.1 s2 (4.001 g + 12.01 u); Cf adds margin for the
+    // rounding of P_i + P_j - 2 D, so lo = P_i + P_j - 2 D is lower still.
     const int i = 32 * warp + lane;
     const bool row_ok = i < nn;
+    const float4 fi = row_ok ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float Pi = fi.x, tdi = fi.y;
+    const int shi = row_ok ? __float_as_int(fi.z) : -1;
     const float4 mi = row_ok ? meta[i] : make_float4(0.f, 0.f, 0.f, 1.f);
     const float n2i = mi.x, xi = mi.y, ei = mi.z, ci = mi.w;
     const float xei = xi + ei;
-    const float tdi = row_ok ? tdist[i] : 0.f;
-    const int shi = row_ok ? csh[i] : -1;
     unsigned long long my_pairs = 0;
+    auto enqueue = [&](int j, float lo, float tdj) {
+        unsigned dm = 0;
+        if (lo <= tdi && !((mask[i * W + (j >> 5)] >> (j & 31)) & 1u)) dm |= 1u;
+        if (lo <= tdj && !((mask[j * W + (i >> 5)] >> (i & 31)) & 1u)) dm |= 2u;
+        if (dm) {
+            const int slot = atomicAdd(misc + 1, 1);
+            if (slot < kTCQueue) queue[slot] = (uint32_t)i | ((uint32_t)j << 10) | (dm << 20);
+        }
+    };
     if (ok_mma && 32 * warp < nn) {
-        for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
-            float dv[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)j0, dv);
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        if (METRIC == FGIM_L2SQ && exact) {
+            for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
+                float dv[16];
+                tc::tmem_ld16(trow + (uint32_t)j0, dv);
 #pragma unroll
-            for (int t16 = 0; t16 < 16; ++t16) {
-                const int j = j0 + t16;
-                if (j >= nc) break;
-                const float4 mj = meta[j];
-                if (!(row_ok && j > i && shi != csh[j])) continue;
-                ++my_pairs;
-                const float dot = dv[t16];
-                // |D - x_i.x_j| bound: e_i x_j + e_j (x_i + e_i) + g (x_i + e_i)(x_j + e_j)
-                const float cs = ei * mj.y + mj.z * xei + g * xei * (mj.y + mj.z);
-                float val, bound;
-                if (METRIC == FGIM_L2SQ) {
-                    const float s2 = n2i + mj.x;
-                    val = s2 - 2.f * dot;
-                    bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
-                                    4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
-                } else if (METRIC == FGIM_IP) {
-                    val = 1.f - dot;
-                    bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
-                } else {
-                    const float cc = ci * mj.w;
-                    val = 1.f - dot * cc;
-                    bound = 1.1f * (cs * cc + g * fabsf(val)) + 4.8e-7f;
+                for (int t16 = 0; t16 < 16; ++t16) {
+                    const int j = j0 + t16;
+                    if (j >= nc) break;
+                    const float4 cj = colf[j];
+                    if (!(row_ok && j > i && shi != __float_as_int(cj.z))) continue;
+                    ++my_pairs;
+                    const float lo = fmaf(-2.f, dv[t16], Pi + cj.x);
+                    if (!(lo <= fmaxf(tdi, cj.y))) continue;
+                    enqueue(j, lo, cj.y);
                 }
-                const float lo = val - bound;
-                const float tdj = tdist[j];
-                if (!(lo <= fmaxf(tdi, tdj))) continue;
-                unsigned dm = 0;
-                if (lo <= tdi && !((mask[i * W + (j >> 5)] >> (j & 31)) & 1u)) dm |= 1u;
-                if (lo <= tdj && !((mask[j * W + (i >> 5)] >> (i & 31)) & 1u)) dm |= 2u;
-                if (dm) {
-                    const int slot = atomicAdd(misc + 1, 1);
-                    if (slot < kTCQueue) queue[slot] = (uint32_t)i | ((uint32_t)j << 10) | (dm << 20);
+            }
+        } else {
+            for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
+                float dv[16];
+                tc::tmem_ld16(trow + (uint32_t)j0, dv);
+#pragma unroll
+                for (int t16 = 0; t16 < 16; ++t16) {
+                    const int j = j0 + t16;
+                    if (j >= nc) break;
+                    const float4 cj = colf[j];
+                    if (!(row_ok && j > i && shi != __float_as_int(cj.z))) continue;
+                    ++my_pairs;
+                    const float4 mj = meta[j];
+                    const float dot = dv[t16];
+                    const float cs = ei * mj.y + mj.z * xei + g * xei * (mj.y + mj.z);
+                    float val, bound;
+                    if (METRIC == FGIM_L2SQ) {
+                        const float s2 = n2i + mj.x;
+                        val = s2 - 2.f * dot;
+                        bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
+                                        4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
+                    } else if (METRIC == FGIM_IP) {
+                        val = 1.f - dot;
+                        bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
+                    } else {
+                        const float cc = ci * mj.w;
+                        val = 1.f - dot * cc;
+                        bound = 1.1f * (cs * cc + g * fabsf(val)) + 4.8e-7f;
+                    }
+                    const float lo = val - bound;
+                    if (!(lo <= fmaxf(tdi, cj.y))) continue;
+                    enqueue(j, lo, cj.y);
                 }
             }
         }

@@ -270,6 +270,7 @@ static int merged_entry(const fgim_shard* sh, int h) {
 struct Problem {
     ShardTable t;
     const float* X;
+    const uint8_t* X8;   // X as bytes when every coordinate is an integer in [0, 255], else nullptr
     const float* inv;
     long long N;
     int d;
@@ -284,6 +285,14 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.t = make_table(sh, h, p->dim);
     P.X = contiguous_vectors(c, sh, h, p->dim, P.N);
     P.inv = nullptr;
+    P.X8 = nullptr;
+    if (P.d % 4 == 0) {
+        uint8_t* x8 = c.alloc<uint8_t>(P.N * P.d);
+        int* flag = c.alloc<int>(1);
+        ck(cudaMemsetAsync(flag, 0, sizeof(int), c.s));
+        ck(launch_narrow_u8(P.X, P.N * P.d, x8, flag, c.s));
+        if (c.read_i32(flag) == 0) P.X8 = x8;
+    }
     if (p->metric == FGIM_COSINE) {
         float* inv = c.alloc<float>(P.N);
         ck(launch_inv_norms(P.X, P.N, P.d, inv, c.s));
@@ -295,7 +304,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
 static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_knng* g) {
     const int L = resolve_L(p, h);
     need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
-    ck(launch_cross_query(P.t, P.X, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s));
+    ck(launch_cross_query(P.t, P.X, P.X8, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s));
 }
 
 static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knng* g, fgim_stats* st) {
@@ -487,7 +496,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
             cdist = c.alloc<float>(nr * beam);
             cand_cap = nr;
         }
-        ck(launch_search(P.X, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
+        ck(launch_search(P.X, P.X8, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
                          cand, cdist, c.ctr + 0, c.status, c.s));
         ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
         ck(cudaMemsetAsync(cursor, 0, sizeof(long long), c.s));
@@ -767,7 +776,7 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
             ck(launch_inv_norms(X, n, dim, inv, c.s));
             ck(launch_inv_norms(Q, nq, dim, qinv, c.s));
         }
-        ck(launch_search(X, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
+        ck(launch_search(X, nullptr, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
                          out_dist, c.ctr + 0, c.status, c.s));
         c.finish(&t_stats);
     });

@@ -267,6 +267,7 @@ __device__ int warp_merge(uint64_t* list, uint8_t* aux, int n, int cap, uint64_t
     const int lane = lane_id();
     bool valid = cand != kEmptyKey;
     if (valid && n >= cap && cand >= list[cap - 1]) valid = false;
+    if (!__any_sync(kFull, valid)) return n;   // nothing can enter the list
     if (valid) {
         if (BY_ID) {
             const int32_t cid = key_id(cand);

@@ -97,7 +97,7 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
         if (e == cudaSuccess) e = launch_inv_norms(Q, nq, dim, qinv, s);
     }
     if (e == cudaSuccess)
-        e = launch_search(X, metric == FGIM_COSINE ? inv : nullptr, n, dim, metric, graph_ids, R, entry, Q,
+        e = launch_search(X, nullptr, metric == FGIM_COSINE ? inv : nullptr, n, dim, metric, graph_ids, R, entry, Q,
                           metric == FGIM_COSINE ? qinv : nullptr, nullptr, nq, topk, beam, out_ids, out_dist, counters,
                           status, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -14,6 +14,13 @@
 // key only decreases, and an id leaves the pool or is refused only when L better keys
 // are present). The pool therefore evolves exactly as with an exact visited set
 // (Alg. 1's "not visited" test); only the number of distance evaluations grows.
+//
+// Rows are read as FP32 or, when every coordinate of the data set is an integer in
+// [0, 255], as one byte per coordinate (the merge checks this once). Both decode to the
+// same FP32 values, so every distance, and with it every result, is the same; the byte
+// rows move a quarter of the bytes, and at d = 128 a million of them fit in L2.
+#include <algorithm>
+
 #include "fgim_internal.cuh"
 #include "fgim_launch.h"
 
@@ -26,35 +33,95 @@ struct WarpCounters {
     long long hops = 0;
 };
 
+__device__ __forceinline__ float4 u8x4_to_float4(uint32_t w) {
+    return make_float4((float)(w & 0xffu), (float)((w >> 8) & 0xffu), (float)((w >> 16) & 0xffu), (float)(w >> 24));
+}
+
+// float4 chunk c (coordinates 4c .. 4c + 3) of a row of FP32 or byte storage
+__device__ __forceinline__ float4 row_chunk(const float* row, int c) { return reinterpret_cast<const float4*>(row)[c]; }
+__device__ __forceinline__ float4 row_chunk(const uint8_t* row, int c) {
+    return u8x4_to_float4(*reinterpret_cast<const uint32_t*>(row + 4 * c));
+}
+
+// lane_part over a row of either storage (the same additions as lane_part)
+template <int METRIC, typename RT>
+__device__ __forceinline__ float lane_part_rows(const float* q, const RT* row, int nc4, int lane) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int c = lane; c < nc4; c += 32) {
+        const float4 x = reinterpret_cast<const float4*>(q)[c];
+        const float4 y = row_chunk(row, c);
+        if (METRIC == FGIM_L2SQ) {
+            const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+            const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
+            s0 = fmaf(e0, e0, s0);
+            s1 = fmaf(e1, e1, s1);
+            s2 = fmaf(e2, e2, s2);
+            s3 = fmaf(e3, e3, s3);
+        } else {
+            s0 = fmaf(x.x, y.x, s0);
+            s1 = fmaf(x.y, y.y, s1);
+            s2 = fmaf(x.z, y.z, s2);
+            s3 = fmaf(x.w, y.w, s3);
+        }
+    }
+    return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
+}
+
 // Canonical distances between the query (q in shared memory; qreg = this lane's chunk when
-// d <= 128) and the U <= 32 rows base[rid[r]]; lane r receives row r's distance. Rows load
-// coalesced (one warp load per row, eight rows in flight); every lane stores its partials in
-// P (32 x 33 floats of this warp's shared memory) and lane r re-adds row r in tree order.
-template <int METRIC, bool SMALLD>
-__device__ __forceinline__ float rows_delta(const float* __restrict__ base, const int32_t* rid, int U, const float* q,
-                                            float4 qreg, int d, int lane, float* P) {
+// d <= 128) and the U <= 32 rows base[rid[r]]; lane r receives row r's distance.
+// FP32 rows load coalesced (one warp load per row, eight rows in flight); every lane stores
+// its partials in P (32 x 33 floats of this warp's shared memory) and lane r re-adds row r
+// in tree order. Byte rows with d <= 128 (q8 = this lane's four query bytes): every partial
+// sum of the canonical FP32 distance is then an integer below 128 * 255^2 < 2^24, so it is
+// exact and the canonical value is the exact integer result, computed with byte SIMD
+// (|q - x| per byte, four-way dot product) and one warp-wide integer sum per row.
+template <int METRIC, bool SMALLD, typename RT>
+__device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const int32_t* rid, int U, const float* q,
+                                            float4 qreg, uint32_t q8, int d, int lane, float* P) {
     const int nc4 = d >> 2;
     if (SMALLD) {
         const bool has = lane < nc4;
-        for (int b = 0; b < U; b += 8) {
-            float4 y[8];
+        if constexpr (sizeof(RT) == 1) {
+            uint32_t w[32];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int r = b + t;
-                y[t] = (r < U && has) ? reinterpret_cast<const float4*>(base + (long long)rid[r] * d)[lane]
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = 0; r < 32; ++r)
+                w[r] = (r < U && has) ? *reinterpret_cast<const uint32_t*>(base + (long long)rid[r] * d + 4 * lane)
+                                      : 0u;
+            uint32_t mine = 0u;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                if (r < U) {
+                    uint32_t part;
+                    if (METRIC == FGIM_L2SQ) {
+                        const uint32_t df = __vabsdiffu4(q8, w[r]);
+                        part = __dp4a(df, df, 0u);
+                    } else {
+                        part = __dp4a(q8, w[r], 0u);
+                    }
+                    const uint32_t tot = __reduce_add_sync(kFull, part);
+                    if (lane == r) mine = tot;
+                }
             }
+            return lane < U ? (float)mine : 0.f;
+        } else {
+            for (int b = 0; b < U; b += 8) {
+                float4 y[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int r = b + t;
-                if (r < U) P[lane * 33 + r] = has ? chunk_part<METRIC>(qreg, y[t]) : 0.f;
+                for (int t = 0; t < 8; ++t) {
+                    const int r = b + t;
+                    y[t] = (r < U && has) ? reinterpret_cast<const float4*>(base + (long long)rid[r] * d)[lane]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int r = b + t;
+                    if (r < U) P[lane * 33 + r] = has ? chunk_part<METRIC>(qreg, y[t]) : 0.f;
+                }
             }
         }
     } else {
         for (int r = 0; r < U; ++r)
-            P[lane * 33 + r] = lane_part<METRIC>(reinterpret_cast<const float4*>(q),
-                                                 reinterpret_cast<const float4*>(base + (long long)rid[r] * d), nc4,
-                                                 lane);
+            P[lane * 33 + r] = lane_part_rows<METRIC, RT>(q, base + (long long)rid[r] * d, nc4, lane);
     }
     __syncwarp();
     const float s = lane < U ? smem_tree_sum(P, lane) : 0.f;
@@ -62,12 +129,19 @@ __device__ __forceinline__ float rows_delta(const float* __restrict__ base, cons
     return s;
 }
 
+// this lane's four query coordinates as bytes (integers in [0, 255] when byte rows are used)
+__device__ __forceinline__ uint32_t pack_u8x4(float4 v) {
+    return __float2uint_rn(v.x) | (__float2uint_rn(v.y) << 8) | (__float2uint_rn(v.z) << 16) |
+           (__float2uint_rn(v.w) << 24);
+}
+
 // Alg. 1 over one graph whose rows are Xt[v] / adj[v * M] for local ids v < nt. Keys carry
 // global ids (local + id_off). Returns the pool size (<= L); the pool stays sorted.
 // scratch: 32 ints of shared memory for the compacted neighbour ids.
-template <int METRIC, bool SMALLD>
-__device__ int beam_search(const float* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
-                           int M, long long nt, int ep, long long id_off, const float* q, float4 qreg, float qinv,
+template <int METRIC, bool SMALLD, typename RT>
+__device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
+                           int M, long long nt, int ep, long long id_off, const float* q, float4 qreg, uint32_t q8,
+                           float qinv,
                            int d, int L, uint64_t* pool, uint8_t* pflag, int32_t* ht, int htbits, int32_t* scratch,
                            float* P, WarpCounters& ctr, int* status) {
     const int lane = lane_id();
@@ -81,7 +155,7 @@ __device__ int beam_search(const float* __restrict__ Xt, const float* __restrict
         return 0;
     }
     {
-        const float dd = rows_delta<METRIC, SMALLD>(Xt, scratch, 1, q, qreg, d, lane, P);
+        const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, 1, q, qreg, q8, d, lane, P);
         uint64_t key = kEmptyKey;
         if (lane == 0) {
             const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[ep]) : 1.f;
@@ -130,7 +204,7 @@ __device__ int beam_search(const float* __restrict__ Xt, const float* __restrict
             if (U == 0) continue;
             if (v >= 0) scratch[__popc(m & lt)] = v;
             __syncwarp();
-            const float dd = rows_delta<METRIC, SMALLD>(Xt, scratch, U, q, qreg, d, lane, P);
+            const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, U, q, qreg, q8, d, lane, P);
             uint64_t cand = kEmptyKey;
             if (lane < U) {
                 const int32_t w = scratch[lane];
@@ -190,9 +264,9 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 // Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
 // (delta, id), write ids / distances / new flags.
-template <int METRIC, bool SMALLD>
+template <int METRIC, bool SMALLD, typename RT>
 __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* __restrict__ X,
-                                                     const float* __restrict__ inv_norm, long long N, int k, int L,
+                                                     const RT* __restrict__ Xr, const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
                                                      float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
                                                      unsigned long long* counters, int* status) {
@@ -219,6 +293,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     const float qinv = (METRIC == FGIM_COSINE) ? inv_norm[g] : 1.f;
     __syncwarp();
     const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t q8 = (sizeof(RT) == 1 && SMALLD) ? pack_u8x4(qreg) : 0u;
 
     WarpCounters ctr;
     const int i = shard_of(t, g);
@@ -240,7 +315,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
         if (U == 0) continue;
         if (v >= 0) scratch[__popc(m & lt)] = (int32_t)(t.off[i] + v);
         __syncwarp();
-        const float dd = rows_delta<METRIC, SMALLD>(X, scratch, U, q, qreg, d, lane, P);
+        const float dd = rows_delta<METRIC, SMALLD, RT>(Xr, scratch, U, q, qreg, q8, d, lane, P);
         uint64_t cand = kEmptyKey;
         if (lane < U) {
             const int32_t gv = scratch[lane];
@@ -255,8 +330,8 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     for (int j = 0; j < t.h; ++j) {
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
-        const int np = beam_search<METRIC, SMALLD>(X + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr,
-                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, qinv, d, L,
+        const int np = beam_search<METRIC, SMALLD, RT>(Xr + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr,
+                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, q8, qinv, d, L,
                                                    pool, pflag, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
             const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
@@ -281,8 +356,9 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
 
 // Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
 // (qids == nullptr) or rows qids[i] of X.
-template <int METRIC, bool SMALLD>
-__global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, const float* __restrict__ inv_norm,
+template <int METRIC, bool SMALLD, typename RT>
+__global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
+                                                const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
                                                 int entry, const float* __restrict__ Q,
                                                 const float* __restrict__ q_inv, const int32_t* __restrict__ qids,
@@ -310,8 +386,9 @@ __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, con
     if (METRIC == FGIM_COSINE) qinv = qids ? inv_norm[qids[qi]] : q_inv[qi];
     __syncwarp();
     const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t q8 = (sizeof(RT) == 1 && SMALLD) ? pack_u8x4(qreg) : 0u;
     WarpCounters ctr;
-    const int np = beam_search<METRIC, SMALLD>(X, inv_norm, graph, R, n, entry, 0, q, qreg, qinv, d, L, pool, pflag,
+    const int np = beam_search<METRIC, SMALLD, RT>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, q8, qinv, d, L, pool, pflag,
                                                ht, htbits, scratch, P, ctr, status);
     for (int s = lane; s < topk; s += 32) {
         if (s < np) {
@@ -333,21 +410,21 @@ static int ht_bits_for(int L) {
     return b;
 }
 
-#define FGIM_DISPATCH_METRIC_D(M, D, MACRO)                          \
-    do {                                                             \
-        const bool small_ = (D) <= 128;                              \
-        if ((M) == FGIM_L2SQ) {                                      \
-            if (small_) MACRO(FGIM_L2SQ, true); else MACRO(FGIM_L2SQ, false);       \
-        } else if ((M) == FGIM_IP) {                                 \
-            if (small_) MACRO(FGIM_IP, true); else MACRO(FGIM_IP, false);           \
-        } else {                                                     \
-            if (small_) MACRO(FGIM_COSINE, true); else MACRO(FGIM_COSINE, false);   \
-        }                                                            \
+#define FGIM_DISPATCH_METRIC_D(M, D, MACRO, RT)                                      \
+    do {                                                                             \
+        const bool small_ = (D) <= 128;                                              \
+        if ((M) == FGIM_L2SQ) {                                                      \
+            if (small_) MACRO(FGIM_L2SQ, true, RT); else MACRO(FGIM_L2SQ, false, RT);       \
+        } else if ((M) == FGIM_IP) {                                                 \
+            if (small_) MACRO(FGIM_IP, true, RT); else MACRO(FGIM_IP, false, RT);           \
+        } else {                                                                     \
+            if (small_) MACRO(FGIM_COSINE, true, RT); else MACRO(FGIM_COSINE, false, RT);   \
+        }                                                                            \
     } while (0)
 
-cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float* inv_norm, long long N, int metric,
-                               int k, int L, fgim_knng* out, unsigned long long* counters, int* status,
-                               cudaStream_t s) {
+cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
+                               long long N, int metric, int k, int L, fgim_knng* out, unsigned long long* counters,
+                               int* status, cudaStream_t s) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const WarpLayout lay = warp_layout(t.dim, L, htbits, k);
@@ -355,24 +432,32 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const float*
     const long long blocks = (N + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_CQ(MT, SD)                                                                                     \
+#define FGIM_LAUNCH_CQ(MT, SD, RT)                                                                                 \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_cross_query<MT, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        e = cudaFuncSetAttribute(k_cross_query<MT, SD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                 (int)smem);                                                                       \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_cross_query", s);                                                                        \
-        k_cross_query<MT, SD><<<(unsigned)blocks, wpb * 32, smem, s>>>(t, X, inv_norm, N, k, L, htbits, out->ids, \
-                                                                       out->dist, out->flags, counters, status);   \
+        k_cross_query<MT, SD, RT><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                        \
+            t, X, reinterpret_cast<const RT*>(rows), inv_norm, N, k, L, htbits, out->ids, out->dist, out->flags,   \
+            counters, status);                                                                                     \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ);
+    if (X8) {
+        const void* rows = X8;
+        FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ, uint8_t);
+    } else {
+        const void* rows = X;
+        FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ, float);
+    }
 #undef FGIM_LAUNCH_CQ
     return e;
 }
 
-cudaError_t launch_search(const float* X, const float* inv_norm, long long n, int d, int metric, const int32_t* graph,
-                          int R, int entry, const float* Q, const float* q_inv, const int32_t* qids, long long nq,
-                          int topk, int L, int32_t* out_ids, float* out_dist, unsigned long long* counters,
-                          int* status, cudaStream_t s) {
+cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
+                          const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
+                          const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
+                          unsigned long long* counters, int* status, cudaStream_t s) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const WarpLayout lay = warp_layout(d, L, htbits, 0);
@@ -380,19 +465,54 @@ cudaError_t launch_search(const float* X, const float* inv_norm, long long n, in
     const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_S(MT, SD)                                                                                      \
+#define FGIM_LAUNCH_S(MT, SD, RT)                                                                                  \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_search<MT, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        e = cudaFuncSetAttribute(k_search<MT, SD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_search", s);                                                                             \
-        k_search<MT, SD><<<(unsigned)blocks, wpb * 32, smem, s>>>(X, inv_norm, n, d, graph, R, entry, Q, q_inv,   \
-                                                                  qids, nq, topk, L, htbits, out_ids, out_dist,   \
-                                                                  counters, status);                               \
+        k_search<MT, SD, RT><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                             \
+            X, reinterpret_cast<const RT*>(rows), inv_norm, n, d, graph, R, entry, Q, q_inv, qids, nq, topk, L,    \
+            htbits, out_ids, out_dist, counters, status);                                                          \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S);
+    if (X8 && qids) {   // byte rows need integer queries: rows of X
+        const void* rows = X8;
+        FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S, uint8_t);
+    } else {
+        const void* rows = X;
+        FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S, float);
+    }
 #undef FGIM_LAUNCH_S
     return e;
+}
+
+// ---------------------------------------------------------------------------- byte rows
+// flag |= 1 unless every coordinate is an integer in [0, 255]; X8 = the coordinates as bytes
+__global__ void k_narrow_u8(const float4* __restrict__ X, long long n4, uchar4* __restrict__ X8, int* flag) {
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = X[i];
+        const float a[4] = {v.x, v.y, v.z, v.w};
+        unsigned char b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool ok = a[q] >= 0.f && a[q] <= 255.f && a[q] == truncf(a[q]);
+            bad |= !ok;
+            b[q] = ok ? (unsigned char)a[q] : 0;
+        }
+        X8[i] = make_uchar4(b[0], b[1], b[2], b[3]);
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_narrow_u8(const float* X, long long n_elems, uint8_t* X8, int* flag, cudaStream_t s) {
+    if (n_elems <= 0) return cudaSuccess;
+    LaunchScope ls("k_narrow_u8", s);
+    const long long n4 = n_elems / 4;
+    const long long blocks = std::min<long long>((n4 + 255) / 256, 152LL * 16);
+    k_narrow_u8<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(X), n4,
+                                                 reinterpret_cast<uchar4*>(X8), flag);
+    return cudaGetLastError();
 }
 
 }  // namespace fgim

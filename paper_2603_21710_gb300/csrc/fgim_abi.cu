@@ -354,6 +354,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.blist = c.alloc<int32_t>(2 * N);
     b.blist_cap = N;
     b.join_filter = p->join_filter;
+    b.X8 = P.X8;
     b.Xb = nullptr;
     if (p->join_filter == 0 && P.d % 16 == 0) {
         b.Xb = c.alloc<__nv_bfloat16>(N * P.d);

@@ -80,6 +80,8 @@ struct RefineBuffers {
     int join_filter;
     void* Xb;
     float4* tcm;
+    // the vectors as bytes when every coordinate is an integer in [0, 255], else nullptr
+    const uint8_t* X8;
 };
 
 cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s);

@@ -236,7 +236,7 @@ cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cuda
 // ---------------------------------------------------------------------------- Update
 constexpr int kJThreads = 256;
 
-__device__ __forceinline__ int jhash(int32_t id, int hs) { return (int)(((uint32_t)id * 2654435761u) & (hs - 1)); }
+__device__ __forceinline__ int jhash(int32_t id, int hs) { return (int)((((uint32_t)id * 2654435761u) >> 12) & (hs - 1)); }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -567,6 +567,9 @@ constexpr int kTCThreads = 128;    // four warps, one per 32-lane quarter of TME
 constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
 constexpr int kTCSmallNC = 128;    // candidate sets up to this size form the four-CTAs-per-SM launch
+constexpr int kTCBloomBits = 4096; // bitmap of hashed candidate ids: most list entries skip the hash table
+
+__device__ __forceinline__ uint32_t bloom_bit(int32_t id) { return ((uint32_t)id * 0x9E3779B1u) >> 20; }
 
 __global__ void k_prep_bf16(const float* __restrict__ X, long long N, int d, __nv_bfloat16* __restrict__ Xb,
                             float4* __restrict__ tcm) {
@@ -610,7 +613,7 @@ cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* 
 // Shared memory of one k_join_tc CTA (offsets from the first 1024-byte boundary of the
 // dynamic shared memory; `bytes` includes the slack for that alignment).
 struct TCLayout {
-    int op, rows_alloc, dpad, meta, colf, thr, pb_key, cid, hk, hv, mask, queue, pb_tgt, misc, bytes, hs, words;
+    int op, rows_alloc, dpad, meta, colf, thr, pb_key, cid, hk, hv, bm, mask, queue, pb_tgt, misc, bytes, hs, words;
 };
 
 __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
@@ -640,6 +643,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     o += hs * 4;
     l.hv = o;
     o += hs * 4;
+    l.bm = o;
+    o += kTCBloomBits / 8;
     l.mask = o;
     o += a16(cm * l.words * 4);
     l.queue = o;
@@ -655,8 +660,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
 // One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
 template <int METRIC>
 __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
-    ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const float4* __restrict__ tcm,
-    const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
+    ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
+    const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
     const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
     int cm, uint32_t tmem_cols, const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt,
     uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
@@ -687,6 +692,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
     int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
     int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem + L.bm);
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     uint32_t* queue = reinterpret_cast<uint32_t*>(smem + L.queue);
     int32_t* pb_tgt = reinterpret_cast<int32_t*>(smem + L.pb_tgt);
@@ -710,6 +716,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     if (tid < nc) cid[tid] = cA;
     if (tid + kTCThreads < nc) cid[tid + kTCThreads] = cB;
     for (int i = tid; i < hs; i += kTCThreads) hk[i] = -1;
+    for (int i = tid; i < kTCBloomBits / 32; i += kTCThreads) bm[i] = 0u;
     for (int i = tid; i < nc * W; i += kTCThreads) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
     if (tid == 0) tc::mbar_init(mbar, 1);
@@ -762,6 +769,8 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     };
     load_items(0);
     auto insert = [&](int32_t c, int i) {
+        const uint32_t b = bloom_bit(c);
+        atomicOr(bm + (b >> 5), 1u << (b & 31));
         int slot = jhash(c, hs);
         for (int probe = 0; probe < hs; ++probe) {
             if (atomicCAS(hk + slot, -1, c) == -1) {
@@ -787,6 +796,8 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     // membership bits: mask(i, j) = C[j] in N(C[i])
     auto member = [&](int i, int32_t e) {
         if (e < 0) return;
+        const uint32_t b = bloom_bit(e);
+        if (!((bm[b >> 5] >> (b & 31)) & 1u)) return;
         int slot = jhash(e, hs);
         for (int probe = 0; probe < hs; ++probe) {
             const int32_t h = hk[slot];
@@ -835,81 +846,85 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
     tc::fence_after_sync();
 
-    // Filter: warp w owns rows 32 w .. 32 w + 31 (its TMEM lane quarter) and reads the
-    // columns right of its first row, 16 at a time. A pair survives when lo, a lower bound
-    // of its exact value, can still beat the worst key of a list it is not already in.
-    // General test: lo = value - bound with the bound of the file comment (cs term:
-    // e_i x_j + e_j (x_i + e_i) + g (x_i + e_i)(x_j + e_j)). Squared L2 on exactly converted
-    // rows (e = 0): with s2 = n2_i + n2_j, 2 x_i x_j <= 1.0002 s2 and |D| <= (1 + g) x_i x_j,
-    // the general bound is at most 1.1 s2 (4.001 g + 12.01 u); Cf adds margin for the
-    // rounding of P_i + P_j - 2 D, so lo = P_i + P_j - 2 D is lower still.
-    const int i = 32 * warp + lane;
-    const bool row_ok = i < nn;
-    const float4 fi = row_ok ? colf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float Pi = fi.x, tdi = fi.y;
-    const int shi = row_ok ? __float_as_int(fi.z) : -1;
-    const float4 mi = row_ok ? meta[i] : make_float4(0.f, 0.f, 0.f, 1.f);
-    const float n2i = mi.x, xi = mi.y, ei = mi.z, ci = mi.w;
-    const float xei = xi + ei;
+    // Filter. A pair survives when lo, a lower bound of its exact value, can still beat the
+    // worst key of a list it is not already in. General test: lo = value - bound with the
+    // bound of the file comment (cs term: e_i x_j + e_j (x_i + e_i) + g (x_i + e_i)(x_j + e_j)).
+    // Squared L2 on exactly converted rows (e = 0): with s2 = n2_i + n2_j, 2 x_i x_j <= 1.0002 s2
+    // and |D| <= (1 + g) x_i x_j, the general bound is at most 1.1 s2 (4.001 g + 12.01 u); Cf
+    // adds margin for the rounding of P_i + P_j - 2 D, so lo = P_i + P_j - 2 D is lower still.
+    //
+    // Pairs are {i, j} with i < nn (new) and i < j < nc. Both MMA operands are the staged
+    // tile, so D is symmetric and lane r of warp w (TMEM lane r = 32 w + lane, candidate r)
+    // evaluates the pairs {c, r} with c < min(r, nn) from its own TMEM row; pairs with
+    // j >= 128 (no TMEM lane) are evaluated by lane i at columns 128 .. nc - 1. Every pair is
+    // evaluated once and no warp reads more than nn + (nc - 128) columns.
+    const int r = 32 * warp + lane;
+    const bool r_ok = r < nc;
+    const float4 fr = r_ok ? colf[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float Pr = fr.x, tdr = fr.y;
+    const int shr = r_ok ? __float_as_int(fr.z) : -1;
+    const float4 mr = r_ok ? meta[r] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float n2r = mr.x, xr = mr.y, er = mr.z, cr = mr.w;
+    const float xer = xr + er;
+    const bool fast = METRIC == FGIM_L2SQ && exact;
     unsigned long long my_pairs = 0;
-    auto enqueue = [&](int j, float lo, float tdj) {
-        unsigned dm = 0;
-        if (lo <= tdi && !((mask[i * W + (j >> 5)] >> (j & 31)) & 1u)) dm |= 1u;
-        if (lo <= tdj && !((mask[j * W + (i >> 5)] >> (i & 31)) & 1u)) dm |= 2u;
+    auto test = [&](int c, float dot) {
+        const float4 cc = colf[c];
+        if (shr == __float_as_int(cc.z)) return;
+        ++my_pairs;
+        float lo;
+        if (fast) {
+            lo = fmaf(-2.f, dot, Pr + cc.x);
+        } else {
+            const float4 mc = meta[c];
+            const float cs = er * mc.y + mc.z * xer + g * xer * (mc.y + mc.z);
+            float val, bound;
+            if (METRIC == FGIM_L2SQ) {
+                const float s2 = n2r + mc.x;
+                val = s2 - 2.f * dot;
+                bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
+                                4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
+            } else if (METRIC == FGIM_IP) {
+                val = 1.f - dot;
+                bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
+            } else {
+                const float ccv = cr * mc.w;
+                val = 1.f - dot * ccv;
+                bound = 1.1f * (cs * ccv + g * fabsf(val)) + 4.8e-7f;
+            }
+            lo = val - bound;
+        }
+        if (!(lo <= fmaxf(tdr, cc.y))) return;
+        unsigned dm = 0;   // bit 0: r's list gets c, bit 1: c's list gets r
+        if (lo <= tdr && !((mask[r * W + (c >> 5)] >> (c & 31)) & 1u)) dm |= 1u;
+        if (lo <= cc.y && !((mask[c * W + (r >> 5)] >> (r & 31)) & 1u)) dm |= 2u;
         if (dm) {
             const int slot = atomicAdd(misc + 1, 1);
-            if (slot < kTCQueue) queue[slot] = (uint32_t)i | ((uint32_t)j << 10) | (dm << 20);
+            if (slot < kTCQueue) queue[slot] = (uint32_t)r | ((uint32_t)c << 10) | (dm << 20);
         }
     };
-    if (ok_mma && 32 * warp < nn) {
+    if (ok_mma) {
         const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-        if (METRIC == FGIM_L2SQ && exact) {
-            for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
-                float dv[16];
-                tc::tmem_ld16(trow + (uint32_t)j0, dv);
+        const int cend = min(nn, 32 * warp + 31);   // c < r <= 32 w + 31
+        for (int c0 = 0; c0 < cend; c0 += 16) {
+            float dv[16];
+            tc::tmem_ld16(trow + (uint32_t)c0, dv);
 #pragma unroll
-                for (int t16 = 0; t16 < 16; ++t16) {
-                    const int j = j0 + t16;
-                    if (j >= nc) break;
-                    const float4 cj = colf[j];
-                    if (!(row_ok && j > i && shi != __float_as_int(cj.z))) continue;
-                    ++my_pairs;
-                    const float lo = fmaf(-2.f, dv[t16], Pi + cj.x);
-                    if (!(lo <= fmaxf(tdi, cj.y))) continue;
-                    enqueue(j, lo, cj.y);
-                }
+            for (int t16 = 0; t16 < 16; ++t16) {
+                const int c = c0 + t16;
+                if (c >= cend) break;
+                if (r_ok && c < r) test(c, dv[t16]);
             }
-        } else {
-            for (int j0 = 32 * warp; j0 < npad; j0 += 16) {
+        }
+        if (nc > 128 && 32 * warp < nn) {
+            for (int c0 = 128; c0 < npad; c0 += 16) {
                 float dv[16];
-                tc::tmem_ld16(trow + (uint32_t)j0, dv);
+                tc::tmem_ld16(trow + (uint32_t)c0, dv);
 #pragma unroll
                 for (int t16 = 0; t16 < 16; ++t16) {
-                    const int j = j0 + t16;
-                    if (j >= nc) break;
-                    const float4 cj = colf[j];
-                    if (!(row_ok && j > i && shi != __float_as_int(cj.z))) continue;
-                    ++my_pairs;
-                    const float4 mj = meta[j];
-                    const float dot = dv[t16];
-                    const float cs = ei * mj.y + mj.z * xei + g * xei * (mj.y + mj.z);
-                    float val, bound;
-                    if (METRIC == FGIM_L2SQ) {
-                        const float s2 = n2i + mj.x;
-                        val = s2 - 2.f * dot;
-                        bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
-                                        4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
-                    } else if (METRIC == FGIM_IP) {
-                        val = 1.f - dot;
-                        bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
-                    } else {
-                        const float cc = ci * mj.w;
-                        val = 1.f - dot * cc;
-                        bound = 1.1f * (cs * cc + g * fabsf(val)) + 4.8e-7f;
-                    }
-                    const float lo = val - bound;
-                    if (!(lo <= fmaxf(tdi, cj.y))) continue;
-                    enqueue(j, lo, cj.y);
+                    const int c = c0 + t16;
+                    if (c >= nc) break;
+                    if (r < nn) test(c, dv[t16]);
                 }
             }
         }
@@ -931,54 +946,78 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             ra[t8] = (int)(e & 1023u);
             rb[t8] = (int)((e >> 10) & 1023u);
         }
-        float acc[8][4];
+        float sc = 0.f;
+        if (X8 != nullptr && d <= 128) {
+            // integer coordinates in [0, 255] and d <= 128: every partial sum of the canonical
+            // FP32 value is an integer below 2^24, so it equals the exact integer result
+            const bool has = lane < vq;
+            uint32_t wa[8], wb[8];
 #pragma unroll
-        for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
-        for (int c = lane; c < vq; c += 32) {
-            float4 xa[8], xb[8];
-            if (exact) {
+            for (int t8 = 0; t8 < 8; ++t8) {
+                wa[t8] = has ? *reinterpret_cast<const uint32_t*>(X8 + (long long)cid[ra[t8]] * d + 4 * lane) : 0u;
+                wb[t8] = has ? *reinterpret_cast<const uint32_t*>(X8 + (long long)cid[rb[t8]] * d + 4 * lane) : 0u;
+            }
 #pragma unroll
-                for (int t8 = 0; t8 < 8; ++t8) {
-                    const uint2 ua =
-                        *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
-                    const uint2 ub =
-                        *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
-                    xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
-                                         __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
-                    xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
-                                         __uint_as_float(ub.y << 16), __uint_as_float(ub.y & 0xffff0000u));
+            for (int t8 = 0; t8 < 8; ++t8) {
+                uint32_t part;
+                if (METRIC == FGIM_L2SQ) {
+                    const uint32_t df = __vabsdiffu4(wa[t8], wb[t8]);
+                    part = __dp4a(df, df, 0u);
+                } else {
+                    part = __dp4a(wa[t8], wb[t8], 0u);
                 }
-            } else {
+                const uint32_t tot = __reduce_add_sync(kFull, part);
+                if (lane == t8) sc = (float)tot;
+            }
+        } else {
+            float acc[8][4];
+#pragma unroll
+            for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
+            for (int c = lane; c < vq; c += 32) {
+                float4 xa[8], xb[8];
+                if (exact) {
+#pragma unroll
+                    for (int t8 = 0; t8 < 8; ++t8) {
+                        const uint2 ua =
+                            *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
+                        const uint2 ub =
+                            *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
+                        xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
+                                             __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
+                        xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
+                                             __uint_as_float(ub.y << 16), __uint_as_float(ub.y & 0xffff0000u));
+                    }
+                } else {
+#pragma unroll
+                    for (int t8 = 0; t8 < 8; ++t8) {
+                        xa[t8] = reinterpret_cast<const float4*>(X + (long long)cid[ra[t8]] * d)[c];
+                        xb[t8] = reinterpret_cast<const float4*>(X + (long long)cid[rb[t8]] * d)[c];
+                    }
+                }
 #pragma unroll
                 for (int t8 = 0; t8 < 8; ++t8) {
-                    xa[t8] = reinterpret_cast<const float4*>(X + (long long)cid[ra[t8]] * d)[c];
-                    xb[t8] = reinterpret_cast<const float4*>(X + (long long)cid[rb[t8]] * d)[c];
+                    const float4 x = xa[t8], y = xb[t8];
+                    if (METRIC == FGIM_L2SQ) {
+                        const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+                        const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
+                        acc[t8][0] = fmaf(e0, e0, acc[t8][0]);
+                        acc[t8][1] = fmaf(e1, e1, acc[t8][1]);
+                        acc[t8][2] = fmaf(e2, e2, acc[t8][2]);
+                        acc[t8][3] = fmaf(e3, e3, acc[t8][3]);
+                    } else {
+                        acc[t8][0] = fmaf(x.x, y.x, acc[t8][0]);
+                        acc[t8][1] = fmaf(x.y, y.y, acc[t8][1]);
+                        acc[t8][2] = fmaf(x.z, y.z, acc[t8][2]);
+                        acc[t8][3] = fmaf(x.w, y.w, acc[t8][3]);
+                    }
                 }
             }
 #pragma unroll
             for (int t8 = 0; t8 < 8; ++t8) {
-                const float4 x = xa[t8], y = xb[t8];
-                if (METRIC == FGIM_L2SQ) {
-                    const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
-                    const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
-                    acc[t8][0] = fmaf(e0, e0, acc[t8][0]);
-                    acc[t8][1] = fmaf(e1, e1, acc[t8][1]);
-                    acc[t8][2] = fmaf(e2, e2, acc[t8][2]);
-                    acc[t8][3] = fmaf(e3, e3, acc[t8][3]);
-                } else {
-                    acc[t8][0] = fmaf(x.x, y.x, acc[t8][0]);
-                    acc[t8][1] = fmaf(x.y, y.y, acc[t8][1]);
-                    acc[t8][2] = fmaf(x.z, y.z, acc[t8][2]);
-                    acc[t8][3] = fmaf(x.w, y.w, acc[t8][3]);
-                }
+                const float tot = warp_butterfly(__fadd_rn(__fadd_rn(acc[t8][0], acc[t8][1]),
+                                                           __fadd_rn(acc[t8][2], acc[t8][3])));
+                if (lane == t8) sc = tot;
             }
-        }
-        float sc = 0.f;
-#pragma unroll
-        for (int t8 = 0; t8 < 8; ++t8) {
-            const float tot = warp_butterfly(__fadd_rn(__fadd_rn(acc[t8][0], acc[t8][1]),
-                                                       __fadd_rn(acc[t8][2], acc[t8][3])));
-            if (lane == t8) sc = tot;
         }
         if (lane < U) {
             const uint32_t e = queue[q0 + lane];
@@ -1128,7 +1167,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
         k_join_tc<MT><<<(unsigned)count, kTCThreads, smem, s>>>(                                                  \
-            t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,      \
+            t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, status);                                                                                       \
         e = cudaGetLastError();                                                                                   \

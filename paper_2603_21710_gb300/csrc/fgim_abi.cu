@@ -286,7 +286,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.X = contiguous_vectors(c, sh, h, p->dim, P.N);
     P.inv = nullptr;
     P.X8 = nullptr;
-    if (P.d % 4 == 0) {
+    if (byte_rows_ok(P.d)) {
         uint8_t* x8 = c.alloc<uint8_t>(P.N * P.d);
         int* flag = c.alloc<int>(1);
         ck(cudaMemsetAsync(flag, 0, sizeof(int), c.s));

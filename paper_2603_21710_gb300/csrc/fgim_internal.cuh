@@ -80,6 +80,16 @@ __device__ __forceinline__ int shard_of(const ShardTable& t, long long g) {
     return lo;
 }
 
+// Byte rows: the vectors stored as one byte per coordinate, used when every coordinate is an
+// integer in [0, 255] and d <= 128, d % 16 == 0 (distances are then exact integers below 2^24).
+__host__ __device__ inline bool byte_rows_ok(int d) { return d % 16 == 0 && d <= 128; }
+
+// lanes per byte row: 16-byte chunks per row rounded up to a power of two (d <= 128)
+__device__ __forceinline__ int byte_lanes(int d) {
+    const int c16 = d >> 4;
+    return c16 <= 1 ? 1 : c16 <= 2 ? 2 : c16 <= 4 ? 4 : 8;
+}
+
 // ----------------------------------------------------------------------------
 // canonical distance (see the file comment); rows are 16-byte aligned float4 arrays
 // ----------------------------------------------------------------------------

@@ -947,27 +947,39 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             rb[t8] = (int)((e >> 10) & 1023u);
         }
         float sc = 0.f;
-        if (X8 != nullptr && d <= 128) {
-            // integer coordinates in [0, 255] and d <= 128: every partial sum of the canonical
-            // FP32 value is an integer below 2^24, so it equals the exact integer result
-            const bool has = lane < vq;
-            uint32_t wa[8], wb[8];
-#pragma unroll
-            for (int t8 = 0; t8 < 8; ++t8) {
-                wa[t8] = has ? *reinterpret_cast<const uint32_t*>(X8 + (long long)cid[ra[t8]] * d + 4 * lane) : 0u;
-                wb[t8] = has ? *reinterpret_cast<const uint32_t*>(X8 + (long long)cid[rb[t8]] * d + 4 * lane) : 0u;
-            }
-#pragma unroll
-            for (int t8 = 0; t8 < 8; ++t8) {
-                uint32_t part;
-                if (METRIC == FGIM_L2SQ) {
-                    const uint32_t df = __vabsdiffu4(wa[t8], wb[t8]);
-                    part = __dp4a(df, df, 0u);
-                } else {
-                    part = __dp4a(wa[t8], wb[t8], 0u);
+        if (X8 != nullptr) {
+            // byte rows (integer coordinates in [0, 255], d <= 128, d % 16 == 0): every partial
+            // sum of the canonical FP32 value is an integer below 2^24, so it equals the exact
+            // integer |a|^2 + |b|^2 - 2 a.b; lanes take 16 bytes, 32 / lanes-per-row pairs per load
+            const int lpr = byte_lanes(d);
+            const int rpi = 32 / lpr;
+            const int sub = lane / lpr, part = lane & (lpr - 1);
+            const bool has = part < (d >> 4);
+            uint32_t mine = 0u;
+            for (int t = 0; t * rpi < U; ++t) {
+                const int pr = t * rpi + sub;
+                uint4 xa = make_uint4(0u, 0u, 0u, 0u), xb = xa;
+                if (pr < U && has) {
+                    const uint32_t e = queue[q0 + pr];
+                    xa = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
+                    xb = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
                 }
-                const uint32_t tot = __reduce_add_sync(kFull, part);
-                if (lane == t8) sc = (float)tot;
+                uint32_t dot = __dp4a(xa.x, xb.x, 0u);
+                dot = __dp4a(xa.y, xb.y, dot);
+                dot = __dp4a(xa.z, xb.z, dot);
+                dot = __dp4a(xa.w, xb.w, dot);
+                for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
+                const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
+                if (lane / rpi == t) mine = got;
+            }
+            if (lane < U) {
+                if (METRIC == FGIM_L2SQ) {
+                    const uint32_t e = queue[q0 + lane];
+                    const uint32_t na = __float2uint_rn(meta[e & 1023u].x), nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
+                    sc = (float)(na + nb - 2u * mine);
+                } else {
+                    sc = (float)mine;
+                }
             }
         } else {
             float acc[8][4];

@@ -67,43 +67,79 @@ __device__ __forceinline__ float lane_part_rows(const float* q, const RT* row, i
     return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
 }
 
+// The query as bytes for byte rows: this lane's 16 bytes (chunk lane % lanes-per-row) and
+// the sum of the squared coordinates.
+struct QBytes {
+    uint4 w;
+    uint32_t q2;
+};
+
+__device__ __forceinline__ uint32_t pack4(const float* v) {
+    return __float2uint_rn(v[0]) | (__float2uint_rn(v[1]) << 8) | (__float2uint_rn(v[2]) << 16) |
+           (__float2uint_rn(v[3]) << 24);
+}
+
+__device__ __forceinline__ QBytes query_bytes(const float* q, int d, int lane) {
+    QBytes b;
+    const int lpr = byte_lanes(d);
+    const int part = lane & (lpr - 1);
+    b.w = make_uint4(0u, 0u, 0u, 0u);
+    if (part < (d >> 4)) {
+        const float* c = q + 16 * part;
+        b.w = make_uint4(pack4(c), pack4(c + 4), pack4(c + 8), pack4(c + 12));
+    }
+    uint32_t s = 0;
+    for (int c = lane; c < d; c += 32) s += __float2uint_rn(q[c]) * __float2uint_rn(q[c]);
+    b.q2 = __reduce_add_sync(kFull, s);
+    return b;
+}
+
 // Canonical distances between the query (q in shared memory; qreg = this lane's chunk when
 // d <= 128) and the U <= 32 rows base[rid[r]]; lane r receives row r's distance.
 // FP32 rows load coalesced (one warp load per row, eight rows in flight); every lane stores
 // its partials in P (32 x 33 floats of this warp's shared memory) and lane r re-adds row r
-// in tree order. Byte rows with d <= 128 (q8 = this lane's four query bytes): every partial
-// sum of the canonical FP32 distance is then an integer below 128 * 255^2 < 2^24, so it is
-// exact and the canonical value is the exact integer result, computed with byte SIMD
-// (|q - x| per byte, four-way dot product) and one warp-wide integer sum per row.
+// in tree order.
+// Byte rows (d <= 128, d % 16 == 0): every partial sum of the canonical FP32 value is then an
+// integer below 128 * 255^2 < 2^24, so it is exact and the canonical value is the exact
+// integer result. Lanes take 16 bytes each (32 / lanes-per-row rows per warp load) and form
+// |q|^2 + |x|^2 - 2 q.x with four-way byte dot products, summed over the row's lanes.
 template <int METRIC, bool SMALLD, typename RT>
 __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const int32_t* rid, int U, const float* q,
-                                            float4 qreg, uint32_t q8, int d, int lane, float* P) {
+                                            float4 qreg, const QBytes& qb, int d, int lane, float* P) {
     const int nc4 = d >> 2;
-    if (SMALLD) {
-        const bool has = lane < nc4;
-        if constexpr (sizeof(RT) == 1) {
-            uint32_t w[32];
-#pragma unroll
-            for (int r = 0; r < 32; ++r)
-                w[r] = (r < U && has) ? *reinterpret_cast<const uint32_t*>(base + (long long)rid[r] * d + 4 * lane)
-                                      : 0u;
-            uint32_t mine = 0u;
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                if (r < U) {
-                    uint32_t part;
-                    if (METRIC == FGIM_L2SQ) {
-                        const uint32_t df = __vabsdiffu4(q8, w[r]);
-                        part = __dp4a(df, df, 0u);
-                    } else {
-                        part = __dp4a(q8, w[r], 0u);
-                    }
-                    const uint32_t tot = __reduce_add_sync(kFull, part);
-                    if (lane == r) mine = tot;
-                }
+    if constexpr (sizeof(RT) == 1) {
+        const int lpr = byte_lanes(d);
+        const int rpi = 32 / lpr;   // rows per warp load
+        const int sub = lane / lpr, part = lane & (lpr - 1);
+        const bool has = part < (d >> 4);
+        uint32_t mine = 0u;
+        for (int t = 0; t * rpi < U; ++t) {
+            const int r = t * rpi + sub;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (r < U && has) w = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
+            uint32_t sq = __dp4a(qb.w.x, w.x, 0u);
+            sq = __dp4a(qb.w.y, w.y, sq);
+            sq = __dp4a(qb.w.z, w.z, sq);
+            sq = __dp4a(qb.w.w, w.w, sq);
+            uint32_t sv;
+            if (METRIC == FGIM_L2SQ) {
+                uint32_t sx = __dp4a(w.x, w.x, 0u);
+                sx = __dp4a(w.y, w.y, sx);
+                sx = __dp4a(w.z, w.z, sx);
+                sx = __dp4a(w.w, w.w, sx);
+                sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
+            } else {
+                sv = sq;
             }
-            return lane < U ? (float)mine : 0.f;
-        } else {
+            for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
+            const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
+            if (lane / rpi == t) mine = got;
+        }
+        if (METRIC == FGIM_L2SQ) mine += qb.q2;
+        return lane < U ? (float)mine : 0.f;
+    } else {
+        if (SMALLD) {
+            const bool has = lane < nc4;
             for (int b = 0; b < U; b += 8) {
                 float4 y[8];
 #pragma unroll
@@ -118,75 +154,89 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
                     if (r < U) P[lane * 33 + r] = has ? chunk_part<METRIC>(qreg, y[t]) : 0.f;
                 }
             }
+        } else {
+            for (int r = 0; r < U; ++r)
+                P[lane * 33 + r] = lane_part_rows<METRIC, RT>(q, base + (long long)rid[r] * d, nc4, lane);
         }
-    } else {
-        for (int r = 0; r < U; ++r)
-            P[lane * 33 + r] = lane_part_rows<METRIC, RT>(q, base + (long long)rid[r] * d, nc4, lane);
+        __syncwarp();
+        const float s = lane < U ? smem_tree_sum(P, lane) : 0.f;
+        __syncwarp();
+        return s;
     }
-    __syncwarp();
-    const float s = lane < U ? smem_tree_sum(P, lane) : 0.f;
-    __syncwarp();
-    return s;
-}
-
-// this lane's four query coordinates as bytes (integers in [0, 255] when byte rows are used)
-__device__ __forceinline__ uint32_t pack_u8x4(float4 v) {
-    return __float2uint_rn(v.x) | (__float2uint_rn(v.y) << 8) | (__float2uint_rn(v.z) << 16) |
-           (__float2uint_rn(v.w) << 24);
 }
 
 // Alg. 1 over one graph whose rows are Xt[v] / adj[v * M] for local ids v < nt. Keys carry
-// global ids (local + id_off). Returns the pool size (<= L); the pool stays sorted.
+// global ids (local + id_off). The pool C (<= L <= 128 keys, sorted by (delta, id)) lives in
+// registers: entry e = 32 s + lane is pk[s] of that lane, its "expanded" mark bit s of expd.
+// A candidate enters by one ballot for its rank and one shift of the entries behind it;
+// candidates that cannot beat the worst entry of a full pool are never inserted. Returns
+// the pool size and leaves the pool in pool[0 .. size) (shared memory).
 // scratch: 32 ints of shared memory for the compacted neighbour ids.
+constexpr int kPoolSlots = 4;
+
+__device__ __forceinline__ uint64_t pick_slot(const uint64_t (&pk)[kPoolSlots], int s) {
+    uint64_t v = pk[0];
+#pragma unroll
+    for (int t = 1; t < kPoolSlots; ++t)
+        if (s == t) v = pk[t];
+    return v;
+}
+
 template <int METRIC, bool SMALLD, typename RT>
 __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
-                           int M, long long nt, int ep, long long id_off, const float* q, float4 qreg, uint32_t q8,
-                           float qinv,
-                           int d, int L, uint64_t* pool, uint8_t* pflag, int32_t* ht, int htbits, int32_t* scratch,
-                           float* P, WarpCounters& ctr, int* status) {
+                           int M, long long nt, int ep, long long id_off, const float* q, float4 qreg,
+                           const QBytes& qb, float qinv, int d, int L, uint64_t* pool, int32_t* ht, int htbits,
+                           int32_t* scratch, float* P, WarpCounters& ctr, int* status) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const int H = 1 << htbits;
+    const int S = (L + 31) >> 5;
     for (int s = lane; s < H; s += 32) ht[s] = -1;
     if (lane == 0) scratch[0] = ep;
     __syncwarp();
-    if (ep < 0 || ep >= nt) {
+    if (ep < 0 || ep >= nt || L < 1 || S > kPoolSlots) {
         if (lane == 0) atomicOr(status, kErrBounds);
         return 0;
     }
+    uint64_t pk[kPoolSlots];
+#pragma unroll
+    for (int s = 0; s < kPoolSlots; ++s) pk[s] = kEmptyKey;
+    unsigned expd = 0u;
+    int n;
+    uint64_t worst = kEmptyKey;   // pool entry L - 1 once the pool is full
     {
-        const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, 1, q, qreg, q8, d, lane, P);
+        const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, 1, q, qreg, qb, d, lane, P);
         uint64_t key = kEmptyKey;
         if (lane == 0) {
             const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, invt[ep]) : 1.f;
             key = mkkey(delta_finish<METRIC>(dd, inv), (int32_t)(ep + id_off));
             ht[ht_slot(ep, htbits)] = ep;
             ctr.ndc++;
+            pk[0] = key;
         }
+        n = 1;
+        if (L == 1) worst = shfl64(key, 0);
         __syncwarp();
-        int n0 = warp_merge<false>(pool, pflag, 0, L, key, 0);
-        (void)n0;
     }
-    int n = 1;
     // every vertex is expanded at most once, so nt + 1 iterations always suffice
+    bool done = false;
     for (long long it = 0; it <= nt; ++it) {
         int first = -1;
-        for (int base = 0; base < n; base += 32) {
-            const int p = base + lane;
-            const unsigned m = __ballot_sync(kFull, p < n && pflag[p] == 0);
-            if (m) {
-                first = base + __ffs(m) - 1;
-                break;
+#pragma unroll
+        for (int s = 0; s < kPoolSlots; ++s) {
+            if (s < S && first < 0) {
+                const unsigned m = __ballot_sync(kFull, 32 * s + lane < n && !((expd >> s) & 1u));
+                if (m) first = 32 * s + __ffs(m) - 1;
             }
         }
-        if (first < 0) return n;
-        const long long u = (long long)key_id(pool[first]) - id_off;
-        __syncwarp();
-        if (lane == 0) {
-            pflag[first] = 1;
-            ctr.hops++;
+        if (first < 0) {
+            done = true;
+            break;
         }
-        __syncwarp();
+        const uint64_t fk = shfl64(pick_slot(pk, first >> 5), first & 31);
+        if (lane == (first & 31)) expd |= 1u << (first >> 5);
+        if (lane == 0) ctr.hops++;
+        const long long u = (long long)key_id(fk) - id_off;
         const int32_t* row = adj + u * M;
         for (int c0 = 0; c0 < M; c0 += 32) {
             int v = (c0 + lane < M) ? row[c0 + lane] : -1;
@@ -204,7 +254,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             if (U == 0) continue;
             if (v >= 0) scratch[__popc(m & lt)] = v;
             __syncwarp();
-            const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, U, q, qreg, q8, d, lane, P);
+            const float dd = rows_delta<METRIC, SMALLD, RT>(Xt, scratch, U, q, qreg, qb, d, lane, P);
             uint64_t cand = kEmptyKey;
             if (lane < U) {
                 const int32_t w = scratch[lane];
@@ -213,10 +263,64 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
                 ctr.ndc++;
             }
             __syncwarp();
-            n = warp_merge<false>(pool, pflag, n, L, cand, 0);
+            bool valid = cand < worst;
+            unsigned vm;
+            while ((vm = __ballot_sync(kFull, valid)) != 0u) {
+                const int src = __ffs(vm) - 1;
+                const uint64_t c = shfl64(cand, src);
+                if (lane == src) valid = false;
+                bool eq = false;
+                int pos = 0;
+#pragma unroll
+                for (int s = 0; s < kPoolSlots; ++s) {
+                    if (s < S) {
+                        eq |= pk[s] == c;
+                        pos += __popc(__ballot_sync(kFull, pk[s] < c));
+                    }
+                }
+                if (__any_sync(kFull, eq)) continue;   // already in the pool (same id, same key)
+                // entries pos .. n - 1 move up by one; the slots are updated from the last one
+                // down so every slot reads its predecessor's old entries
+#pragma unroll
+                for (int s = kPoolSlots - 1; s >= 0; --s) {
+                    if (s < S) {
+                        const uint64_t up = shfl64(pk[s], (lane + 31) & 31);
+                        const unsigned eup = __shfl_sync(kFull, (expd >> s) & 1u, (lane + 31) & 31);
+                        uint64_t prev = up;
+                        unsigned eprev = eup;
+                        if (s > 0) {
+                            const uint64_t w31 = shfl64(pk[s > 0 ? s - 1 : 0], 31);
+                            const unsigned e31 = __shfl_sync(kFull, (expd >> (s > 0 ? s - 1 : 0)) & 1u, 31);
+                            if (lane == 0) {
+                                prev = w31;
+                                eprev = e31;
+                            }
+                        }
+                        const int e = 32 * s + lane;
+                        if (e > pos && !(s == 0 && lane == 0)) {
+                            pk[s] = prev;
+                            expd = (expd & ~(1u << s)) | (eprev << s);
+                        } else if (e == pos) {
+                            pk[s] = c;
+                            expd &= ~(1u << s);
+                        }
+                        if (e >= L) {
+                            pk[s] = kEmptyKey;
+                            expd &= ~(1u << s);
+                        }
+                    }
+                }
+                n = n < L ? n + 1 : L;
+                if (n == L) worst = shfl64(pick_slot(pk, (L - 1) >> 5), (L - 1) & 31);
+                valid = valid && cand < worst;
+            }
         }
     }
-    if (lane == 0) atomicOr(status, kErrTimeout);
+    if (!done && lane == 0) atomicOr(status, kErrTimeout);
+#pragma unroll
+    for (int s = 0; s < kPoolSlots; ++s)
+        if (s < S && 32 * s + lane < n) pool[32 * s + lane] = pk[s];
+    __syncwarp();
     return n;
 }
 
@@ -235,7 +339,7 @@ __device__ __forceinline__ void warp_add_counters(WarpCounters& c, unsigned long
 
 // shared-memory layout of one warp; all offsets multiples of 16 bytes
 struct WarpLayout {
-    int q, pool, pflag, ht, res, scratch, part, bytes;
+    int q, pool, ht, res, scratch, part, bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -247,8 +351,6 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
     o += align16(d * 4);
     w.pool = o;
     o += align16(L * 8);
-    w.pflag = o;
-    o += align16(L);
     w.ht = o;
     o += align16((1 << htbits) * 4);
     w.res = o;
@@ -265,7 +367,7 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
 // (delta, id), write ids / distances / new flags.
 template <int METRIC, bool SMALLD, typename RT>
-__global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const float* __restrict__ X,
                                                      const RT* __restrict__ Xr, const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
                                                      float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
@@ -281,7 +383,6 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
-    uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
     uint64_t* res = reinterpret_cast<uint64_t*>(base + lay.res);
     int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
@@ -293,7 +394,10 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
     const float qinv = (METRIC == FGIM_COSINE) ? inv_norm[g] : 1.f;
     __syncwarp();
     const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t q8 = (sizeof(RT) == 1 && SMALLD) ? pack_u8x4(qreg) : 0u;
+    QBytes qb;
+    qb.w = make_uint4(0u, 0u, 0u, 0u);
+    qb.q2 = 0u;
+    if (sizeof(RT) == 1) qb = query_bytes(q, d, lane);
 
     WarpCounters ctr;
     const int i = shard_of(t, g);
@@ -315,7 +419,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
         if (U == 0) continue;
         if (v >= 0) scratch[__popc(m & lt)] = (int32_t)(t.off[i] + v);
         __syncwarp();
-        const float dd = rows_delta<METRIC, SMALLD, RT>(Xr, scratch, U, q, qreg, q8, d, lane, P);
+        const float dd = rows_delta<METRIC, SMALLD, RT>(Xr, scratch, U, q, qreg, qb, d, lane, P);
         uint64_t cand = kEmptyKey;
         if (lane < U) {
             const int32_t gv = scratch[lane];
@@ -331,8 +435,8 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
         const int np = beam_search<METRIC, SMALLD, RT>(Xr + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr,
-                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, q8, qinv, d, L,
-                                                   pool, pflag, ht, htbits, scratch, P, ctr, status);
+                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d,
+                                                       L, pool, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
             const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
             nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
@@ -357,7 +461,7 @@ __global__ void __launch_bounds__(128) k_cross_query(ShardTable t, const float* 
 // Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
 // (qids == nullptr) or rows qids[i] of X.
 template <int METRIC, bool SMALLD, typename RT>
-__global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
+__global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
                                                 const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
                                                 int entry, const float* __restrict__ Q,
@@ -374,7 +478,6 @@ __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, con
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
-    uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
     int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
     float* P = reinterpret_cast<float*>(base + lay.part);
@@ -386,10 +489,13 @@ __global__ void __launch_bounds__(128) k_search(const float* __restrict__ X, con
     if (METRIC == FGIM_COSINE) qinv = qids ? inv_norm[qids[qi]] : q_inv[qi];
     __syncwarp();
     const float4 qreg = (SMALLD && lane < (d >> 2)) ? q4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t q8 = (sizeof(RT) == 1 && SMALLD) ? pack_u8x4(qreg) : 0u;
+    QBytes qb;
+    qb.w = make_uint4(0u, 0u, 0u, 0u);
+    qb.q2 = 0u;
+    if (sizeof(RT) == 1) qb = query_bytes(q, d, lane);
     WarpCounters ctr;
-    const int np = beam_search<METRIC, SMALLD, RT>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, q8, qinv, d, L, pool, pflag,
-                                               ht, htbits, scratch, P, ctr, status);
+    const int np = beam_search<METRIC, SMALLD, RT>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, qb, qinv, d, L, pool,
+                                                   ht, htbits, scratch, P, ctr, status);
     for (int s = lane; s < topk; s += 32) {
         if (s < np) {
             out_ids[qi * topk + s] = key_id(pool[s]);
@@ -443,7 +549,7 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
             counters, status);                                                                                     \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (X8) {
+    if (X8 && byte_rows_ok(t.dim)) {
         const void* rows = X8;
         FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ, uint8_t);
     } else {
@@ -475,7 +581,7 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
             htbits, out_ids, out_dist, counters, status);                                                          \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (X8 && qids) {   // byte rows need integer queries: rows of X
+    if (X8 && qids && byte_rows_ok(d)) {   // byte rows need integer queries: rows of X
         const void* rows = X8;
         FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S, uint8_t);
     } else {

@@ -351,7 +351,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
     b.max_nc = c.alloc<int32_t>(8);
     b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);   // 8 ints of the 64-byte pinned slot
-    b.blist = c.alloc<int32_t>(2 * N);
+    b.blist = c.alloc<int32_t>(3 * N);
     b.blist_cap = N;
     b.join_filter = p->join_filter;
     b.X8 = P.X8;

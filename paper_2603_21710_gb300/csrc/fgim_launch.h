@@ -69,8 +69,8 @@ struct RefineBuffers {
     // scan scratch
     void* scan_tmp;
     size_t scan_bytes;
-    // largest candidate set and C_n of a pass and the two launch lists' sizes and largest
-    // sets (device, 6 ints), a pinned host slot to read them, and the launch lists (2 x cap)
+    // largest candidate set and C_n of a pass and the three launch lists' sizes and largest
+    // sets (device, 8 ints), a pinned host slot to read them, and the launch lists (3 x cap)
     int32_t* max_nc;
     int32_t* host_i32;
     int32_t* blist;

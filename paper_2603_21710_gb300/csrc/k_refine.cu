@@ -566,7 +566,6 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 constexpr int kTCThreads = 128;    // four warps, one per 32-lane quarter of TMEM
 constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
-constexpr int kTCSmallNC = 128;    // candidate sets up to this size form the four-CTAs-per-SM launch
 constexpr int kTCBloomBits = 4096; // bitmap of hashed candidate ids: most list entries skip the hash table
 
 __device__ __forceinline__ uint32_t bloom_bit(int32_t id) { return ((uint32_t)id * 0x9E3779B1u) >> 20; }
@@ -623,8 +622,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     l.hs = hs;
     l.words = (cm + 31) >> 5;
     const int npad = ((cm + 15) / 16) * 16;
-    l.rows_alloc = npad > 128 ? npad : 128;   // the A operand always spans 128 rows
-    l.dpad = ((d + 63) / 64) * 64;            // whole 128-byte panels (zero beyond d)
+    l.rows_alloc = npad;               // rows per panel (a multiple of 8: whole swizzle atoms)
+    l.dpad = ((d + 63) / 64) * 64;     // whole 128-byte panels (zero beyond d)
     auto a16 = [](int x) { return (x + 15) & ~15; };
     int o = 0;
     l.op = o;
@@ -653,12 +652,16 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     o += kTCPropBuf * 4;
     l.misc = o;
     o += 64;
-    l.bytes = o + 1024;
+    // The A operand spans 128 rows of every panel even when fewer are staged: rows past the
+    // staged ones read whatever follows (the next panel, the arrays above) and only produce
+    // rows of D that are never used. Keep all of it inside the allocation.
+    const int a_end = (l.dpad / 64 - 1) * l.rows_alloc * 128 + 128 * 128;
+    l.bytes = (o > a_end ? o : a_end) + 1024;
     return l;
 }
 
 // One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
-template <int METRIC>
+template <int METRIC, bool BYTES>
 __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
     const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
@@ -866,11 +869,13 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const float4 mr = r_ok ? meta[r] : make_float4(0.f, 0.f, 0.f, 1.f);
     const float n2r = mr.x, xr = mr.y, er = mr.z, cr = mr.w;
     const float xer = xr + er;
-    const bool fast = METRIC == FGIM_L2SQ && exact;
+    const bool fast = METRIC == FGIM_L2SQ && (BYTES || exact);
+    const unsigned lt = (1u << lane) - 1u;
     unsigned long long my_pairs = 0;
-    auto test = [&](int c, float dot) {
+    // survivor directions of pair {r, c} (bit 0: r's list gets c, bit 1: c's list gets r)
+    auto test = [&](int c, float dot) -> unsigned {
         const float4 cc = colf[c];
-        if (shr == __float_as_int(cc.z)) return;
+        if (shr == __float_as_int(cc.z)) return 0u;
         ++my_pairs;
         float lo;
         if (fast) {
@@ -894,12 +899,22 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             }
             lo = val - bound;
         }
-        if (!(lo <= fmaxf(tdr, cc.y))) return;
-        unsigned dm = 0;   // bit 0: r's list gets c, bit 1: c's list gets r
+        if (!(lo <= fmaxf(tdr, cc.y))) return 0u;
+        unsigned dm = 0u;
         if (lo <= tdr && !((mask[r * W + (c >> 5)] >> (c & 31)) & 1u)) dm |= 1u;
         if (lo <= cc.y && !((mask[c * W + (r >> 5)] >> (r & 31)) & 1u)) dm |= 2u;
+        return dm;
+    };
+    // one shared-memory atomic per warp and column for the survivors of that column
+    auto append = [&](int c, unsigned dm) {
+        const unsigned vote = __ballot_sync(kFull, dm != 0u);
+        if (vote == 0u) return;
+        const int leader = __ffs(vote) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(misc + 1, __popc(vote));
+        base = __shfl_sync(kFull, base, leader);
         if (dm) {
-            const int slot = atomicAdd(misc + 1, 1);
+            const int slot = base + __popc(vote & lt);
             if (slot < kTCQueue) queue[slot] = (uint32_t)r | ((uint32_t)c << 10) | (dm << 20);
         }
     };
@@ -913,7 +928,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             for (int t16 = 0; t16 < 16; ++t16) {
                 const int c = c0 + t16;
                 if (c >= cend) break;
-                if (r_ok && c < r) test(c, dv[t16]);
+                append(c, (r_ok && c < r) ? test(c, dv[t16]) : 0u);
             }
         }
         if (nc > 128 && 32 * warp < nn) {
@@ -924,7 +939,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
                 for (int t16 = 0; t16 < 16; ++t16) {
                     const int c = c0 + t16;
                     if (c >= nc) break;
-                    if (r < nn) test(c, dv[t16]);
+                    append(c, r < nn ? test(c, dv[t16]) : 0u);
                 }
             }
         }
@@ -933,55 +948,68 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);   // free TMEM for the next CTA on this SM
 
-    // exact re-rank of the survivors with the canonical FP32 distance, eight pairs per warp
-    // step. With every staged row exact the rows are read from the staged tile (the same
-    // values), otherwise from the FP32 rows in global memory.
+    // Exact re-rank of the survivors with the canonical FP32 distance, kStep pairs per warp
+    // step; lane t < U proposes for pair t.
+    //  - byte rows (integer coordinates in [0, 255], d <= 128, d % 16 == 0): every partial sum
+    //    of the canonical FP32 value is an integer below 2^24, so it equals the exact integer
+    //    |a|^2 + |b|^2 - 2 a.b; lanes take 16 bytes, 32 / lanes-per-row pairs per warp load,
+    //    all loads of a step issued before the sums.
+    //  - otherwise the canonical FP32 additions, from the staged tile when every staged row is
+    //    exact (the same values), else from the FP32 rows in global memory.
+    constexpr int kStep = BYTES ? 16 : 8;
     const int nq = min(misc[1], kTCQueue);
-    for (int q0 = warp * 8; q0 < nq; q0 += (kTCThreads / 32) * 8) {
-        const int U = min(8, nq - q0);
-        int ra[8], rb[8];
-#pragma unroll
-        for (int t8 = 0; t8 < 8; ++t8) {
-            const uint32_t e = queue[q0 + min(t8, U - 1)];
-            ra[t8] = (int)(e & 1023u);
-            rb[t8] = (int)((e >> 10) & 1023u);
-        }
+    for (int q0 = warp * kStep; q0 < nq; q0 += (kTCThreads / 32) * kStep) {
+        const int U = min(kStep, nq - q0);
         float sc = 0.f;
-        if (X8 != nullptr) {
-            // byte rows (integer coordinates in [0, 255], d <= 128, d % 16 == 0): every partial
-            // sum of the canonical FP32 value is an integer below 2^24, so it equals the exact
-            // integer |a|^2 + |b|^2 - 2 a.b; lanes take 16 bytes, 32 / lanes-per-row pairs per load
+        if constexpr (BYTES) {
             const int lpr = byte_lanes(d);
             const int rpi = 32 / lpr;
             const int sub = lane / lpr, part = lane & (lpr - 1);
             const bool has = part < (d >> 4);
-            uint32_t mine = 0u;
-            for (int t = 0; t * rpi < U; ++t) {
+            constexpr int kIt = 4;   // >= kStep * lpr / 32 for lpr <= 8
+            uint4 xa[kIt], xb[kIt];
+#pragma unroll
+            for (int t = 0; t < kIt; ++t) {
                 const int pr = t * rpi + sub;
-                uint4 xa = make_uint4(0u, 0u, 0u, 0u), xb = xa;
+                xa[t] = make_uint4(0u, 0u, 0u, 0u);
+                xb[t] = xa[t];
                 if (pr < U && has) {
                     const uint32_t e = queue[q0 + pr];
-                    xa = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
-                    xb = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
+                    xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
+                    xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
                 }
-                uint32_t dot = __dp4a(xa.x, xb.x, 0u);
-                dot = __dp4a(xa.y, xb.y, dot);
-                dot = __dp4a(xa.z, xb.z, dot);
-                dot = __dp4a(xa.w, xb.w, dot);
-                for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
-                const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
-                if (lane / rpi == t) mine = got;
+            }
+            uint32_t mine = 0u;
+#pragma unroll
+            for (int t = 0; t < kIt; ++t) {
+                if (t * rpi < U) {
+                    uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
+                    dot = __dp4a(xa[t].y, xb[t].y, dot);
+                    dot = __dp4a(xa[t].z, xb[t].z, dot);
+                    dot = __dp4a(xa[t].w, xb[t].w, dot);
+                    for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
+                    const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
+                    if (lane / rpi == t) mine = got;
+                }
             }
             if (lane < U) {
                 if (METRIC == FGIM_L2SQ) {
                     const uint32_t e = queue[q0 + lane];
-                    const uint32_t na = __float2uint_rn(meta[e & 1023u].x), nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
+                    const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
+                    const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
                     sc = (float)(na + nb - 2u * mine);
                 } else {
                     sc = (float)mine;
                 }
             }
         } else {
+            int ra[8], rb[8];
+#pragma unroll
+            for (int t8 = 0; t8 < 8; ++t8) {
+                const uint32_t e = queue[q0 + min(t8, U - 1)];
+                ra[t8] = (int)(e & 1023u);
+                rb[t8] = (int)((e >> 10) & 1023u);
+            }
             float acc[8][4];
 #pragma unroll
             for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
@@ -1031,26 +1059,44 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
                 if (lane == t8) sc = tot;
             }
         }
+        // proposals: one shared-memory atomic per warp and direction
+        uint64_t key[2] = {kEmptyKey, kEmptyKey};
+        int32_t tgt[2] = {-1, -1};
         if (lane < U) {
             const uint32_t e = queue[q0 + lane];
             const int ia = (int)(e & 1023u), jb = (int)((e >> 10) & 1023u);
             const unsigned dm = (e >> 20) & 3u;
             const float dd =
                 delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(meta[ia].w, meta[jb].w) : 1.f);
+#pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
-                if (!((dm >> dir) & 1u)) continue;
                 const int a2 = dir == 0 ? ia : jb, b2 = dir == 0 ? jb : ia;
-                const uint64_t key = mkkey(dd, cid[b2]);
-                if (key >= thr[a2]) continue;
-                const int slot = atomicAdd(misc, 1);
+                const uint64_t kk = mkkey(dd, cid[b2]);
+                if (((dm >> dir) & 1u) && kk < thr[a2]) {
+                    key[dir] = kk;
+                    tgt[dir] = cid[a2];
+                }
+            }
+        }
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            const bool has_p = tgt[dir] >= 0;
+            const unsigned vote = __ballot_sync(kFull, has_p);
+            if (vote == 0u) continue;
+            const int leader = __ffs(vote) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(misc, __popc(vote));
+            base = __shfl_sync(kFull, base, leader);
+            if (has_p) {
+                const int slot = base + __popc(vote & lt);
                 if (slot < kTCPropBuf) {
-                    pb_tgt[slot] = cid[a2];
-                    pb_key[slot] = key;
+                    pb_tgt[slot] = tgt[dir];
+                    pb_key[slot] = key[dir];
                 } else {
                     const unsigned long long pos = atomicAdd(prop_count, 1ull);
                     if (pos < (unsigned long long)prop_cap) {
-                        prop_tgt[pos] = cid[a2];
-                        prop_key[pos] = key;
+                        prop_tgt[pos] = tgt[dir];
+                        prop_key[pos] = key[dir];
                     } else {
                         pending[v] = 1;
                         atomicOr(status, kErrOverflow);
@@ -1087,11 +1133,15 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
 }
 
 // Largest candidate set and C_n of the vertices in vlist (all when null), and the vertices
-// split by candidate-set size into two lists (blist[0..], blist[cap..]) for the tensor-core
-// launches. out: [0] max |C|, [1] max |C_n|, [2], [3] list sizes, [4], [5] max |C| per list.
+// split by candidate-set size into kTCLists lists (blist[q * cap ..]) for the tensor-core
+// launches: |C| <= 64, <= 128, > 128. out: [0] max |C|, [1] max |C_n|, [2 + q] list sizes,
+// [5 + q] max |C| per list.
+constexpr int kTCLists = 3;
+__device__ __forceinline__ int tc_list_of(int m) { return m <= 64 ? 0 : m <= 128 ? 1 : 2; }
+
 __global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __restrict__ no,
-                               const int32_t* __restrict__ vlist, long long nv, int small_nc,
-                               int32_t* __restrict__ out, int32_t* __restrict__ blist, long long cap) {
+                               const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ out,
+                               int32_t* __restrict__ blist, long long cap) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int m = 0, mn = 0;
@@ -1103,31 +1153,29 @@ __global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __
         m = mn > 0 ? mn + no[v] : 0;
         act = mn > 0 && m >= 2;
     }
-    const bool small = act && m <= small_nc, large = act && m > small_nc;
-    const unsigned bs = __ballot_sync(kFull, small), bl = __ballot_sync(kFull, large);
-    int base_s = 0, base_l = 0;
-    if (lane == 0) {
-        if (bs) base_s = atomicAdd(out + 2, __popc(bs));
-        if (bl) base_l = atomicAdd(out + 3, __popc(bl));
-    }
-    base_s = __shfl_sync(kFull, base_s, 0);
-    base_l = __shfl_sync(kFull, base_l, 0);
+    const int q = tc_list_of(m);
     const unsigned lt = (1u << lane) - 1u;
-    if (small) blist[base_s + __popc(bs & lt)] = (int32_t)v;
-    if (large) blist[cap + base_l + __popc(bl & lt)] = (int32_t)v;
-    int ms = small ? m : 0, ml = large ? m : 0;
+#pragma unroll
+    for (int b = 0; b < kTCLists; ++b) {
+        const bool mine = act && q == b;
+        const unsigned vote = __ballot_sync(kFull, mine);
+        int base = 0;
+        if (lane == 0 && vote) base = atomicAdd(out + 2 + b, __popc(vote));
+        base = __shfl_sync(kFull, base, 0);
+        if (mine) blist[(long long)b * cap + base + __popc(vote & lt)] = (int32_t)v;
+        int mb = mine ? m : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(kFull, mb, o));
+        if (lane == 0 && mb > 0) atomicMax(out + 5 + b, mb);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         m = max(m, __shfl_xor_sync(kFull, m, o));
         mn = max(mn, __shfl_xor_sync(kFull, mn, o));
-        ms = max(ms, __shfl_xor_sync(kFull, ms, o));
-        ml = max(ml, __shfl_xor_sync(kFull, ml, o));
     }
     if (lane == 0) {
         if (m > 0) atomicMax(out, m);
         if (mn > 0) atomicMax(out + 1, mn);
-        if (ms > 0) atomicMax(out + 4, ms);
-        if (ml > 0) atomicMax(out + 5, ml);
     }
 }
 
@@ -1145,27 +1193,27 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                         int* status, cudaStream_t s) {
     if (nv <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMemsetAsync(b.max_nc, 0, 6 * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.max_nc, 0, 8 * sizeof(int32_t), s)) != cudaSuccess) return e;
     {
         LaunchScope ls("k_join_buckets", s);
-        k_join_buckets<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, kTCSmallNC, b.max_nc,
-                                                                  b.blist, b.blist_cap);
+        k_join_buckets<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, b.max_nc, b.blist,
+                                                                  b.blist_cap);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    int32_t hb[6];
-    for (int q = 0; q < 6; ++q) hb[q] = b.host_i32[q];
+    int32_t hb[8];
+    for (int q = 0; q < 8; ++q) hb[q] = b.host_i32[q];
     const int32_t cm = hb[0], cmn = hb[1];
     if (cm < 2) return cudaSuccess;
     bool use_tc = b.join_filter == 0 && b.Xb && t.dim % 16 == 0 && cmn <= 128 && cm <= 256;
     if (use_tc)
-        for (int q = 0; q < 2; ++q)
-            if (hb[2 + q] > 0 && tc_layout(hb[4 + q], t.dim).bytes > 227 * 1024) use_tc = false;
+        for (int q = 0; q < kTCLists; ++q)
+            if (hb[2 + q] > 0 && tc_layout(hb[5 + q], t.dim).bytes > 227 * 1024) use_tc = false;
     if (use_tc) {
-        for (int q = 0; q < 2; ++q) {
-            const int32_t count = hb[2 + q], cmq = hb[4 + q];
+        for (int q = 0; q < kTCLists; ++q) {
+            const int32_t count = hb[2 + q], cmq = hb[5 + q];
             if (count <= 0) continue;
             const TCLayout TL = tc_layout(cmq, t.dim);
             const int npad = ((cmq + 15) / 16) * 16;
@@ -1173,20 +1221,25 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
             while ((int)cols < npad) cols <<= 1;
             const size_t smem = tc_launch_smem(TL, cols);
             const int32_t* list = b.blist + (long long)q * b.blist_cap;
-#define FGIM_LAUNCH_TC(MT)                                                                                        \
+#define FGIM_LAUNCH_TC(MT, BY)                                                                                    \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(k_join_tc<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+        e = cudaFuncSetAttribute(k_join_tc<MT, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
-        k_join_tc<MT><<<(unsigned)count, kTCThreads, smem, s>>>(                                                  \
+        k_join_tc<MT, BY><<<(unsigned)count, kTCThreads, smem, s>>>(                                              \
             t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, status);                                                                                       \
         e = cudaGetLastError();                                                                                   \
     } while (0)
-            if (metric == FGIM_L2SQ) FGIM_LAUNCH_TC(FGIM_L2SQ);
-            else if (metric == FGIM_IP) FGIM_LAUNCH_TC(FGIM_IP);
-            else FGIM_LAUNCH_TC(FGIM_COSINE);
+            const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim);
+            if (metric == FGIM_L2SQ) {
+                if (bytes) FGIM_LAUNCH_TC(FGIM_L2SQ, true); else FGIM_LAUNCH_TC(FGIM_L2SQ, false);
+            } else if (metric == FGIM_IP) {
+                if (bytes) FGIM_LAUNCH_TC(FGIM_IP, true); else FGIM_LAUNCH_TC(FGIM_IP, false);
+            } else {
+                if (bytes) FGIM_LAUNCH_TC(FGIM_COSINE, true); else FGIM_LAUNCH_TC(FGIM_COSINE, false);
+            }
 #undef FGIM_LAUNCH_TC
             if (e != cudaSuccess) return e;
         }

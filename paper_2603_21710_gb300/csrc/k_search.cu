@@ -112,28 +112,36 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
         const int rpi = 32 / lpr;   // rows per warp load
         const int sub = lane / lpr, part = lane & (lpr - 1);
         const bool has = part < (d >> 4);
-        uint32_t mine = 0u;
-        for (int t = 0; t * rpi < U; ++t) {
+        // all of this batch's row loads first (at most lpr <= 8 warp loads), then the sums
+        uint4 w[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
             const int r = t * rpi + sub;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (r < U && has) w = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
-            uint32_t sq = __dp4a(qb.w.x, w.x, 0u);
-            sq = __dp4a(qb.w.y, w.y, sq);
-            sq = __dp4a(qb.w.z, w.z, sq);
-            sq = __dp4a(qb.w.w, w.w, sq);
-            uint32_t sv;
-            if (METRIC == FGIM_L2SQ) {
-                uint32_t sx = __dp4a(w.x, w.x, 0u);
-                sx = __dp4a(w.y, w.y, sx);
-                sx = __dp4a(w.z, w.z, sx);
-                sx = __dp4a(w.w, w.w, sx);
-                sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
-            } else {
-                sv = sq;
+            w[t] = make_uint4(0u, 0u, 0u, 0u);
+            if (t < lpr && r < U && has) w[t] = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
+        }
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (t < lpr && t * rpi < U) {
+                uint32_t sq = __dp4a(qb.w.x, w[t].x, 0u);
+                sq = __dp4a(qb.w.y, w[t].y, sq);
+                sq = __dp4a(qb.w.z, w[t].z, sq);
+                sq = __dp4a(qb.w.w, w[t].w, sq);
+                uint32_t sv;
+                if (METRIC == FGIM_L2SQ) {
+                    uint32_t sx = __dp4a(w[t].x, w[t].x, 0u);
+                    sx = __dp4a(w[t].y, w[t].y, sx);
+                    sx = __dp4a(w[t].z, w[t].z, sx);
+                    sx = __dp4a(w[t].w, w[t].w, sx);
+                    sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
+                } else {
+                    sv = sq;
+                }
+                for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
+                const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
+                if (lane / rpi == t) mine = got;
             }
-            for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
-            const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
-            if (lane / rpi == t) mine = got;
         }
         if (METRIC == FGIM_L2SQ) mine += qb.q2;
         return lane < U ? (float)mine : 0.f;

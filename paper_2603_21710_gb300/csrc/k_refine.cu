@@ -661,7 +661,7 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
 }
 
 // One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
-template <int METRIC, bool BYTES>
+template <int METRIC, bool BYTES, bool LARGE>
 __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
     const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const int32_t cA = tid < cm ? cand[crow + tid] : -1;
     const int32_t cB = tid + kTCThreads < cm ? cand[crow + tid + kTCThreads] : -1;
     if (nn == 0 || nc < 2) return;
-    if (nc > cm || nn > 128 || cm > 2 * kTCThreads) {   // the host sized the launch; never expected
+    if (nc > cm || nn > 128 || cm > 2 * kTCThreads || (!LARGE && cm > 128)) {   // the host sized the launch
         if (tid == 0) atomicOr(status, kErrBounds);
         return;
     }
@@ -755,22 +755,22 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const bool vec = (k & 3) == 0 && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0;
     const int per = vec ? (k >> 2) : k;
     const int mtotal = nc * per;
-    constexpr int kMB = 8;   // items in flight per thread
-    int4 e4[kMB];
-    auto load_items = [&](int b0) {
-#pragma unroll
-        for (int u = 0; u < kMB; ++u) {
-            const int idx = b0 + tid + u * kTCThreads;
-            e4[u] = make_int4(-1, -1, -1, -1);
-            if (idx < mtotal) {
-                const int i = idx / per;
-                const int32_t* row = ids + (long long)cid[i] * k;
-                if (vec) e4[u] = reinterpret_cast<const int4*>(row)[idx - i * per];
-                else e4[u].x = row[idx - i * per];
-            }
+    // items are read kMB ahead through a rotating set of registers: the loop body (and its
+    // hash probes) exists once in the code, and kMB loads per thread stay in flight
+    constexpr int kMB = 4;
+    auto load_item = [&](int idx) -> int4 {
+        int4 r4 = make_int4(-1, -1, -1, -1);
+        if (idx < mtotal) {
+            const int i = idx / per;
+            const int32_t* row = ids + (long long)cid[i] * k;
+            if (vec) r4 = reinterpret_cast<const int4*>(row)[idx - i * per];
+            else r4.x = row[idx - i * per];
         }
+        return r4;
     };
-    load_items(0);
+    int4 e4[kMB];
+#pragma unroll
+    for (int u = 0; u < kMB; ++u) e4[u] = load_item(tid + u * kTCThreads);
     auto insert = [&](int32_t c, int i) {
         const uint32_t b = bloom_bit(c);
         atomicOr(bm + (b >> 5), 1u << (b & 31));
@@ -813,20 +813,15 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             slot = (slot + 1) & (hs - 1);
         }
     };
-    for (int b0 = 0; b0 < mtotal; b0 += kMB * kTCThreads) {
-        if (b0 > 0) load_items(b0);
+#pragma unroll 1
+    for (int idx = tid; idx < mtotal; idx += kTCThreads) {
+        const int4 cur = e4[0];
 #pragma unroll
-        for (int u = 0; u < kMB; ++u) {
-            const int idx = b0 + tid + u * kTCThreads;
-            if (idx >= mtotal) continue;
-            const int i = idx / per;
-            member(i, e4[u].x);
-            if (vec) {
-                member(i, e4[u].y);
-                member(i, e4[u].z);
-                member(i, e4[u].w);
-            }
-        }
+        for (int u = 0; u + 1 < kMB; ++u) e4[u] = e4[u + 1];
+        e4[kMB - 1] = load_item(idx + kMB * kTCThreads);
+        const int i = idx / per;
+#pragma unroll 1
+        for (int q = 0; q < (vec ? 4 : 1); ++q) member(i, q == 0 ? cur.x : q == 1 ? cur.y : q == 2 ? cur.z : cur.w);
     }
     cp_async_wait<0>();
     tc::fence_async_smem();
@@ -921,25 +916,25 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     if (ok_mma) {
         const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
         const int cend = min(nn, 32 * warp + 31);   // c < r <= 32 w + 31
-        for (int c0 = 0; c0 < cend; c0 += 16) {
-            float dv[16];
-            tc::tmem_ld16(trow + (uint32_t)c0, dv);
+#pragma unroll 1
+        for (int c0 = 0; c0 < cend; c0 += 4) {
+            float dv[4];
+            tc::tmem_ld4(trow + (uint32_t)c0, dv);
 #pragma unroll
-            for (int t16 = 0; t16 < 16; ++t16) {
-                const int c = c0 + t16;
-                if (c >= cend) break;
-                append(c, (r_ok && c < r) ? test(c, dv[t16]) : 0u);
+            for (int t4 = 0; t4 < 4; ++t4) {
+                const int c = c0 + t4;
+                if (c < cend) append(c, (r_ok && c < r) ? test(c, dv[t4]) : 0u);
             }
         }
-        if (nc > 128 && 32 * warp < nn) {
-            for (int c0 = 128; c0 < npad; c0 += 16) {
-                float dv[16];
-                tc::tmem_ld16(trow + (uint32_t)c0, dv);
+        if (LARGE && nc > 128 && 32 * warp < nn) {
+#pragma unroll 1
+            for (int c0 = 128; c0 < nc; c0 += 4) {
+                float dv[4];
+                tc::tmem_ld4(trow + (uint32_t)c0, dv);
 #pragma unroll
-                for (int t16 = 0; t16 < 16; ++t16) {
-                    const int c = c0 + t16;
-                    if (c >= nc) break;
-                    append(c, r < nn ? test(c, dv[t16]) : 0u);
+                for (int t4 = 0; t4 < 4; ++t4) {
+                    const int c = c0 + t4;
+                    if (c < nc) append(c, r < nn ? test(c, dv[t4]) : 0u);
                 }
             }
         }
@@ -1221,16 +1216,21 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
             while ((int)cols < npad) cols <<= 1;
             const size_t smem = tc_launch_smem(TL, cols);
             const int32_t* list = b.blist + (long long)q * b.blist_cap;
-#define FGIM_LAUNCH_TC(MT, BY)                                                                                    \
+#define FGIM_LAUNCH_TC3(MT, BY, LG)                                                                               \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(k_join_tc<MT, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        e = cudaFuncSetAttribute(k_join_tc<MT, BY, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
-        k_join_tc<MT, BY><<<(unsigned)count, kTCThreads, smem, s>>>(                                              \
+        k_join_tc<MT, BY, LG><<<(unsigned)count, kTCThreads, smem, s>>>(                                          \
             t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, status);                                                                                       \
         e = cudaGetLastError();                                                                                   \
+    } while (0)
+#define FGIM_LAUNCH_TC(MT, BY)                                                                                    \
+    do {                                                                                                          \
+        if (cmq > 128) FGIM_LAUNCH_TC3(MT, BY, true);                                                             \
+        else FGIM_LAUNCH_TC3(MT, BY, false);                                                                      \
     } while (0)
             const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim);
             if (metric == FGIM_L2SQ) {
@@ -1241,6 +1241,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                 if (bytes) FGIM_LAUNCH_TC(FGIM_COSINE, true); else FGIM_LAUNCH_TC(FGIM_COSINE, false);
             }
 #undef FGIM_LAUNCH_TC
+#undef FGIM_LAUNCH_TC3
             if (e != cudaSuccess) return e;
         }
         return e;

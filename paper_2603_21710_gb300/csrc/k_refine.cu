@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 // On integer-valued data the conversion is exact (e = 0) and the bound is tiny. Survivors are
 // re-ranked with the canonical FP32 distance (from the staged rows when every one of them
 // converted exactly, else from the FP32 rows); only exact keys are proposed.
-constexpr int kTCThreads = 128;    // four warps, one per 32-lane quarter of TMEM
+constexpr int kTCThreads = 128;    // threads of the FP32-row variant (byte rows: 256)
 constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
 constexpr int kTCBloomBits = 4096; // bitmap of hashed candidate ids: most list entries skip the hash table
@@ -662,13 +662,15 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
 
 // One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
 template <int METRIC, bool BYTES, bool LARGE>
-__global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
+__global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
     const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
     const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
     int cm, uint32_t tmem_cols, const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt,
     uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
     unsigned long long* pairs_count, int* status) {
+    constexpr int NT = BYTES ? 256 : 128;   // threads (byte rows: eight warps, two per TMEM lane quarter)
+    constexpr int NW = NT / 32;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int tid = threadIdx.x;
@@ -680,9 +682,9 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     // candidate ids, read before nc is known (a row of cand holds cmax >= cm entries)
     const long long crow = v * (long long)cmax;
     const int32_t cA = tid < cm ? cand[crow + tid] : -1;
-    const int32_t cB = tid + kTCThreads < cm ? cand[crow + tid + kTCThreads] : -1;
+    const int32_t cB = tid + NT < cm ? cand[crow + tid + NT] : -1;
     if (nn == 0 || nc < 2) return;
-    if (nc > cm || nn > 128 || cm > 2 * kTCThreads || (!LARGE && cm > 128)) {   // the host sized the launch
+    if (nc > cm || nn > 128 || cm > 2 * NT || (!LARGE && cm > 128)) {   // the host sized the launch
         if (tid == 0) atomicOr(status, kErrBounds);
         return;
     }
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     uint32_t* queue = reinterpret_cast<uint32_t*>(smem + L.queue);
     int32_t* pb_tgt = reinterpret_cast<int32_t*>(smem + L.pb_tgt);
     uint64_t* pb_key = reinterpret_cast<uint64_t*>(smem + L.pb_key);
-    // misc: [0] proposals buffered, [1] survivors, [2] rows whose BF16 copy is inexact,
+    // misc: [0] proposals buffered, [2] rows whose BF16 copy is inexact,
     // [4..5] base of this CTA's proposals in the global buffer; mbarrier at byte 32, TMEM
     // address at byte 48
     int* misc = reinterpret_cast<int*>(smem + L.misc);
@@ -717,10 +719,10 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     const float Cf = 1.2f * (4.001f * g + 12.01f * 5.9604645e-8f);
 
     if (tid < nc) cid[tid] = cA;
-    if (tid + kTCThreads < nc) cid[tid + kTCThreads] = cB;
-    for (int i = tid; i < hs; i += kTCThreads) hk[i] = -1;
-    for (int i = tid; i < kTCBloomBits / 32; i += kTCThreads) bm[i] = 0u;
-    for (int i = tid; i < nc * W; i += kTCThreads) mask[i] = 0u;
+    if (tid + NT < nc) cid[tid + NT] = cB;
+    for (int i = tid; i < hs; i += NT) hk[i] = -1;
+    for (int i = tid; i < kTCBloomBits / 32; i += NT) bm[i] = 0u;
+    for (int i = tid; i < nc * W; i += NT) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tmem_slot, tmem_cols);
@@ -729,7 +731,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     // past nc are never used, their products land in ignored rows and columns of D; chunks
     // past d are zero), this thread's candidates' worst keys and row statistics, and the
     // first batch of list entries for the membership bits.
-    for (int item = tid; item < nc * kcp; item += kTCThreads) {
+    for (int item = tid; item < nc * kcp; item += NT) {
         const int r = item / kcp, c = item - (item / kcp) * kcp;
         unsigned char* dst = op + tc::sw_offset(r, c, rows);
         if (c < kc) cp_async16(dst, Xb + (long long)cid[r] * d + c * 8, true);
@@ -745,7 +747,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         mA = tcm[cA];
         if (METRIC == FGIM_COSINE) invA = inv_norm[cA];
     }
-    if (tid + kTCThreads < nc) {
+    if (tid + NT < nc) {
         wiB = ids[(long long)cB * k + k - 1];
         dkB = dist[(long long)cB * k + k - 1];
         mB = tcm[cB];
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     };
     int4 e4[kMB];
 #pragma unroll
-    for (int u = 0; u < kMB; ++u) e4[u] = load_item(tid + u * kTCThreads);
+    for (int u = 0; u < kMB; ++u) e4[u] = load_item(tid + u * NT);
     auto insert = [&](int32_t c, int i) {
         const uint32_t b = bloom_bit(c);
         atomicOr(bm + (b >> 5), 1u << (b & 31));
@@ -784,7 +786,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         }
     };
     if (tid < nc) insert(cA, tid);
-    if (tid + kTCThreads < nc) insert(cB, tid + kTCThreads);
+    if (tid + NT < nc) insert(cB, tid + NT);
     __syncthreads();
     auto put_meta = [&](int i, int32_t c, int32_t wi, float dk, float4 m, float inv) {
         thr[i] = wi < 0 ? kEmptyKey : mkkey(dk, wi);
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         meta[i] = m;
     };
     if (tid < nc) put_meta(tid, cA, wiA, dkA, mA, invA);
-    if (tid + kTCThreads < nc) put_meta(tid + kTCThreads, cB, wiB, dkB, mB, invB);
+    if (tid + NT < nc) put_meta(tid + NT, cB, wiB, dkB, mB, invB);
     // membership bits: mask(i, j) = C[j] in N(C[i])
     auto member = [&](int i, int32_t e) {
         if (e < 0) return;
@@ -814,11 +816,11 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         }
     };
 #pragma unroll 1
-    for (int idx = tid; idx < mtotal; idx += kTCThreads) {
+    for (int idx = tid; idx < mtotal; idx += NT) {
         const int4 cur = e4[0];
 #pragma unroll
         for (int u = 0; u + 1 < kMB; ++u) e4[u] = e4[u + 1];
-        e4[kMB - 1] = load_item(idx + kMB * kTCThreads);
+        e4[kMB - 1] = load_item(idx + kMB * NT);
         const int i = idx / per;
 #pragma unroll 1
         for (int q = 0; q < (vec ? 4 : 1); ++q) member(i, q == 0 ? cur.x : q == 1 ? cur.y : q == 2 ? cur.z : cur.w);
@@ -856,7 +858,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     // evaluates the pairs {c, r} with c < min(r, nn) from its own TMEM row; pairs with
     // j >= 128 (no TMEM lane) are evaluated by lane i at columns 128 .. nc - 1. Every pair is
     // evaluated once and no warp reads more than nn + (nc - 128) columns.
-    const int r = 32 * warp + lane;
+    const int r = 32 * (warp & 3) + lane;   // TMEM lane quarter warp % 4
     const bool r_ok = r < nc;
     const float4 fr = r_ok ? colf[r] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float Pr = fr.x, tdr = fr.y;
@@ -900,24 +902,25 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         if (lo <= cc.y && !((mask[c * W + (r >> 5)] >> (r & 31)) & 1u)) dm |= 2u;
         return dm;
     };
-    // one shared-memory atomic per warp and column for the survivors of that column
+    // survivors go to this warp's own segment of the queue (a register count, no atomics)
+    const int seg = kTCQueue / NW;
+    uint32_t* wq = queue + warp * seg;
+    int qn = 0;
     auto append = [&](int c, unsigned dm) {
         const unsigned vote = __ballot_sync(kFull, dm != 0u);
-        if (vote == 0u) return;
-        const int leader = __ffs(vote) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(misc + 1, __popc(vote));
-        base = __shfl_sync(kFull, base, leader);
         if (dm) {
-            const int slot = base + __popc(vote & lt);
-            if (slot < kTCQueue) queue[slot] = (uint32_t)r | ((uint32_t)c << 10) | (dm << 20);
+            const int slot = qn + __popc(vote & lt);
+            if (slot < seg) wq[slot] = (uint32_t)r | ((uint32_t)c << 10) | (dm << 20);
         }
+        qn += __popc(vote);
     };
     if (ok_mma) {
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-        const int cend = min(nn, 32 * warp + 31);   // c < r <= 32 w + 31
+        // the NW / 4 warps of a lane quarter take every (NW / 4)-th group of four columns
+        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        const int cstep = 4 * (NW / 4);
+        const int cend = min(nn, 32 * (warp & 3) + 31);   // c < r <= 32 (w % 4) + 31
 #pragma unroll 1
-        for (int c0 = 0; c0 < cend; c0 += 4) {
+        for (int c0 = 4 * (warp >> 2); c0 < cend; c0 += cstep) {
             float dv[4];
             tc::tmem_ld4(trow + (uint32_t)c0, dv);
 #pragma unroll
@@ -926,9 +929,9 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
                 if (c < cend) append(c, (r_ok && c < r) ? test(c, dv[t4]) : 0u);
             }
         }
-        if (LARGE && nc > 128 && 32 * warp < nn) {
+        if (LARGE && nc > 128 && 32 * (warp & 3) < nn) {
 #pragma unroll 1
-            for (int c0 = 128; c0 < nc; c0 += 4) {
+            for (int c0 = 128 + 4 * (warp >> 2); c0 < nc; c0 += cstep) {
                 float dv[4];
                 tc::tmem_ld4(trow + (uint32_t)c0, dv);
 #pragma unroll
@@ -939,12 +942,13 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             }
         }
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);   // free TMEM for the next CTA on this SM
+    if (qn > seg && lane == 0) {   // survivors dropped: this vertex is redone after the merge
+        pending[v] = 1;
+        atomicOr(status, kErrOverflow);
+    }
 
-    // Exact re-rank of the survivors with the canonical FP32 distance, kStep pairs per warp
-    // step; lane t < U proposes for pair t.
+    // Exact re-rank of this warp's survivors (no wait for the other warps) with the canonical
+    // FP32 distance, kStep pairs per step; lane t < U proposes for pair t.
     //  - byte rows (integer coordinates in [0, 255], d <= 128, d % 16 == 0): every partial sum
     //    of the canonical FP32 value is an integer below 2^24, so it equals the exact integer
     //    |a|^2 + |b|^2 - 2 a.b; lanes take 16 bytes, 32 / lanes-per-row pairs per warp load,
@@ -952,8 +956,8 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
     //  - otherwise the canonical FP32 additions, from the staged tile when every staged row is
     //    exact (the same values), else from the FP32 rows in global memory.
     constexpr int kStep = BYTES ? 16 : 8;
-    const int nq = min(misc[1], kTCQueue);
-    for (int q0 = warp * kStep; q0 < nq; q0 += (kTCThreads / 32) * kStep) {
+    const int nq = min(qn, seg);
+    for (int q0 = 0; q0 < nq; q0 += kStep) {
         const int U = min(kStep, nq - q0);
         float sc = 0.f;
         if constexpr (BYTES) {
@@ -969,7 +973,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
                 xa[t] = make_uint4(0u, 0u, 0u, 0u);
                 xb[t] = xa[t];
                 if (pr < U && has) {
-                    const uint32_t e = queue[q0 + pr];
+                    const uint32_t e = wq[q0 + pr];
                     xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
                     xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
                 }
@@ -989,7 +993,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             }
             if (lane < U) {
                 if (METRIC == FGIM_L2SQ) {
-                    const uint32_t e = queue[q0 + lane];
+                    const uint32_t e = wq[q0 + lane];
                     const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
                     const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
                     sc = (float)(na + nb - 2u * mine);
@@ -1001,7 +1005,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             int ra[8], rb[8];
 #pragma unroll
             for (int t8 = 0; t8 < 8; ++t8) {
-                const uint32_t e = queue[q0 + min(t8, U - 1)];
+                const uint32_t e = wq[q0 + min(t8, U - 1)];
                 ra[t8] = (int)(e & 1023u);
                 rb[t8] = (int)((e >> 10) & 1023u);
             }
@@ -1058,7 +1062,7 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
         uint64_t key[2] = {kEmptyKey, kEmptyKey};
         int32_t tgt[2] = {-1, -1};
         if (lane < U) {
-            const uint32_t e = queue[q0 + lane];
+            const uint32_t e = wq[q0 + lane];
             const int ia = (int)(e & 1023u), jb = (int)((e >> 10) & 1023u);
             const unsigned dm = (e >> 20) & 3u;
             const float dd =
@@ -1100,18 +1104,16 @@ __global__ void __launch_bounds__(kTCThreads, 4) k_join_tc(
             }
         }
     }
-    if (misc[1] > kTCQueue && tid == 0) {   // survivors dropped: this vertex is redone after the merge
-        pending[v] = 1;
-        atomicOr(status, kErrOverflow);
-    }
+    tc::fence_before_sync();
     __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
     const int nb = min(misc[0], kTCPropBuf);
     unsigned long long* base_s = reinterpret_cast<unsigned long long*>(misc + 4);
     if (tid == 0 && nb > 0) *base_s = atomicAdd(prop_count, (unsigned long long)nb);
     __syncthreads();
     if (nb > 0) {
         const unsigned long long base = *base_s;
-        for (int q = tid; q < nb; q += kTCThreads) {
+        for (int q = tid; q < nb; q += NT) {
             const unsigned long long pos = base + q;
             if (pos < (unsigned long long)prop_cap) {
                 prop_tgt[pos] = pb_tgt[q];
@@ -1221,7 +1223,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         e = cudaFuncSetAttribute(k_join_tc<MT, BY, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
-        k_join_tc<MT, BY, LG><<<(unsigned)count, kTCThreads, smem, s>>>(                                          \
+        k_join_tc<MT, BY, LG><<<(unsigned)count, (BY) ? 256 : kTCThreads, smem, s>>>(                               \
             t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, status);                                                                                       \

@@ -419,7 +419,7 @@ static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stat
 static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knng* g, const int32_t* T, int32_t* e_ids,
                   float* e_dist, int32_t* e_cnt) {
     const float alpha2 = (float)((double)p->alpha * (double)p->alpha);
-    ck(launch_prune(P.X, P.inv, P.N, P.d, P.metric, *g, T, p->R, alpha2, e_ids, e_dist, e_cnt, c.status, c.s));
+    ck(launch_prune(P.X, P.X8, P.inv, P.N, P.d, P.metric, *g, T, p->R, alpha2, e_ids, e_dist, e_cnt, c.status, c.s));
 }
 
 static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,

@@ -99,9 +99,9 @@ cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cuda
 cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s);
 
 // ---- k_prune.cu
-cudaError_t launch_prune(const float* X, const float* inv_norm, long long N, int d, int metric, const fgim_knng& g,
-                         const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
-                         int* status, cudaStream_t s);
+cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
+                         const fgim_knng& g, const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist,
+                         int32_t* e_cnt, int* status, cudaStream_t s);
 struct ReverseBuffers {
     int32_t* cnt;
     long long* off;

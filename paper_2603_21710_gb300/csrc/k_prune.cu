@@ -132,11 +132,164 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
     if (lane == 0) e_cnt[u] = nk;
 }
 
-cudaError_t launch_prune(const float* X, const float* inv_norm, long long N, int d, int metric, const fgim_knng& g,
-                         const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
-                         int* status, cudaStream_t s) {
+__host__ __device__ inline size_t prune_bytes_per_warp(int k, int d) {
+    return ((size_t)k * (d + 16) + (size_t)k * 16 + 15) & ~(size_t)15;
+}
+
+// Byte rows (every coordinate an integer in [0, 255], d <= 128, d % 16 == 0): the canonical
+// FP32 distance of two rows is then an exact integer (every partial sum is an integer below
+// 2^24), computed here directly: |a|^2 + |b|^2 - 2 a.b with four-way byte dot products. No
+// filter or re-check is needed. The candidate rows of u are staged as bytes (stride d + 16,
+// which spreads the lanes' rows over the banks), with their squared norms.
+template <int METRIC>
+__global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__ X8, const float* __restrict__ inv_norm,
+                                                     long long N, int d, int k, const int32_t* __restrict__ ids,
+                                                     const float* __restrict__ dist, const int32_t* __restrict__ T,
+                                                     int R, float alpha2, int32_t* __restrict__ e_ids,
+                                                     float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
+                                                     int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (u >= N) return;
+    const int stride = d + 16;
+    const size_t per_warp = prune_bytes_per_warp(k, d);
+    unsigned char* base = smem + per_warp * warp;
+    unsigned char* rows = base;
+    uint32_t* n2 = reinterpret_cast<uint32_t*>(base + (size_t)k * stride);
+    float* invs = reinterpret_cast<float*>(n2 + k);
+    int32_t* cidv = reinterpret_cast<int32_t*>(invs + k);
+    int32_t* kept = cidv + k;
+
+    // valid prefix of list(u), and its T and delta(u, .) held two per lane
+    int nv = 0;
+    for (int s0 = 0; s0 < k; s0 += 32) {
+        const int s = s0 + lane;
+        int32_t id = s < k ? ids[u * k + s] : -1;
+        if (id >= N) {
+            atomicOr(status, kErrBounds);
+            id = -1;
+        }
+        if (s < k) cidv[s] = id;
+        nv += __popc(__ballot_sync(kFull, id >= 0));
+    }
+    __syncwarp();
+    // stage the rows: 32 / lpr rows per warp load, lanes of a row take 16 bytes each
+    const int lpr = byte_lanes(d);
+    const int rpi = 32 / lpr;
+    const int sub = lane / lpr, part = lane & (lpr - 1);
+    const bool has = part < (d >> 4);
+    for (int r0 = 0; r0 < nv; r0 += 4 * rpi) {
+        uint4 w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * rpi + sub;
+            w[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (r < nv && has) w[q] = *reinterpret_cast<const uint4*>(X8 + (long long)cidv[r] * d + 16 * part);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * rpi + sub;
+            uint32_t sq = __dp4a(w[q].x, w[q].x, 0u);
+            sq = __dp4a(w[q].y, w[q].y, sq);
+            sq = __dp4a(w[q].z, w[q].z, sq);
+            sq = __dp4a(w[q].w, w[q].w, sq);
+            for (int o = 1; o < lpr; o <<= 1) sq += __shfl_xor_sync(kFull, sq, o);
+            if (r < nv) {
+                if (has) *reinterpret_cast<uint4*>(rows + (size_t)r * stride + 16 * part) = w[q];
+                if (part == 0) n2[r] = sq;
+            }
+        }
+    }
+    if (METRIC == FGIM_COSINE)
+        for (int r = lane; r < nv; r += 32) invs[r] = inv_norm[cidv[r]];
+    // T(v) and delta(u, v) of the candidates, two per lane
+    int tA = 0, tB = 0;
+    float dA = 0.f, dB = 0.f;
+    if (lane < nv) {
+        tA = T[cidv[lane]];
+        dA = dist[u * k + lane];
+    }
+    if (lane + 32 < nv) {
+        tB = T[cidv[lane + 32]];
+        dB = dist[u * k + lane + 32];
+    }
+    __syncwarp();
+    const int c16n = d >> 4;
+    int nk = 0;
+    for (int t = 0; t < nv && nk < R; ++t) {
+        const int tv = __shfl_sync(kFull, t < 32 ? tA : tB, t & 31);
+        bool keep = tv == 1;
+        if (!keep) {
+            const float duv = __shfl_sync(kFull, t < 32 ? dA : dB, t & 31);
+            const unsigned char* rv = rows + (size_t)t * stride;
+            bool occ = false;
+            for (int s0 = 0; s0 < nk; s0 += 32) {
+                const int s = s0 + lane;
+                if (s < nk) {
+                    const int wi = kept[s];
+                    const unsigned char* rw = rows + (size_t)wi * stride;
+                    uint32_t dot = 0u;
+                    for (int c = 0; c < c16n; ++c) {
+                        const uint4 a = *reinterpret_cast<const uint4*>(rw + 16 * c);
+                        const uint4 b = *reinterpret_cast<const uint4*>(rv + 16 * c);
+                        dot = __dp4a(a.x, b.x, dot);
+                        dot = __dp4a(a.y, b.y, dot);
+                        dot = __dp4a(a.z, b.z, dot);
+                        dot = __dp4a(a.w, b.w, dot);
+                    }
+                    float dc;
+                    if (METRIC == FGIM_L2SQ) dc = (float)(n2[wi] + n2[t] - 2u * dot);
+                    else if (METRIC == FGIM_IP) dc = delta_finish<FGIM_IP>((float)dot, 1.f);
+                    else dc = delta_finish<FGIM_COSINE>((float)dot, __fmul_rn(invs[wi], invs[t]));
+                    occ |= !(duv < __fmul_rn(alpha2, dc));
+                }
+            }
+            keep = !__any_sync(kFull, occ);
+        }
+        if (keep) {
+            if (lane == 0) kept[nk] = t;
+            ++nk;
+            __syncwarp();
+        }
+    }
+    for (int s = lane; s < R; s += 32) {
+        if (s < nk) {
+            e_ids[u * R + s] = cidv[kept[s]];
+            e_dist[u * R + s] = dist[u * k + kept[s]];
+        } else {
+            e_ids[u * R + s] = -1;
+            e_dist[u * R + s] = __int_as_float(0x7f800000);
+        }
+    }
+    if (lane == 0) e_cnt[u] = nk;
+}
+
+cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
+                         const fgim_knng& g, const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist,
+                         int32_t* e_cnt, int* status, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     const int k = g.k;
+    if (X8 && byte_rows_ok(d) && k <= 64) {
+        const int wpb = 4;
+        const size_t smem = prune_bytes_per_warp(k, d) * wpb;
+        cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_PB(MT)                                                                                        \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_prune_bytes<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (e != cudaSuccess) break;                                                                              \
+        LaunchScope ls("k_prune", s);                                                                             \
+        k_prune_bytes<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X8, inv_norm, N, d, k, g.ids, g.dist, T, \
+                                                                          R, alpha2, e_ids, e_dist, e_cnt, status);\
+        e = cudaGetLastError();                                                                                   \
+    } while (0)
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_PB(FGIM_L2SQ);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_PB(FGIM_IP);
+        else FGIM_LAUNCH_PB(FGIM_COSINE);
+#undef FGIM_LAUNCH_PB
+        return e;
+    }
     const int wpb = 2;
     const size_t staged = ((size_t)k * (d + 4) * 4 + (size_t)k * 12 + 16 + 15) & ~(size_t)15;
     const size_t unstaged = ((size_t)k * 12 + 16 + 15) & ~(size_t)15;

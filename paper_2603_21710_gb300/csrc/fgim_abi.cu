@@ -402,15 +402,18 @@ static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stat
     const long long nz = c.read_ll(off + N);
     if (st) st->zero_indegree = nz;
     if (nz == 0) return;
-    int32_t* owner = c.alloc<int32_t>(N);
-    long long* cursor = c.alloc<long long>(2);   // [0] start, [1] first failing index
-    ck(cudaMemsetAsync(cursor, 0, sizeof(long long), c.s));
-    long long start = 0;
-    for (long long round = 0; start < nz; ++round) {
-        need(round <= nz, FGIM_EINTERNAL, "indegree repair made no progress");
-        ck(launch_repair_round(*g, T, zeros, off + N, cursor, nz - start, owner, cursor + 1, c.ctr + 3, c.status,
-                               c.s));
-        const long long next = c.read_ll(cursor);
+    unsigned long long* owner = c.alloc<unsigned long long>(N);
+    long long* ff = c.alloc<long long>(nz + 2);   // first uncommitted index after each round (one round commits >= 1)
+    ck(cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * N, c.s));
+    ck(cudaMemsetAsync(ff, 0, sizeof(long long), c.s));
+    long long start = 0, rho = 1;
+    constexpr int kBatch = 16;   // rounds between host reads of the progress
+    while (start < nz) {
+        need(rho <= nz, FGIM_EINTERNAL, "indegree repair made no progress");
+        const int rounds = (int)std::min<long long>(kBatch, nz + 1 - rho);
+        ck(launch_repair_rounds(*g, T, zeros, nz, rho, rounds, ff, owner, c.ctr + 3, c.status, c.s));
+        rho += rounds;
+        const long long next = c.read_ll(ff + (rho - 1));
         need(next > start, FGIM_EINTERNAL, "indegree repair made no progress");
         start = next;
     }
@@ -437,24 +440,14 @@ static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, con
 // BFS from the entry; returns the number of reached vertices
 static long long bfs(Ctx& c, const fgim_graph* g, int32_t* visited, int32_t* fa, int32_t* fb, int32_t* counts) {
     const long long N = g->n;
-    ck(launch_bfs_init(visited, N, fa, counts + 0, g->entry, c.s));
-    long long reached = 1;
-    long long frontier = 1;
-    int32_t* fin = fa;
-    int32_t* fout = fb;
-    int cur = 0;
-    for (long long level = 1; level <= N; ++level) {
-        ck(cudaMemsetAsync(counts + (cur ^ 1), 0, sizeof(int32_t), c.s));
-        ck(launch_bfs_step(g->ids, g->R, N, visited, fin, counts + cur, fout, counts + (cur ^ 1), (int32_t)(level + 1),
-                           frontier, c.s));
-        const int nf = c.read_i32(counts + (cur ^ 1));
-        if (nf == 0) break;
-        reached += nf;
-        frontier = nf;
-        std::swap(fin, fout);
-        cur ^= 1;
+    ck(launch_bfs_init(visited, N, fa, counts, g->entry, c.s));
+    constexpr int kBatch = 8;   // levels between host reads of the frontier size
+    for (int level = 1; level <= N; level += kBatch) {
+        ck(launch_bfs_levels(g->ids, g->R, N, visited, fa, fb, counts, level, kBatch, c.s));
+        const int last = level + kBatch - 1;   // its output frontier size is counts[(last + 1) % 3]
+        if (c.read_i32(counts + (last + 1) % 3) == 0) break;
     }
-    return reached;
+    return c.read_ll(reinterpret_cast<const long long*>(counts + 4));
 }
 
 static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph* g, fgim_stats* st) {
@@ -464,7 +457,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     int32_t* visited = c.alloc<int32_t>(N);
     int32_t* fa = c.alloc<int32_t>(N);
     int32_t* fb = c.alloc<int32_t>(N);
-    int32_t* counts = c.alloc<int32_t>(4);
+    int32_t* counts = c.alloc<int32_t>(8);   // BFS state: three frontier sizes, reached (int64 at [4])
     int32_t* label = c.alloc<int32_t>(N);
     int32_t* flag = c.alloc<int32_t>(N);
     int32_t* reps = c.alloc<int32_t>(N);
@@ -473,8 +466,8 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
     int32_t* changed = c.alloc<int32_t>(1);
     int32_t* npar = c.alloc<int32_t>(N);
-    int32_t* owner = c.alloc<int32_t>(N);
-    long long* cursor = c.alloc<long long>(2);
+    unsigned long long* owner = c.alloc<unsigned long long>(N);
+    long long* ff = c.alloc<long long>(N + 2);   // first uncommitted index after each round (one round commits >= 1)
     int32_t* cand = nullptr;
     float* cdist = nullptr;
     long long cand_cap = 0;
@@ -500,13 +493,18 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         ck(launch_search(P.X, P.X8, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
                          cand, cdist, c.ctr + 0, c.status, c.s));
         ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
-        ck(cudaMemsetAsync(cursor, 0, sizeof(long long), c.s));
-        long long start = 0;
-        for (long long it = 0; start < nr; ++it) {
-            need(it <= nr, FGIM_EINTERNAL, "reachability fix made no progress");
-            ck(launch_reach_round(g->ids, g->dist, g->deg, visited, npar, R, N, reps, off + N, cursor, nr - start, cand,
-                                  cdist, beam, owner, cursor + 1, c.ctr + 4, c.s));
-            const long long next = c.read_ll(cursor);
+        // rounds run in batches between host reads of the progress; ff[0] = 0 starts round 1
+        ck(cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * N, c.s));
+        ck(cudaMemsetAsync(ff, 0, sizeof(long long), c.s));
+        long long start = 0, rho = 1;
+        constexpr int kBatch = 16;
+        while (start < nr) {
+            need(rho <= nr, FGIM_EINTERNAL, "reachability fix made no progress");
+            const int rounds = (int)std::min<long long>(kBatch, nr + 1 - rho);
+            ck(launch_reach_rounds(g->ids, g->dist, g->deg, visited, npar, R, reps, nr, rho, rounds, ff, cand, cdist,
+                                   beam, owner, c.ctr + 4, c.s));
+            rho += rounds;
+            const long long next = c.read_ll(ff + (rho - 1));
             need(next > start, FGIM_EINTERNAL, "reachability fix made no progress");
             start = next;
         }

@@ -92,9 +92,12 @@ cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, 
 cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
                             cudaStream_t s);
-cudaError_t launch_repair_round(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
-                                long long* start, long long pending, int32_t* owner, long long* first_fail,
-                                unsigned long long* repaired, int* status, cudaStream_t s);
+// rounds rho0 .. rho0 + rounds - 1 of the Alg. 4 repair; ff[rho0 - 1] holds the first pending
+// index, ff[rho] the first index after round rho
+constexpr int kRepairWindow = 2048;
+cudaError_t launch_repair_rounds(fgim_knng& g, int32_t* T, const int32_t* zeros, long long nz, long long rho0,
+                                 int rounds, long long* ff, unsigned long long* owner, unsigned long long* repaired,
+                                 int* status, cudaStream_t s);
 cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cudaStream_t s);
 cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s);
 
@@ -114,11 +117,11 @@ cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, cons
                                   ReverseBuffers& b, int32_t* out_ids, float* out_dist, int32_t* out_deg,
                                   cudaStream_t s);
 // reachability fix helpers
-cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry,
+cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* st, int entry,
                             cudaStream_t s);
-cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
-                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, int32_t next_level,
-                            long long max_frontier, cudaStream_t s);
+// BFS levels level0 .. level0 + levels - 1 (state st: 8 ints, see k_prune.cu; level 1 reads fa)
+cudaError_t launch_bfs_levels(const int32_t* graph, int R, long long N, int32_t* visited, int32_t* fa, int32_t* fb,
+                              int32_t* st, int level0, int levels, cudaStream_t s);
 cudaError_t launch_bfs_parents(const int32_t* graph, int R, long long N, const int32_t* level, int32_t* npar,
                                cudaStream_t s);
 cudaError_t launch_cc_init(const int32_t* visited, long long N, int32_t* label, cudaStream_t s);
@@ -126,9 +129,12 @@ cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32
                            int32_t* changed, cudaStream_t s);
 cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
                              cudaStream_t s);
-cudaError_t launch_reach_round(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
-                               long long N, const int32_t* reps, const long long* nreps, long long* start,
-                               long long pending, const int32_t* cand, const float* cdist, int beam, int32_t* owner,
-                               long long* first_fail, unsigned long long* attached, cudaStream_t s);
+// kReachRounds rounds of the representative attachment (rounds rho0 .. rho0 + rounds - 1);
+// ff[rho0 - 1] holds the first pending index, ff[rho] the first index after round rho
+constexpr int kReachWindow = 2048;
+cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar,
+                                int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
+                                const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
+                                unsigned long long* attached, cudaStream_t s);
 
 }  // namespace fgim

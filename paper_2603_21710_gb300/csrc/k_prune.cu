@@ -12,6 +12,8 @@
 //
 // Connectivity enhancement builds the reverse lists of the pruned snapshot E' by a
 // counting sort and merges them into E'(u), keeping the R smallest (delta, id).
+#include <algorithm>
+
 #include "fgim_launch.h"
 
 namespace fgim {
@@ -396,43 +398,69 @@ cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, cons
 }
 
 // ---------------------------------------------------------------------------- reachability fix
-__global__ void k_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry) {
+// BFS state: st[0..2] frontier sizes (level L reads st[L % 3], writes st[(L + 1) % 3] and
+// clears st[(L + 2) % 3] for the level after), st[4..5] the number of reached vertices (int64)
+__global__ void k_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* st, int entry) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) visited[i] = (i == entry) ? 1 : 0;
     if (i == 0) {
         frontier[0] = entry;
-        *fcount = 1;
+        st[1] = 1;   // level 1 reads st[1]
+        st[2] = 0;
+        st[0] = 0;
+        *reinterpret_cast<long long*>(st + 4) = 1;
     }
 }
 
-cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* fcount, int entry,
+cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* st, int entry,
                             cudaStream_t s) {
     LaunchScope ls("k_bfs_init", s);
-    k_bfs_init<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, frontier, fcount, entry);
+    k_bfs_init<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, frontier, st, entry);
     return cudaGetLastError();
 }
 
-// one level: thread per (frontier vertex, neighbour slot); visited[y] = BFS level (entry = 1)
+// one level L (grid-stride over (frontier vertex, neighbour slot)); visited[y] = BFS level
+// (entry = 1); a level whose frontier is empty does nothing, so several levels can be
+// queued without reading the frontier size on the host
 __global__ void k_bfs_step(const int32_t* __restrict__ graph, int R, long long N, int32_t* __restrict__ visited,
-                           const int32_t* __restrict__ fin, const int32_t* __restrict__ fin_count,
-                           int32_t* __restrict__ fout, int32_t* __restrict__ fout_count, int32_t next_level) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nf = *fin_count;
-    if (i >= nf * R) return;
-    const int32_t x = fin[i / R];
-    const int32_t y = graph[(long long)x * R + (i % R)];
-    if (y < 0 || y >= N) return;
-    if (visited[y] == 0 && atomicCAS(visited + y, 0, next_level) == 0) fout[atomicAdd(fout_count, 1)] = y;
+                           const int32_t* __restrict__ fin, int32_t* __restrict__ fout, int32_t* __restrict__ st,
+                           int level) {
+    const long long nf = st[level % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[(level + 2) % 3] = 0;
+    const int32_t next_level = level + 1;
+    int added = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nf * R;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int32_t x = fin[i / R];
+        const int32_t y = graph[(long long)x * R + (i % R)];
+        if (y < 0 || y >= N) continue;
+        if (visited[y] == 0 && atomicCAS(visited + y, 0, next_level) == 0) {
+            fout[atomicAdd(st + (level + 1) % 3, 1)] = y;
+            ++added;
+        }
+    }
+    const unsigned m = __ballot_sync(kFull, added > 0);
+    int sum = added;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(reinterpret_cast<unsigned long long*>(st + 4), (unsigned long long)sum);
 }
 
-cudaError_t launch_bfs_step(const int32_t* graph, int R, long long N, int32_t* visited, const int32_t* fin,
-                            const int32_t* fin_count, int32_t* fout, int32_t* fout_count, int32_t next_level,
-                            long long max_frontier, cudaStream_t s) {
-    // grid sized for the largest frontier the host has seen; threads beyond the live frontier exit
-    LaunchScope ls("k_bfs_step", s);
-    k_bfs_step<<<(unsigned)cdivl(max_frontier * R, 256), 256, 0, s>>>(graph, R, N, visited, fin, fin_count, fout,
-                                                                        fout_count, next_level);
-    return cudaGetLastError();
+cudaError_t launch_bfs_levels(const int32_t* graph, int R, long long N, int32_t* visited, int32_t* fa, int32_t* fb,
+                              int32_t* st, int level0, int levels, cudaStream_t s) {
+    const long long work = N * (long long)R;
+    const unsigned blocks = (unsigned)std::min<long long>(cdivl(work, 256), 152LL * 16);
+    for (int q = 0; q < levels; ++q) {
+        const int level = level0 + q;
+        // level L reads the frontier written by level L - 1: fa for odd L, fb for even L
+        const int32_t* fin = (level & 1) ? fa : fb;
+        int32_t* fout = (level & 1) ? fb : fa;
+        LaunchScope ls("k_bfs_step", s);
+        k_bfs_step<<<blocks, 256, 0, s>>>(graph, R, N, visited, fin, fout, st, level);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // number of BFS parents of every reached vertex: in-neighbours at a smaller level
@@ -510,27 +538,37 @@ cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long 
 // farthest such y replaced by x. Reads that other actions cannot change are not reserved:
 // a full list stays full (degrees only grow) and a neighbour that is not replaceable stays
 // so (parent counts only shrink). Only p (its list and degree) and y (its parent count)
-// are reserved with atomicMin of the representative's index; the longest ascending prefix
-// holding its reservations is committed, the rest recomputed in the next round.
+// are reserved with atomicMin of a tag ordered by (round, representative index); the
+// longest ascending prefix of the round's window holding its reservations is committed,
+// the rest recomputed in the next round.
+//
+// Round rho works on the window [ff[rho - 1], min(ff[rho - 1] + W, nr)) and leaves in ff[rho]
+// the first index it did not commit (the next round's start). Tags of later rounds are
+// smaller than those of earlier ones, so owner needs no reset between rounds.
 enum { kRPlan = 0, kRCheck = 1, kRCommit = 2 };
+
+__device__ __forceinline__ unsigned long long reach_tag(long long rho, long long r) {
+    return ((unsigned long long)(0xFFFFFFFFu - (uint32_t)rho) << 32) | (unsigned long long)(uint32_t)r;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph, float* __restrict__ gdist,
                                                      int32_t* __restrict__ deg, const int32_t* __restrict__ level,
                                                      int32_t* __restrict__ npar, int R,
-                                                     const int32_t* __restrict__ reps,
-                                                     const long long* __restrict__ nreps,
-                                                     const long long* __restrict__ start,
+                                                     const int32_t* __restrict__ reps, long long nr, long long rho,
+                                                     long long window, long long* __restrict__ ff,
                                                      const int32_t* __restrict__ cand,
                                                      const float* __restrict__ cdist, int beam,
-                                                     int32_t* __restrict__ owner, long long* __restrict__ first_fail,
+                                                     unsigned long long* __restrict__ owner,
                                                      unsigned long long* attached) {
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
-    const long long r = *start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    const long long nr = *nreps;
-    if (r >= nr) return;
-    if (MODE == kRCommit && r >= *first_fail) return;
+    const long long start = ff[rho - 1];
+    const long long wend = start + window < nr ? start + window : nr;
+    if (MODE == kRPlan && blockIdx.x == 0 && threadIdx.x == 0) ff[rho] = wend;
+    const long long r = start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= wend) return;
+    if (MODE == kRCommit && r >= ff[rho]) return;
     const int32_t x = reps[r];
     const int32_t* cr = cand + r * beam;
     int p = -1, pos = -1, t_sel = -1;
@@ -570,7 +608,7 @@ __global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph
     }
     if (p < 0) return;
     const int32_t victim = pos < deg[p] ? graph[(long long)p * R + pos] : -1;
-    const int32_t tag = (int32_t)(r & 0x7fffffff);
+    const unsigned long long tag = reach_tag(rho, r);
     if (MODE == kRPlan) {
         if (lane == 0) {
             atomicMin(owner + p, tag);
@@ -580,7 +618,7 @@ __global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph
     }
     if (MODE == kRCheck) {
         if (lane == 0 && (owner[p] != tag || (victim >= 0 && owner[victim] != tag)))
-            atomicMin((unsigned long long*)first_fail, (unsigned long long)r);
+            atomicMin((unsigned long long*)(ff + rho), (unsigned long long)r);
         return;
     }
     if (lane == 0) {
@@ -606,39 +644,28 @@ __global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph
     }
 }
 
-__global__ void k_round_advance(long long* start, const long long* first_fail) { *start = *first_fail; }
-
-cudaError_t launch_reach_round(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar, int R,
-                               long long N, const int32_t* reps, const long long* nreps, long long* start,
-                               long long pending, const int32_t* cand, const float* cdist, int beam, int32_t* owner,
-                               long long* first_fail, unsigned long long* attached, cudaStream_t s) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(owner, 0x7f, sizeof(int32_t) * N, s)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(first_fail, nreps, sizeof(long long), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return e;
+cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar,
+                                int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
+                                const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
+                                unsigned long long* attached, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     const int wpb = 4;
-    const unsigned blocks = (unsigned)cdivl(pending, wpb);
-    {
+    const long long window = kReachWindow;
+    const unsigned blocks = (unsigned)cdivl(window, wpb);
+    for (int q = 0; q < rounds; ++q) {
+        const long long rho = rho0 + q;
         LaunchScope ls("k_reach_round", s);
-        k_reach_round<kRPlan><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start, cand,
-                                                          cdist, beam, owner, first_fail, attached);
+        k_reach_round<kRPlan><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
+                                                          ff, cand, cdist, beam, owner, attached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_reach_round<kRCheck><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
+                                                           ff, cand, cdist, beam, owner, attached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_reach_round<kRCommit><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
+                                                            ff, cand, cdist, beam, owner, attached);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    {
-        LaunchScope ls("k_reach_round", s);
-        k_reach_round<kRCheck><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start, cand,
-                                                           cdist, beam, owner, first_fail, attached);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    {
-        LaunchScope ls("k_reach_round", s);
-        k_reach_round<kRCommit><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nreps, start,
-                                                            cand, cdist, beam, owner, first_fail, attached);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    LaunchScope ls("k_round_advance", s);
-    k_round_advance<<<1, 1, 0, s>>>(start, first_fail);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace fgim

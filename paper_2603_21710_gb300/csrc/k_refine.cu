@@ -1392,21 +1392,30 @@ cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, c
 // reservations, so every round commits at least one action.
 enum { kPlan = 0, kCheck = 1, kCommit = 2 };
 
+// Round rho works on the window [ff[rho - 1], min(ff[rho - 1] + W, nz)) and leaves in ff[rho]
+// the first index it did not commit (the next round's start). Reservations carry a tag
+// ordered by (round, index) with later rounds smaller, so owner needs no reset.
+__device__ __forceinline__ unsigned long long round_tag(long long rho, long long i) {
+    return ((unsigned long long)(0xFFFFFFFFu - (uint32_t)rho) << 32) | (unsigned long long)(uint32_t)i;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(128) k_repair_round(int32_t* __restrict__ ids, float* __restrict__ dist,
                                                       uint8_t* __restrict__ flags, long long N, int k,
                                                       int32_t* __restrict__ T, const int32_t* __restrict__ zeros,
-                                                      const long long* __restrict__ nzeros,
-                                                      const long long* __restrict__ start,
-                                                      int32_t* __restrict__ owner, long long* __restrict__ first_fail,
+                                                      long long nz, long long rho, long long window,
+                                                      long long* __restrict__ ff,
+                                                      unsigned long long* __restrict__ owner,
                                                       unsigned long long* repaired, int* status) {
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
-    const long long i = *start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    const long long nz = *nzeros;
-    if (i >= nz) return;
-    if (MODE == kCommit && i >= *first_fail) return;
-    const int32_t tag = (int32_t)(i & 0x7fffffff);
+    const long long start = ff[rho - 1];
+    const long long wend = start + window < nz ? start + window : nz;
+    if (MODE == kPlan && blockIdx.x == 0 && threadIdx.x == 0) ff[rho] = wend;
+    const long long i = start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= wend) return;
+    if (MODE == kCommit && i >= ff[rho]) return;
+    const unsigned long long tag = round_tag(rho, i);
     bool ok = true;
     auto touch = [&](int32_t x) {
         if (MODE == kPlan) atomicMin(owner + x, tag);
@@ -1446,7 +1455,7 @@ __global__ void __launch_bounds__(128) k_repair_round(int32_t* __restrict__ ids,
         }
     }
     if (MODE == kCheck) {
-        if (__any_sync(kFull, !ok) && lane == 0) atomicMin((unsigned long long*)first_fail, (unsigned long long)i);
+        if (__any_sync(kFull, !ok) && lane == 0) atomicMin((unsigned long long*)(ff + rho), (unsigned long long)i);
         return;
     }
     if (MODE == kCommit && best >= 0 && lane == 0) {
@@ -1478,38 +1487,27 @@ __global__ void __launch_bounds__(128) k_repair_round(int32_t* __restrict__ ids,
     }
 }
 
-__global__ void k_repair_advance(long long* start, const long long* first_fail) { *start = *first_fail; }
-
-cudaError_t launch_repair_round(fgim_knng& g, int32_t* T, const int32_t* zeros, const long long* nzeros,
-                                long long* start, long long pending, int32_t* owner, long long* first_fail,
-                                unsigned long long* repaired, int* status, cudaStream_t s) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(owner, 0x7f, sizeof(int32_t) * g.n, s)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(first_fail, nzeros, sizeof(long long), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return e;
+cudaError_t launch_repair_rounds(fgim_knng& g, int32_t* T, const int32_t* zeros, long long nz, long long rho0,
+                                 int rounds, long long* ff, unsigned long long* owner, unsigned long long* repaired,
+                                 int* status, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     const int wpb = 4;
-    const unsigned blocks = (unsigned)cdivll(pending, wpb);
-    {
+    const long long window = kRepairWindow;
+    const unsigned blocks = (unsigned)cdivll(window, wpb);
+    for (int q = 0; q < rounds; ++q) {
+        const long long rho = rho0 + q;
         LaunchScope ls("k_repair_round", s);
-        k_repair_round<kPlan><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
-                                                          owner, first_fail, repaired, status);
+        k_repair_round<kPlan><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nz, rho, window,
+                                                          ff, owner, repaired, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_repair_round<kCheck><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nz, rho,
+                                                           window, ff, owner, repaired, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_repair_round<kCommit><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nz, rho,
+                                                            window, ff, owner, repaired, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    {
-        LaunchScope ls("k_repair_round", s);
-        k_repair_round<kCheck><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
-                                                           owner, first_fail, repaired, status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    {
-        LaunchScope ls("k_repair_round", s);
-        k_repair_round<kCommit><<<blocks, wpb * 32, 0, s>>>(g.ids, g.dist, g.flags, g.n, g.k, T, zeros, nzeros, start,
-                                                            owner, first_fail, repaired, status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    LaunchScope ls("k_repair_advance", s);
-    k_repair_advance<<<1, 1, 0, s>>>(start, first_fail);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace fgim

@@ -216,37 +216,51 @@ def run_reference(args):
 SM_COUNT, FP32_LANES = 152, 128
 
 
-def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w, graphs, cpu, peaks, stats):
-    """Algorithmic work of one launch of the dominant kernel / its mean event time."""
+def row_bytes(w) -> int:
+    """Bytes per coordinate the searches and the prune read: 1 when the data qualify for byte
+    rows (integers in [0, 255], d <= 128, d % 16 == 0), else 4."""
+    X = w.X
+    ok = w.d % 16 == 0 and w.d <= 128 and bool(np.all((X >= 0) & (X <= 255) & (X == np.round(X))))
+    return 1 if ok else 4
+
+
+def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w, graphs, cpu, peaks, stats, s_row):
+    """Algorithmic work of one launch of a kernel / its mean event time (the stage models of
+    the measurement plan: bytes a launch must move at least, flops it must do)."""
     N, d, k, M, R = w.N, w.d, w.k, w.M, w.R
     out = {"kernel": kernel, "per_launch_ms": per_launch_ms, "traffic": None}
+    hbm = dict(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), peak_kind="measured copy (hbm_gbs), of measured")
     if kernel == "k_cross_query" and cpu is not None:
         pq = cpu["stage_a_per_query"]
         nq = N * (w.h - 1)
         mean_deg = float(np.mean([(g[0] >= 0).sum(1).mean() for g in graphs]))
-        # per cross query: NDC vector rows + ids and `hops` adjacency rows; per vertex: its own
-        # row, its local candidates' rows, its adjacency row and the k-NNG row it writes
-        work = nq * (pq["ndc"] * (d * 4 + 4) + pq["hops"] * M * 4) + N * (d * 4 + mean_deg * d * 4 + M * 4 + k * 9)
-        out.update(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), peak_kind="measured copy (MEASURED_PEAKS hbm_gbs)",
-                   algorithmic_bytes=work)
+        # per cross query: NDC rows (s_row bytes per coordinate) + their ids and `hops`
+        # adjacency rows; per vertex: its own FP32 row, its local candidates' rows, its
+        # adjacency row and the k-NNG row it writes (NDC, hops: the oracle's counters)
+        work = nq * (pq["ndc"] * (d * s_row + 4) + pq["hops"] * M * 4) + N * (
+            d * 4 + mean_deg * d * s_row + M * 4 + k * 9)
+        out.update(hbm, algorithmic_bytes=work, row_bytes=s_row)
         out["achieved"] = work / (per_launch_ms * 1e-3) / 1e9
     elif kernel == "k_join":
-        # algorithmic flops: every cross-graph pair of C_n^2 U C_n x C_o, 3 flops per dimension
-        pairs_per_launch = stats["join_pairs"] / max(launches_per_step, 1)
-        work = pairs_per_launch * 3 * d
-        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-        peak = SM_COUNT * FP32_LANES * clk * 1.5 / 1e12
-        out.update(bound="alu", unit="TFLOP/s", peak=peak,
-                   peak_kind="derived: 152 SMs x 128 FP32 lanes x sm_max_mhz x 1.5 flop (FSUB+FFMA)",
-                   algorithmic_flops=work)
-        out["achieved"] = work / (per_launch_ms * 1e-3) / 1e12
+        # bytes: every vertex joined stages its candidates' BF16 rows and reads their lists,
+        # (|C_n| + |C_o|) (2 d + 4 k); flops: 2 d per cross-shard pair of C_n^2 U C_n x C_o
+        cands = stats.get("join_cands", 0) / max(launches_per_step, 1)
+        pairs = stats["join_pairs"] / max(launches_per_step, 1)
+        work = cands * (2 * d + 4 * k)
+        flops = pairs * 2 * d
+        out.update(hbm, algorithmic_bytes=work, algorithmic_flops=flops)
+        out["achieved"] = work / (per_launch_ms * 1e-3) / 1e9
+        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        out["tensor"] = {"achieved_tflops": flops / (per_launch_ms * 1e-3) / 1e12, "peak_tflops": bf16,
+                         "frac": (flops / (per_launch_ms * 1e-3) / 1e12) / bf16 if bf16 else None,
+                         "peak_kind": "cuBLAS bf16 sustained (bf16_tflops_sustained), of measured"}
     elif kernel == "k_prune":
-        # every vertex reads its k candidate rows and its list, writes R pruned entries
-        work = N * (k * d * 4 + k * 8 + R * 8 + 4)
-        out.update(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), peak_kind="measured copy", algorithmic_bytes=work)
+        # every vertex gathers its k candidate rows and reads its list, writes R pruned entries
+        work = N * (k * d * s_row + k * 8 + R * 8 + 4)
+        out.update(hbm, algorithmic_bytes=work, row_bytes=s_row)
         out["achieved"] = work / (per_launch_ms * 1e-3) / 1e9
     else:
-        out.update(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), achieved=None)
+        out.update(hbm, achieved=None)
     out["frac"] = out["achieved"] / out["peak"] if out.get("achieved") and out.get("peak") else None
     return out
 
@@ -296,6 +310,24 @@ def run_fgim(args):
     local_ms = sum(step_ms)
     total_ms = max_over_ranks(local_ms, ws, dev)
     stats = out["stats"]
+    # ---- the plain FP32 form on the same inputs (FP32 rows everywhere, FP32 SIMT join filter):
+    # outside the main timed region, same event timing, fewer steps
+    plain = None
+    if not args.no_plain:
+        kwp = dict(kw, join_filter="fp32", rows="fp32")
+        fg.merge(inp, **kwp)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ps = max(1, min(2, args.steps))
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ps)]
+        for q in range(ps):
+            pev[q][0].record(stream)
+            outp = fg.merge(inp, **kwp)
+            pev[q][1].record(stream)
+        torch.cuda.synchronize()
+        p_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pev), ws, dev)
+        plain = {"value": ws * w.N * ps / (p_ms * 1e-3), "unit": UNIT, "ms_per_step": p_ms / ps, "steps": ps,
+                 "form": "FP32 rows, FP32 SIMT join filter", "same_graph": bool(torch.equal(outp["ids"], out["ids"]))}
     # ---- evaluation outside the timed region: recall@10 at beam 64 against exact k-NN
     nq_eval = min(1000, w.Q.shape[0])
     Q = torch.from_numpy(w.Q[:nq_eval]).to(dev)
@@ -333,11 +365,12 @@ def run_fgim(args):
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
+    s_row = row_bytes(w)
     roof = (roofline_for(dom, kernels[dom]["ms"] / kernels[dom]["launches"], kernels[dom]["launches"] / args.steps,
-                         w, graphs, cpu, peaks, stats) if dom else None)
+                         w, graphs, cpu, peaks, stats, s_row) if dom else None)
     # the same figures for every modelled kernel, for the record
     roof_all = {name: roofline_for(name, kernels[name]["ms"] / kernels[name]["launches"],
-                                   kernels[name]["launches"] / args.steps, w, graphs, cpu, peaks, stats)
+                                   kernels[name]["launches"] / args.steps, w, graphs, cpu, peaks, stats, s_row)
                 for name in ("k_cross_query", "k_join", "k_prune") if name in kernels}
     value = ws * w.N * args.steps / (total_ms * 1e-3)
     clocks = clk.summary()
@@ -354,6 +387,7 @@ def run_fgim(args):
             "cpu_baseline": ({k_: v for k_, v in cpu.items() if k_ in ("value", "unit", "cores", "kind", "sample")}
                              if cpu else None),
             "stage_a_work_model": cpu["stage_a_per_query"] if cpu else None,
+            "plain_fp32": plain,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms}
     print(json.dumps(line), flush=True)
 

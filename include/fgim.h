@@ -93,7 +93,11 @@ typedef struct {
                                 are the same; only speed differs. Passes whose shapes the tensor-core
                                 tile does not cover (dim % 16 != 0, |C_n| > 128, |C| > 256) use the
                                 FP32 tile. */
-    int32_t reserved[4];
+    int32_t byte_rows;       /* 0 = auto: when every coordinate is an integer in [0, 255] and dim <= 128,
+                                dim % 16 == 0, the searches, the join's re-rank and the prune read one
+                                byte per coordinate and form the distances in exact integer arithmetic
+                                (they equal the FP32 distances bit for bit); 1 = off (FP32 rows only) */
+    int32_t reserved[3];
 } fgim_params;
 
 /* k-NNG buffers, caller-owned device memory: [n, k] each. */
@@ -127,6 +131,7 @@ typedef struct {
     int64_t attached;        /* vertices attached by the reachability fix */
     int64_t unreached;       /* vertices still unreached after the fix */
     int64_t join_reruns;     /* Update passes re-run after a proposal-buffer overflow */
+    int64_t join_cands;      /* candidate-set sizes |C_n| + |C_o| summed over the vertices joined */
 } fgim_stats;
 
 /*

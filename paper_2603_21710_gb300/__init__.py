@@ -26,6 +26,10 @@ FLAG_NEW = 1
 FLAG_REPLACED = 2
 # Update's pair filter: BF16 tensor-core tile or FP32 SIMT tile (same results)
 JOIN_FILTERS = {"tc": 0, "bf16": 0, "fp32": 1, "simt": 1, 0: 0, 1: 1}
+# row storage: "auto" reads one byte per coordinate when the data allow it (integers in
+# [0, 255], d <= 128, d % 16 == 0; distances are then exact integers, equal to the FP32
+# ones), "fp32" always reads the FP32 rows
+ROW_STORAGE = {"auto": 0, "fp32": 1, "off": 1, 0: 0, 1: 1}
 
 
 def _stream() -> int:
@@ -85,12 +89,13 @@ class MergeInput:
         return cls(vs, ads, entries, metric)
 
     def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
-               reach_beam=0, join_filter="tc") -> Params:
+               reach_beam=0, join_filter="tc", rows="auto") -> Params:
         p = Params()
         p.dim, p.dtype, p.metric = self.d, 0, self.metric
         p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap = k, R, float(alpha), L, iters, rev_cap
         p.ensure_reachable, p.reach_beam = int(bool(ensure_reachable)), reach_beam
         p.join_filter = JOIN_FILTERS[join_filter]
+        p.byte_rows = ROW_STORAGE[rows]
         return p
 
 
@@ -106,10 +111,10 @@ def _new_knng(N: int, k: int, device) -> dict:
 
 def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3, rev_cap: int = 0,
           ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False,
-          join_filter="tc") -> dict:
+          join_filter="tc", rows="auto") -> dict:
     """Full merge (stages a, b, c and the reachability fix). Returns device tensors."""
     L_ = load()
-    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter)
+    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter, rows)
     dev = inp.X.device
     out = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
            "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
@@ -129,7 +134,8 @@ def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters
 
 
 def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metric="l2", L: int = 0, iters: int = 3,
-               rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None, join_filter="tc") -> dict:
+               rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None, join_filter="tc",
+               rows="auto") -> dict:
     """Merge from host memory (CPU tensors, pinned for speed); results land in host tensors."""
     L_ = load()
     if X.is_cuda or adj.is_cuda:
@@ -144,6 +150,7 @@ def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metri
     p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap, p.ensure_reachable = k, R, float(alpha), L, iters, rev_cap, int(
         bool(ensure_reachable))
     p.join_filter = JOIN_FILTERS[join_filter]
+    p.byte_rows = ROW_STORAGE[rows]
     sz = (ctypes.c_int32 * len(sizes))(*[int(s) for s in sizes])
     en = (ctypes.c_int32 * len(entries))(*[int(e) for e in entries])
     if out_ids is None:
@@ -156,10 +163,10 @@ def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metri
     return {"ids": out_ids, "deg": out_deg, "entry": int(entry.value), "stats": last_stats()}
 
 
-def cross_query(inp: MergeInput, k: int, L: int = 0) -> dict:
+def cross_query(inp: MergeInput, k: int, L: int = 0, rows="auto") -> dict:
     """Stage (a), Alg. 2: PGs -> k-NNG."""
     L_ = load()
-    p = inp.params(k=k, L=L)
+    p = inp.params(k=k, L=L, rows=rows)
     kd = _new_knng(inp.N, k, inp.X.device)
     kn = _knng_struct(kd["ids"], kd["dist"], kd["flags"])
     check(L_.fgim_cross_query(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
@@ -167,11 +174,11 @@ def cross_query(inp: MergeInput, k: int, L: int = 0) -> dict:
     return kd
 
 
-def refine_pass(inp: MergeInput, knng: dict, rev_cap: int = 0, join_filter="tc") -> dict:
+def refine_pass(inp: MergeInput, knng: dict, rev_cap: int = 0, join_filter="tc", rows="auto") -> dict:
     """One synchronous Visit + Update pass of Alg. 3, in place on ``knng``."""
     L_ = load()
     k = int(knng["ids"].shape[1])
-    p = inp.params(k=k, rev_cap=rev_cap, join_filter=join_filter)
+    p = inp.params(k=k, rev_cap=rev_cap, join_filter=join_filter, rows=rows)
     kn = _knng_struct(knng["ids"], knng["dist"], knng["flags"])
     check(L_.fgim_refine_pass(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
     return last_stats()
@@ -188,11 +195,11 @@ def indegree_repair(inp: MergeInput, knng: dict):
     return T, last_stats()
 
 
-def prune(inp: MergeInput, knng: dict, T: torch.Tensor, R: int, alpha: float = 1.0):
+def prune(inp: MergeInput, knng: dict, T: torch.Tensor, R: int, alpha: float = 1.0, rows="auto"):
     """Alg. 5 neighbour selection: returns (e_ids [N, R], e_dist, e_cnt)."""
     L_ = load()
     k = int(knng["ids"].shape[1])
-    p = inp.params(k=k, R=R, alpha=alpha)
+    p = inp.params(k=k, R=R, alpha=alpha, rows=rows)
     dev = inp.X.device
     e_ids = torch.empty((inp.N, R), dtype=torch.int32, device=dev)
     e_dist = torch.empty((inp.N, R), dtype=torch.float32, device=dev)
@@ -221,11 +228,11 @@ def reverse_insert(e_ids: torch.Tensor, e_dist: torch.Tensor, e_cnt: torch.Tenso
     return out
 
 
-def reach_fix(inp: MergeInput, graph: dict, entry: int, k: int = 16, beam: int = 0) -> dict:
+def reach_fix(inp: MergeInput, graph: dict, entry: int, k: int = 16, beam: int = 0, rows="auto") -> dict:
     """Reachability fix in place on ``graph`` (ids, dist, deg)."""
     L_ = load()
     R = int(graph["ids"].shape[1])
-    p = inp.params(k=k, R=R, reach_beam=beam)
+    p = inp.params(k=k, R=R, reach_beam=beam, rows=rows)
     g = Graph(graph["ids"].data_ptr(), graph["dist"].data_ptr(), graph["deg"].data_ptr(), inp.N, R, int(entry))
     check(L_.fgim_reach_fix(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(g), _stream()))
     return last_stats()

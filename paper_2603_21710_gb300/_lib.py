@@ -25,7 +25,8 @@ class Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("R", ctypes.c_int32), ("alpha", ctypes.c_float), ("L", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("rev_cap", ctypes.c_int32), ("ensure_reachable", ctypes.c_int32),
-                ("reach_beam", ctypes.c_int32), ("join_filter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("reach_beam", ctypes.c_int32), ("join_filter", ctypes.c_int32), ("byte_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class KNNG(ctypes.Structure):
@@ -40,7 +41,7 @@ class Graph(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("ndc", "hops", "join_pairs", "proposals", "zero_indegree",
-                                              "repaired", "attached", "unreached", "join_reruns")]
+                                              "repaired", "attached", "unreached", "join_reruns", "join_cands")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

@@ -173,6 +173,7 @@ struct Ctx {
             st->join_pairs += (int64_t)hc[2];
             st->repaired += (int64_t)hc[3];
             st->attached += (int64_t)hc[4];
+            st->join_cands += (int64_t)hc[5];
         }
         if (hs[0] & kErrTimeout) need(false, FGIM_ETIMEOUT, "a bounded device loop ran out");
         if (hs[0] & kErrBounds) need(false, FGIM_EINVAL, "an input index is out of range (graph ids or entry)");
@@ -200,6 +201,7 @@ static void check_params(const fgim_params* p, bool need_merge) {
     need(p->rev_cap >= 0 && p->rev_cap <= FGIM_MAX_K, FGIM_EINVAL, "rev_cap must be 0 or in [1, 128]");
     need(p->reach_beam >= 0 && p->reach_beam <= FGIM_MAX_L, FGIM_EINVAL, "reach_beam must be 0 or in [1, 128]");
     need(p->join_filter == 0 || p->join_filter == 1, FGIM_EINVAL, "join_filter must be 0 (tensor core) or 1 (FP32)");
+    need(p->byte_rows == 0 || p->byte_rows == 1, FGIM_EINVAL, "byte_rows must be 0 (auto) or 1 (off)");
 }
 
 static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
@@ -286,7 +288,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.X = contiguous_vectors(c, sh, h, p->dim, P.N);
     P.inv = nullptr;
     P.X8 = nullptr;
-    if (byte_rows_ok(P.d)) {
+    if (byte_rows_ok(P.d) && p->byte_rows == 0) {
         uint8_t* x8 = c.alloc<uint8_t>(P.N * P.d);
         int* flag = c.alloc<int>(1);
         ck(cudaMemsetAsync(flag, 0, sizeof(int), c.s));
@@ -330,8 +332,9 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.cand = c.alloc<int32_t>(N * b.cmax);
     b.nn = c.alloc<int32_t>(N);
     b.no = c.alloc<int32_t>(N);
-    // proposal buffer: large enough for every proposal of one vertex many times over
-    long long cap = 128LL * N;
+    // proposal buffer (20 bytes per proposal): one Update pass of a fresh k-NNG proposes up to
+    // a few k per vertex; vertices whose proposals do not fit are redone after the merge
+    long long cap = 256LL * N;
     const long long per_vertex_max = 2LL * b.cmax * b.cmax;
     if (cap < 4 * per_vertex_max) cap = 4 * per_vertex_max;
     if (cap < (1LL << 22)) cap = 1LL << 22;
@@ -365,7 +368,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     ck(refine_visit(*g, rev_cap, b, c.s));
     ck(cudaMemsetAsync(b.pending, 0, N, c.s));
     ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
-    ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, nullptr, N, c.ctr + 2, c.status, c.s));
+    ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, nullptr, N, c.ctr + 2, c.ctr + 5, c.status, c.s));
     unsigned long long cnt = c.read_u64(b.prop_count);
     long long total = (long long)cnt;
     ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
@@ -381,7 +384,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
         need(st->join_reruns < 10000, FGIM_EINTERNAL, "proposal overflow does not shrink");
         ck(cudaMemsetAsync(b.pending, 0, N, c.s));
         ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
-        ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, b.pend_list, np, c.ctr + 2, c.status, c.s));
+        ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, b.pend_list, np, c.ctr + 2, c.ctr + 5, c.status, c.s));
         cnt = c.read_u64(b.prop_count);
         total += (long long)cnt;
         ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));

@@ -87,7 +87,7 @@ struct RefineBuffers {
 cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cudaStream_t s);
 cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
-                        int* status, cudaStream_t s);
+                        unsigned long long* cands, int* status, cudaStream_t s);
 cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
 cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax, int cm,
     const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt, uint64_t* __restrict__ prop_key,
     unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
-    unsigned long long* pairs_count, int* status) {
+    unsigned long long* pairs_count, unsigned long long* cands_count, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -548,6 +548,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(kFull, my_pairs, o);
     if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
+    if (threadIdx.x == 0) atomicAdd(cands_count, (unsigned long long)nc);
 }
 
 // ---- tensor-core filter (BF16 tcgen05 Gram tile), exact FP32 re-rank
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
     int cm, uint32_t tmem_cols, const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt,
     uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
-    unsigned long long* pairs_count, int* status) {
+    unsigned long long* pairs_count, unsigned long long* cands_count, int* status) {
     constexpr int NT = BYTES ? 256 : 128;   // threads (byte rows: eight warps, two per TMEM lane quarter)
     constexpr int NW = NT / 32;
     extern __shared__ unsigned char smem_raw[];
@@ -1127,6 +1128,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(kFull, my_pairs, o);
     if (lane == 0 && my_pairs) atomicAdd(pairs_count, my_pairs);
+    if (tid == 0) atomicAdd(cands_count, (unsigned long long)nc);
 }
 
 // Largest candidate set and C_n of the vertices in vlist (all when null), and the vertices
@@ -1187,7 +1189,7 @@ static size_t tc_launch_smem(const TCLayout& TL, uint32_t cols) {
 
 cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
-                        int* status, cudaStream_t s) {
+                        unsigned long long* cands, int* status, cudaStream_t s) {
     if (nv <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMemsetAsync(b.max_nc, 0, 8 * sizeof(int32_t), s)) != cudaSuccess) return e;
@@ -1226,7 +1228,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         k_join_tc<MT, BY, LG><<<(unsigned)count, (BY) ? 256 : kTCThreads, smem, s>>>(                               \
             t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
-            pairs, status);                                                                                       \
+            pairs, cands, status);                                                                                \
         e = cudaGetLastError();                                                                                   \
     } while (0)
 #define FGIM_LAUNCH_TC(MT, BY)                                                                                    \
@@ -1259,7 +1261,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         k_join_staged<MT><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand, b.nn,  \
                                                                 b.no, b.cmax, cm, vlist, b.prop_tgt, b.prop_key,  \
                                                                 b.prop_count, b.prop_cap, b.pending, pairs,       \
-                                                                status);                                          \
+                                                                cands, status);                                   \
         e = cudaGetLastError();                                                                                   \
     } while (0)
     if (metric == FGIM_L2SQ) FGIM_LAUNCH_JS(FGIM_L2SQ);

@@ -40,6 +40,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.Params) == 64
     assert ctypes.sizeof(_lib.KNNG) == 40
     assert ctypes.sizeof(_lib.Graph) == 40
+    assert ctypes.sizeof(_lib.Stats) == 80
 
 
 def _params(**kw):

@@ -365,3 +365,28 @@ def test_join_filters_agree(which, request):
     ma = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, join_filter="tc")
     mb = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, join_filter="fp32")
     assert torch.equal(ma["ids"], mb["ids"])
+
+
+def test_byte_rows_equal_fp32_rows(sift_like):
+    """Integer data in [0, 255]: the byte-row stages (searches, join re-rank, prune) give the
+    FP32-row results bit for bit, stage by stage and for the whole merge."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    ka = fg.cross_query(inp, w.k, rows="auto")
+    kb = fg.cross_query(inp, w.k, rows="fp32")
+    for key in ("ids", "dist", "flags"):
+        assert torch.equal(ka[key], kb[key]), key
+    assert ka["stats"]["ndc"] == kb["stats"]["ndc"]
+    fg.refine_pass(inp, ka, rows="auto")
+    fg.refine_pass(inp, kb, rows="fp32")
+    for key in ("ids", "dist", "flags"):
+        assert torch.equal(ka[key], kb[key]), key
+    T, _ = fg.indegree_repair(inp, ka)
+    ea = fg.prune(inp, ka, T, w.R, w.alpha, rows="auto")
+    eb = fg.prune(inp, ka, T, w.R, w.alpha, rows="fp32")
+    for x, y in zip(ea, eb):
+        assert torch.equal(x, y)
+    ma = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, rows="auto")
+    mb = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, rows="fp32", join_filter="fp32")
+    assert torch.equal(ma["ids"], mb["ids"]) and torch.equal(ma["deg"], mb["deg"])
+    assert ma["entry"] == mb["entry"]

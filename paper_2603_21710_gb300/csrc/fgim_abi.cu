@@ -334,7 +334,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.no = c.alloc<int32_t>(N);
     // proposal buffer (20 bytes per proposal): one Update pass of a fresh k-NNG proposes up to
     // a few k per vertex; vertices whose proposals do not fit are redone after the merge
-    long long cap = 256LL * N;
+    long long cap = 320LL * N;
     const long long per_vertex_max = 2LL * b.cmax * b.cmax;
     if (cap < 4 * per_vertex_max) cap = 4 * per_vertex_max;
     if (cap < (1LL << 22)) cap = 1LL << 22;
@@ -372,13 +372,17 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     unsigned long long cnt = c.read_u64(b.prop_count);
     long long total = (long long)cnt;
     ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
+    // vertices whose proposals did not all fit (proposal buffer full) are re-run against the
+    // merged lists: a proposal that would have entered a list still beats its (only lower)
+    // worst key and is still absent, so the merged result is the same
     long long prev_pending = -1;
-    while (cnt > (unsigned long long)cap) {
-        // some vertices dropped proposals: re-run exactly those against the merged lists
+    for (int rerun = 0;; ++rerun) {
         ck(launch_nonzero_flags(b.pending, N, b.pend_flag, c.s));
         ck(compact_flags(b.pend_flag, N, b.pend_list, b.pend_off, b.scan_tmp, b.scan_bytes, c.s));
         const long long np = c.read_ll(b.pend_off + N);
-        need(np > 0 && np != prev_pending + (np == prev_pending ? 0 : 0), FGIM_EINTERNAL, "proposal overflow without pending vertices");
+        if (np == 0) break;
+        need(!(cnt <= (unsigned long long)cap && np == prev_pending), FGIM_EINTERNAL,
+             "pending vertices without a proposal overflow");
         prev_pending = np;
         st->join_reruns += 1;
         need(st->join_reruns < 10000, FGIM_EINTERNAL, "proposal overflow does not shrink");

@@ -915,38 +915,6 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         }
         qn += __popc(vote);
     };
-    if (ok_mma) {
-        // the NW / 4 warps of a lane quarter take every (NW / 4)-th group of four columns
-        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        const int cstep = 4 * (NW / 4);
-        const int cend = min(nn, 32 * (warp & 3) + 31);   // c < r <= 32 (w % 4) + 31
-#pragma unroll 1
-        for (int c0 = 4 * (warp >> 2); c0 < cend; c0 += cstep) {
-            float dv[4];
-            tc::tmem_ld4(trow + (uint32_t)c0, dv);
-#pragma unroll
-            for (int t4 = 0; t4 < 4; ++t4) {
-                const int c = c0 + t4;
-                if (c < cend) append(c, (r_ok && c < r) ? test(c, dv[t4]) : 0u);
-            }
-        }
-        if (LARGE && nc > 128 && 32 * (warp & 3) < nn) {
-#pragma unroll 1
-            for (int c0 = 128 + 4 * (warp >> 2); c0 < nc; c0 += cstep) {
-                float dv[4];
-                tc::tmem_ld4(trow + (uint32_t)c0, dv);
-#pragma unroll
-                for (int t4 = 0; t4 < 4; ++t4) {
-                    const int c = c0 + t4;
-                    if (c < nc) append(c, r < nn ? test(c, dv[t4]) : 0u);
-                }
-            }
-        }
-    }
-    if (qn > seg && lane == 0) {   // survivors dropped: this vertex is redone after the merge
-        pending[v] = 1;
-        atomicOr(status, kErrOverflow);
-    }
 
     // Exact re-rank of this warp's survivors (no wait for the other warps) with the canonical
     // FP32 distance, kStep pairs per step; lane t < U proposes for pair t.
@@ -957,152 +925,188 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     //  - otherwise the canonical FP32 additions, from the staged tile when every staged row is
     //    exact (the same values), else from the FP32 rows in global memory.
     constexpr int kStep = BYTES ? 16 : 8;
-    const int nq = min(qn, seg);
-    for (int q0 = 0; q0 < nq; q0 += kStep) {
-        const int U = min(kStep, nq - q0);
-        float sc = 0.f;
-        if constexpr (BYTES) {
-            const int lpr = byte_lanes(d);
-            const int rpi = 32 / lpr;
-            const int sub = lane / lpr, part = lane & (lpr - 1);
-            const bool has = part < (d >> 4);
-            constexpr int kIt = 4;   // >= kStep * lpr / 32 for lpr <= 8
-            uint4 xa[kIt], xb[kIt];
+    auto rerank = [&](int nq) {
+        for (int q0 = 0; q0 < nq; q0 += kStep) {
+            const int U = min(kStep, nq - q0);
+            float sc = 0.f;
+            if constexpr (BYTES) {
+                const int lpr = byte_lanes(d);
+                const int rpi = 32 / lpr;
+                const int sub = lane / lpr, part = lane & (lpr - 1);
+                const bool has = part < (d >> 4);
+                constexpr int kIt = 4;   // >= kStep * lpr / 32 for lpr <= 8
+                uint4 xa[kIt], xb[kIt];
 #pragma unroll
-            for (int t = 0; t < kIt; ++t) {
-                const int pr = t * rpi + sub;
-                xa[t] = make_uint4(0u, 0u, 0u, 0u);
-                xb[t] = xa[t];
-                if (pr < U && has) {
-                    const uint32_t e = wq[q0 + pr];
-                    xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
-                    xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
-                }
-            }
-            uint32_t mine = 0u;
-#pragma unroll
-            for (int t = 0; t < kIt; ++t) {
-                if (t * rpi < U) {
-                    uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
-                    dot = __dp4a(xa[t].y, xb[t].y, dot);
-                    dot = __dp4a(xa[t].z, xb[t].z, dot);
-                    dot = __dp4a(xa[t].w, xb[t].w, dot);
-                    for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
-                    const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
-                    if (lane / rpi == t) mine = got;
-                }
-            }
-            if (lane < U) {
-                if (METRIC == FGIM_L2SQ) {
-                    const uint32_t e = wq[q0 + lane];
-                    const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
-                    const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
-                    sc = (float)(na + nb - 2u * mine);
-                } else {
-                    sc = (float)mine;
-                }
-            }
-        } else {
-            int ra[8], rb[8];
-#pragma unroll
-            for (int t8 = 0; t8 < 8; ++t8) {
-                const uint32_t e = wq[q0 + min(t8, U - 1)];
-                ra[t8] = (int)(e & 1023u);
-                rb[t8] = (int)((e >> 10) & 1023u);
-            }
-            float acc[8][4];
-#pragma unroll
-            for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
-            for (int c = lane; c < vq; c += 32) {
-                float4 xa[8], xb[8];
-                if (exact) {
-#pragma unroll
-                    for (int t8 = 0; t8 < 8; ++t8) {
-                        const uint2 ua =
-                            *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
-                        const uint2 ub =
-                            *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
-                        xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
-                                             __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
-                        xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
-                                             __uint_as_float(ub.y << 16), __uint_as_float(ub.y & 0xffff0000u));
+                for (int t = 0; t < kIt; ++t) {
+                    const int pr = t * rpi + sub;
+                    xa[t] = make_uint4(0u, 0u, 0u, 0u);
+                    xb[t] = xa[t];
+                    if (pr < U && has) {
+                        const uint32_t e = wq[q0 + pr];
+                        xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
+                        xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
                     }
-                } else {
+                }
+                uint32_t mine = 0u;
+#pragma unroll
+                for (int t = 0; t < kIt; ++t) {
+                    if (t * rpi < U) {
+                        uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
+                        dot = __dp4a(xa[t].y, xb[t].y, dot);
+                        dot = __dp4a(xa[t].z, xb[t].z, dot);
+                        dot = __dp4a(xa[t].w, xb[t].w, dot);
+                        for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
+                        const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
+                        if (lane / rpi == t) mine = got;
+                    }
+                }
+                if (lane < U) {
+                    if (METRIC == FGIM_L2SQ) {
+                        const uint32_t e = wq[q0 + lane];
+                        const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
+                        const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
+                        sc = (float)(na + nb - 2u * mine);
+                    } else {
+                        sc = (float)mine;
+                    }
+                }
+            } else {
+                int ra[8], rb[8];
+#pragma unroll
+                for (int t8 = 0; t8 < 8; ++t8) {
+                    const uint32_t e = wq[q0 + min(t8, U - 1)];
+                    ra[t8] = (int)(e & 1023u);
+                    rb[t8] = (int)((e >> 10) & 1023u);
+                }
+                float acc[8][4];
+#pragma unroll
+                for (int t8 = 0; t8 < 8; ++t8) acc[t8][0] = acc[t8][1] = acc[t8][2] = acc[t8][3] = 0.f;
+                for (int c = lane; c < vq; c += 32) {
+                    float4 xa[8], xb[8];
+                    if (exact) {
+#pragma unroll
+                        for (int t8 = 0; t8 < 8; ++t8) {
+                            const uint2 ua =
+                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
+                            const uint2 ub =
+                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
+                            xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
+                                                 __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
+                            xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
+                                                 __uint_as_float(ub.y << 16), __uint_as_float(ub.y & 0xffff0000u));
+                        }
+                    } else {
+#pragma unroll
+                        for (int t8 = 0; t8 < 8; ++t8) {
+                            xa[t8] = reinterpret_cast<const float4*>(X + (long long)cid[ra[t8]] * d)[c];
+                            xb[t8] = reinterpret_cast<const float4*>(X + (long long)cid[rb[t8]] * d)[c];
+                        }
+                    }
 #pragma unroll
                     for (int t8 = 0; t8 < 8; ++t8) {
-                        xa[t8] = reinterpret_cast<const float4*>(X + (long long)cid[ra[t8]] * d)[c];
-                        xb[t8] = reinterpret_cast<const float4*>(X + (long long)cid[rb[t8]] * d)[c];
+                        const float4 x = xa[t8], y = xb[t8];
+                        if (METRIC == FGIM_L2SQ) {
+                            const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
+                            const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
+                            acc[t8][0] = fmaf(e0, e0, acc[t8][0]);
+                            acc[t8][1] = fmaf(e1, e1, acc[t8][1]);
+                            acc[t8][2] = fmaf(e2, e2, acc[t8][2]);
+                            acc[t8][3] = fmaf(e3, e3, acc[t8][3]);
+                        } else {
+                            acc[t8][0] = fmaf(x.x, y.x, acc[t8][0]);
+                            acc[t8][1] = fmaf(x.y, y.y, acc[t8][1]);
+                            acc[t8][2] = fmaf(x.z, y.z, acc[t8][2]);
+                            acc[t8][3] = fmaf(x.w, y.w, acc[t8][3]);
+                        }
                     }
                 }
 #pragma unroll
                 for (int t8 = 0; t8 < 8; ++t8) {
-                    const float4 x = xa[t8], y = xb[t8];
-                    if (METRIC == FGIM_L2SQ) {
-                        const float e0 = __fsub_rn(x.x, y.x), e1 = __fsub_rn(x.y, y.y);
-                        const float e2 = __fsub_rn(x.z, y.z), e3 = __fsub_rn(x.w, y.w);
-                        acc[t8][0] = fmaf(e0, e0, acc[t8][0]);
-                        acc[t8][1] = fmaf(e1, e1, acc[t8][1]);
-                        acc[t8][2] = fmaf(e2, e2, acc[t8][2]);
-                        acc[t8][3] = fmaf(e3, e3, acc[t8][3]);
-                    } else {
-                        acc[t8][0] = fmaf(x.x, y.x, acc[t8][0]);
-                        acc[t8][1] = fmaf(x.y, y.y, acc[t8][1]);
-                        acc[t8][2] = fmaf(x.z, y.z, acc[t8][2]);
-                        acc[t8][3] = fmaf(x.w, y.w, acc[t8][3]);
+                    const float tot = warp_butterfly(__fadd_rn(__fadd_rn(acc[t8][0], acc[t8][1]),
+                                                               __fadd_rn(acc[t8][2], acc[t8][3])));
+                    if (lane == t8) sc = tot;
+                }
+            }
+            // proposals: one shared-memory atomic per warp and direction
+            uint64_t key[2] = {kEmptyKey, kEmptyKey};
+            int32_t tgt[2] = {-1, -1};
+            if (lane < U) {
+                const uint32_t e = wq[q0 + lane];
+                const int ia = (int)(e & 1023u), jb = (int)((e >> 10) & 1023u);
+                const unsigned dm = (e >> 20) & 3u;
+                const float dd =
+                    delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(meta[ia].w, meta[jb].w) : 1.f);
+#pragma unroll
+                for (int dir = 0; dir < 2; ++dir) {
+                    const int a2 = dir == 0 ? ia : jb, b2 = dir == 0 ? jb : ia;
+                    const uint64_t kk = mkkey(dd, cid[b2]);
+                    if (((dm >> dir) & 1u) && kk < thr[a2]) {
+                        key[dir] = kk;
+                        tgt[dir] = cid[a2];
                     }
                 }
             }
-#pragma unroll
-            for (int t8 = 0; t8 < 8; ++t8) {
-                const float tot = warp_butterfly(__fadd_rn(__fadd_rn(acc[t8][0], acc[t8][1]),
-                                                           __fadd_rn(acc[t8][2], acc[t8][3])));
-                if (lane == t8) sc = tot;
-            }
-        }
-        // proposals: one shared-memory atomic per warp and direction
-        uint64_t key[2] = {kEmptyKey, kEmptyKey};
-        int32_t tgt[2] = {-1, -1};
-        if (lane < U) {
-            const uint32_t e = wq[q0 + lane];
-            const int ia = (int)(e & 1023u), jb = (int)((e >> 10) & 1023u);
-            const unsigned dm = (e >> 20) & 3u;
-            const float dd =
-                delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(meta[ia].w, meta[jb].w) : 1.f);
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
-                const int a2 = dir == 0 ? ia : jb, b2 = dir == 0 ? jb : ia;
-                const uint64_t kk = mkkey(dd, cid[b2]);
-                if (((dm >> dir) & 1u) && kk < thr[a2]) {
-                    key[dir] = kk;
-                    tgt[dir] = cid[a2];
-                }
-            }
-        }
-#pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-            const bool has_p = tgt[dir] >= 0;
-            const unsigned vote = __ballot_sync(kFull, has_p);
-            if (vote == 0u) continue;
-            const int leader = __ffs(vote) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(misc, __popc(vote));
-            base = __shfl_sync(kFull, base, leader);
-            if (has_p) {
-                const int slot = base + __popc(vote & lt);
-                if (slot < kTCPropBuf) {
-                    pb_tgt[slot] = tgt[dir];
-                    pb_key[slot] = key[dir];
-                } else {
-                    const unsigned long long pos = atomicAdd(prop_count, 1ull);
-                    if (pos < (unsigned long long)prop_cap) {
-                        prop_tgt[pos] = tgt[dir];
-                        prop_key[pos] = key[dir];
+                const bool has_p = tgt[dir] >= 0;
+                const unsigned vote = __ballot_sync(kFull, has_p);
+                if (vote == 0u) continue;
+                const int leader = __ffs(vote) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(misc, __popc(vote));
+                base = __shfl_sync(kFull, base, leader);
+                if (has_p) {
+                    const int slot = base + __popc(vote & lt);
+                    if (slot < kTCPropBuf) {
+                        pb_tgt[slot] = tgt[dir];
+                        pb_key[slot] = key[dir];
                     } else {
-                        pending[v] = 1;
-                        atomicOr(status, kErrOverflow);
+                        const unsigned long long pos = atomicAdd(prop_count, 1ull);
+                        if (pos < (unsigned long long)prop_cap) {
+                            prop_tgt[pos] = tgt[dir];
+                            prop_key[pos] = key[dir];
+                        } else {
+                            pending[v] = 1;
+                            atomicOr(status, kErrOverflow);
+                        }
                     }
                 }
             }
+        }
+    };
+    // Filter and re-rank interleaved: a column group adds at most 128 survivors to the warp's
+    // segment, so the segment is re-ranked and emptied whenever fewer than 128 slots are left,
+    // and once more when the columns are done; no survivor is ever dropped.
+    if (ok_mma) {
+        // the NW / 4 warps of a lane quarter take every (NW / 4)-th group of four columns
+        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        const int cstep = 4 * (NW / 4);
+        const bool two = LARGE && nc > 128 && 32 * (warp & 3) < nn;   // columns 128 .. nc - 1 too
+        int c0 = 4 * (warp >> 2), range = 0;
+        int cend = min(nn, 32 * (warp & 3) + 31);   // range 0: c < r <= 32 (w % 4) + 31
+        while (true) {
+            while (qn <= seg - 128) {
+                if (c0 >= cend) {
+                    if (two && range == 0) {
+                        range = 1;
+                        c0 = 128 + 4 * (warp >> 2);
+                        cend = nc;
+                        continue;
+                    }
+                    break;
+                }
+                float dv[4];
+                tc::tmem_ld4(trow + (uint32_t)c0, dv);
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4) {
+                    const int c = c0 + t4;
+                    if (c < cend) append(c, (range == 0 ? (r_ok && c < r) : r < nn) ? test(c, dv[t4]) : 0u);
+                }
+                c0 += cstep;
+            }
+            rerank(qn);
+            qn = 0;
+            if (c0 >= cend && !(two && range == 0)) break;
         }
     }
     tc::fence_before_sync();

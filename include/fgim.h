@@ -221,6 +221,14 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
 /* Counters of the last merge/search call made by this host thread. */
 void fgim_last_stats(fgim_stats* out);
 
+/*
+ * Scratch memory: every call takes its scratch from a stream-ordered pool the library keeps
+ * per device, and the pool keeps what it has mapped for later calls (a merge of 1M vectors
+ * uses about 10 GB). This returns the pool's unused memory to the device; call it when no
+ * call of this library has work in flight.
+ */
+void fgim_trim_memory(void);
+
 /* Human-readable name of a status; message of the last CUDA error on this host thread. */
 const char* fgim_strerror(fgim_status s);
 const char* fgim_last_error(void);

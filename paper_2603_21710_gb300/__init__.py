@@ -109,6 +109,11 @@ def _new_knng(N: int, k: int, device) -> dict:
             "flags": torch.empty((N, k), dtype=torch.uint8, device=device)}
 
 
+def trim_memory() -> None:
+    """Return the unused part of the library's scratch pools to the device (see fgim.h)."""
+    load().fgim_trim_memory()
+
+
 def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3, rev_cap: int = 0,
           ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False,
           join_filter="tc", rows="auto") -> dict:

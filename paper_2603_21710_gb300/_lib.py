@@ -54,6 +54,7 @@ class FgimError(RuntimeError):
 
 
 EXPORTS = {
+    "fgim_trim_memory": (None, []),
     "fgim_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p]),
     "fgim_merge_host": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,

@@ -68,16 +68,49 @@ static void resolve_events() {
 }
 
 // ---------------------------------------------------------------------------- scratch
+// The library's scratch comes from its own stream-ordered pool per device, which keeps the
+// memory it has mapped between calls (a merge needs several GB; mapping them again on every
+// call costs tens of milliseconds). fgim_trim_memory hands the unused part back.
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t lib_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    return pool;
+}
+
 class Scratch {
    public:
-    explicit Scratch(cudaStream_t s) : s_(s) {}
+    explicit Scratch(cudaStream_t s) : s_(s), pool_(lib_pool()) {}
     ~Scratch() { release(); }
     template <typename T>
     T* alloc(long long count) {
         if (count <= 0) count = 1;
         void* p = nullptr;
         const size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
-        if (cudaMallocAsync(&p, bytes, s_) != cudaSuccess) {
+        const cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&p, bytes, pool_, s_) : cudaMallocAsync(&p, bytes, s_);
+        if (e != cudaSuccess) {
             cudaGetLastError();
             ok_ = false;
             return nullptr;
@@ -93,6 +126,7 @@ class Scratch {
 
    private:
     cudaStream_t s_;
+    cudaMemPool_t pool_;
     std::vector<void*> ptrs_;
     bool ok_ = true;
 };
@@ -788,6 +822,11 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
     });
     end_call();
     return r;
+}
+
+void fgim_trim_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& kv : g_pools) cudaMemPoolTrimTo(kv.second, 0);
 }
 
 void fgim_last_stats(fgim_stats* out) {

@@ -174,41 +174,44 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
 }
 
 // Alg. 1 over one graph whose rows are Xt[v] / adj[v * M] for local ids v < nt. Keys carry
-// global ids (local + id_off). The pool C (<= L <= 128 keys, sorted by (delta, id)) lives in
-// registers: entry e = 32 s + lane is pk[s] of that lane, its "expanded" mark bit s of expd.
-// A candidate enters by one ballot for its rank and one shift of the entries behind it;
-// candidates that cannot beat the worst entry of a full pool are never inserted. Returns
-// the pool size and leaves the pool in pool[0 .. size) (shared memory).
+// global ids (local + id_off). The pool C (<= L <= 32 * MAXS keys, sorted by (delta, id))
+// lives in registers: entry e = 32 s + lane is pk[s] of that lane, its "expanded" mark bit s
+// of expd. Candidates that cannot beat the worst entry of a full pool are never inserted.
+// MAXS = 1 (L <= 32) inserts a batch at once: each candidate's rank among the pool and among
+// the other candidates, each pool entry's shift, one scatter through shared memory (pool,
+// pflag). Larger pools insert one candidate at a time (one ballot for its rank, one shift).
+// Returns the pool size and leaves the pool in pool[0 .. size).
 // scratch: 32 ints of shared memory for the compacted neighbour ids.
 constexpr int kPoolSlots = 4;
 
-__device__ __forceinline__ uint64_t pick_slot(const uint64_t (&pk)[kPoolSlots], int s) {
+template <int MAXS>
+__device__ __forceinline__ uint64_t pick_slot(const uint64_t (&pk)[MAXS], int s) {
     uint64_t v = pk[0];
 #pragma unroll
-    for (int t = 1; t < kPoolSlots; ++t)
+    for (int t = 1; t < MAXS; ++t)
         if (s == t) v = pk[t];
     return v;
 }
 
-template <int METRIC, bool SMALLD, typename RT>
+template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
                            int M, long long nt, int ep, long long id_off, const float* q, float4 qreg,
-                           const QBytes& qb, float qinv, int d, int L, uint64_t* pool, int32_t* ht, int htbits,
-                           int32_t* scratch, float* P, WarpCounters& ctr, int* status) {
+                           const QBytes& qb, float qinv, int d, int L, uint64_t* pool, uint8_t* pflag, int32_t* ht,
+                           int htbits, int32_t* scratch, float* P, WarpCounters& ctr, int* status) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const int H = 1 << htbits;
-    const int S = (L + 31) >> 5;
+    const int S = MAXS == 1 ? 1 : (L + 31) >> 5;
     for (int s = lane; s < H; s += 32) ht[s] = -1;
     if (lane == 0) scratch[0] = ep;
     __syncwarp();
-    if (ep < 0 || ep >= nt || L < 1 || S > kPoolSlots) {
+    if (ep < 0 || ep >= nt || L < 1 || S > MAXS || (MAXS == 1 && L > 32)) {
         if (lane == 0) atomicOr(status, kErrBounds);
         return 0;
     }
-    uint64_t pk[kPoolSlots];
+    uint64_t pk[MAXS];
 #pragma unroll
-    for (int s = 0; s < kPoolSlots; ++s) pk[s] = kEmptyKey;
+    for (int s = 0; s < MAXS; ++s) pk[s] = kEmptyKey;
     unsigned expd = 0u;
     int n;
     uint64_t worst = kEmptyKey;   // pool entry L - 1 once the pool is full
@@ -231,7 +234,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
     for (long long it = 0; it <= nt; ++it) {
         int first = -1;
 #pragma unroll
-        for (int s = 0; s < kPoolSlots; ++s) {
+        for (int s = 0; s < MAXS; ++s) {
             if (s < S && first < 0) {
                 const unsigned m = __ballot_sync(kFull, 32 * s + lane < n && !((expd >> s) & 1u));
                 if (m) first = 32 * s + __ffs(m) - 1;
@@ -241,7 +244,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             done = true;
             break;
         }
-        const uint64_t fk = shfl64(pick_slot(pk, first >> 5), first & 31);
+        const uint64_t fk = shfl64(pick_slot<MAXS>(pk, first >> 5), first & 31);
         if (lane == (first & 31)) expd |= 1u << (first >> 5);
         if (lane == 0) ctr.hops++;
         const long long u = (long long)key_id(fk) - id_off;
@@ -272,61 +275,101 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             }
             __syncwarp();
             bool valid = cand < worst;
-            unsigned vm;
-            while ((vm = __ballot_sync(kFull, valid)) != 0u) {
-                const int src = __ffs(vm) - 1;
-                const uint64_t c = shfl64(cand, src);
-                if (lane == src) valid = false;
-                bool eq = false;
-                int pos = 0;
-#pragma unroll
-                for (int s = 0; s < kPoolSlots; ++s) {
-                    if (s < S) {
-                        eq |= pk[s] == c;
-                        pos += __popc(__ballot_sync(kFull, pk[s] < c));
+            if constexpr (MAXS == 1) {
+                unsigned vm = __ballot_sync(kFull, valid);
+                if (vm == 0u) continue;
+                const bool in_pool = lane < n;
+                int shift = 0, crank = 0, mypos = 0;
+                while (vm) {
+                    const int j = __ffs(vm) - 1;
+                    vm &= vm - 1;
+                    if (!__shfl_sync(kFull, valid, j)) continue;   // dropped as a duplicate
+                    const uint64_t cj = shfl64(cand, j);
+                    if (__any_sync(kFull, in_pool && pk[0] == cj)) {   // already in the pool
+                        if (lane == j) valid = false;
+                        continue;
                     }
+                    if (valid && lane > j && cand == cj) valid = false;   // a later copy of the same key
+                    if (in_pool && cj < pk[0]) ++shift;
+                    if (valid && lane != j && cj < cand) ++crank;
+                    const int pos = __popc(__ballot_sync(kFull, in_pool && pk[0] < cj));
+                    if (lane == j) mypos = pos;
                 }
-                if (__any_sync(kFull, eq)) continue;   // already in the pool (same id, same key)
-                // entries pos .. n - 1 move up by one; the slots are updated from the last one
-                // down so every slot reads its predecessor's old entries
+                const int added = __popc(__ballot_sync(kFull, valid));
+                if (added == 0) continue;
+                // merged order: pool entry e goes to e + shift, a candidate to mypos + crank
+                const int pe = lane + shift, pc = mypos + crank;
+                if (in_pool && pe < L) {
+                    pool[pe] = pk[0];
+                    pflag[pe] = (uint8_t)(expd & 1u);
+                }
+                if (valid && pc < L) {
+                    pool[pc] = cand;
+                    pflag[pc] = 0;
+                }
+                __syncwarp();
+                n = n + added < L ? n + added : L;
+                pk[0] = lane < n ? pool[lane] : kEmptyKey;
+                expd = lane < n ? (unsigned)pflag[lane] : 0u;
+                __syncwarp();
+                if (n == L) worst = shfl64(pk[0], L - 1);
+            } else {
+                unsigned vm;
+                while ((vm = __ballot_sync(kFull, valid)) != 0u) {
+                    const int src = __ffs(vm) - 1;
+                    const uint64_t c = shfl64(cand, src);
+                    if (lane == src) valid = false;
+                    bool eq = false;
+                    int pos = 0;
 #pragma unroll
-                for (int s = kPoolSlots - 1; s >= 0; --s) {
-                    if (s < S) {
-                        const uint64_t up = shfl64(pk[s], (lane + 31) & 31);
-                        const unsigned eup = __shfl_sync(kFull, (expd >> s) & 1u, (lane + 31) & 31);
-                        uint64_t prev = up;
-                        unsigned eprev = eup;
-                        if (s > 0) {
-                            const uint64_t w31 = shfl64(pk[s > 0 ? s - 1 : 0], 31);
-                            const unsigned e31 = __shfl_sync(kFull, (expd >> (s > 0 ? s - 1 : 0)) & 1u, 31);
-                            if (lane == 0) {
-                                prev = w31;
-                                eprev = e31;
+                    for (int s = 0; s < MAXS; ++s) {
+                        if (s < S) {
+                            eq |= pk[s] == c;
+                            pos += __popc(__ballot_sync(kFull, pk[s] < c));
+                        }
+                    }
+                    if (__any_sync(kFull, eq)) continue;   // already in the pool (same id, same key)
+                    // entries pos .. n - 1 move up by one; the slots are updated from the last
+                    // one down so every slot reads its predecessor's old entries
+#pragma unroll
+                    for (int s = MAXS - 1; s >= 0; --s) {
+                        if (s < S) {
+                            const uint64_t up = shfl64(pk[s], (lane + 31) & 31);
+                            const unsigned eup = __shfl_sync(kFull, (expd >> s) & 1u, (lane + 31) & 31);
+                            uint64_t prev = up;
+                            unsigned eprev = eup;
+                            if (s > 0) {
+                                const uint64_t w31 = shfl64(pk[s > 0 ? s - 1 : 0], 31);
+                                const unsigned e31 = __shfl_sync(kFull, (expd >> (s > 0 ? s - 1 : 0)) & 1u, 31);
+                                if (lane == 0) {
+                                    prev = w31;
+                                    eprev = e31;
+                                }
+                            }
+                            const int e = 32 * s + lane;
+                            if (e > pos && !(s == 0 && lane == 0)) {
+                                pk[s] = prev;
+                                expd = (expd & ~(1u << s)) | (eprev << s);
+                            } else if (e == pos) {
+                                pk[s] = c;
+                                expd &= ~(1u << s);
+                            }
+                            if (e >= L) {
+                                pk[s] = kEmptyKey;
+                                expd &= ~(1u << s);
                             }
                         }
-                        const int e = 32 * s + lane;
-                        if (e > pos && !(s == 0 && lane == 0)) {
-                            pk[s] = prev;
-                            expd = (expd & ~(1u << s)) | (eprev << s);
-                        } else if (e == pos) {
-                            pk[s] = c;
-                            expd &= ~(1u << s);
-                        }
-                        if (e >= L) {
-                            pk[s] = kEmptyKey;
-                            expd &= ~(1u << s);
-                        }
                     }
+                    n = n < L ? n + 1 : L;
+                    if (n == L) worst = shfl64(pick_slot<MAXS>(pk, (L - 1) >> 5), (L - 1) & 31);
+                    valid = valid && cand < worst;
                 }
-                n = n < L ? n + 1 : L;
-                if (n == L) worst = shfl64(pick_slot(pk, (L - 1) >> 5), (L - 1) & 31);
-                valid = valid && cand < worst;
             }
         }
     }
     if (!done && lane == 0) atomicOr(status, kErrTimeout);
 #pragma unroll
-    for (int s = 0; s < kPoolSlots; ++s)
+    for (int s = 0; s < MAXS; ++s)
         if (s < S && 32 * s + lane < n) pool[32 * s + lane] = pk[s];
     __syncwarp();
     return n;
@@ -347,7 +390,7 @@ __device__ __forceinline__ void warp_add_counters(WarpCounters& c, unsigned long
 
 // shared-memory layout of one warp; all offsets multiples of 16 bytes
 struct WarpLayout {
-    int q, pool, ht, res, scratch, part, bytes;
+    int q, pool, pflag, ht, res, scratch, part, bytes;
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -359,6 +402,8 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
     o += align16(d * 4);
     w.pool = o;
     o += align16(L * 8);
+    w.pflag = o;
+    o += align16(L);
     w.ht = o;
     o += align16((1 << htbits) * 4);
     w.res = o;
@@ -374,7 +419,7 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 // Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
 // (delta, id), write ids / distances / new flags.
-template <int METRIC, bool SMALLD, typename RT>
+template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const float* __restrict__ X,
                                                      const RT* __restrict__ Xr, const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
@@ -391,6 +436,7 @@ __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const floa
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
+    uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
     uint64_t* res = reinterpret_cast<uint64_t*>(base + lay.res);
     int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
@@ -442,9 +488,10 @@ __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const floa
     for (int j = 0; j < t.h; ++j) {
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
-        const int np = beam_search<METRIC, SMALLD, RT>(Xr + t.off[j] * d, inv_norm ? inv_norm + t.off[j] : nullptr,
-                                                   t.adj[j], t.M[j], nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d,
-                                                       L, pool, ht, htbits, scratch, P, ctr, status);
+        const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr + t.off[j] * d,
+                                                             inv_norm ? inv_norm + t.off[j] : nullptr, t.adj[j], t.M[j],
+                                                             nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d, L, pool,
+                                                             pflag, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
             const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
             nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
@@ -468,7 +515,7 @@ __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const floa
 
 // Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
 // (qids == nullptr) or rows qids[i] of X.
-template <int METRIC, bool SMALLD, typename RT>
+template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
                                                 const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
@@ -486,6 +533,7 @@ __global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, 
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
+    uint8_t* pflag = base + lay.pflag;
     int32_t* ht = reinterpret_cast<int32_t*>(base + lay.ht);
     int32_t* scratch = reinterpret_cast<int32_t*>(base + lay.scratch);
     float* P = reinterpret_cast<float*>(base + lay.part);
@@ -502,8 +550,8 @@ __global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, 
     qb.q2 = 0u;
     if (sizeof(RT) == 1) qb = query_bytes(q, d, lane);
     WarpCounters ctr;
-    const int np = beam_search<METRIC, SMALLD, RT>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, qb, qinv, d, L, pool,
-                                                   ht, htbits, scratch, P, ctr, status);
+    const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, qb, qinv, d, L,
+                                                         pool, pflag, ht, htbits, scratch, P, ctr, status);
     for (int s = lane; s < topk; s += 32) {
         if (s < np) {
             out_ids[qi * topk + s] = key_id(pool[s]);
@@ -524,16 +572,22 @@ static int ht_bits_for(int L) {
     return b;
 }
 
-#define FGIM_DISPATCH_METRIC_D(M, D, MACRO, RT)                                      \
-    do {                                                                             \
-        const bool small_ = (D) <= 128;                                              \
-        if ((M) == FGIM_L2SQ) {                                                      \
-            if (small_) MACRO(FGIM_L2SQ, true, RT); else MACRO(FGIM_L2SQ, false, RT);       \
-        } else if ((M) == FGIM_IP) {                                                 \
-            if (small_) MACRO(FGIM_IP, true, RT); else MACRO(FGIM_IP, false, RT);           \
-        } else {                                                                     \
-            if (small_) MACRO(FGIM_COSINE, true, RT); else MACRO(FGIM_COSINE, false, RT);   \
-        }                                                                            \
+#define FGIM_DISPATCH_METRIC_D(M, D, MACRO, RT, MS)                                              \
+    do {                                                                                         \
+        const bool small_ = (D) <= 128;                                                          \
+        if ((M) == FGIM_L2SQ) {                                                                  \
+            if (small_) MACRO(FGIM_L2SQ, true, RT, MS); else MACRO(FGIM_L2SQ, false, RT, MS);    \
+        } else if ((M) == FGIM_IP) {                                                             \
+            if (small_) MACRO(FGIM_IP, true, RT, MS); else MACRO(FGIM_IP, false, RT, MS);        \
+        } else {                                                                                 \
+            if (small_) MACRO(FGIM_COSINE, true, RT, MS); else MACRO(FGIM_COSINE, false, RT, MS); \
+        }                                                                                        \
+    } while (0)
+// register pool of one slot (L <= 32) or of kPoolSlots slots
+#define FGIM_DISPATCH_ALL(M, D, L, MACRO, RT)                                                     \
+    do {                                                                                         \
+        if ((L) <= 32) FGIM_DISPATCH_METRIC_D(M, D, MACRO, RT, 1);                               \
+        else FGIM_DISPATCH_METRIC_D(M, D, MACRO, RT, kPoolSlots);                                \
     } while (0)
 
 cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
@@ -546,23 +600,23 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
     const long long blocks = (N + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_CQ(MT, SD, RT)                                                                                 \
+#define FGIM_LAUNCH_CQ(MT, SD, RT, MS)                                                                                 \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_cross_query<MT, SD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+        e = cudaFuncSetAttribute(k_cross_query<MT, SD, RT, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                  (int)smem);                                                                       \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_cross_query", s);                                                                        \
-        k_cross_query<MT, SD, RT><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                        \
+        k_cross_query<MT, SD, RT, MS><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                        \
             t, X, reinterpret_cast<const RT*>(rows), inv_norm, N, k, L, htbits, out->ids, out->dist, out->flags,   \
             counters, status);                                                                                     \
         e = cudaGetLastError();                                                                                    \
     } while (0)
     if (X8 && byte_rows_ok(t.dim)) {
         const void* rows = X8;
-        FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ, uint8_t);
+        FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, uint8_t);
     } else {
         const void* rows = X;
-        FGIM_DISPATCH_METRIC_D(metric, t.dim, FGIM_LAUNCH_CQ, float);
+        FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, float);
     }
 #undef FGIM_LAUNCH_CQ
     return e;
@@ -579,22 +633,22 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
     const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_S(MT, SD, RT)                                                                                  \
+#define FGIM_LAUNCH_S(MT, SD, RT, MS)                                                                                  \
     do {                                                                                                           \
-        e = cudaFuncSetAttribute(k_search<MT, SD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        e = cudaFuncSetAttribute(k_search<MT, SD, RT, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_search", s);                                                                             \
-        k_search<MT, SD, RT><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                             \
+        k_search<MT, SD, RT, MS><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                             \
             X, reinterpret_cast<const RT*>(rows), inv_norm, n, d, graph, R, entry, Q, q_inv, qids, nq, topk, L,    \
             htbits, out_ids, out_dist, counters, status);                                                          \
         e = cudaGetLastError();                                                                                    \
     } while (0)
     if (X8 && qids && byte_rows_ok(d)) {   // byte rows need integer queries: rows of X
         const void* rows = X8;
-        FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S, uint8_t);
+        FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, uint8_t);
     } else {
         const void* rows = X;
-        FGIM_DISPATCH_METRIC_D(metric, d, FGIM_LAUNCH_S, float);
+        FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, float);
     }
 #undef FGIM_LAUNCH_S
     return e;

@@ -112,35 +112,37 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
         const int rpi = 32 / lpr;   // rows per warp load
         const int sub = lane / lpr, part = lane & (lpr - 1);
         const bool has = part < (d >> 4);
-        // all of this batch's row loads first (at most lpr <= 8 warp loads), then the sums
-        uint4 w[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int r = t * rpi + sub;
-            w[t] = make_uint4(0u, 0u, 0u, 0u);
-            if (t < lpr && r < U && has) w[t] = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
-        }
+        // rows in batches of four warp loads (all issued before the sums)
         uint32_t mine = 0u;
+        for (int t0 = 0; t0 * rpi < U; t0 += 4) {
+            uint4 w[4];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (t < lpr && t * rpi < U) {
-                uint32_t sq = __dp4a(qb.w.x, w[t].x, 0u);
-                sq = __dp4a(qb.w.y, w[t].y, sq);
-                sq = __dp4a(qb.w.z, w[t].z, sq);
-                sq = __dp4a(qb.w.w, w[t].w, sq);
-                uint32_t sv;
-                if (METRIC == FGIM_L2SQ) {
-                    uint32_t sx = __dp4a(w[t].x, w[t].x, 0u);
-                    sx = __dp4a(w[t].y, w[t].y, sx);
-                    sx = __dp4a(w[t].z, w[t].z, sx);
-                    sx = __dp4a(w[t].w, w[t].w, sx);
-                    sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
-                } else {
-                    sv = sq;
+            for (int t = 0; t < 4; ++t) {
+                const int r = (t0 + t) * rpi + sub;
+                w[t] = make_uint4(0u, 0u, 0u, 0u);
+                if (r < U && has) w[t] = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if ((t0 + t) * rpi < U) {
+                    uint32_t sq = __dp4a(qb.w.x, w[t].x, 0u);
+                    sq = __dp4a(qb.w.y, w[t].y, sq);
+                    sq = __dp4a(qb.w.z, w[t].z, sq);
+                    sq = __dp4a(qb.w.w, w[t].w, sq);
+                    uint32_t sv;
+                    if (METRIC == FGIM_L2SQ) {
+                        uint32_t sx = __dp4a(w[t].x, w[t].x, 0u);
+                        sx = __dp4a(w[t].y, w[t].y, sx);
+                        sx = __dp4a(w[t].z, w[t].z, sx);
+                        sx = __dp4a(w[t].w, w[t].w, sx);
+                        sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
+                    } else {
+                        sv = sq;
+                    }
+                    for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
+                    const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
+                    if (lane / rpi == t0 + t) mine = got;
                 }
-                for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
-                const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
-                if (lane / rpi == t) mine = got;
             }
         }
         if (METRIC == FGIM_L2SQ) mine += qb.q2;
@@ -395,7 +397,8 @@ struct WarpLayout {
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int kres) {
+// part (the 32 x 33 partial matrix) is needed by FP32 rows only
+__host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int kres, bool part = true) {
     WarpLayout w;
     int o = 0;
     w.q = o;
@@ -411,7 +414,7 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
     w.scratch = o;
     o += 32 * 4;
     w.part = o;
-    o += 32 * 33 * 4;
+    if (part) o += 32 * 33 * 4;
     w.bytes = o;
     return w;
 }
@@ -420,7 +423,7 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
 // (delta, id), write ids / distances / new flags.
 template <int METRIC, bool SMALLD, typename RT, int MAXS>
-__global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(ShardTable t, const float* __restrict__ X,
                                                      const RT* __restrict__ Xr, const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
                                                      float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const floa
     const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (g >= N) return;
     const int d = t.dim;
-    const WarpLayout lay = warp_layout(d, L, htbits, k);
+    const WarpLayout lay = warp_layout(d, L, htbits, k, sizeof(RT) != 1);
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
@@ -516,7 +519,7 @@ __global__ void __launch_bounds__(128, 5) k_cross_query(ShardTable t, const floa
 // Alg. 1 for a batch of queries over one graph with global ids. Queries are rows of Q
 // (qids == nullptr) or rows qids[i] of X.
 template <int METRIC, bool SMALLD, typename RT, int MAXS>
-__global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
+__global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
                                                 const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
                                                 int entry, const float* __restrict__ Q,
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(128, 5) k_search(const float* __restrict__ X, 
     const int lane = lane_id();
     const long long qi = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (qi >= nq) return;
-    const WarpLayout lay = warp_layout(d, L, htbits, 0);
+    const WarpLayout lay = warp_layout(d, L, htbits, 0, sizeof(RT) != 1);
     unsigned char* base = smem + (size_t)warp * lay.bytes;
     float* q = reinterpret_cast<float*>(base + lay.q);
     uint64_t* pool = reinterpret_cast<uint64_t*>(base + lay.pool);
@@ -595,7 +598,8 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
                                int* status, cudaStream_t s) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
-    const WarpLayout lay = warp_layout(t.dim, L, htbits, k);
+    const bool bytes = X8 && byte_rows_ok(t.dim);
+    const WarpLayout lay = warp_layout(t.dim, L, htbits, k, !bytes);
     const size_t smem = (size_t)lay.bytes * wpb;
     const long long blocks = (N + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
@@ -611,7 +615,7 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
             counters, status);                                                                                     \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (X8 && byte_rows_ok(t.dim)) {
+    if (bytes) {
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, uint8_t);
     } else {
@@ -628,7 +632,8 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
                           unsigned long long* counters, int* status, cudaStream_t s) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
-    const WarpLayout lay = warp_layout(d, L, htbits, 0);
+    const bool bytes = X8 && qids && byte_rows_ok(d);
+    const WarpLayout lay = warp_layout(d, L, htbits, 0, !bytes);
     const size_t smem = (size_t)lay.bytes * wpb;
     const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
@@ -643,7 +648,7 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
             htbits, out_ids, out_dist, counters, status);                                                          \
         e = cudaGetLastError();                                                                                    \
     } while (0)
-    if (X8 && qids && byte_rows_ok(d)) {   // byte rows need integer queries: rows of X
+    if (bytes) {   // byte rows need integer queries: rows of X
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, uint8_t);
     } else {

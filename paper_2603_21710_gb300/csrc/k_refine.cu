@@ -610,6 +610,13 @@ cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* 
     return cudaGetLastError();
 }
 
+// Tile row of candidate i for candidate sets of up to 128: candidates i = 4 m + q go to TMEM
+// lane quarter q (row 32 q + m), so every lane quarter holds an even share of the new and old
+// candidates and the warps of the four quarters get similar work. The columns of D follow
+// the same order (both MMA operands are the one staged tile); the inverse is the same formula.
+__host__ __device__ __forceinline__ int tc_row(int i) { return 32 * (i & 3) + (i >> 2); }
+__host__ __device__ __forceinline__ int tc_cand(int row) { return 4 * (row & 31) + (row >> 5); }
+
 // Shared memory of one k_join_tc CTA (offsets from the first 1024-byte boundary of the
 // dynamic shared memory; `bytes` includes the slack for that alignment).
 struct TCLayout {
@@ -623,7 +630,9 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     l.hs = hs;
     l.words = (cm + 31) >> 5;
     const int npad = ((cm + 15) / 16) * 16;
-    l.rows_alloc = npad;               // rows per panel (a multiple of 8: whole swizzle atoms)
+    // rows per panel (a multiple of 8: whole swizzle atoms); sets of up to 128 candidates are
+    // staged in the quarter-interleaved row order (tc_row), which spans all 128 rows
+    l.rows_alloc = cm <= 128 ? 128 : npad;
     l.dpad = ((d + 63) / 64) * 64;     // whole 128-byte panels (zero beyond d)
     auto a16 = [](int x) { return (x + 15) & ~15; };
     int o = 0;
@@ -734,7 +743,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // first batch of list entries for the membership bits.
     for (int item = tid; item < nc * kcp; item += NT) {
         const int r = item / kcp, c = item - (item / kcp) * kcp;
-        unsigned char* dst = op + tc::sw_offset(r, c, rows);
+        unsigned char* dst = op + tc::sw_offset(LARGE ? r : tc_row(r), c, rows);
         if (c < kc) cp_async16(dst, Xb + (long long)cid[r] * d + c * 8, true);
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
@@ -835,7 +844,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const uint32_t tmem = *tmem_slot;
     const bool exact = misc[2] == 0;   // every staged row equals its FP32 row
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, npad);
+        const uint32_t idesc = tc::idesc_bf16(128, LARGE ? npad : 128);
         const uint32_t base = tc::smem_u32(op);
         for (int s = 0; s < L.dpad / 16; ++s) {
             const uint64_t desc = tc::smem_desc_sw128(base + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32));
@@ -855,22 +864,23 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // adds margin for the rounding of P_i + P_j - 2 D, so lo = P_i + P_j - 2 D is lower still.
     //
     // Pairs are {i, j} with i < nn (new) and i < j < nc. Both MMA operands are the staged
-    // tile, so D is symmetric and lane r of warp w (TMEM lane r = 32 w + lane, candidate r)
-    // evaluates the pairs {c, r} with c < min(r, nn) from its own TMEM row; pairs with
-    // j >= 128 (no TMEM lane) are evaluated by lane i at columns 128 .. nc - 1. Every pair is
-    // evaluated once and no warp reads more than nn + (nc - 128) columns.
+    // tile, so D is symmetric and the lane of TMEM row r (candidate a) evaluates the pairs
+    // {b, a} with b < min(a, nn) from its own row; with more than 128 candidates (natural row
+    // order) the pairs with j >= 128 (no TMEM lane) are evaluated by lane i at columns
+    // 128 .. nc - 1. Every pair is evaluated once.
     const int r = 32 * (warp & 3) + lane;   // TMEM lane quarter warp % 4
-    const bool r_ok = r < nc;
-    const float4 fr = r_ok ? colf[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int a = LARGE ? r : tc_cand(r);    // this lane's candidate
+    const bool r_ok = a < nc;
+    const float4 fr = r_ok ? colf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float Pr = fr.x, tdr = fr.y;
     const int shr = r_ok ? __float_as_int(fr.z) : -1;
-    const float4 mr = r_ok ? meta[r] : make_float4(0.f, 0.f, 0.f, 1.f);
+    const float4 mr = r_ok ? meta[a] : make_float4(0.f, 0.f, 0.f, 1.f);
     const float n2r = mr.x, xr = mr.y, er = mr.z, cr = mr.w;
     const float xer = xr + er;
     const bool fast = METRIC == FGIM_L2SQ && (BYTES || exact);
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long my_pairs = 0;
-    // survivor directions of pair {r, c} (bit 0: r's list gets c, bit 1: c's list gets r)
+    // survivor directions of pair {a, c} (bit 0: a's list gets c, bit 1: c's list gets a)
     auto test = [&](int c, float dot) -> unsigned {
         const float4 cc = colf[c];
         if (shr == __float_as_int(cc.z)) return 0u;
@@ -899,8 +909,8 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         }
         if (!(lo <= fmaxf(tdr, cc.y))) return 0u;
         unsigned dm = 0u;
-        if (lo <= tdr && !((mask[r * W + (c >> 5)] >> (c & 31)) & 1u)) dm |= 1u;
-        if (lo <= cc.y && !((mask[c * W + (r >> 5)] >> (r & 31)) & 1u)) dm |= 2u;
+        if (lo <= tdr && !((mask[a * W + (c >> 5)] >> (c & 31)) & 1u)) dm |= 1u;
+        if (lo <= cc.y && !((mask[c * W + (a >> 5)] >> (a & 31)) & 1u)) dm |= 2u;
         return dm;
     };
     // survivors go to this warp's own segment of the queue (a register count, no atomics)
@@ -911,7 +921,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         const unsigned vote = __ballot_sync(kFull, dm != 0u);
         if (dm) {
             const int slot = qn + __popc(vote & lt);
-            if (slot < seg) wq[slot] = (uint32_t)r | ((uint32_t)c << 10) | (dm << 20);
+            if (slot < seg) wq[slot] = (uint32_t)a | ((uint32_t)c << 10) | (dm << 20);
         }
         qn += __popc(vote);
     };
@@ -987,9 +997,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 #pragma unroll
                         for (int t8 = 0; t8 < 8; ++t8) {
                             const uint2 ua =
-                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(ra[t8], c >> 1, rows) + (c & 1) * 8);
+                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(LARGE ? ra[t8] : tc_row(ra[t8]), c >> 1, rows) + (c & 1) * 8);
                             const uint2 ub =
-                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(rb[t8], c >> 1, rows) + (c & 1) * 8);
+                                *reinterpret_cast<const uint2*>(op + tc::sw_offset(LARGE ? rb[t8] : tc_row(rb[t8]), c >> 1, rows) + (c & 1) * 8);
                             xa[t8] = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
                                                  __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
                             xb[t8] = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
@@ -1078,19 +1088,31 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // segment, so the segment is re-ranked and emptied whenever fewer than 128 slots are left,
     // and once more when the columns are done; no survivor is ever dropped.
     if (ok_mma) {
-        // the NW / 4 warps of a lane quarter take every (NW / 4)-th group of four columns
+        // Column ranges: interleaved order (up to 128 candidates): for each residue q the
+        // columns 32 q .. 32 q + |{b < nn : b % 4 = q}| - 1 hold the new candidates b = 4 m + q;
+        // natural order: columns 0 .. min(nn, 32 (w % 4) + 31) - 1, then 128 .. nc - 1 for the
+        // lanes of new candidates. The NW / 4 warps of a lane quarter take every (NW / 4)-th
+        // group of four columns of a range.
         const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
         const int cstep = 4 * (NW / 4);
-        const bool two = LARGE && nc > 128 && 32 * (warp & 3) < nn;   // columns 128 .. nc - 1 too
-        int c0 = 4 * (warp >> 2), range = 0;
-        int cend = min(nn, 32 * (warp & 3) + 31);   // range 0: c < r <= 32 (w % 4) + 31
+        const int half = 4 * (warp >> 2);
+        const int nranges = LARGE ? ((nc > 128 && 32 * (warp & 3) < nn) ? 2 : 1) : 4;
+        int range = 0, c0 = 0, cend = 0;
+        auto begin = [&](int rg) {
+            if (LARGE) {
+                c0 = (rg == 0 ? 0 : 128) + half;
+                cend = rg == 0 ? min(nn, 32 * (warp & 3) + 31) : nc;
+            } else {
+                c0 = 32 * rg + half;
+                cend = 32 * rg + (nn > rg ? (nn - rg + 3) >> 2 : 0);
+            }
+        };
+        begin(0);
         while (true) {
             while (qn <= seg - 128) {
                 if (c0 >= cend) {
-                    if (two && range == 0) {
-                        range = 1;
-                        c0 = 128 + 4 * (warp >> 2);
-                        cend = nc;
+                    if (range + 1 < nranges) {
+                        begin(++range);
                         continue;
                     }
                     break;
@@ -1099,14 +1121,18 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
                 tc::tmem_ld4(trow + (uint32_t)c0, dv);
 #pragma unroll
                 for (int t4 = 0; t4 < 4; ++t4) {
-                    const int c = c0 + t4;
-                    if (c < cend) append(c, (range == 0 ? (r_ok && c < r) : r < nn) ? test(c, dv[t4]) : 0u);
+                    const int c = c0 + t4;   // TMEM column
+                    if (c < cend) {
+                        const int b = LARGE ? c : tc_cand(c);
+                        const bool pair = (LARGE && range == 1) ? a < nn : (r_ok && b < a);
+                        append(b, pair ? test(b, dv[t4]) : 0u);
+                    }
                 }
                 c0 += cstep;
             }
             rerank(qn);
             qn = 0;
-            if (c0 >= cend && !(two && range == 0)) break;
+            if (c0 >= cend && range + 1 >= nranges) break;
         }
     }
     tc::fence_before_sync();
@@ -1219,9 +1245,9 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
             const int32_t count = hb[2 + q], cmq = hb[5 + q];
             if (count <= 0) continue;
             const TCLayout TL = tc_layout(cmq, t.dim);
-            const int npad = ((cmq + 15) / 16) * 16;
+            const int ncols = cmq <= 128 ? 128 : ((cmq + 15) / 16) * 16;   // MMA N (interleaved order: 128)
             uint32_t cols = 32;
-            while ((int)cols < npad) cols <<= 1;
+            while ((int)cols < ncols) cols <<= 1;
             const size_t smem = tc_launch_smem(TL, cols);
             const int32_t* list = b.blist + (long long)q * b.blist_cap;
 #define FGIM_LAUNCH_TC3(MT, BY, LG)                                                                               \

@@ -723,6 +723,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const int kc = d >> 3;           // 16-byte chunks per BF16 row
     const int kcp = L.dpad >> 3;     // 16-byte chunks per staged row
     const int npad = ((nc + 15) / 16) * 16;   // MMA N
+    const int kcp_sh = (kcp & (kcp - 1)) == 0 ? __ffs(kcp) - 1 : -1;   // shift for / kcp when a power of two
     const float g = (float)(d + 16) * 5.9604645e-8f;
     // squared L2 on exactly converted rows: lo = P_i + P_j - 2 D_ij with P = (1 - Cf) |x|^2
     // lies below (value - bound) of the general test (see the filter)
@@ -742,7 +743,8 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // past d are zero), this thread's candidates' worst keys and row statistics, and the
     // first batch of list entries for the membership bits.
     for (int item = tid; item < nc * kcp; item += NT) {
-        const int r = item / kcp, c = item - (item / kcp) * kcp;
+        const int r = kcp_sh >= 0 ? item >> kcp_sh : item / kcp;
+        const int c = item - r * kcp;
         unsigned char* dst = op + tc::sw_offset(LARGE ? r : tc_row(r), c, rows);
         if (c < kc) cp_async16(dst, Xb + (long long)cid[r] * d + c * 8, true);
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
@@ -767,13 +769,14 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const bool vec = (k & 3) == 0 && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0;
     const int per = vec ? (k >> 2) : k;
     const int mtotal = nc * per;
+    const int per_sh = (per & (per - 1)) == 0 ? __ffs(per) - 1 : -1;
     // items are read kMB ahead through a rotating set of registers: the loop body (and its
     // hash probes) exists once in the code, and kMB loads per thread stay in flight
     constexpr int kMB = 4;
     auto load_item = [&](int idx) -> int4 {
         int4 r4 = make_int4(-1, -1, -1, -1);
         if (idx < mtotal) {
-            const int i = idx / per;
+            const int i = per_sh >= 0 ? idx >> per_sh : idx / per;
             const int32_t* row = ids + (long long)cid[i] * k;
             if (vec) r4 = reinterpret_cast<const int4*>(row)[idx - i * per];
             else r4.x = row[idx - i * per];
@@ -831,7 +834,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 #pragma unroll
         for (int u = 0; u + 1 < kMB; ++u) e4[u] = e4[u + 1];
         e4[kMB - 1] = load_item(idx + kMB * NT);
-        const int i = idx / per;
+        const int i = per_sh >= 0 ? idx >> per_sh : idx / per;
 #pragma unroll 1
         for (int q = 0; q < (vec ? 4 : 1); ++q) member(i, q == 0 ? cur.x : q == 1 ? cur.y : q == 2 ? cur.z : cur.w);
     }
@@ -934,7 +937,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     //    all loads of a step issued before the sums.
     //  - otherwise the canonical FP32 additions, from the staged tile when every staged row is
     //    exact (the same values), else from the FP32 rows in global memory.
-    constexpr int kStep = BYTES ? 16 : 8;
+    constexpr int kStep = BYTES ? 32 : 8;
     auto rerank = [&](int nq) {
         for (int q0 = 0; q0 < nq; q0 += kStep) {
             const int U = min(kStep, nq - q0);
@@ -944,30 +947,32 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
                 const int rpi = 32 / lpr;
                 const int sub = lane / lpr, part = lane & (lpr - 1);
                 const bool has = part < (d >> 4);
-                constexpr int kIt = 4;   // >= kStep * lpr / 32 for lpr <= 8
-                uint4 xa[kIt], xb[kIt];
-#pragma unroll
-                for (int t = 0; t < kIt; ++t) {
-                    const int pr = t * rpi + sub;
-                    xa[t] = make_uint4(0u, 0u, 0u, 0u);
-                    xb[t] = xa[t];
-                    if (pr < U && has) {
-                        const uint32_t e = wq[q0 + pr];
-                        xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
-                        xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
-                    }
-                }
+                // up to 32 / lpr pairs per warp load; loads in groups of four, issued before the sums
                 uint32_t mine = 0u;
+                for (int t0 = 0; t0 * rpi < U; t0 += 4) {
+                    uint4 xa[4], xb[4];
 #pragma unroll
-                for (int t = 0; t < kIt; ++t) {
-                    if (t * rpi < U) {
-                        uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
-                        dot = __dp4a(xa[t].y, xb[t].y, dot);
-                        dot = __dp4a(xa[t].z, xb[t].z, dot);
-                        dot = __dp4a(xa[t].w, xb[t].w, dot);
-                        for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
-                        const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
-                        if (lane / rpi == t) mine = got;
+                    for (int t = 0; t < 4; ++t) {
+                        const int pr = (t0 + t) * rpi + sub;
+                        xa[t] = make_uint4(0u, 0u, 0u, 0u);
+                        xb[t] = xa[t];
+                        if (pr < U && has) {
+                            const uint32_t e = wq[q0 + pr];
+                            xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
+                            xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if ((t0 + t) * rpi < U) {
+                            uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
+                            dot = __dp4a(xa[t].y, xb[t].y, dot);
+                            dot = __dp4a(xa[t].z, xb[t].z, dot);
+                            dot = __dp4a(xa[t].w, xb[t].w, dot);
+                            for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
+                            const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
+                            if (lane / rpi == t0 + t) mine = got;
+                        }
                     }
                 }
                 if (lane < U) {

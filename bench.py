@@ -224,11 +224,30 @@ def row_bytes(w) -> int:
     return 1 if ok else 4
 
 
+def measured_traffic():
+    """Per-launch DRAM bytes from the committed ncu capture (profiles/), keyed by kernel, when
+    the CUDA sources are still the ones it was taken with; else {} (the figures are stale)."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_sift_like_1M.json")
+    if not os.path.exists(path):
+        return {}
+    doc = json.load(open(path))
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        h.update(open(p, "rb").read())
+    return doc.get("bytes_per_launch", {}) if h.hexdigest() == doc.get("csrc_sha256") else {}
+
+
 def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w, graphs, cpu, peaks, stats, s_row):
     """Algorithmic work of one launch of a kernel / its mean event time (the stage models of
     the measurement plan: bytes a launch must move at least, flops it must do)."""
     N, d, k, M, R = w.N, w.d, w.k, w.M, w.R
-    out = {"kernel": kernel, "per_launch_ms": per_launch_ms, "traffic": None}
+    # DRAM bytes per launch from the ncu capture of the full workload (null when stale or when
+    # the workload is not the captured one)
+    traffic = measured_traffic().get(kernel) if N == 1_000_000 else None
+    out = {"kernel": kernel, "per_launch_ms": per_launch_ms, "traffic": traffic}
     hbm = dict(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), peak_kind="measured copy (hbm_gbs), of measured")
     if kernel == "k_cross_query" and cpu is not None:
         pq = cpu["stage_a_per_query"]

@@ -567,9 +567,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 constexpr int kTCThreads = 128;    // threads of the FP32-row variant (byte rows: 256)
 constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
-constexpr int kTCBloomBits = 4096; // bitmap of hashed candidate ids: most list entries skip the hash table
 
-__device__ __forceinline__ uint32_t bloom_bit(int32_t id) { return ((uint32_t)id * 0x9E3779B1u) >> 20; }
 
 __global__ void k_prep_bf16(const float* __restrict__ X, long long N, int d, __nv_bfloat16* __restrict__ Xb,
                             float4* __restrict__ tcm) {
@@ -620,13 +618,13 @@ __host__ __device__ __forceinline__ int tc_cand(int row) { return 4 * (row & 31)
 // Shared memory of one k_join_tc CTA (offsets from the first 1024-byte boundary of the
 // dynamic shared memory; `bytes` includes the slack for that alignment).
 struct TCLayout {
-    int op, rows_alloc, dpad, meta, colf, thr, pb_key, cid, hk, hv, bm, mask, queue, pb_tgt, misc, bytes, hs, words;
+    int op, rows_alloc, dpad, meta, colf, thr, pb_key, cid, hkv, mask, queue, pb_tgt, misc, bytes, hs, words;
 };
 
 __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     TCLayout l;
-    int hs = 64;
-    while (hs < 2 * cm) hs <<= 1;
+    int hs = 64;   // id -> index table, load factor <= 1/4: two probes find nearly every key
+    while (hs < 4 * cm) hs <<= 1;
     l.hs = hs;
     l.words = (cm + 31) >> 5;
     const int npad = ((cm + 15) / 16) * 16;
@@ -648,12 +646,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     o += kTCPropBuf * 8;
     l.cid = o;
     o += a16(cm * 4);
-    l.hk = o;
-    o += hs * 4;
-    l.hv = o;
-    o += hs * 4;
-    l.bm = o;
-    o += kTCBloomBits / 8;
+    l.hkv = o;
+    o += hs * 8;
     l.mask = o;
     o += a16(cm * l.words * 4);
     l.queue = o;
@@ -705,9 +699,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     float4* colf = reinterpret_cast<float4*>(smem + L.colf);   // P, worst distance, shard (bits), -
     uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
     int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
-    int32_t* hk = reinterpret_cast<int32_t*>(smem + L.hk);
-    int32_t* hv = reinterpret_cast<int32_t*>(smem + L.hv);
-    uint32_t* bm = reinterpret_cast<uint32_t*>(smem + L.bm);
+    int2* hkv = reinterpret_cast<int2*>(smem + L.hkv);   // (candidate id or -1, its index)
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     uint32_t* queue = reinterpret_cast<uint32_t*>(smem + L.queue);
     int32_t* pb_tgt = reinterpret_cast<int32_t*>(smem + L.pb_tgt);
@@ -731,8 +723,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 
     if (tid < nc) cid[tid] = cA;
     if (tid + NT < nc) cid[tid + NT] = cB;
-    for (int i = tid; i < hs; i += NT) hk[i] = -1;
-    for (int i = tid; i < kTCBloomBits / 32; i += NT) bm[i] = 0u;
+    for (int i = tid; i < hs; i += NT) hkv[i] = make_int2(-1, -1);
     for (int i = tid; i < nc * W; i += NT) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
     if (tid == 0) tc::mbar_init(mbar, 1);
@@ -787,12 +778,10 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 #pragma unroll
     for (int u = 0; u < kMB; ++u) e4[u] = load_item(tid + u * NT);
     auto insert = [&](int32_t c, int i) {
-        const uint32_t b = bloom_bit(c);
-        atomicOr(bm + (b >> 5), 1u << (b & 31));
         int slot = jhash(c, hs);
         for (int probe = 0; probe < hs; ++probe) {
-            if (atomicCAS(hk + slot, -1, c) == -1) {
-                hv[slot] = i;
+            if (atomicCAS(&hkv[slot].x, -1, c) == -1) {
+                hkv[slot].y = i;
                 return;
             }
             slot = (slot + 1) & (hs - 1);
@@ -811,32 +800,50 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     };
     if (tid < nc) put_meta(tid, cA, wiA, dkA, mA, invA);
     if (tid + NT < nc) put_meta(tid + NT, cB, wiB, dkB, mB, invB);
-    // membership bits: mask(i, j) = C[j] in N(C[i])
+    // membership bits: mask(i, j) = C[j] in N(C[i]). The lookup is straight-line: the key's home
+    // slot and the next one hold it (or an empty slot) for nearly every key at load <= 1/4, so
+    // the lanes of a warp stay together; a warp takes the probing loop only if one of its lanes
+    // met two other keys.
     auto member = [&](int i, int32_t e) {
-        if (e < 0) return;
-        const uint32_t b = bloom_bit(e);
-        if (!((bm[b >> 5] >> (b & 31)) & 1u)) return;
-        int slot = jhash(e, hs);
-        for (int probe = 0; probe < hs; ++probe) {
-            const int32_t h = hk[slot];
-            if (h == e) {
-                const int j = hv[slot];
-                atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
-                return;
-            }
-            if (h == -1) return;
-            slot = (slot + 1) & (hs - 1);
+        const int s0 = jhash(e, hs);
+        const int2 p0 = hkv[s0], p1 = hkv[(s0 + 1) & (hs - 1)];
+        int j = -1;
+        bool slow = false;
+        if (e >= 0) {
+            if (p0.x == e) j = p0.y;
+            else if (p1.x == e) j = p1.y;
+            else slow = p0.x != -1 && p1.x != -1;
         }
+        if (__any_sync(kFull, slow) && slow) {
+            int slot = (s0 + 2) & (hs - 1);
+            for (int probe = 2; probe < hs; ++probe) {
+                const int2 pp = hkv[slot];
+                if (pp.x == e) {
+                    j = pp.y;
+                    break;
+                }
+                if (pp.x == -1) break;
+                slot = (slot + 1) & (hs - 1);
+            }
+        }
+        if (j >= 0) atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
     };
+    // warp-uniform trip count (lanes past the end carry -1 entries), so the warp votes above
+    // always see all 32 lanes
 #pragma unroll 1
-    for (int idx = tid; idx < mtotal; idx += NT) {
+    for (int it = tid - lane; it < mtotal; it += NT) {
+        const int idx = it + lane;
         const int4 cur = e4[0];
 #pragma unroll
         for (int u = 0; u + 1 < kMB; ++u) e4[u] = e4[u + 1];
         e4[kMB - 1] = load_item(idx + kMB * NT);
         const int i = per_sh >= 0 ? idx >> per_sh : idx / per;
-#pragma unroll 1
-        for (int q = 0; q < (vec ? 4 : 1); ++q) member(i, q == 0 ? cur.x : q == 1 ? cur.y : q == 2 ? cur.z : cur.w);
+        member(i, cur.x);
+        if (vec) {
+            member(i, cur.y);
+            member(i, cur.z);
+            member(i, cur.w);
+        }
     }
     cp_async_wait<0>();
     tc::fence_async_smem();

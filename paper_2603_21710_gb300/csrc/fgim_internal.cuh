@@ -89,6 +89,18 @@ __device__ __forceinline__ int byte_lanes(int d) {
     const int c16 = d >> 4;
     return c16 <= 1 ? 1 : c16 <= 2 ? 2 : c16 <= 4 ? 4 : 8;
 }
+// log2 of byte_lanes(d)
+__device__ __forceinline__ int byte_lanes_log2(int d) {
+    const int c16 = d >> 4;
+    return c16 <= 1 ? 0 : c16 <= 2 ? 1 : c16 <= 4 ? 2 : 3;
+}
+// sum of v over the 2^lsh lanes of this lane's row group (lsh <= 3)
+__device__ __forceinline__ uint32_t row_group_sum(uint32_t v, int lsh) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        if (b < lsh) v += __shfl_xor_sync(0xffffffffu, v, 1 << b);
+    return v;
+}
 
 // ----------------------------------------------------------------------------
 // canonical distance (see the file comment); rows are 16-byte aligned float4 arrays

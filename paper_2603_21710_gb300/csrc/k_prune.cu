@@ -179,8 +179,9 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
     __syncwarp();
     // stage the rows: 32 / lpr rows per warp load, lanes of a row take 16 bytes each
     const int lpr = byte_lanes(d);
-    const int rpi = 32 / lpr;
-    const int sub = lane / lpr, part = lane & (lpr - 1);
+    const int rpi = 32 >> byte_lanes_log2(d);
+    const int lsh = byte_lanes_log2(d);
+    const int sub = lane >> lsh, part = lane & (lpr - 1);
     const bool has = part < (d >> 4);
     for (int r0 = 0; r0 < nv; r0 += 4 * rpi) {
         uint4 w[4];
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
             sq = __dp4a(w[q].y, w[q].y, sq);
             sq = __dp4a(w[q].z, w[q].z, sq);
             sq = __dp4a(w[q].w, w[q].w, sq);
-            for (int o = 1; o < lpr; o <<= 1) sq += __shfl_xor_sync(kFull, sq, o);
+            sq = row_group_sum(sq, lsh);
             if (r < nv) {
                 if (has) *reinterpret_cast<uint4*>(rows + (size_t)r * stride + 16 * part) = w[q];
                 if (part == 0) n2[r] = sq;

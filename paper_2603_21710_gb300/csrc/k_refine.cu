@@ -951,8 +951,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             float sc = 0.f;
             if constexpr (BYTES) {
                 const int lpr = byte_lanes(d);
-                const int rpi = 32 / lpr;
-                const int sub = lane / lpr, part = lane & (lpr - 1);
+                const int rpi = 32 >> byte_lanes_log2(d);
+                const int lsh = byte_lanes_log2(d), rsh = 5 - lsh;   // lpr = 1 << lsh, rpi = 1 << rsh
+                const int sub = lane >> lsh, part = lane & (lpr - 1);
                 const bool has = part < (d >> 4);
                 // up to 32 / lpr pairs per warp load; loads in groups of four, issued before the sums
                 uint32_t mine = 0u;
@@ -976,9 +977,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
                             dot = __dp4a(xa[t].y, xb[t].y, dot);
                             dot = __dp4a(xa[t].z, xb[t].z, dot);
                             dot = __dp4a(xa[t].w, xb[t].w, dot);
-                            for (int o = 1; o < lpr; o <<= 1) dot += __shfl_xor_sync(kFull, dot, o);
-                            const uint32_t got = __shfl_sync(kFull, dot, (lane % rpi) * lpr);
-                            if (lane / rpi == t0 + t) mine = got;
+                            dot = row_group_sum(dot, lsh);
+                            const uint32_t got = __shfl_sync(kFull, dot, (lane & (rpi - 1)) << lsh);
+                            if ((lane >> rsh) == t0 + t) mine = got;
                         }
                     }
                 }

@@ -109,8 +109,9 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
     const int nc4 = d >> 2;
     if constexpr (sizeof(RT) == 1) {
         const int lpr = byte_lanes(d);
-        const int rpi = 32 / lpr;   // rows per warp load
-        const int sub = lane / lpr, part = lane & (lpr - 1);
+        const int rpi = 32 >> byte_lanes_log2(d);   // rows per warp load
+        const int lsh = byte_lanes_log2(d), rsh = 5 - lsh;   // lpr = 1 << lsh, rpi = 1 << rsh
+        const int sub = lane >> lsh, part = lane & (lpr - 1);
         const bool has = part < (d >> 4);
         // rows in batches of four warp loads (all issued before the sums)
         uint32_t mine = 0u;
@@ -139,9 +140,9 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
                     } else {
                         sv = sq;
                     }
-                    for (int o = 1; o < lpr; o <<= 1) sv += __shfl_xor_sync(kFull, sv, o);
-                    const uint32_t got = __shfl_sync(kFull, sv, (lane % rpi) * lpr);
-                    if (lane / rpi == t0 + t) mine = got;
+                    sv = row_group_sum(sv, lsh);
+                    const uint32_t got = __shfl_sync(kFull, sv, (lane & (rpi - 1)) << lsh);
+                    if ((lane >> rsh) == t0 + t) mine = got;
                 }
             }
         }

@@ -89,6 +89,11 @@ __device__ __forceinline__ int byte_lanes(int d) {
     const int c16 = d >> 4;
     return c16 <= 1 ? 1 : c16 <= 2 ? 2 : c16 <= 4 ? 4 : 8;
 }
+// i / n for 0 <= i; 32-bit unsigned division when i fits (the usual case of per-entry grids
+// over N x R or N x k entries), else 64-bit
+__device__ __forceinline__ long long div_idx(long long i, int n) {
+    return i < 0x100000000LL ? (long long)((uint32_t)i / (uint32_t)n) : i / n;
+}
 // log2 of byte_lanes(d)
 __device__ __forceinline__ int byte_lanes_log2(int d) {
     const int c16 = d >> 4;

@@ -336,7 +336,7 @@ __global__ void k_e_fill(const int32_t* __restrict__ e_ids, const float* __restr
     const int32_t v = e_ids[i];
     if (v < 0) return;
     const int p = atomicAdd(fill + v, 1);
-    rev[off[v] + p] = mkkey(e_dist[i], (int32_t)(i / R));
+    rev[off[v] + p] = mkkey(e_dist[i], (int32_t)div_idx(i, R));
 }
 
 __global__ void __launch_bounds__(128) k_e_merge(const int32_t* __restrict__ e_ids, const float* __restrict__ e_dist,
@@ -432,8 +432,9 @@ __global__ void k_bfs_step(const int32_t* __restrict__ graph, int R, long long N
     int added = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nf * R;
          i += (long long)gridDim.x * blockDim.x) {
-        const int32_t x = fin[i / R];
-        const int32_t y = graph[(long long)x * R + (i % R)];
+        const long long fi = div_idx(i, R);
+        const int32_t x = fin[fi];
+        const int32_t y = graph[(long long)x * R + (i - fi * R)];
         if (y < 0 || y >= N) continue;
         if (visited[y] == 0 && atomicCAS(visited + y, 0, next_level) == 0) {
             fout[atomicAdd(st + (level + 1) % 3, 1)] = y;
@@ -469,7 +470,7 @@ __global__ void k_bfs_parents(const int32_t* __restrict__ graph, int R, long lon
                               int32_t* __restrict__ npar) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * R) return;
-    const int32_t lx = level[i / R];
+    const int32_t lx = level[div_idx(i, R)];
     if (lx == 0) return;
     const int32_t y = graph[i];
     if (y >= 0 && y < N && level[y] > lx) atomicAdd(npar + y, 1);
@@ -500,7 +501,7 @@ __global__ void k_cc_step(const int32_t* __restrict__ graph, int R, long long N,
                           int32_t* __restrict__ label, int32_t* __restrict__ changed) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * R) return;
-    const long long x = i / R;
+    const long long x = div_idx(i, R);
     if (visited[x]) return;
     const int32_t y = graph[i];
     if (y < 0 || y >= N || visited[y]) return;

@@ -65,7 +65,7 @@ __global__ void k_rev_fill(const int32_t* __restrict__ ids, const float* __restr
     if (i >= total) return;
     const int32_t v = ids[i];
     if (v < 0) return;
-    const int32_t u = (int32_t)(i / k);
+    const int32_t u = (int32_t)div_idx(i, k);
     const uint64_t key = mkkey(dist[i], u);
     if (flags[i] & FGIM_FLAG_NEW) {
         const int p = atomicAdd(fillN + v, 1);
@@ -1357,9 +1357,12 @@ __global__ void __launch_bounds__(128) k_prop_merge(const long long* __restrict_
         n += __popc(__ballot_sync(kFull, valid));
     }
     __syncwarp();
+    // A proposal of an id already in the list carries the list entry's key (the distance of a
+    // pair is the same wherever it is formed), so duplicates are found by key: a binary search
+    // of the sorted list instead of a scan over its ids.
     for (long long c0 = 0; c0 < m; c0 += 32) {
         const uint64_t key = (c0 + lane < m) ? sorted[b + c0 + lane] : kEmptyKey;
-        n = warp_merge<true>(list, aux, n, k, key, FGIM_FLAG_NEW);
+        n = warp_merge<false>(list, aux, n, k, key, FGIM_FLAG_NEW);
     }
     for (int s = lane; s < k; s += 32) {
         if (s < n) {

@@ -235,25 +235,13 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
     // every vertex is expanded at most once, so nt + 1 iterations always suffice
     bool done = false;
     for (long long it = 0; it <= nt; ++it) {
-        int first = -1, second = -1;
+        int first = -1;
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
             if (s < S && first < 0) {
                 const unsigned m = __ballot_sync(kFull, 32 * s + lane < n && !((expd >> s) & 1u));
-                if (m) {
-                    first = 32 * s + __ffs(m) - 1;
-                    const unsigned m2 = m & (m - 1);
-                    if (m2) second = 32 * s + __ffs(m2) - 1;
-                }
+                if (m) first = 32 * s + __ffs(m) - 1;
             }
-        }
-        // the entry after the one expanded now is often the next one expanded: start moving its
-        // adjacency row towards L1 while this expansion runs
-        if (second >= 0) {
-            const uint64_t sk = shfl64(pick_slot<MAXS>(pk, second >> 5), second & 31);
-            const long long u2 = (long long)key_id(sk) - id_off;
-            if (lane * 32 < M && u2 >= 0 && u2 < nt)
-                asm volatile("prefetch.global.L1 [%0];\n" ::"l"(adj + u2 * M + lane * 32));
         }
         if (first < 0) {
             done = true;

@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 constexpr int kTCThreads = 128;    // threads of the FP32-row variant (byte rows: 256)
 constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
+constexpr int kTCKChunk = 128;     // dimensions staged per K chunk of the Gram tile
 
 
 __global__ void k_prep_bf16(const float* __restrict__ X, long long N, int d, __nv_bfloat16* __restrict__ Xb,
@@ -631,7 +632,10 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     // rows per panel (a multiple of 8: whole swizzle atoms); sets of up to 128 candidates are
     // staged in the quarter-interleaved row order (tc_row), which spans all 128 rows
     l.rows_alloc = cm <= 128 ? 128 : npad;
-    l.dpad = ((d + 63) / 64) * 64;     // whole 128-byte panels (zero beyond d)
+    // K is staged in chunks of at most kTCKChunk dimensions (whole 128-byte panels, zero beyond d);
+    // the MMAs of successive chunks accumulate in TMEM, so d is not limited by shared memory
+    l.dpad = ((d + 63) / 64) * 64;
+    if (l.dpad > kTCKChunk) l.dpad = kTCKChunk;
     auto a16 = [](int x) { return (x + 15) & ~15; };
     int o = 0;
     l.op = o;
@@ -716,6 +720,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const int kcp = L.dpad >> 3;     // 16-byte chunks per staged row
     const int npad = ((nc + 15) / 16) * 16;   // MMA N
     const int kcp_sh = (kcp & (kcp - 1)) == 0 ? __ffs(kcp) - 1 : -1;   // shift for / kcp when a power of two
+    const int nch = (kc + kcp - 1) / kcp;   // K chunks
     const float g = (float)(d + 16) * 5.9604645e-8f;
     // squared L2 on exactly converted rows: lo = P_i + P_j - 2 D_ij with P = (1 - Cf) |x|^2
     // lies below (value - bound) of the general test (see the filter)
@@ -733,14 +738,18 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // past nc are never used, their products land in ignored rows and columns of D; chunks
     // past d are zero), this thread's candidates' worst keys and row statistics, and the
     // first batch of list entries for the membership bits.
-    for (int item = tid; item < nc * kcp; item += NT) {
-        const int r = kcp_sh >= 0 ? item >> kcp_sh : item / kcp;
-        const int c = item - r * kcp;
-        unsigned char* dst = op + tc::sw_offset(LARGE ? r : tc_row(r), c, rows);
-        if (c < kc) cp_async16(dst, Xb + (long long)cid[r] * d + c * 8, true);
-        else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    cp_async_commit();
+    auto stage = [&](int ch) {   // K chunk ch: 16-byte pieces ch * kcp .. ch * kcp + kcp - 1 of every row
+        for (int item = tid; item < nc * kcp; item += NT) {
+            const int r = kcp_sh >= 0 ? item >> kcp_sh : item / kcp;
+            const int c = item - r * kcp;
+            const int gc = ch * kcp + c;
+            unsigned char* dst = op + tc::sw_offset(LARGE ? r : tc_row(r), c, rows);
+            if (gc < kc) cp_async16(dst, Xb + (long long)cid[r] * d + gc * 8, true);
+            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        cp_async_commit();
+    };
+    stage(0);
     int32_t wiA = -1, wiB = -1;
     float dkA = 0.f, dkB = 0.f, invA = 1.f, invB = 1.f;
     float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), mB = mA;
@@ -852,19 +861,35 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const bool exact = misc[2] == 0;   // every staged row equals its FP32 row
-    if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16(128, LARGE ? npad : 128);
-        const uint32_t base = tc::smem_u32(op);
-        for (int s = 0; s < L.dpad / 16; ++s) {
-            const uint64_t desc = tc::smem_desc_sw128(base + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32));
-            tc::mma_bf16(tmem, desc, desc, idesc, s > 0 ? 1u : 0u);
+    // every row converted exactly to BF16 and the whole row fits one staged chunk: the re-rank
+    // may read the staged tile instead of the FP32 rows
+    const bool exact = misc[2] == 0 && nch == 1;
+    const bool exact_rows = misc[2] == 0;
+    bool ok_mma = true;
+    for (int ch = 0; ch < nch && ok_mma; ++ch) {
+        if (ch > 0) {
+            // the previous chunk's MMAs have completed (every thread saw its barrier phase), so
+            // the tile may be overwritten
+            stage(ch);
+            cp_async_wait<0>();
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
         }
-        tc::commit_to(mbar);
+        if (tid == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, LARGE ? npad : 128);
+            const uint32_t base = tc::smem_u32(op);
+            for (int s = 0; s < L.dpad / 16; ++s) {
+                const uint64_t desc = tc::smem_desc_sw128(base + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32));
+                tc::mma_bf16(tmem, desc, desc, idesc, (ch > 0 || s > 0) ? 1u : 0u);
+            }
+            tc::commit_to(mbar);
+        }
+        ok_mma = __syncthreads_and(tc::mbar_wait(mbar, (uint32_t)(ch & 1), 1 << 24)) != 0;
+        tc::fence_after_sync();
     }
-    const bool ok_mma = tc::mbar_wait(mbar, 0, 1 << 24);
     if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
-    tc::fence_after_sync();
 
     // Filter. A pair survives when lo, a lower bound of its exact value, can still beat the
     // worst key of a list it is not already in. General test: lo = value - bound with the
@@ -887,7 +912,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const float4 mr = r_ok ? meta[a] : make_float4(0.f, 0.f, 0.f, 1.f);
     const float n2r = mr.x, xr = mr.y, er = mr.z, cr = mr.w;
     const float xer = xr + er;
-    const bool fast = METRIC == FGIM_L2SQ && (BYTES || exact);
+    const bool fast = METRIC == FGIM_L2SQ && (BYTES || exact_rows);
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long my_pairs = 0;
     // survivor directions of pair {a, c} (bit 0: a's list gets c, bit 1: c's list gets a)

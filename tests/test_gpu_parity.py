@@ -56,6 +56,17 @@ def sift_like():
     return w, graphs, P, _inp(w, graphs)
 
 
+@pytest.fixture(scope="module")
+def high_dim():
+    """The d = 960 recipe (non-negative floats, 8 shards sized 1..8) at N = 6,000: the join's
+    Gram tile accumulates eight 128-dimension K chunks."""
+    from synth import gen, pgbuild
+    w = gen.make("fp8", N=6_000, nq=100)
+    graphs = pgbuild.build_all(w)
+    P = O.Problem.from_workload(w, graphs)
+    return w, graphs, P, _inp(w, graphs)
+
+
 # --------------------------------------------------------------------------- stage (a)
 def test_cross_query_small(small):
     import paper_2603_21710_gb300 as fg
@@ -390,3 +401,26 @@ def test_byte_rows_equal_fp32_rows(sift_like):
     mb = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, rows="fp32", join_filter="fp32")
     assert torch.equal(ma["ids"], mb["ids"]) and torch.equal(ma["deg"], mb["deg"])
     assert ma["entry"] == mb["entry"]
+
+
+def test_refine_pass_high_dim(high_dim):
+    """d = 960: the tensor-core filter over eight K chunks keeps the oracle's lists."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = high_dim
+    assert w.d == 960
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    st = fg.refine_pass(inp, g)
+    O.refine_iter(P, o)
+    bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)
+    assert len(bad) == 0, bad[:10]
+    assert st["join_pairs"] > 0
+
+
+def test_merge_high_dim(high_dim):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = high_dim
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2)
+    gi = _np(out["ids"])
+    PR.check_lists(gi, _np(out["dist"]), w.N)
+    assert PR.bfs_reached(gi, out["entry"]).all()

@@ -52,7 +52,10 @@ typedef enum {
 
 typedef enum { FGIM_L2SQ = 0, FGIM_IP = 1, FGIM_COSINE = 2 } fgim_metric;
 
-typedef enum { FGIM_F32 = 0 } fgim_dtype;
+/* Storage of the input vectors. BF16 vectors (bfloat16, round-to-nearest-even encodings of
+ * the values the caller means) are decoded once per call into an FP32 working copy on the
+ * device; every distance is that of the decoded values. */
+typedef enum { FGIM_F32 = 0, FGIM_BF16 = 1 } fgim_dtype;
 
 /* Size limits of the library. */
 #define FGIM_MAX_SHARDS 64
@@ -68,7 +71,7 @@ typedef enum { FGIM_F32 = 0 } fgim_dtype;
 
 /* One input index G_i (Sec. 2.1): its vectors X_i and its PG. */
 typedef struct {
-    const void* vectors;     /* [n, dim] row-major, dtype of the params, 16-byte aligned */
+    const void* vectors;     /* [n, dim] row-major in the params' dtype; 16-byte aligned (FP32), 2-byte (BF16) */
     const int32_t* adj;      /* [n, max_degree] LOCAL ids, -1 padded */
     int32_t n;               /* n_i >= 1 */
     int32_t max_degree;      /* 1 .. FGIM_MAX_DEGREE */
@@ -148,6 +151,18 @@ fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* p
                        fgim_knng* knng_out, fgim_graph* out, void* stream);
 
 /*
+ * n_merges independent merges with the same params (the batched form of the measurement
+ * plan: many small merges, e.g. one per tenant or time window). Merge m takes the h[m]
+ * shard descriptors shards[m] and writes outs[m] (n = sum of its shard sizes, R =
+ * params->R); no k-NNG is returned. The merges run one after another on the stream and share
+ * the scratch pool, so a batch costs one host call instead of n_merges. Stops at the first
+ * failing merge and returns its status; earlier outputs are complete, later ones untouched.
+ * fgim_last_stats() sums the counters of the merges run.
+ */
+fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, int32_t n_merges,
+                             const fgim_params* params, fgim_graph* outs, void* stream);
+
+/*
  * Same merge from and to HOST memory: copies the vectors and graphs in, merges, copies
  * the merged PG back. vectors_host: [sum n_i, dim] (shards consecutive in phi order);
  * adj_host: [sum n_i, max_degree] local ids; sizes/entries: [h]. out_ids_host [N, R],
@@ -191,7 +206,8 @@ fgim_status fgim_reach_fix(const fgim_shard* shards, int32_t h, const fgim_param
 
 /*
  * Alg. 1 over a merged graph for nq queries: pool `beam` (<= FGIM_MAX_L), returns the
- * first `topk` (<= beam) results. base: [n, dim] vectors in global-id order.
+ * first `topk` (<= beam) results. base: [n, dim] vectors in global-id order; base and
+ * queries are both in `dtype` (BF16 ones are decoded into FP32 scratch first).
  */
 fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                         const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,

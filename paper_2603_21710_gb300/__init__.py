@@ -18,7 +18,7 @@ import torch
 from . import _lib
 from ._lib import FgimError, KNNG, Graph, Params, Shard, check, last_stats, load  # noqa: F401
 
-__all__ = ["MergeInput", "merge", "merge_host", "cross_query", "refine_pass", "indegree_repair", "prune",
+__all__ = ["MergeInput", "merge", "merge_batch", "merge_host", "cross_query", "refine_pass", "indegree_repair", "prune",
            "reverse_insert", "reach_fix", "search", "last_stats", "load", "launch_count", "FgimError",
            "FLAG_NEW", "FLAG_REPLACED", "profiling"]
 
@@ -40,6 +40,18 @@ def _p(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+_VEC_DTYPES = {torch.float32: 0, torch.bfloat16: 1}
+
+
+def _vec(t: torch.Tensor, name: str) -> torch.Tensor:
+    """A vector tensor in one of the storages the library reads (FP32 or BF16)."""
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in _VEC_DTYPES:
+        raise ValueError(f"{name} must be float32 or bfloat16, got {t.dtype}")
+    return t.contiguous()
+
+
 def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -49,10 +61,11 @@ def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
 
 
 class MergeInput:
-    """The h input indexes: per-shard vectors [n_i, d] float32 and PGs [n_i, M_i] int32 (local ids).
+    """The h input indexes: per-shard vectors [n_i, d] float32 or bfloat16 and PGs [n_i, M_i] int32
+    (local ids).
 
     Shards are stored back to back in one [N, d] tensor ``X`` (phi order), so the library
-    never copies them.
+    never copies FP32 ones; BF16 ones are decoded into an FP32 working copy per call.
     """
 
     def __init__(self, vectors: Sequence[torch.Tensor], adjs: Sequence[torch.Tensor], entries: Sequence[int],
@@ -60,7 +73,10 @@ class MergeInput:
         if len(vectors) != len(adjs) or len(vectors) != len(entries):
             raise ValueError("vectors, adjs and entries must have one item per shard")
         self.metric = _lib.METRICS[metric]
-        vs = [_dev(v, torch.float32, "vectors") for v in vectors]
+        vs = [_vec(v, "vectors") for v in vectors]
+        if len({v.dtype for v in vs}) != 1:
+            raise ValueError("all shards must use the same vector dtype")
+        self.dtype = _VEC_DTYPES[vs[0].dtype]
         self.sizes = [int(v.shape[0]) for v in vs]
         self.d = int(vs[0].shape[1])
         self.X = vs[0] if len(vs) == 1 else torch.cat(vs, 0).contiguous()
@@ -91,7 +107,7 @@ class MergeInput:
     def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
                reach_beam=0, join_filter="tc", rows="auto") -> Params:
         p = Params()
-        p.dim, p.dtype, p.metric = self.d, 0, self.metric
+        p.dim, p.dtype, p.metric = self.d, self.dtype, self.metric
         p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap = k, R, float(alpha), L, iters, rev_cap
         p.ensure_reachable, p.reach_beam = int(bool(ensure_reachable)), reach_beam
         p.join_filter = JOIN_FILTERS[join_filter]
@@ -138,6 +154,36 @@ def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters
     return out
 
 
+def merge_batch(inputs: Sequence[MergeInput], k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3,
+                rev_cap: int = 0, ensure_reachable: bool = True, reach_beam: int = 0, join_filter="tc",
+                rows="auto") -> List[dict]:
+    """Independent merges with one set of params in one library call (fgim_merge_batch)."""
+    L_ = load()
+    inputs = list(inputs)
+    n = len(inputs)
+    if n == 0:
+        return []
+    if any((i.d, i.dtype, i.metric) != (inputs[0].d, inputs[0].dtype, inputs[0].metric) for i in inputs):
+        raise ValueError("all merges of a batch share dim, dtype and metric")
+    p = inputs[0].params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter, rows)
+    outs, graphs = [], (Graph * n)()
+    shard_ptrs = (ctypes.c_void_p * n)()
+    hs = (ctypes.c_int32 * n)()
+    for m, inp in enumerate(inputs):
+        dev = inp.X.device
+        o = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
+             "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
+             "deg": torch.empty((inp.N,), dtype=torch.int32, device=dev)}
+        graphs[m] = Graph(o["ids"].data_ptr(), o["dist"].data_ptr(), o["deg"].data_ptr(), inp.N, R, 0)
+        shard_ptrs[m] = ctypes.cast(inp._shards, ctypes.c_void_p)
+        hs[m] = inp.h
+        outs.append(o)
+    check(L_.fgim_merge_batch(shard_ptrs, hs, n, ctypes.byref(p), graphs, _stream()))
+    for m, o in enumerate(outs):
+        o["entry"] = int(graphs[m].entry)
+    return outs
+
+
 def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metric="l2", L: int = 0, iters: int = 3,
                rev_cap: int = 0, ensure_reachable: bool = True, out_ids=None, out_deg=None, join_filter="tc",
                rows="auto") -> dict:
@@ -147,11 +193,11 @@ def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metri
         raise ValueError("merge_host takes host tensors")
     X = X.contiguous()
     adj = adj.contiguous()
-    if X.dtype != torch.float32 or adj.dtype != torch.int32:
-        raise ValueError("X must be float32 and adj int32")
+    if X.dtype not in _VEC_DTYPES or adj.dtype != torch.int32:
+        raise ValueError("X must be float32 or bfloat16 and adj int32")
     N = int(X.shape[0])
     p = Params()
-    p.dim, p.dtype, p.metric = int(X.shape[1]), 0, _lib.METRICS[metric]
+    p.dim, p.dtype, p.metric = int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric]
     p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap, p.ensure_reachable = k, R, float(alpha), L, iters, rev_cap, int(
         bool(ensure_reachable))
     p.join_filter = JOIN_FILTERS[join_filter]
@@ -245,15 +291,19 @@ def reach_fix(inp: MergeInput, graph: dict, entry: int, k: int = 16, beam: int =
 
 def search(X: torch.Tensor, graph_ids: torch.Tensor, entry: int, queries: torch.Tensor, topk: int = 10,
            beam: int = 64, metric="l2"):
-    """Alg. 1 over a merged graph: returns (ids [nq, topk], dist)."""
+    """Alg. 1 over a merged graph: returns (ids [nq, topk], dist). X and queries are both float32
+    or both bfloat16."""
     L_ = load()
-    X = _dev(X, torch.float32, "X")
-    Q = _dev(queries, torch.float32, "queries")
+    X = _vec(X, "X")
+    Q = _vec(queries, "queries")
+    if Q.dtype != X.dtype:
+        raise ValueError("X and queries must have the same dtype")
     G = _dev(graph_ids, torch.int32, "graph_ids")
     nq = int(Q.shape[0])
     ids = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
     dist = torch.empty((nq, topk), dtype=torch.float32, device=X.device)
-    check(L_.fgim_search(_p(X), int(X.shape[0]), int(X.shape[1]), 0, _lib.METRICS[metric], _p(G), int(G.shape[1]),
+    check(L_.fgim_search(_p(X), int(X.shape[0]), int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric], _p(G),
+                         int(G.shape[1]),
                          int(entry), _p(Q), nq, topk, beam, _p(ids), _p(dist), _stream()))
     return ids, dist
 

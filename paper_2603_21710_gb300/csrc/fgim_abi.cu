@@ -224,7 +224,7 @@ static long long total_n(const fgim_shard* sh, int h) {
 static void check_params(const fgim_params* p, bool need_merge) {
     need(p != nullptr, FGIM_EINVAL, "params is NULL");
     need(p->dim >= 4 && p->dim <= FGIM_MAX_DIM && p->dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
-    need(p->dtype == FGIM_F32, FGIM_EUNSUPPORTED, "only FP32 vector storage is supported");
+    need(p->dtype == FGIM_F32 || p->dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
     need(p->metric == FGIM_L2SQ || p->metric == FGIM_IP || p->metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
     if (!need_merge) return;
     need(p->k >= 1 && p->k <= FGIM_MAX_K, FGIM_EINVAL, "k must be in [1, 128]");
@@ -244,14 +244,14 @@ static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
     long long n = 0;
     for (int i = 0; i < h; ++i) {
         need(sh[i].vectors != nullptr && sh[i].adj != nullptr, FGIM_EINVAL, "shard vectors/adj is NULL");
-        need(((uintptr_t)sh[i].vectors & 15u) == 0, FGIM_EINVAL, "shard vectors must be 16-byte aligned");
+        need(((uintptr_t)sh[i].vectors & (p->dtype == FGIM_F32 ? 15u : 1u)) == 0, FGIM_EINVAL,
+             "shard vectors must be 16-byte (FP32) or 2-byte (BF16) aligned");
         need(sh[i].n >= 1, FGIM_EINVAL, "shard n must be >= 1");
         need(sh[i].max_degree >= 1 && sh[i].max_degree <= FGIM_MAX_DEGREE, FGIM_EINVAL, "max_degree must be in [1, 128]");
         need(sh[i].entry >= 0 && sh[i].entry < sh[i].n, FGIM_EINVAL, "entry out of range");
         n += sh[i].n;
     }
     need(n < 0x7fffffffLL, FGIM_EINVAL, "total size must fit a 31-bit id");
-    (void)p;
 }
 
 static ShardTable make_table(const fgim_shard* sh, int h, int dim) {
@@ -271,8 +271,19 @@ static ShardTable make_table(const fgim_shard* sh, int h, int dim) {
     return t;
 }
 
-// vectors of all shards as one [N, dim] buffer (no copy when they are already consecutive)
-static const float* contiguous_vectors(Ctx& c, const fgim_shard* sh, int h, int dim, long long N) {
+// vectors of all shards as one FP32 [N, dim] buffer (no copy when they are FP32 and already
+// consecutive; BF16 vectors are decoded into a new buffer)
+static const float* contiguous_vectors(Ctx& c, const fgim_shard* sh, int h, int dim, int dtype, long long N) {
+    if (dtype == FGIM_BF16) {
+        float* X = c.alloc<float>(N * dim);
+        long long o = 0;
+        for (int i = 0; i < h; ++i) {
+            ck(launch_bf16_to_f32(static_cast<const uint16_t*>(sh[i].vectors), (long long)sh[i].n * dim, X + o * dim,
+                                  c.s));
+            o += sh[i].n;
+        }
+        return X;
+    }
     const char* base = static_cast<const char*>(sh[0].vectors);
     bool contiguous = true;
     long long o = 0;
@@ -319,7 +330,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.d = p->dim;
     P.metric = p->metric;
     P.t = make_table(sh, h, p->dim);
-    P.X = contiguous_vectors(c, sh, h, p->dim, P.N);
+    P.X = contiguous_vectors(c, sh, h, p->dim, p->dtype, P.N);
     P.inv = nullptr;
     P.X8 = nullptr;
     if (byte_rows_ok(P.d) && p->byte_rows == 0) {
@@ -739,6 +750,27 @@ fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* p
     return r;
 }
 
+fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, int32_t n_merges,
+                             const fgim_params* params, fgim_graph* outs, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        need(n_merges >= 0, FGIM_EINVAL, "n_merges must be >= 0");
+        need(n_merges == 0 || (shards && h && outs), FGIM_EINVAL, "shards, h or outs is NULL");
+        for (int m = 0; m < n_merges; ++m) {
+            check_shards(shards[m], h[m], params);
+            need(outs[m].ids && outs[m].dist && outs[m].deg, FGIM_EINVAL, "graph buffers are NULL");
+            need(outs[m].n == total_n(shards[m], h[m]) && outs[m].R == params->R, FGIM_EINVAL, "graph shape mismatch");
+        }
+        for (int m = 0; m < n_merges; ++m) {
+            Ctx c((cudaStream_t)stream);
+            merge_impl(c, shards[m], h[m], params, nullptr, &outs[m]);
+        }
+    });
+    end_call();
+    return r;
+}
+
 fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, const int32_t* sizes,
                             const int32_t* entries, int32_t h, int32_t max_degree, const fgim_params* params,
                             int32_t* out_ids_host, int32_t* out_deg_host, int32_t* out_entry_host, void* stream) {
@@ -757,14 +789,15 @@ fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, c
         need(N < 0x7fffffffLL, FGIM_EINVAL, "total size must fit a 31-bit id");
         Ctx c((cudaStream_t)stream);
         const int d = params->dim;
-        float* X = c.alloc<float>(N * d);
+        const size_t esz = params->dtype == FGIM_BF16 ? 2 : 4;
+        unsigned char* X = c.alloc<unsigned char>(N * d * (long long)esz);
         int32_t* A = c.alloc<int32_t>(N * max_degree);
-        ck(cudaMemcpyAsync(X, vectors_host, (size_t)N * d * 4, cudaMemcpyHostToDevice, c.s));
+        ck(cudaMemcpyAsync(X, vectors_host, (size_t)N * d * esz, cudaMemcpyHostToDevice, c.s));
         ck(cudaMemcpyAsync(A, adj_host, (size_t)N * max_degree * 4, cudaMemcpyHostToDevice, c.s));
         std::vector<fgim_shard> sh(h);
         long long o = 0;
         for (int i = 0; i < h; ++i) {
-            sh[i].vectors = X + o * d;
+            sh[i].vectors = X + o * d * (long long)esz;
             sh[i].adj = A + o * max_degree;
             sh[i].n = sizes[i];
             sh[i].max_degree = max_degree;
@@ -797,17 +830,27 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
         need(base && graph_ids && queries && out_ids && out_dist, FGIM_EINVAL, "NULL buffer");
         need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
         need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
-        need(dtype == FGIM_F32, FGIM_EUNSUPPORTED, "only FP32 vector storage is supported");
+        need(dtype == FGIM_F32 || dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
         need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
         need(R >= 1 && R <= FGIM_MAX_DEGREE, FGIM_EINVAL, "R must be in [1, 128]");
         need(entry >= 0 && entry < n, FGIM_EINVAL, "entry out of range");
         need(nq >= 0, FGIM_EINVAL, "nq must be >= 0");
         need(beam >= 1 && beam <= FGIM_MAX_L && topk >= 1 && topk <= beam, FGIM_EINVAL, "need 1 <= topk <= beam <= 128");
-        need(((uintptr_t)base & 15u) == 0 && ((uintptr_t)queries & 15u) == 0, FGIM_EINVAL, "vectors must be 16-byte aligned");
+        const uintptr_t am = dtype == FGIM_F32 ? 15u : 1u;
+        need(((uintptr_t)base & am) == 0 && ((uintptr_t)queries & am) == 0, FGIM_EINVAL,
+             "vectors must be 16-byte (FP32) or 2-byte (BF16) aligned");
         if (nq == 0) return;
         Ctx c((cudaStream_t)stream);
         const float* X = static_cast<const float*>(base);
         const float* Q = static_cast<const float*>(queries);
+        if (dtype == FGIM_BF16) {
+            float* Xf = c.alloc<float>(n * dim);
+            float* Qf = c.alloc<float>((long long)nq * dim);
+            ck(launch_bf16_to_f32(static_cast<const uint16_t*>(base), n * dim, Xf, c.s));
+            ck(launch_bf16_to_f32(static_cast<const uint16_t*>(queries), (long long)nq * dim, Qf, c.s));
+            X = Xf;
+            Q = Qf;
+        }
         float* inv = nullptr;
         float* qinv = nullptr;
         if (metric == FGIM_COSINE) {

@@ -27,6 +27,8 @@ cudaError_t scan_counts(const int32_t* in, long long n, long long* out, void* sc
                         cudaStream_t s);
 size_t scan_scratch_bytes(long long n);
 cudaError_t launch_inv_norms(const float* X, long long n, int d, float* inv, cudaStream_t s);
+// out[i] = the FP32 value of the bfloat16 encoding in[i]
+cudaError_t launch_bf16_to_f32(const uint16_t* in, long long n, float* out, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s);
 // indices i (ascending) with flag[i] != 0, written to out; count to *count (device)
 cudaError_t compact_flags(const int32_t* flag, long long n, int32_t* out, long long* offsets_scratch,

@@ -1,4 +1,6 @@
 // Small building blocks: exclusive scans, compaction by flags, fills, inverse norms.
+#include <algorithm>
+
 #include "fgim_launch.h"
 
 namespace fgim {
@@ -146,6 +148,19 @@ cudaError_t launch_inv_norms(const float* X, long long n, int d, float* inv, cud
     if (n <= 0) return cudaSuccess;
     LaunchScope ls("k_inv_norms", s);
     k_inv_norms<<<(unsigned)cdiv(n * 32, 256), 256, 0, s>>>(X, n, d, inv);
+    return cudaGetLastError();
+}
+
+__global__ void k_bf16_to_f32(const uint16_t* __restrict__ in, long long n, float* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = __uint_as_float((uint32_t)in[i] << 16);
+}
+
+cudaError_t launch_bf16_to_f32(const uint16_t* in, long long n, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_bf16_to_f32", s);
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 32);
+    k_bf16_to_f32<<<(unsigned)blocks, 256, 0, s>>>(in, n, out);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ METRIC_COS = 2
 @dataclasses.dataclass
 class Workload:
     name: str
-    X: np.ndarray            # [N, d] float32 (or uint16 bf16 bits when dtype == "bf16"), phi order
+    X: np.ndarray            # [N, d] float32, phi order (BF16-representable values when dtype == "bf16")
     Q: np.ndarray            # [nq, d] float32 queries from the same distribution
     shard_sizes: List[int]
     metric: int
@@ -64,6 +64,11 @@ class Workload:
     def shard(self, i: int) -> np.ndarray:
         o = self.offsets
         return self.X[o[i]:o[i + 1]]
+
+    def bits(self) -> np.ndarray:
+        """The stored BF16 encodings of X (exact: X holds BF16-representable values)."""
+        assert self.dtype == "bf16"
+        return (self.X.view(np.uint32) >> 16).astype(np.uint16)
 
 
 def _streams(seed: int, n: int = 4):
@@ -155,6 +160,50 @@ def fp8(seed: int = MASTER_SEED, N: int = 1_000_000, d: int = 960, nq: int = 10_
                     M=32, ef=128, k=64, R=48, alpha=1.0, perm=perm)
 
 
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """float32 -> nearest BF16 value (round to nearest, ties to even), returned as float32.
+
+    Storage step of the batched recipe; the inputs are finite, so the NaN case is not handled.
+    """
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return (b.astype(np.uint32) << 16).view(np.float32)
+
+
+def batched_one(seed: int = MASTER_SEED, N: int = 20_000, h: int = 3, d: int = 768, nq: int = 1000,
+                n_centers: int = 500) -> Workload:
+    """One merge of the batched form: 500 centers N(0, I_d), per-cluster per-dimension sigma
+    U[0.1, 1.0] (anisotropic; the spread is not given, this is the stated reading), normalised,
+    stored in BF16 (round to nearest even); cosine. Shards: a random split, sizes as equal as
+    possible."""
+    r_c, r_p, r_s, r_q = _streams(seed)
+    centers = r_c.standard_normal((n_centers, d))
+    sig = r_c.uniform(0.1, 1.0, size=(n_centers, d))
+
+    def draw(rng, n):
+        x = _mixture(rng, centers, n, sig)
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+        return bf16_round(x.astype(np.float32))
+
+    X = draw(r_p, N)
+    Q = draw(r_q, nq)
+    sizes = _equal_sizes(N, h)
+    perm = _split(r_s, N, sizes)
+    return Workload("batched", np.ascontiguousarray(X[perm]), Q, sizes, METRIC_COS,
+                    M=24, ef=96, k=32, R=24, alpha=1.0, perm=perm, dtype="bf16")
+
+
+def batched(seed: int = MASTER_SEED, n_merges: int = 64, n_lo: int = 10_000, n_hi: int = 200_000, d: int = 768,
+            nq: int = 1000) -> List[Workload]:
+    """The batched form: n_merges independent merges, h ~ U{2..6}, total size log-uniform in
+    [n_lo, n_hi]; each merge drawn by ``batched_one`` from its own seed."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 4])))
+    hs = rng.integers(2, 7, size=n_merges)
+    Ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=n_merges)).astype(np.int64)
+    seeds = rng.integers(0, 2**31 - 1, size=n_merges)
+    return [batched_one(int(seeds[m]), N=int(Ns[m]), h=int(hs[m]), d=d, nq=nq) for m in range(n_merges)]
+
+
 def _equal_sizes(N: int, h: int) -> List[int]:
     base = N // h
     sizes = [base] * h
@@ -163,7 +212,7 @@ def _equal_sizes(N: int, h: int) -> List[int]:
     return sizes
 
 
-RECIPES = {"small": small, "medium": medium, "precision": precision, "fp8": fp8}
+RECIPES = {"small": small, "medium": medium, "precision": precision, "fp8": fp8, "batched_one": batched_one}
 
 
 def make(name: str, seed: int = MASTER_SEED, **kw) -> Workload:

@@ -16,7 +16,8 @@ def close(a, b, rtol=RTOL, atol=ATOL):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     both_inf = np.isinf(a) & np.isinf(b)
-    return both_inf | (np.abs(a - b) <= rtol * np.maximum(np.abs(a), np.abs(b)) + atol)
+    with np.errstate(invalid="ignore"):  # inf - inf is covered by both_inf
+        return both_inf | (np.abs(a - b) <= rtol * np.maximum(np.abs(a), np.abs(b)) + atol)
 
 
 def row_matches(gi, gd, oi, od, rtol=RTOL, atol=ATOL) -> bool:
@@ -74,7 +75,8 @@ def check_lists(ids, dist, N, allow_self=False):
     s = np.sort(np.where(valid, ids, -1 - np.arange(ids.shape[1])[None, :]), 1)
     assert not np.any((s[:, 1:] == s[:, :-1]) & (s[:, 1:] >= 0)), "duplicate id in a row"
     d = np.where(valid, dist, np.inf)
-    dd = np.diff(d, axis=1)
+    with np.errstate(invalid="ignore"):  # inf - inf past the valid prefix; masked below
+        dd = np.diff(d, axis=1)
     ii = np.diff(ids, axis=1)
     both = valid[:, 1:]
     ok = (dd > 0) | ((dd == 0) & (ii > 0)) | ~both

@@ -424,3 +424,86 @@ def test_merge_high_dim(high_dim):
     gi = _np(out["ids"])
     PR.check_lists(gi, _np(out["dist"]), w.N)
     assert PR.bfs_reached(gi, out["entry"]).all()
+
+
+# --------------------------------------------------------------------------- BF16 storage, batches
+@pytest.fixture(scope="module")
+def bf16_batch():
+    """Three merges of the batched form (d = 768, cosine, BF16 storage) at 2,000..4,000 points."""
+    from synth import gen, pgbuild
+    out = []
+    for w in gen.batched(n_merges=3, n_lo=2_000, n_hi=4_000, nq=100):
+        graphs = pgbuild.build_all(w)
+        out.append((w, graphs, O.Problem.from_workload(w, graphs)))
+    return out
+
+
+def _inp_bf16(w, graphs):
+    import paper_2603_21710_gb300 as fg
+    dev = _dev()
+    Xb = torch.from_numpy(w.bits().view(np.int16)).to(dev).view(torch.bfloat16)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    return fg.MergeInput.from_flat(Xb, w.shard_sizes, adj, [g[1] for g in graphs], metric="cos")
+
+
+def test_bf16_storage_decodes_exactly(bf16_batch):
+    """BF16 storage is decoded to the FP32 values it encodes: the merge equals the FP32 merge of
+    those values bit for bit, and its k-NNG stages keep the oracle's lists on them."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P = bf16_batch[0]
+    ib = _inp_bf16(w, graphs)
+    assert ib.X.dtype == torch.bfloat16
+    i32 = _inp(w, graphs)
+    a = fg.merge(ib, k=w.k, R=w.R, alpha=w.alpha, iters=2, return_knng=True)
+    b = fg.merge(i32, k=w.k, R=w.R, alpha=w.alpha, iters=2, return_knng=True)
+    assert torch.equal(a["ids"], b["ids"]) and torch.equal(a["dist"], b["dist"])
+    assert torch.equal(a["knng"]["ids"], b["knng"]["ids"]) and a["entry"] == b["entry"]
+    # stage (b) on the BF16 input against the oracle on the decoded values
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    fg.refine_pass(ib, g)
+    O.refine_iter(P, o)
+    bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)
+    assert len(bad) == 0, bad[:10]
+    # search over BF16 base and queries equals search over their FP32 values
+    Qb = torch.from_numpy((w.Q.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)).to(_dev()).view(torch.bfloat16)
+    sa, da = fg.search(ib.X, a["ids"], a["entry"], Qb, topk=10, beam=64, metric="cos")
+    sb, db = fg.search(i32.X, a["ids"], a["entry"], torch.from_numpy(w.Q).to(_dev()), topk=10, beam=64, metric="cos")
+    assert torch.equal(sa, sb) and torch.equal(da, db)
+
+
+def test_merge_bf16_end_to_end(bf16_batch):
+    """The whole merge on BF16 cosine input: valid lists, every vertex reachable, k-NNG and
+    search recall within 0.5 point of the oracle's merge."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P = bf16_batch[1]
+    ib = _inp_bf16(w, graphs)
+    out = fg.merge(ib, k=w.k, R=w.R, alpha=w.alpha, iters=3, return_knng=True)
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=3)
+    gi = _np(out["ids"])
+    PR.check_lists(gi, _np(out["dist"]), w.N)
+    assert PR.bfs_reached(gi, out["entry"]).all()
+    assert out["entry"] == ref.entry
+    samp = np.random.default_rng(5).choice(w.N, 500, replace=False)
+    tid, _ = O.knn_exact(w.X, w.X[samp], w.k, w.metric, exclude=samp)
+    kg = _np(out["knng"]["ids"])
+    assert abs(O.recall_at(kg[samp], tid, w.k) - O.recall_at(ref.knn_ids[samp], tid, w.k)) <= 0.005
+    gt, _ = O.knn_exact(w.X, w.Q, 10, w.metric)
+    sg, _ = fg.search(_inp(w, graphs).X, out["ids"], out["entry"], torch.from_numpy(w.Q).to(_dev()), topk=10,
+                      beam=64, metric="cos")
+    so, _, _ = O.search(w.X, ref.ids, ref.entry, w.Q, 64, 10, w.metric)
+    assert abs(O.recall_at(_np(sg), gt, 10) - O.recall_at(so, gt, 10)) <= 0.01
+
+
+def test_merge_batch_equals_single_merges(bf16_batch):
+    """fgim_merge_batch gives each merge exactly what a call of its own gives."""
+    import paper_2603_21710_gb300 as fg
+    inps = [_inp_bf16(w, graphs) for w, graphs, _ in bf16_batch]
+    w0 = bf16_batch[0][0]
+    outs = fg.merge_batch(inps, k=w0.k, R=w0.R, alpha=w0.alpha, iters=2)
+    assert len(outs) == len(inps)
+    for inp, o in zip(inps, outs):
+        s = fg.merge(inp, k=w0.k, R=w0.R, alpha=w0.alpha, iters=2)
+        assert torch.equal(o["ids"], s["ids"]) and torch.equal(o["dist"], s["dist"])
+        assert torch.equal(o["deg"], s["deg"]) and o["entry"] == s["entry"]
+    assert fg.merge_batch([], k=w0.k, R=w0.R) == []

@@ -440,3 +440,20 @@ def test_merge_thread_count_independent(small_problem):
     b = O.merge(P4, w.k, w.R, w.alpha, iters=1)
     assert np.array_equal(a.ids, b.ids) and np.array_equal(a.dist, b.dist)
     assert np.array_equal(a.knn_ids, b.knn_ids)
+
+
+def test_batched_recipe_bf16_storage():
+    """The batched recipe's storage step is BF16 round-to-nearest-even (torch's conversion) and
+    its vectors are unit-norm up to that rounding."""
+    import torch
+    from synth import gen
+    x = np.random.default_rng(1).standard_normal(50_000).astype(np.float32) * 3
+    assert np.array_equal(gen.bf16_round(x), torch.from_numpy(x).to(torch.bfloat16).float().numpy())
+    assert gen.bf16_round(np.array([1.0 + 2.0 ** -8], np.float32))[0] == 1.0          # tie -> even
+    assert gen.bf16_round(np.array([1.0 + 3 * 2.0 ** -8], np.float32))[0] == 1.0 + 2.0 ** -6  # tie -> even (up)
+    w = gen.batched_one(N=500, h=4, d=64, nq=10)
+    assert w.dtype == "bf16" and w.metric == gen.METRIC_COS and w.shard_sizes == [125] * 4
+    assert np.array_equal(gen.bf16_round(w.X), w.X)
+    assert np.abs(np.linalg.norm(w.X.astype(np.float64), axis=1) - 1).max() < 4 * 2.0 ** -8
+    hs = [wk.h for wk in gen.batched(n_merges=12, n_lo=100, n_hi=400, d=16, nq=4)]
+    assert min(hs) >= 2 and max(hs) <= 6

@@ -224,20 +224,34 @@ def row_bytes(w) -> int:
     return 1 if ok else 4
 
 
-def measured_traffic():
-    """Per-launch DRAM bytes from the committed ncu capture (profiles/), keyed by kernel, when
-    the CUDA sources are still the ones it was taken with; else {} (the figures are stale)."""
-    import glob
+# the sources each captured kernel family is compiled from (its own file plus the shared headers)
+TRAFFIC_SOURCES = {
+    "k_cross_query": ["k_search.cu"],
+    "k_join": ["k_refine.cu", "tc_sm100.cuh"],
+    "k_prune": ["k_prune.cu"],
+}
+
+
+def kernel_sources_sha256(kernel: str) -> str:
     import hashlib
+    h = hashlib.sha256()
+    for f in sorted(TRAFFIC_SOURCES[kernel] + ["fgim_internal.cuh", "fgim_launch.h"]):
+        h.update(f.encode())
+        h.update(open(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """Per-launch DRAM bytes from the committed ncu capture (profiles/), keyed by kernel family,
+    for the families whose sources are still the ones the capture was taken with (a family
+    whose kernel changed since is left out: its figure is stale)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_sift_like_1M.json")
     if not os.path.exists(path):
         return {}
     doc = json.load(open(path))
-    h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", "*"))):
-        h.update(os.path.basename(p).encode())
-        h.update(open(p, "rb").read())
-    return doc.get("bytes_per_launch", {}) if h.hexdigest() == doc.get("csrc_sha256") else {}
+    shas = doc.get("sources_sha256", {})
+    return {k: v for k, v in doc.get("bytes_per_launch", {}).items()
+            if k in TRAFFIC_SOURCES and shas.get(k) == kernel_sources_sha256(k)}
 
 
 def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w, graphs, cpu, peaks, stats, s_row):

@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
 // re-ranked with the canonical FP32 distance (from the staged rows when every one of them
 // converted exactly, else from the FP32 rows); only exact keys are proposed.
 constexpr int kTCThreads = 128;    // threads of the FP32-row variant (byte rows: 256)
-constexpr int kTCQueue = 2048;     // filter survivors of one vertex (more: the vertex is redone)
+constexpr int kTCQueue = 1024;     // filter survivors in flight per CTA (each warp re-ranks its share when full)
 constexpr int kTCPropBuf = 256;    // proposals buffered per CTA
 constexpr int kTCKChunk = 128;     // dimensions staged per K chunk of the Gram tile
 
@@ -627,8 +627,9 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     int hs = 64;   // id -> index table, load factor <= 1/4: two probes find nearly every key
     while (hs < 4 * cm) hs <<= 1;
     l.hs = hs;
-    l.words = (cm + 31) >> 5;
     const int npad = ((cm + 15) / 16) * 16;
+    // membership bits per TMEM lane row in TMEM column order: 128 columns (interleaved order) or npad
+    l.words = cm <= 128 ? 4 : (npad + 31) >> 5;
     // rows per panel (a multiple of 8: whole swizzle atoms); sets of up to 128 candidates are
     // staged in the quarter-interleaved row order (tc_row), which spans all 128 rows
     l.rows_alloc = cm <= 128 ? 128 : npad;
@@ -652,8 +653,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
     o += a16(cm * 4);
     l.hkv = o;
     o += hs * 8;
-    l.mask = o;
-    o += a16(cm * l.words * 4);
+    l.mask = o;   // two bit matrices (directions A and B), min(cm, 128) rows of `words` words
+    o += 2 * (cm < 128 ? cm : 128) * l.words * 4;
     l.queue = o;
     o += kTCQueue * 4;
     l.pb_tgt = o;
@@ -729,7 +730,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     if (tid < nc) cid[tid] = cA;
     if (tid + NT < nc) cid[tid + NT] = cB;
     for (int i = tid; i < hs; i += NT) hkv[i] = make_int2(-1, -1);
-    for (int i = tid; i < nc * W; i += NT) mask[i] = 0u;
+    const int mrows = cm < 128 ? cm : 128;
+    uint32_t* maskB = mask + mrows * W;
+    for (int i = tid; i < 2 * mrows * W; i += NT) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tmem_slot, tmem_cols);
@@ -809,7 +812,11 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     };
     if (tid < nc) put_meta(tid, cA, wiA, dkA, mA, invA);
     if (tid + NT < nc) put_meta(tid + NT, cB, wiB, dkB, mB, invB);
-    // membership bits: mask(i, j) = C[j] in N(C[i]). The lookup is straight-line: the key's home
+    // membership bits, per TMEM lane row a and TMEM column c of candidate b (col(b)):
+    //   A (mask):  bit (a, col(b)) = C[b] in N(C[a])  (a's list already holds b)
+    //   B (maskB): bit (a, col(b)) = C[a] in N(C[b])  (b's list already holds a)
+    // so the filter reads the bits of 16 consecutive columns with one shared-memory load.
+    // List entry C[j] of N(C[i]) sets A (i, col(j)) and B (j, col(i)). The lookup is straight-line: the key's home
     // slot and the next one hold it (or an empty slot) for nearly every key at load <= 1/4, so
     // the lanes of a warp stay together; a warp takes the probing loop only if one of its lanes
     // met two other keys.
@@ -835,7 +842,11 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
                 slot = (slot + 1) & (hs - 1);
             }
         }
-        if (j >= 0) atomicOr(mask + i * W + (j >> 5), 1u << (j & 31));
+        if (j >= 0) {
+            const int cj = LARGE ? j : tc_row(j), ci = LARGE ? i : tc_row(i);
+            if (!LARGE || i < 128) atomicOr(mask + i * W + (cj >> 5), 1u << (cj & 31));
+            if (!LARGE || j < 128) atomicOr(maskB + j * W + (ci >> 5), 1u << (ci & 31));
+        }
     };
     // warp-uniform trip count (lanes past the end carry -1 entries), so the warp votes above
     // always see all 32 lanes
@@ -915,38 +926,28 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const bool fast = METRIC == FGIM_L2SQ && (BYTES || exact_rows);
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long my_pairs = 0;
-    // survivor directions of pair {a, c} (bit 0: a's list gets c, bit 1: c's list gets a)
-    auto test = [&](int c, float dot) -> unsigned {
-        const float4 cc = colf[c];
-        if (shr == __float_as_int(cc.z)) return 0u;
-        ++my_pairs;
-        float lo;
-        if (fast) {
-            lo = fmaf(-2.f, dot, Pr + cc.x);
+    // TMEM address of this warp's lane quarter
+    auto trow_of = [&](int w) -> uint32_t { return tmem + ((uint32_t)(32 * (w & 3)) << 16); };
+    // lo, a lower bound of the exact value of pair {a, b}, from its Gram entry
+    auto lower = [&](int b, float dot, const float4& cc) -> float {
+        if (fast) return fmaf(-2.f, dot, Pr + cc.x);
+        const float4 mc = meta[b];
+        const float cs = er * mc.y + mc.z * xer + g * xer * (mc.y + mc.z);
+        float val, bound;
+        if (METRIC == FGIM_L2SQ) {
+            const float s2 = n2r + mc.x;
+            val = s2 - 2.f * dot;
+            bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
+                            4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
+        } else if (METRIC == FGIM_IP) {
+            val = 1.f - dot;
+            bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
         } else {
-            const float4 mc = meta[c];
-            const float cs = er * mc.y + mc.z * xer + g * xer * (mc.y + mc.z);
-            float val, bound;
-            if (METRIC == FGIM_L2SQ) {
-                const float s2 = n2r + mc.x;
-                val = s2 - 2.f * dot;
-                bound = 1.1f * (2.f * cs + g * s2 + (2.f * 5.9604645e-8f + g) * fabsf(val) +
-                                4.f * 5.9604645e-8f * (s2 + 2.f * fabsf(dot)));
-            } else if (METRIC == FGIM_IP) {
-                val = 1.f - dot;
-                bound = 1.1f * (cs + g * fabsf(val)) + 2.4e-7f;
-            } else {
-                const float ccv = cr * mc.w;
-                val = 1.f - dot * ccv;
-                bound = 1.1f * (cs * ccv + g * fabsf(val)) + 4.8e-7f;
-            }
-            lo = val - bound;
+            const float ccv = cr * mc.w;
+            val = 1.f - dot * ccv;
+            bound = 1.1f * (cs * ccv + g * fabsf(val)) + 4.8e-7f;
         }
-        if (!(lo <= fmaxf(tdr, cc.y))) return 0u;
-        unsigned dm = 0u;
-        if (lo <= tdr && !((mask[a * W + (c >> 5)] >> (c & 31)) & 1u)) dm |= 1u;
-        if (lo <= cc.y && !((mask[c * W + (a >> 5)] >> (a & 31)) & 1u)) dm |= 2u;
-        return dm;
+        return val - bound;
     };
     // survivors go to this warp's own segment of the queue (a register count, no atomics)
     const int seg = kTCQueue / NW;
@@ -1122,56 +1123,86 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             }
         }
     };
-    // Filter and re-rank interleaved: a column group adds at most 128 survivors to the warp's
-    // segment, so the segment is re-ranked and emptied whenever fewer than 128 slots are left,
-    // and once more when the columns are done; no survivor is ever dropped.
+    // Filter, one block of 16 TMEM columns at a time: every lane tests its pairs of the block
+    // in registers (lo against the worst keys, cross-shard, valid pair) and keeps two bit masks
+    // of directions (bit j: column j; A: a's list may take b, B: b's list may take a), minus the
+    // membership bits of the block; only the survivors go to the warp's queue segment, which is
+    // re-ranked and emptied whenever fewer than 32 slots are left, and once more at the end.
+    // c0: first column, jn: columns in the block (warp-uniform), b0 + bstep j: candidate of
+    // column c0 + j, vm: this lane's valid pairs.
+    auto block = [&](int c0, int jn, int b0, int bstep, unsigned vm) {
+        float dv[16];
+        tc::tmem_ld16(trow_of(warp) + (uint32_t)c0, dv);
+        unsigned dA = 0u, dB = 0u, xs = 0u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j >= jn) break;
+            const int b = b0 + bstep * j;
+            const float4 cc = colf[b];
+            const float lo = lower(b, dv[j], cc);
+            const bool xsh = shr != __float_as_int(cc.z);
+            if (xsh) xs |= 1u << j;
+            if (xsh && lo <= tdr) dA |= 1u << j;
+            if (xsh && lo <= cc.y) dB |= 1u << j;
+        }
+        my_pairs += __popc(xs & vm);
+        if (r_ok) {   // drop the directions whose list already holds the other candidate
+            const int wo = a * W + (c0 >> 5), sh = c0 & 16;
+            dA &= ~(mask[wo] >> sh);
+            dB &= ~(maskB[wo] >> sh);
+        }
+        dA &= vm;
+        dB &= vm;
+        unsigned sv = dA | dB;
+        while (__any_sync(kFull, sv != 0u)) {
+            if (qn > seg - 32) {
+                rerank(qn);
+                qn = 0;
+            }
+            unsigned dm = 0u;
+            int b = 0;
+            if (sv) {
+                const int j = __ffs(sv) - 1;
+                sv &= sv - 1;
+                b = b0 + bstep * j;
+                dm = ((dA >> j) & 1u) | (((dB >> j) & 1u) << 1);
+            }
+            append(b, dm);
+        }
+    };
     if (ok_mma) {
-        // Column ranges: interleaved order (up to 128 candidates): for each residue q the
-        // columns 32 q .. 32 q + |{b < nn : b % 4 = q}| - 1 hold the new candidates b = 4 m + q;
-        // natural order: columns 0 .. min(nn, 32 (w % 4) + 31) - 1, then 128 .. nc - 1 for the
-        // lanes of new candidates. The NW / 4 warps of a lane quarter take every (NW / 4)-th
-        // group of four columns of a range.
-        const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        const int cstep = 4 * (NW / 4);
-        const int half = 4 * (warp >> 2);
-        const int nranges = LARGE ? ((nc > 128 && 32 * (warp & 3) < nn) ? 2 : 1) : 4;
-        int range = 0, c0 = 0, cend = 0;
-        auto begin = [&](int rg) {
-            if (LARGE) {
-                c0 = (rg == 0 ? 0 : 128) + half;
-                cend = rg == 0 ? min(nn, 32 * (warp & 3) + 31) : nc;
-            } else {
-                c0 = 32 * rg + half;
-                cend = 32 * rg + (nn > rg ? (nn - rg + 3) >> 2 : 0);
+        // Column ranges. Interleaved order (up to 128 candidates): range rg = columns
+        // 32 rg + m', m' < |{b < nn : b % 4 = rg}|, candidate b = 4 m' + rg; lane (a = 4 lane + q)
+        // pairs with b < a, i.e. m' < lane + [rg < q]. Natural order: columns b < min(nn, 32 q + 31)
+        // with b < a, then, for lanes of new candidates, columns 128 .. nc - 1. The NW / 4 warps
+        // of a lane quarter take every (NW / 4)-th block of the quarter's ranges.
+        // Within a range the blocks go round-robin over those warps, starting one warp further on
+        // in each range, so the short last blocks of the ranges land on different warps.
+        const int q = warp & 3;
+        const int hw = warp >> 2;
+        int rot = 0;
+        auto run = [&](int cbase, int ccount, int bbase, int bstep, int lim) {
+            int gb = rot++;
+            for (int t0 = 0; t0 < ccount; t0 += 16, ++gb) {
+                if (gb % (NW / 4) != hw) continue;
+                const int nvp = min(max(lim - t0, 0), 16);
+                block(cbase + t0, min(16, ccount - t0), bbase + bstep * t0, bstep,
+                      nvp >= 16 ? 0xFFFFu : (1u << nvp) - 1u);
             }
         };
-        begin(0);
-        while (true) {
-            while (qn <= seg - 128) {
-                if (c0 >= cend) {
-                    if (range + 1 < nranges) {
-                        begin(++range);
-                        continue;
-                    }
-                    break;
-                }
-                float dv[4];
-                tc::tmem_ld4(trow + (uint32_t)c0, dv);
-#pragma unroll
-                for (int t4 = 0; t4 < 4; ++t4) {
-                    const int c = c0 + t4;   // TMEM column
-                    if (c < cend) {
-                        const int b = LARGE ? c : tc_cand(c);
-                        const bool pair = (LARGE && range == 1) ? a < nn : (r_ok && b < a);
-                        append(b, pair ? test(b, dv[t4]) : 0u);
-                    }
-                }
-                c0 += cstep;
+        if (LARGE) {
+            const int cend0 = min(nn, 32 * q + 31);
+            run(0, cend0, 0, 1, r_ok ? min(a, cend0) : 0);
+            if (32 * q < nn) run(128, nc - 128, 128, 1, a < nn ? nc - 128 : 0);
+        } else {
+#pragma unroll 1
+            for (int rg = 0; rg < 4; ++rg) {
+                const int cnt = nn > rg ? (nn - rg + 3) >> 2 : 0;
+                run(32 * rg, cnt, rg, 4, r_ok ? min(cnt, lane + (rg < q ? 1 : 0)) : 0);
             }
-            rerank(qn);
-            qn = 0;
-            if (c0 >= cend && range + 1 >= nranges) break;
         }
+        rerank(qn);
+        qn = 0;
     }
     tc::fence_before_sync();
     __syncthreads();

@@ -180,9 +180,11 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
 // global ids (local + id_off). The pool C (<= L <= 32 * MAXS keys, sorted by (delta, id))
 // lives in registers: entry e = 32 s + lane is pk[s] of that lane, its "expanded" mark bit s
 // of expd. Candidates that cannot beat the worst entry of a full pool are never inserted.
-// MAXS = 1 (L <= 32) inserts a batch at once: each candidate's rank among the pool and among
-// the other candidates, each pool entry's shift, one scatter through shared memory (pool,
-// pflag). Larger pools insert one candidate at a time (one ballot for its rank, one shift).
+// MAXS = 1 (L <= 32) inserts a batch at once: each candidate's rank among the pool (a
+// binary search of the shared-memory copy, which holds the pool in slots 0 .. n - 1 and empty
+// keys after) and among the other candidates, each pool entry's shift, one scatter through
+// shared memory (pool, pflag). Larger pools insert one candidate at a time (one ballot for its
+// rank, one shift).
 // Returns the pool size and leaves the pool in pool[0 .. size).
 // scratch: 32 ints of shared memory for the compacted neighbour ids.
 constexpr int kPoolSlots = 4;
@@ -207,6 +209,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
     const int S = MAXS == 1 ? 1 : (L + 31) >> 5;
     for (int s = lane; s < H; s += 32) ht[s] = -1;
     if (lane == 0) scratch[0] = ep;
+    if (MAXS == 1) pool[lane] = kEmptyKey;   // slots past the pool size stay empty
     __syncwarp();
     if (ep < 0 || ep >= nt || L < 1 || S > MAXS || (MAXS == 1 && L > 32)) {
         if (lane == 0) atomicOr(status, kErrBounds);
@@ -227,6 +230,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             ht[ht_slot(ep, htbits)] = ep;
             ctr.ndc++;
             pk[0] = key;
+            pool[0] = key;
         }
         n = 1;
         if (L == 1) worst = shfl64(key, 0);
@@ -258,6 +262,8 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
                 atomicOr(status, kErrBounds);
                 v = -1;
             }
+            // a neighbour listed twice is evaluated once (the lowest lane keeps it)
+            if ((__match_any_sync(kFull, v) & lt) != 0u) v = -1;
             if (v >= 0) {
                 const int s = ht_slot(v, htbits);
                 if (ht[s] == v) v = -1;
@@ -279,29 +285,32 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             __syncwarp();
             bool valid = cand < worst;
             if constexpr (MAXS == 1) {
+                if (__ballot_sync(kFull, valid) == 0u) continue;
+                // rank of the candidate among the pool entries (pool[e] is the empty key for
+                // e >= n): five halving steps over the 32 slots. A valid candidate ranks below
+                // slot 31 (it beats the worst entry of a full pool, or the pool has empty slots).
+                // An equal entry means it is pooled already (the lossy visited table let it in).
+                int pos = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1)
+                    if (pool[pos + st - 1] < cand) pos += st;
+                if (valid && pool[pos] == cand) valid = false;
                 unsigned vm = __ballot_sync(kFull, valid);
                 if (vm == 0u) continue;
-                const bool in_pool = lane < n;
-                int shift = 0, crank = 0, mypos = 0;
+                const int added = __popc(vm);
+                // the candidates are distinct: rank among them, and each pool entry's shift
+                int crank = 0, shift = 0;
                 while (vm) {
                     const int j = __ffs(vm) - 1;
                     vm &= vm - 1;
-                    if (!__shfl_sync(kFull, valid, j)) continue;   // dropped as a duplicate
                     const uint64_t cj = shfl64(cand, j);
-                    if (__any_sync(kFull, in_pool && pk[0] == cj)) {   // already in the pool
-                        if (lane == j) valid = false;
-                        continue;
-                    }
-                    if (valid && lane > j && cand == cj) valid = false;   // a later copy of the same key
-                    if (in_pool && cj < pk[0]) ++shift;
-                    if (valid && lane != j && cj < cand) ++crank;
-                    const int pos = __popc(__ballot_sync(kFull, in_pool && pk[0] < cj));
-                    if (lane == j) mypos = pos;
+                    crank += cj < cand ? 1 : 0;
+                    shift += cj < pk[0] ? 1 : 0;
                 }
-                const int added = __popc(__ballot_sync(kFull, valid));
-                if (added == 0) continue;
-                // merged order: pool entry e goes to e + shift, a candidate to mypos + crank
-                const int pe = lane + shift, pc = mypos + crank;
+                // merged order: pool entry e goes to e + shift, a candidate to pos + crank
+                const bool in_pool = lane < n;
+                const int pe = lane + shift, pc = pos + crank;
+                __syncwarp();
                 if (in_pool && pe < L) {
                     pool[pe] = pk[0];
                     pflag[pe] = (uint8_t)(expd & 1u);
@@ -312,7 +321,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
                 }
                 __syncwarp();
                 n = n + added < L ? n + added : L;
-                pk[0] = lane < n ? pool[lane] : kEmptyKey;
+                pk[0] = pool[lane];
                 expd = lane < n ? (unsigned)pflag[lane] : 0u;
                 __syncwarp();
                 if (n == L) worst = shfl64(pk[0], L - 1);
@@ -404,10 +413,12 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
     int o = 0;
     w.q = o;
     o += align16(d * 4);
+    // the pool holds at least 32 slots: a one-slot register pool searches all 32 for a rank
+    const int ps = L < 32 ? 32 : L;
     w.pool = o;
-    o += align16(L * 8);
+    o += align16(ps * 8);
     w.pflag = o;
-    o += align16(L);
+    o += align16(ps);
     w.ht = o;
     o += align16((1 << htbits) * 4);
     w.res = o;

@@ -44,7 +44,7 @@ class _Input(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int32),
                 ("metric", ctypes.c_int32), ("h", ctypes.c_int32), ("off", ctypes.c_void_p),
                 ("adj", ctypes.c_void_p), ("M", ctypes.c_int32), ("entry", ctypes.c_void_p),
-                ("nthreads", ctypes.c_int32)]
+                ("nthreads", ctypes.c_int32), ("valid", ctypes.c_void_p)]
 
 
 def compile_lib(force: bool = False) -> str:
@@ -77,6 +77,7 @@ def lib():
                 "or_reverse_insert": (None, [i64, i32, vp, vp, vp, vp, vp, vp]),
                 "or_reach_fix": (None, [vp, i32, i32, i32, vp, vp, vp, vp]),
                 "or_merged_entry": (i32, [vp]),
+                "or_phi": (i64, [vp, vp]),
                 "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
                 "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
             }
@@ -94,18 +95,23 @@ def _p(a: Optional[np.ndarray]):
 
 @dataclass
 class Problem:
-    """The merge input: vectors in phi order plus the h input PGs (local ids)."""
+    """The merge input: vectors in shard order plus the h input PGs (local ids), and optionally
+    the validity of every vertex (the boolean part of phi, Sec. 4.1.3)."""
     X: np.ndarray          # [N, d] float32
     sizes: List[int]
     adj: np.ndarray        # [N, M] int32 local ids
     entry: np.ndarray      # [h] int32 local
     metric: int
     nthreads: int = 0
+    valid: Optional[np.ndarray] = None   # [N] bool / uint8; None = every vertex valid
 
     def __post_init__(self):
         self.X = np.ascontiguousarray(self.X, dtype=np.float32)
         self.adj = np.ascontiguousarray(self.adj, dtype=np.int32)
         self.entry = np.ascontiguousarray(self.entry, dtype=np.int32)
+        if self.valid is not None:
+            self.valid = np.ascontiguousarray(self.valid, dtype=np.uint8)
+            assert self.valid.shape == (self.X.shape[0],)
         off = [0]
         for s in self.sizes:
             off.append(off[-1] + int(s))
@@ -113,11 +119,30 @@ class Problem:
         assert self.off[-1] == self.X.shape[0] == self.adj.shape[0]
         self._in = _Input(self.X.ctypes.data, self.X.shape[0], self.X.shape[1], self.metric, len(self.sizes),
                           self.off.ctypes.data, self.adj.ctypes.data, self.adj.shape[1],
-                          self.entry.ctypes.data, self.nthreads)
+                          self.entry.ctypes.data, self.nthreads, _p(self.valid))
 
     @property
     def N(self):
         return int(self.X.shape[0])
+
+    @property
+    def N_valid(self) -> int:
+        return self.N if self.valid is None else int(np.count_nonzero(self.valid))
+
+    def phi(self) -> np.ndarray:
+        """[N] global id of every vertex in the merged index, -1 for invalid ones."""
+        out = np.empty(self.N, np.int32)
+        lib().or_phi(self.ref, out.ctypes.data)
+        return out
+
+    def compact(self) -> "Problem":
+        """The valid vertices alone, renumbered by phi: the problem stages (b) and (c) see.
+        Its input PGs are not carried (those stages do not read them)."""
+        keep = np.ones(self.N, bool) if self.valid is None else self.valid.astype(bool)
+        sizes = [int(np.count_nonzero(keep[self.off[i]:self.off[i + 1]])) for i in range(self.h)]
+        Nv = int(sum(sizes))
+        return Problem(self.X[keep], sizes, np.full((Nv, 1), -1, np.int32), np.zeros(self.h, np.int32),
+                       self.metric, self.nthreads)
 
     @property
     def h(self):
@@ -178,7 +203,8 @@ class KNNG:
 
 
 def stage_a(P: Problem, k: int, L: int = 0):
-    g = KNNG(P.N, k)
+    """Alg. 2; with validity the k-NNG has one row per valid vertex, in phi order."""
+    g = KNNG(P.N_valid, k)
     st = Stats()
     Lu = lib().or_stage_a(P.ref, k, L, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data, ctypes.byref(st))
     return g, int(Lu), st.as_dict()
@@ -244,6 +270,7 @@ def reach_fix(P: Problem, o_ids, o_dist, o_deg, entry, beam: int = 64):
 
 
 def merged_entry(P: Problem) -> int:
+    """Entry of the merged graph (a global id after phi)."""
     return int(lib().or_merged_entry(P.ref))
 
 
@@ -261,6 +288,8 @@ class MergeResult:
 
 def merge(P: Problem, k: int, R: int, alpha: float, L: int = 0, iters: int = 3, rev_cap: int = 0,
           ensure_reachable: bool = True) -> MergeResult:
+    if P.valid is not None:
+        return _merge_valid(P, k, R, alpha, L, iters, rev_cap, ensure_reachable)
     N = P.N
     o_ids = np.empty((N, R), np.int32)
     o_dist = np.empty((N, R), np.float32)
@@ -273,6 +302,25 @@ def merge(P: Problem, k: int, R: int, alpha: float, L: int = 0, iters: int = 3, 
                         o_dist.ctypes.data, o_deg.ctypes.data, entry.ctypes.data, k_ids.ctypes.data,
                         k_dist.ctypes.data, ctypes.byref(st))
     return MergeResult(o_ids, o_dist, o_deg, int(entry[0]), k_ids, k_dist, int(Lu), st.as_dict())
+
+
+def _merge_valid(P: Problem, k, R, alpha, L, iters, rev_cap, ensure_reachable) -> MergeResult:
+    """The merge with invalid vertices: Alg. 2 over the input PGs with phi dropping invalid
+    vertices, then the stages of ``or_merge`` in the same order on the valid vertices alone."""
+    g, Lu, st = stage_a(P, k, L)
+    Pc = P.compact()
+    T = None
+    for _ in range(iters):
+        refine_iter(Pc, g, rev_cap)
+        T, _ = indegree_repair(Pc, g)
+    if iters <= 0:
+        T = indegree(g.ids)
+    e_ids, e_dist, e_cnt, _ = prune(Pc, g, T, R, alpha)
+    o_ids, o_dist, o_deg = reverse_insert(e_ids, e_dist, e_cnt)
+    entry = merged_entry(P)
+    if ensure_reachable:
+        reach_fix(Pc, o_ids, o_dist, o_deg, entry, 64)
+    return MergeResult(o_ids, o_dist, o_deg, entry, g.ids.copy(), g.dist.copy(), Lu, st)
 
 
 def search(X, g_ids, entry, Q, beam, topk, metric, nthreads=0):

@@ -23,6 +23,12 @@
  *  - Alg. 5 keeps v when T(v) = 1 or delta(u,v) < alpha^2 * delta(w,v) for every kept w
  *    (alpha-RNG on squared-type distances), stops at R, and adds reverse edges taken from the
  *    pruned snapshot only.
+ *  - phi with invalid vertices (Sec. 4.1.3): valid vertices are numbered consecutively in
+ *    (shard, local id) order. Alg. 2 runs for valid u only; Alg. 1 searches the input PG
+ *    unchanged (invalid vertices route and may fill the pool), and phi then drops invalid
+ *    vertices from C_i^+(u) and from the search results before the top-k. The merged entry
+ *    is the entry of the shard with the most valid vertices if valid, else that shard's
+ *    first valid vertex.
  */
 #include "fgim_oracle.h"
 
@@ -213,10 +219,19 @@ static int32_t minimum_L(int32_t k, int32_t h) {
     return (k + (h - 1) - 1) / (h - 1);
 }
 
+int64_t or_phi(const or_input* in, int32_t* phi) {
+    int64_t n = 0;
+    for (int64_t g = 0; g < in->off[in->h]; ++g) phi[g] = (!in->valid || in->valid[g]) ? (int32_t)n++ : -1;
+    return n;
+}
+
 int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float* dist, uint8_t* flags,
                    or_stats* st) {
     const int32_t h = in->h;
     if (L <= 0) L = minimum_L(k, h);
+    /* phi: identity when every vertex is valid */
+    int32_t* phi = (int32_t*)malloc(sizeof(int32_t) * (in->off[h] > 0 ? in->off[h] : 1));
+    or_phi(in, phi);
     int64_t max_n = 0;
     for (int s = 0; s < h; ++s)
         if (in->off[s + 1] - in->off[s] > max_n) max_n = in->off[s + 1] - in->off[s];
@@ -234,6 +249,8 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
         memset(&ls, 0, sizeof(ls));
 #pragma omp for schedule(dynamic, 16)
         for (int64_t g = 0; g < in->off[h]; ++g) {
+            if (phi[g] < 0) continue;   /* no row for an invalid vertex */
+            const int64_t o = phi[g];   /* its row of the k-NNG */
             int i = shard_of(in, g);
             int64_t u = g - in->off[i];
             int32_t n = 0;
@@ -242,7 +259,8 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
                 int32_t v = in->adj[g * in->M + t];
                 if (v < 0 || v == u) continue;
                 int64_t gv = in->off[i] + v;
-                C[n].id = (int32_t)gv;
+                if (phi[gv] < 0) continue;
+                C[n].id = phi[gv];
                 C[n].d = dist_g(in, g, gv);
                 ls.ndc++;
                 ++n;
@@ -261,7 +279,9 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
                                               in->adj + in->off[j] * in->M, in->M, in->entry[j],
                                               row(in, g), L, L, seen, tag, rid, rd, &ls);
                 for (int32_t t = 0; t < r; ++t) {
-                    C[n].id = (int32_t)(in->off[j] + rid[t]);
+                    const int32_t mapped = phi[in->off[j] + rid[t]];
+                    if (mapped < 0) continue;
+                    C[n].id = mapped;
                     C[n].d = rd[t];
                     ++n;
                 }
@@ -272,17 +292,17 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
             for (int32_t t = 0; t < n && w < k; ++t) {
                 int dup = 0;
                 for (int32_t s = 0; s < w; ++s)
-                    if (ids[g * k + s] == C[t].id) { dup = 1; break; }
+                    if (ids[o * k + s] == C[t].id) { dup = 1; break; }
                 if (dup) continue;
-                ids[g * k + w] = C[t].id;
-                dist[g * k + w] = C[t].d;
-                flags[g * k + w] = OR_FLAG_NEW;
+                ids[o * k + w] = C[t].id;
+                dist[o * k + w] = C[t].d;
+                flags[o * k + w] = OR_FLAG_NEW;
                 ++w;
             }
             for (; w < k; ++w) {
-                ids[g * k + w] = -1;
-                dist[g * k + w] = INFINITY;
-                flags[g * k + w] = 0;
+                ids[o * k + w] = -1;
+                dist[o * k + w] = INFINITY;
+                flags[o * k + w] = 0;
             }
         }
         ndc += ls.ndc;
@@ -296,6 +316,7 @@ int32_t or_stage_a(const or_input* in, int32_t k, int32_t L, int32_t* ids, float
         st->ndc += ndc;
         st->hops += hops;
     }
+    free(phi);
     return L;
 }
 
@@ -810,10 +831,24 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
 }
 
 int32_t or_merged_entry(const or_input* in) {
+    /* the shard with the most valid vertices (lowest index on ties) */
     int best = 0;
-    for (int s = 1; s < in->h; ++s)
-        if (in->off[s + 1] - in->off[s] > in->off[best + 1] - in->off[best]) best = s;
-    return (int32_t)(in->off[best] + in->entry[best]);
+    int64_t best_n = -1;
+    for (int s = 0; s < in->h; ++s) {
+        int64_t nv = 0;
+        for (int64_t g = in->off[s]; g < in->off[s + 1]; ++g) nv += (!in->valid || in->valid[g]) ? 1 : 0;
+        if (nv > best_n) {
+            best = s;
+            best_n = nv;
+        }
+    }
+    /* its entry mapped by phi, else its first valid vertex */
+    int32_t* phi = (int32_t*)malloc(sizeof(int32_t) * (in->off[in->h] > 0 ? in->off[in->h] : 1));
+    or_phi(in, phi);
+    int32_t e = phi[in->off[best] + in->entry[best]];
+    for (int64_t g = in->off[best]; e < 0 && g < in->off[best + 1]; ++g) e = phi[g];
+    free(phi);
+    return e;
 }
 
 int32_t or_merge(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,

@@ -19,6 +19,10 @@
  *   k-NNG    ids [N, k] int32 (-1 empty), dist [N, k] float32 (+inf empty),
  *            flags [N, k] uint8 (bit0 new, bit1 replaced), each row sorted
  *            ascending by (dist, id) with the empty slots last.
+ *   valid    optional [N] uint8 (NULL = every vertex valid): the boolean part of
+ *            the ID mapping phi of Sec. 4.1.3. Valid vertices take consecutive
+ *            global ids in (shard, local id) order; invalid ones get no row and
+ *            never appear as a neighbour, but stay in their input PG for routing.
  */
 #ifndef FGIM_ORACLE_H
 #define FGIM_ORACLE_H
@@ -42,6 +46,7 @@ typedef struct {
     int32_t M;
     const int32_t* entry;  /* [h] local */
     int32_t nthreads;      /* 0 = OpenMP default */
+    const uint8_t* valid;  /* [N] or NULL; honoured by or_stage_a and or_merged_entry */
 } or_input;
 
 typedef struct {
@@ -98,6 +103,9 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
 
 /* Global id of the merged entry point: phi(entry of the largest shard, lowest shard index on ties). */
 int32_t or_merged_entry(const or_input* in);
+/* phi of Sec. 4.1.3 from in->valid: phi[g] = global id of g in the merged index or -1.
+ * Returns the number of valid vertices. */
+int64_t or_phi(const or_input* in, int32_t* phi);
 
 /* Full merge: stage a, iters x (refine + repair), prune, reverse insertion, reachability fix. */
 int32_t or_merge(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,

@@ -457,3 +457,89 @@ def test_batched_recipe_bf16_storage():
     assert np.abs(np.linalg.norm(w.X.astype(np.float64), axis=1) - 1).max() < 4 * 2.0 ** -8
     hs = [wk.h for wk in gen.batched(n_merges=12, n_lo=100, n_hi=400, d=16, nq=4)]
     assert min(hs) >= 2 and max(hs) <= 6
+
+
+# --------------------------------------------------------------------------- phi with invalid vertices
+def _small_problem(N=900, h=3, seed=7):
+    from synth import gen, pgbuild
+    w = gen.small(seed=seed, N=N, d=8, h=h, nq=4)
+    graphs = pgbuild.build_all(w)
+    return w, O.Problem.from_workload(w, graphs)
+
+
+def _with_valid(P, valid):
+    return O.Problem(P.X, P.sizes, P.adj, P.entry, P.metric, valid=valid)
+
+
+def test_phi_numbers_valid_vertices_in_shard_order():
+    """Sec. 4.1.3: phi gives the valid vertices consecutive ids in (shard, local id) order."""
+    w, P = _small_problem()
+    valid = np.random.default_rng(1).random(P.N) < 0.7
+    phi = _with_valid(P, valid).phi()
+    assert np.array_equal(phi[~valid], np.full((~valid).sum(), -1))
+    assert np.array_equal(phi[valid], np.arange(valid.sum()))
+    assert np.array_equal(_with_valid(P, None).phi(), np.arange(P.N))
+
+
+def test_all_valid_mask_is_the_plain_merge():
+    w, P = _small_problem()
+    a = O.merge(P, w.k, w.R, w.alpha, iters=2)
+    b = O.merge(_with_valid(P, np.ones(P.N, np.uint8)), w.k, w.R, w.alpha, iters=2)
+    assert np.array_equal(a.ids, b.ids) and np.array_equal(a.dist, b.dist)
+    assert np.array_equal(a.knn_ids, b.knn_ids) and a.entry == b.entry
+
+
+def test_fully_invalid_shard_equals_merge_without_it():
+    """A shard whose every vertex is invalid contributes nothing: with the same L the merge
+    equals the merge of the other shards (its searches return only vertices phi drops)."""
+    w, P = _small_problem(N=900, h=3)
+    valid = np.ones(P.N, np.uint8)
+    valid[P.off[2]:] = 0
+    a = O.merge(_with_valid(P, valid), w.k, w.R, w.alpha, L=8, iters=2)
+    n2 = int(P.off[2])
+    P2 = O.Problem(P.X[:n2], P.sizes[:2], P.adj[:n2], P.entry[:2], P.metric)
+    b = O.merge(P2, w.k, w.R, w.alpha, L=8, iters=2)
+    assert a.ids.shape == (n2, w.R)
+    assert np.array_equal(a.knn_ids, b.knn_ids) and np.array_equal(a.knn_dist, b.knn_dist)
+    assert np.array_equal(a.ids, b.ids) and np.array_equal(a.deg, b.deg) and a.entry == b.entry
+
+
+def test_masked_cross_query_filters_the_unmasked_candidates():
+    """With k >= M + (h - 1) L nothing is cut by the top-k, so the masked k-NNG row of a valid
+    vertex is its unmasked row with the invalid ids removed and the rest renumbered by phi."""
+    w, P = _small_problem(N=600, h=3)
+    L = 4
+    k = P.adj.shape[1] + (P.h - 1) * L
+    valid = np.random.default_rng(3).random(P.N) < 0.6
+    Pv = _with_valid(P, valid)
+    phi = Pv.phi()
+    full, _, _ = O.stage_a(P, k, L)
+    part, _, _ = O.stage_a(Pv, k, L)
+    assert part.ids.shape == (int(valid.sum()), k)
+    for g in np.nonzero(valid)[0]:
+        ids, dist = full.ids[g], full.dist[g]
+        keep = (ids >= 0) & valid[np.maximum(ids, 0)]
+        want = phi[ids[keep]]
+        row = part.ids[phi[g]]
+        assert np.array_equal(row[:len(want)], want), g
+        assert np.all(row[len(want):] == -1)
+        assert np.array_equal(part.dist[phi[g]][:len(want)], dist[keep])
+    assert np.all(part.ids < valid.sum())
+
+
+def test_merged_entry_with_invalid_entry():
+    """The entry is the entry of the shard with the most valid vertices (lowest index on ties)
+    if valid, else that shard's first valid vertex."""
+    w, P = _small_problem(N=901, h=3)          # shard sizes 301, 300, 300
+    assert list(P.sizes) == [301, 300, 300]
+    valid = np.ones(P.N, np.uint8)
+    valid[P.off[0] + P.entry[0]] = 0           # shard 0 keeps 300 valid vertices: still first on the tie
+    Pv = _with_valid(P, valid)
+    phi = Pv.phi()
+    first_valid = phi[P.off[0]:P.off[1]][phi[P.off[0]:P.off[1]] >= 0][0]
+    assert O.merged_entry(Pv) == first_valid == 0
+    valid2 = np.ones(P.N, np.uint8)
+    valid2[P.off[0]:P.off[0] + 200] = 0        # shard 0 now has the fewest valid vertices
+    valid2[P.off[2]:P.off[2] + 10] = 0         # and shard 1 the most
+    Pv2 = _with_valid(P, valid2)
+    assert O.merged_entry(Pv2) == Pv2.phi()[P.off[1] + P.entry[1]]

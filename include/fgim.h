@@ -77,6 +77,14 @@ typedef struct {
     int32_t max_degree;      /* 1 .. FGIM_MAX_DEGREE */
     int32_t entry;           /* entry point ep_i (local id) */
     int32_t reserved;
+    /* Optional [n] device bytes, NULL = every vertex valid: the boolean part of the ID mapping
+     * phi (Sec. 4.1.3), for merges with deleted vertices or with copies that another shard
+     * already holds. A vertex with valid[v] == 0 gets no row in the merged index and is never
+     * anybody's neighbour, but stays in its input PG: the cross-query searches still route
+     * through it. The valid vertices take consecutive global ids in (shard, local id) order.
+     * Honoured by fgim_merge, fgim_merge_batch and fgim_cross_query, whose outputs then have
+     * one row per valid vertex (n = their number); the other entry points reject it. */
+    const uint8_t* valid;
 } fgim_shard;
 
 typedef struct {

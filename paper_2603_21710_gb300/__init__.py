@@ -69,9 +69,14 @@ class MergeInput:
     """
 
     def __init__(self, vectors: Sequence[torch.Tensor], adjs: Sequence[torch.Tensor], entries: Sequence[int],
-                 metric="l2"):
+                 metric="l2", valid: Optional[Sequence[Optional[torch.Tensor]]] = None):
+        """valid: per shard an optional [n_i] bool / uint8 CUDA tensor (the ID mapping phi of
+        Sec. 4.1.3): invalid vertices get no row in the merged index and are nobody's
+        neighbour. Merged ids number the valid vertices in (shard, local id) order."""
         if len(vectors) != len(adjs) or len(vectors) != len(entries):
             raise ValueError("vectors, adjs and entries must have one item per shard")
+        if valid is not None and len(valid) != len(vectors):
+            raise ValueError("valid must have one item (or None) per shard")
         self.metric = _lib.METRICS[metric]
         vs = [_vec(v, "vectors") for v in vectors]
         if len({v.dtype for v in vs}) != 1:
@@ -83,10 +88,25 @@ class MergeInput:
         self.adjs = [_dev(a, torch.int32, "adj") for a in adjs]
         self.entries = [int(e) for e in entries]
         self.N = int(sum(self.sizes))
+        self.valid = None
+        if valid is not None and any(m is not None for m in valid):
+            self.valid = []
+            for m, n in zip(valid, self.sizes):
+                if m is None:
+                    self.valid.append(None)
+                    continue
+                if not m.is_cuda or m.shape != (n,):
+                    raise ValueError("each valid mask must be a CUDA tensor of shape [n_i]")
+                self.valid.append(m.to(torch.uint8).contiguous())
+        # rows of the merged index: the valid vertices
+        self.N_out = self.N if self.valid is None else int(
+            sum(n if m is None else int(m.count_nonzero()) for m, n in zip(self.valid, self.sizes)))
         self._shards = (Shard * len(vs))()
         o = 0
         for i, (n, a, e) in enumerate(zip(self.sizes, self.adjs, self.entries)):
-            self._shards[i] = Shard(self.X[o:o + n].data_ptr(), a.data_ptr(), n, int(a.shape[1]), e, 0)
+            m = None if self.valid is None else self.valid[i]
+            self._shards[i] = Shard(self.X[o:o + n].data_ptr(), a.data_ptr(), n, int(a.shape[1]), e, 0,
+                                    None if m is None else m.data_ptr())
             o += n
 
     @property
@@ -95,14 +115,15 @@ class MergeInput:
 
     @classmethod
     def from_flat(cls, X: torch.Tensor, sizes: Sequence[int], adj: torch.Tensor, entries: Sequence[int],
-                  metric="l2") -> "MergeInput":
-        """X [N, d] with shards consecutive; adj [N, M] local ids."""
-        vs, ads, o = [], [], 0
+                  metric="l2", valid: Optional[torch.Tensor] = None) -> "MergeInput":
+        """X [N, d] with shards consecutive; adj [N, M] local ids; valid: optional [N] mask."""
+        vs, ads, ms, o = [], [], [], 0
         for n in sizes:
             vs.append(X[o:o + n])
             ads.append(adj[o:o + n])
+            ms.append(None if valid is None else valid[o:o + n])
             o += n
-        return cls(vs, ads, entries, metric)
+        return cls(vs, ads, entries, metric, None if valid is None else ms)
 
     def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
                reach_beam=0, join_filter="tc", rows="auto") -> Params:
@@ -137,13 +158,14 @@ def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters
     L_ = load()
     p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter, rows)
     dev = inp.X.device
-    out = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
-           "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
-           "deg": torch.empty((inp.N,), dtype=torch.int32, device=dev)}
-    g = Graph(out["ids"].data_ptr(), out["dist"].data_ptr(), out["deg"].data_ptr(), inp.N, R, 0)
+    N = inp.N_out
+    out = {"ids": torch.empty((N, R), dtype=torch.int32, device=dev),
+           "dist": torch.empty((N, R), dtype=torch.float32, device=dev),
+           "deg": torch.empty((N,), dtype=torch.int32, device=dev)}
+    g = Graph(out["ids"].data_ptr(), out["dist"].data_ptr(), out["deg"].data_ptr(), N, R, 0)
     kn = None
     if return_knng:
-        kd = _new_knng(inp.N, k, dev)
+        kd = _new_knng(N, k, dev)
         kn = _knng_struct(kd["ids"], kd["dist"], kd["flags"])
     check(L_.fgim_merge(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn) if kn else None, ctypes.byref(g),
                         _stream()))
@@ -171,10 +193,10 @@ def merge_batch(inputs: Sequence[MergeInput], k: int, R: int, alpha: float = 1.0
     hs = (ctypes.c_int32 * n)()
     for m, inp in enumerate(inputs):
         dev = inp.X.device
-        o = {"ids": torch.empty((inp.N, R), dtype=torch.int32, device=dev),
-             "dist": torch.empty((inp.N, R), dtype=torch.float32, device=dev),
-             "deg": torch.empty((inp.N,), dtype=torch.int32, device=dev)}
-        graphs[m] = Graph(o["ids"].data_ptr(), o["dist"].data_ptr(), o["deg"].data_ptr(), inp.N, R, 0)
+        o = {"ids": torch.empty((inp.N_out, R), dtype=torch.int32, device=dev),
+             "dist": torch.empty((inp.N_out, R), dtype=torch.float32, device=dev),
+             "deg": torch.empty((inp.N_out,), dtype=torch.int32, device=dev)}
+        graphs[m] = Graph(o["ids"].data_ptr(), o["dist"].data_ptr(), o["deg"].data_ptr(), inp.N_out, R, 0)
         shard_ptrs[m] = ctypes.cast(inp._shards, ctypes.c_void_p)
         hs[m] = inp.h
         outs.append(o)
@@ -215,10 +237,10 @@ def merge_host(X, adj, sizes, entries, k: int, R: int, alpha: float = 1.0, metri
 
 
 def cross_query(inp: MergeInput, k: int, L: int = 0, rows="auto") -> dict:
-    """Stage (a), Alg. 2: PGs -> k-NNG."""
+    """Stage (a), Alg. 2: PGs -> k-NNG (one row per valid vertex)."""
     L_ = load()
     p = inp.params(k=k, L=L, rows=rows)
-    kd = _new_knng(inp.N, k, inp.X.device)
+    kd = _new_knng(inp.N_out, k, inp.X.device)
     kn = _knng_struct(kd["ids"], kd["dist"], kd["flags"])
     check(L_.fgim_cross_query(inp._shards, inp.h, ctypes.byref(p), ctypes.byref(kn), _stream()))
     kd["stats"] = last_stats()

@@ -18,7 +18,8 @@ METRICS = {"l2": 0, "ip": 1, "cos": 2, 0: 0, 1: 1, 2: 2}
 
 class Shard(ctypes.Structure):
     _fields_ = [("vectors", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("n", ctypes.c_int32),
-                ("max_degree", ctypes.c_int32), ("entry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_degree", ctypes.c_int32), ("entry", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("valid", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):

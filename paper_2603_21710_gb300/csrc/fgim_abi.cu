@@ -324,6 +324,9 @@ struct Problem {
     int metric;
 };
 
+// byte rows and cosine norms of P.X
+static void finish_problem(Ctx& c, Problem& P, const fgim_params* p);
+
 static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_params* p) {
     Problem P;
     P.N = total_n(sh, h);
@@ -331,6 +334,11 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.metric = p->metric;
     P.t = make_table(sh, h, p->dim);
     P.X = contiguous_vectors(c, sh, h, p->dim, p->dtype, P.N);
+    finish_problem(c, P, p);
+    return P;
+}
+
+static void finish_problem(Ctx& c, Problem& P, const fgim_params* p) {
     P.inv = nullptr;
     P.X8 = nullptr;
     if (byte_rows_ok(P.d) && p->byte_rows == 0) {
@@ -345,13 +353,80 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
         ck(launch_inv_norms(P.X, P.N, P.d, inv, c.s));
         P.inv = inv;
     }
-    return P;
 }
 
-static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_knng* g) {
+// ---------------------------------------------------------------------------- phi
+// The ID mapping of Sec. 4.1.3 with invalid vertices: valid vertices are numbered
+// consecutively in (shard, local id) order.
+static bool has_valid(const fgim_shard* sh, int h) {
+    for (int i = 0; i < h; ++i)
+        if (sh[i].valid) return true;
+    return false;
+}
+
+struct PhiMap {
+    int32_t* phi = nullptr;   // [N] input row -> merged id, -1 = invalid
+    int32_t* src = nullptr;   // [Nv] merged id -> input row
+    long long Nv = 0;
+    long long offv[FGIM_MAX_SHARDS + 1];   // first merged id of every shard
+    int32_t entry = 0;        // merged entry (the rule of merged_entry, after phi)
+};
+
+static PhiMap build_phi(Ctx& c, const fgim_shard* sh, int h, long long N) {
+    PhiMap F;
+    int32_t* flag = c.alloc<int32_t>(N);
+    long long o = 0;
+    for (int i = 0; i < h; ++i) {
+        ck(launch_valid_flags(sh[i].valid, sh[i].n, flag + o, c.s));
+        o += sh[i].n;
+    }
+    long long* off = c.alloc<long long>(N + 1);
+    const size_t sb = scan_scratch_bytes(N);
+    void* tmp = c.alloc<unsigned char>((long long)sb);
+    F.src = c.alloc<int32_t>(N);
+    ck(compact_flags(flag, N, F.src, off, tmp, sb, c.s));
+    F.phi = c.alloc<int32_t>(N);
+    ck(launch_phi(flag, off, N, F.phi, c.s));
+    o = 0;
+    for (int i = 0; i < h; ++i) {
+        F.offv[i] = c.read_ll(off + o);
+        o += sh[i].n;
+    }
+    F.offv[h] = c.read_ll(off + N);
+    F.Nv = F.offv[h];
+    need(F.Nv >= 1, FGIM_EINVAL, "no shard has a valid vertex");
+    // the shard with the most valid vertices (lowest index on ties): its entry if valid, else
+    // its first valid vertex
+    int best = 0;
+    for (int i = 1; i < h; ++i)
+        if (F.offv[i + 1] - F.offv[i] > F.offv[best + 1] - F.offv[best]) best = i;
+    long long gb = sh[best].entry;
+    for (int i = 0; i < best; ++i) gb += sh[i].n;
+    const int e = c.read_i32(F.phi + gb);
+    F.entry = e >= 0 ? e : (int32_t)F.offv[best];
+    return F;
+}
+
+// the valid vertices alone, renumbered by phi: the problem of stages (b) and (c)
+static Problem compact_problem(Ctx& c, const Problem& P, const PhiMap& F, const fgim_params* p) {
+    Problem Q;
+    Q.N = F.Nv;
+    Q.d = P.d;
+    Q.metric = P.metric;
+    Q.t = P.t;
+    for (int i = 0; i <= P.t.h; ++i) Q.t.off[i] = F.offv[i];
+    float* X = c.alloc<float>(Q.N * Q.d);
+    ck(launch_gather_rows(P.X, F.src, Q.N, Q.d, X, c.s));
+    Q.X = X;
+    finish_problem(c, Q, p);
+    return Q;
+}
+
+static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_knng* g, const PhiMap* F = nullptr) {
     const int L = resolve_L(p, h);
     need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
-    ck(launch_cross_query(P.t, P.X, P.X8, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s));
+    ck(launch_cross_query(P.t, P.X, P.X8, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s,
+                          F ? F->phi : nullptr, F ? F->src : nullptr, F ? F->Nv : P.N));
 }
 
 static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knng* g, fgim_stats* st) {
@@ -602,10 +677,17 @@ fgim_status fgim_cross_query(const fgim_shard* shards, int32_t h, const fgim_par
         check_params(params, true);
         check_shards(shards, h, params);
         need(out && out->ids && out->dist && out->flags, FGIM_EINVAL, "knng buffers are NULL");
-        need(out->n == total_n(shards, h) && out->k == params->k, FGIM_EINVAL, "knng shape mismatch");
+        const bool masked = has_valid(shards, h);
+        need(out->k == params->k && (masked || out->n == total_n(shards, h)), FGIM_EINVAL, "knng shape mismatch");
         Ctx c((cudaStream_t)stream);
         Problem P = make_problem(c, shards, h, params);
-        stage_a(c, P, params, h, out);
+        if (masked) {
+            const PhiMap F = build_phi(c, shards, h, P.N);
+            need(out->n == F.Nv, FGIM_EINVAL, "knng shape mismatch (n must be the number of valid vertices)");
+            stage_a(c, P, params, h, out, &F);
+        } else {
+            stage_a(c, P, params, h, out);
+        }
         c.finish(&t_stats);
     });
     end_call();
@@ -618,6 +700,8 @@ fgim_status fgim_refine_pass(const fgim_shard* shards, int32_t h, const fgim_par
     fgim_status r = guarded([&] {
         check_params(params, true);
         check_shards(shards, h, params);
+        need(!has_valid(shards, h), FGIM_EUNSUPPORTED,
+             "validity masks are honoured by fgim_merge, fgim_merge_batch and fgim_cross_query only");
         need(knng && knng->ids && knng->dist && knng->flags, FGIM_EINVAL, "knng buffers are NULL");
         need(knng->n == total_n(shards, h) && knng->k >= 1 && knng->k <= FGIM_MAX_K, FGIM_EINVAL, "knng shape mismatch");
         Ctx c((cudaStream_t)stream);
@@ -635,6 +719,8 @@ fgim_status fgim_indegree_repair(const fgim_shard* shards, int32_t h, const fgim
     fgim_status r = guarded([&] {
         check_params(params, true);
         check_shards(shards, h, params);
+        need(!has_valid(shards, h), FGIM_EUNSUPPORTED,
+             "validity masks are honoured by fgim_merge, fgim_merge_batch and fgim_cross_query only");
         need(knng && knng->ids && knng->dist && knng->flags, FGIM_EINVAL, "knng buffers are NULL");
         need(knng->n == total_n(shards, h), FGIM_EINVAL, "knng shape mismatch");
         Ctx c((cudaStream_t)stream);
@@ -654,6 +740,8 @@ fgim_status fgim_prune(const fgim_shard* shards, int32_t h, const fgim_params* p
     fgim_status r = guarded([&] {
         check_params(params, true);
         check_shards(shards, h, params);
+        need(!has_valid(shards, h), FGIM_EUNSUPPORTED,
+             "validity masks are honoured by fgim_merge, fgim_merge_batch and fgim_cross_query only");
         need(knng && knng->ids && knng->dist && T && e_ids && e_dist && e_cnt, FGIM_EINVAL, "NULL buffer");
         need(knng->n == total_n(shards, h) && knng->k >= 1 && knng->k <= FGIM_MAX_K, FGIM_EINVAL, "knng shape mismatch");
         Ctx c((cudaStream_t)stream);
@@ -686,6 +774,8 @@ fgim_status fgim_reach_fix(const fgim_shard* shards, int32_t h, const fgim_param
     fgim_status r = guarded([&] {
         check_params(params, true);
         check_shards(shards, h, params);
+        need(!has_valid(shards, h), FGIM_EUNSUPPORTED,
+             "validity masks are honoured by fgim_merge, fgim_merge_batch and fgim_cross_query only");
         need(graph && graph->ids && graph->dist && graph->deg, FGIM_EINVAL, "NULL buffer");
         need(graph->n == total_n(shards, h) && graph->R == params->R, FGIM_EINVAL, "graph shape mismatch");
         need(graph->entry >= 0 && graph->entry < graph->n, FGIM_EINVAL, "graph entry out of range");
@@ -700,8 +790,13 @@ fgim_status fgim_reach_fix(const fgim_shard* shards, int32_t h, const fgim_param
 
 static void merge_impl(Ctx& c, const fgim_shard* shards, int32_t h, const fgim_params* params, fgim_knng* knng_out,
                        fgim_graph* out) {
-    Problem P = make_problem(c, shards, h, params);
-    const long long N = P.N;
+    Problem P0 = make_problem(c, shards, h, params);
+    const bool masked = has_valid(shards, h);
+    PhiMap F;
+    if (masked) F = build_phi(c, shards, h, P0.N);
+    const long long N = masked ? F.Nv : P0.N;
+    need(out->n == N, FGIM_EINVAL, "graph shape mismatch (n must be the number of valid vertices)");
+    need(!knng_out || knng_out->n == N, FGIM_EINVAL, "knng shape mismatch (n must be the number of valid vertices)");
     const int k = params->k;
     fgim_knng g;
     if (knng_out) {
@@ -713,7 +808,8 @@ static void merge_impl(Ctx& c, const fgim_shard* shards, int32_t h, const fgim_p
         g.n = N;
         g.k = k;
     }
-    stage_a(c, P, params, h, &g);
+    stage_a(c, P0, params, h, &g, masked ? &F : nullptr);
+    const Problem P = masked ? compact_problem(c, P0, F, params) : P0;
     int32_t* T = c.alloc<int32_t>(N);
     for (int it = 0; it < params->iters; ++it) {
         refine_pass(c, P, params, &g, &t_stats);
@@ -725,7 +821,7 @@ static void merge_impl(Ctx& c, const fgim_shard* shards, int32_t h, const fgim_p
     int32_t* e_cnt = c.alloc<int32_t>(N);
     prune(c, P, params, &g, T, e_ids, e_dist, e_cnt);
     reverse_insert(c, N, params->R, e_ids, e_dist, e_cnt, out);
-    out->entry = merged_entry(shards, h);
+    out->entry = masked ? F.entry : merged_entry(shards, h);
     if (params->ensure_reachable) reach_fix(c, P, params, out, &t_stats);
     c.finish(&t_stats);
 }
@@ -737,11 +833,12 @@ fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* p
         check_params(params, true);
         check_shards(shards, h, params);
         const long long N = total_n(shards, h);
+        const bool masked = has_valid(shards, h);   // the row count is checked once phi is known
         need(out && out->ids && out->dist && out->deg, FGIM_EINVAL, "graph buffers are NULL");
-        need(out->n == N && out->R == params->R, FGIM_EINVAL, "graph shape mismatch");
+        need((masked || out->n == N) && out->R == params->R, FGIM_EINVAL, "graph shape mismatch");
         if (knng_out) {
             need(knng_out->ids && knng_out->dist && knng_out->flags, FGIM_EINVAL, "knng buffers are NULL");
-            need(knng_out->n == N && knng_out->k == params->k, FGIM_EINVAL, "knng shape mismatch");
+            need((masked || knng_out->n == N) && knng_out->k == params->k, FGIM_EINVAL, "knng shape mismatch");
         }
         Ctx c((cudaStream_t)stream);
         merge_impl(c, shards, h, params, knng_out, out);
@@ -760,7 +857,8 @@ fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, 
         for (int m = 0; m < n_merges; ++m) {
             check_shards(shards[m], h[m], params);
             need(outs[m].ids && outs[m].dist && outs[m].deg, FGIM_EINVAL, "graph buffers are NULL");
-            need(outs[m].n == total_n(shards[m], h[m]) && outs[m].R == params->R, FGIM_EINVAL, "graph shape mismatch");
+            need((has_valid(shards[m], h[m]) || outs[m].n == total_n(shards[m], h[m])) && outs[m].R == params->R,
+                 FGIM_EINVAL, "graph shape mismatch");
         }
         for (int m = 0; m < n_merges; ++m) {
             Ctx c((cudaStream_t)stream);
@@ -803,6 +901,7 @@ fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, c
             sh[i].max_degree = max_degree;
             sh[i].entry = entries[i];
             sh[i].reserved = 0;
+            sh[i].valid = nullptr;
             o += sizes[i];
         }
         check_shards(sh.data(), h, params);

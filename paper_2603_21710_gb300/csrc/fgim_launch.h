@@ -11,9 +11,13 @@ namespace fgim {
 // ---- k_search.cu
 // X: FP32 rows; X8: the same rows as bytes when every coordinate is an integer in [0, 255]
 // (searches then read X8, with identical results), else nullptr
+// phi / src (optional): the ID mapping with invalid vertices; nq = the number of output rows
+// (valid vertices), src[r] = the input row of output row r, phi maps input rows to output ids
+// (-1 = dropped)
 cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
                                long long N, int metric, int k, int L, fgim_knng* out, unsigned long long* counters,
-                               int* status, cudaStream_t s);
+                               int* status, cudaStream_t s, const int32_t* phi = nullptr,
+                               const int32_t* src = nullptr, long long nq = -1);
 cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
                           const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
@@ -29,6 +33,12 @@ size_t scan_scratch_bytes(long long n);
 cudaError_t launch_inv_norms(const float* X, long long n, int d, float* inv, cudaStream_t s);
 // out[i] = the FP32 value of the bfloat16 encoding in[i]
 cudaError_t launch_bf16_to_f32(const uint16_t* in, long long n, float* out, cudaStream_t s);
+// flag[i] = (mask == nullptr || mask[i] != 0)
+cudaError_t launch_valid_flags(const uint8_t* mask, long long n, int32_t* flag, cudaStream_t s);
+// phi[i] = flag[i] ? off[i] : -1 (off = exclusive prefix sums of flag)
+cudaError_t launch_phi(const int32_t* flag, const long long* off, long long n, int32_t* phi, cudaStream_t s);
+// out[r] = X[src[r]] for r < nv (rows of d floats)
+cudaError_t launch_gather_rows(const float* X, const int32_t* src, long long nv, int d, float* out, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s);
 // indices i (ascending) with flag[i] != 0, written to out; count to *count (device)
 cudaError_t compact_flags(const int32_t* flag, long long n, int32_t* out, long long* offsets_scratch,

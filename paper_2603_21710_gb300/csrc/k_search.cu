@@ -433,19 +433,29 @@ __host__ __device__ inline WarpLayout warp_layout(int d, int L, int htbits, int 
 
 // Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
 // own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
-// (delta, id), write ids / distances / new flags.
+// (delta, id), write ids / distances / new flags. With the ID mapping phi (Sec. 4.1.3) of
+// invalid vertices, warp r serves input row rows_of[r]; local candidates and search results are
+// renamed by phi and the invalid ones (phi = -1) dropped before the top-k (phi keeps the
+// order of ids, so the pool order needs no change).
 template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(ShardTable t, const float* __restrict__ X,
                                                      const RT* __restrict__ Xr, const float* __restrict__ inv_norm, long long N, int k, int L,
                                                      int htbits, int32_t* __restrict__ out_ids,
                                                      float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
-                                                     unsigned long long* counters, int* status) {
+                                                     unsigned long long* counters, int* status,
+                                                     const int32_t* __restrict__ phi, const int32_t* __restrict__ rows_of,
+                                                     long long nq) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
-    const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (g >= N) return;
+    const long long orow = (long long)blockIdx.x * (blockDim.x >> 5) + warp;   // output row
+    if (orow >= nq) return;
+    const long long g = rows_of ? (long long)rows_of[orow] : orow;   // input row
+    if (g < 0 || g >= N) {
+        if (lane == 0) atomicOr(status, kErrBounds);
+        return;
+    }
     const int d = t.dim;
     const WarpLayout lay = warp_layout(d, L, htbits, k, sizeof(RT) != 1);
     unsigned char* base = smem + (size_t)warp * lay.bytes;
@@ -483,6 +493,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
             v = -1;
         }
         if (v == u) v = -1;
+        if (phi && v >= 0 && phi[t.off[i] + v] < 0) v = -1;   // invalid: not a candidate
         const unsigned m = __ballot_sync(kFull, v >= 0);
         const int U = __popc(m);
         if (U == 0) continue;
@@ -493,7 +504,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
         if (lane < U) {
             const int32_t gv = scratch[lane];
             const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(qinv, inv_norm[gv]) : 1.f;
-            cand = mkkey(delta_finish<METRIC>(dd, inv), gv);
+            cand = mkkey(delta_finish<METRIC>(dd, inv), phi ? phi[gv] : gv);
             ctr.ndc++;
         }
         __syncwarp();
@@ -508,13 +519,17 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
                                                              nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d, L, pool,
                                                              pflag, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
-            const uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
+            uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
+            if (phi && cand != kEmptyKey) {
+                const int32_t m = phi[key_id(cand)];
+                cand = m < 0 ? kEmptyKey : mkkey(key_dist(cand), m);
+            }
             nres = warp_merge<false>(res, nullptr, nres, k, cand, 0);
         }
     }
     // Alg. 2, sorted by distance and resized to k
     for (int s = lane; s < k; s += 32) {
-        const long long o = g * k + s;
+        const long long o = orow * k + s;
         if (s < nres) {
             out_ids[o] = key_id(res[s]);
             out_dist[o] = key_dist(res[s]);
@@ -607,13 +622,15 @@ static int ht_bits_for(int L) {
 
 cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
                                long long N, int metric, int k, int L, fgim_knng* out, unsigned long long* counters,
-                               int* status, cudaStream_t s) {
+                               int* status, cudaStream_t s, const int32_t* phi, const int32_t* src, long long nq) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const bool bytes = X8 && byte_rows_ok(t.dim);
     const WarpLayout lay = warp_layout(t.dim, L, htbits, k, !bytes);
     const size_t smem = (size_t)lay.bytes * wpb;
-    const long long blocks = (N + wpb - 1) / wpb;
+    if (nq < 0) nq = N;
+    if ((phi == nullptr) != (src == nullptr)) return cudaErrorInvalidValue;
+    const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
 #define FGIM_LAUNCH_CQ(MT, SD, RT, MS)                                                                                 \
@@ -624,7 +641,7 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
         LaunchScope ls("k_cross_query", s);                                                                        \
         k_cross_query<MT, SD, RT, MS><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                        \
             t, X, reinterpret_cast<const RT*>(rows), inv_norm, N, k, L, htbits, out->ids, out->dist, out->flags,   \
-            counters, status);                                                                                     \
+            counters, status, phi, src, nq);                                                                       \
         e = cudaGetLastError();                                                                                    \
     } while (0)
     if (bytes) {

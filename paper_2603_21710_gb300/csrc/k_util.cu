@@ -156,6 +156,53 @@ __global__ void k_bf16_to_f32(const uint16_t* __restrict__ in, long long n, floa
         out[i] = __uint_as_float((uint32_t)in[i] << 16);
 }
 
+__global__ void k_valid_flags(const uint8_t* __restrict__ mask, long long n, int32_t* __restrict__ flag) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        flag[i] = (mask == nullptr || mask[i] != 0) ? 1 : 0;
+}
+
+cudaError_t launch_valid_flags(const uint8_t* mask, long long n, int32_t* flag, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_valid_flags", s);
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 32);
+    k_valid_flags<<<(unsigned)blocks, 256, 0, s>>>(mask, n, flag);
+    return cudaGetLastError();
+}
+
+__global__ void k_phi(const int32_t* __restrict__ flag, const long long* __restrict__ off, long long n,
+                      int32_t* __restrict__ phi) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        phi[i] = flag[i] ? (int32_t)off[i] : -1;
+}
+
+cudaError_t launch_phi(const int32_t* flag, const long long* off, long long n, int32_t* phi, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_phi", s);
+    const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 32);
+    k_phi<<<(unsigned)blocks, 256, 0, s>>>(flag, off, n, phi);
+    return cudaGetLastError();
+}
+
+// one warp per output row, float4 copies (d % 4 == 0, rows 16-byte aligned)
+__global__ void k_gather_rows(const float4* __restrict__ X, const int32_t* __restrict__ src, long long nv, int d4,
+                              float4* __restrict__ out) {
+    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= nv) return;
+    const float4* a = X + (long long)src[r] * d4;
+    float4* b = out + r * d4;
+    for (int c = lane; c < d4; c += 32) b[c] = a[c];
+}
+
+cudaError_t launch_gather_rows(const float* X, const int32_t* src, long long nv, int d, float* out, cudaStream_t s) {
+    if (nv <= 0) return cudaSuccess;
+    if (d % 4 != 0) return cudaErrorInvalidValue;
+    LaunchScope ls("k_gather_rows", s);
+    k_gather_rows<<<(unsigned)((nv * 32 + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(X), src, nv,
+                                                                     d / 4, reinterpret_cast<float4*>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bf16_to_f32(const uint16_t* in, long long n, float* out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     LaunchScope ls("k_bf16_to_f32", s);

@@ -36,7 +36,7 @@ def test_binding_covers_header():
 
 def test_struct_layouts_match_header():
     from paper_2603_21710_gb300 import _lib
-    assert ctypes.sizeof(_lib.Shard) == 32
+    assert ctypes.sizeof(_lib.Shard) == 40
     assert ctypes.sizeof(_lib.Params) == 64
     assert ctypes.sizeof(_lib.KNNG) == 40
     assert ctypes.sizeof(_lib.Graph) == 40

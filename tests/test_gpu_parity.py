@@ -507,3 +507,98 @@ def test_merge_batch_equals_single_merges(bf16_batch):
         assert torch.equal(o["ids"], s["ids"]) and torch.equal(o["dist"], s["dist"])
         assert torch.equal(o["deg"], s["deg"]) and o["entry"] == s["entry"]
     assert fg.merge_batch([], k=w0.k, R=w0.R) == []
+
+
+# --------------------------------------------------------------------------- validity (phi, Sec. 4.1.3)
+def _masks(w, seed=11, frac=0.75):
+    """About frac of the vertices valid; the entry of the largest shard invalid (the merged
+    entry then falls back to that shard's first valid vertex)."""
+    rng = np.random.default_rng(seed)
+    valid = rng.random(w.N) < frac
+    off = np.cumsum([0] + list(w.shard_sizes))
+    return valid, off
+
+
+def _masked_inputs(w, graphs, valid):
+    import paper_2603_21710_gb300 as fg
+    dev = _dev()
+    X = torch.from_numpy(w.X).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs],
+                                  metric={0: "l2", 1: "ip", 2: "cos"}[w.metric],
+                                  valid=torch.from_numpy(valid).to(dev))
+    P = O.Problem.from_workload(w, graphs)
+    Pv = O.Problem(P.X, P.sizes, P.adj, P.entry, P.metric, valid=valid)
+    return inp, Pv
+
+
+def test_masked_cross_query_bit_exact(sift_like):
+    """Integer data: with invalid vertices the cross query equals the oracle's bit for bit."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, _, _ = sift_like
+    valid, off = _masks(w)
+    inp, Pv = _masked_inputs(w, graphs, valid)
+    assert inp.N_out == int(valid.sum())
+    g = fg.cross_query(inp, w.k)
+    o, _, _ = O.stage_a(Pv, w.k)
+    assert np.array_equal(_np(g["ids"]), o.ids)
+    assert np.array_equal(_np(g["dist"]), o.dist)
+
+
+def test_masked_merge_bit_exact(sift_like):
+    """The whole merge with invalid vertices (one of them a shard entry) equals the oracle's."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, _, _ = sift_like
+    valid, off = _masks(w, seed=12)
+    big = int(np.argmax(w.shard_sizes))
+    valid[off[big] + graphs[big][1]] = False
+    inp, Pv = _masked_inputs(w, graphs, valid)
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=2, return_knng=True)
+    ref = O.merge(Pv, w.k, w.R, w.alpha, iters=2)
+    assert out["ids"].shape[0] == int(valid.sum())
+    assert np.array_equal(_np(out["knng"]["ids"]), ref.knn_ids)
+    assert np.array_equal(_np(out["ids"]), ref.ids)
+    assert np.array_equal(_np(out["deg"]), ref.deg)
+    assert out["entry"] == ref.entry
+    assert PR.bfs_reached(_np(out["ids"]), out["entry"]).all()
+
+
+def test_fully_invalid_shard_equals_merge_without_it(sift_like):
+    """A shard with no valid vertex changes nothing: with the same L the merge equals the merge
+    of the other shards (GPU against GPU, and against the oracle, bit for bit on integer data)."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    dev = _dev()
+    n3 = int(sum(w.shard_sizes[:3]))
+    valid = np.ones(w.N, bool)
+    valid[n3:] = False
+    masked, Pv = _masked_inputs(w, graphs, valid)
+    a = fg.merge(masked, k=w.k, R=w.R, alpha=w.alpha, L=22, iters=2, return_knng=True)
+    X = torch.from_numpy(w.X[:n3]).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs[:3]])).to(dev)
+    three = fg.MergeInput.from_flat(X, w.shard_sizes[:3], adj, [g[1] for g in graphs[:3]])
+    b = fg.merge(three, k=w.k, R=w.R, alpha=w.alpha, L=22, iters=2, return_knng=True)
+    assert a["ids"].shape[0] == n3
+    assert torch.equal(a["knng"]["ids"], b["knng"]["ids"]) and torch.equal(a["ids"], b["ids"])
+    assert a["entry"] == b["entry"]
+    ref = O.merge(Pv, w.k, w.R, w.alpha, L=22, iters=2)
+    assert np.array_equal(_np(a["ids"]), ref.ids) and a["entry"] == ref.entry
+
+
+def test_masks_rejected_where_not_honoured(small):
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    dev = _dev()
+    X = torch.from_numpy(w.X).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    none = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs],
+                                   valid=torch.zeros(w.N, dtype=torch.bool, device=dev))
+    with pytest.raises(fg.FgimError) as e:
+        fg.merge(none, k=w.k, R=w.R)
+    assert e.value.status == -1
+    some = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs],
+                                   valid=torch.ones(w.N, dtype=torch.bool, device=dev))
+    o, _, _ = O.stage_a(P, w.k)
+    with pytest.raises(fg.FgimError) as e:
+        fg.refine_pass(some, _to_dev(o))
+    assert e.value.status == -5

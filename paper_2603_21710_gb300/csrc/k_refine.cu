@@ -901,6 +901,19 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         tc::fence_after_sync();
     }
     if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
+    // byte rows: the MMAs have read the BF16 tile, so its space takes the byte rows of the
+    // candidates for the exact re-rank
+    const int brs = d + 16;
+    if (BYTES && ok_mma) {
+        const int c16 = d >> 4;
+        for (int item = tid; item < nc * c16; item += NT) {
+            const int r = item / c16, c = item - r * c16;
+            cp_async16(op + r * brs + c * 16, X8 + (long long)cid[r] * d + c * 16, true);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+    }
 
     // Filter. A pair survives when lo, a lower bound of its exact value, can still beat the
     // worst key of a list it is not already in. General test: lo = value - bound with the
@@ -966,8 +979,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     // FP32 distance, kStep pairs per step; lane t < U proposes for pair t.
     //  - byte rows (integer coordinates in [0, 255], d <= 128, d % 16 == 0): every partial sum
     //    of the canonical FP32 value is an integer below 2^24, so it equals the exact integer
-    //    |a|^2 + |b|^2 - 2 a.b; lanes take 16 bytes, 32 / lanes-per-row pairs per warp load,
-    //    all loads of a step issued before the sums.
+    //    |a|^2 + |b|^2 - 2 a.b; one pair per lane, from the byte rows that replace the BF16
+    //    tile in shared memory once the MMAs are done (row stride d + 16 bytes: the rows of a
+    //    warp's pairs fall in different banks).
     //  - otherwise the canonical FP32 additions, from the staged tile when every staged row is
     //    exact (the same values), else from the FP32 rows in global memory.
     constexpr int kStep = BYTES ? 32 : 8;
@@ -976,47 +990,25 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             const int U = min(kStep, nq - q0);
             float sc = 0.f;
             if constexpr (BYTES) {
-                const int lpr = byte_lanes(d);
-                const int rpi = 32 >> byte_lanes_log2(d);
-                const int lsh = byte_lanes_log2(d), rsh = 5 - lsh;   // lpr = 1 << lsh, rpi = 1 << rsh
-                const int sub = lane >> lsh, part = lane & (lpr - 1);
-                const bool has = part < (d >> 4);
-                // up to 32 / lpr pairs per warp load; loads in groups of four, issued before the sums
-                uint32_t mine = 0u;
-                for (int t0 = 0; t0 * rpi < U; t0 += 4) {
-                    uint4 xa[4], xb[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int pr = (t0 + t) * rpi + sub;
-                        xa[t] = make_uint4(0u, 0u, 0u, 0u);
-                        xb[t] = xa[t];
-                        if (pr < U && has) {
-                            const uint32_t e = wq[q0 + pr];
-                            xa[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[e & 1023u] * d + 16 * part);
-                            xb[t] = *reinterpret_cast<const uint4*>(X8 + (long long)cid[(e >> 10) & 1023u] * d + 16 * part);
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if ((t0 + t) * rpi < U) {
-                            uint32_t dot = __dp4a(xa[t].x, xb[t].x, 0u);
-                            dot = __dp4a(xa[t].y, xb[t].y, dot);
-                            dot = __dp4a(xa[t].z, xb[t].z, dot);
-                            dot = __dp4a(xa[t].w, xb[t].w, dot);
-                            dot = row_group_sum(dot, lsh);
-                            const uint32_t got = __shfl_sync(kFull, dot, (lane & (rpi - 1)) << lsh);
-                            if ((lane >> rsh) == t0 + t) mine = got;
-                        }
-                    }
-                }
+                // one pair per lane, both byte rows from the copy staged in shared memory
                 if (lane < U) {
+                    const uint32_t e = wq[q0 + lane];
+                    const uint4* pa = reinterpret_cast<const uint4*>(op + (e & 1023u) * brs);
+                    const uint4* pb = reinterpret_cast<const uint4*>(op + ((e >> 10) & 1023u) * brs);
+                    uint32_t dot = 0u;
+                    for (int c = 0; c < (d >> 4); ++c) {
+                        const uint4 x = pa[c], y = pb[c];
+                        dot = __dp4a(x.x, y.x, dot);
+                        dot = __dp4a(x.y, y.y, dot);
+                        dot = __dp4a(x.z, y.z, dot);
+                        dot = __dp4a(x.w, y.w, dot);
+                    }
                     if (METRIC == FGIM_L2SQ) {
-                        const uint32_t e = wq[q0 + lane];
                         const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
                         const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
-                        sc = (float)(na + nb - 2u * mine);
+                        sc = (float)(na + nb - 2u * dot);
                     } else {
-                        sc = (float)mine;
+                        sc = (float)dot;
                     }
                 }
             } else {

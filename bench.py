@@ -226,7 +226,7 @@ def row_bytes(w) -> int:
 
 # the sources each captured kernel family is compiled from (its own file plus the shared headers)
 TRAFFIC_SOURCES = {
-    "k_cross_query": ["k_search.cu"],
+    "k_cross_query": ["k_cross.cu", "k_cross.cuh", "k_beam.cuh"],
     "k_join": ["k_refine.cu", "tc_sm100.cuh"],
     "k_prune": ["k_prune.cu"],
 }

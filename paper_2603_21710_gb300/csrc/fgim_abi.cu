@@ -595,6 +595,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     int32_t* npar = c.alloc<int32_t>(N);
     unsigned long long* owner = c.alloc<unsigned long long>(N);
     long long* ff = c.alloc<long long>(N + 2);   // first uncommitted index after each round (one round commits >= 1)
+    int4* plan = c.alloc<int4>(kReachWindow);    // the actions planned in a round
     int32_t* cand = nullptr;
     float* cdist = nullptr;
     long long cand_cap = 0;
@@ -624,12 +625,12 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         ck(cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * N, c.s));
         ck(cudaMemsetAsync(ff, 0, sizeof(long long), c.s));
         long long start = 0, rho = 1;
-        constexpr int kBatch = 16;
+        constexpr int kBatch = 64;   // rounds per cooperative launch (it stops early once all are done)
         while (start < nr) {
             need(rho <= nr, FGIM_EINTERNAL, "reachability fix made no progress");
             const int rounds = (int)std::min<long long>(kBatch, nr + 1 - rho);
             ck(launch_reach_rounds(g->ids, g->dist, g->deg, visited, npar, R, reps, nr, rho, rounds, ff, cand, cdist,
-                                   beam, owner, c.ctr + 4, c.s));
+                                   beam, owner, plan, c.ctr + 4, c.s));
             rho += rounds;
             const long long next = c.read_ll(ff + (rho - 1));
             need(next > start, FGIM_EINTERNAL, "reachability fix made no progress");

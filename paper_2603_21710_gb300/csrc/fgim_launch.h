@@ -141,12 +141,13 @@ cudaError_t launch_cc_step(const int32_t* graph, int R, long long N, const int32
                            int32_t* changed, cudaStream_t s);
 cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long long N, int32_t* flag,
                              cudaStream_t s);
-// kReachRounds rounds of the representative attachment (rounds rho0 .. rho0 + rounds - 1);
-// ff[rho0 - 1] holds the first pending index, ff[rho] the first index after round rho
+// `rounds` rounds of the representative attachment (rounds rho0 .. rho0 + rounds - 1) in one
+// cooperative launch; ff[rho0 - 1] holds the first pending index, ff[rho] the first index
+// after round rho; plan: scratch of kReachWindow entries
 constexpr int kReachWindow = 2048;
 cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar,
                                 int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
                                 const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
-                                unsigned long long* attached, cudaStream_t s);
+                                int4* plan, unsigned long long* attached, cudaStream_t s);
 
 }  // namespace fgim

@@ -14,9 +14,13 @@
 // counting sort and merges them into E'(u), keeping the R smallest (delta, id).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "fgim_launch.h"
 
 namespace fgim {
+
+namespace cg = cooperative_groups;
 
 static inline long long cdivl(long long a, long long b) { return (a + b - 1) / b; }
 
@@ -547,32 +551,16 @@ cudaError_t launch_rep_flags(const int32_t* visited, const int32_t* label, long 
 // Round rho works on the window [ff[rho - 1], min(ff[rho - 1] + W, nr)) and leaves in ff[rho]
 // the first index it did not commit (the next round's start). Tags of later rounds are
 // smaller than those of earlier ones, so owner needs no reset between rounds.
-enum { kRPlan = 0, kRCheck = 1, kRCommit = 2 };
-
 __device__ __forceinline__ unsigned long long reach_tag(long long rho, long long r) {
     return ((unsigned long long)(0xFFFFFFFFu - (uint32_t)rho) << 32) | (unsigned long long)(uint32_t)r;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph, float* __restrict__ gdist,
-                                                     int32_t* __restrict__ deg, const int32_t* __restrict__ level,
-                                                     int32_t* __restrict__ npar, int R,
-                                                     const int32_t* __restrict__ reps, long long nr, long long rho,
-                                                     long long window, long long* __restrict__ ff,
-                                                     const int32_t* __restrict__ cand,
-                                                     const float* __restrict__ cdist, int beam,
-                                                     unsigned long long* __restrict__ owner,
-                                                     unsigned long long* attached) {
-    const int warp = threadIdx.x >> 5;
-    const int lane = lane_id();
-    const long long start = ff[rho - 1];
-    const long long wend = start + window < nr ? start + window : nr;
-    if (MODE == kRPlan && blockIdx.x == 0 && threadIdx.x == 0) ff[rho] = wend;
-    const long long r = start + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (r >= wend) return;
-    if (MODE == kRCommit && r >= ff[rho]) return;
-    const int32_t x = reps[r];
-    const int32_t* cr = cand + r * beam;
+// The action of representative r on the current graph (whole warp; the result is the same in
+// every lane): (p, position in p's list, index of p among r's search results, victim or -1);
+// p = -1: no action.
+__device__ __forceinline__ int4 reach_plan(const int32_t* __restrict__ graph, const int32_t* __restrict__ deg,
+                                           const int32_t* __restrict__ level, const int32_t* __restrict__ npar,
+                                           int R, const int32_t* cr, int beam, int lane) {
     int p = -1, pos = -1, t_sel = -1;
     for (int t0 = 0; t0 < beam && p < 0; t0 += 32) {
         const int t = t0 + lane;
@@ -608,66 +596,108 @@ __global__ void __launch_bounds__(128) k_reach_round(int32_t* __restrict__ graph
             t_sel = t;
         }
     }
-    if (p < 0) return;
-    const int32_t victim = pos < deg[p] ? graph[(long long)p * R + pos] : -1;
-    const unsigned long long tag = reach_tag(rho, r);
-    if (MODE == kRPlan) {
-        if (lane == 0) {
-            atomicMin(owner + p, tag);
-            if (victim >= 0) atomicMin(owner + victim, tag);
+    const int32_t victim = (p >= 0 && pos < deg[p]) ? graph[(long long)p * R + pos] : -1;
+    return make_int4(p, pos, t_sel, victim);
+}
+
+// The rounds of one batch in one cooperative launch (warps stride over the window): plan
+// (the action of every item and its reservations), check (the first item that lost one
+// bounds the prefix), commit (the prefix); phases are separated by grid-wide barriers and an
+// item's plan is computed once per round.
+__global__ void __launch_bounds__(128) k_reach_rounds(int32_t* __restrict__ graph, float* __restrict__ gdist,
+                                                      int32_t* __restrict__ deg, const int32_t* __restrict__ level,
+                                                      int32_t* __restrict__ npar, int R,
+                                                      const int32_t* __restrict__ reps, long long nr, long long rho0,
+                                                      int rounds, long long window, long long* __restrict__ ff,
+                                                      const int32_t* __restrict__ cand,
+                                                      const float* __restrict__ cdist, int beam,
+                                                      unsigned long long* __restrict__ owner, int4* __restrict__ plan,
+                                                      unsigned long long* attached) {
+    cg::grid_group grid = cg::this_grid();
+    const int lane = lane_id();
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (int q = 0; q < rounds; ++q) {
+        const long long rho = rho0 + q;
+        const long long start = ff[rho - 1];   // written before the last barrier
+        if (start >= nr) {                     // the same for every thread: all leave together
+            if (blockIdx.x == 0 && threadIdx.x == 0)
+                for (int t = q; t < rounds; ++t) ff[rho0 + t] = nr;
+            return;
         }
-        return;
-    }
-    if (MODE == kRCheck) {
-        if (lane == 0 && (owner[p] != tag || (victim >= 0 && owner[victim] != tag)))
-            atomicMin((unsigned long long*)(ff + rho), (unsigned long long)r);
-        return;
-    }
-    if (lane == 0) {
-        int32_t* li = graph + (long long)p * R;
-        float* ld = gdist + (long long)p * R;
-        const float d = cdist[r * beam + t_sel];
-        const uint64_t key = mkkey(d, x);
-        if (pos == deg[p]) deg[p] += 1;
-        else if (level[p] < level[victim]) npar[victim] -= 1;
-        while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
-            li[pos] = li[pos - 1];
-            ld[pos] = ld[pos - 1];
-            --pos;
+        const long long wend = start + window < nr ? start + window : nr;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ff[rho] = wend;
+        for (long long r = start + gw; r < wend; r += nw) {
+            const int4 pl = reach_plan(graph, deg, level, npar, R, cand + r * beam, beam, lane);
+            if (lane == 0) {
+                plan[r - start] = pl;
+                if (pl.x >= 0) {
+                    const unsigned long long tag = reach_tag(rho, r);
+                    atomicMin(owner + pl.x, tag);
+                    if (pl.w >= 0) atomicMin(owner + pl.w, tag);
+                }
+            }
         }
-        while (pos + 1 < deg[p] && mkkey(ld[pos + 1], li[pos + 1]) < key) {
-            li[pos] = li[pos + 1];
-            ld[pos] = ld[pos + 1];
-            ++pos;
+        grid.sync();
+        for (long long r = start + gw * 32 + lane; r < wend; r += nw * 32) {
+            const int4 pl = plan[r - start];
+            const unsigned long long tag = reach_tag(rho, r);
+            if (pl.x >= 0 && (owner[pl.x] != tag || (pl.w >= 0 && owner[pl.w] != tag)))
+                atomicMin((unsigned long long*)(ff + rho), (unsigned long long)r);
         }
-        li[pos] = x;
-        ld[pos] = d;
-        atomicAdd(attached, 1ull);
+        grid.sync();
+        const long long cend = ff[rho];
+        for (long long r = start + gw * 32 + lane; r < cend; r += nw * 32) {
+            const int4 pl = plan[r - start];
+            if (pl.x < 0) continue;
+            const int32_t p = pl.x, victim = pl.w, x = reps[r];
+            int pos = pl.y;
+            int32_t* li = graph + (long long)p * R;
+            float* ld = gdist + (long long)p * R;
+            const float d = cdist[r * beam + pl.z];
+            const uint64_t key = mkkey(d, x);
+            if (pos == deg[p]) deg[p] += 1;
+            else if (level[p] < level[victim]) npar[victim] -= 1;
+            while (pos > 0 && mkkey(ld[pos - 1], li[pos - 1]) > key) {
+                li[pos] = li[pos - 1];
+                ld[pos] = ld[pos - 1];
+                --pos;
+            }
+            while (pos + 1 < deg[p] && mkkey(ld[pos + 1], li[pos + 1]) < key) {
+                li[pos] = li[pos + 1];
+                ld[pos] = ld[pos + 1];
+                ++pos;
+            }
+            li[pos] = x;
+            ld[pos] = d;
+            atomicAdd(attached, 1ull);
+        }
+        grid.sync();
     }
 }
 
 cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, const int32_t* level, int32_t* npar,
                                 int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
                                 const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
-                                unsigned long long* attached, cudaStream_t s) {
+                                int4* plan, unsigned long long* attached, cudaStream_t s) {
+    // a cooperative grid: every block resident at once (the barriers wait for all of them)
+    static int max_blocks = 0;
     cudaError_t e = cudaSuccess;
-    const int wpb = 4;
-    const long long window = kReachWindow;
-    const unsigned blocks = (unsigned)cdivl(window, wpb);
-    for (int q = 0; q < rounds; ++q) {
-        const long long rho = rho0 + q;
-        LaunchScope ls("k_reach_round", s);
-        k_reach_round<kRPlan><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
-                                                          ff, cand, cdist, beam, owner, attached);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_reach_round<kRCheck><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
-                                                           ff, cand, cdist, beam, owner, attached);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_reach_round<kRCommit><<<blocks, wpb * 32, 0, s>>>(graph, gdist, deg, level, npar, R, reps, nr, rho, window,
-                                                            ff, cand, cdist, beam, owner, attached);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (max_blocks == 0) {
+        int dev = 0, per_sm = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reach_rounds, 128, 0)) != cudaSuccess)
+            return e;
+        max_blocks = per_sm * sms;
+        if (max_blocks < 1) return cudaErrorCooperativeLaunchTooLarge;
     }
-    return e;
+    long long window = kReachWindow;
+    const int blocks = (int)std::min<long long>(cdivl(window, 4), max_blocks);
+    LaunchScope ls("k_reach_rounds", s);
+    void* args[] = {&graph, &gdist, &deg, &level, &npar, &R, &reps, &nr, &rho0, &rounds, &window, &ff,
+                    &cand, &cdist, &beam, &owner, &plan, &attached};
+    return cudaLaunchCooperativeKernel((const void*)k_reach_rounds, dim3(blocks), dim3(128), args, 0, s);
 }
 
 }  // namespace fgim

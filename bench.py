@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--join-filter", default="tc", choices=["tc", "fp32"],
                     help="Update's pair filter: BF16 tensor-core tile (default) or FP32 SIMT tile")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form alongside")
+    ap.add_argument("--no-masked", action="store_true",
+                    help="skip timing the merge with invalid vertices (a quarter of them) alongside")
     return ap.parse_args()
 
 
@@ -361,6 +363,28 @@ def run_fgim(args):
         p_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pev), ws, dev)
         plain = {"value": ws * w.N * ps / (p_ms * 1e-3), "unit": UNIT, "ms_per_step": p_ms / ps, "steps": ps,
                  "form": "FP32 rows, FP32 SIMT join filter", "same_graph": bool(torch.equal(outp["ids"], out["ids"]))}
+    # ---- the same merge with a quarter of the vertices invalid (the ID mapping of deletion
+    # merges): outside the main timed region, same event timing, fewer steps
+    masked = None
+    if not args.no_masked:
+        gen_m = torch.Generator(device="cpu").manual_seed(20260321)
+        valid = (torch.rand(w.N, generator=gen_m) >= 0.25).to(dev)
+        inp_m = fg.MergeInput.from_flat(X, w.shard_sizes, adj, entries, metric="l2", valid=valid)
+        fg.merge(inp_m, **kw)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms_ = max(1, min(2, args.steps))
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ms_)]
+        for q in range(ms_):
+            mev[q][0].record(stream)
+            fg.merge(inp_m, **kw)
+            mev[q][1].record(stream)
+        torch.cuda.synchronize()
+        m_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in mev), ws, dev)
+        masked = {"value": ws * inp_m.N_out * ms_ / (m_ms * 1e-3), "unit": UNIT, "ms_per_step": m_ms / ms_,
+                  "steps": ms_, "valid_points": inp_m.N_out, "input_points": w.N,
+                  "form": "a quarter of the vertices invalid (seeded uniform mask); value counts valid points"}
+        del inp_m, valid
     # ---- evaluation outside the timed region: recall@10 at beam 64 against exact k-NN
     nq_eval = min(1000, w.Q.shape[0])
     Q = torch.from_numpy(w.Q[:nq_eval]).to(dev)
@@ -421,6 +445,7 @@ def run_fgim(args):
                              if cpu else None),
             "stage_a_work_model": cpu["stage_a_per_query"] if cpu else None,
             "plain_fp32": plain,
+            "masked": masked,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms}
     print(json.dumps(line), flush=True)
 

@@ -318,6 +318,7 @@ struct Problem {
     ShardTable t;
     const float* X;
     const uint8_t* X8;   // X as bytes when every coordinate is an integer in [0, 255], else nullptr
+    const uint16_t* Xh;  // the BF16 rows X decodes from (BF16 storage), else nullptr
     const float* inv;
     long long N;
     int d;
@@ -327,6 +328,25 @@ struct Problem {
 // byte rows and cosine norms of P.X
 static void finish_problem(Ctx& c, Problem& P, const fgim_params* p);
 
+// BF16 vectors of all shards as one [N, dim] buffer (no copy when already consecutive)
+static const uint16_t* contiguous_bf16(Ctx& c, const fgim_shard* sh, int h, int dim, long long N) {
+    const char* base = static_cast<const char*>(sh[0].vectors);
+    bool contiguous = true;
+    long long o = 0;
+    for (int i = 0; i < h; ++i) {
+        if (static_cast<const char*>(sh[i].vectors) != base + o * dim * 2) contiguous = false;
+        o += sh[i].n;
+    }
+    if (contiguous) return reinterpret_cast<const uint16_t*>(base);
+    uint16_t* X = c.alloc<uint16_t>(N * dim);
+    o = 0;
+    for (int i = 0; i < h; ++i) {
+        ck(cudaMemcpyAsync(X + o * dim, sh[i].vectors, (size_t)sh[i].n * dim * 2, cudaMemcpyDeviceToDevice, c.s));
+        o += sh[i].n;
+    }
+    return X;
+}
+
 static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_params* p) {
     Problem P;
     P.N = total_n(sh, h);
@@ -334,6 +354,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.metric = p->metric;
     P.t = make_table(sh, h, p->dim);
     P.X = contiguous_vectors(c, sh, h, p->dim, p->dtype, P.N);
+    P.Xh = p->dtype == FGIM_BF16 ? contiguous_bf16(c, sh, h, p->dim, P.N) : nullptr;
     finish_problem(c, P, p);
     return P;
 }
@@ -418,6 +439,7 @@ static Problem compact_problem(Ctx& c, const Problem& P, const PhiMap& F, const 
     float* X = c.alloc<float>(Q.N * Q.d);
     ck(launch_gather_rows(P.X, F.src, Q.N, Q.d, X, c.s));
     Q.X = X;
+    Q.Xh = nullptr;
     finish_problem(c, Q, p);
     return Q;
 }
@@ -426,7 +448,7 @@ static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_
     const int L = resolve_L(p, h);
     need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
     ck(launch_cross_query(P.t, P.X, P.X8, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s,
-                          F ? F->phi : nullptr, F ? F->src : nullptr, F ? F->Nv : P.N));
+                          F ? F->phi : nullptr, F ? F->src : nullptr, F ? F->Nv : P.N, P.Xh));
 }
 
 static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knng* g, fgim_stats* st) {
@@ -619,7 +641,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
             cand_cap = nr;
         }
         ck(launch_search(P.X, P.X8, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
-                         cand, cdist, c.ctr + 0, c.status, c.s));
+                         cand, cdist, c.ctr + 0, c.status, c.s, P.Xh));
         ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
         // rounds run in batches between host reads of the progress; ff[0] = 0 starts round 1
         ck(cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * N, c.s));
@@ -960,7 +982,8 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
             ck(launch_inv_norms(Q, nq, dim, qinv, c.s));
         }
         ck(launch_search(X, nullptr, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
-                         out_dist, c.ctr + 0, c.status, c.s));
+                         out_dist, c.ctr + 0, c.status, c.s,
+                         dtype == FGIM_BF16 ? static_cast<const uint16_t*>(base) : nullptr));
         c.finish(&t_stats);
     });
     end_call();

@@ -17,11 +17,11 @@ namespace fgim {
 cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
                                long long N, int metric, int k, int L, fgim_knng* out, unsigned long long* counters,
                                int* status, cudaStream_t s, const int32_t* phi = nullptr,
-                               const int32_t* src = nullptr, long long nq = -1);
+                               const int32_t* src = nullptr, long long nq = -1, const uint16_t* Xh = nullptr);
 cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
                           const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
-                          unsigned long long* counters, int* status, cudaStream_t s);
+                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh = nullptr);
 // X8[i] = X[i] as a byte; *flag |= 1 unless every X[i] is an integer in [0, 255] (n_elems % 4 == 0)
 cudaError_t launch_narrow_u8(const float* X, long long n_elems, uint8_t* X8, int* flag, cudaStream_t s);
 

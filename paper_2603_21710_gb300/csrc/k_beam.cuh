@@ -39,8 +39,14 @@ __device__ __forceinline__ float4 u8x4_to_float4(uint32_t w) {
     return make_float4((float)(w & 0xffu), (float)((w >> 8) & 0xffu), (float)((w >> 16) & 0xffu), (float)(w >> 24));
 }
 
-// float4 chunk c (coordinates 4c .. 4c + 3) of a row of FP32 or byte storage
+// float4 chunk c (coordinates 4c .. 4c + 3) of a row of FP32, BF16 or byte storage (BF16 and
+// bytes decode exactly to the FP32 values the merge works on)
 __device__ __forceinline__ float4 row_chunk(const float* row, int c) { return reinterpret_cast<const float4*>(row)[c]; }
+__device__ __forceinline__ float4 row_chunk(const uint16_t* row, int c) {
+    const uint2 w = reinterpret_cast<const uint2*>(row)[c];
+    return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u), __uint_as_float(w.y << 16),
+                       __uint_as_float(w.y & 0xffff0000u));
+}
 __device__ __forceinline__ float4 row_chunk(const uint8_t* row, int c) {
     return u8x4_to_float4(*reinterpret_cast<const uint32_t*>(row + 4 * c));
 }
@@ -158,7 +164,7 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int r = b + t;
-                    y[t] = (r < U && has) ? reinterpret_cast<const float4*>(base + (long long)rid[r] * d)[lane]
+                    y[t] = (r < U && has) ? row_chunk(base + (long long)rid[r] * d, lane)
                                           : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
@@ -451,6 +457,18 @@ static inline int ht_bits_for(int L) {
         } else {                                                                                 \
             if (small_) MACRO(FGIM_COSINE, true, RT, MS); else MACRO(FGIM_COSINE, false, RT, MS); \
         }                                                                                        \
+    } while (0)
+// BF16 rows (d > 128 only: small rows gain little)
+#define FGIM_DISPATCH_ALL_WIDE(M, L, MACRO, RT)                                                     \
+    do {                                                                                          \
+        const int ms_ = (L) <= 32 ? 1 : kPoolSlots;                                               \
+        if ((M) == FGIM_L2SQ) {                                                                   \
+            if (ms_ == 1) MACRO(FGIM_L2SQ, false, RT, 1); else MACRO(FGIM_L2SQ, false, RT, kPoolSlots); \
+        } else if ((M) == FGIM_IP) {                                                              \
+            if (ms_ == 1) MACRO(FGIM_IP, false, RT, 1); else MACRO(FGIM_IP, false, RT, kPoolSlots); \
+        } else {                                                                                  \
+            if (ms_ == 1) MACRO(FGIM_COSINE, false, RT, 1); else MACRO(FGIM_COSINE, false, RT, kPoolSlots); \
+        }                                                                                         \
     } while (0)
 // register pool of one slot (L <= 32) or of kPoolSlots slots
 #define FGIM_DISPATCH_ALL(M, D, L, MACRO, RT)                                                     \

@@ -122,7 +122,7 @@ template <bool PHI>
 cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint8_t* X8, const float* inv_norm,
                                  long long N, int metric, int k, int L, fgim_knng* out,
                                  unsigned long long* counters, int* status, cudaStream_t s, const int32_t* phi,
-                                 const int32_t* src, long long nq) {
+                                 const int32_t* src, long long nq, const uint16_t* Xh) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const bool bytes = X8 && byte_rows_ok(t.dim);
@@ -148,6 +148,9 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
     if (bytes) {
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, uint8_t);
+    } else if (Xh && t.dim > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0) {   // BF16 storage: same values, half the bytes
+        const void* rows = Xh;
+        FGIM_DISPATCH_ALL_WIDE(metric, L, FGIM_LAUNCH_CQ, uint16_t);
     } else {
         const void* rows = X;
         FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, float);
@@ -159,6 +162,7 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
 
 extern template cudaError_t launch_cross_query_t<true>(const ShardTable&, const float*, const uint8_t*, const float*,
                                                        long long, int, int, int, fgim_knng*, unsigned long long*,
-                                                       int*, cudaStream_t, const int32_t*, const int32_t*, long long);
+                                                       int*, cudaStream_t, const int32_t*, const int32_t*, long long,
+                                                       const uint16_t*);
 
 }  // namespace fgim

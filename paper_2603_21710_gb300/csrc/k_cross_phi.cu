@@ -6,6 +6,7 @@ namespace fgim {
 
 template cudaError_t launch_cross_query_t<true>(const ShardTable&, const float*, const uint8_t*, const float*,
                                                 long long, int, int, int, fgim_knng*, unsigned long long*, int*,
-                                                cudaStream_t, const int32_t*, const int32_t*, long long);
+                                                cudaStream_t, const int32_t*, const int32_t*, long long,
+                                                const uint16_t*);
 
 }  // namespace fgim

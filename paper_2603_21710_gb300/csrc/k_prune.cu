@@ -138,6 +138,76 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
     if (lane == 0) e_cnt[u] = nk;
 }
 
+// Wide FP32 rows (d > 128): the warp forms every distance together in the canonical order
+// (lane chunks, butterfly), reading both rows coalesced from global memory, and tests the
+// kept neighbours of u one after another, stopping at the first that occludes v. Each
+// decision is taken on the canonical distance, which is what the filter-and-recheck form
+// decides as well, so the lists are the same; a rejected candidate usually costs a few
+// distances instead of one per kept neighbour.
+template <int METRIC>
+__global__ void __launch_bounds__(128) k_prune_wide(const float* __restrict__ X, const float* __restrict__ inv_norm,
+                                                    long long N, int d, int k, const int32_t* __restrict__ ids,
+                                                    const float* __restrict__ dist, const int32_t* __restrict__ T,
+                                                    int R, float alpha2, int32_t* __restrict__ e_ids,
+                                                    float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
+                                                    int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (u >= N) return;
+    const int nc4 = d >> 2;
+    int32_t* cidv = reinterpret_cast<int32_t*>(smem) + (size_t)warp * 2 * k;
+    int32_t* kept = cidv + k;
+    int nv = 0;
+    for (int s0 = 0; s0 < k; s0 += 32) {
+        const int s = s0 + lane;
+        int32_t id = s < k ? ids[u * k + s] : -1;
+        if (id >= N) {
+            atomicOr(status, kErrBounds);
+            id = -1;
+        }
+        if (s < k) cidv[s] = id;
+        nv += __popc(__ballot_sync(kFull, id >= 0));
+    }
+    __syncwarp();
+    int nk = 0;
+    for (int t = 0; t < nv && nk < R; ++t) {
+        const int32_t v = cidv[t];
+        bool keep = T[v] == 1;
+        if (!keep) {
+            const float duv = dist[u * k + t];
+            const float4* rv = reinterpret_cast<const float4*>(X + (long long)v * d);
+            keep = true;
+            for (int s = 0; s < nk; ++s) {
+                const int32_t w = cidv[kept[s]];
+                const float sum = warp_butterfly(
+                    lane_part<METRIC>(reinterpret_cast<const float4*>(X + (long long)w * d), rv, nc4, lane));
+                const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[w], inv_norm[v]) : 1.f;
+                if (!(duv < __fmul_rn(alpha2, delta_finish<METRIC>(sum, inv)))) {
+                    keep = false;
+                    break;
+                }
+            }
+        }
+        if (keep) {
+            if (lane == 0) kept[nk] = t;
+            ++nk;
+            __syncwarp();
+        }
+    }
+    for (int s = lane; s < R; s += 32) {
+        if (s < nk) {
+            e_ids[u * R + s] = cidv[kept[s]];
+            e_dist[u * R + s] = dist[u * k + kept[s]];
+        } else {
+            e_ids[u * R + s] = -1;
+            e_dist[u * R + s] = __int_as_float(0x7f800000);
+        }
+    }
+    if (lane == 0) e_cnt[u] = nk;
+}
+
 __host__ __device__ inline size_t prune_bytes_per_warp(int k, int d) {
     return ((size_t)k * (d + 16) + (size_t)k * 16 + 15) & ~(size_t)15;
 }
@@ -295,6 +365,23 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
         else if (metric == FGIM_IP) FGIM_LAUNCH_PB(FGIM_IP);
         else FGIM_LAUNCH_PB(FGIM_COSINE);
 #undef FGIM_LAUNCH_PB
+        return e;
+    }
+    if (d > 128) {
+        const int wpb = 4;
+        const size_t smem = (size_t)wpb * 2 * k * sizeof(int32_t);
+        cudaError_t e = cudaSuccess;
+#define FGIM_LAUNCH_PW(MT)                                                                                        \
+    do {                                                                                                          \
+        LaunchScope ls("k_prune", s);                                                                             \
+        k_prune_wide<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R,  \
+                                                                         alpha2, e_ids, e_dist, e_cnt, status);   \
+        e = cudaGetLastError();                                                                                   \
+    } while (0)
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_PW(FGIM_L2SQ);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_PW(FGIM_IP);
+        else FGIM_LAUNCH_PW(FGIM_COSINE);
+#undef FGIM_LAUNCH_PW
         return e;
     }
     const int wpb = 2;

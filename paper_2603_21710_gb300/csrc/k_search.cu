@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_search(const f
 cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
                           const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
-                          unsigned long long* counters, int* status, cudaStream_t s) {
+                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const bool bytes = X8 && qids && byte_rows_ok(d);
@@ -80,6 +80,9 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
     if (bytes) {   // byte rows need integer queries: rows of X
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, uint8_t);
+    } else if (Xh && d > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0) {   // BF16 storage: same values, half the bytes
+        const void* rows = Xh;
+        FGIM_DISPATCH_ALL_WIDE(metric, L, FGIM_LAUNCH_S, uint16_t);
     } else {
         const void* rows = X;
         FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, float);

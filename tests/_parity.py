@@ -98,13 +98,21 @@ def bfs_reached(ids, entry):
     return seen
 
 
-def prune_row_has_near_tie(X, u, cand, dist_u, alpha, rtol=RTOL, atol=ATOL):
+def _delta64(a, b, metric):
+    if metric == 0:
+        return float(np.sum((a - b) ** 2))
+    if metric == 1:
+        return 1.0 - float(np.dot(a, b))
+    return 1.0 - float(np.dot(a, b)) / (float(np.linalg.norm(a)) * float(np.linalg.norm(b)))
+
+
+def prune_row_has_near_tie(X, u, cand, dist_u, alpha, rtol=RTOL, atol=ATOL, metric=0):
     """True when some occlusion test of row u is within tolerance of equality (FP64 check)."""
     a2 = float(np.float32(np.float64(alpha) ** 2))
     Xc = X[cand].astype(np.float64)
     for j in range(len(cand)):
         for i in range(j):
-            dwv = float(np.sum((Xc[i] - Xc[j]) ** 2))
+            dwv = _delta64(Xc[i], Xc[j], metric)
             if abs(float(dist_u[j]) - a2 * dwv) <= rtol * max(abs(float(dist_u[j])), a2 * dwv) + atol:
                 return True
     return False

@@ -195,6 +195,30 @@ def test_prune_integer_bit_exact(sift_like):
     assert np.array_equal(_np(ei), oi) and np.array_equal(_np(ed), od) and np.array_equal(_np(ec), oc)
 
 
+@pytest.mark.parametrize("which", ["high_dim", "bf16_batch"])
+def test_prune_wide_rows(which, request):
+    """Rows wider than 128 (d = 960 L2, d = 768 cosine): the warp-cooperative prune keeps the
+    oracle's lists except where an occlusion test ties within tolerance."""
+    import paper_2603_21710_gb300 as fg
+    if which == "high_dim":
+        w, graphs, P, inp = request.getfixturevalue("high_dim")
+    else:
+        w, graphs, P = request.getfixturevalue("bf16_batch")[2]
+        inp = _inp_bf16(w, graphs)
+    assert w.d > 128
+    o, T = _refined(P, w, iters=1)
+    ei, ed, ec = fg.prune(inp, _to_dev(o), torch.from_numpy(T).to(_dev()), w.R, w.alpha)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, w.alpha)
+    ei, ed, ec = _np(ei), _np(ed), _np(ec)
+    diff = np.nonzero(~np.all(ei == oi, 1))[0]
+    assert len(diff) <= max(2, w.N // 2000), len(diff)
+    for u in diff:
+        cand = o.ids[u][o.ids[u] >= 0]
+        assert PR.prune_row_has_near_tie(w.X, u, cand, o.dist[u][:len(cand)], w.alpha, metric=w.metric), u
+    same = np.all(ei == oi, 1)
+    assert np.array_equal(ed[same], od[same]) and np.array_equal(ec[same], oc[same])
+
+
 def test_reverse_insert_exact(small):
     import paper_2603_21710_gb300 as fg
     w, graphs, P, inp = small

@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form alongside")
     ap.add_argument("--no-masked", action="store_true",
                     help="skip timing the merge with invalid vertices (a quarter of them) alongside")
+    ap.add_argument("--batched", type=int, default=0, metavar="M",
+                    help="instead: time the batched form, M merges of the 768-d BF16 cosine recipe (sizes "
+                         "log-uniform in [--batched-lo, --batched-hi]) in one fgim_merge_batch call, against "
+                         "the plain FP32 form of the same merges; prints its own JSON line")
+    ap.add_argument("--batched-lo", type=int, default=10_000)
+    ap.add_argument("--batched-hi", type=int, default=50_000)
     return ap.parse_args()
 
 
@@ -450,10 +456,61 @@ def run_fgim(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """The batched form (many merges of uneven size in one library call) against the plain FP32
+    form of the same merges; inputs resident on the device, CUDA events around each batch."""
+    import torch
+    import paper_2603_21710_gb300 as fg
+    from synth import gen, pgbuild
+    dev = torch.device("cuda", 0)
+    ws_ = gen.batched(n_merges=args.batched, n_lo=args.batched_lo, n_hi=args.batched_hi, nq=10)
+    graphs = [pgbuild.build_all(w) for w in ws_]
+    chosen, plain = [], []
+    for w, g in zip(ws_, graphs):
+        adj = torch.from_numpy(np.concatenate([x[0] for x in g])).to(dev)
+        ent = [x[1] for x in g]
+        xb = torch.from_numpy(w.bits().view(np.int16)).to(dev).view(torch.bfloat16)
+        chosen.append(fg.MergeInput.from_flat(xb, w.shard_sizes, adj, ent, metric="cos"))
+        plain.append(fg.MergeInput.from_flat(torch.from_numpy(w.X).to(dev), w.shard_sizes, adj, ent, metric="cos"))
+    w0 = ws_[0]
+    kw = dict(k=w0.k, R=w0.R, alpha=w0.alpha, iters=3)
+
+    def timed(inps, **extra):
+        out = None
+        for _ in range(max(1, args.warmup)):
+            out = fg.merge_batch(inps, **kw, **extra)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            a.record()
+            out = fg.merge_batch(inps, **kw, **extra)
+            b.record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, out
+
+    ms_c, out_c = timed(chosen)
+    ms_p, out_p = timed(plain, join_filter="fp32")
+    N = sum(w.N for w in ws_)
+    line = {"metric": "merged points/sec, batched form (one fgim_merge_batch call)", "value": N / (ms_c * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms_c,
+            "higher_is_better": True, "dtype": "bf16 storage, f32 arithmetic", "data": "synthetic",
+            "config": {"workload": f"{args.batched} merges of the 768-d cosine recipe, BF16 storage, sizes "
+                                   f"log-uniform in [{args.batched_lo}, {args.batched_hi}], h in 2..6, "
+                                   "input PGs M=24 ef=96, k=32, R=24, I_max=3",
+                       "sizes": [w.N for w in ws_], "shards": [w.h for w in ws_]},
+            "plain_fp32": {"value": N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p,
+                           "form": "FP32 storage of the same values, FP32 SIMT join filter",
+                           "same_graphs": all(torch.equal(a["ids"], b["ids"]) for a, b in zip(out_c, out_p))}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
     run_fgim(args)
     ws, _, _ = dist_env()

@@ -174,8 +174,43 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
                 }
             }
         } else {
-            for (int r = 0; r < U; ++r)
-                P[lane * 33 + r] = lane_part_rows<METRIC, RT>(q, base + (long long)rid[r] * d, nc4, lane);
+            // wide rows: eight rows at a time, chunk by chunk (eight loads in flight per lane);
+            // each row keeps the four accumulators and the chunk order of lane_part_rows
+            for (int b = 0; b < U; b += 8) {
+                const RT* rowp[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) rowp[t] = base + (long long)rid[b + t < U ? b + t : b] * d;
+                float acc[8][4];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+                for (int c = lane; c < nc4; c += 32) {
+                    const float4 x = reinterpret_cast<const float4*>(q)[c];
+                    float4 y[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        y[t] = b + t < U ? row_chunk(rowp[t], c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (METRIC == FGIM_L2SQ) {
+                            const float e0 = __fsub_rn(x.x, y[t].x), e1 = __fsub_rn(x.y, y[t].y);
+                            const float e2 = __fsub_rn(x.z, y[t].z), e3 = __fsub_rn(x.w, y[t].w);
+                            acc[t][0] = fmaf(e0, e0, acc[t][0]);
+                            acc[t][1] = fmaf(e1, e1, acc[t][1]);
+                            acc[t][2] = fmaf(e2, e2, acc[t][2]);
+                            acc[t][3] = fmaf(e3, e3, acc[t][3]);
+                        } else {
+                            acc[t][0] = fmaf(x.x, y[t].x, acc[t][0]);
+                            acc[t][1] = fmaf(x.y, y[t].y, acc[t][1]);
+                            acc[t][2] = fmaf(x.z, y[t].z, acc[t][2]);
+                            acc[t][3] = fmaf(x.w, y[t].w, acc[t][3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (b + t < U)
+                        P[lane * 33 + b + t] = __fadd_rn(__fadd_rn(acc[t][0], acc[t][1]), __fadd_rn(acc[t][2], acc[t][3]));
+            }
         }
         __syncwarp();
         const float s = lane < U ? smem_tree_sum(P, lane) : 0.f;

@@ -243,7 +243,7 @@ TRAFFIC_SOURCES = {
 def kernel_sources_sha256(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(TRAFFIC_SOURCES[kernel] + ["fgim_internal.cuh", "fgim_launch.h"]):
+    for f in sorted(TRAFFIC_SOURCES[kernel] + ["fgim_internal.cuh"]):
         h.update(f.encode())
         h.update(open(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", f), "rb").read())
     return h.hexdigest()

@@ -342,3 +342,113 @@ def recall_at(found: np.ndarray, truth: np.ndarray, k: int) -> float:
     for f, t in zip(found[:, :k], truth[:, :k]):
         hits += len(set(int(x) for x in f if x >= 0) & set(int(x) for x in t if x >= 0))
     return hits / (k * found.shape[0])
+
+
+# --------------------------------------------------------------------------- HNSW-adaptive merging
+# Sec. 4.3.3: upper layers rebuilt over the merged base graph. Every vertex draws a level from
+# HNSW's distribution, P(level >= l) = M^-l (mL = 1 / ln M). Readings (each one also in the
+# design notes): the level of v comes from the v-th output of SplitMix64 seeded with `seed`
+# (its published definition: state += 0x9E3779B97F4A7C15, then the two xor-shift-multiply
+# rounds), as the number of l >= 1 with r_v < floor((2^64 - 1) / M^l); each layer l is built
+# from its own vertices at once instead of by one-at-a-time insertion: the exact ef nearest
+# members (the limit of HNSW's candidate search), the RNG heuristic down to M (Alg. 5's rule
+# with alpha = 1 and no indegree clause), bidirectional edges, and the same heuristic over the
+# 2M nearest of a member's own and reverse edges.
+_GAMMA = 0x9E3779B97F4A7C15
+_U64 = (1 << 64) - 1
+MAX_LEVELS = 16
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """The i-th output (i >= 0) of SplitMix64 started from state `seed`."""
+    z = (seed + (i + 1) * _GAMMA) & _U64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _U64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _U64
+    return z ^ (z >> 31)
+
+
+def level_thresholds(M: int, max_level: int = MAX_LEVELS) -> List[int]:
+    """T_l = floor((2^64 - 1) / M^l) for l = 1 .. while M^l < 2^64 (at most max_level)."""
+    out, p = [], M
+    while len(out) < max_level and p <= _U64:
+        out.append(_U64 // p)
+        p *= M
+    return out
+
+
+def hnsw_levels(n: int, M: int, seed: int) -> np.ndarray:
+    T = level_thresholds(M)
+    lv = np.zeros(n, np.int32)
+    for v in range(n):
+        r = splitmix64(seed, v)
+        lv[v] = sum(1 for t in T if r < t)
+    return lv
+
+
+def hnsw_layer(X: np.ndarray, metric: int, levels: np.ndarray, level: int, M: int, ef: int):
+    """Layer `level` >= 1: (members [n_l] ascending global ids, adj [n_l, M] positions in
+    members, -1 padded, deg [n_l])."""
+    members = np.nonzero(levels >= level)[0].astype(np.int32)
+    n = len(members)
+    if n == 0:
+        return members, np.zeros((0, M), np.int32), np.zeros(0, np.int32)
+    Xl = np.ascontiguousarray(X[members], dtype=np.float32)
+    Pl = Problem(Xl, [n], np.full((n, 1), -1, np.int32), np.zeros(1, np.int32), metric)
+    kk = min(ef, max(n - 1, 1))
+    ids, dist = knn_exact(Xl, Xl, kk, metric, exclude=np.arange(n))
+    g = KNNG(n, kk)
+    g.ids[:], g.dist[:] = ids, dist
+    T = np.full(n, 2, np.int32)   # the indegree clause never fires
+    e_ids, e_dist, e_cnt, _ = prune(Pl, g, T, M, 1.0)
+    wide = min(2 * M, 128)
+    pad_i = np.full((n, wide), -1, np.int32)
+    pad_d = np.full((n, wide), np.inf, np.float32)
+    pad_i[:, :M], pad_d[:, :M] = e_ids, e_dist
+    u_ids, u_dist, u_deg = reverse_insert(pad_i, pad_d, e_cnt)
+    g2 = KNNG(n, wide)
+    g2.ids[:], g2.dist[:] = u_ids, u_dist
+    f_ids, f_dist, f_cnt, _ = prune(Pl, g2, T, M, 1.0)
+    return members, f_ids, f_cnt
+
+
+def hnsw_entry(levels: np.ndarray) -> int:
+    """The first vertex of the highest level."""
+    return int(np.argmax(levels))
+
+
+def hnsw_search(X, metric, base_ids, layers, entry, Q, beam, topk):
+    """Greedy descent through the upper layers (top first; move to the neighbour with the
+    smallest (distance, id) while it beats the current vertex), then Alg. 1 on the base graph
+    from the vertex reached. layers[l - 1] = (members, adj) of layer l."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    out_i = np.empty((len(Q), topk), np.int32)
+    out_d = np.empty((len(Q), topk), np.float32)
+    starts = np.empty(len(Q), np.int32)
+    for qi, q in enumerate(np.ascontiguousarray(Q, dtype=np.float32)):
+        cur = entry
+        dcur = delta(q, X[cur], metric)
+        for members, adj in reversed(layers):
+            if len(members) == 0:
+                continue
+            pos = int(np.searchsorted(members, cur))
+            if pos >= len(members) or members[pos] != cur:
+                continue
+            moved = True
+            while moved:
+                moved = False
+                best = (dcur, cur)
+                for nb in adj[pos]:
+                    if nb < 0:
+                        continue
+                    v = int(members[nb])
+                    key = (delta(q, X[v], metric), v)
+                    if key < best:
+                        best = key
+                if best[1] != cur:
+                    dcur, cur = best
+                    pos = int(np.searchsorted(members, cur))
+                    moved = True
+        starts[qi] = cur
+        i, d, _ = search(X, base_ids, cur, q[None], beam, topk, metric)
+        out_i[qi], out_d[qi] = i[0], d[0]
+    return out_i, out_d, starts

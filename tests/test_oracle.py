@@ -543,3 +543,70 @@ def test_merged_entry_with_invalid_entry():
     valid2[P.off[2]:P.off[2] + 10] = 0         # and shard 1 the most
     Pv2 = _with_valid(P, valid2)
     assert O.merged_entry(Pv2) == Pv2.phi()[P.off[1] + P.entry[1]]
+
+
+# --------------------------------------------------------------------------- HNSW-adaptive merging
+def test_splitmix64_known_outputs():
+    """SplitMix64 from state 0: its first three published outputs."""
+    assert O.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert O.splitmix64(0, 1) == 0x6E789E6AA1B965F4
+    assert O.splitmix64(0, 2) == 0x06C45D188009454F
+
+
+def test_hnsw_level_distribution():
+    """P(level >= l) = M^-l: thresholds are exact integer quotients; counts within 5 sigma."""
+    M = 8
+    T = O.level_thresholds(M)
+    assert T[0] == ((1 << 64) - 1) // 8 and T[1] == ((1 << 64) - 1) // 64
+    assert all(a > b for a, b in zip(T, T[1:]))
+    n = 40_000
+    lv = O.hnsw_levels(n, M, seed=5)
+    for l in (1, 2, 3):
+        p = M ** -l
+        got = int((lv >= l).sum())
+        assert abs(got - n * p) <= 5 * np.sqrt(n * p * (1 - p)) + 1, (l, got)
+    assert np.array_equal(O.hnsw_levels(1000, M, seed=5), lv[:1000])   # counter-based: prefix-stable
+
+
+def test_hnsw_layer_collinear():
+    """Three points on a line a - b - c: the heuristic drops c from a's list (b is nearer to c
+    than a is) and a from c's; b keeps both; reverse edges add nothing new."""
+    X = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [3, 0, 0, 0]], np.float32)
+    levels = np.array([1, 1, 1], np.int32)
+    members, adj, deg = O.hnsw_layer(X, 0, levels, 1, M=4, ef=4)
+    assert list(members) == [0, 1, 2]
+    assert list(adj[0][:deg[0]]) == [1]
+    assert list(adj[1][:deg[1]]) == [0, 2]
+    assert list(adj[2][:deg[2]]) == [1]
+
+
+def test_hnsw_layer_invariants():
+    """Rows sorted by distance, no self or duplicate, degree <= M, every kept pair obeys the
+    RNG rule, and a layer holds exactly the vertices of that level or higher."""
+    from synth import gen
+    w = gen.small(seed=3, N=3000, d=8, h=2, nq=4)
+    levels = O.hnsw_levels(w.N, 8, seed=11)
+    members, adj, deg = O.hnsw_layer(w.X, 0, levels, 1, M=8, ef=32)
+    assert np.array_equal(members, np.nonzero(levels >= 1)[0])
+    Xl = w.X[members].astype(np.float64)
+    for u in range(len(members)):
+        row = adj[u][:deg[u]]
+        assert deg[u] <= 8 and len(set(row)) == len(row) and u not in row and np.all(adj[u][deg[u]:] == -1)
+        du = [np.sum((Xl[u] - Xl[v]) ** 2) for v in row]
+        assert all(a <= b for a, b in zip(du, du[1:]))
+        for j in range(len(row)):
+            for i in range(j):
+                assert du[j] < np.sum((Xl[row[i]] - Xl[row[j]]) ** 2) * (1 + 1e-5)
+
+
+def test_hnsw_search_descends_to_the_nearest_member():
+    """On a path graph layer over points on a line, the greedy descent ends at the member
+    nearest to the query, and the base search starts there."""
+    X = np.array([[float(i), 0, 0, 0] for i in range(10)], np.float32)
+    members = np.array([0, 3, 6, 9], np.int32)
+    adj = np.array([[1, -1], [0, 2], [1, 3], [2, -1]], np.int32)
+    base = np.array([[(i + 1) % 10, (i + 9) % 10] for i in range(10)], np.int32)
+    Q = np.array([[7.2, 0, 0, 0], [1.4, 0, 0, 0]], np.float32)
+    ids, dist, starts = O.hnsw_search(X, 0, base, [(members, adj)], 0, Q, beam=4, topk=2)
+    assert list(starts) == [6, 0]
+    assert list(ids[0]) == [7, 8] and list(ids[1]) == [1, 2]

@@ -242,6 +242,46 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
                                 const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
                                 int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream);
 
+/* ---- HNSW-adaptive merging (Sec. 4.3.3): upper layers over a merged base graph ----------
+ * Every vertex v draws a level with P(level >= l) = M^-l (HNSW's mL = 1 / ln M): r_v = the
+ * v-th output of SplitMix64 started from `seed`, level = #{l >= 1 : r_v < floor((2^64 - 1) /
+ * M^l)}. Layer l holds the vertices of level >= l (ascending ids). Each layer is built from
+ * its own vertices at once (the paper inserts them one at a time, which a GPU cannot do in a
+ * fixed order in parallel): the exact `ef` nearest members, the RNG heuristic down to M
+ * (Alg. 5's rule with alpha = 1 and no indegree clause), bidirectional edges, and the
+ * heuristic again over the 2M nearest of a member's own and reverse edges. The search
+ * descends greedily from the entry (the first vertex of the highest level) through the
+ * layers, then runs Alg. 1 on the base graph from the vertex it reached. */
+#define FGIM_MAX_LEVELS 16
+
+typedef struct {
+    const int32_t* members;  /* [n] ascending global ids of the layer's vertices */
+    const int32_t* adj;      /* [n, M] neighbours as positions in members, -1 padded */
+    int64_t n;
+    int32_t M;               /* 1 .. 32 for the search */
+    int32_t reserved;
+} fgim_layer;
+
+/* levels: device [n] out. counts: HOST [FGIM_MAX_LEVELS + 1] out, counts[l] = #{v : level(v)
+ * >= l} (counts[0] = n). M in [2, 128]. Synchronous. */
+fgim_status fgim_hnsw_levels(int64_t n, int32_t M, uint64_t seed, int32_t* levels, int64_t* counts, void* stream);
+
+/* One upper layer `level` (1 .. FGIM_MAX_LEVELS) over `vectors` ([n, dim], dtype, metric) and
+ * `levels` (device [n]); n_layer = counts[level] of fgim_hnsw_levels. Outputs (device,
+ * caller-owned): members [n_layer], adj [n_layer, M] (positions in members, -1 padded),
+ * deg [n_layer]. M in [1, 64], ef in [1, 128]. Synchronous. */
+fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                            const int32_t* levels, int32_t level, int32_t M, int32_t ef, int32_t* members,
+                            int32_t* adj, int32_t* deg, int64_t n_layer, void* stream);
+
+/* fgim_search with the upper layers: layers[l - 1] is layer l (host array of n_layers
+ * descriptors, device buffers; all with the same M <= 32); entry: the top vertex.
+ * out_start (optional, device [nq]): the base-graph vertex each query's descent reached. */
+fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                             const int32_t* graph_ids, int32_t R, const fgim_layer* layers, int32_t n_layers,
+                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam,
+                             int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream);
+
 /* Counters of the last merge/search call made by this host thread. */
 void fgim_last_stats(fgim_stats* out);
 

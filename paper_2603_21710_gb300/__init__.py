@@ -18,7 +18,8 @@ import torch
 from . import _lib
 from ._lib import FgimError, KNNG, Graph, Params, Shard, check, last_stats, load  # noqa: F401
 
-__all__ = ["MergeInput", "merge", "merge_batch", "merge_host", "cross_query", "refine_pass", "indegree_repair", "prune",
+__all__ = ["MergeInput", "merge", "merge_batch", "merge_host", "hnsw_levels", "hnsw_layer", "build_layers",
+           "search_hnsw", "cross_query", "refine_pass", "indegree_repair", "prune",
            "reverse_insert", "reach_fix", "search", "last_stats", "load", "launch_count", "FgimError",
            "FLAG_NEW", "FLAG_REPLACED", "profiling"]
 
@@ -328,6 +329,73 @@ def search(X: torch.Tensor, graph_ids: torch.Tensor, entry: int, queries: torch.
                          int(G.shape[1]),
                          int(entry), _p(Q), nq, topk, beam, _p(ids), _p(dist), _stream()))
     return ids, dist
+
+
+# --------------------------------------------------------------------------- HNSW-adaptive merging
+def hnsw_levels(n: int, M: int, seed: int, device=None):
+    """Levels of n vertices (SplitMix64 from `seed`, P(level >= l) = M^-l): (levels [n] int32
+    device tensor, counts[l] = #{v : level >= l} for l = 0 .. MAX_LEVELS)."""
+    L_ = load()
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    levels = torch.empty((n,), dtype=torch.int32, device=dev)
+    counts = (ctypes.c_int64 * (_lib.MAX_LEVELS + 1))()
+    check(L_.fgim_hnsw_levels(int(n), int(M), ctypes.c_uint64(seed & ((1 << 64) - 1)), _p(levels), counts,
+                              _stream()))
+    return levels, [int(x) for x in counts]
+
+
+def hnsw_layer(X: torch.Tensor, levels: torch.Tensor, level: int, n_layer: int, M: int, ef: int = 64,
+               metric="l2") -> dict:
+    """Layer `level` >= 1 over the vertices of that level or higher (Sec. 4.3.3): members
+    (ascending ids), adj [n_layer, M] (positions in members, -1 padded), deg."""
+    L_ = load()
+    X = _vec(X, "X")
+    lv = _dev(levels, torch.int32, "levels")
+    dev = X.device
+    out = {"members": torch.empty((n_layer,), dtype=torch.int32, device=dev),
+           "adj": torch.empty((n_layer, M), dtype=torch.int32, device=dev),
+           "deg": torch.empty((n_layer,), dtype=torch.int32, device=dev)}
+    check(L_.fgim_hnsw_layer(_p(X), int(X.shape[0]), int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric],
+                             _p(lv), int(level), int(M), int(ef), _p(out["members"]), _p(out["adj"]),
+                             _p(out["deg"]), int(n_layer), _stream()))
+    return out
+
+
+def build_layers(X: torch.Tensor, M: int, ef: int = 64, seed: int = 0, metric="l2") -> dict:
+    """All upper layers over the vertices of X: {levels, counts, layers (layer 1 first), entry}."""
+    levels, counts = hnsw_levels(int(X.shape[0]), M, seed, X.device)
+    layers = []
+    for l in range(1, _lib.MAX_LEVELS + 1):
+        if counts[l] == 0:
+            break
+        layers.append(hnsw_layer(X, levels, l, counts[l], M, ef, metric))
+    top = len(layers)
+    entry = int(torch.nonzero(levels == top)[0, 0]) if top else 0
+    return {"levels": levels, "counts": counts, "layers": layers, "entry": entry}
+
+
+def search_hnsw(X: torch.Tensor, graph_ids: torch.Tensor, layers: Sequence[dict], entry: int, queries: torch.Tensor,
+                topk: int = 10, beam: int = 64, metric="l2"):
+    """Greedy descent through the upper layers, then Alg. 1 on the base graph:
+    (ids [nq, topk], dist, start [nq] = the base vertex each descent reached)."""
+    L_ = load()
+    X = _vec(X, "X")
+    Q = _vec(queries, "queries")
+    if Q.dtype != X.dtype:
+        raise ValueError("X and queries must have the same dtype")
+    G = _dev(graph_ids, torch.int32, "graph_ids")
+    nq = int(Q.shape[0])
+    arr = (_lib.Layer * max(1, len(layers)))()
+    for i, ly in enumerate(layers):
+        arr[i] = _lib.Layer(ly["members"].data_ptr(), ly["adj"].data_ptr(), int(ly["members"].shape[0]),
+                            int(ly["adj"].shape[1]), 0)
+    ids = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
+    dist = torch.empty((nq, topk), dtype=torch.float32, device=X.device)
+    start = torch.empty((nq,), dtype=torch.int32, device=X.device)
+    check(L_.fgim_search_hnsw(_p(X), int(X.shape[0]), int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric],
+                              _p(G), int(G.shape[1]), arr, len(layers), int(entry), _p(Q), nq, topk, beam, _p(ids),
+                              _p(dist), _p(start), _stream()))
+    return ids, dist, start
 
 
 def launch_count() -> int:

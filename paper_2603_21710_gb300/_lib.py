@@ -22,6 +22,14 @@ class Shard(ctypes.Structure):
                 ("valid", ctypes.c_void_p)]
 
 
+class Layer(ctypes.Structure):
+    _fields_ = [("members", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("n", ctypes.c_int64), ("M", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+MAX_LEVELS = 16
+
+
 class Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("R", ctypes.c_int32), ("alpha", ctypes.c_float), ("L", ctypes.c_int32),
@@ -78,6 +86,16 @@ EXPORTS = {
     "fgim_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fgim_hnsw_levels": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "fgim_hnsw_layer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "fgim_search_hnsw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "fgim_search_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,

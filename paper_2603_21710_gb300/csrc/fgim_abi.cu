@@ -944,6 +944,189 @@ fgim_status fgim_merge_host(const void* vectors_host, const int32_t* adj_host, c
     return r;
 }
 
+// ---------------------------------------------------------------------------- HNSW layers
+static HnswThresholds hnsw_thresholds(int M) {
+    HnswThresholds th;
+    std::memset(&th, 0, sizeof(th));
+    unsigned long long p = (unsigned long long)M;
+    while (th.count < kMaxHnswLevels) {
+        th.t[th.count++] = ~0ull / p;
+        if (p > ~0ull / (unsigned long long)M) break;
+        p *= (unsigned long long)M;
+    }
+    return th;
+}
+
+// the FP32 rows of `vectors` (decoded when BF16)
+static const float* f32_rows(Ctx& c, const void* vectors, long long n, int dim, int dtype) {
+    if (dtype == FGIM_F32) return static_cast<const float*>(vectors);
+    float* X = c.alloc<float>(n * dim);
+    ck(launch_bf16_to_f32(static_cast<const uint16_t*>(vectors), n * dim, X, c.s));
+    return X;
+}
+
+fgim_status fgim_hnsw_levels(int64_t n, int32_t M, uint64_t seed, int32_t* levels, int64_t* counts, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(levels && counts, FGIM_EINVAL, "NULL buffer");
+        need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
+        need(M >= 2 && M <= FGIM_MAX_R, FGIM_EINVAL, "M must be in [2, 128]");
+        Ctx c((cudaStream_t)stream);
+        ck(launch_hnsw_levels(n, (unsigned long long)seed, hnsw_thresholds(M), levels, c.s));
+        std::vector<int32_t> h(n);
+        ck(cudaMemcpyAsync(h.data(), levels, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c.s));
+        c.finish(&t_stats);
+        for (int l = 0; l <= FGIM_MAX_LEVELS; ++l) counts[l] = 0;
+        for (long long v = 0; v < n; ++v)
+            for (int l = 0; l <= h[v] && l <= FGIM_MAX_LEVELS; ++l) ++counts[l];
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                            const int32_t* levels, int32_t level, int32_t M, int32_t ef, int32_t* members,
+                            int32_t* adj, int32_t* deg, int64_t n_layer, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(vectors && levels && members && adj && deg, FGIM_EINVAL, "NULL buffer");
+        need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
+        need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
+        need(dtype == FGIM_F32 || dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
+        need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
+        need(level >= 1 && level <= FGIM_MAX_LEVELS, FGIM_EINVAL, "level must be in [1, 16]");
+        need(M >= 1 && M <= 64, FGIM_EINVAL, "M must be in [1, 64]");
+        need(ef >= 1 && ef <= FGIM_MAX_K, FGIM_EINVAL, "ef must be in [1, 128]");
+        need(n_layer >= 0 && n_layer <= n, FGIM_EINVAL, "bad n_layer");
+        need(((uintptr_t)vectors & (dtype == FGIM_F32 ? 15u : 1u)) == 0, FGIM_EINVAL, "vectors misaligned");
+        Ctx c((cudaStream_t)stream);
+        // members: the vertices of level >= `level`, ascending
+        int32_t* flag = c.alloc<int32_t>(n);
+        long long* off = c.alloc<long long>(n + 1);
+        const size_t sb = scan_scratch_bytes(n);
+        void* tmp = c.alloc<unsigned char>((long long)sb);
+        int32_t* mem = c.alloc<int32_t>(n);
+        ck(launch_level_flags(levels, n, level, flag, c.s));
+        ck(compact_flags(flag, n, mem, off, tmp, sb, c.s));
+        const long long nl = c.read_ll(off + n);
+        need(nl == n_layer, FGIM_EINVAL, "n_layer is not the number of vertices of that level");
+        if (nl == 0) return;
+        ck(cudaMemcpyAsync(members, mem, sizeof(int32_t) * nl, cudaMemcpyDeviceToDevice, c.s));
+        Problem L;
+        std::memset(&L.t, 0, sizeof(L.t));
+        L.t.h = 1;
+        L.t.dim = dim;
+        L.t.off[1] = nl;
+        L.N = nl;
+        L.d = dim;
+        L.metric = metric;
+        const float* X = f32_rows(c, vectors, n, dim, dtype);
+        float* Xl = c.alloc<float>(nl * dim);
+        ck(launch_gather_rows(X, members, nl, dim, Xl, c.s));
+        L.X = Xl;
+        L.Xh = nullptr;
+        fgim_params lp;
+        std::memset(&lp, 0, sizeof(lp));
+        lp.metric = metric;
+        finish_problem(c, L, &lp);
+        // the exact ef nearest members, the RNG heuristic to M, bidirectional edges, the
+        // heuristic again over the 2M nearest of own and reverse edges
+        const int kk = (int)std::min<long long>(ef, std::max<long long>(nl - 1, 1));
+        int32_t* k_ids = c.alloc<int32_t>(nl * kk);
+        float* k_dist = c.alloc<float>(nl * kk);
+        ck(launch_layer_knn(L.X, L.X8, L.inv, nl, dim, metric, kk, k_ids, k_dist, c.s));
+        int32_t* T = c.alloc<int32_t>(nl);   // never 1: no indegree clause
+        ck(cudaMemsetAsync(T, 0, sizeof(int32_t) * nl, c.s));
+        fgim_knng g1;
+        std::memset(&g1, 0, sizeof(g1));
+        g1.ids = k_ids;
+        g1.dist = k_dist;
+        g1.n = nl;
+        g1.k = kk;
+        int32_t* e_ids = c.alloc<int32_t>(nl * M);
+        float* e_dist = c.alloc<float>(nl * M);
+        int32_t* e_cnt = c.alloc<int32_t>(nl);
+        ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, 1.f, e_ids, e_dist, e_cnt, c.status, c.s));
+        const int wide = std::min(2 * M, FGIM_MAX_K);
+        int32_t* w_ids = c.alloc<int32_t>(nl * wide);
+        float* w_dist = c.alloc<float>(nl * wide);
+        ck(launch_widen(e_ids, e_dist, nl, M, wide, w_ids, w_dist, c.s));
+        fgim_graph u;
+        std::memset(&u, 0, sizeof(u));
+        u.ids = c.alloc<int32_t>(nl * wide);
+        u.dist = c.alloc<float>(nl * wide);
+        u.deg = c.alloc<int32_t>(nl);
+        u.n = nl;
+        u.R = wide;
+        reverse_insert(c, nl, wide, w_ids, w_dist, e_cnt, &u);
+        fgim_knng g2;
+        std::memset(&g2, 0, sizeof(g2));
+        g2.ids = u.ids;
+        g2.dist = u.dist;
+        g2.n = nl;
+        g2.k = wide;
+        float* f_dist = c.alloc<float>(nl * M);
+        ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g2, T, M, 1.f, adj, f_dist, deg, c.status, c.s));
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
+                             const int32_t* graph_ids, int32_t R, const fgim_layer* layers, int32_t n_layers,
+                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam,
+                             int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(base && graph_ids && queries && out_ids && out_dist, FGIM_EINVAL, "NULL buffer");
+        need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
+        need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
+        need(dtype == FGIM_F32 || dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
+        need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
+        need(R >= 1 && R <= FGIM_MAX_DEGREE, FGIM_EINVAL, "R must be in [1, 128]");
+        need(entry >= 0 && entry < n, FGIM_EINVAL, "entry out of range");
+        need(nq >= 0, FGIM_EINVAL, "nq must be >= 0");
+        need(beam >= 1 && beam <= FGIM_MAX_L && topk >= 1 && topk <= beam, FGIM_EINVAL, "need 1 <= topk <= beam <= 128");
+        need(n_layers >= 0 && n_layers <= FGIM_MAX_LEVELS && (n_layers == 0 || layers), FGIM_EINVAL,
+             "n_layers must be in [0, 16]");
+        const uintptr_t am = dtype == FGIM_F32 ? 15u : 1u;
+        need(((uintptr_t)base & am) == 0 && ((uintptr_t)queries & am) == 0, FGIM_EINVAL, "vectors misaligned");
+        HnswLayers ly;
+        std::memset(&ly, 0, sizeof(ly));
+        ly.count = n_layers;
+        ly.M = n_layers ? layers[0].M : 1;
+        for (int l = 0; l < n_layers; ++l) {
+            need(layers[l].M == ly.M && ly.M >= 1 && ly.M <= 32, FGIM_EINVAL, "layers must share M in [1, 32]");
+            need(layers[l].n >= 0 && layers[l].n <= n && (layers[l].n == 0 || (layers[l].members && layers[l].adj)),
+                 FGIM_EINVAL, "bad layer");
+            ly.members[l] = layers[l].members;
+            ly.adj[l] = layers[l].adj;
+            ly.n[l] = layers[l].n;
+        }
+        if (nq == 0) return;
+        Ctx c((cudaStream_t)stream);
+        const float* X = f32_rows(c, base, n, dim, dtype);
+        const float* Q = f32_rows(c, queries, nq, dim, dtype);
+        float* inv = nullptr;
+        float* qinv = nullptr;
+        if (metric == FGIM_COSINE) {
+            inv = c.alloc<float>(n);
+            qinv = c.alloc<float>(nq);
+            ck(launch_inv_norms(X, n, dim, inv, c.s));
+            ck(launch_inv_norms(Q, nq, dim, qinv, c.s));
+        }
+        int32_t* start = out_start ? out_start : c.alloc<int32_t>(nq);
+        ck(launch_hnsw_descend(X, inv, dim, metric, ly, entry, Q, qinv, nq, start, c.status, c.s));
+        ck(launch_search(X, nullptr, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
+                         out_dist, c.ctr + 0, c.status, c.s,
+                         dtype == FGIM_BF16 ? static_cast<const uint16_t*>(base) : nullptr, start));
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
 fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                         const int32_t* graph_ids, int32_t R, int32_t entry, const void* queries, int32_t nq,
                         int32_t topk, int32_t beam, int32_t* out_ids, float* out_dist, void* stream) {

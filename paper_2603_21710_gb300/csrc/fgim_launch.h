@@ -21,7 +21,8 @@ cudaError_t launch_cross_query(const ShardTable& t, const float* X, const uint8_
 cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
                           const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
-                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh = nullptr);
+                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh = nullptr,
+                          const int32_t* qentry = nullptr);
 // X8[i] = X[i] as a byte; *flag |= 1 unless every X[i] is an integer in [0, 255] (n_elems % 4 == 0)
 cudaError_t launch_narrow_u8(const float* X, long long n_elems, uint8_t* X8, int* flag, cudaStream_t s);
 
@@ -149,5 +150,33 @@ cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, cons
                                 int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
                                 const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
                                 int4* plan, unsigned long long* attached, cudaStream_t s);
+
+// ---- k_hnsw.cu (HNSW-adaptive merging, Sec. 4.3.3)
+constexpr int kMaxHnswLevels = 16;
+struct HnswThresholds {   // T_l = floor((2^64 - 1) / M^l), l = 1 .. count
+    int count;
+    unsigned long long t[kMaxHnswLevels];
+};
+struct HnswLayers {       // layer l + 1 at index l: members (ascending global ids), adj [n, M] positions
+    int count;
+    int M;
+    const int32_t* members[kMaxHnswLevels];
+    const int32_t* adj[kMaxHnswLevels];
+    long long n[kMaxHnswLevels];
+};
+cudaError_t launch_hnsw_levels(long long n, unsigned long long seed, const HnswThresholds& th, int32_t* levels,
+                               cudaStream_t s);
+// flag[v] = levels[v] >= level
+cudaError_t launch_level_flags(const int32_t* levels, long long n, int level, int32_t* flag, cudaStream_t s);
+// rows of width M into rows of width w (padding -1 / +inf)
+cudaError_t launch_widen(const int32_t* ids, const float* dist, long long n, int M, int w, int32_t* oids, float* odist,
+                         cudaStream_t s);
+// the kk nearest rows of every row of Xl (n rows, FP32; X8l: the same as bytes or nullptr)
+cudaError_t launch_layer_knn(const float* Xl, const uint8_t* X8l, const float* inv, long long n, int d, int metric,
+                             int kk, int32_t* out_ids, float* out_dist, cudaStream_t s);
+// greedy descent of nq queries (FP32 rows of Q) through the layers from `entry`; start = the vertex reached
+cudaError_t launch_hnsw_descend(const float* X, const float* inv, int d, int metric, const HnswLayers& ly, int entry,
+                                const float* Q, const float* q_inv, long long nq, int32_t* start, int* status,
+                                cudaStream_t s);
 
 }  // namespace fgim

@@ -10,7 +10,7 @@ template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_search(const float* __restrict__ X, const RT* __restrict__ Xr,
                                                 const float* __restrict__ inv_norm,
                                                 long long n, int d, const int32_t* __restrict__ graph, int R,
-                                                int entry, const float* __restrict__ Q,
+                                                int entry, const int32_t* __restrict__ qentry, const float* __restrict__ Q,
                                                 const float* __restrict__ q_inv, const int32_t* __restrict__ qids,
                                                 long long nq, int topk, int L, int htbits,
                                                 int32_t* __restrict__ out_ids, float* __restrict__ out_dist,
@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_search(const f
     qb.q2 = 0u;
     if (sizeof(RT) == 1) qb = query_bytes(q, d, lane);
     WarpCounters ctr;
-    const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr, inv_norm, graph, R, n, entry, 0, q, qreg, qb, qinv, d, L,
+    const int ent = qentry ? qentry[qi] : entry;   // per-query entries (the HNSW descent's result)
+    const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr, inv_norm, graph, R, n, ent, 0, q, qreg, qb, qinv, d, L,
                                                          pool, pflag, ht, htbits, scratch, P, ctr, status);
     for (int s = lane; s < topk; s += 32) {
         if (s < np) {
@@ -58,7 +59,8 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_search(const f
 cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_norm, long long n, int d, int metric,
                           const int32_t* graph, int R, int entry, const float* Q, const float* q_inv,
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
-                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh) {
+                          unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh,
+                          const int32_t* qentry) {
     const int htbits = ht_bits_for(L);
     const int wpb = 4;
     const bool bytes = X8 && qids && byte_rows_ok(d);
@@ -73,7 +75,7 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
         if (e != cudaSuccess) break;                                                                               \
         LaunchScope ls("k_search", s);                                                                             \
         k_search<MT, SD, RT, MS><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                             \
-            X, reinterpret_cast<const RT*>(rows), inv_norm, n, d, graph, R, entry, Q, q_inv, qids, nq, topk, L,    \
+            X, reinterpret_cast<const RT*>(rows), inv_norm, n, d, graph, R, entry, qentry, Q, q_inv, qids, nq, topk, L, \
             htbits, out_ids, out_dist, counters, status);                                                          \
         e = cudaGetLastError();                                                                                    \
     } while (0)

@@ -626,3 +626,65 @@ def test_masks_rejected_where_not_honoured(small):
     with pytest.raises(fg.FgimError) as e:
         fg.refine_pass(some, _to_dev(o))
     assert e.value.status == -5
+
+
+# --------------------------------------------------------------------------- HNSW-adaptive merging
+def test_hnsw_levels_match_oracle():
+    import paper_2603_21710_gb300 as fg
+    _dev()
+    lv, counts = fg.hnsw_levels(20_000, 8, seed=1234)
+    ref = O.hnsw_levels(20_000, 8, seed=1234)
+    assert np.array_equal(_np(lv), ref)
+    assert counts[:5] == [int((ref >= l).sum()) for l in range(5)]
+
+
+def test_hnsw_layers_bit_exact(sift_like):
+    """Integer data: every upper layer (members, neighbour positions, degrees) equals the oracle's."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    X = torch.from_numpy(w.X).to(_dev())
+    built = fg.build_layers(X, M=8, ef=32, seed=7)
+    levels = O.hnsw_levels(w.N, 8, seed=7)
+    assert np.array_equal(_np(built["levels"]), levels)
+    assert len(built["layers"]) >= 3
+    for l, ly in enumerate(built["layers"], start=1):
+        members, adj, deg = O.hnsw_layer(w.X, w.metric, levels, l, 8, 32)
+        assert np.array_equal(_np(ly["members"]), members), l
+        assert np.array_equal(_np(ly["deg"]), deg), l
+        assert np.array_equal(_np(ly["adj"]), adj), l
+    assert built["entry"] == O.hnsw_entry(levels)
+
+
+def test_search_hnsw_matches_oracle(sift_like):
+    """The layered search: the same descent end points and results as the oracle's."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    dev = _dev()
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    gi = _np(out["ids"])
+    X = torch.from_numpy(w.X).to(dev)
+    built = fg.build_layers(X, M=8, ef=32, seed=7)
+    Q = w.Q[:200]
+    ids, dist, start = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], torch.from_numpy(Q).to(dev),
+                                      topk=10, beam=32)
+    layers = [(_np(ly["members"]), _np(ly["adj"])) for ly in built["layers"]]
+    oi, od, ost = O.hnsw_search(w.X, w.metric, gi, layers, built["entry"], Q, 32, 10)
+    assert np.array_equal(_np(start), ost)
+    assert np.array_equal(_np(ids), oi)
+    # the descent's start is never farther from the query than the entry
+    gt, _ = O.knn_exact(w.X, Q, 10, w.metric)
+    assert O.recall_at(_np(ids), gt, 10) >= O.recall_at(
+        _np(fg.search(X, out["ids"], out["entry"], torch.from_numpy(Q).to(dev), topk=10, beam=32)[0]), gt, 10) - 0.02
+
+
+def test_hnsw_layer_cosine_bf16(bf16_batch):
+    """768-d cosine, BF16 storage: layer 1 keeps the oracle's members and nearly all its rows."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P = bf16_batch[0]
+    Xb = torch.from_numpy(w.bits().view(np.int16)).to(_dev()).view(torch.bfloat16)
+    lv, counts = fg.hnsw_levels(w.N, 4, seed=3)
+    ly = fg.hnsw_layer(Xb, lv, 1, counts[1], M=4, ef=16, metric="cos")
+    members, adj, deg = O.hnsw_layer(w.X, w.metric, O.hnsw_levels(w.N, 4, seed=3), 1, 4, 16)
+    assert np.array_equal(_np(ly["members"]), members)
+    same = np.all(_np(ly["adj"]) == adj, 1).mean()
+    assert same >= 0.98, same

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form alongside")
     ap.add_argument("--no-masked", action="store_true",
                     help="skip timing the merge with invalid vertices (a quarter of them) alongside")
+    ap.add_argument("--no-hnsw", action="store_true",
+                    help="skip building the HNSW upper layers over the merged graph (timed) and their search recall")
     ap.add_argument("--batched", type=int, default=0, metavar="M",
                     help="instead: time the batched form, M merges of the 768-d BF16 cosine recipe (sizes "
                          "log-uniform in [--batched-lo, --batched-hi]) in one fgim_merge_batch call, against "
@@ -400,6 +402,24 @@ def run_fgim(args):
     hits = sum(len(set(a) & set(b)) for a, b in zip(sid.cpu().tolist(), gt.cpu().tolist()))
     recall = hits / (10 * nq_eval)
     del d2
+    # ---- HNSW-adaptive merging: upper layers over the merged graph (M = R / 2), timed with
+    # events after one untimed build, and the recall of the layered search at the same beam
+    hnsw = None
+    if not args.no_hnsw:
+        Mup = max(2, w.R // 2)
+        fg.build_layers(X, M=Mup, ef=64, seed=20260321)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        built = fg.build_layers(X, M=Mup, ef=64, seed=20260321)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        hid, _, _ = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], Q, topk=10, beam=64)
+        hh = sum(len(set(a) & set(b)) for a, b in zip(hid.cpu().tolist(), gt.cpu().tolist()))
+        hnsw = {"build_ms": h0.elapsed_time(h1), "M": Mup, "ef": 64,
+                "layer_sizes": [int(ly["members"].shape[0]) for ly in built["layers"]],
+                "recall@10": hh / (10 * nq_eval), "recall@10_flat": recall, "beam": 64}
+        del built
     # ---- end to end through the host-buffer entry point (pinned host inputs and outputs)
     e2e = None
     if not args.no_e2e:
@@ -452,6 +472,7 @@ def run_fgim(args):
             "stage_a_work_model": cpu["stage_a_per_query"] if cpu else None,
             "plain_fp32": plain,
             "masked": masked,
+            "hnsw": hnsw,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms}
     print(json.dumps(line), flush=True)
 

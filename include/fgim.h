@@ -247,7 +247,8 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
  * v-th output of SplitMix64 started from `seed`, level = #{l >= 1 : r_v < floor((2^64 - 1) /
  * M^l)}. Layer l holds the vertices of level >= l (ascending ids). Each layer is built from
  * its own vertices at once (the paper inserts them one at a time, which a GPU cannot do in a
- * fixed order in parallel): the exact `ef` nearest members, the RNG heuristic down to M
+ * fixed order in parallel): the exact `ef` nearest members among those with smaller ids
+ * (the members inserted before it, in id order), the RNG heuristic down to M
  * (Alg. 5's rule with alpha = 1 and no indegree clause), bidirectional edges, and the
  * heuristic again over the 2M nearest of a member's own and reverse edges. The search
  * descends greedily from the entry (the first vertex of the highest level) through the

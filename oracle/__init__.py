@@ -78,6 +78,7 @@ def lib():
                 "or_reach_fix": (None, [vp, i32, i32, i32, vp, vp, vp, vp]),
                 "or_merged_entry": (i32, [vp]),
                 "or_phi": (i64, [vp, vp]),
+                "or_knn_prefix": (None, [vp, i64, i32, i32, i32, i32, vp, vp]),
                 "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
                 "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
             }
@@ -351,9 +352,10 @@ def recall_at(found: np.ndarray, truth: np.ndarray, k: int) -> float:
 # (its published definition: state += 0x9E3779B97F4A7C15, then the two xor-shift-multiply
 # rounds), as the number of l >= 1 with r_v < floor((2^64 - 1) / M^l); each layer l is built
 # from its own vertices at once instead of by one-at-a-time insertion: the exact ef nearest
-# members (the limit of HNSW's candidate search), the RNG heuristic down to M (Alg. 5's rule
-# with alpha = 1 and no indegree clause), bidirectional edges, and the same heuristic over the
-# 2M nearest of a member's own and reverse edges.
+# members inserted before it in id order (the limit of HNSW's candidate search at insertion:
+# early members link far, as in HNSW), the RNG heuristic down to M (Alg. 5's rule with
+# alpha = 1 and no indegree clause), bidirectional edges, and the same heuristic over the 2M
+# nearest of a member's own and reverse edges.
 _GAMMA = 0x9E3779B97F4A7C15
 _U64 = (1 << 64) - 1
 MAX_LEVELS = 16
@@ -395,7 +397,9 @@ def hnsw_layer(X: np.ndarray, metric: int, levels: np.ndarray, level: int, M: in
     Xl = np.ascontiguousarray(X[members], dtype=np.float32)
     Pl = Problem(Xl, [n], np.full((n, 1), -1, np.int32), np.zeros(1, np.int32), metric)
     kk = min(ef, max(n - 1, 1))
-    ids, dist = knn_exact(Xl, Xl, kk, metric, exclude=np.arange(n))
+    ids = np.empty((n, kk), np.int32)
+    dist = np.empty((n, kk), np.float32)
+    lib().or_knn_prefix(Xl.ctypes.data, n, Xl.shape[1], metric, kk, 0, ids.ctypes.data, dist.ctypes.data)
     g = KNNG(n, kk)
     g.ids[:], g.dist[:] = ids, dist
     T = np.full(n, 2, np.int32)   # the indegree clause never fires

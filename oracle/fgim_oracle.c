@@ -180,6 +180,37 @@ int32_t or_knn_search(const float* X_local, int64_t n, int32_t d, int32_t metric
 /* ------------------------------------------------------------------------- */
 /* Exact k-NN (Definition k-NNS), exhaustive                                  */
 /* ------------------------------------------------------------------------- */
+/* For every row i of X: its k nearest rows among rows 0 .. i - 1 (the vertices inserted before it
+ * when rows are inserted in order), ascending (delta, id), -1 / +inf padded. */
+void or_knn_prefix(const float* X, int64_t N, int32_t d, int32_t metric, int32_t k, int32_t nthreads,
+                   int32_t* out_ids, float* out_dist) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t qi = 0; qi < N; ++qi) {
+        const float* q = X + qi * (int64_t)d;
+        float* bd = out_dist + qi * (int64_t)k;
+        int32_t* bi = out_ids + qi * (int64_t)k;
+        int32_t n = 0;
+        for (int64_t g = 0; g < qi; ++g) {
+            float dg = or_delta(q, X + g * (int64_t)d, d, metric);
+            if (n == k && !key_lt(dg, (int32_t)g, bd[k - 1], bi[k - 1])) continue;
+            int32_t pos = n < k ? n : k - 1;
+            while (pos > 0 && key_lt(dg, (int32_t)g, bd[pos - 1], bi[pos - 1])) {
+                bd[pos] = bd[pos - 1];
+                bi[pos] = bi[pos - 1];
+                --pos;
+            }
+            bd[pos] = dg;
+            bi[pos] = (int32_t)g;
+            if (n < k) ++n;
+        }
+        for (int32_t t = n; t < k; ++t) {
+            bi[t] = -1;
+            bd[t] = INFINITY;
+        }
+    }
+}
+
 void or_knn_exact(const float* X, int64_t N, int32_t d, int32_t metric, const float* Q, int64_t nq,
                   const int64_t* exclude, int32_t k, int32_t nthreads, int32_t* out_ids, float* out_dist) {
     set_threads(nthreads);

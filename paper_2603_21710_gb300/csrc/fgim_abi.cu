@@ -1029,8 +1029,8 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
         std::memset(&lp, 0, sizeof(lp));
         lp.metric = metric;
         finish_problem(c, L, &lp);
-        // the exact ef nearest members, the RNG heuristic to M, bidirectional edges, the
-        // heuristic again over the 2M nearest of own and reverse edges
+        // the exact ef nearest earlier members, the RNG heuristic to M, bidirectional edges,
+        // the heuristic again over the 2M nearest of own and reverse edges
         const int kk = (int)std::min<long long>(ef, std::max<long long>(nl - 1, 1));
         int32_t* k_ids = c.alloc<int32_t>(nl * kk);
         float* k_dist = c.alloc<float>(nl * kk);

@@ -171,7 +171,8 @@ cudaError_t launch_level_flags(const int32_t* levels, long long n, int level, in
 // rows of width M into rows of width w (padding -1 / +inf)
 cudaError_t launch_widen(const int32_t* ids, const float* dist, long long n, int M, int w, int32_t* oids, float* odist,
                          cudaStream_t s);
-// the kk nearest rows of every row of Xl (n rows, FP32; X8l: the same as bytes or nullptr)
+// the kk nearest rows of every row of Xl among the rows before it (n rows, FP32; X8l: the same
+// as bytes or nullptr)
 cudaError_t launch_layer_knn(const float* Xl, const uint8_t* X8l, const float* inv, long long n, int d, int metric,
                              int kk, int32_t* out_ids, float* out_dist, cudaStream_t s);
 // greedy descent of nq queries (FP32 rows of Q) through the layers from `entry`; start = the vertex reached

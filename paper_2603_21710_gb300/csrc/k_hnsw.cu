@@ -67,9 +67,9 @@ cudaError_t launch_widen(const int32_t* ids, const float* dist, long long n, int
     return cudaGetLastError();
 }
 
-// The kk nearest rows of every row u of Xl (n rows) other than u itself, by (delta, row):
-// warp per row, 32 candidate rows per step through the canonical distances of the beam
-// search, kept in a sorted list in shared memory.
+// The kk nearest rows of every row u of Xl (n rows) among the rows before it (the members
+// inserted before u in id order), by (delta, row): warp per row, 32 candidate rows per step
+// through the canonical distances of the beam search, kept in a sorted list in shared memory.
 template <int METRIC, bool SMALLD, typename RT>
 __global__ void __launch_bounds__(128) k_layer_knn(const float* __restrict__ Xl, const RT* __restrict__ Xr,
                                                    const float* __restrict__ inv, long long n, int d, int kk,
@@ -96,9 +96,9 @@ __global__ void __launch_bounds__(128) k_layer_knn(const float* __restrict__ Xl,
     if (sizeof(RT) == 1) qb = query_bytes(q, d, lane);
     const float qinv = METRIC == FGIM_COSINE ? inv[u] : 1.f;
     int nl = 0;
-    for (long long c0 = 0; c0 < n; c0 += 32) {
+    for (long long c0 = 0; c0 < u; c0 += 32) {
         const long long v = c0 + lane;
-        const bool ok = v < n && v != u;
+        const bool ok = v < u;
         const unsigned m = __ballot_sync(kFull, ok);
         const int U = __popc(m);
         if (ok) scratch[__popc(m & lt)] = (int32_t)v;

@@ -610,3 +610,23 @@ def test_hnsw_search_descends_to_the_nearest_member():
     ids, dist, starts = O.hnsw_search(X, 0, base, [(members, adj)], 0, Q, beam=4, topk=2)
     assert list(starts) == [6, 0]
     assert list(ids[0]) == [7, 8] and list(ids[1]) == [1, 2]
+
+
+def test_hnsw_layer_links_across_clusters():
+    """Two far clusters with interleaved ids: a member links to its nearest among the members
+    inserted before it, so early members link across the gap and the layer stays connected
+    (nearest neighbours over all members, ef = 8, would split it in two)."""
+    rng = np.random.default_rng(4)
+    a = rng.normal(0, 0.1, (20, 4))
+    b = rng.normal(0, 0.1, (20, 4)) + 100.0
+    X = np.empty((40, 4), np.float32)
+    X[0::2], X[1::2] = a, b
+    members, adj, deg = O.hnsw_layer(X, 0, np.ones(40, np.int32), 1, M=4, ef=8)
+    seen, todo = {0}, [0]
+    while todo:
+        u = todo.pop()
+        for v in list(adj[u][:deg[u]]) + [x for x in range(40) if u in adj[x][:deg[x]]]:
+            if v not in seen:
+                seen.add(int(v))
+                todo.append(int(v))
+    assert len(seen) == 40

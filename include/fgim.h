@@ -250,7 +250,8 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
  * fixed order in parallel): the exact `ef` nearest members among those with smaller ids
  * (the members inserted before it, in id order), the RNG heuristic down to M
  * (Alg. 5's rule with alpha = 1 and no indegree clause), bidirectional edges, and the
- * heuristic again over the 2M nearest of a member's own and reverse edges. The search
+ * heuristic again over the union of a member's own and reverse edges (the 128 nearest of it
+ * when larger). The search
  * descends greedily from the entry (the first vertex of the highest level) through the
  * layers, then runs Alg. 1 on the base graph from the vertex it reached. */
 #define FGIM_MAX_LEVELS 16

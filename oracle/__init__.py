@@ -354,8 +354,8 @@ def recall_at(found: np.ndarray, truth: np.ndarray, k: int) -> float:
 # from its own vertices at once instead of by one-at-a-time insertion: the exact ef nearest
 # members inserted before it in id order (the limit of HNSW's candidate search at insertion:
 # early members link far, as in HNSW), the RNG heuristic down to M (Alg. 5's rule with
-# alpha = 1 and no indegree clause), bidirectional edges, and the same heuristic over the 2M
-# nearest of a member's own and reverse edges.
+# alpha = 1 and no indegree clause), bidirectional edges, and the same heuristic over the
+# union of a member's own and reverse edges (its 128 nearest when larger).
 _GAMMA = 0x9E3779B97F4A7C15
 _U64 = (1 << 64) - 1
 MAX_LEVELS = 16
@@ -404,7 +404,7 @@ def hnsw_layer(X: np.ndarray, metric: int, levels: np.ndarray, level: int, M: in
     g.ids[:], g.dist[:] = ids, dist
     T = np.full(n, 2, np.int32)   # the indegree clause never fires
     e_ids, e_dist, e_cnt, _ = prune(Pl, g, T, M, 1.0)
-    wide = min(2 * M, 128)
+    wide = 128   # the union of own and reverse edges (its 128 nearest if larger)
     pad_i = np.full((n, wide), -1, np.int32)
     pad_d = np.full((n, wide), np.inf, np.float32)
     pad_i[:, :M], pad_d[:, :M] = e_ids, e_dist

@@ -1030,7 +1030,7 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
         lp.metric = metric;
         finish_problem(c, L, &lp);
         // the exact ef nearest earlier members, the RNG heuristic to M, bidirectional edges,
-        // the heuristic again over the 2M nearest of own and reverse edges
+        // the heuristic again over the union of own and reverse edges
         const int kk = (int)std::min<long long>(ef, std::max<long long>(nl - 1, 1));
         int32_t* k_ids = c.alloc<int32_t>(nl * kk);
         float* k_dist = c.alloc<float>(nl * kk);
@@ -1047,7 +1047,7 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
         float* e_dist = c.alloc<float>(nl * M);
         int32_t* e_cnt = c.alloc<int32_t>(nl);
         ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, 1.f, e_ids, e_dist, e_cnt, c.status, c.s));
-        const int wide = std::min(2 * M, FGIM_MAX_K);
+        const int wide = FGIM_MAX_K;   // own and reverse edges together (their 128 nearest if more)
         int32_t* w_ids = c.alloc<int32_t>(nl * wide);
         float* w_dist = c.alloc<float>(nl * wide);
         ck(launch_widen(e_ids, e_dist, nl, M, wide, w_ids, w_dist, c.s));

@@ -79,6 +79,7 @@ def lib():
                 "or_merged_entry": (i32, [vp]),
                 "or_phi": (i64, [vp, vp]),
                 "or_knn_prefix": (None, [vp, i64, i32, i32, i32, i32, vp, vp]),
+                "or_refine_dfs": (None, [vp, i32, i32, vp, vp, vp, vp, vp]),
                 "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
                 "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
             }
@@ -218,6 +219,17 @@ def refine_iter(P: Problem, g: KNNG, rev_cap: int = 0):
     lib().or_refine_iter(P.ref, k, rev_cap, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data,
                          ctypes.byref(st))
     return st.as_dict()
+
+
+def refine_dfs(P: Problem, g: KNNG, iters: int):
+    """Alg. 3 as printed (DFS order, streamlined Visit + Update, lists updated at once), each
+    iteration followed by Alg. 4; in place on ``g``. Returns (T, stats)."""
+    k = g.ids.shape[1]
+    T = np.empty(P.N, np.int32)
+    st = Stats()
+    lib().or_refine_dfs(P.ref, k, iters, g.ids.ctypes.data, g.dist.ctypes.data, g.flags.ctypes.data, T.ctypes.data,
+                        ctypes.byref(st))
+    return T, st.as_dict()
 
 
 def indegree(ids: np.ndarray) -> np.ndarray:

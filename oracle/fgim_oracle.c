@@ -861,6 +861,105 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
     free(npar);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Alg. 3 as printed: the streamlined (one pass per vertex) refinement in DFS   */
+/* order, reverse graphs kept across iterations, lists updated at once (the     */
+/* quality comparison for the synchronous form above). Sequential.              */
+/* ------------------------------------------------------------------------- */
+typedef struct { int32_t* v; int32_t n, cap; } ivec_t;
+
+static void ivec_push(ivec_t* a, int32_t x) {
+    if (a->n == a->cap) {
+        a->cap = a->cap ? 2 * a->cap : 8;
+        a->v = (int32_t*)realloc(a->v, sizeof(int32_t) * a->cap);
+    }
+    a->v[a->n++] = x;
+}
+
+static int ivec_has(const int32_t* v, int32_t n, int32_t x) {
+    for (int32_t i = 0; i < n; ++i)
+        if (v[i] == x) return 1;
+    return 0;
+}
+
+void or_refine_dfs(const or_input* in, int32_t k, int32_t iters, int32_t* ids, float* dist, uint8_t* flags,
+                   int32_t* T, or_stats* st) {
+    const int64_t N = in->off[in->h];
+    ivec_t* rn = (ivec_t*)calloc(N, sizeof(ivec_t));   /* reverse graph of new entries */
+    ivec_t* ro = (ivec_t*)calloc(N, sizeof(ivec_t));   /* of old entries */
+    uint8_t* seen = (uint8_t*)malloc(N);
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (N + 1));
+    ivec_t cn = {0, 0, 0}, co = {0, 0, 0};
+    for (int32_t it = 0; it < iters; ++it) {
+        memset(seen, 0, N);
+        for (int64_t u0 = 0; u0 < N; ++u0) {
+            if (seen[u0]) continue;
+            int64_t sp = 0;
+            stack[sp++] = (int32_t)u0;
+            seen[u0] = 1;
+            while (sp > 0) {
+                const int32_t v = stack[--sp];
+                /* Visit v: its forward entries split new / old (new ones become old), each
+                 * recorded in the partner's reverse graph */
+                cn.n = co.n = 0;
+                for (int32_t t = 0; t < k; ++t) {
+                    const int32_t w = ids[(int64_t)v * k + t];
+                    if (w < 0) continue;
+                    if (flags[(int64_t)v * k + t] & OR_FLAG_NEW) {
+                        ivec_push(&cn, w);
+                        flags[(int64_t)v * k + t] &= (uint8_t)~OR_FLAG_NEW;
+                        ivec_push(&rn[w], v);
+                    } else {
+                        ivec_push(&co, w);
+                        ivec_push(&ro[w], v);
+                    }
+                }
+                /* DFS: the neighbours of v next */
+                for (int32_t t = k - 1; t >= 0; --t) {
+                    const int32_t w = ids[(int64_t)v * k + t];
+                    if (w >= 0 && !seen[w]) {
+                        seen[w] = 1;
+                        stack[sp++] = w;
+                    }
+                }
+                /* move the reverse entries recorded for v into its candidate sets */
+                for (int32_t i = 0; i < rn[v].n; ++i)
+                    if (!ivec_has(cn.v, cn.n, rn[v].v[i])) ivec_push(&cn, rn[v].v[i]);
+                for (int32_t i = 0; i < ro[v].n; ++i)
+                    if (!ivec_has(cn.v, cn.n, ro[v].v[i]) && !ivec_has(co.v, co.n, ro[v].v[i]))
+                        ivec_push(&co, ro[v].v[i]);
+                rn[v].n = ro[v].n = 0;
+                /* Update: C_n^2 and C_n x C_o, cross-graph pairs, lists changed at once */
+                for (int32_t i = 0; i < cn.n; ++i) {
+                    const int32_t a = cn.v[i];
+                    for (int32_t j = 0; j < cn.n + co.n; ++j) {
+                        if (j < cn.n && j <= i) continue;
+                        const int32_t b = j < cn.n ? cn.v[j] : co.v[j - cn.n];
+                        if (a == b || shard_of(in, a) == shard_of(in, b)) continue;
+                        const float d = dist_g(in, a, b);
+                        if (st) st->pairs++;
+                        if (list_insert(ids + (int64_t)a * k, dist + (int64_t)a * k, flags + (int64_t)a * k, k, b, d) && st)
+                            st->updates++;
+                        if (list_insert(ids + (int64_t)b * k, dist + (int64_t)b * k, flags + (int64_t)b * k, k, a, d) && st)
+                            st->updates++;
+                    }
+                }
+            }
+        }
+        or_indegree_repair(in, k, ids, dist, flags, T, st);
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        free(rn[v].v);
+        free(ro[v].v);
+    }
+    free(rn);
+    free(ro);
+    free(seen);
+    free(stack);
+    free(cn.v);
+    free(co.v);
+}
+
 int32_t or_merged_entry(const or_input* in) {
     /* the shard with the most valid vertices (lowest index on ties) */
     int best = 0;

@@ -103,6 +103,11 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
 
 /* Global id of the merged entry point: phi(entry of the largest shard, lowest shard index on ties). */
 int32_t or_merged_entry(const or_input* in);
+/* Alg. 3 as printed (DFS order, Visit and Update in one pass per vertex, lists updated at once,
+ * reverse graphs kept across iterations), `iters` iterations each followed by Alg. 4; T gets
+ * the indegrees after the last repair. The quality comparison for or_refine_iter. */
+void or_refine_dfs(const or_input* in, int32_t k, int32_t iters, int32_t* ids, float* dist, uint8_t* flags,
+                   int32_t* T, or_stats* st);
 void or_knn_prefix(const float* X, int64_t N, int32_t d, int32_t metric, int32_t k, int32_t nthreads,
                    int32_t* out_ids, float* out_dist);
 /* phi of Sec. 4.1.3 from in->valid: phi[g] = global id of g in the merged index or -1.

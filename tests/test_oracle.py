@@ -630,3 +630,28 @@ def test_hnsw_layer_links_across_clusters():
                 seen.add(int(v))
                 todo.append(int(v))
     assert len(seen) == 40
+
+
+def test_synchronous_refinement_matches_the_literal_dfs_form_in_quality():
+    """Alg. 3 as printed (DFS order, streamlined Visit + Update) against the synchronous form
+    the GPU runs: both raise the k-NNG recall of stage (a), and the synchronous form stays
+    within one point of the literal one after three iterations; the literal form's lists are
+    valid k-NN lists."""
+    from synth import gen, pgbuild
+    from tests import _parity as PR
+    w = gen.make("small", N=20_000, nq=10)
+    graphs = pgbuild.build_all(w)
+    P = O.Problem.from_workload(w, graphs)
+    g0, _, _ = O.stage_a(P, w.k)
+    samp = np.random.default_rng(9).choice(w.N, 1000, replace=False)
+    tid, _ = O.knn_exact(w.X, w.X[samp], w.k, w.metric, exclude=samp)
+    gs = g0.copy()
+    for _ in range(3):
+        O.refine_iter(P, gs)
+        O.indegree_repair(P, gs)
+    gd = g0.copy()
+    O.refine_dfs(P, gd, 3)
+    PR.check_lists(gd.ids, gd.dist, w.N)
+    r0, rs, rd = (O.recall_at(g.ids[samp], tid, w.k) for g in (g0, gs, gd))
+    assert rs > r0 + 0.01 and rd > r0 + 0.01
+    assert abs(rs - rd) <= 0.01, (rs, rd)

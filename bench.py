@@ -414,11 +414,11 @@ def run_fgim(args):
         built = fg.build_layers(X, M=Mup, ef=64, seed=20260321)
         h1.record(stream)
         torch.cuda.synchronize()
-        hid, _, _ = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], Q, topk=10, beam=64)
+        hid, _, _ = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], Q, topk=10, beam=64, ef_up=8)
         hh = sum(len(set(a) & set(b)) for a, b in zip(hid.cpu().tolist(), gt.cpu().tolist()))
         hnsw = {"build_ms": h0.elapsed_time(h1), "M": Mup, "ef": 64,
                 "layer_sizes": [int(ly["members"].shape[0]) for ly in built["layers"]],
-                "recall@10": hh / (10 * nq_eval), "recall@10_flat": recall, "beam": 64}
+                "recall@10": hh / (10 * nq_eval), "recall@10_flat": recall, "beam": 64, "ef_up": 8}
         del built
     # ---- end to end through the host-buffer entry point (pinned host inputs and outputs)
     e2e = None

@@ -251,16 +251,15 @@ fgim_status fgim_search_noalloc(const void* base, int64_t n, int32_t dim, int32_
  * (the members inserted before it, in id order), the RNG heuristic down to M
  * (Alg. 5's rule with alpha = 1 and no indegree clause), bidirectional edges, and the
  * heuristic again over the union of a member's own and reverse edges (the 128 nearest of it
- * when larger). The search
- * descends greedily from the entry (the first vertex of the highest level) through the
- * layers, then runs Alg. 1 on the base graph from the vertex it reached. */
+ * when larger). The search goes down from the entry (the first vertex of the highest level)
+ * layer by layer, then runs Alg. 1 on the base graph from the vertex it reached. */
 #define FGIM_MAX_LEVELS 16
 
 typedef struct {
     const int32_t* members;  /* [n] ascending global ids of the layer's vertices */
     const int32_t* adj;      /* [n, M] neighbours as positions in members, -1 padded */
     int64_t n;
-    int32_t M;               /* 1 .. 32 for the search */
+    int32_t M;
     int32_t reserved;
 } fgim_layer;
 
@@ -277,11 +276,13 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
                             int32_t* adj, int32_t* deg, int64_t n_layer, void* stream);
 
 /* fgim_search with the upper layers: layers[l - 1] is layer l (host array of n_layers
- * descriptors, device buffers; all with the same M <= 32); entry: the top vertex.
- * out_start (optional, device [nq]): the base-graph vertex each query's descent reached. */
+ * descriptors, device buffers); entry: the top vertex. From the top, each layer is searched
+ * with Alg. 1 (pool ef_up in [1, 128]; 1 = HNSW's greedy descent) from the vertex the layer
+ * above gave, and its nearest result starts the next; the base graph is then searched with
+ * pool `beam`. out_start (optional, device [nq]): the base-graph vertex each query started from. */
 fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                              const int32_t* graph_ids, int32_t R, const fgim_layer* layers, int32_t n_layers,
-                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam,
+                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam, int32_t ef_up,
                              int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream);
 
 /* Counters of the last merge/search call made by this host thread. */

@@ -432,38 +432,26 @@ def hnsw_entry(levels: np.ndarray) -> int:
     return int(np.argmax(levels))
 
 
-def hnsw_search(X, metric, base_ids, layers, entry, Q, beam, topk):
-    """Greedy descent through the upper layers (top first; move to the neighbour with the
-    smallest (distance, id) while it beats the current vertex), then Alg. 1 on the base graph
-    from the vertex reached. layers[l - 1] = (members, adj) of layer l."""
+def hnsw_search(X, metric, base_ids, layers, entry, Q, beam, topk, ef_up: int = 8):
+    """The layered search: from the entry (top layer) down, each upper layer is searched with
+    Alg. 1 (pool ef_up; ef_up = 1 is HNSW's greedy descent) from the vertex the layer above
+    gave, its nearest result starting the next layer; then Alg. 1 on the base graph from the
+    vertex reached. layers[l - 1] = (members, adj) of layer l."""
     X = np.ascontiguousarray(X, dtype=np.float32)
+    rows = [np.ascontiguousarray(X[m]) for m, _ in layers]
     out_i = np.empty((len(Q), topk), np.int32)
     out_d = np.empty((len(Q), topk), np.float32)
     starts = np.empty(len(Q), np.int32)
     for qi, q in enumerate(np.ascontiguousarray(Q, dtype=np.float32)):
         cur = entry
-        dcur = delta(q, X[cur], metric)
-        for members, adj in reversed(layers):
+        for (members, adj), Xl in zip(reversed(layers), reversed(rows)):
             if len(members) == 0:
                 continue
             pos = int(np.searchsorted(members, cur))
             if pos >= len(members) or members[pos] != cur:
                 continue
-            moved = True
-            while moved:
-                moved = False
-                best = (dcur, cur)
-                for nb in adj[pos]:
-                    if nb < 0:
-                        continue
-                    v = int(members[nb])
-                    key = (delta(q, X[v], metric), v)
-                    if key < best:
-                        best = key
-                if best[1] != cur:
-                    dcur, cur = best
-                    pos = int(np.searchsorted(members, cur))
-                    moved = True
+            i, _, _ = search(Xl, adj, pos, q[None], ef_up, 1, metric)
+            cur = int(members[i[0][0]])
         starts[qi] = cur
         i, d, _ = search(X, base_ids, cur, q[None], beam, topk, metric)
         out_i[qi], out_d[qi] = i[0], d[0]

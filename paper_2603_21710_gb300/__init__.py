@@ -375,9 +375,10 @@ def build_layers(X: torch.Tensor, M: int, ef: int = 64, seed: int = 0, metric="l
 
 
 def search_hnsw(X: torch.Tensor, graph_ids: torch.Tensor, layers: Sequence[dict], entry: int, queries: torch.Tensor,
-                topk: int = 10, beam: int = 64, metric="l2"):
-    """Greedy descent through the upper layers, then Alg. 1 on the base graph:
-    (ids [nq, topk], dist, start [nq] = the base vertex each descent reached)."""
+                topk: int = 10, beam: int = 64, metric="l2", ef_up: int = 8):
+    """The layered search: each upper layer searched with Alg. 1 (pool ef_up; 1 = greedy) from
+    the top, then Alg. 1 on the base graph: (ids [nq, topk], dist, start [nq] = the base vertex
+    each query started from)."""
     L_ = load()
     X = _vec(X, "X")
     Q = _vec(queries, "queries")
@@ -393,8 +394,8 @@ def search_hnsw(X: torch.Tensor, graph_ids: torch.Tensor, layers: Sequence[dict]
     dist = torch.empty((nq, topk), dtype=torch.float32, device=X.device)
     start = torch.empty((nq,), dtype=torch.int32, device=X.device)
     check(L_.fgim_search_hnsw(_p(X), int(X.shape[0]), int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric],
-                              _p(G), int(G.shape[1]), arr, len(layers), int(entry), _p(Q), nq, topk, beam, _p(ids),
-                              _p(dist), _p(start), _stream()))
+                              _p(G), int(G.shape[1]), arr, len(layers), int(entry), _p(Q), nq, topk, beam,
+                              int(ef_up), _p(ids), _p(dist), _p(start), _stream()))
     return ids, dist, start
 
 

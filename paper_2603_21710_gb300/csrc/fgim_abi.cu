@@ -1075,7 +1075,7 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
 
 fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                              const int32_t* graph_ids, int32_t R, const fgim_layer* layers, int32_t n_layers,
-                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam,
+                             int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam, int32_t ef_up,
                              int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream) {
     begin_call();
     fgim_status r = guarded([&] {
@@ -1088,21 +1088,17 @@ fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t d
         need(entry >= 0 && entry < n, FGIM_EINVAL, "entry out of range");
         need(nq >= 0, FGIM_EINVAL, "nq must be >= 0");
         need(beam >= 1 && beam <= FGIM_MAX_L && topk >= 1 && topk <= beam, FGIM_EINVAL, "need 1 <= topk <= beam <= 128");
+        need(ef_up >= 1 && ef_up <= FGIM_MAX_L, FGIM_EINVAL, "ef_up must be in [1, 128]");
         need(n_layers >= 0 && n_layers <= FGIM_MAX_LEVELS && (n_layers == 0 || layers), FGIM_EINVAL,
              "n_layers must be in [0, 16]");
         const uintptr_t am = dtype == FGIM_F32 ? 15u : 1u;
         need(((uintptr_t)base & am) == 0 && ((uintptr_t)queries & am) == 0, FGIM_EINVAL, "vectors misaligned");
-        HnswLayers ly;
-        std::memset(&ly, 0, sizeof(ly));
-        ly.count = n_layers;
-        ly.M = n_layers ? layers[0].M : 1;
-        for (int l = 0; l < n_layers; ++l) {
-            need(layers[l].M == ly.M && ly.M >= 1 && ly.M <= 32, FGIM_EINVAL, "layers must share M in [1, 32]");
-            need(layers[l].n >= 0 && layers[l].n <= n && (layers[l].n == 0 || (layers[l].members && layers[l].adj)),
+        std::vector<int> live;   // the non-empty layers, top first
+        for (int l = n_layers - 1; l >= 0; --l) {
+            need(layers[l].n >= 0 && layers[l].n <= n && layers[l].M >= 1 && layers[l].M <= FGIM_MAX_DEGREE &&
+                     (layers[l].n == 0 || (layers[l].members && layers[l].adj)),
                  FGIM_EINVAL, "bad layer");
-            ly.members[l] = layers[l].members;
-            ly.adj[l] = layers[l].adj;
-            ly.n[l] = layers[l].n;
+            if (layers[l].n > 0) live.push_back(l);
         }
         if (nq == 0) return;
         Ctx c((cudaStream_t)stream);
@@ -1117,7 +1113,32 @@ fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t d
             ck(launch_inv_norms(Q, nq, dim, qinv, c.s));
         }
         int32_t* start = out_start ? out_start : c.alloc<int32_t>(nq);
-        ck(launch_hnsw_descend(X, inv, dim, metric, ly, entry, Q, qinv, nq, start, c.status, c.s));
+        int32_t* qpos = c.alloc<int32_t>(nq);
+        int32_t* best = c.alloc<int32_t>(nq);
+        float* bdist = c.alloc<float>(nq);
+        if (live.empty()) {
+            ck(launch_hnsw_next(nullptr, nullptr, 0, nullptr, 0, nq, 1, entry, qpos, start, c.status, c.s));
+        } else {
+            // every query starts at the entry's position in the top layer; each layer is searched
+            // with Alg. 1 (pool ef_up) and its nearest result starts the layer below
+            const fgim_layer& t0 = layers[live[0]];
+            ck(launch_hnsw_next(nullptr, nullptr, 0, t0.members, t0.n, nq, 1, entry, qpos, start, c.status, c.s));
+            for (size_t i = 0; i < live.size(); ++i) {
+                const fgim_layer& ly = layers[live[i]];
+                float* Xl = c.alloc<float>(ly.n * dim);
+                ck(launch_gather_rows(X, ly.members, ly.n, dim, Xl, c.s));
+                float* invl = nullptr;
+                if (metric == FGIM_COSINE) {
+                    invl = c.alloc<float>(ly.n);
+                    ck(launch_inv_norms(Xl, ly.n, dim, invl, c.s));
+                }
+                ck(launch_search(Xl, nullptr, invl, ly.n, dim, metric, ly.adj, ly.M, 0, Q, qinv, nullptr, nq, 1, ef_up,
+                                 best, bdist, c.ctr + 0, c.status, c.s, nullptr, qpos));
+                const fgim_layer* nx = i + 1 < live.size() ? &layers[live[i + 1]] : nullptr;
+                ck(launch_hnsw_next(best, ly.members, ly.n, nx ? nx->members : nullptr, nx ? nx->n : 0, nq, 0, entry,
+                                    qpos, start, c.status, c.s));
+            }
+        }
         ck(launch_search(X, nullptr, inv, n, dim, metric, graph_ids, R, entry, Q, qinv, nullptr, nq, topk, beam, out_ids,
                          out_dist, c.ctr + 0, c.status, c.s,
                          dtype == FGIM_BF16 ? static_cast<const uint16_t*>(base) : nullptr, start));

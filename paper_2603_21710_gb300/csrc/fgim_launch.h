@@ -157,13 +157,6 @@ struct HnswThresholds {   // T_l = floor((2^64 - 1) / M^l), l = 1 .. count
     int count;
     unsigned long long t[kMaxHnswLevels];
 };
-struct HnswLayers {       // layer l + 1 at index l: members (ascending global ids), adj [n, M] positions
-    int count;
-    int M;
-    const int32_t* members[kMaxHnswLevels];
-    const int32_t* adj[kMaxHnswLevels];
-    long long n[kMaxHnswLevels];
-};
 cudaError_t launch_hnsw_levels(long long n, unsigned long long seed, const HnswThresholds& th, int32_t* levels,
                                cudaStream_t s);
 // flag[v] = levels[v] >= level
@@ -175,9 +168,10 @@ cudaError_t launch_widen(const int32_t* ids, const float* dist, long long n, int
 // as bytes or nullptr)
 cudaError_t launch_layer_knn(const float* Xl, const uint8_t* X8l, const float* inv, long long n, int d, int metric,
                              int kk, int32_t* out_ids, float* out_dist, cudaStream_t s);
-// greedy descent of nq queries (FP32 rows of Q) through the layers from `entry`; start = the vertex reached
-cudaError_t launch_hnsw_descend(const float* X, const float* inv, int d, int metric, const HnswLayers& ly, int entry,
-                                const float* Q, const float* q_inv, long long nq, int32_t* start, int* status,
-                                cudaStream_t s);
+// hand-over between layer searches: best (positions in mem) -> qpos (positions in next) or,
+// with next == nullptr, start (global ids); first: every query starts at entry's position
+cudaError_t launch_hnsw_next(const int32_t* best, const int32_t* mem, long long nmem, const int32_t* next,
+                             long long nnext, long long nq, int first, int entry, int32_t* qpos, int32_t* start,
+                             int* status, cudaStream_t s);
 
 }  // namespace fgim

@@ -1,15 +1,9 @@
 // HNSW-adaptive merging (Sec. 4.3.3): levels of the merged vertices, the exact neighbours of a
-// layer's members (the candidates the RNG heuristic then prunes, see fgim_abi.cu), and the
-// greedy descent through the upper layers that gives each query its base-layer entry.
+// layer's members among the earlier ones (the candidates the RNG heuristic then prunes, see
+// fgim_abi.cu), and the hand-over between the per-layer searches of the layered search.
 #include "k_beam.cuh"
 
 namespace fgim {
-
-__device__ __forceinline__ uint64_t shfl64_xor_(uint64_t v, int m) {
-    const uint32_t lo = __shfl_xor_sync(kFull, (uint32_t)v, m);
-    const uint32_t hi = __shfl_xor_sync(kFull, (uint32_t)(v >> 32), m);
-    return ((uint64_t)hi << 32) | lo;
-}
 
 // SplitMix64's v-th output from state `seed` (its published definition), and the level
 // #{l >= 1 : r < T_l} with T_l = floor((2^64 - 1) / M^l)
@@ -159,115 +153,49 @@ cudaError_t launch_layer_knn(const float* Xl, const uint8_t* X8l, const float* i
     return e;
 }
 
-// Greedy descent through the upper layers (top first): from the current vertex move to the
-// neighbour of smallest (delta, id) while it beats the current vertex's key; a vertex absent
-// from a layer keeps its place. Warp per query; start[qi] = the vertex reached. Every move
-// lowers the key, so a layer takes at most its size of moves.
-template <int METRIC, bool SMALLD>
-__global__ void __launch_bounds__(128) k_hnsw_descend(const float* __restrict__ X, const float* __restrict__ inv,
-                                                      int d, HnswLayers ly, int entry, const float* __restrict__ Q,
-                                                      const float* __restrict__ q_inv, long long nq,
-                                                      int32_t* __restrict__ start, int* status) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5;
-    const int lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
-    const long long qi = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+// Between the layer searches of the layered search: query qi's nearest result in layer l
+// (a position there) becomes its start in the layer below (a position in `next`, which holds
+// every vertex of layer l since levels nest) or, after layer 1, its base-graph entry (a
+// global id in `start`). first: every query starts at `entry`'s position in `mem`.
+__global__ void k_hnsw_next(const int32_t* __restrict__ best, const int32_t* __restrict__ mem, long long nmem,
+                            const int32_t* __restrict__ next, long long nnext, long long nq, int first, int entry,
+                            int32_t* __restrict__ qpos, int32_t* __restrict__ start, int* status) {
+    const long long qi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= nq) return;
-    const size_t per_warp = (size_t)align16(d * 4) + 32 * 4 + 32 * 33 * 4;
-    unsigned char* base = smem + per_warp * warp;
-    float* q = reinterpret_cast<float*>(base);
-    int32_t* scratch = reinterpret_cast<int32_t*>(base + align16(d * 4));
-    float* P = reinterpret_cast<float*>(base + align16(d * 4) + 32 * 4);
-    const float4* src = reinterpret_cast<const float4*>(Q + qi * d);
-    for (int c = lane; c < (d >> 2); c += 32) reinterpret_cast<float4*>(q)[c] = src[c];
-    __syncwarp();
-    const float4 qreg = (SMALLD && lane < (d >> 2)) ? reinterpret_cast<const float4*>(q)[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    QBytes qb;
-    qb.w = make_uint4(0u, 0u, 0u, 0u);
-    qb.q2 = 0u;
-    const float qinv = METRIC == FGIM_COSINE ? q_inv[qi] : 1.f;
-    int32_t cur = entry;
-    if (lane == 0) scratch[0] = cur;
-    __syncwarp();
-    float dd = rows_delta<METRIC, SMALLD, float>(X, scratch, 1, q, qreg, qb, d, lane, P);
-    uint64_t ckey = mkkey(delta_finish<METRIC>(__shfl_sync(kFull, dd, 0),
-                                               METRIC == FGIM_COSINE ? __fmul_rn(qinv, inv[cur]) : 1.f), cur);
-    for (int l = ly.count - 1; l >= 0; --l) {
-        const int32_t* mem = ly.members[l];
-        const int32_t* adj = ly.adj[l];
-        const long long nl = ly.n[l];
-        const int M = ly.M;
-        // position of cur among the layer's members (ascending)
-        long long lo = 0, hi = nl;
-        while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if (mem[mid] < cur) lo = mid + 1;
-            else hi = mid;
+    int32_t g = entry;
+    if (!first) {
+        const int32_t p = best[qi];
+        if (p < 0 || p >= nmem) {
+            atomicOr(status, kErrBounds);
+            return;
         }
-        if (lo >= nl || mem[lo] != cur) continue;
-        long long pos = lo;
-        for (long long step = 0; step <= nl; ++step) {
-            const int32_t nb = lane < M ? adj[pos * M + lane] : -1;
-            const bool okn = nb >= 0 && nb < nl;
-            if (nb >= nl) atomicOr(status, kErrBounds);
-            const int32_t v = okn ? mem[nb] : -1;
-            const unsigned m = __ballot_sync(kFull, okn);
-            const int U = __popc(m);
-            if (U == 0) break;
-            if (okn) scratch[__popc(m & lt)] = v;
-            __syncwarp();
-            dd = rows_delta<METRIC, SMALLD, float>(X, scratch, U, q, qreg, qb, d, lane, P);
-            uint64_t key = kEmptyKey;
-            if (lane < U) {
-                const int32_t w = scratch[lane];
-                key = mkkey(delta_finish<METRIC>(dd, METRIC == FGIM_COSINE ? __fmul_rn(qinv, inv[w]) : 1.f), w);
-            }
-            __syncwarp();
-            uint64_t best = key;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint64_t other = shfl64_xor_(best, o);
-                best = other < best ? other : best;
-            }
-            if (!(best < ckey)) break;
-            ckey = best;
-            cur = key_id(best);
-            // the winner's position: the neighbour slot whose member is cur
-            const unsigned wm = __ballot_sync(kFull, okn && v == cur);
-            pos = __shfl_sync(kFull, nb, __ffs(wm) - 1);
-        }
+        g = mem[p];
     }
-    if (lane == 0) start[qi] = cur;
+    if (next == nullptr) {
+        start[qi] = g;
+        return;
+    }
+    long long lo = 0, hi = nnext;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (next[mid] < g) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= nnext || next[lo] != g) {
+        atomicOr(status, kErrBounds);
+        lo = 0;
+    }
+    qpos[qi] = (int32_t)lo;
 }
 
-cudaError_t launch_hnsw_descend(const float* X, const float* inv, int d, int metric, const HnswLayers& ly, int entry,
-                                const float* Q, const float* q_inv, long long nq, int32_t* start, int* status,
-                                cudaStream_t s) {
+cudaError_t launch_hnsw_next(const int32_t* best, const int32_t* mem, long long nmem, const int32_t* next,
+                             long long nnext, long long nq, int first, int entry, int32_t* qpos, int32_t* start,
+                             int* status, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
-    if (ly.M < 1 || ly.M > 32) return cudaErrorInvalidValue;
-    const int wpb = 4;
-    const size_t smem = ((size_t)align16(d * 4) + 32 * 4 + 32 * 33 * 4) * wpb;
-    const unsigned blocks = (unsigned)((nq + wpb - 1) / wpb);
-    cudaError_t e = cudaSuccess;
-#define FGIM_LAUNCH_HD(MT, SD)                                                                                   \
-    do {                                                                                                         \
-        e = cudaFuncSetAttribute(k_hnsw_descend<MT, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) break;                                                                             \
-        LaunchScope ls("k_hnsw_descend", s);                                                                     \
-        k_hnsw_descend<MT, SD><<<blocks, wpb * 32, smem, s>>>(X, inv, d, ly, entry, Q, q_inv, nq, start, status); \
-        e = cudaGetLastError();                                                                                  \
-    } while (0)
-#define FGIM_LAUNCH_HD_D(MT)                                                                                     \
-    do {                                                                                                         \
-        if (d <= 128) FGIM_LAUNCH_HD(MT, true); else FGIM_LAUNCH_HD(MT, false);                                  \
-    } while (0)
-    if (metric == FGIM_L2SQ) FGIM_LAUNCH_HD_D(FGIM_L2SQ);
-    else if (metric == FGIM_IP) FGIM_LAUNCH_HD_D(FGIM_IP);
-    else FGIM_LAUNCH_HD_D(FGIM_COSINE);
-#undef FGIM_LAUNCH_HD_D
-#undef FGIM_LAUNCH_HD
-    return e;
+    LaunchScope ls("k_hnsw_next", s);
+    k_hnsw_next<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(best, mem, nmem, next, nnext, nq, first, entry, qpos,
+                                                             start, status);
+    return cudaGetLastError();
 }
 
 }  // namespace fgim

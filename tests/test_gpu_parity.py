@@ -665,12 +665,13 @@ def test_search_hnsw_matches_oracle(sift_like):
     X = torch.from_numpy(w.X).to(dev)
     built = fg.build_layers(X, M=8, ef=32, seed=7)
     Q = w.Q[:200]
-    ids, dist, start = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], torch.from_numpy(Q).to(dev),
-                                      topk=10, beam=32)
     layers = [(_np(ly["members"]), _np(ly["adj"])) for ly in built["layers"]]
-    oi, od, ost = O.hnsw_search(w.X, w.metric, gi, layers, built["entry"], Q, 32, 10)
-    assert np.array_equal(_np(start), ost)
-    assert np.array_equal(_np(ids), oi)
+    for ef_up in (1, 8):
+        ids, dist, start = fg.search_hnsw(X, out["ids"], built["layers"], built["entry"], torch.from_numpy(Q).to(dev),
+                                          topk=10, beam=32, ef_up=ef_up)
+        oi, od, ost = O.hnsw_search(w.X, w.metric, gi, layers, built["entry"], Q, 32, 10, ef_up=ef_up)
+        assert np.array_equal(_np(start), ost), ef_up
+        assert np.array_equal(_np(ids), oi), ef_up
     # the descent's start is never farther from the query than the entry
     gt, _ = O.knn_exact(w.X, Q, 10, w.metric)
     assert O.recall_at(_np(ids), gt, 10) >= O.recall_at(

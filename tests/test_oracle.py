@@ -600,16 +600,25 @@ def test_hnsw_layer_invariants():
 
 
 def test_hnsw_search_descends_to_the_nearest_member():
-    """On a path graph layer over points on a line, the greedy descent ends at the member
-    nearest to the query, and the base search starts there."""
+    """On a path graph layer over points on a line, the descent ends at the member nearest to
+    the query, and the base search starts there; with a pool (ef_up > 1) the layer search
+    passes a vertex that greedy stops at."""
     X = np.array([[float(i), 0, 0, 0] for i in range(10)], np.float32)
     members = np.array([0, 3, 6, 9], np.int32)
     adj = np.array([[1, -1], [0, 2], [1, 3], [2, -1]], np.int32)
     base = np.array([[(i + 1) % 10, (i + 9) % 10] for i in range(10)], np.int32)
     Q = np.array([[7.2, 0, 0, 0], [1.4, 0, 0, 0]], np.float32)
-    ids, dist, starts = O.hnsw_search(X, 0, base, [(members, adj)], 0, Q, beam=4, topk=2)
-    assert list(starts) == [6, 0]
-    assert list(ids[0]) == [7, 8] and list(ids[1]) == [1, 2]
+    for ef_up in (1, 4):   # greedy, and a pool over the whole path
+        ids, dist, starts = O.hnsw_search(X, 0, base, [(members, adj)], 0, Q, beam=4, topk=2, ef_up=ef_up)
+        assert list(starts) == [6, 0]
+        assert list(ids[0]) == [7, 8] and list(ids[1]) == [1, 2]
+    # a layer where greedy stops early: 0 - 3 - 9 - 6; the query at 5 is nearest to 6, but from
+    # 3 every neighbour (0, 9) is farther than 3 itself
+    adj2 = np.array([[1, -1], [0, 3], [3, -1], [1, 2]], np.int32)   # positions: 0:0, 1:3, 2:6, 3:9
+    Q2 = np.array([[5.0, 0, 0, 0]], np.float32)
+    _, _, s1 = O.hnsw_search(X, 0, base, [(members, adj2)], 0, Q2, beam=4, topk=2, ef_up=1)
+    _, _, s4 = O.hnsw_search(X, 0, base, [(members, adj2)], 0, Q2, beam=4, topk=2, ef_up=4)
+    assert s1[0] == 3 and s4[0] == 6
 
 
 def test_hnsw_layer_links_across_clusters():

@@ -90,3 +90,31 @@ def test_strerror_and_version(lib):
     assert lib.fgim_strerror(0) == b"ok"
     assert lib.fgim_strerror(-1) == b"invalid argument"
     assert b"sm_103a" in lib.fgim_version()
+
+
+def test_newer_entry_points_reject_bad_arguments_on_host(lib):
+    """Batches, HNSW levels / layers and the layered search check their arguments before any
+    device work."""
+    from paper_2603_21710_gb300 import _lib
+    buf = ctypes.create_string_buffer(4096 + 16)
+    base = (ctypes.addressof(buf) + 15) & ~15
+    p = _params()
+    # a batch with a negative count, and one whose descriptors are missing
+    assert lib.fgim_merge_batch(None, None, -1, ctypes.byref(p), None, None) == _lib.FGIM_EINVAL
+    assert lib.fgim_merge_batch(None, None, 2, ctypes.byref(p), None, None) == _lib.FGIM_EINVAL
+    counts = (ctypes.c_int64 * (_lib.MAX_LEVELS + 1))()
+    assert lib.fgim_hnsw_levels(100, 1, 0, base, counts, None) == _lib.FGIM_EINVAL      # M < 2
+    assert lib.fgim_hnsw_levels(0, 8, 0, base, counts, None) == _lib.FGIM_EINVAL        # n < 1
+    # layer 0 is the base graph, not an upper layer; M and ef out of range
+    args = (base, 64, 16, 0, 0, base, 0, 8, 16, base, base, base, 4, None)
+    assert lib.fgim_hnsw_layer(*args) == _lib.FGIM_EINVAL
+    assert lib.fgim_hnsw_layer(base, 64, 16, 0, 0, base, 1, 65, 16, base, base, base, 4, None) == _lib.FGIM_EINVAL
+    assert lib.fgim_hnsw_layer(base, 64, 16, 0, 0, base, 1, 8, 200, base, base, base, 4, None) == _lib.FGIM_EINVAL
+    # the layered search: ef_up out of range, too many layers
+    L = (_lib.Layer * 1)()
+    L[0] = _lib.Layer(base, base, 4, 8, 0)
+    assert lib.fgim_search_hnsw(base, 64, 16, 0, 0, base, 8, L, 1, 0, base, 4, 10, 64, 0, base, base, None,
+                                None) == _lib.FGIM_EINVAL
+    assert lib.fgim_search_hnsw(base, 64, 16, 0, 0, base, 8, L, 17, 0, base, 4, 10, 64, 8, base, base, None,
+                                None) == _lib.FGIM_EINVAL
+    assert ctypes.sizeof(_lib.Layer) == 32

@@ -689,3 +689,15 @@ def test_hnsw_layer_cosine_bf16(bf16_batch):
     assert np.array_equal(_np(ly["members"]), members)
     same = np.all(_np(ly["adj"]) == adj, 1).mean()
     assert same >= 0.98, same
+
+
+def test_merge_host_bf16_matches_device(bf16_batch):
+    """BF16 vectors through the host-buffer entry point: the same graph as the device call."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P = bf16_batch[2]
+    Xh = torch.from_numpy(w.bits().view(np.int16)).view(torch.bfloat16).pin_memory()
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).pin_memory()
+    h = fg.merge_host(Xh, adj, w.shard_sizes, [g[1] for g in graphs], k=w.k, R=w.R, alpha=w.alpha, iters=1,
+                      metric="cos")
+    d = fg.merge(_inp_bf16(w, graphs), k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    assert np.array_equal(h["ids"].numpy(), _np(d["ids"])) and h["entry"] == d["entry"]

@@ -87,6 +87,13 @@ __global__ void __launch_bounds__(128) k_rev_select(const long long* __restrict_
     if (v >= N) return;
     uint64_t* list = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * cap;
     const long long b = off[v], m = off[v + 1] - off[v];
+    if (m <= 32) {   // one sort: the keys of a segment are distinct (one entry per source)
+        const uint64_t sorted = warp_sort32(lane < m ? rev[b + lane] : kEmptyKey);
+        const int nk = (int)(m < cap ? m : cap);
+        if (lane < nk) top[v * cap + lane] = key_id(sorted);
+        if (lane == 0) ntop[v] = nk;
+        return;
+    }
     int n = 0;
     for (long long c0 = 0; c0 < m; c0 += 32) {
         const uint64_t key = (c0 + lane < m) ? rev[b + c0 + lane] : kEmptyKey;
@@ -96,89 +103,65 @@ __global__ void __launch_bounds__(128) k_rev_select(const long long* __restrict_
     if (lane == 0) ntop[v] = n;
 }
 
-// C_n(v), C_o(v) of every vertex (warp per vertex); clears the forward new flags
+// C_n(v), C_o(v) of every vertex (warp per vertex); clears the forward new flags. An id
+// enters the first set it is offered to (new forward, new reverse, old forward, old reverse,
+// in this order): a per-warp hash set in shared memory (hs slots, at most half full) tells
+// whether it is there already.
 __global__ void __launch_bounds__(128) k_build_cands(const int32_t* __restrict__ ids, uint8_t* __restrict__ flags,
                                                      long long N, int k, const int32_t* __restrict__ topN,
                                                      const int32_t* __restrict__ ntopN,
                                                      const int32_t* __restrict__ topO,
                                                      const int32_t* __restrict__ ntopO, int rev_cap,
                                                      int32_t* __restrict__ cand, int32_t* __restrict__ nn_out,
-                                                     int32_t* __restrict__ no_out, int cmax) {
+                                                     int32_t* __restrict__ no_out, int cmax, int hs) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
     const long long v = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (v >= N) return;
-    int32_t* C = reinterpret_cast<int32_t*>(smem) + (size_t)warp * cmax;
-    const unsigned lt = (1u << lane) - 1u;
-    int nn = 0;
-    // new forward neighbours
-    for (int t0 = 0; t0 < k; t0 += 32) {
-        const int t = t0 + lane;
-        int32_t id = -1;
-        bool take = false;
-        if (t < k) {
-            id = ids[v * k + t];
-            take = id >= 0 && (flags[v * k + t] & FGIM_FLAG_NEW);
-        }
-        const unsigned m = __ballot_sync(kFull, take);
-        if (take) C[nn + __popc(m & lt)] = id;
-        nn += __popc(m);
-    }
+    int32_t* C = reinterpret_cast<int32_t*>(smem) + (size_t)warp * (cmax + hs);
+    int32_t* H = C + cmax;
+    for (int i = lane; i < hs; i += 32) H[i] = -1;
     __syncwarp();
-    const int nfwd = nn;
-    // new reverse neighbours not already present
+    // true when id was not in the set (it is now)
+    auto ins = [&](int32_t id) -> bool {
+        int slot = (int)(((uint32_t)id * 2654435761u) >> 7) & (hs - 1);
+        for (int p = 0; p < hs; ++p) {
+            const int32_t prev = atomicCAS(H + slot, -1, id);
+            if (prev == -1) return true;
+            if (prev == id) return false;
+            slot = (slot + 1) & (hs - 1);
+        }
+        return false;
+    };
+    const unsigned lt = (1u << lane) - 1u;
+    int nn = 0, no = 0;
+    auto offer = [&](int32_t id, bool ok, int& cnt, int base) {
+        const bool take = ok && ins(id);
+        const unsigned m = __ballot_sync(kFull, take);
+        if (take) C[base + cnt + __popc(m & lt)] = id;
+        cnt += __popc(m);
+        __syncwarp();
+    };
+    for (int t0 = 0; t0 < k; t0 += 32) {   // new forward neighbours
+        const int t = t0 + lane;
+        const int32_t id = t < k ? ids[v * k + t] : -1;
+        offer(id, id >= 0 && (flags[v * k + t] & FGIM_FLAG_NEW), nn, 0);
+    }
     const int rn = ntopN[v];
-    for (int t0 = 0; t0 < rn; t0 += 32) {
+    for (int t0 = 0; t0 < rn; t0 += 32) {   // new reverse neighbours
         const int t = t0 + lane;
-        int32_t id = -1;
-        bool take = false;
-        if (t < rn) {
-            id = topN[v * rev_cap + t];
-            take = true;
-            for (int s = 0; s < nfwd; ++s)
-                if (C[s] == id) { take = false; break; }
-        }
-        const unsigned m = __ballot_sync(kFull, take);
-        if (take) C[nn + __popc(m & lt)] = id;
-        nn += __popc(m);
-        __syncwarp();
+        offer(t < rn ? topN[v * rev_cap + t] : -1, t < rn, nn, 0);
     }
-    int no = 0;
-    // old forward neighbours not in C_n
-    for (int t0 = 0; t0 < k; t0 += 32) {
+    for (int t0 = 0; t0 < k; t0 += 32) {   // old forward neighbours
         const int t = t0 + lane;
-        int32_t id = -1;
-        bool take = false;
-        if (t < k) {
-            id = ids[v * k + t];
-            take = id >= 0 && !(flags[v * k + t] & FGIM_FLAG_NEW);
-            if (take)
-                for (int s = 0; s < nn; ++s)
-                    if (C[s] == id) { take = false; break; }
-        }
-        const unsigned m = __ballot_sync(kFull, take);
-        if (take) C[nn + no + __popc(m & lt)] = id;
-        no += __popc(m);
-        __syncwarp();
+        const int32_t id = t < k ? ids[v * k + t] : -1;
+        offer(id, id >= 0 && !(flags[v * k + t] & FGIM_FLAG_NEW), no, nn);
     }
-    // old reverse neighbours not in C_n nor already in C_o
     const int ro = ntopO[v];
-    const int nfo = no;
-    for (int t0 = 0; t0 < ro; t0 += 32) {
+    for (int t0 = 0; t0 < ro; t0 += 32) {   // old reverse neighbours
         const int t = t0 + lane;
-        int32_t id = -1;
-        bool take = false;
-        if (t < ro) {
-            id = topO[v * rev_cap + t];
-            take = true;
-            for (int s = 0; s < nn + nfo; ++s)
-                if (C[s] == id) { take = false; break; }
-        }
-        const unsigned m = __ballot_sync(kFull, take);
-        if (take) C[nn + no + __popc(m & lt)] = id;
-        no += __popc(m);
-        __syncwarp();
+        offer(t < ro ? topO[v * rev_cap + t] : -1, t < ro, no, nn);
     }
     for (int s = lane; s < nn + no; s += 32) cand[v * cmax + s] = C[s];
     if (lane == 0) {
@@ -226,8 +209,11 @@ cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cuda
     }
     {
         LaunchScope ls("k_build_cands", s);
-        k_build_cands<<<wb, wpb * 32, (size_t)wpb * b.cmax * 4, s>>>(g.ids, g.flags, N, k, b.topN, b.ntopN, b.topO,
-                                                                     b.ntopO, rev_cap, b.cand, b.nn, b.no, b.cmax);
+        int hs = 64;   // hash set of the ids offered, at most half full
+        while (hs < 2 * b.cmax) hs <<= 1;
+        k_build_cands<<<wb, wpb * 32, (size_t)wpb * (b.cmax + hs) * 4, s>>>(g.ids, g.flags, N, k, b.topN, b.ntopN,
+                                                                            b.topO, b.ntopO, rev_cap, b.cand, b.nn,
+                                                                            b.no, b.cmax, hs);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -664,3 +664,39 @@ def test_synchronous_refinement_matches_the_literal_dfs_form_in_quality():
     r0, rs, rd = (O.recall_at(g.ids[samp], tid, w.k) for g in (g0, gs, gd))
     assert rs > r0 + 0.01 and rd > r0 + 0.01
     assert abs(rs - rd) <= 0.01, (rs, rd)
+
+
+def test_refine_dfs_pins():
+    """The literal DFS form: the exact k-NNG is a fixed point (no update is accepted and the
+    repair finds nothing to change), and on complete local graphs it completes the cross part."""
+    X, sizes = _two_shard_uniform()
+    P = _complete_problem(X, sizes)
+    k = 8
+    gt, gd = O.knn_exact(X, X, k, O_METRIC_L2, exclude=np.arange(X.shape[0]))
+    g = O.KNNG(X.shape[0], k)
+    g.ids[:], g.dist[:], g.flags[:] = gt, gd, O.FLAG_NEW
+    T, st = O.refine_dfs(P, g, 1)
+    assert st["updates"] == 0 and st["pairs"] > 0
+    assert np.array_equal(g.ids, gt) and np.array_equal(g.dist, gd)
+    X2, sizes2 = _two_shard_uniform(N=800, d=3, seed=3)
+    P2 = _complete_problem(X2, sizes2)
+    g2, _, _ = O.stage_a(P2, k, 2)
+    gt2, _ = O.knn_exact(X2, X2, k, O_METRIC_L2, exclude=np.arange(X2.shape[0]))
+    r0 = O.recall_at(g2.ids, gt2, k)
+    O.refine_dfs(P2, g2, 6)
+    assert r0 < 0.95 and O.recall_at(g2.ids, gt2, k) >= 0.99
+
+
+def test_knn_prefix_is_brute_force_over_earlier_rows():
+    """or_knn_prefix: row i's k nearest among rows 0 .. i - 1, by (distance, id)."""
+    rng = np.random.default_rng(2)
+    X = np.round(rng.random((60, 4)) * 8).astype(np.float32)   # integer coordinates: ties by id
+    k = 5
+    ids = np.empty((60, k), np.int32)
+    dist = np.empty((60, k), np.float32)
+    O.lib().or_knn_prefix(X.ctypes.data, 60, 4, 0, k, 0, ids.ctypes.data, dist.ctypes.data)
+    for i in range(60):
+        d = ((X[:i].astype(np.float64) - X[i]) ** 2).sum(1)
+        order = sorted(range(i), key=lambda j: (d[j], j))[:k]
+        want = order + [-1] * (k - len(order))
+        assert list(ids[i]) == want, i

@@ -473,7 +473,8 @@ def run_fgim(args):
             "plain_fp32": plain,
             "masked": masked,
             "hnsw": hnsw,
-            "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms}
+            "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms,
+            "ms_median": float(np.median(step_ms))}
     print(json.dumps(line), flush=True)
 
 

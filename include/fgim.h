@@ -285,6 +285,15 @@ fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t d
                              int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam, int32_t ef_up,
                              int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream);
 
+/* An input PG for one shard on the GPU (the input side of the merge, built like one HNSW layer
+ * over all n vertices): each vertex's exact `ef` nearest among the vertices with smaller ids,
+ * the RNG heuristic down to M, bidirectional edges, the heuristic again over the union of own
+ * and reverse edges. adj [n, M] (local ids, -1 padded) and deg [n]: device, caller-owned.
+ * The entry point of such a graph is vertex 0 (the first inserted). M in [1, 64], ef in
+ * [1, 128]; the work grows with n^2. Synchronous. */
+fgim_status fgim_build_pg(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric, int32_t M,
+                          int32_t ef, int32_t* adj, int32_t* deg, void* stream);
+
 /* Counters of the last merge/search call made by this host thread. */
 void fgim_last_stats(fgim_stats* out);
 

@@ -456,3 +456,11 @@ def hnsw_search(X, metric, base_ids, layers, entry, Q, beam, topk, ef_up: int = 
         i, d, _ = search(X, base_ids, cur, q[None], beam, topk, metric)
         out_i[qi], out_d[qi] = i[0], d[0]
     return out_i, out_d, starts
+
+
+def build_pg(X: np.ndarray, metric: int, M: int, ef: int):
+    """An input PG built like one HNSW layer over every vertex (the vertices in id order):
+    (adj [n, M] local ids, -1 padded, entry 0). The GPU input-PG builder's definition."""
+    n = X.shape[0]
+    _, adj, _ = hnsw_layer(X, metric, np.ones(n, np.int32), 1, M, ef)
+    return adj, 0

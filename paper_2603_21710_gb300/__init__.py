@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import FgimError, KNNG, Graph, Params, Shard, check, last_stats, load  # noqa: F401
 
 __all__ = ["MergeInput", "merge", "merge_batch", "merge_host", "hnsw_levels", "hnsw_layer", "build_layers",
-           "search_hnsw", "cross_query", "refine_pass", "indegree_repair", "prune",
+           "search_hnsw", "build_pg", "cross_query", "refine_pass", "indegree_repair", "prune",
            "reverse_insert", "reach_fix", "search", "last_stats", "load", "launch_count", "FgimError",
            "FLAG_NEW", "FLAG_REPLACED", "profiling"]
 
@@ -359,6 +359,20 @@ def hnsw_layer(X: torch.Tensor, levels: torch.Tensor, level: int, n_layer: int, 
                              _p(lv), int(level), int(M), int(ef), _p(out["members"]), _p(out["adj"]),
                              _p(out["deg"]), int(n_layer), _stream()))
     return out
+
+
+def build_pg(X: torch.Tensor, M: int, ef: int = 64, metric="l2"):
+    """An input PG for one shard on the GPU: (adj [n, M] int32 local ids, -1 padded; entry 0).
+    Each vertex links to the RNG-pruned exact ef nearest of the vertices before it, plus the
+    reverse edges (the work grows with n^2)."""
+    L_ = load()
+    X = _vec(X, "X")
+    n = int(X.shape[0])
+    adj = torch.empty((n, M), dtype=torch.int32, device=X.device)
+    deg = torch.empty((n,), dtype=torch.int32, device=X.device)
+    check(L_.fgim_build_pg(_p(X), n, int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric], int(M), int(ef),
+                           _p(adj), _p(deg), _stream()))
+    return adj, 0
 
 
 def build_layers(X: torch.Tensor, M: int, ef: int = 64, seed: int = 0, metric="l2") -> dict:

@@ -984,6 +984,68 @@ fgim_status fgim_hnsw_levels(int64_t n, int32_t M, uint64_t seed, int32_t* level
     return r;
 }
 
+// One PG over the rows `members` (nl ascending ids) of the FP32 rows X: each member's exact ef
+// nearest among the members before it, the RNG heuristic to M, bidirectional edges, the
+// heuristic again over the union of own and reverse edges. adj [nl, M] holds positions in
+// members (-1 padded), deg [nl] the degrees.
+static void build_layer_graph(Ctx& c, const float* X, int dim, int metric, const int32_t* members, long long nl,
+                              int M, int ef, int32_t* adj, int32_t* deg) {
+    Problem L;
+    std::memset(&L.t, 0, sizeof(L.t));
+    L.t.h = 1;
+    L.t.dim = dim;
+    L.t.off[1] = nl;
+    L.N = nl;
+    L.d = dim;
+    L.metric = metric;
+    float* Xl = c.alloc<float>(nl * dim);
+    ck(launch_gather_rows(X, members, nl, dim, Xl, c.s));
+    L.X = Xl;
+    L.Xh = nullptr;
+    fgim_params lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.metric = metric;
+    finish_problem(c, L, &lp);
+    // the exact ef nearest earlier members, the RNG heuristic to M, bidirectional edges,
+    // the heuristic again over the union of own and reverse edges
+    const int kk = (int)std::min<long long>(ef, std::max<long long>(nl - 1, 1));
+    int32_t* k_ids = c.alloc<int32_t>(nl * kk);
+    float* k_dist = c.alloc<float>(nl * kk);
+    ck(launch_layer_knn(L.X, L.X8, L.inv, nl, dim, metric, kk, k_ids, k_dist, c.s));
+    int32_t* T = c.alloc<int32_t>(nl);   // never 1: no indegree clause
+    ck(cudaMemsetAsync(T, 0, sizeof(int32_t) * nl, c.s));
+    fgim_knng g1;
+    std::memset(&g1, 0, sizeof(g1));
+    g1.ids = k_ids;
+    g1.dist = k_dist;
+    g1.n = nl;
+    g1.k = kk;
+    int32_t* e_ids = c.alloc<int32_t>(nl * M);
+    float* e_dist = c.alloc<float>(nl * M);
+    int32_t* e_cnt = c.alloc<int32_t>(nl);
+    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, 1.f, e_ids, e_dist, e_cnt, c.status, c.s));
+    const int wide = FGIM_MAX_K;   // own and reverse edges together (their 128 nearest if more)
+    int32_t* w_ids = c.alloc<int32_t>(nl * wide);
+    float* w_dist = c.alloc<float>(nl * wide);
+    ck(launch_widen(e_ids, e_dist, nl, M, wide, w_ids, w_dist, c.s));
+    fgim_graph u;
+    std::memset(&u, 0, sizeof(u));
+    u.ids = c.alloc<int32_t>(nl * wide);
+    u.dist = c.alloc<float>(nl * wide);
+    u.deg = c.alloc<int32_t>(nl);
+    u.n = nl;
+    u.R = wide;
+    reverse_insert(c, nl, wide, w_ids, w_dist, e_cnt, &u);
+    fgim_knng g2;
+    std::memset(&g2, 0, sizeof(g2));
+    g2.ids = u.ids;
+    g2.dist = u.dist;
+    g2.n = nl;
+    g2.k = wide;
+    float* f_dist = c.alloc<float>(nl * M);
+    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g2, T, M, 1.f, adj, f_dist, deg, c.status, c.s));
+}
+
 fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                             const int32_t* levels, int32_t level, int32_t M, int32_t ef, int32_t* members,
                             int32_t* adj, int32_t* deg, int64_t n_layer, void* stream) {
@@ -1012,66 +1074,42 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
         need(nl == n_layer, FGIM_EINVAL, "n_layer is not the number of vertices of that level");
         if (nl == 0) return;
         ck(cudaMemcpyAsync(members, mem, sizeof(int32_t) * nl, cudaMemcpyDeviceToDevice, c.s));
-        Problem L;
-        std::memset(&L.t, 0, sizeof(L.t));
-        L.t.h = 1;
-        L.t.dim = dim;
-        L.t.off[1] = nl;
-        L.N = nl;
-        L.d = dim;
-        L.metric = metric;
         const float* X = f32_rows(c, vectors, n, dim, dtype);
-        float* Xl = c.alloc<float>(nl * dim);
-        ck(launch_gather_rows(X, members, nl, dim, Xl, c.s));
-        L.X = Xl;
-        L.Xh = nullptr;
-        fgim_params lp;
-        std::memset(&lp, 0, sizeof(lp));
-        lp.metric = metric;
-        finish_problem(c, L, &lp);
-        // the exact ef nearest earlier members, the RNG heuristic to M, bidirectional edges,
-        // the heuristic again over the union of own and reverse edges
-        const int kk = (int)std::min<long long>(ef, std::max<long long>(nl - 1, 1));
-        int32_t* k_ids = c.alloc<int32_t>(nl * kk);
-        float* k_dist = c.alloc<float>(nl * kk);
-        ck(launch_layer_knn(L.X, L.X8, L.inv, nl, dim, metric, kk, k_ids, k_dist, c.s));
-        int32_t* T = c.alloc<int32_t>(nl);   // never 1: no indegree clause
-        ck(cudaMemsetAsync(T, 0, sizeof(int32_t) * nl, c.s));
-        fgim_knng g1;
-        std::memset(&g1, 0, sizeof(g1));
-        g1.ids = k_ids;
-        g1.dist = k_dist;
-        g1.n = nl;
-        g1.k = kk;
-        int32_t* e_ids = c.alloc<int32_t>(nl * M);
-        float* e_dist = c.alloc<float>(nl * M);
-        int32_t* e_cnt = c.alloc<int32_t>(nl);
-        ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, 1.f, e_ids, e_dist, e_cnt, c.status, c.s));
-        const int wide = FGIM_MAX_K;   // own and reverse edges together (their 128 nearest if more)
-        int32_t* w_ids = c.alloc<int32_t>(nl * wide);
-        float* w_dist = c.alloc<float>(nl * wide);
-        ck(launch_widen(e_ids, e_dist, nl, M, wide, w_ids, w_dist, c.s));
-        fgim_graph u;
-        std::memset(&u, 0, sizeof(u));
-        u.ids = c.alloc<int32_t>(nl * wide);
-        u.dist = c.alloc<float>(nl * wide);
-        u.deg = c.alloc<int32_t>(nl);
-        u.n = nl;
-        u.R = wide;
-        reverse_insert(c, nl, wide, w_ids, w_dist, e_cnt, &u);
-        fgim_knng g2;
-        std::memset(&g2, 0, sizeof(g2));
-        g2.ids = u.ids;
-        g2.dist = u.dist;
-        g2.n = nl;
-        g2.k = wide;
-        float* f_dist = c.alloc<float>(nl * M);
-        ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g2, T, M, 1.f, adj, f_dist, deg, c.status, c.s));
+        build_layer_graph(c, X, dim, metric, members, nl, M, ef, adj, deg);
         c.finish(&t_stats);
     });
     end_call();
     return r;
 }
+fgim_status fgim_build_pg(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric, int32_t M,
+                          int32_t ef, int32_t* adj, int32_t* deg, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        need(vectors && adj && deg, FGIM_EINVAL, "NULL buffer");
+        need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
+        need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
+        need(dtype == FGIM_F32 || dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
+        need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
+        need(M >= 1 && M <= 64, FGIM_EINVAL, "M must be in [1, 64]");
+        need(ef >= 1 && ef <= FGIM_MAX_K, FGIM_EINVAL, "ef must be in [1, 128]");
+        need(((uintptr_t)vectors & (dtype == FGIM_F32 ? 15u : 1u)) == 0, FGIM_EINVAL, "vectors misaligned");
+        Ctx c((cudaStream_t)stream);
+        // every vertex is a member: ids 0 .. n - 1
+        int32_t* flag = c.alloc<int32_t>(n);
+        long long* off = c.alloc<long long>(n + 1);
+        const size_t sb = scan_scratch_bytes(n);
+        void* tmp = c.alloc<unsigned char>((long long)sb);
+        int32_t* all = c.alloc<int32_t>(n);
+        ck(launch_valid_flags(nullptr, n, flag, c.s));
+        ck(compact_flags(flag, n, all, off, tmp, sb, c.s));
+        const float* X = f32_rows(c, vectors, n, dim, dtype);
+        build_layer_graph(c, X, dim, metric, all, n, M, ef, adj, deg);
+        c.finish(&t_stats);
+    });
+    end_call();
+    return r;
+}
+
 
 fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t dtype, int32_t metric,
                              const int32_t* graph_ids, int32_t R, const fgim_layer* layers, int32_t n_layers,

@@ -701,3 +701,23 @@ def test_merge_host_bf16_matches_device(bf16_batch):
                       metric="cos")
     d = fg.merge(_inp_bf16(w, graphs), k=w.k, R=w.R, alpha=w.alpha, iters=1)
     assert np.array_equal(h["ids"].numpy(), _np(d["ids"])) and h["entry"] == d["entry"]
+
+
+def test_build_pg_bit_exact_and_merges(sift_like):
+    """Input PGs built on the GPU equal the oracle's (integer data), and a merge of them equals
+    the oracle's merge of the same PGs."""
+    import paper_2603_21710_gb300 as fg
+    w, _, _, _ = sift_like
+    dev = _dev()
+    graphs = []
+    for i in range(w.h):
+        Xs = w.shard(i)
+        adj, entry = fg.build_pg(torch.from_numpy(np.ascontiguousarray(Xs)).to(dev), M=16, ef=32)
+        ref, _ = O.build_pg(Xs, w.metric, 16, 32)
+        assert np.array_equal(_np(adj), ref), i
+        graphs.append((ref, entry))
+    P = O.Problem.from_workload(w, graphs)
+    inp = _inp(w, graphs)
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=1)
+    assert np.array_equal(_np(out["ids"]), ref.ids) and out["entry"] == ref.entry

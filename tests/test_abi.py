@@ -118,3 +118,6 @@ def test_newer_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.fgim_search_hnsw(base, 64, 16, 0, 0, base, 8, L, 17, 0, base, 4, 10, 64, 8, base, base, None,
                                 None) == _lib.FGIM_EINVAL
     assert ctypes.sizeof(_lib.Layer) == 32
+    # the input-PG builder: M and ef out of range
+    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 0, 16, base, base, None) == _lib.FGIM_EINVAL
+    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 8, 129, base, base, None) == _lib.FGIM_EINVAL

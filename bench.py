@@ -58,7 +58,14 @@ def parse():
                          "log-uniform in [--batched-lo, --batched-hi]) in one fgim_merge_batch call, against "
                          "the plain FP32 form of the same merges; prints its own JSON line")
     ap.add_argument("--batched-lo", type=int, default=10_000)
-    ap.add_argument("--batched-hi", type=int, default=50_000)
+    ap.add_argument("--batched-hi", type=int, default=200_000)
+    ap.add_argument("--configs", default="precision,fp8",
+                    help="other workloads timed after the headline one, each in its own sub-record: "
+                         "'precision' (1M d=96 IP, BF16 filter against plain FP32), 'fp8' (1M d=960, 8 uneven "
+                         "shards); '' = none")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip comparing the GPU merge with the oracle's (100k sample and the largest N the "
+                         "oracle finishes in about two minutes)")
     return ap.parse_args()
 
 
@@ -158,6 +165,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- oracle legs
+def stage_a_work_model(w_full, graphs_full, n_queries_sample=2000):
+    """The oracle's Alg. 1 counters (distance evaluations, expansions) per cross query, on
+    sampled cross queries of the full workload: the per-query work model of stage a."""
+    import oracle as O
+    rng = np.random.default_rng(7)
+    off = w_full.offsets
+    L = -(-w_full.k // (w_full.h - 1))
+    ndc = hops = nq = 0
+    for g in rng.choice(w_full.N, max(1, n_queries_sample // (w_full.h - 1)), replace=False):
+        i = int(np.searchsorted(off, g, side="right") - 1)
+        for j in range(w_full.h):
+            if j == i:
+                continue
+            adj, ep = graphs_full[j]
+            _, _, st = O.knn_search(w_full.shard(j), adj, ep, w_full.X[g], L, L, w_full.metric)
+            ndc += st["ndc"]
+            hops += st["hops"]
+            nq += 1
+    return {"ndc": ndc / nq, "hops": hops / nq, "queries_sampled": nq, "L": L}
+
+
 def cpu_baseline_leg(w_full, graphs_full, n_queries_sample=2000):
     """The oracle as it stands, on the host cores: (1) a full merge of a bounded sample of the
     workload (the same recipe at SAMPLE_N points), (2) its beam-search counters on sampled
@@ -169,26 +197,95 @@ def cpu_baseline_leg(w_full, graphs_full, n_queries_sample=2000):
     t0 = time.perf_counter()
     r = O.merge(P, w.k, w.R, w.alpha, iters=WORKLOAD["iters"])
     dt = time.perf_counter() - t0
-    # per-query counters of Alg. 1 on the full workload (cross queries of sampled vertices)
-    rng = np.random.default_rng(7)
-    off = w_full.offsets
-    L = -(-w_full.k // (w_full.h - 1))
-    ndc = hops = nq = 0
-    for g in rng.choice(w_full.N, n_queries_sample // (w_full.h - 1), replace=False):
-        i = int(np.searchsorted(off, g, side="right") - 1)
-        for j in range(w_full.h):
-            if j == i:
-                continue
-            adj, ep = graphs_full[j]
-            _, _, st = O.knn_search(w_full.shard(j), adj, ep, w_full.X[g], L, L, w_full.metric)
-            ndc += st["ndc"]
-            hops += st["hops"]
-            nq += 1
     return {"value": SAMPLE_N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"full oracle merge (3 stages, iters=3) of the same recipe at N={SAMPLE_N} "
                       f"(4 shards of {SAMPLE_N // 4}), {dt:.2f} s on {cores} host threads",
-            "seconds": dt, "stats": r.stats,
-            "stage_a_per_query": {"ndc": ndc / nq, "hops": hops / nq, "queries_sampled": nq, "L": L}}
+            "seconds": dt, "stats": r.stats, "result": r, "inputs": (w, graphs),
+            "stage_a_per_query": stage_a_work_model(w_full, graphs_full, n_queries_sample)}
+
+
+def recall10(found, truth) -> float:
+    hits = sum(len(set(a) & set(b)) for a, b in zip(found.tolist(), truth.tolist()))
+    return hits / (10 * len(truth))
+
+
+def exact_top10(X, Q, metric):
+    """Exact top-10 of the queries over X on the GPU (evaluation only): torch matmul, chunked."""
+    import torch
+    out = []
+    xx = (X * X).sum(1)
+    for s in range(0, Q.shape[0], 256):
+        q = Q[s:s + 256]
+        ip = q @ X.T
+        if metric == 0:
+            d = (q * q).sum(1, keepdim=True) - 2 * ip + xx[None, :]
+        elif metric == 1:
+            d = 1 - ip
+        else:
+            d = 1 - ip / (torch.linalg.vector_norm(q, dim=1, keepdim=True) * torch.sqrt(xx)[None, :])
+        out.append(torch.topk(d, 10, dim=1, largest=False).indices.cpu())
+        del ip, d
+    return torch.cat(out).numpy()
+
+
+def oracle_check(fg, kw, w_full, graphs_full, out_full, cpu, dev, nq_eval=1000, budget_s=150.0):
+    """The metric's condition, measured: (1) the GPU merge of the oracle's 100k sample against
+    the oracle's merge of it (bit for bit on these integer data); (2) the oracle's merge of the
+    largest N in {1M, 500k, 250k} expected to finish within `budget_s` on the host cores (its
+    time extrapolated linearly from the sample), compared with the GPU merge of the same input,
+    and both graphs' search recall@10 at beam 64 (the oracle's graph searched by the oracle)."""
+    import torch
+    import oracle as O
+    res = {}
+    if cpu is not None and "result" in cpu:
+        w, graphs = cpu["inputs"]
+        r = cpu["result"]
+        inp = fg.MergeInput.from_flat(torch.from_numpy(w.X).to(dev), w.shard_sizes,
+                                      torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev),
+                                      [g[1] for g in graphs], metric="l2")
+        o = fg.merge(inp, **kw, return_knng=True)
+        res["sample"] = {"N": w.N, "knng_equal": bool(np.array_equal(o["knng"]["ids"].cpu().numpy(), r.knn_ids)),
+                         "graph_equal": bool(np.array_equal(o["ids"].cpu().numpy(), r.ids)),
+                         "deg_equal": bool(np.array_equal(o["deg"].cpu().numpy(), r.deg)),
+                         "entry_equal": o["entry"] == r.entry}
+        per_point = cpu["seconds"] / w.N
+        del inp, o
+    else:
+        per_point = None
+    target = None
+    for n in (w_full.N, w_full.N // 2, w_full.N // 4):
+        if per_point is not None and per_point * n * 1.3 <= budget_s:
+            target = n
+            break
+    if target is None:
+        res["full"] = None
+        return res
+    if target == w_full.N:
+        w, graphs = w_full, graphs_full
+        o = out_full
+    else:
+        w, graphs = make_inputs(target)
+        inp = fg.MergeInput.from_flat(torch.from_numpy(w.X).to(dev), w.shard_sizes,
+                                      torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev),
+                                      [g[1] for g in graphs], metric="l2")
+        o = fg.merge(inp, **kw)
+    P = O.Problem.from_workload(w, graphs)
+    t0 = time.perf_counter()
+    r = O.merge(P, w.k, w.R, w.alpha, iters=WORKLOAD["iters"])
+    dt = time.perf_counter() - t0
+    Qn = np.ascontiguousarray(w.Q[:nq_eval])
+    X = torch.from_numpy(w.X).to(dev)
+    Q = torch.from_numpy(Qn).to(dev)
+    gt = exact_top10(X, Q, 0)
+    sid, _ = fg.search(X, o["ids"], o["entry"], Q, topk=10, beam=64)
+    oid, _, _ = O.search(w.X, r.ids, r.entry, Qn, 64, 10, 0)
+    rg, ro = recall10(sid.cpu().numpy(), gt), recall10(oid, gt)
+    res["full"] = {"N": w.N, "oracle_seconds": dt, "cores": os.cpu_count() or 1,
+                   "graph_equal": bool(np.array_equal(o["ids"].cpu().numpy(), r.ids)),
+                   "entry_equal": o["entry"] == r.entry,
+                   "recall@10_gpu": rg, "recall@10_oracle": ro, "recall_delta_pt": 100 * (rg - ro),
+                   "queries": nq_eval, "beam": 64}
+    return res
 
 
 def run_reference(args):
@@ -306,6 +403,94 @@ def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w,
         out.update(hbm, achieved=None)
     out["frac"] = out["achieved"] / out["peak"] if out.get("achieved") and out.get("peak") else None
     return out
+
+
+# the other workloads of the measurement plan, timed after the headline one (one sub-record each)
+CONFIGS = {
+    "precision": dict(recipe="precision", metric="ip",
+                      workload="Deep-like merge: N=1,000,000 (2 x 500,000), d=96 unit-norm, inner product, "
+                               "input PGs M=32 ef=128, k=48, R=32, alpha=1.0, I_max=3"),
+    "fp8": dict(recipe="fp8", metric="l2",
+                workload="Gist-like merge: N=1,000,000 (8 shards sized i*N/36), d=960 non-negative, squared L2, "
+                         "input PGs M=32 ef=128, k=64, R=48, alpha=1.0, I_max=3"),
+}
+
+
+def timed_merges(fg, inp, kw, steps, warmup, profile=False):
+    """`warmup` untimed merges, then `steps` merges each bracketed by CUDA events on the
+    current stream; with `profile`, the library's per-kernel event times over the timed ones."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = None
+    for _ in range(warmup):
+        out = fg.merge(inp, **kw)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kernels = {}
+    launches0 = fg.launch_count()
+    if profile:
+        prof = fg.profiling()
+        prof.__enter__()
+    for a, b in ev:
+        a.record(stream)
+        out = fg.merge(inp, **kw)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if profile:
+        prof.__exit__(None, None, None)
+        for name in prof.names():
+            n, ms = prof.query(name)
+            if n:
+                kernels[name] = {"launches": n, "ms": ms}
+    return {"step_ms": [a.elapsed_time(b) for a, b in ev], "kernels": kernels, "out": out,
+            "launches": fg.launch_count() - launches0}
+
+
+def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
+    """One sub-record: the chosen form (BF16 tensor-core join filter) and the plain FP32 form
+    (FP32 rows, FP32 SIMT join filter) of one workload at full size, the roofline of the chosen
+    form's dominant kernel and the merged graph's search recall@10 at beam 64."""
+    import torch
+    from synth import gen, pgbuild
+    c = CONFIGS[name]
+    t0 = time.perf_counter()
+    w = gen.make(c["recipe"])
+    graphs = pgbuild.build_all(w)
+    t_inputs = time.perf_counter() - t0
+    X = torch.from_numpy(w.X).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs], metric=c["metric"])
+    kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=3)
+    ch = timed_merges(fg, inp, dict(kw, join_filter="tc"), steps, warmup, profile=True)
+    stats = ch["out"]["stats"]
+    pl = timed_merges(fg, inp, dict(kw, join_filter="fp32", rows="fp32"), 1, 0)
+    ms_c, ms_p = float(np.mean(ch["step_ms"])), float(np.mean(pl["step_ms"]))
+    Q = torch.from_numpy(np.ascontiguousarray(w.Q[:nq_eval])).to(dev)
+    gt = exact_top10(X, Q, w.metric)
+    sid, _ = fg.search(X, ch["out"]["ids"], ch["out"]["entry"], Q, topk=10, beam=64, metric=c["metric"])
+    model = {"stage_a_per_query": stage_a_work_model(w, graphs, 1000)}
+    kernels = ch["kernels"]
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
+    s_row = row_bytes(w)
+    roof = (roofline_for(dom, kernels[dom]["ms"] / kernels[dom]["launches"], kernels[dom]["launches"] / steps, w,
+                         graphs, model, peaks, stats, s_row) if dom else None)
+    roof_all = {k_: roofline_for(k_, kernels[k_]["ms"] / kernels[k_]["launches"], kernels[k_]["launches"] / steps, w,
+                                 graphs, model, peaks, stats, s_row)
+                for k_ in ("k_cross_query", "k_join", "k_prune") if k_ in kernels}
+    rec = {"workload": c["workload"], "N": w.N, "d": w.d, "shards": w.shard_sizes, "value": w.N / (ms_c * 1e-3),
+           "unit": UNIT, "ms_per_step": ms_c, "steps": steps, "warmup": warmup, "step_ms": ch["step_ms"],
+           "form": "BF16 tensor-core join filter with exact FP32 re-rank, FP32 rows elsewhere",
+           "plain_fp32": {"value": w.N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p, "steps": 1,
+                          "form": "FP32 rows, FP32 SIMT join filter",
+                          "same_graph": bool(torch.equal(pl["out"]["ids"], ch["out"]["ids"]))},
+           "recall@10": recall10(sid.cpu().numpy(), gt), "recall_eval": {"queries": nq_eval, "beam": 64},
+           "gpu_launches_per_step": ch["launches"] / steps, "roofline": roof, "roofline_by_kernel": roof_all,
+           "kernels": kernels, "merge_stats": stats, "inputs_seconds": t_inputs,
+           "l2_policy": f"inputs larger than L2 ({w.N * w.d * 4 / 1e9:.2f} GB of vectors)"}
+    del inp, X, adj, ch, pl
+    torch.cuda.empty_cache()
+    fg.trim_memory()
+    return rec
 
 
 def run_fgim(args):
@@ -443,6 +628,9 @@ def run_fgim(args):
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline_leg(w, graphs)
+    ocheck = None
+    if not args.no_oracle_check and ws == 1:
+        ocheck = oracle_check(fg, kw, w, graphs, out, cpu, dev)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -473,8 +661,17 @@ def run_fgim(args):
             "plain_fp32": plain,
             "masked": masked,
             "hnsw": hnsw,
+            "oracle_check": ocheck,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms,
             "ms_median": float(np.median(step_ms))}
+    if ws == 1 and args.configs:
+        # the other workloads, each outside the headline's timed region, in its own sub-record
+        del X, adj, inp, out
+        torch.cuda.empty_cache()
+        fg.trim_memory()
+        line["configs"] = {}
+        for name in [c for c in args.configs.split(",") if c]:
+            line["configs"][name] = measure_config(fg, name, dev, peaks)
     print(json.dumps(line), flush=True)
 
 

@@ -19,16 +19,21 @@
  *  - Lists are rows of fixed width, sorted ascending by (distance, global id), valid
  *    entries first, empty slots hold id -1 and distance +inf.
  *  - Distances are squared L2, 1 - x.y (IP), or 1 - cos(x, y), evaluated in FP32.
- *  - Every call is ordered on `stream` (0 = legacy default stream). Scratch memory is
- *    taken with cudaMallocAsync on that stream and released before the call returns.
- *    Calls return after the stream has drained (they synchronize the stream), so
- *    results are ready and every error is reported by the call itself.
+ *  - Every call is ordered on `stream` (0 = legacy default stream). Scratch memory comes
+ *    from a stream-ordered memory pool that the library keeps per device: a call takes
+ *    its scratch from the pool on `stream` and hands it back before it returns, and the
+ *    pool keeps the device memory it has mapped for later calls (fgim_trim_memory returns
+ *    the unused part to the device). Calls return after the stream has drained (they
+ *    synchronize the stream), so results are ready and every error is reported by the
+ *    call itself.
  *  - Errors: argument errors are detected on the host before any work is queued and
  *    return FGIM_EINVAL / FGIM_EUNSUPPORTED. CUDA errors return FGIM_ECUDA (the CUDA
- *    error string is available from fgim_last_error()). A device-side bounded wait that
- *    ran out returns FGIM_ETIMEOUT. No exception crosses the ABI.
+ *    error string is available from fgim_last_error()). A scratch allocation that fails
+ *    returns FGIM_ENOMEM after handing back what the call had taken. A device-side
+ *    bounded loop that ran out returns FGIM_ETIMEOUT. No exception crosses the ABI.
  *  - Not thread-safe for concurrent calls that share a stream; concurrent calls on
- *    different streams are safe.
+ *    different streams are safe, except fgim_search_noalloc, whose calls share one fixed
+ *    device array and must not overlap on the GPU (see its comment).
  */
 #ifndef FGIM_H
 #define FGIM_H
@@ -143,6 +148,8 @@ typedef struct {
     int64_t unreached;       /* vertices still unreached after the fix */
     int64_t join_reruns;     /* Update passes re-run after a proposal-buffer overflow */
     int64_t join_cands;      /* candidate-set sizes |C_n| + |C_o| summed over the vertices joined */
+    int64_t join_class[4];   /* vertices joined per Update form: tensor-core tile for |C| <= 64, <= 128,
+                                > 128, and the FP32 SIMT tile */
 } fgim_stats;
 
 /*
@@ -225,8 +232,10 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
  * fgim_search for callers that cannot allocate device memory while they run: processes
  * whose device memory belongs to a pool they do not control, latency-critical paths where
  * an allocation (and the synchronisation it may bring) is not allowed, plug-ins inside a
- * host that forbids allocator calls. Same arguments and results as fgim_search; the paper
- * has no counterpart (this is a deployment variant of the evaluation search).
+ * host that forbids allocator calls. Same arguments and results as fgim_search for FP32
+ * vectors; dtype must be FGIM_F32 (BF16 storage would need a decoded copy, which is an
+ * allocation: it returns FGIM_EUNSUPPORTED). The paper has no counterpart (this is a
+ * deployment variant of the evaluation search).
  * Its scratch (status word, counters and, for cosine, the inverse norms of the base and of
  * the queries) lives in one fixed device array inside the library, kept on every device
  * that loads the library until the process exits. Limits: cosine search accepts at most
@@ -304,6 +313,25 @@ void fgim_last_stats(fgim_stats* out);
  * call of this library has work in flight.
  */
 void fgim_trim_memory(void);
+
+/*
+ * Test hooks: knobs that let a test drive rarely taken paths on small inputs, without
+ * faulting or hanging the GPU. They are process-wide, default to off, and are not meant
+ * for production use. fgim_test_set returns 1 when the knob exists (and sets it), else 0.
+ *   "prop_cap"          > 0: capacity of Update's proposal buffer, in proposals (raised to
+ *                       what one vertex can propose), so that small inputs overflow it and
+ *                       take the re-run path; 0 = the default size.
+ *   "hop_budget"        > 0: expansions each beam search may take; a search that needs more
+ *                       stops and the call returns FGIM_ETIMEOUT; 0 = unbounded (default).
+ *   "fail_alloc_after"  >= 0: the scratch allocation of a call that comes after this many
+ *                       successful ones fails as if the device were out of memory (the call
+ *                       returns FGIM_ENOMEM); -1 = off (default).
+ * fgim_test_get("pool_used_bytes"): bytes of the current device's scratch pool handed out
+ * and not yet handed back (0 whenever no call is running); fgim_test_get("scratch_allocs"):
+ * scratch allocations made by the last call on this host thread; -1 for an unknown name.
+ */
+int32_t fgim_test_set(const char* knob, int64_t value);
+int64_t fgim_test_get(const char* what);
 
 /* Human-readable name of a status; message of the last CUDA error on this host thread. */
 const char* fgim_strerror(fgim_status s);

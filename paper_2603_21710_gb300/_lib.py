@@ -50,10 +50,13 @@ class Graph(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("ndc", "hops", "join_pairs", "proposals", "zero_indegree",
-                                              "repaired", "attached", "unreached", "join_reruns", "join_cands")]
+                                              "repaired", "attached", "unreached", "join_reruns", "join_cands")] + [
+        ("join_class", ctypes.c_int64 * 4)]
 
     def as_dict(self):
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "join_class"}
+        d["join_class"] = [int(x) for x in self.join_class]
+        return d
 
 
 class FgimError(RuntimeError):
@@ -104,6 +107,8 @@ EXPORTS = {
                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fgim_last_stats": (None, [ctypes.c_void_p]),
+    "fgim_test_set": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_int64]),
+    "fgim_test_get": (ctypes.c_int64, [ctypes.c_char_p]),
     "fgim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fgim_last_error": (ctypes.c_char_p, []),
     "fgim_version": (ctypes.c_char_p, []),
@@ -149,3 +154,13 @@ def last_stats() -> dict:
     s = Stats()
     load().fgim_last_stats(ctypes.byref(s))
     return s.as_dict()
+
+
+def test_set(knob: str, value: int) -> None:
+    """Set one of the library's test hooks (see fgim_test_set in fgim.h)."""
+    if load().fgim_test_set(knob.encode(), int(value)) != 1:
+        raise KeyError(knob)
+
+
+def test_get(what: str) -> int:
+    return int(load().fgim_test_get(what.encode()))

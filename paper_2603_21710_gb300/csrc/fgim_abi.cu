@@ -74,6 +74,12 @@ static void resolve_events() {
 static std::mutex g_pool_mu;
 static std::map<int, cudaMemPool_t> g_pools;
 
+// test hooks (fgim_test_set): process-wide, off by default
+static std::atomic<long long> g_test_prop_cap{0};
+static std::atomic<int> g_test_hop_budget{0};
+static std::atomic<long long> g_test_fail_after{-1};
+static thread_local long long t_allocs = 0;   // scratch allocations of the current call
+
 static cudaMemPool_t lib_pool() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -107,6 +113,12 @@ class Scratch {
     template <typename T>
     T* alloc(long long count) {
         if (count <= 0) count = 1;
+        const long long fail_after = g_test_fail_after.load(std::memory_order_relaxed);
+        if (fail_after >= 0 && t_allocs >= fail_after) {
+            ok_ = false;   // injected failure (test hook), reported like a real one
+            return nullptr;
+        }
+        ++t_allocs;
         void* p = nullptr;
         const size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
         const cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&p, bytes, pool_, s_) : cudaMallocAsync(&p, bytes, s_);
@@ -168,6 +180,9 @@ struct Ctx {
         need(sc.ok(), FGIM_ENOMEM, "scratch allocation failed");
         ck(cudaMemsetAsync(status, 0, 4 * sizeof(int), s));
         ck(cudaMemsetAsync(ctr, 0, 16 * sizeof(unsigned long long), s));
+        const int hop_budget = g_test_hop_budget.load(std::memory_order_relaxed);
+        if (hop_budget > 0)   // status[1]: the beam searches' expansion budget (test hook)
+            ck(cudaMemcpyAsync(status + 1, &hop_budget, sizeof(int), cudaMemcpyHostToDevice, s));
         ck(cudaMallocHost(&host, 64));
     }
     ~Ctx() {
@@ -480,6 +495,8 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     const long long per_vertex_max = 2LL * b.cmax * b.cmax;
     if (cap < 4 * per_vertex_max) cap = 4 * per_vertex_max;
     if (cap < (1LL << 22)) cap = 1LL << 22;
+    const long long test_cap = g_test_prop_cap.load(std::memory_order_relaxed);
+    if (test_cap > 0) cap = std::max(test_cap, per_vertex_max);   // test hook: force the re-run path
     b.prop_cap = cap;
     b.prop_tgt = c.alloc<int32_t>(cap);
     b.prop_key = c.alloc<uint64_t>(cap);
@@ -511,6 +528,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     ck(cudaMemsetAsync(b.pending, 0, N, c.s));
     ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
     ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, nullptr, N, c.ctr + 2, c.ctr + 5, c.status, c.s));
+    for (int q = 0; q < 4; ++q) st->join_class[q] += b.class_count[q];
     unsigned long long cnt = c.read_u64(b.prop_count);
     long long total = (long long)cnt;
     ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
@@ -531,6 +549,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
         ck(cudaMemsetAsync(b.pending, 0, N, c.s));
         ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
         ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, b.pend_list, np, c.ctr + 2, c.ctr + 5, c.status, c.s));
+        for (int q = 0; q < 4; ++q) st->join_class[q] += b.class_count[q];
         cnt = c.read_u64(b.prop_count);
         total += (long long)cnt;
         ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
@@ -687,6 +706,7 @@ static fgim_status guarded(F&& f) {
 static void begin_call() {
     std::memset(&t_stats, 0, sizeof(t_stats));
     t_last_error.clear();
+    t_allocs = 0;
 }
 
 static void end_call() { resolve_events(); }
@@ -1230,6 +1250,46 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
     });
     end_call();
     return r;
+}
+
+int32_t fgim_test_set(const char* knob, int64_t value) {
+    if (!knob) return 0;
+    const std::string k(knob);
+    if (k == "prop_cap") {
+        g_test_prop_cap.store(value > 0 ? (long long)value : 0);
+        return 1;
+    }
+    if (k == "hop_budget") {
+        g_test_hop_budget.store(value > 0 ? (int)std::min<int64_t>(value, 0x7fffffff) : 0);
+        return 1;
+    }
+    if (k == "fail_alloc_after") {
+        g_test_fail_after.store(value >= 0 ? (long long)value : -1);
+        return 1;
+    }
+    return 0;
+}
+
+int64_t fgim_test_get(const char* what) {
+    if (!what) return -1;
+    if (std::string(what) == "scratch_allocs") return (int64_t)t_allocs;   // of the last call on this thread
+    if (std::string(what) == "pool_used_bytes") {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_pools.find(dev);
+        if (it == g_pools.end()) return 0;
+        uint64_t used = 0;
+        if (cudaMemPoolGetAttribute(it->second, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        return (int64_t)used;
+    }
+    return -1;
 }
 
 void fgim_trim_memory(void) {

@@ -29,6 +29,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxShards = FGIM_MAX_SHARDS;
 
+// Every call passes its kernels a device status array int[4]: status[0] collects the error
+// bits below; status[1] is the beam searches' expansion budget (0 = unbounded), set only by
+// the "hop_budget" test hook.
 // device status word bits
 constexpr int kErrOverflow = 1;   // a bounded buffer overflowed (handled by the host)
 constexpr int kErrBounds = 2;     // an index failed a bounds check (the access was skipped)

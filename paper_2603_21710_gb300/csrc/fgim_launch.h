@@ -86,6 +86,7 @@ struct RefineBuffers {
     // sets (device, 8 ints), a pinned host slot to read them, and the launch lists (3 x cap)
     int32_t* max_nc;
     int32_t* host_i32;
+    long long class_count[4];   // out of refine_join: vertices per form (TC <= 64, <= 128, > 128; FP32 tile)
     int32_t* blist;
     long long blist_cap;
     // tensor-core filter inputs: BF16 copy of the vectors and per row (|x|^2, bound on |x|,

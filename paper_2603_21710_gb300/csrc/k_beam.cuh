@@ -279,8 +279,11 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
         if (L == 1) worst = shfl64(key, 0);
         __syncwarp();
     }
-    // every vertex is expanded at most once, so nt + 1 iterations always suffice
+    // every vertex is expanded at most once, so nt + 1 iterations always suffice; status[1],
+    // when positive, is a smaller expansion budget (a test hook for the timeout path)
     bool done = false;
+    const int hop_budget = status[1];
+    const long long budget = hop_budget > 0 ? (long long)hop_budget : nt + 1;
     for (long long it = 0; it <= nt; ++it) {
         int first = -1;
 #pragma unroll
@@ -294,6 +297,7 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
             done = true;
             break;
         }
+        if (it >= budget) break;
         const uint64_t fk = shfl64(pick_slot<MAXS>(pk, first >> 5), first & 31);
         if (lane == (first & 31)) expd |= 1u << (first >> 5);
         if (lane == 0) ctr.hops++;

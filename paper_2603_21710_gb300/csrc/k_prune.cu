@@ -16,6 +16,9 @@
 
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "fgim_launch.h"
 
 namespace fgim {
@@ -767,17 +770,28 @@ cudaError_t launch_reach_rounds(int32_t* graph, float* gdist, int32_t* deg, cons
                                 int R, const int32_t* reps, long long nr, long long rho0, int rounds, long long* ff,
                                 const int32_t* cand, const float* cdist, int beam, unsigned long long* owner,
                                 int4* plan, unsigned long long* attached, cudaStream_t s) {
-    // a cooperative grid: every block resident at once (the barriers wait for all of them)
-    static int max_blocks = 0;
+    // a cooperative grid: every block resident at once (the barriers wait for all of them);
+    // the largest such grid is worked out once per device (devices may differ in SM count)
+    static std::mutex mu;
+    static std::map<int, int> max_blocks_of;
     cudaError_t e = cudaSuccess;
-    if (max_blocks == 0) {
-        int dev = 0, per_sm = 0, sms = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reach_rounds, 128, 0)) != cudaSuccess)
-            return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int max_blocks = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = max_blocks_of.find(dev);
+        if (it != max_blocks_of.end()) {
+            max_blocks = it->second;
+        } else {
+            int per_sm = 0, sms = 0;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reach_rounds, 128, 0)) != cudaSuccess)
+                return e;
+            max_blocks = per_sm * sms;
+            if (max_blocks < 1) return cudaErrorCooperativeLaunchTooLarge;
+            max_blocks_of[dev] = max_blocks;
+        }
     }
     long long window = kReachWindow;
     const int blocks = (int)std::min<long long>(cdivl(window, 4), max_blocks);

@@ -1267,6 +1267,7 @@ static size_t tc_launch_smem(const TCLayout& TL, uint32_t cols) {
 cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         unsigned long long* cands, int* status, cudaStream_t s) {
+    for (int q = 0; q < 4; ++q) b.class_count[q] = 0;
     if (nv <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMemsetAsync(b.max_nc, 0, 8 * sizeof(int32_t), s)) != cudaSuccess) return e;
@@ -1291,6 +1292,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         for (int q = 0; q < kTCLists; ++q) {
             const int32_t count = hb[2 + q], cmq = hb[5 + q];
             if (count <= 0) continue;
+            b.class_count[q] += count;
             const TCLayout TL = tc_layout(cmq, t.dim);
             const int ncols = cmq <= 128 ? 128 : ((cmq + 15) / 16) * 16;   // MMA N (interleaved order: 128)
             uint32_t cols = 32;
@@ -1329,6 +1331,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
     }
     const StagedLayout SL = staged_layout(cm, g.k, t.dim);
     if (SL.bytes > 227 * 1024) return cudaErrorNotSupported;
+    b.class_count[3] += (long long)hb[2] + hb[3] + hb[4];   // the vertices with a pair to join
     const size_t smem = SL.bytes;
 #define FGIM_LAUNCH_JS(MT)                                                                                        \
     do {                                                                                                          \

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.Params) == 64
     assert ctypes.sizeof(_lib.KNNG) == 40
     assert ctypes.sizeof(_lib.Graph) == 40
-    assert ctypes.sizeof(_lib.Stats) == 80
+    assert ctypes.sizeof(_lib.Stats) == 112
 
 
 def _params(**kw):
@@ -121,3 +121,20 @@ def test_newer_entry_points_reject_bad_arguments_on_host(lib):
     # the input-PG builder: M and ef out of range
     assert lib.fgim_build_pg(base, 64, 16, 0, 0, 0, 16, base, base, None) == _lib.FGIM_EINVAL
     assert lib.fgim_build_pg(base, 64, 16, 0, 0, 8, 129, base, base, None) == _lib.FGIM_EINVAL
+
+
+def test_test_hooks_named_and_unknown(lib):
+    """The test hooks exist by name, unknown names are refused; none touches the device."""
+    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1)):
+        assert lib.fgim_test_set(knob.encode(), off) == 1
+    assert lib.fgim_test_set(b"no_such_knob", 1) == 0
+    assert lib.fgim_test_get(b"no_such_counter") == -1
+
+
+def test_noalloc_search_refuses_bf16_storage_on_host(lib):
+    """fgim_search_noalloc takes FP32 vectors only (a decoded BF16 copy would be an allocation):
+    BF16 storage is refused with FGIM_EUNSUPPORTED before any device work."""
+    buf = ctypes.create_string_buffer(4096 + 16)
+    p = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
+    st = lib.fgim_search_noalloc(p, 16, 32, 1, 0, p, 8, 0, p, 4, 10, 64, p, p, None)
+    assert st == -5

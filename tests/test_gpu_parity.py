@@ -456,7 +456,7 @@ def bf16_batch():
     """Three merges of the batched form (d = 768, cosine, BF16 storage) at 2,000..4,000 points."""
     from synth import gen, pgbuild
     out = []
-    for w in gen.batched(n_merges=3, n_lo=2_000, n_hi=4_000, nq=100):
+    for w in gen.batched(n_merges=3, n_lo=2_000, n_hi=4_000, nq=1000):
         graphs = pgbuild.build_all(w)
         out.append((w, graphs, O.Problem.from_workload(w, graphs)))
     return out
@@ -516,7 +516,8 @@ def test_merge_bf16_end_to_end(bf16_batch):
     sg, _ = fg.search(_inp(w, graphs).X, out["ids"], out["entry"], torch.from_numpy(w.Q).to(_dev()), topk=10,
                       beam=64, metric="cos")
     so, _, _ = O.search(w.X, ref.ids, ref.entry, w.Q, 64, 10, w.metric)
-    assert abs(O.recall_at(_np(sg), gt, 10) - O.recall_at(so, gt, 10)) <= 0.01
+    assert w.Q.shape[0] >= 1000
+    assert abs(O.recall_at(_np(sg), gt, 10) - O.recall_at(so, gt, 10)) <= 0.005
 
 
 def test_merge_batch_equals_single_merges(bf16_batch):
@@ -721,3 +722,167 @@ def test_build_pg_bit_exact_and_merges(sift_like):
     out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
     ref = O.merge(P, w.k, w.R, w.alpha, iters=1)
     assert np.array_equal(_np(out["ids"]), ref.ids) and out["entry"] == ref.entry
+
+
+# --------------------------------------------------------------------------- the precision recipe
+@pytest.fixture(scope="module")
+def deep_like():
+    """The precision recipe (unit-norm d = 96, inner product, 2 shards, k = 48) at N = 40,000
+    with the cluster count scaled like the points (80 centers)."""
+    from synth import gen, pgbuild
+    w = gen.make("precision", N=40_000, nq=1000, n_centers=80)
+    graphs = pgbuild.build_all(w)
+    P = O.Problem.from_workload(w, graphs)
+    return w, graphs, P, _inp(w, graphs)
+
+
+def test_precision_recipe_refine_pass_and_merge(deep_like):
+    """IP on unit vectors with the BF16 tensor-core filter: a refinement pass keeps the oracle's
+    lists; the whole merge's k-NNG recall and search recall@10 (1,000 queries, beam 64) are
+    within 0.5 point of the oracle-merged graph's."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = deep_like
+    assert w.metric == 1 and w.d == 96 and w.k == 48
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    st = fg.refine_pass(inp, g, join_filter="tc")
+    O.refine_iter(P, o)
+    bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)
+    assert len(bad) == 0, bad[:10]
+    assert sum(st["join_class"][:3]) > 0 and st["join_class"][3] == 0, st["join_class"]
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=3, return_knng=True)
+    ref = O.merge(P, w.k, w.R, w.alpha, iters=3)
+    gi = _np(out["ids"])
+    PR.check_lists(gi, _np(out["dist"]), w.N)
+    assert PR.bfs_reached(gi, out["entry"]).all() and out["entry"] == ref.entry
+    samp = np.random.default_rng(8).choice(w.N, 2000, replace=False)
+    tid, _ = O.knn_exact(w.X, w.X[samp], w.k, w.metric, exclude=samp)
+    kg = _np(out["knng"]["ids"])
+    assert abs(O.recall_at(kg[samp], tid, w.k) - O.recall_at(ref.knn_ids[samp], tid, w.k)) <= 0.005
+    gt, _ = O.knn_exact(w.X, w.Q, 10, w.metric)
+    sg, _ = fg.search(inp.X, out["ids"], out["entry"], torch.from_numpy(w.Q).to(_dev()), topk=10, beam=64,
+                      metric="ip")
+    so, _, _ = O.search(w.X, ref.ids, ref.entry, w.Q, 64, 10, w.metric)
+    assert abs(O.recall_at(_np(sg), gt, 10) - O.recall_at(so, gt, 10)) <= 0.005
+
+
+# --------------------------------------------------------------------------- join forms reached
+def test_parity_inputs_reach_every_join_form(sift_like, small):
+    """The Sift-like parity input reaches all three tensor-core size classes of Update over the
+    passes of a merge (the first pass has only new candidates, |C| <= 128; later passes add old
+    ones); k = 96 (candidate sets above the tile's limits) takes the FP32 tile, and its lists
+    still equal the oracle's."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    seen = [0, 0, 0, 0]
+    for _ in range(3):
+        st = fg.refine_pass(inp, g)
+        seen = [a + b for a, b in zip(seen, st["join_class"])]
+        fg.indegree_repair(inp, g)
+    assert all(c > 0 for c in seen[:3]), seen
+    ws, gs, Ps, inps = small
+    os_, _, _ = O.stage_a(Ps, 96)
+    g = _to_dev(os_)
+    st = fg.refine_pass(inps, g, join_filter="tc")
+    O.refine_iter(Ps, os_)
+    assert st["join_class"][3] > 0, st["join_class"]
+    bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), os_.ids, os_.dist)
+    assert len(bad) == 0, bad[:10]
+
+
+# --------------------------------------------------------------------------- rarely taken paths (test hooks)
+@pytest.fixture
+def hooks():
+    import paper_2603_21710_gb300 as fg
+    fg.load()
+    yield fg._lib
+    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1)):
+        fg._lib.test_set(knob, off)
+
+
+@pytest.mark.parametrize("join_filter", ["tc", "fp32"])
+def test_proposal_overflow_rerun_bit_exact(sift_like, hooks, join_filter):
+    """A proposal buffer far too small for one pass: the vertices whose proposals did not fit
+    are re-run against the merged lists, and the pass still equals the oracle's bit for bit."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    hooks.test_set("prop_cap", 1)   # raised to what one vertex can propose
+    st = fg.refine_pass(inp, g, join_filter=join_filter)
+    hooks.test_set("prop_cap", 0)
+    O.refine_iter(P, o)
+    assert st["join_reruns"] > 0
+    assert np.array_equal(_np(g["ids"]), o.ids)
+    assert np.array_equal(_np(g["dist"]), o.dist)
+    assert np.array_equal(_np(g["flags"]), o.flags)
+
+
+def test_hop_budget_runs_out_cleanly(small, hooks):
+    """A beam search whose expansion budget runs out stops, the call returns FGIM_ETIMEOUT, and
+    the next call on the same context works."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    Q = torch.from_numpy(w.Q[:64]).to(_dev())
+    hooks.test_set("hop_budget", 2)
+    with pytest.raises(fg.FgimError) as e:
+        fg.cross_query(inp, w.k)
+    assert e.value.status == -4
+    with pytest.raises(fg.FgimError) as e:
+        fg.search(inp.X, out["ids"], out["entry"], Q, topk=10, beam=64)
+    assert e.value.status == -4
+    hooks.test_set("hop_budget", 0)
+    g = fg.cross_query(inp, w.k)
+    o, _, _ = O.stage_a(P, w.k)
+    assert np.all(_np(g["ids"]) == o.ids, 1).mean() >= 0.99
+
+
+def test_alloc_failure_is_enomem_and_leaks_nothing(small, hooks):
+    """A scratch allocation that fails at any point of a merge returns FGIM_ENOMEM, every byte the
+    call had taken goes back to the pool, and the next merge equals an undisturbed one."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    ref = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    n = hooks.test_get("scratch_allocs")
+    assert n > 10
+    torch.cuda.synchronize()
+    assert hooks.test_get("pool_used_bytes") == 0
+    for after in sorted({0, 1, n // 4, n // 2, n - 1}):
+        hooks.test_set("fail_alloc_after", after)
+        with pytest.raises(fg.FgimError) as e:
+            fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+        hooks.test_set("fail_alloc_after", -1)
+        torch.cuda.synchronize()
+        assert e.value.status == -2, after
+        assert hooks.test_get("pool_used_bytes") == 0, after
+    again = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    assert torch.equal(again["ids"], ref["ids"]) and again["entry"] == ref["entry"]
+
+
+# --------------------------------------------------------------------------- input-PG builder, float data
+@pytest.mark.parametrize("metric", ["l2", "cos"])
+def test_build_pg_float_data_matches_oracle(metric):
+    """The GPU input-PG builder on float data (the small recipe; and the same rows under cosine):
+    distances within the FP32 tolerance and neighbour lists equal wherever distances differ by
+    more than it."""
+    import paper_2603_21710_gb300 as fg
+    from synth import gen
+    w = gen.make("small", N=4000, nq=10)
+    Xs = np.ascontiguousarray(w.X[:3000])
+    m = {"l2": 0, "cos": 2}[metric]
+    adj, entry = fg.build_pg(torch.from_numpy(Xs).to(_dev()), M=12, ef=32, metric=metric)
+    ref, ref_entry = O.build_pg(Xs, m, 12, 32)
+    ga = _np(adj)
+    assert entry == ref_entry
+    def dists(A):
+        D = np.full(A.shape, np.inf, np.float32)
+        for u in range(A.shape[0]):
+            for t in range(A.shape[1]):
+                if A[u, t] >= 0:
+                    D[u, t] = O.delta(Xs[u], Xs[A[u, t]], m)
+        return D
+    bad = PR.lists_match(ga, dists(ga), ref, dists(ref))
+    assert len(bad) <= 0.002 * Xs.shape[0], bad[:10]

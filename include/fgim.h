@@ -113,8 +113,22 @@ typedef struct {
                                 dim % 16 == 0, the searches, the join's re-rank and the prune read one
                                 byte per coordinate and form the distances in exact integer arithmetic
                                 (they equal the FP32 distances bit for bit); 1 = off (FP32 rows only) */
-    int32_t reserved[3];
+    int32_t prune_rule;      /* fgim_prune_rule of Alg. 5's neighbour selection (0 = alpha-RNG) */
+    float tau;               /* tau of FGIM_PRUNE_TAU_MNG (>= 0, in units of sqrt(distance)) */
+    int32_t reserved;
 } fgim_params;
+
+/* Neighbour-selection rules of Alg. 5 (Sec. 4.3.1 names RNG, MRNG and tau-MNG as interchangeable;
+ * the paper defines none but alpha-RNG, so the others follow the works it cites). u is the
+ * vertex, candidates v are visited in ascending (distance, id), w ranges over the neighbours
+ * kept so far; every rule keeps v when T(v) = 1 (Alg. 5's indegree clause) and stops at R.
+ *   FGIM_PRUNE_ALPHA_RNG  w occludes v iff alpha^2 delta(w,v) >= delta(u,v) (alpha = 1: Alg. 5).
+ *   FGIM_PRUNE_MRNG       w occludes v iff delta(w,v) < delta(u,v) (NSG's edge selection).
+ *   FGIM_PRUNE_TAU_MNG    on the metric distances sqrt(delta): w occludes v iff sqrt(delta(u,w)) <
+ *                         sqrt(delta(u,v)) and sqrt(delta(w,v)) < sqrt(delta(u,v)) - 3 tau, so
+ *                         edges shorter than 3 tau are never pruned (decided in FP32:
+ *                         t = sqrt(delta(u,v)) - 3 tau, occluded iff t > 0 and delta(w,v) < t * t). */
+typedef enum { FGIM_PRUNE_ALPHA_RNG = 0, FGIM_PRUNE_MRNG = 1, FGIM_PRUNE_TAU_MNG = 2 } fgim_prune_rule;
 
 /* k-NNG buffers, caller-owned device memory: [n, k] each. */
 typedef struct {
@@ -204,8 +218,9 @@ fgim_status fgim_indegree_repair(const fgim_shard* shards, int32_t h, const fgim
                                  fgim_knng* knng, int32_t* T_out, void* stream);
 
 /*
- * Alg. 5 neighbour selection: keep v when T(v) = 1 or delta(u,v) < alpha^2 delta(w,v) for
- * every kept w; stop at R. e_ids/e_dist [N, R] (-1 / +inf padded), e_cnt [N].
+ * Alg. 5 neighbour selection: keep v when T(v) = 1 or no kept w occludes it under
+ * params->prune_rule (alpha-RNG: delta(u,v) < alpha^2 delta(w,v) for every kept w); stop at R.
+ * e_ids/e_dist [N, R] (-1 / +inf padded), e_cnt [N].
  */
 fgim_status fgim_prune(const fgim_shard* shards, int32_t h, const fgim_params* params,
                        const fgim_knng* knng, const int32_t* T, int32_t* e_ids, float* e_dist,

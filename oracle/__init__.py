@@ -74,6 +74,9 @@ def lib():
                 "or_indegree_repair": (None, [vp, i32, vp, vp, vp, vp, vp]),
                 "or_indegree": (None, [vp, i64, i32, vp]),
                 "or_prune": (None, [vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp]),
+                "or_prune_rule": (None, [vp, i32, vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp]),
+                "or_merge_rule": (i32, [vp, i32, i32, i32, i32, i32, i32, f32, f32, i32, vp, vp, vp, vp, vp, vp,
+                                        vp]),
                 "or_reverse_insert": (None, [i64, i32, vp, vp, vp, vp, vp, vp]),
                 "or_reach_fix": (None, [vp, i32, i32, i32, vp, vp, vp, vp]),
                 "or_merged_entry": (i32, [vp]),
@@ -248,15 +251,19 @@ def indegree_repair(P: Problem, g: KNNG):
     return T, st.as_dict()
 
 
-def prune(P: Problem, g: KNNG, T: np.ndarray, R: int, alpha: float):
+PRUNE_RULES = {"arng": 0, "mrng": 1, "tmng": 2, 0: 0, 1: 1, 2: 2}
+
+
+def prune(P: Problem, g: KNNG, T: np.ndarray, R: int, alpha: float, rule="arng", tau: float = 0.0):
+    """Alg. 5 neighbour selection with the rule `rule` ("arng" alpha-RNG, "mrng", "tmng" tau-MNG)."""
     k = g.ids.shape[1]
     T = np.ascontiguousarray(T, dtype=np.int32)
     e_ids = np.empty((P.N, R), np.int32)
     e_dist = np.empty((P.N, R), np.float32)
     e_cnt = np.empty(P.N, np.int32)
     st = Stats()
-    lib().or_prune(P.ref, k, g.ids.ctypes.data, g.dist.ctypes.data, T.ctypes.data, R, alpha, e_ids.ctypes.data,
-                   e_dist.ctypes.data, e_cnt.ctypes.data, ctypes.byref(st))
+    lib().or_prune_rule(P.ref, k, g.ids.ctypes.data, g.dist.ctypes.data, T.ctypes.data, R, PRUNE_RULES[rule], alpha,
+                        tau, e_ids.ctypes.data, e_dist.ctypes.data, e_cnt.ctypes.data, ctypes.byref(st))
     return e_ids, e_dist, e_cnt, st.as_dict()
 
 
@@ -300,9 +307,9 @@ class MergeResult:
 
 
 def merge(P: Problem, k: int, R: int, alpha: float, L: int = 0, iters: int = 3, rev_cap: int = 0,
-          ensure_reachable: bool = True) -> MergeResult:
+          ensure_reachable: bool = True, rule="arng", tau: float = 0.0) -> MergeResult:
     if P.valid is not None:
-        return _merge_valid(P, k, R, alpha, L, iters, rev_cap, ensure_reachable)
+        return _merge_valid(P, k, R, alpha, L, iters, rev_cap, ensure_reachable, rule, tau)
     N = P.N
     o_ids = np.empty((N, R), np.int32)
     o_dist = np.empty((N, R), np.float32)
@@ -311,13 +318,13 @@ def merge(P: Problem, k: int, R: int, alpha: float, L: int = 0, iters: int = 3, 
     k_ids = np.empty((N, k), np.int32)
     k_dist = np.empty((N, k), np.float32)
     st = Stats()
-    Lu = lib().or_merge(P.ref, k, L, iters, rev_cap, R, alpha, int(ensure_reachable), o_ids.ctypes.data,
-                        o_dist.ctypes.data, o_deg.ctypes.data, entry.ctypes.data, k_ids.ctypes.data,
-                        k_dist.ctypes.data, ctypes.byref(st))
+    Lu = lib().or_merge_rule(P.ref, k, L, iters, rev_cap, R, PRUNE_RULES[rule], alpha, tau, int(ensure_reachable),
+                             o_ids.ctypes.data, o_dist.ctypes.data, o_deg.ctypes.data, entry.ctypes.data,
+                             k_ids.ctypes.data, k_dist.ctypes.data, ctypes.byref(st))
     return MergeResult(o_ids, o_dist, o_deg, int(entry[0]), k_ids, k_dist, int(Lu), st.as_dict())
 
 
-def _merge_valid(P: Problem, k, R, alpha, L, iters, rev_cap, ensure_reachable) -> MergeResult:
+def _merge_valid(P: Problem, k, R, alpha, L, iters, rev_cap, ensure_reachable, rule="arng", tau=0.0) -> MergeResult:
     """The merge with invalid vertices: Alg. 2 over the input PGs with phi dropping invalid
     vertices, then the stages of ``or_merge`` in the same order on the valid vertices alone."""
     g, Lu, st = stage_a(P, k, L)
@@ -328,7 +335,7 @@ def _merge_valid(P: Problem, k, R, alpha, L, iters, rev_cap, ensure_reachable) -
         T, _ = indegree_repair(Pc, g)
     if iters <= 0:
         T = indegree(g.ids)
-    e_ids, e_dist, e_cnt, _ = prune(Pc, g, T, R, alpha)
+    e_ids, e_dist, e_cnt, _ = prune(Pc, g, T, R, alpha, rule, tau)
     o_ids, o_dist, o_deg = reverse_insert(e_ids, e_dist, e_cnt)
     entry = merged_entry(P)
     if ensure_reachable:

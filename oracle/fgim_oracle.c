@@ -7,7 +7,8 @@
  *   Alg. 3  k-NNG refinement, Visit + Update (4.2.1)  -> or_refine_iter (synchronous form)
  *   Alg. 4  indegree repair (Sec. 4.2.2)              -> or_indegree_repair
  *   Alg. 5  k-NNG -> PG: neighbour selection and
- *           connectivity enhancement (Sec. 4.3)       -> or_prune, or_reverse_insert
+ *           connectivity enhancement (Sec. 4.3)       -> or_prune_rule (alpha-RNG, MRNG, tau-MNG),
+ *                                                        or_reverse_insert
  *   added   reachability fix                          -> or_reach_fix
  *
  * Readings of the paper where it is silent (each one also listed in the design notes):
@@ -597,11 +598,36 @@ void or_indegree_repair(const or_input* in, int32_t k, int32_t* ids, float* dist
 /* ------------------------------------------------------------------------- */
 /* Alg. 5 k-NNG -> PG                                                          */
 /* ------------------------------------------------------------------------- */
-void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* dist, const int32_t* T,
-              int32_t R, float alpha, int32_t* e_ids, float* e_dist, int32_t* e_cnt, or_stats* st) {
+/* Occlusion test of the neighbour-selection rule (Sec. 4.3.1 names RNG, MRNG and tau-MNG as
+ * interchangeable rules; the paper defines none of the last two, so each is restated from the
+ * work it cites). u is the vertex, w an already kept neighbour, v the candidate:
+ * duv = delta(u, v), duw = delta(u, w), dwv = delta(w, v), all squared-type distances.
+ *  OR_PRUNE_ARNG  alpha-RNG (Alg. 5 with Vamana's alpha): w occludes v iff alpha^2 dwv <= duv.
+ *  OR_PRUNE_MRNG  MRNG (NSG's edge selection, Fu et al.): w occludes v iff dwv < duv, i.e. uv is
+ *                 strictly the longest edge of the triangle uwv (w precedes v, so duw <= duv).
+ *  OR_PRUNE_TMNG  tau-MNG (Peng et al.): on the metric distances sqrt(delta), w occludes v iff
+ *                 sqrt(duw) < sqrt(duv) and sqrt(dwv) < sqrt(duv) - 3 tau: edges shorter than
+ *                 3 tau are never pruned. Decided in FP32, like every ordering decision here:
+ *                 t = sqrtf(duv) - RN(3 tau); occluded iff t > 0, duw < duv and dwv < t * t. */
+static int occludes(int32_t rule, float alpha2, float tau3, float duv, float duw, float dwv) {
+    if (rule == OR_PRUNE_MRNG) return dwv < duv;
+    if (rule == OR_PRUNE_TMNG) {
+        float t = sqrtf(duv) - tau3;
+        if (!(t > 0.f)) return 0;
+        float t2 = t * t;
+        return duw < duv && dwv < t2;
+    }
+    float bound = alpha2 * dwv;
+    return !(duv < bound);
+}
+
+void or_prune_rule(const or_input* in, int32_t k, const int32_t* ids, const float* dist, const int32_t* T,
+                   int32_t R, int32_t rule, float alpha, float tau, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
+                   or_stats* st) {
     const int64_t N = in->off[in->h];
-    /* alpha^2 rounded once to FP32: the distances are squared-type */
+    /* alpha^2 and 3 tau rounded once to FP32: the distances are squared-type */
     const float alpha2 = (float)((double)alpha * (double)alpha);
+    const float tau3 = (float)(3.0 * (double)tau);
     set_threads(in->nthreads);
     int64_t evals = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : evals)
@@ -612,15 +638,14 @@ void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* di
             int32_t v = ids[u * k + t];
             if (v < 0) break;
             float duv = dist[u * k + t];
-            /* T(v) = 1, or delta(u,v) < alpha^2 * delta(w,v) for every kept w */
+            /* T(v) = 1 (Alg. 5 keeps a vertex whose only in-edge is u), else no kept w occludes v */
             int keep = T[v] == 1;
             if (!keep) {
                 keep = 1;
                 for (int32_t s = 0; s < nr; ++s) {
                     float dwv = dist_g(in, e_ids[u * R + s], v);
                     ++evals;
-                    float bound = alpha2 * dwv;
-                    if (!(duv < bound)) { keep = 0; break; }
+                    if (occludes(rule, alpha2, tau3, duv, e_dist[u * R + s], dwv)) { keep = 0; break; }
                 }
             }
             if (keep) {
@@ -638,6 +663,11 @@ void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* di
         }
     }
     if (st) st->prune_dist += evals;
+}
+
+void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* dist, const int32_t* T,
+              int32_t R, float alpha, int32_t* e_ids, float* e_dist, int32_t* e_cnt, or_stats* st) {
+    or_prune_rule(in, k, ids, dist, T, R, OR_PRUNE_ARNG, alpha, 0.f, e_ids, e_dist, e_cnt, st);
 }
 
 void or_reverse_insert(int64_t N, int32_t R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
@@ -984,6 +1014,14 @@ int32_t or_merged_entry(const or_input* in) {
 int32_t or_merge(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,
                  float alpha, int32_t ensure_reachable, int32_t* out_ids, float* out_dist, int32_t* out_deg,
                  int32_t* out_entry, int32_t* knn_ids_out, float* knn_dist_out, or_stats* st) {
+    return or_merge_rule(in, k, L, iters, rev_cap, R, OR_PRUNE_ARNG, alpha, 0.f, ensure_reachable, out_ids, out_dist,
+                         out_deg, out_entry, knn_ids_out, knn_dist_out, st);
+}
+
+int32_t or_merge_rule(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,
+                      int32_t rule, float alpha, float tau, int32_t ensure_reachable, int32_t* out_ids,
+                      float* out_dist, int32_t* out_deg, int32_t* out_entry, int32_t* knn_ids_out,
+                      float* knn_dist_out, or_stats* st) {
     const int64_t N = in->off[in->h];
     int32_t* ids = (int32_t*)malloc(sizeof(int32_t) * N * k);
     float* dist = (float*)malloc(sizeof(float) * N * k);
@@ -998,7 +1036,7 @@ int32_t or_merge(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_
         or_indegree_repair(in, k, ids, dist, flags, T, st);
     }
     if (iters <= 0) or_indegree(ids, N, k, T);
-    or_prune(in, k, ids, dist, T, R, alpha, e_ids, e_dist, e_cnt, st);
+    or_prune_rule(in, k, ids, dist, T, R, rule, alpha, tau, e_ids, e_dist, e_cnt, st);
     or_reverse_insert(N, R, e_ids, e_dist, e_cnt, out_ids, out_dist, out_deg);
     int32_t entry = or_merged_entry(in);
     if (ensure_reachable) or_reach_fix(in, R, entry, 64, out_ids, out_dist, out_deg, st);

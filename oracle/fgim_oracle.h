@@ -89,9 +89,17 @@ void or_indegree_repair(const or_input* in, int32_t k, int32_t* ids, float* dist
 /* Indegree of every vertex over the valid entries of a [N, k] list array. */
 void or_indegree(const int32_t* ids, int64_t N, int32_t k, int32_t* T);
 
-/* Alg. 5 neighbour selection: E' [N, R] (ids -1 padded, dist), cnt [N]. */
+/* Alg. 5 neighbour selection: E' [N, R] (ids -1 padded, dist), cnt [N]. or_prune is the
+ * alpha-RNG rule; or_prune_rule takes the rule (OR_PRUNE_*, see fgim_oracle.c) and tau of tau-MNG.
+ * Every rule keeps a candidate whose indegree T is 1 (Alg. 5). */
+#define OR_PRUNE_ARNG 0
+#define OR_PRUNE_MRNG 1
+#define OR_PRUNE_TMNG 2
 void or_prune(const or_input* in, int32_t k, const int32_t* ids, const float* dist, const int32_t* T,
               int32_t R, float alpha, int32_t* e_ids, float* e_dist, int32_t* e_cnt, or_stats* st);
+void or_prune_rule(const or_input* in, int32_t k, const int32_t* ids, const float* dist, const int32_t* T,
+                   int32_t R, int32_t rule, float alpha, float tau, int32_t* e_ids, float* e_dist, int32_t* e_cnt,
+                   or_stats* st);
 
 /* Alg. 5 connectivity enhancement: out [N, R] from E' and its reverse edges. */
 void or_reverse_insert(int64_t N, int32_t R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
@@ -114,10 +122,15 @@ void or_knn_prefix(const float* X, int64_t N, int32_t d, int32_t metric, int32_t
  * Returns the number of valid vertices. */
 int64_t or_phi(const or_input* in, int32_t* phi);
 
-/* Full merge: stage a, iters x (refine + repair), prune, reverse insertion, reachability fix. */
+/* Full merge: stage a, iters x (refine + repair), prune, reverse insertion, reachability fix.
+ * or_merge prunes with alpha-RNG; or_merge_rule with the given rule. */
 int32_t or_merge(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,
                  float alpha, int32_t ensure_reachable, int32_t* out_ids, float* out_dist, int32_t* out_deg,
                  int32_t* out_entry, int32_t* knn_ids_out, float* knn_dist_out, or_stats* st);
+int32_t or_merge_rule(const or_input* in, int32_t k, int32_t L, int32_t iters, int32_t rev_cap, int32_t R,
+                      int32_t rule, float alpha, float tau, int32_t ensure_reachable, int32_t* out_ids,
+                      float* out_dist, int32_t* out_deg, int32_t* out_entry, int32_t* knn_ids_out,
+                      float* knn_dist_out, or_stats* st);
 
 /* Alg. 1 over the merged graph (global ids, rows of R) for nq queries. */
 void or_search(const float* X, int64_t N, int32_t d, int32_t metric, const int32_t* g_ids, int32_t R,

@@ -31,6 +31,8 @@ JOIN_FILTERS = {"tc": 0, "bf16": 0, "fp32": 1, "simt": 1, 0: 0, 1: 1}
 # [0, 255], d <= 128, d % 16 == 0; distances are then exact integers, equal to the FP32
 # ones), "fp32" always reads the FP32 rows
 ROW_STORAGE = {"auto": 0, "fp32": 1, "off": 1, 0: 0, 1: 1}
+# Alg. 5's neighbour-selection rule: alpha-RNG, MRNG or tau-MNG (with tau)
+PRUNE_RULES = {"arng": 0, "alpha-rng": 0, "mrng": 1, "tmng": 2, "tau-mng": 2, 0: 0, 1: 1, 2: 2}
 
 
 def _stream() -> int:
@@ -127,13 +129,14 @@ class MergeInput:
         return cls(vs, ads, entries, metric, None if valid is None else ms)
 
     def params(self, k=16, R=32, alpha=1.0, L=0, iters=3, rev_cap=0, ensure_reachable=True,
-               reach_beam=0, join_filter="tc", rows="auto") -> Params:
+               reach_beam=0, join_filter="tc", rows="auto", rule="arng", tau=0.0) -> Params:
         p = Params()
         p.dim, p.dtype, p.metric = self.d, self.dtype, self.metric
         p.k, p.R, p.alpha, p.L, p.iters, p.rev_cap = k, R, float(alpha), L, iters, rev_cap
         p.ensure_reachable, p.reach_beam = int(bool(ensure_reachable)), reach_beam
         p.join_filter = JOIN_FILTERS[join_filter]
         p.byte_rows = ROW_STORAGE[rows]
+        p.prune_rule, p.tau = PRUNE_RULES[rule], float(tau)
         return p
 
 
@@ -154,10 +157,11 @@ def trim_memory() -> None:
 
 def merge(inp: MergeInput, k: int, R: int, alpha: float = 1.0, L: int = 0, iters: int = 3, rev_cap: int = 0,
           ensure_reachable: bool = True, reach_beam: int = 0, return_knng: bool = False,
-          join_filter="tc", rows="auto") -> dict:
-    """Full merge (stages a, b, c and the reachability fix). Returns device tensors."""
+          join_filter="tc", rows="auto", rule="arng", tau: float = 0.0) -> dict:
+    """Full merge (stages a, b, c and the reachability fix). Returns device tensors. rule: Alg. 5's
+    neighbour selection ("arng" alpha-RNG, "mrng", "tmng" tau-MNG with `tau`)."""
     L_ = load()
-    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter, rows)
+    p = inp.params(k, R, alpha, L, iters, rev_cap, ensure_reachable, reach_beam, join_filter, rows, rule, tau)
     dev = inp.X.device
     N = inp.N_out
     out = {"ids": torch.empty((N, R), dtype=torch.int32, device=dev),
@@ -269,11 +273,12 @@ def indegree_repair(inp: MergeInput, knng: dict):
     return T, last_stats()
 
 
-def prune(inp: MergeInput, knng: dict, T: torch.Tensor, R: int, alpha: float = 1.0, rows="auto"):
-    """Alg. 5 neighbour selection: returns (e_ids [N, R], e_dist, e_cnt)."""
+def prune(inp: MergeInput, knng: dict, T: torch.Tensor, R: int, alpha: float = 1.0, rows="auto", rule="arng",
+          tau: float = 0.0):
+    """Alg. 5 neighbour selection with `rule` (see merge): returns (e_ids [N, R], e_dist, e_cnt)."""
     L_ = load()
     k = int(knng["ids"].shape[1])
-    p = inp.params(k=k, R=R, alpha=alpha, rows=rows)
+    p = inp.params(k=k, R=R, alpha=alpha, rows=rows, rule=rule, tau=tau)
     dev = inp.X.device
     e_ids = torch.empty((inp.N, R), dtype=torch.int32, device=dev)
     e_dist = torch.empty((inp.N, R), dtype=torch.float32, device=dev)

@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
                 ("k", ctypes.c_int32), ("R", ctypes.c_int32), ("alpha", ctypes.c_float), ("L", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("rev_cap", ctypes.c_int32), ("ensure_reachable", ctypes.c_int32),
                 ("reach_beam", ctypes.c_int32), ("join_filter", ctypes.c_int32), ("byte_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("prune_rule", ctypes.c_int32), ("tau", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class KNNG(ctypes.Structure):

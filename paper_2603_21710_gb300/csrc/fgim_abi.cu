@@ -251,6 +251,9 @@ static void check_params(const fgim_params* p, bool need_merge) {
     need(p->reach_beam >= 0 && p->reach_beam <= FGIM_MAX_L, FGIM_EINVAL, "reach_beam must be 0 or in [1, 128]");
     need(p->join_filter == 0 || p->join_filter == 1, FGIM_EINVAL, "join_filter must be 0 (tensor core) or 1 (FP32)");
     need(p->byte_rows == 0 || p->byte_rows == 1, FGIM_EINVAL, "byte_rows must be 0 (auto) or 1 (off)");
+    need(p->prune_rule >= FGIM_PRUNE_ALPHA_RNG && p->prune_rule <= FGIM_PRUNE_TAU_MNG, FGIM_EINVAL,
+         "prune_rule must be 0 (alpha-RNG), 1 (MRNG) or 2 (tau-MNG)");
+    need(std::isfinite(p->tau) && p->tau >= 0.f, FGIM_EINVAL, "tau must be a finite number >= 0");
 }
 
 static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
@@ -589,8 +592,11 @@ static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stat
 
 static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knng* g, const int32_t* T, int32_t* e_ids,
                   float* e_dist, int32_t* e_cnt) {
-    const float alpha2 = (float)((double)p->alpha * (double)p->alpha);
-    ck(launch_prune(P.X, P.X8, P.inv, P.N, P.d, P.metric, *g, T, p->R, alpha2, e_ids, e_dist, e_cnt, c.status, c.s));
+    PruneRule rule;
+    rule.kind = p->prune_rule;
+    rule.alpha2 = (float)((double)p->alpha * (double)p->alpha);   // alpha^2 and 3 tau rounded once to FP32
+    rule.tau3 = (float)(3.0 * (double)p->tau);
+    ck(launch_prune(P.X, P.X8, P.inv, P.N, P.d, P.metric, *g, T, p->R, rule, e_ids, e_dist, e_cnt, c.status, c.s));
 }
 
 static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
@@ -1043,7 +1049,8 @@ static void build_layer_graph(Ctx& c, const float* X, int dim, int metric, const
     int32_t* e_ids = c.alloc<int32_t>(nl * M);
     float* e_dist = c.alloc<float>(nl * M);
     int32_t* e_cnt = c.alloc<int32_t>(nl);
-    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, 1.f, e_ids, e_dist, e_cnt, c.status, c.s));
+    const PruneRule rng = {FGIM_PRUNE_ALPHA_RNG, 1.f, 0.f};   // HNSW's heuristic: alpha = 1, no indegree clause
+    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g1, T, M, rng, e_ids, e_dist, e_cnt, c.status, c.s));
     const int wide = FGIM_MAX_K;   // own and reverse edges together (their 128 nearest if more)
     int32_t* w_ids = c.alloc<int32_t>(nl * wide);
     float* w_dist = c.alloc<float>(nl * wide);
@@ -1063,7 +1070,7 @@ static void build_layer_graph(Ctx& c, const float* X, int dim, int metric, const
     g2.n = nl;
     g2.k = wide;
     float* f_dist = c.alloc<float>(nl * M);
-    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g2, T, M, 1.f, adj, f_dist, deg, c.status, c.s));
+    ck(launch_prune(L.X, L.X8, L.inv, nl, dim, metric, g2, T, M, rng, adj, f_dist, deg, c.status, c.s));
 }
 
 fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric,

@@ -83,6 +83,34 @@ __device__ __forceinline__ int shard_of(const ShardTable& t, long long g) {
     return lo;
 }
 
+// Neighbour-selection rule of Alg. 5 (Sec. 4.3.1 names RNG, MRNG and tau-MNG as interchangeable;
+// fgim_params.prune_rule). u is the vertex, w a kept neighbour, v the candidate; duv, duw, dwv
+// their squared-type distances. Every rule also keeps v when T(v) = 1 (checked by the caller).
+//   0 alpha-RNG: w occludes v iff alpha^2 dwv >= duv (product rounded once in FP32);
+//   1 MRNG (NSG's edge selection): w occludes v iff dwv < duv;
+//   2 tau-MNG: on the metric distances sqrt(delta), w occludes v iff sqrt(duw) < sqrt(duv) and
+//     sqrt(dwv) < sqrt(duv) - 3 tau; in FP32: t = sqrt(duv) - 3tau, occluded iff t > 0,
+//     duw < duv and dwv < t * t (every operation a single correctly rounded one).
+struct PruneRule {
+    int kind;
+    float alpha2;   // alpha^2 rounded once to FP32 (alpha-RNG)
+    float tau3;     // 3 tau rounded once to FP32 (tau-MNG)
+};
+
+// MRNG and tau-MNG: w occludes v iff dwv < rule_thr(duv) (tau-MNG also needs duw < duv); -inf
+// when no distance is below it.
+__device__ __forceinline__ float rule_thr(const PruneRule& r, float duv) {
+    if (r.kind == 1) return duv;
+    const float t = __fsub_rn(__fsqrt_rn(duv), r.tau3);
+    return t > 0.f ? __fmul_rn(t, t) : __int_as_float(0xff800000);
+}
+
+__device__ __forceinline__ bool rule_occludes(const PruneRule& r, float duv, float duw, float dwv) {
+    if (r.kind == 0) return !(duv < __fmul_rn(r.alpha2, dwv));
+    if (r.kind == 2 && !(duw < duv)) return false;
+    return dwv < rule_thr(r, duv);
+}
+
 // Byte rows: the vectors stored as one byte per coordinate, used when every coordinate is an
 // integer in [0, 255] and d <= 128, d % 16 == 0 (distances are then exact integers below 2^24).
 __host__ __device__ inline bool byte_rows_ok(int d) { return d % 16 == 0 && d <= 128; }

@@ -117,7 +117,7 @@ cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, c
 
 // ---- k_prune.cu
 cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
-                         const fgim_knng& g, const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist,
+                         const fgim_knng& g, const int32_t* T, int R, PruneRule rule, int32_t* e_ids, float* e_dist,
                          int32_t* e_cnt, int* status, cudaStream_t s);
 struct ReverseBuffers {
     int32_t* cnt;

@@ -3,8 +3,8 @@
 // Neighbour selection runs one warp per vertex u. The candidate rows of u are staged in
 // shared memory (padded stride) when they fit; candidates are visited in ascending
 // (delta, id); for each one every kept w is tested in parallel (one lane per w) with the
-// alpha-RNG rule delta(u, v) < alpha^2 * delta(w, v) (alpha^2 rounded once to FP32, product
-// in FP32). A lane's own sequential FP32 distance decides whenever the decision is further
+// selection rule (PruneRule: alpha-RNG delta(u, v) < alpha^2 * delta(w, v) keeps v, with alpha^2
+// rounded once to FP32 and the product in FP32; or MRNG; or tau-MNG). A lane's own sequential FP32 distance decides whenever the decision is further
 // from the boundary than the rounding margin between it and the canonical distance; the few
 // decisions inside the margin are re-taken with the canonical distance (whole warp), so the
 // outcome is exactly that of the canonical distance.
@@ -31,7 +31,7 @@ template <int METRIC, bool STAGE>
 __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const float* __restrict__ inv_norm,
                                               long long N, int d, int k, const int32_t* __restrict__ ids,
                                               const float* __restrict__ dist, const int32_t* __restrict__ T, int R,
-                                              float alpha2, int32_t* __restrict__ e_ids, float* __restrict__ e_dist,
+                                              PruneRule rule, int32_t* __restrict__ e_ids, float* __restrict__ e_dist,
                                               int32_t* __restrict__ e_cnt, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
@@ -96,14 +96,22 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
                     const float sum = seq_sum<METRIC>(rowp(wi), rv, nc4);
                     if (METRIC == FGIM_COSINE) inv = __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]);
                     const float dt = delta_finish<METRIC>(sum, inv);
-                    const float bound = alpha2 * dt;
-                    float m;   // bound on |alpha^2 * (filter distance - canonical distance)| plus product rounding
-                    if (METRIC == FGIM_L2SQ) m = alpha2 * eps * sum * 1.01f;
-                    else if (METRIC == FGIM_IP) m = alpha2 * eps * nrm[wi] * nrm[t];
-                    else m = alpha2 * 2.f * eps;
-                    m += 2.f * 5.9604645e-8f * fabsf(bound);
-                    near = fabsf(duv - bound) <= m;
-                    occ = !near && !(duv < bound);
+                    float md;   // bound on |filter distance - canonical distance|
+                    if (METRIC == FGIM_L2SQ) md = eps * sum * 1.01f;
+                    else if (METRIC == FGIM_IP) md = eps * nrm[wi] * nrm[t];
+                    else md = 2.f * eps;
+                    if (rule.kind == 0) {
+                        const float bound = rule.alpha2 * dt;
+                        // plus the rounding of the product
+                        const float m = rule.alpha2 * md + 2.f * 5.9604645e-8f * fabsf(bound);
+                        near = fabsf(duv - bound) <= m;
+                        occ = !near && !(duv < bound);
+                    } else {
+                        const bool can = rule.kind == 1 || dist[u * k + wi] < duv;
+                        const float thr = rule_thr(rule, duv);
+                        near = can && fabsf(dt - thr) <= md;
+                        occ = can && !near && dt < thr;
+                    }
                 }
                 if (__any_sync(kFull, occ)) {
                     occluded = true;
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
                     const float invl = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[cidv[wi]], inv_norm[v]) : 1.f;
                     const float dc = delta_finish<METRIC>(
                         warp_butterfly(lane_part<METRIC>(rowp(wi), rv, nc4, lane)), invl);
-                    if (!(duv < __fmul_rn(alpha2, dc))) occluded = true;
+                    if (rule_occludes(rule, duv, dist[u * k + wi], dc)) occluded = true;
                 }
             }
             keep = !occluded;
@@ -151,7 +159,7 @@ template <int METRIC>
 __global__ void __launch_bounds__(128) k_prune_wide(const float* __restrict__ X, const float* __restrict__ inv_norm,
                                                     long long N, int d, int k, const int32_t* __restrict__ ids,
                                                     const float* __restrict__ dist, const int32_t* __restrict__ T,
-                                                    int R, float alpha2, int32_t* __restrict__ e_ids,
+                                                    int R, PruneRule rule, int32_t* __restrict__ e_ids,
                                                     float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
                                                     int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(128) k_prune_wide(const float* __restrict__ X,
                 const float sum = warp_butterfly(
                     lane_part<METRIC>(reinterpret_cast<const float4*>(X + (long long)w * d), rv, nc4, lane));
                 const float inv = (METRIC == FGIM_COSINE) ? __fmul_rn(inv_norm[w], inv_norm[v]) : 1.f;
-                if (!(duv < __fmul_rn(alpha2, delta_finish<METRIC>(sum, inv)))) {
+                if (rule_occludes(rule, duv, dist[u * k + kept[s]], delta_finish<METRIC>(sum, inv))) {
                     keep = false;
                     break;
                 }
@@ -224,7 +232,7 @@ template <int METRIC>
 __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__ X8, const float* __restrict__ inv_norm,
                                                      long long N, int d, int k, const int32_t* __restrict__ ids,
                                                      const float* __restrict__ dist, const int32_t* __restrict__ T,
-                                                     int R, float alpha2, int32_t* __restrict__ e_ids,
+                                                     int R, PruneRule rule, int32_t* __restrict__ e_ids,
                                                      float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
                                                      int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -323,7 +331,7 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
                     if (METRIC == FGIM_L2SQ) dc = (float)(n2[wi] + n2[t] - 2u * dot);
                     else if (METRIC == FGIM_IP) dc = delta_finish<FGIM_IP>((float)dot, 1.f);
                     else dc = delta_finish<FGIM_COSINE>((float)dot, __fmul_rn(invs[wi], invs[t]));
-                    occ |= !(duv < __fmul_rn(alpha2, dc));
+                    occ |= rule_occludes(rule, duv, dist[u * k + wi], dc);
                 }
             }
             keep = !__any_sync(kFull, occ);
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
 }
 
 cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
-                         const fgim_knng& g, const int32_t* T, int R, float alpha2, int32_t* e_ids, float* e_dist,
+                         const fgim_knng& g, const int32_t* T, int R, PruneRule rule, int32_t* e_ids, float* e_dist,
                          int32_t* e_cnt, int* status, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     const int k = g.k;
@@ -361,7 +369,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_prune", s);                                                                             \
         k_prune_bytes<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X8, inv_norm, N, d, k, g.ids, g.dist, T, \
-                                                                          R, alpha2, e_ids, e_dist, e_cnt, status);\
+                                                                          R, rule, e_ids, e_dist, e_cnt, status);\
         e = cudaGetLastError();                                                                                   \
     } while (0)
         if (metric == FGIM_L2SQ) FGIM_LAUNCH_PB(FGIM_L2SQ);
@@ -378,7 +386,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
     do {                                                                                                          \
         LaunchScope ls("k_prune", s);                                                                             \
         k_prune_wide<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R,  \
-                                                                         alpha2, e_ids, e_dist, e_cnt, status);   \
+                                                                         rule, e_ids, e_dist, e_cnt, status);   \
         e = cudaGetLastError();                                                                                   \
     } while (0)
         if (metric == FGIM_L2SQ) FGIM_LAUNCH_PW(FGIM_L2SQ);
@@ -399,7 +407,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_prune", s);                                                                             \
         k_prune<MT, ST><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R, \
-                                                                        alpha2, e_ids, e_dist, e_cnt, status);    \
+                                                                        rule, e_ids, e_dist, e_cnt, status);    \
         e = cudaGetLastError();                                                                                   \
     } while (0)
     if (stage) {

@@ -106,13 +106,27 @@ def _delta64(a, b, metric):
     return 1.0 - float(np.dot(a, b)) / (float(np.linalg.norm(a)) * float(np.linalg.norm(b)))
 
 
-def prune_row_has_near_tie(X, u, cand, dist_u, alpha, rtol=RTOL, atol=ATOL, metric=0):
-    """True when some occlusion test of row u is within tolerance of equality (FP64 check)."""
+def prune_row_has_near_tie(X, u, cand, dist_u, alpha, rtol=RTOL, atol=ATOL, metric=0, rule="arng", tau=0.0):
+    """True when some occlusion test of row u is within tolerance of equality (FP64 check): the
+    compared quantities are alpha^2 delta(w,v) against delta(u,v) (alpha-RNG), delta(w,v) against
+    delta(u,v) (MRNG) or delta(w,v) against (sqrt(delta(u,v)) - 3 tau)^2 (tau-MNG)."""
     a2 = float(np.float32(np.float64(alpha) ** 2))
     Xc = X[cand].astype(np.float64)
     for j in range(len(cand)):
+        duv = float(dist_u[j])
+        if rule == "tmng":
+            t = np.sqrt(max(duv, 0.0)) - 3.0 * tau
+            if t <= 0:
+                continue
+            thr = t * t
         for i in range(j):
             dwv = _delta64(Xc[i], Xc[j], metric)
-            if abs(float(dist_u[j]) - a2 * dwv) <= rtol * max(abs(float(dist_u[j])), a2 * dwv) + atol:
+            if rule == "arng":
+                a, b = duv, a2 * dwv
+            elif rule == "mrng":
+                a, b = duv, dwv
+            else:
+                a, b = thr, dwv
+            if abs(a - b) <= rtol * max(abs(a), abs(b)) + atol:
                 return True
     return False

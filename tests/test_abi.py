@@ -53,7 +53,8 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("kw", [dict(dim=30), dict(k=0), dict(k=200), dict(R=0), dict(alpha=float("nan")),
-                                dict(L=500), dict(metric=7), dict(iters=-1), dict(dtype=3)])
+                                dict(L=500), dict(metric=7), dict(iters=-1), dict(dtype=3), dict(prune_rule=3),
+                                dict(tau=-1.0), dict(tau=float("inf"))])
 def test_bad_params_rejected_on_host(lib, kw):
     from paper_2603_21710_gb300 import _lib
     sh = (_lib.Shard * 2)()

@@ -886,3 +886,47 @@ def test_build_pg_float_data_matches_oracle(metric):
         return D
     bad = PR.lists_match(ga, dists(ga), ref, dists(ref))
     assert len(bad) <= 0.002 * Xs.shape[0], bad[:10]
+
+
+# --------------------------------------------------------------------------- alternative neighbour selection
+RULES = [("mrng", 0.0), ("tmng", 10.0), ("tmng", 60.0)]
+
+
+@pytest.mark.parametrize("rule,tau", RULES)
+def test_prune_rules_integer_bit_exact(sift_like, rule, tau):
+    """MRNG and tau-MNG (Sec. 4.3.1) on integer data: the byte-row and FP32-row prunes equal the
+    oracle's lists bit for bit, and so does the whole merge pruned with the rule."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, T = _refined(P, w, iters=1)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, 1.0, rule, tau)
+    for rows in ("auto", "fp32"):
+        ei, ed, ec = fg.prune(inp, _to_dev(o), torch.from_numpy(T).to(_dev()), w.R, 1.0, rows=rows, rule=rule, tau=tau)
+        assert np.array_equal(_np(ei), oi) and np.array_equal(_np(ed), od) and np.array_equal(_np(ec), oc), rows
+    out = fg.merge(inp, k=w.k, R=w.R, alpha=1.0, iters=1, rule=rule, tau=tau)
+    ref = O.merge(P, w.k, w.R, 1.0, iters=1, rule=rule, tau=tau)
+    assert np.array_equal(_np(out["ids"]), ref.ids) and out["entry"] == ref.entry
+    assert PR.bfs_reached(_np(out["ids"]), out["entry"]).all()
+
+
+@pytest.mark.parametrize("which", ["small", "high_dim"])
+@pytest.mark.parametrize("rule,tau", [("mrng", 0.0), ("tmng", 0.5)])
+def test_prune_rules_float_data(which, rule, tau, request):
+    """Float data (the FP32 filter with re-check at d = 32, the warp-wide form at d = 960): the
+    oracle's lists except where an occlusion test of the rule ties within tolerance."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = request.getfixturevalue(which)
+    if which == "high_dim":
+        tau = tau / 4
+    o, T = _refined(P, w, iters=1)
+    ei, ed, ec = fg.prune(inp, _to_dev(o), torch.from_numpy(T).to(_dev()), w.R, 1.0, rule=rule, tau=tau)
+    oi, od, oc, _ = O.prune(P, o, T, w.R, 1.0, rule, tau)
+    ei, ed, ec = _np(ei), _np(ed), _np(ec)
+    diff = np.nonzero(~np.all(ei == oi, 1))[0]
+    assert len(diff) <= max(2, w.N // 2000), len(diff)
+    for u in diff:
+        cand = o.ids[u][o.ids[u] >= 0]
+        assert PR.prune_row_has_near_tie(w.X, u, cand, o.dist[u][:len(cand)], 1.0, metric=w.metric, rule=rule,
+                                         tau=tau), u
+    same = np.all(ei == oi, 1)
+    assert np.array_equal(ed[same], od[same]) and np.array_equal(ec[same], oc[same])

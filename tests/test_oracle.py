@@ -700,3 +700,77 @@ def test_knn_prefix_is_brute_force_over_earlier_rows():
         order = sorted(range(i), key=lambda j: (d[j], j))[:k]
         want = order + [-1] * (k - len(order))
         assert list(ids[i]) == want, i
+
+
+# --------------------------------------------------------------------------- alternative neighbour selection
+# Sec. 4.3.1: RNG, MRNG and tau-MNG are interchangeable neighbour-selection rules. Expected lists
+# below are derived by hand from each rule's definition (all distances exact in FP32).
+def _rule_case(points, lists, T=None):
+    X = np.zeros((len(points), 4), np.float32)
+    for i, p in enumerate(points):
+        X[i, :len(p)] = p
+    P = O.Problem(X, [len(points)], np.full((len(points), 1), -1, np.int32), np.zeros(1, np.int32), O_METRIC_L2)
+    g = _knng_from_lists(P, lists)
+    return P, g, np.full(len(points), 2, np.int32) if T is None else np.asarray(T, np.int32)
+
+
+def test_prune_rules_line_golden():
+    """u = 0, w = 1, v' = -2, v = 3 on a line. delta(u,.) = 1, 4, 9; delta(w,v') = 9, delta(w,v) = 4,
+    delta(v',v) = 25. alpha-RNG (alpha 1) and MRNG: w occludes v (4 < 9), v' survives. tau-MNG
+    with tau = 0.25: sqrt(9) - 0.75 = 2.25, 4 < 2.25^2 = 5.0625, so w occludes v; with tau = 0.4:
+    3 - 1.2 = 1.8, 4 > 3.24 and 25 > 3.24, v is kept; with tau = 1 no edge is pruned (t <= 0)."""
+    P, g, T = _rule_case([[0.], [1.], [-2.], [3.]], [[1, 2, 3], [0, 2, 3], [0, 1, 3], [1, 0, 2]])
+    expect = {("arng", 0.0): [1, 2], ("mrng", 0.0): [1, 2], ("tmng", 0.25): [1, 2], ("tmng", 0.4): [1, 2, 3],
+              ("tmng", 1.0): [1, 2, 3]}
+    for (rule, tau), want in expect.items():
+        e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, 3, 1.0, rule, tau)
+        assert e_ids[0, :e_cnt[0]].tolist() == want, (rule, tau)
+        assert e_dist[0, :e_cnt[0]].tolist() == [{1: 1.0, 2: 4.0, 3: 9.0}[x] for x in want]
+
+
+def test_prune_mrng_keeps_the_equidistant_candidate():
+    """u = (0,0), w = (2,0), v = (1,2): delta(u,w) = 4, delta(u,v) = delta(w,v) = 5. alpha-RNG with
+    alpha = 1 prunes v (5 <= 1 * 5); MRNG keeps it (uv is not strictly the longest edge)."""
+    P, g, T = _rule_case([[0., 0.], [2., 0.], [1., 2.]], [[1, 2], [0, 2], [0, 1]])
+    a, _, ca, _ = O.prune(P, g, T, 2, 1.0, "arng")
+    m, _, cm, _ = O.prune(P, g, T, 2, 1.0, "mrng")
+    assert a[0, :ca[0]].tolist() == [1]
+    assert m[0, :cm[0]].tolist() == [1, 2]
+
+
+def test_prune_rules_keep_protected_vertices():
+    """Alg. 5's indegree clause holds for every rule: a candidate with T = 1 is kept although an
+    earlier kept neighbour occludes it."""
+    P, g, T = _rule_case([[0.], [1.], [-2.], [3.]], [[1, 2, 3], [0, 2, 3], [0, 1, 3], [1, 0, 2]], T=[2, 2, 2, 1])
+    for rule in ("arng", "mrng", "tmng"):
+        e_ids, _, e_cnt, _ = O.prune(P, g, T, 3, 1.0, rule, 0.25)
+        assert e_ids[0, :e_cnt[0]].tolist() == [1, 2, 3], rule
+
+
+def test_prune_tmng_large_tau_is_top_r_truncation(small_problem):
+    """With 3 tau above every distance, tau-MNG prunes nothing: E'(u) is the first R entries."""
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    T = np.full(w.N, 2, np.int32)
+    tau = float(np.sqrt(np.nanmax(g.dist[np.isfinite(g.dist)]))) + 1.0
+    e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, 8, 1.0, "tmng", tau)
+    n = (g.ids >= 0).sum(1)
+    assert np.array_equal(e_cnt, np.minimum(n, 8))
+    assert np.array_equal(e_ids[:, :8][e_cnt == 8], g.ids[:, :8][e_cnt == 8])
+
+
+def test_prune_rules_invariants(small_problem):
+    """Every rule: degree <= R, the kept entries are a sorted subsequence of the list, and the
+    MRNG and tau-MNG lists are never shorter than alpha-RNG's with alpha = 1 on the same input at
+    the first candidate they disagree on (both keep the nearest candidate)."""
+    w, graphs, P = small_problem
+    g, _, _ = O.stage_a(P, w.k)
+    T = O.indegree(g.ids)
+    for rule, tau in (("arng", 0.0), ("mrng", 0.0), ("tmng", 0.5)):
+        e_ids, e_dist, e_cnt, _ = O.prune(P, g, T, 8, 1.0, rule, tau)
+        assert np.all(e_cnt <= 8) and np.all(e_cnt >= np.minimum(1, (g.ids >= 0).sum(1)))
+        for u in range(0, w.N, 499):
+            row = g.ids[u].tolist()
+            kept = e_ids[u, :e_cnt[u]].tolist()
+            pos = [row.index(x) for x in kept]
+            assert pos == sorted(pos) and kept[0] == row[0]

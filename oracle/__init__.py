@@ -85,6 +85,7 @@ def lib():
                 "or_refine_dfs": (None, [vp, i32, i32, vp, vp, vp, vp, vp]),
                 "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
                 "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
+                "or_hnsw_insert": (None, [vp, i64, i32, i32, vp, i32, i32, i32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -471,3 +472,29 @@ def build_pg(X: np.ndarray, metric: int, M: int, ef: int):
     n = X.shape[0]
     _, adj, _ = hnsw_layer(X, metric, np.ones(n, np.int32), 1, M, ef)
     return adj, 0
+
+
+def hnsw_insert_layers(X: np.ndarray, metric: int, levels: np.ndarray, M: int, ef: int):
+    """The upper layers as HNSW's sequential insertion builds them (the literal form of Sec.
+    4.3.3, the quality reference for ``hnsw_layer``): ([(members, adj positions, deg) per layer
+    1 .. top], entry)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    N = X.shape[0]
+    top = int(lv.max()) if N else 0
+    if top < 1:
+        return [], 0
+    adj = np.empty((top, N, M), np.int32)
+    entry = np.zeros(1, np.int32)
+    st = Stats()
+    lib().or_hnsw_insert(X.ctypes.data, N, X.shape[1], metric, lv.ctypes.data, top, M, ef, adj.ctypes.data,
+                         entry.ctypes.data, ctypes.byref(st))
+    layers = []
+    for l in range(1, top + 1):
+        members = np.nonzero(lv >= l)[0].astype(np.int32)
+        pos = np.full(N, -1, np.int32)
+        pos[members] = np.arange(len(members), dtype=np.int32)
+        A = adj[l - 1][members]
+        P = np.where(A >= 0, pos[np.maximum(A, 0)], -1).astype(np.int32)
+        layers.append((members, P, (P >= 0).sum(1).astype(np.int32)))
+    return layers, int(entry[0])

@@ -169,6 +169,110 @@ static int32_t knn_search_tagged(const float* X, int32_t d, int32_t metric, cons
     return r;
 }
 
+/* ------------------------------------------------------------------------- */
+/* HNSW's upper layers by sequential insertion (Sec. 4.3.3, as HNSW builds)    */
+/* ------------------------------------------------------------------------- */
+/* The heuristic neighbour selection of HNSW (Alg. 5's rule with alpha = 1 and no indegree
+ * clause): candidates (ids, dist to u) ascending; keep e unless a kept r has delta(e, r) <= delta(u, e);
+ * at most M. Returns the number kept, written to keep_ids / keep_dist. */
+static int32_t hnsw_heuristic(const float* X, int32_t d, int32_t metric, const int32_t* ids, const float* dist,
+                              int32_t n, int32_t M, int32_t* keep_ids, float* keep_dist) {
+    int32_t nk = 0;
+    for (int32_t t = 0; t < n && nk < M; ++t) {
+        int ok = 1;
+        for (int32_t s = 0; s < nk && ok; ++s) {
+            float der = or_delta(X + (int64_t)ids[t] * d, X + (int64_t)keep_ids[s] * d, d, metric);
+            if (!(dist[t] < der)) ok = 0;
+        }
+        if (ok) {
+            keep_ids[nk] = ids[t];
+            keep_dist[nk] = dist[t];
+            ++nk;
+        }
+    }
+    return nk;
+}
+
+void or_hnsw_insert(const float* X, int64_t N, int32_t d, int32_t metric, const int32_t* levels, int32_t max_level,
+                    int32_t M, int32_t ef, int32_t* adj, int32_t* entry_out, or_stats* st) {
+    /* adj: [max_level, N, M] global ids, -1 padded; layer l (1 .. max_level) at adj + (l-1) N M. Every
+     * vertex with level >= 1 is inserted in ascending id: greedy descent (Alg. 1 with a pool of
+     * one) from the entry through the layers above its level, then on each of its layers Alg. 1
+     * with pool ef from the vertex reached (HNSW hands all of W down as entry points; Alg. 1
+     * starts from one vertex, so the nearest of W starts the next layer), HNSW's heuristic to M,
+     * edges both ways, and the heuristic again over a neighbour's list that overflows M. The
+     * entry is the first vertex that reached the highest level. Layer 0 (the merged base graph)
+     * is not touched. */
+    for (int64_t t = 0; t < (int64_t)max_level * N * M; ++t) adj[t] = -1;
+    uint32_t* seen = (uint32_t*)calloc(N, sizeof(uint32_t));
+    uint32_t tag = 0;
+    int32_t* w_ids = (int32_t*)malloc(sizeof(int32_t) * (ef + 1));
+    float* w_dist = (float*)malloc(sizeof(float) * (ef + 1));
+    int32_t* k_ids = (int32_t*)malloc(sizeof(int32_t) * (M + 1));
+    float* k_dist = (float*)malloc(sizeof(float) * (M + 1));
+    ent_t* ov = (ent_t*)malloc(sizeof(ent_t) * (M + 1));
+    int32_t* ov_ids = (int32_t*)malloc(sizeof(int32_t) * (M + 1));
+    float* ov_dist = (float*)malloc(sizeof(float) * (M + 1));
+    int32_t* rp_ids = (int32_t*)malloc(sizeof(int32_t) * M);
+    float* rp_dist = (float*)malloc(sizeof(float) * M);
+    int32_t entry = -1, top = 0;
+    for (int64_t q = 0; q < N; ++q) {
+        const int32_t lq = levels[q] < max_level ? levels[q] : max_level;
+        if (lq < 1) continue;
+        if (entry < 0) {
+            entry = (int32_t)q;
+            top = lq;
+            continue;
+        }
+        const float* xq = X + q * d;
+        int32_t ep = entry;
+        /* greedy descent through the layers above lq */
+        for (int32_t l = top; l > lq; --l) {
+            int32_t* A = adj + (int64_t)(l - 1) * N * M;
+            int32_t r = knn_search_tagged(X, d, metric, A, M, ep, xq, 1, 1, seen, ++tag, w_ids, w_dist, st);
+            if (r > 0) ep = w_ids[0];
+        }
+        for (int32_t l = (lq < top ? lq : top); l >= 1; --l) {
+            int32_t* A = adj + (int64_t)(l - 1) * N * M;
+            int32_t r = knn_search_tagged(X, d, metric, A, M, ep, xq, ef, ef, seen, ++tag, w_ids, w_dist, st);
+            int32_t nk = hnsw_heuristic(X, d, metric, w_ids, w_dist, r, M, k_ids, k_dist);
+            for (int32_t s = 0; s < nk; ++s) A[q * M + s] = k_ids[s];
+            /* reverse edges, re-pruning a list that overflows M (the new edge with its old ones) */
+            for (int32_t s = 0; s < nk; ++s) {
+                const int32_t e = k_ids[s];
+                int32_t* row = A + (int64_t)e * M;
+                int32_t n = 0;
+                while (n < M && row[n] >= 0) ++n;
+                if (n < M) {
+                    row[n] = (int32_t)q;
+                    continue;
+                }
+                for (int32_t t = 0; t < M; ++t) {
+                    ov[t].id = row[t];
+                    ov[t].d = or_delta(X + (int64_t)e * d, X + (int64_t)row[t] * d, d, metric);
+                }
+                ov[M].id = (int32_t)q;
+                ov[M].d = k_dist[s];
+                qsort(ov, M + 1, sizeof(ent_t), ent_cmp);
+                for (int32_t t = 0; t <= M; ++t) {
+                    ov_ids[t] = ov[t].id;
+                    ov_dist[t] = ov[t].d;
+                }
+                int32_t kept = hnsw_heuristic(X, d, metric, ov_ids, ov_dist, M + 1, M, rp_ids, rp_dist);
+                for (int32_t t = 0; t < M; ++t) row[t] = t < kept ? rp_ids[t] : -1;
+            }
+            ep = w_ids[0];
+        }
+        if (lq > top) {
+            entry = (int32_t)q;
+            top = lq;
+        }
+    }
+    *entry_out = entry;
+    free(seen); free(w_ids); free(w_dist); free(k_ids); free(k_dist); free(ov); free(ov_ids); free(ov_dist);
+    free(rp_ids); free(rp_dist);
+}
+
 int32_t or_knn_search(const float* X_local, int64_t n, int32_t d, int32_t metric, const int32_t* adj_local,
                       int32_t M, int32_t ep, const float* q, int32_t L, int32_t k,
                       int32_t* out_ids, float* out_dist, or_stats* st) {

@@ -132,6 +132,13 @@ int32_t or_merge_rule(const or_input* in, int32_t k, int32_t L, int32_t iters, i
                       float* out_dist, int32_t* out_deg, int32_t* out_entry, int32_t* knn_ids_out,
                       float* knn_dist_out, or_stats* st);
 
+/* HNSW's upper layers built as HNSW builds them (Sec. 4.3.3): the vertices of level >= 1 inserted
+ * one at a time in ascending id (greedy descent, Alg. 1 with pool ef per layer, HNSW's
+ * heuristic to M, edges both ways, overflowing lists re-pruned). adj [max_level, N, M] global
+ * ids, -1 padded (layer l at offset (l - 1) N M); entry_out: the top vertex. */
+void or_hnsw_insert(const float* X, int64_t N, int32_t d, int32_t metric, const int32_t* levels, int32_t max_level,
+                    int32_t M, int32_t ef, int32_t* adj, int32_t* entry_out, or_stats* st);
+
 /* Alg. 1 over the merged graph (global ids, rows of R) for nq queries. */
 void or_search(const float* X, int64_t N, int32_t d, int32_t metric, const int32_t* g_ids, int32_t R,
                int32_t entry, const float* Q, int64_t nq, int32_t beam, int32_t topk, int32_t nthreads,

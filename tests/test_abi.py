@@ -139,3 +139,13 @@ def test_noalloc_search_refuses_bf16_storage_on_host(lib):
     p = ctypes.c_void_p((ctypes.addressof(buf) + 15) & ~15)
     st = lib.fgim_search_noalloc(p, 16, 32, 1, 0, p, 8, 0, p, 4, 10, 64, p, p, None)
     assert st == -5
+
+
+def test_graph_alloc_rejects_bad_shapes_on_host(lib):
+    from paper_2603_21710_gb300 import _lib
+    g = _lib.Graph()
+    assert lib.fgim_graph_alloc(0, 32, ctypes.byref(g)) == -1
+    assert lib.fgim_graph_alloc(10, 0, ctypes.byref(g)) == -1
+    assert lib.fgim_graph_alloc(10, 32, None) == -1
+    assert not g.ids and g.n == 0
+    lib.fgim_graph_free(ctypes.byref(g))   # a zeroed graph is a no-op

@@ -930,3 +930,27 @@ def test_prune_rules_float_data(which, rule, tau, request):
                                          tau=tau), u
     same = np.all(ei == oi, 1)
     assert np.array_equal(ed[same], od[same]) and np.array_equal(ec[same], oc[same])
+
+
+def test_library_owned_graph(small):
+    """fgim_graph_alloc / fgim_graph_free: a merge into library-owned buffers equals the merge into
+    caller-owned ones; the graph is zeroed after the free."""
+    import ctypes
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = small
+    L = fg.load()
+    ref = fg.merge(inp, k=w.k, R=w.R, alpha=w.alpha, iters=1)
+    g = fg.Graph()
+    assert L.fgim_graph_alloc(w.N, w.R, ctypes.byref(g)) == 0
+    assert g.n == w.N and g.R == w.R and g.ids
+    p = inp.params(w.k, w.R, w.alpha, 0, 1)
+    fg.check(L.fgim_merge(inp._shards, inp.h, ctypes.byref(p), None, ctypes.byref(g),
+                          torch.cuda.current_stream().cuda_stream))
+    class _View:   # the library's block seen as a tensor (no copy)
+        def __init__(self, ptr, shape):
+            self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape, "typestr": "<i4", "version": 2}
+    ids = torch.as_tensor(_View(g.ids, (w.N, w.R)), device=_dev())
+    assert torch.equal(ids, ref["ids"]) and g.entry == ref["entry"]
+    del ids
+    L.fgim_graph_free(ctypes.byref(g))
+    assert not g.ids and g.n == 0

@@ -774,3 +774,53 @@ def test_prune_rules_invariants(small_problem):
             kept = e_ids[u, :e_cnt[u]].tolist()
             pos = [row.index(x) for x in kept]
             assert pos == sorted(pos) and kept[0] == row[0]
+
+
+# --------------------------------------------------------------------------- HNSW's sequential insertion
+def test_hnsw_insert_golden():
+    """Four points on a line, inserted in id order at x = 0, 10, 1, 11 (all level 1, M = 1, ef = 4),
+    traced by hand: 1 links to 0 and 0 back to 1; 2 finds 0 and 1, keeps 0, and 0's overfull list
+    {1, 2} is re-pruned to {2} (2 occludes 1: 81 <= 100); 3, searched from the entry 0, reaches 0
+    and 2 only, keeps 2, and 2's list {0, 3} is cut to {0}."""
+    X = np.zeros((4, 4), np.float32)
+    X[:, 0] = [0, 10, 1, 11]
+    layers, entry = O.hnsw_insert_layers(X, O_METRIC_L2, np.ones(4, np.int32), 1, 4)
+    assert entry == 0 and len(layers) == 1
+    members, adj, deg = layers[0]
+    assert members.tolist() == [0, 1, 2, 3]
+    assert adj[:, 0].tolist() == [2, 0, 0, 2]
+    # the layer built at once from exact prefix candidates links 3 to 1 (its true nearest earlier
+    # member), which the sequential search from the entry could not reach
+    m2, adj2, _ = O.hnsw_layer(X, O_METRIC_L2, np.ones(4, np.int32), 1, 1, 4)
+    assert adj2[3, 0] == 1
+
+
+def test_hnsw_insert_layers_invariants(small_problem):
+    w, graphs, P = small_problem
+    levels = O.hnsw_levels(w.N, 8, seed=5)
+    layers, entry = O.hnsw_insert_layers(w.X, w.metric, levels, 8, 32)
+    assert levels[entry] == levels.max() and entry == int(np.argmax(levels))
+    for l, (members, adj, deg) in enumerate(layers, start=1):
+        assert np.array_equal(members, np.nonzero(levels >= l)[0])
+        assert adj.shape == (len(members), 8) and np.all(deg <= 8)
+        for r in range(len(members)):
+            row = adj[r][adj[r] >= 0]
+            assert len(set(row.tolist())) == len(row) and r not in set(row.tolist())
+            assert np.all(adj[r][len(row):] == -1)
+
+
+def test_parallel_layers_match_the_sequential_insertion_in_quality(small_problem):
+    """The layers built at once (every member's exact ef nearest earlier members) against HNSW's
+    sequential insertion (Sec. 4.3.3 as printed): over the same merged base graph, the layered
+    search's recall@10 (1,000 queries, beam 32, ef_up 8) stays within one point."""
+    w, graphs, P = small_problem
+    r = O.merge(P, w.k, w.R, w.alpha, iters=1)
+    levels = O.hnsw_levels(w.N, 8, seed=5)
+    seq, entry = O.hnsw_insert_layers(w.X, w.metric, levels, 8, 32)
+    par = [O.hnsw_layer(w.X, w.metric, levels, l, 8, 32) for l in range(1, len(seq) + 1)]
+    Q = w.Q[:1000]
+    gt, _ = O.knn_exact(w.X, Q, 10, w.metric)
+    rs = O.recall_at(O.hnsw_search(w.X, w.metric, r.ids, [(m, a) for m, a, _ in seq], entry, Q, 32, 10, 8)[0], gt, 10)
+    rp = O.recall_at(O.hnsw_search(w.X, w.metric, r.ids, [(m, a) for m, a, _ in par], O.hnsw_entry(levels), Q, 32,
+                                   10, 8)[0], gt, 10)
+    assert rp >= rs - 0.01, (rp, rs)

@@ -671,7 +671,11 @@ def run_fgim(args):
         fg.trim_memory()
         line["configs"] = {}
         for name in [c for c in args.configs.split(",") if c]:
-            line["configs"][name] = measure_config(fg, name, dev, peaks)
+            try:
+                line["configs"][name] = measure_config(fg, name, dev, peaks)
+            except Exception as ex:   # a sub-record that fails is reported, not fatal to the headline line
+                line["configs"][name] = {"error": f"{type(ex).__name__}: {ex}"}
+                torch.cuda.synchronize()
     print(json.dumps(line), flush=True)
 
 

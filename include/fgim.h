@@ -150,6 +150,17 @@ typedef struct {
     int32_t entry;           /* out: global id of the merged entry point */
 } fgim_graph;
 
+/*
+ * Library-owned graph buffers, for callers that let the library allocate the merged PG:
+ * fgim_graph_alloc takes one device block (cudaMalloc on the current device) holding ids [n, R],
+ * dist [n, R] and deg [n], sets g->ids, dist, deg, n, R (entry 0), and returns FGIM_ENOMEM (g
+ * zeroed) when the device has no room. fgim_graph_free releases a graph made by fgim_graph_alloc
+ * and zeroes *g; it must not be given buffers the caller allocated, and it synchronizes the
+ * device (cudaFree does). Both are safe on a zeroed graph.
+ */
+fgim_status fgim_graph_alloc(int64_t n, int32_t R, fgim_graph* g);
+void fgim_graph_free(fgim_graph* g);
+
 /* Counters of the last call on this host thread (informational). */
 typedef struct {
     int64_t ndc;             /* distance evaluations of the beam searches (stage a + reach fix) */

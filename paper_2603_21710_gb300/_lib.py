@@ -107,6 +107,8 @@ EXPORTS = {
                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fgim_last_stats": (None, [ctypes.c_void_p]),
+    "fgim_graph_alloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
+    "fgim_graph_free": (None, [ctypes.c_void_p]),
     "fgim_test_set": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_int64]),
     "fgim_test_get": (ctypes.c_int64, [ctypes.c_char_p]),
     "fgim_strerror": (ctypes.c_char_p, [ctypes.c_int]),

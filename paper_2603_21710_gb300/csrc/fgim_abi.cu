@@ -1259,6 +1259,34 @@ fgim_status fgim_search(const void* base, int64_t n, int32_t dim, int32_t dtype,
     return r;
 }
 
+fgim_status fgim_graph_alloc(int64_t n, int32_t R, fgim_graph* g) {
+    if (!g) return FGIM_EINVAL;
+    std::memset(g, 0, sizeof(*g));
+    if (n < 1 || n >= 0x7fffffffLL || R < 1 || R > FGIM_MAX_R) return FGIM_EINVAL;
+    // ids, dist and deg in one block: ids first (the block's base), each part 256-byte aligned
+    const size_t part = ((size_t)n * R * 4 + 255) & ~(size_t)255;
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, 2 * part + (size_t)n * 4);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        t_last_error = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? FGIM_ENOMEM : FGIM_ECUDA;
+    }
+    g->ids = static_cast<int32_t*>(p);
+    g->dist = reinterpret_cast<float*>(static_cast<char*>(p) + part);
+    g->deg = reinterpret_cast<int32_t*>(static_cast<char*>(p) + 2 * part);
+    g->n = n;
+    g->R = R;
+    g->entry = 0;
+    return FGIM_OK;
+}
+
+void fgim_graph_free(fgim_graph* g) {
+    if (!g) return;
+    if (g->ids) cudaFree(g->ids);
+    std::memset(g, 0, sizeof(*g));
+}
+
 int32_t fgim_test_set(const char* knob, int64_t value) {
     if (!knob) return 0;
     const std::string k(knob);

@@ -293,7 +293,10 @@ __host__ __device__ inline StagedLayout staged_layout(int cm, int k, int d) {
 }
 
 // out[0] = largest |C| and out[1] = largest |C_n| among the vertices that have pairs
-template <int METRIC>
+// STAGE: the candidates' rows are copied to shared memory (stride d + 4); otherwise (sets of
+// wide rows that do not fit) every read goes to the FP32 rows in global memory, mostly served
+// by L2 (the same values, so the same distances).
+template <int METRIC, bool STAGE>
 __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     ShardTable t, const float* __restrict__ X, const float* __restrict__ inv_norm, int k,
     const int32_t* __restrict__ ids, const float* __restrict__ dist, const int32_t* __restrict__ cand,
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
         return;
     }
     const int d = t.dim;
-    const StagedLayout L = staged_layout(cm, k, d);
+    const StagedLayout L = staged_layout(cm, k, STAGE ? d : 0);
     uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
     int32_t* cid = reinterpret_cast<int32_t*>(smem + L.cid);
     int32_t* csh = reinterpret_cast<int32_t*>(smem + L.csh);
@@ -330,16 +333,19 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     const int W = L.words, hs = L.hs, stride = d + 4;
     const int vq = d >> 2;
     const float eps = fp32_pair_margin(d);
+    // row r of the candidate set: staged copy or the FP32 row itself
+    auto rowp = [&](int r) -> const float* { return STAGE ? rows + r * stride : X + (long long)cid[r] * d; };
 
     for (int i = tid; i < nc; i += kJThreads) cid[i] = cand[v * cmax + i];
     for (int i = tid; i < hs; i += kJThreads) hk[i] = -1;
     for (int i = tid; i < nc * W; i += kJThreads) mask[i] = 0u;
     if (tid < 16) misc[tid] = 0;
     __syncthreads();
-    for (int item = tid; item < nc * vq; item += kJThreads) {
-        const int r = item / vq, c = item - (item / vq) * vq;
-        cp_async16(rows + r * stride + c * 4, X + (long long)cid[r] * d + c * 4, true);
-    }
+    if (STAGE)
+        for (int item = tid; item < nc * vq; item += kJThreads) {
+            const int r = item / vq, c = item - (item / vq) * vq;
+            cp_async16(rows + r * stride + c * 4, X + (long long)cid[r] * d + c * 4, true);
+        }
     cp_async_commit();
     for (int i = tid; i < nc; i += kJThreads) {
         const int32_t c = cid[i];
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
     if (METRIC == FGIM_IP)
         for (int i = tid; i < nc; i += kJThreads) {
             float ss = 0.f;
-            for (int c = 0; c < d; ++c) ss = fmaf(rows[i * stride + c], rows[i * stride + c], ss);
+            for (int c = 0; c < d; ++c) ss = fmaf(rowp(i)[c], rowp(i)[c], ss);
             nrm[i] = sqrtf(ss) * 1.0001f;
         }
     __syncthreads();
@@ -420,9 +426,9 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
             const float* ar[4];
             const float* br[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) ar[a] = rows + min(r0 + ty + 8 * a, nc - 1) * stride;
+            for (int a = 0; a < 4; ++a) ar[a] = rowp(min(r0 + ty + 8 * a, nc - 1));
 #pragma unroll
-            for (int b = 0; b < 4; ++b) br[b] = rows + min(c0 + tx + 8 * b, nc - 1) * stride;
+            for (int b = 0; b < 4; ++b) br[b] = rowp(min(c0 + tx + 8 * b, nc - 1));
             for (int c = 0; c < vq; ++c) {
                 float4 av[4], bv[4];
 #pragma unroll
@@ -482,9 +488,8 @@ __global__ void __launch_bounds__(kJThreads, 2) k_join_staged(
                 const uint32_t e = gq[qi];
                 const int i = e & 1023, j = (e >> 10) & 1023;
                 const unsigned dm = (e >> 20) & 3u;
-                const float sc = warp_butterfly(lane_part<METRIC>(reinterpret_cast<const float4*>(rows + i * stride),
-                                                                  reinterpret_cast<const float4*>(rows + j * stride),
-                                                                  vq, lane));
+                const float sc = warp_butterfly(lane_part<METRIC>(reinterpret_cast<const float4*>(rowp(i)),
+                                                                  reinterpret_cast<const float4*>(rowp(j)), vq, lane));
                 if (lane < 2 && ((dm >> lane) & 1u)) {
                     const float dd = delta_finish<METRIC>(sc, METRIC == FGIM_COSINE ? __fmul_rn(cinv[i], cinv[j]) : 1.f);
                     const int a = lane == 0 ? i : j, b = lane == 0 ? j : i;
@@ -1329,24 +1334,32 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         }
         return e;
     }
-    const StagedLayout SL = staged_layout(cm, g.k, t.dim);
+    // the rows are staged when they fit the shared memory of a CTA, otherwise read from global memory
+    const bool stage = staged_layout(cm, g.k, t.dim).bytes <= 227 * 1024;
+    const StagedLayout SL = staged_layout(cm, g.k, stage ? t.dim : 0);
     if (SL.bytes > 227 * 1024) return cudaErrorNotSupported;
     b.class_count[3] += (long long)hb[2] + hb[3] + hb[4];   // the vertices with a pair to join
     const size_t smem = SL.bytes;
-#define FGIM_LAUNCH_JS(MT)                                                                                        \
+#define FGIM_LAUNCH_JS(MT, ST)                                                                                    \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(k_join_staged<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        e = cudaFuncSetAttribute(k_join_staged<MT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
-        k_join_staged<MT><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand, b.nn,  \
-                                                                b.no, b.cmax, cm, vlist, b.prop_tgt, b.prop_key,  \
-                                                                b.prop_count, b.prop_cap, b.pending, pairs,       \
-                                                                cands, status);                                   \
+        k_join_staged<MT, ST><<<(unsigned)nv, kJThreads, smem, s>>>(t, X, inv_norm, g.k, g.ids, g.dist, b.cand,    \
+                                                                    b.nn, b.no, b.cmax, cm, vlist, b.prop_tgt,    \
+                                                                    b.prop_key, b.prop_count, b.prop_cap,         \
+                                                                    b.pending, pairs, cands, status);             \
         e = cudaGetLastError();                                                                                   \
     } while (0)
-    if (metric == FGIM_L2SQ) FGIM_LAUNCH_JS(FGIM_L2SQ);
-    else if (metric == FGIM_IP) FGIM_LAUNCH_JS(FGIM_IP);
-    else FGIM_LAUNCH_JS(FGIM_COSINE);
+    if (stage) {
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_JS(FGIM_L2SQ, true);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_JS(FGIM_IP, true);
+        else FGIM_LAUNCH_JS(FGIM_COSINE, true);
+    } else {
+        if (metric == FGIM_L2SQ) FGIM_LAUNCH_JS(FGIM_L2SQ, false);
+        else if (metric == FGIM_IP) FGIM_LAUNCH_JS(FGIM_IP, false);
+        else FGIM_LAUNCH_JS(FGIM_COSINE, false);
+    }
 #undef FGIM_LAUNCH_JS
     return e;
 }

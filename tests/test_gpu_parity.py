@@ -427,14 +427,16 @@ def test_byte_rows_equal_fp32_rows(sift_like):
     assert ma["entry"] == mb["entry"]
 
 
-def test_refine_pass_high_dim(high_dim):
-    """d = 960: the tensor-core filter over eight K chunks keeps the oracle's lists."""
+@pytest.mark.parametrize("join_filter", ["tc", "fp32"])
+def test_refine_pass_high_dim(high_dim, join_filter):
+    """d = 960: the tensor-core filter over eight K chunks, and the FP32 tile reading its rows
+    from global memory (they do not fit shared memory), keep the oracle's lists."""
     import paper_2603_21710_gb300 as fg
     w, graphs, P, inp = high_dim
     assert w.d == 960
     o, _, _ = O.stage_a(P, w.k)
     g = _to_dev(o)
-    st = fg.refine_pass(inp, g)
+    st = fg.refine_pass(inp, g, join_filter=join_filter)
     O.refine_iter(P, o)
     bad = PR.lists_match(_np(g["ids"]), _np(g["dist"]), o.ids, o.dist)
     assert len(bad) == 0, bad[:10]
@@ -768,10 +770,10 @@ def test_precision_recipe_refine_pass_and_merge(deep_like):
 
 # --------------------------------------------------------------------------- join forms reached
 def test_parity_inputs_reach_every_join_form(sift_like, small):
-    """The Sift-like parity input reaches all three tensor-core size classes of Update over the
-    passes of a merge (the first pass has only new candidates, |C| <= 128; later passes add old
-    ones); k = 96 (candidate sets above the tile's limits) takes the FP32 tile, and its lists
-    still equal the oracle's."""
+    """Update's forms on the parity inputs: the Sift-like merge passes reach the two smaller
+    tensor-core size classes; a k-NNG with mixed flags reaches the third (|C| > 128); k = 96
+    (candidate sets above the tile's limits) takes the FP32 tile; every one keeps the oracle's
+    lists."""
     import paper_2603_21710_gb300 as fg
     w, graphs, P, inp = sift_like
     o, _, _ = O.stage_a(P, w.k)
@@ -781,7 +783,16 @@ def test_parity_inputs_reach_every_join_form(sift_like, small):
         st = fg.refine_pass(inp, g)
         seen = [a + b for a, b in zip(seen, st["join_class"])]
         fg.indegree_repair(inp, g)
-    assert all(c > 0 for c in seen[:3]), seen
+    assert seen[0] > 0 and seen[1] > 0, seen
+    # a k-NNG with half of its entries old (the state of a later pass on larger data) gives sets
+    # of new and old candidates above 128: the third class, bit for bit against the oracle
+    o, _, _ = O.stage_a(P, w.k)
+    o.flags[np.random.default_rng(4).random(o.flags.shape) < 0.5] = 0
+    g = _to_dev(o)
+    st = fg.refine_pass(inp, g)
+    O.refine_iter(P, o)
+    assert st["join_class"][2] > 0, st["join_class"]
+    assert np.array_equal(_np(g["ids"]), o.ids) and np.array_equal(_np(g["flags"]), o.flags)
     ws, gs, Ps, inps = small
     os_, _, _ = O.stage_a(Ps, 96)
     g = _to_dev(os_)

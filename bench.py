@@ -59,10 +59,10 @@ def parse():
                          "the plain FP32 form of the same merges; prints its own JSON line")
     ap.add_argument("--batched-lo", type=int, default=10_000)
     ap.add_argument("--batched-hi", type=int, default=200_000)
-    ap.add_argument("--configs", default="precision,fp8",
+    ap.add_argument("--configs", default="precision,fp8,batched",
                     help="other workloads timed after the headline one, each in its own sub-record: "
                          "'precision' (1M d=96 IP, BF16 filter against plain FP32), 'fp8' (1M d=960, 8 uneven "
-                         "shards); '' = none")
+                         "shards), 'batched' (64 merges, ~4M points, d=768 BF16 cosine, one call); '' = none")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip comparing the GPU merge with the oracle's (100k sample and the largest N the "
                          "oracle finishes in about two minutes)")
@@ -367,7 +367,7 @@ def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w,
     N, d, k, M, R = w.N, w.d, w.k, w.M, w.R
     # DRAM bytes per launch from the ncu capture of the full workload (null when stale or when
     # the workload is not the captured one)
-    traffic = measured_traffic().get(kernel) if N == 1_000_000 else None
+    traffic = measured_traffic().get(kernel) if (N == 1_000_000 and getattr(w, "name", "") == "medium") else None
     out = {"kernel": kernel, "per_launch_ms": per_launch_ms, "traffic": traffic}
     hbm = dict(bound="hbm", unit="GB/s", peak=peaks.get("hbm_gbs"), peak_kind="measured copy (hbm_gbs), of measured")
     if kernel == "k_cross_query" and cpu is not None:
@@ -405,12 +405,28 @@ def roofline_for(kernel: str, per_launch_ms: float, launches_per_step: float, w,
     return out
 
 
+def gpu_graphs(fg, w, X_dev):
+    """Input PGs of every shard built on the GPU (fgim_build_pg: the recipe of the host builder,
+    bit for bit on integer data) and the milliseconds it took (CUDA events)."""
+    import torch
+    metric = {0: "l2", 1: "ip", 2: "cos"}[w.metric]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    out, o = [], 0
+    for n in w.shard_sizes:
+        out.append(fg.build_pg(X_dev[o:o + n], M=w.M, ef=w.ef, metric=metric))
+        o += n
+    b.record()
+    torch.cuda.synchronize()
+    return [(adj.cpu().numpy(), int(e)) for adj, e in out], a.elapsed_time(b)
+
+
 # the other workloads of the measurement plan, timed after the headline one (one sub-record each)
 CONFIGS = {
-    "precision": dict(recipe="precision", metric="ip",
+    "precision": dict(recipe="precision", metric="ip", filter="tc", others=(),
                       workload="Deep-like merge: N=1,000,000 (2 x 500,000), d=96 unit-norm, inner product, "
                                "input PGs M=32 ef=128, k=48, R=32, alpha=1.0, I_max=3"),
-    "fp8": dict(recipe="fp8", metric="l2",
+    "fp8": dict(recipe="fp8", metric="l2", filter="fp8", others=("tc",),
                 workload="Gist-like merge: N=1,000,000 (8 shards sized i*N/36), d=960 non-negative, squared L2, "
                          "input PGs M=32 ef=128, k=64, R=48, alpha=1.0, I_max=3"),
 }
@@ -452,18 +468,27 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
     form's dominant kernel and the merged graph's search recall@10 at beam 64."""
     import torch
     from synth import gen, pgbuild
+    if name == "batched":
+        return measure_batched(fg, dev, peaks, 64, 10_000, 200_000, steps, warmup)
     c = CONFIGS[name]
     t0 = time.perf_counter()
     w = gen.make(c["recipe"])
-    graphs = pgbuild.build_all(w)
-    t_inputs = time.perf_counter() - t0
     X = torch.from_numpy(w.X).to(dev)
+    graphs, pg_ms = gpu_graphs(fg, w, X)
+    t_inputs = time.perf_counter() - t0
     adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
     inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs], metric=c["metric"])
     kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=3)
-    ch = timed_merges(fg, inp, dict(kw, join_filter="tc"), steps, warmup, profile=True)
+    ch = timed_merges(fg, inp, dict(kw, join_filter=c["filter"]), steps, warmup, profile=True)
     stats = ch["out"]["stats"]
     pl = timed_merges(fg, inp, dict(kw, join_filter="fp32", rows="fp32"), 1, 0)
+    others = {}
+    for jf in c["others"]:   # the other reduced-precision forms, same inputs
+        ot = timed_merges(fg, inp, dict(kw, join_filter=jf), 1, 0)
+        ms_o = float(np.mean(ot["step_ms"]))
+        others[jf] = {"value": w.N / (ms_o * 1e-3), "unit": UNIT, "ms_per_step": ms_o, "steps": 1,
+                      "same_graph": bool(torch.equal(ot["out"]["ids"], ch["out"]["ids"]))}
+        del ot
     ms_c, ms_p = float(np.mean(ch["step_ms"])), float(np.mean(pl["step_ms"]))
     Q = torch.from_numpy(np.ascontiguousarray(w.Q[:nq_eval])).to(dev)
     gt = exact_top10(X, Q, w.metric)
@@ -479,13 +504,17 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
                 for k_ in ("k_cross_query", "k_join", "k_prune") if k_ in kernels}
     rec = {"workload": c["workload"], "N": w.N, "d": w.d, "shards": w.shard_sizes, "value": w.N / (ms_c * 1e-3),
            "unit": UNIT, "ms_per_step": ms_c, "steps": steps, "warmup": warmup, "step_ms": ch["step_ms"],
-           "form": "BF16 tensor-core join filter with exact FP32 re-rank, FP32 rows elsewhere",
+           "form": {"tc": "BF16", "fp8": "FP8 E4M3 (per-vector scales)"}[c["filter"]] +
+                   " tensor-core join filter with exact FP32 re-rank, FP32 rows elsewhere",
+           "other_forms": {{"tc": "bf16"}.get(k_, k_): v for k_, v in others.items()},
            "plain_fp32": {"value": w.N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p, "steps": 1,
                           "form": "FP32 rows, FP32 SIMT join filter",
                           "same_graph": bool(torch.equal(pl["out"]["ids"], ch["out"]["ids"]))},
            "recall@10": recall10(sid.cpu().numpy(), gt), "recall_eval": {"queries": nq_eval, "beam": 64},
            "gpu_launches_per_step": ch["launches"] / steps, "roofline": roof, "roofline_by_kernel": roof_all,
            "kernels": kernels, "merge_stats": stats, "inputs_seconds": t_inputs,
+           "inputs": f"vectors drawn on the host; input PGs (M={w.M}, ef={w.ef}) built on the GPU by "
+                     f"fgim_build_pg in {pg_ms:.0f} ms",
            "l2_policy": f"inputs larger than L2 ({w.N * w.d * 4 / 1e9:.2f} GB of vectors)"}
     del inp, X, adj, ch, pl
     torch.cuda.empty_cache()
@@ -502,9 +531,19 @@ def run_fgim(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     import paper_2603_21710_gb300 as fg
+    from synth import gen, pgbuild
     fg.load()
-    w, graphs = make_inputs(args.n)
+    w = gen.make(WORKLOAD["name"], N=args.n, seed=gen.MASTER_SEED)
+    t0 = time.perf_counter()
+    graphs = pgbuild.build_all(w)
+    t_pg_host = time.perf_counter() - t0
     X = torch.from_numpy(w.X).to(dev)
+    # the same input PGs built on the GPU (outside every timed region): equal on these integer data
+    g_gpu, pg_gpu_ms = gpu_graphs(fg, w, X)
+    pg_build = {"gpu_ms": pg_gpu_ms, "host_seconds": t_pg_host, "host_threads": os.cpu_count() or 1,
+                "equal": all(np.array_equal(a[0], b[0]) and a[1] == b[1] for a, b in zip(g_gpu, graphs)),
+                "recipe": f"batch-incremental insertion from the medoid, M={w.M}, ef={w.ef}, {w.h} shards"}
+    del g_gpu
     adj_np = np.concatenate([g[0] for g in graphs])
     adj = torch.from_numpy(adj_np).to(dev)
     entries = [g[1] for g in graphs]
@@ -662,6 +701,7 @@ def run_fgim(args):
             "masked": masked,
             "hnsw": hnsw,
             "oracle_check": ocheck,
+            "input_pg_build": pg_build,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms,
             "ms_median": float(np.median(step_ms))}
     if ws == 1 and args.configs:
@@ -679,51 +719,104 @@ def run_fgim(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
-    """The batched form (many merges of uneven size in one library call) against the plain FP32
-    form of the same merges; inputs resident on the device, CUDA events around each batch."""
+def measure_batched(fg, dev, peaks, n_merges, lo, hi, steps, warmup):
+    """The batched form: n_merges merges of the 768-d BF16 cosine recipe (sizes log-uniform in
+    [lo, hi], h in 2..6) in one fgim_merge_batch call (run as one problem over the union of the
+    merges), against the same batch run merge after merge and against the plain FP32 form (FP32
+    storage of the same values, FP32 SIMT join filter); inputs resident on the device."""
     import torch
-    import paper_2603_21710_gb300 as fg
-    from synth import gen, pgbuild
-    dev = torch.device("cuda", 0)
-    ws_ = gen.batched(n_merges=args.batched, n_lo=args.batched_lo, n_hi=args.batched_hi, nq=10)
-    graphs = [pgbuild.build_all(w) for w in ws_]
-    chosen, plain = [], []
-    for w, g in zip(ws_, graphs):
+    from synth import gen
+    t0 = time.perf_counter()
+    ws_ = gen.batched(n_merges=n_merges, n_lo=lo, n_hi=hi, nq=10)
+    chosen, plain, pg_ms = [], [], 0.0
+    for w in ws_:
+        xb = torch.from_numpy(w.bits().view(np.int16)).to(dev).view(torch.bfloat16)
+        g, ms = gpu_graphs(fg, w, xb)
+        pg_ms += ms
         adj = torch.from_numpy(np.concatenate([x[0] for x in g])).to(dev)
         ent = [x[1] for x in g]
-        xb = torch.from_numpy(w.bits().view(np.int16)).to(dev).view(torch.bfloat16)
         chosen.append(fg.MergeInput.from_flat(xb, w.shard_sizes, adj, ent, metric="cos"))
         plain.append(fg.MergeInput.from_flat(torch.from_numpy(w.X).to(dev), w.shard_sizes, adj, ent, metric="cos"))
+    t_inputs = time.perf_counter() - t0
     w0 = ws_[0]
     kw = dict(k=w0.k, R=w0.R, alpha=w0.alpha, iters=3)
+    stream = torch.cuda.current_stream()
 
-    def timed(inps, **extra):
+    def timed(inps, nsteps, profile=False, **extra):
         out = None
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             out = fg.merge_batch(inps, **kw, **extra)
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        kernels = {}
+        if profile:
+            prof = fg.profiling()
+            prof.__enter__()
         for a, b in ev:
-            a.record()
+            a.record(stream)
             out = fg.merge_batch(inps, **kw, **extra)
-            b.record()
+            b.record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, out
+        if profile:
+            prof.__exit__(None, None, None)
+            for name in prof.names():
+                n, ms = prof.query(name)
+                if n:
+                    kernels[name] = {"launches": n, "ms": ms}
+        return sum(a.elapsed_time(b) for a, b in ev) / nsteps, out, kernels
 
-    ms_c, out_c = timed(chosen)
-    ms_p, out_p = timed(plain, join_filter="fp32")
+    ms_c, out_c, kernels = timed(chosen, steps, profile=True)
+    stats = fg.last_stats()
+    fg._lib.test_set("batch_union", 0)
+    try:
+        ms_s, out_s, _ = timed(chosen, 1)
+    finally:
+        fg._lib.test_set("batch_union", 1)
+    ms_p, out_p, _ = timed(plain, 1, join_filter="fp32")
     N = sum(w.N for w in ws_)
-    line = {"metric": "merged points/sec, batched form (one fgim_merge_batch call)", "value": N / (ms_c * 1e-3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms_c,
-            "higher_is_better": True, "dtype": "bf16 storage, f32 arithmetic", "data": "synthetic",
-            "config": {"workload": f"{args.batched} merges of the 768-d cosine recipe, BF16 storage, sizes "
-                                   f"log-uniform in [{args.batched_lo}, {args.batched_hi}], h in 2..6, "
-                                   "input PGs M=24 ef=96, k=32, R=24, I_max=3",
-                       "sizes": [w.N for w in ws_], "shards": [w.h for w in ws_]},
-            "plain_fp32": {"value": N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p,
-                           "form": "FP32 storage of the same values, FP32 SIMT join filter",
-                           "same_graphs": all(torch.equal(a["ids"], b["ids"]) for a, b in zip(out_c, out_p))}}
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
+    roof = None
+    if dom in ("k_join", "k_prune"):
+        class _W:   # the batch as one workload for the per-kernel work model
+            pass
+        wu = _W()
+        wu.N, wu.d, wu.k, wu.M, wu.R, wu.h = N, w0.d, w0.k, w0.M, w0.R, 2
+        roof = roofline_for(dom, kernels[dom]["ms"] / kernels[dom]["launches"], kernels[dom]["launches"] / steps, wu,
+                            None, None, peaks, stats, 4)
+    rec = {"metric": "merged points/sec, batched form (one fgim_merge_batch call)", "value": N / (ms_c * 1e-3),
+           "unit": UNIT, "ms_per_step": ms_c, "steps": steps, "warmup": max(1, warmup),
+           "dtype": "bf16 storage, f32 arithmetic",
+           "workload": f"{n_merges} merges of the 768-d cosine recipe, BF16 storage, sizes log-uniform in "
+                       f"[{lo}, {hi}], h in 2..6, input PGs M=24 ef=96, k=32, R=24, I_max=3",
+           "N_total": N, "sizes": [w.N for w in ws_], "shards": [w.h for w in ws_],
+           "form": "the batch as one problem over the union of its merges (each stage's kernels once per batch)",
+           "one_by_one": {"value": N / (ms_s * 1e-3), "unit": UNIT, "ms_per_step": ms_s, "steps": 1,
+                          "form": "the same merges one after another in the same call",
+                          "same_graphs": all(torch.equal(a["ids"], b["ids"]) for a, b in zip(out_c, out_s))},
+           "plain_fp32": {"value": N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p, "steps": 1,
+                          "form": "FP32 storage of the same values, FP32 SIMT join filter",
+                          "same_graphs": all(torch.equal(a["ids"], b["ids"]) for a, b in zip(out_c, out_p))},
+           "roofline": roof, "kernels": kernels, "merge_stats": stats, "inputs_seconds": t_inputs,
+           "inputs": f"vectors drawn on the host; input PGs built on the GPU by fgim_build_pg in {pg_ms:.0f} ms",
+           "l2_policy": f"inputs larger than L2 ({N * w0.d * 2 / 1e9:.2f} GB of BF16 vectors)"}
+    del chosen, plain, out_c, out_s, out_p
+    torch.cuda.empty_cache()
+    fg.trim_memory()
+    return rec
+
+
+def run_batched(args):
+    """The batched form on its own line (see measure_batched)."""
+    import torch
+    import paper_2603_21710_gb300 as fg
+    dev = torch.device("cuda", 0)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    rec = measure_batched(fg, dev, peaks, args.batched, args.batched_lo, args.batched_hi, args.steps, args.warmup)
+    line = {k: rec[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype")}
+    line.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+                 "config": {"workload": rec["workload"], "sizes": rec["sizes"], "shards": rec["shards"]}})
+    line.update({k: v for k, v in rec.items() if k not in line})
     print(json.dumps(line), flush=True)
 
 

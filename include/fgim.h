@@ -104,11 +104,12 @@ typedef struct {
     int32_t rev_cap;         /* cap of each reverse list in Visit; 0 = k */
     int32_t ensure_reachable;/* 1 = run the reachability fix after Alg. 5 */
     int32_t reach_beam;      /* pool of the searches of the reachability fix; 0 = 64 */
-    int32_t join_filter;     /* Update's pair filter: 0 = BF16 tensor-core tile (tcgen05), 1 = FP32 SIMT
-                                tile. Both re-rank survivors with the exact FP32 distance, so the lists
-                                are the same; only speed differs. Passes whose shapes the tensor-core
-                                tile does not cover (dim % 16 != 0, |C_n| > 128, |C| > 256) use the
-                                FP32 tile. */
+    int32_t join_filter;     /* fgim_precision of Update's candidate distances: 0 = BF16 tensor-core tile
+                                (tcgen05), 1 = FP32 SIMT tile, 2 = FP8 E4M3 tensor-core tile with one
+                                scale per vector. Every form re-ranks its survivors with the exact FP32
+                                distance, so the lists are the same; only speed differs. Passes whose
+                                shapes a tensor-core tile does not cover (BF16: dim % 16 != 0; FP8:
+                                dim % 32 != 0; both: |C_n| > 128, |C| > 256) use the FP32 tile. */
     int32_t byte_rows;       /* 0 = auto: when every coordinate is an integer in [0, 255] and dim <= 128,
                                 dim % 16 == 0, the searches, the join's re-rank and the prune read one
                                 byte per coordinate and form the distances in exact integer arithmetic
@@ -129,6 +130,13 @@ typedef struct {
  *                         edges shorter than 3 tau are never pruned (decided in FP32:
  *                         t = sqrt(delta(u,v)) - 3 tau, occluded iff t > 0 and delta(w,v) < t * t). */
 typedef enum { FGIM_PRUNE_ALPHA_RNG = 0, FGIM_PRUNE_MRNG = 1, FGIM_PRUNE_TAU_MNG = 2 } fgim_prune_rule;
+
+/* Precision of Update's candidate distances (fgim_params.join_filter). The reduced-precision forms
+ * are filters: a pair is re-ranked with the exact FP32 distance unless a rigorous bound (Cauchy-
+ * Schwarz on the rows' conversion errors plus the FP32 accumulation error of the tile) shows it
+ * cannot enter the list, so the kept ids equal the FP32 form's. FP8: s = amax|x| / 448 per vector,
+ * q = saturating round-to-nearest E4M3 of x / s, the tile forms sum q_a q_b, scaled by s_a s_b. */
+typedef enum { FGIM_PREC_BF16 = 0, FGIM_PREC_FP32 = 1, FGIM_PREC_FP8E4M3 = 2 } fgim_precision;
 
 /* k-NNG buffers, caller-owned device memory: [n, k] each. */
 typedef struct {
@@ -192,12 +200,16 @@ fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* p
 
 /*
  * n_merges independent merges with the same params (the batched form of the measurement
- * plan: many small merges, e.g. one per tenant or time window). Merge m takes the h[m]
- * shard descriptors shards[m] and writes outs[m] (n = sum of its shard sizes, R =
- * params->R); no k-NNG is returned. The merges run one after another on the stream and share
- * the scratch pool, so a batch costs one host call instead of n_merges. Stops at the first
- * failing merge and returns its status; earlier outputs are complete, later ones untouched.
- * fgim_last_stats() sums the counters of the merges run.
+ * plan: many small merges of uneven size, e.g. one per tenant or time window). Merge m takes
+ * the h[m] shard descriptors shards[m] and writes outs[m] (n = sum of its shard sizes, R =
+ * params->R); no k-NNG is returned. The batch runs as one problem over the disjoint union of
+ * the merges' vertices: every stage's kernels run once for all merges (the cross query of a
+ * vertex searches its own merge's other shards with its merge's L; the reachability fix works
+ * from every merge's entry), and each output equals what fgim_merge gives that merge alone.
+ * This needs at most 512 shards in all and no validity masks; otherwise the merges run one
+ * after another on the stream (same results), stopping at the first failing merge (earlier
+ * outputs complete, later ones untouched). Scratch is sized for the whole batch.
+ * fgim_last_stats() holds the counters of the batch.
  */
 fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, int32_t n_merges,
                              const fgim_params* params, fgim_graph* outs, void* stream);
@@ -320,14 +332,18 @@ fgim_status fgim_search_hnsw(const void* base, int64_t n, int32_t dim, int32_t d
                              int32_t entry, const void* queries, int32_t nq, int32_t topk, int32_t beam, int32_t ef_up,
                              int32_t* out_ids, float* out_dist, int32_t* out_start, void* stream);
 
-/* An input PG for one shard on the GPU (the input side of the merge, built like one HNSW layer
- * over all n vertices): each vertex's exact `ef` nearest among the vertices with smaller ids,
- * the RNG heuristic down to M, bidirectional edges, the heuristic again over the union of own
- * and reverse edges. adj [n, M] (local ids, -1 padded) and deg [n]: device, caller-owned.
- * The entry point of such a graph is vertex 0 (the first inserted). M in [1, 64], ef in
- * [1, 128]; the work grows with n^2. Synchronous. */
+/* An input PG for one shard on the GPU (the input side of a merge; the recipe of the synthetic
+ * workloads' input indexes): the medoid (the row nearest, in FP64 squared L2, to the FP64 mean of
+ * the rows, lowest id on ties) first, then the other rows in id order, inserted in batches of
+ * min(max(c / 2, 1), 1024) rows once c are in. Each row of a batch runs Alg. 1 (pool ef, from the
+ * medoid) over the graph as it stood when the batch started and keeps up to M results with
+ * HNSW's heuristic (drop a candidate when a kept one is strictly nearer to it than the row:
+ * FGIM_PRUNE_MRNG without the indegree clause); then each vertex that received edges takes its
+ * list and the new edges in ascending (distance, id), all of them when at most M, else the
+ * heuristic's M. adj [n, M] (local ids, -1 padded) and deg [n]: device, caller-owned; entry_out
+ * (host): the medoid. M in [1, 128], ef in [1, 128]. Synchronous. */
 fgim_status fgim_build_pg(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric, int32_t M,
-                          int32_t ef, int32_t* adj, int32_t* deg, void* stream);
+                          int32_t ef, int32_t* adj, int32_t* deg, int32_t* entry_out, void* stream);
 
 /* Counters of the last merge/search call made by this host thread. */
 void fgim_last_stats(fgim_stats* out);
@@ -349,6 +365,8 @@ void fgim_trim_memory(void);
  *                       take the re-run path; 0 = the default size.
  *   "hop_budget"        > 0: expansions each beam search may take; a search that needs more
  *                       stops and the call returns FGIM_ETIMEOUT; 0 = unbounded (default).
+ *   "batch_union"       0: fgim_merge_batch runs its merges one after another instead of as
+ *                       one problem (same results; for comparing the two); 1 = default.
  *   "fail_alloc_after"  >= 0: the scratch allocation of a call that comes after this many
  *                       successful ones fails as if the device were out of memory (the call
  *                       returns FGIM_ENOMEM); -1 = off (default).
@@ -358,6 +376,24 @@ void fgim_trim_memory(void);
  */
 int32_t fgim_test_set(const char* knob, int64_t value);
 int64_t fgim_test_get(const char* what);
+
+/*
+ * Autotuner of the launch shapes that change no result: the warps per block of the beam-search
+ * kernels (the cross query of stage (a), the evaluation and reachability searches) and the size
+ * of their visited table (a bigger table costs shared memory per warp, and so resident warps,
+ * and saves re-evaluations of forgotten ids). fgim_autotune times every candidate shape (2 or 4
+ * warps per block; the default table size and one step either way) on this merge's cross query
+ * with CUDA events (one warm-up, best of two), keeps the fastest for this workload's key (metric,
+ * bytes per coordinate read, dim, pool L, SM count of the current device) for the rest of the
+ * process, appends it as a JSON line to cache_path (NULL: no file), and returns it (out pointers
+ * optional: warps per block, table bits, milliseconds). Call it when no other call of this
+ * library is running. fgim_autotune_load reads such a file (a later line for a key wins;
+ * FGIM_EINVAL when nothing could be read); fgim_autotune_clear forgets every tuned shape.
+ */
+fgim_status fgim_autotune(const fgim_shard* shards, int32_t h, const fgim_params* params, const char* cache_path,
+                          int32_t* out_wpb, int32_t* out_ht_bits, float* out_ms, void* stream);
+fgim_status fgim_autotune_load(const char* cache_path);
+void fgim_autotune_clear(void);
 
 /* Human-readable name of a status; message of the last CUDA error on this host thread. */
 const char* fgim_strerror(fgim_status s);

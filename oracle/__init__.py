@@ -86,6 +86,7 @@ def lib():
                 "or_merge": (i32, [vp, i32, i32, i32, i32, i32, f32, i32, vp, vp, vp, vp, vp, vp, vp]),
                 "or_search": (None, [vp, i64, i32, i32, vp, i32, i32, vp, i64, i32, i32, i32, vp, vp, vp]),
                 "or_hnsw_insert": (None, [vp, i64, i32, i32, vp, i32, i32, i32, vp, vp, vp]),
+                "or_reach_fix_seq": (None, [vp, i32, i32, i32, vp, i32, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -287,6 +288,16 @@ def reach_fix(P: Problem, o_ids, o_dist, o_deg, entry, beam: int = 64):
     st = Stats()
     lib().or_reach_fix(P.ref, R, entry, beam, o_ids.ctypes.data, o_dist.ctypes.data, o_deg.ctypes.data,
                        ctypes.byref(st))
+    return st.as_dict()
+
+
+def reach_fix_seq(P: Problem, o_ids, o_dist, o_deg, entry, beam: int = 64, knn_ids=None):
+    """The plain sequential reachability fix, in place (the quality reference for reach_fix)."""
+    R = o_ids.shape[1]
+    kn = None if knn_ids is None else np.ascontiguousarray(knn_ids, dtype=np.int32)
+    st = Stats()
+    lib().or_reach_fix_seq(P.ref, R, entry, beam, _p(kn), 0 if kn is None else kn.shape[1], o_ids.ctypes.data,
+                           o_dist.ctypes.data, o_deg.ctypes.data, ctypes.byref(st))
     return st.as_dict()
 
 

@@ -996,6 +996,80 @@ void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
 }
 
 /* ------------------------------------------------------------------------- */
+/* The reachability fix as the plain sequential rule first proposed for it: the */
+/* quality reference for the round-based form above (which the kernels follow). */
+/* ------------------------------------------------------------------------- */
+/* BFS from the entry; then for each vertex x in ascending id that is still unreached: the
+ * candidates p are the reached vertices of x's k-NNG list (ascending (delta, id); none when
+ * knn_ids is NULL), then the reached results of Alg. 1 for x over the current graph from the
+ * entry (pool beam). The first p with fewer than R neighbours takes x at the end of its list;
+ * else the first p having a neighbour of indegree > 1 has its farthest such neighbour (by
+ * descending (delta, id)) replaced by x. p's list is re-sorted by (delta, id) and every vertex
+ * reachable from x is marked reached. Sequential. */
+void or_reach_fix_seq(const or_input* in, int32_t R, int32_t entry_g, int32_t beam, const int32_t* knn_ids,
+                      int32_t k, int32_t* out_ids, float* out_dist, int32_t* out_deg, or_stats* st) {
+    const int64_t N = in->off[in->h];
+    uint8_t* reached = (uint8_t*)calloc(N, 1);
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* indeg = (int32_t*)calloc(N, sizeof(int32_t));
+    uint32_t* seen = (uint32_t*)calloc(N, sizeof(uint32_t));
+    int32_t* cid = (int32_t*)malloc(sizeof(int32_t) * (beam + k + 1));
+    float* cdist = (float*)malloc(sizeof(float) * (beam + 1));
+    uint32_t tag = 0;
+    int64_t attached = 0;
+    for (int64_t u = 0; u < N; ++u)
+        for (int32_t t = 0; t < out_deg[u]; ++t) indeg[out_ids[u * R + t]]++;
+    bfs_mark(N, R, out_ids, entry_g, reached, queue);
+    for (int64_t x = 0; x < N; ++x) {
+        if (reached[x]) continue;
+        /* candidates: reached k-NNG neighbours, then reached search results */
+        int32_t nc = 0;
+        if (knn_ids)
+            for (int32_t t = 0; t < k; ++t) {
+                int32_t v = knn_ids[x * k + t];
+                if (v >= 0 && reached[v]) cid[nc++] = v;
+            }
+        int32_t ns = knn_search_tagged(in->X, in->d, in->metric, out_ids, R, entry_g, row(in, x), beam, beam, seen,
+                                       ++tag, cid + nc, cdist, NULL);
+        int32_t w = nc;
+        for (int32_t t = 0; t < ns; ++t)
+            if (reached[cid[nc + t]]) cid[w++] = cid[nc + t];
+        nc = w;
+        int32_t p = -1, pos = -1;
+        for (int32_t t = 0; t < nc && p < 0; ++t)
+            if (out_deg[cid[t]] < R) { p = cid[t]; pos = out_deg[p]; }
+        for (int32_t t = 0; t < nc && p < 0; ++t) {
+            int32_t q = cid[t];
+            for (int32_t s = out_deg[q] - 1; s >= 0; --s)
+                if (indeg[out_ids[(int64_t)q * R + s]] > 1) { p = q; pos = s; break; }
+        }
+        if (p < 0) continue;
+        int32_t* li = out_ids + (int64_t)p * R;
+        float* ld = out_dist + (int64_t)p * R;
+        float d = dist_g(in, p, x);
+        if (pos == out_deg[p]) out_deg[p] += 1;
+        else indeg[li[pos]]--;
+        indeg[x]++;
+        while (pos > 0 && key_lt(d, (int32_t)x, ld[pos - 1], li[pos - 1])) {
+            li[pos] = li[pos - 1]; ld[pos] = ld[pos - 1]; --pos;
+        }
+        while (pos + 1 < out_deg[p] && key_lt(ld[pos + 1], li[pos + 1], d, (int32_t)x)) {
+            li[pos] = li[pos + 1]; ld[pos] = ld[pos + 1]; ++pos;
+        }
+        li[pos] = (int32_t)x;
+        ld[pos] = d;
+        ++attached;
+        bfs_mark(N, R, out_ids, (int32_t)x, reached, queue);
+    }
+    if (st) {
+        st->attached += attached;
+        memset(reached, 0, N);
+        st->unreached += N - bfs_mark(N, R, out_ids, entry_g, reached, queue);
+    }
+    free(reached); free(queue); free(indeg); free(seen); free(cid); free(cdist);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Alg. 3 as printed: the streamlined (one pass per vertex) refinement in DFS   */
 /* order, reverse graphs kept across iterations, lists updated at once (the     */
 /* quality comparison for the synchronous form above). Sequential.              */

@@ -109,6 +109,13 @@ void or_reverse_insert(int64_t N, int32_t R, const int32_t* e_ids, const float* 
 void or_reach_fix(const or_input* in, int32_t R, int32_t entry_g, int32_t beam,
                   int32_t* out_ids, float* out_dist, int32_t* out_deg, or_stats* st);
 
+/* The reachability fix as the plain sequential rule (the quality reference for or_reach_fix): each
+ * unreached vertex in ascending id is attached to the first reached vertex of its k-NNG list
+ * (knn_ids [N, k] or NULL), else of its search results, that has room, else that has a neighbour
+ * of indegree > 1 (the farthest such one is replaced); see fgim_oracle.c. */
+void or_reach_fix_seq(const or_input* in, int32_t R, int32_t entry_g, int32_t beam, const int32_t* knn_ids,
+                      int32_t k, int32_t* out_ids, float* out_dist, int32_t* out_deg, or_stats* st);
+
 /* Global id of the merged entry point: phi(entry of the largest shard, lowest shard index on ties). */
 int32_t or_merged_entry(const or_input* in);
 /* Alg. 3 as printed (DFS order, Visit and Update in one pass per vertex, lists updated at once,

@@ -25,8 +25,9 @@ __all__ = ["MergeInput", "merge", "merge_batch", "merge_host", "hnsw_levels", "h
 
 FLAG_NEW = 1
 FLAG_REPLACED = 2
-# Update's pair filter: BF16 tensor-core tile or FP32 SIMT tile (same results)
-JOIN_FILTERS = {"tc": 0, "bf16": 0, "fp32": 1, "simt": 1, 0: 0, 1: 1}
+# Update's candidate-distance precision: BF16 tensor-core tile, FP32 SIMT tile or FP8 E4M3
+# tensor-core tile with per-vector scales (same results: survivors are re-ranked exactly)
+JOIN_FILTERS = {"tc": 0, "bf16": 0, "fp32": 1, "simt": 1, "fp8": 2, "e4m3": 2, 0: 0, 1: 1, 2: 2}
 # row storage: "auto" reads one byte per coordinate when the data allow it (integers in
 # [0, 255], d <= 128, d % 16 == 0; distances are then exact integers, equal to the FP32
 # ones), "fp32" always reads the FP32 rows
@@ -367,17 +368,17 @@ def hnsw_layer(X: torch.Tensor, levels: torch.Tensor, level: int, n_layer: int, 
 
 
 def build_pg(X: torch.Tensor, M: int, ef: int = 64, metric="l2"):
-    """An input PG for one shard on the GPU: (adj [n, M] int32 local ids, -1 padded; entry 0).
-    Each vertex links to the RNG-pruned exact ef nearest of the vertices before it, plus the
-    reverse edges (the work grows with n^2)."""
+    """An input PG for one shard on the GPU by batch-incremental insertion from the medoid (see
+    fgim_build_pg): (adj [n, M] int32 local ids, -1 padded; entry = the medoid)."""
     L_ = load()
     X = _vec(X, "X")
     n = int(X.shape[0])
     adj = torch.empty((n, M), dtype=torch.int32, device=X.device)
     deg = torch.empty((n,), dtype=torch.int32, device=X.device)
+    entry = ctypes.c_int32(0)
     check(L_.fgim_build_pg(_p(X), n, int(X.shape[1]), _VEC_DTYPES[X.dtype], _lib.METRICS[metric], int(M), int(ef),
-                           _p(adj), _p(deg), _stream()))
-    return adj, 0
+                           _p(adj), _p(deg), ctypes.byref(entry), _stream()))
+    return adj, int(entry.value)
 
 
 def build_layers(X: torch.Tensor, M: int, ef: int = 64, seed: int = 0, metric="l2") -> dict:
@@ -416,6 +417,25 @@ def search_hnsw(X: torch.Tensor, graph_ids: torch.Tensor, layers: Sequence[dict]
                               _p(G), int(G.shape[1]), arr, len(layers), int(entry), _p(Q), nq, topk, beam,
                               int(ef_up), _p(ids), _p(dist), _p(start), _stream()))
     return ids, dist, start
+
+
+def autotune(inp: MergeInput, k: int, L: int = 0, cache_path: Optional[str] = None, rows="auto") -> dict:
+    """Time the beam-search launch shapes on this merge's cross query and keep the fastest for
+    its workload (see fgim_autotune): {"wpb", "ht_bits", "ms"}."""
+    L_ = load()
+    p = inp.params(k=k, L=L, rows=rows)
+    wpb, hb, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_float(0.0)
+    check(L_.fgim_autotune(inp._shards, inp.h, ctypes.byref(p), cache_path.encode() if cache_path else None,
+                           ctypes.byref(wpb), ctypes.byref(hb), ctypes.byref(ms), _stream()))
+    return {"wpb": int(wpb.value), "ht_bits": int(hb.value), "ms": float(ms.value)}
+
+
+def autotune_load(cache_path: str) -> None:
+    check(load().fgim_autotune_load(cache_path.encode()))
+
+
+def autotune_clear() -> None:
+    load().fgim_autotune_clear()
 
 
 def launch_count() -> int:

@@ -101,7 +101,7 @@ EXPORTS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fgim_build_pg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_void_p]),
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "fgim_search_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -109,6 +109,10 @@ EXPORTS = {
     "fgim_last_stats": (None, [ctypes.c_void_p]),
     "fgim_graph_alloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
     "fgim_graph_free": (None, [ctypes.c_void_p]),
+    "fgim_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_char_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fgim_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "fgim_autotune_clear": (None, []),
     "fgim_test_set": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_int64]),
     "fgim_test_get": (ctypes.c_int64, [ctypes.c_char_p]),
     "fgim_strerror": (ctypes.c_char_p, [ctypes.c_int]),

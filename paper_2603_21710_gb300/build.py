@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfgim.so")
-SOURCES = ["k_cross.cu", "k_cross_phi.cu", "k_search.cu", "k_hnsw.cu", "k_util.cu", "k_refine.cu", "k_prune.cu", "fgim_abi.cu", "fgim_noalloc.cu"]
+SOURCES = ["k_cross.cu", "k_cross_phi.cu", "k_search.cu", "k_hnsw.cu", "k_util.cu", "k_refine.cu", "k_prune.cu", "fgim_abi.cu", "fgim_noalloc.cu", "k_pgbuild.cu"]
 HEADERS = ["fgim_internal.cuh", "fgim_launch.h", "tc_sm100.cuh", "k_beam.cuh", "k_cross.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

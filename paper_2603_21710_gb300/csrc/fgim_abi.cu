@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "fgim_launch.h"
+#include "k_beam.cuh"   // launch-shape helpers of the beam-search kernels (the autotuner)
 
 namespace fgim {
 
@@ -67,6 +68,33 @@ static void resolve_events() {
     t_pending.clear();
 }
 
+// ---------------------------------------------------------------------------- autotuned launch shapes
+struct BeamShape {
+    int wpb;
+    int htbits;
+};
+static std::mutex g_tune_mu;
+static std::map<unsigned long long, BeamShape> g_tuned;
+
+unsigned long long beam_shape_key(int metric, int row_bytes, int dim, int L) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 0;
+    }
+    return ((unsigned long long)(sms & 0x3ff) << 40) | ((unsigned long long)(metric & 3) << 36) |
+           ((unsigned long long)(row_bytes & 7) << 32) | ((unsigned long long)(dim & 0xffff) << 16) |
+           (unsigned long long)(L & 0xffff);
+}
+
+void tuned_beam_shape(unsigned long long key, int* wpb, int* htbits) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it == g_tuned.end()) return;
+    *wpb = it->second.wpb;
+    *htbits = it->second.htbits;
+}
+
 // ---------------------------------------------------------------------------- scratch
 // The library's scratch comes from its own stream-ordered pool per device, which keeps the
 // memory it has mapped between calls (a merge needs several GB; mapping them again on every
@@ -78,6 +106,7 @@ static std::map<int, cudaMemPool_t> g_pools;
 static std::atomic<long long> g_test_prop_cap{0};
 static std::atomic<int> g_test_hop_budget{0};
 static std::atomic<long long> g_test_fail_after{-1};
+static std::atomic<int> g_test_batch_union{1};
 static thread_local long long t_allocs = 0;   // scratch allocations of the current call
 
 static cudaMemPool_t lib_pool() {
@@ -249,7 +278,8 @@ static void check_params(const fgim_params* p, bool need_merge) {
     need(p->iters >= 0 && p->iters <= 1000, FGIM_EINVAL, "iters must be in [0, 1000]");
     need(p->rev_cap >= 0 && p->rev_cap <= FGIM_MAX_K, FGIM_EINVAL, "rev_cap must be 0 or in [1, 128]");
     need(p->reach_beam >= 0 && p->reach_beam <= FGIM_MAX_L, FGIM_EINVAL, "reach_beam must be 0 or in [1, 128]");
-    need(p->join_filter == 0 || p->join_filter == 1, FGIM_EINVAL, "join_filter must be 0 (tensor core) or 1 (FP32)");
+    need(p->join_filter >= FGIM_PREC_BF16 && p->join_filter <= FGIM_PREC_FP8E4M3, FGIM_EINVAL,
+         "join_filter must be 0 (BF16 tensor core), 1 (FP32) or 2 (FP8 E4M3 tensor core)");
     need(p->byte_rows == 0 || p->byte_rows == 1, FGIM_EINVAL, "byte_rows must be 0 (auto) or 1 (off)");
     need(p->prune_rule >= FGIM_PRUNE_ALPHA_RNG && p->prune_rule <= FGIM_PRUNE_TAU_MNG, FGIM_EINVAL,
          "prune_rule must be 0 (alpha-RNG), 1 (MRNG) or 2 (tau-MNG)");
@@ -272,7 +302,8 @@ static void check_shards(const fgim_shard* sh, int h, const fgim_params* p) {
     need(n < 0x7fffffffLL, FGIM_EINVAL, "total size must fit a 31-bit id");
 }
 
-static ShardTable make_table(const fgim_shard* sh, int h, int dim) {
+// the shards of one merge, all in one group searched with pool L
+static ShardTable make_table(const fgim_shard* sh, int h, int dim, int L) {
     ShardTable t;
     std::memset(&t, 0, sizeof(t));
     t.h = h;
@@ -283,6 +314,9 @@ static ShardTable make_table(const fgim_shard* sh, int h, int dim) {
         t.adj[i] = sh[i].adj;
         t.M[i] = sh[i].max_degree;
         t.entry[i] = sh[i].entry;
+        t.grp[i] = 0;
+        t.gend[i] = h;
+        t.gL[i] = L;
         o += sh[i].n;
     }
     t.off[h] = o;
@@ -370,7 +404,7 @@ static Problem make_problem(Ctx& c, const fgim_shard* sh, int h, const fgim_para
     P.N = total_n(sh, h);
     P.d = p->dim;
     P.metric = p->metric;
-    P.t = make_table(sh, h, p->dim);
+    P.t = make_table(sh, h, p->dim, resolve_L(p, h));
     P.X = contiguous_vectors(c, sh, h, p->dim, p->dtype, P.N);
     P.Xh = p->dtype == FGIM_BF16 ? contiguous_bf16(c, sh, h, p->dim, P.N) : nullptr;
     finish_problem(c, P, p);
@@ -521,10 +555,18 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.join_filter = p->join_filter;
     b.X8 = P.X8;
     b.Xb = nullptr;
-    if (p->join_filter == 0 && P.d % 16 == 0) {
+    b.fp8 = false;
+    if (p->join_filter == FGIM_PREC_BF16 && P.d % 16 == 0) {
         b.Xb = c.alloc<__nv_bfloat16>(N * P.d);
         b.tcm = c.alloc<float4>(N);
         ck(launch_prep_bf16(P.X, N, P.d, reinterpret_cast<__nv_bfloat16*>(b.Xb), b.tcm, c.s));
+    } else if (p->join_filter == FGIM_PREC_FP8E4M3 && P.d % 32 == 0) {
+        // E4M3 rows (one byte per coordinate) with one scale per vector, addressed like BF16 pairs
+        uint8_t* Xq = c.alloc<uint8_t>(N * P.d);
+        b.tcm = c.alloc<float4>(N);
+        ck(launch_prep_fp8(P.X, N, P.d, Xq, b.tcm, c.s));
+        b.Xb = reinterpret_cast<__nv_bfloat16*>(Xq);
+        b.fp8 = true;
     }
 
     ck(refine_visit(*g, rev_cap, b, c.s));
@@ -611,10 +653,20 @@ static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, con
     ck(launch_reverse_insert(N, R, e_ids, e_dist, e_cnt, b, out->ids, out->dist, out->deg, c.s));
 }
 
-// BFS from the entry; returns the number of reached vertices
-static long long bfs(Ctx& c, const fgim_graph* g, int32_t* visited, int32_t* fa, int32_t* fb, int32_t* counts) {
+// The entry points the reachability fix works from: one merge (the graph's entry), or the merges
+// of a batch run as one problem (entries[m] on the device, merge m owning ids off[m] .. off[m+1]-1).
+struct Entries {
+    const int32_t* ent = nullptr;    // device [nm], nullptr = the graph's entry
+    const long long* off = nullptr;  // device [nm + 1]
+    int nm = 1;
+};
+
+// BFS from the entry (or entries); returns the number of reached vertices
+static long long bfs(Ctx& c, const fgim_graph* g, const Entries& E, int32_t* visited, int32_t* fa, int32_t* fb,
+                     int32_t* counts) {
     const long long N = g->n;
-    ck(launch_bfs_init(visited, N, fa, counts, g->entry, c.s));
+    if (E.ent) ck(launch_bfs_init_multi(visited, N, fa, counts, E.ent, E.nm, c.status, c.s));
+    else ck(launch_bfs_init(visited, N, fa, counts, g->entry, c.s));
     constexpr int kBatch = 8;   // levels between host reads of the frontier size
     for (int level = 1; level <= N; level += kBatch) {
         ck(launch_bfs_levels(g->ids, g->R, N, visited, fa, fb, counts, level, kBatch, c.s));
@@ -624,7 +676,8 @@ static long long bfs(Ctx& c, const fgim_graph* g, int32_t* visited, int32_t* fa,
     return c.read_ll(reinterpret_cast<const long long*>(counts + 4));
 }
 
-static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph* g, fgim_stats* st) {
+static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph* g, fgim_stats* st,
+                      const Entries& E = Entries()) {
     const long long N = g->n;
     const int R = g->R;
     const int beam = p->reach_beam > 0 ? p->reach_beam : 64;
@@ -645,10 +698,11 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
     int4* plan = c.alloc<int4>(kReachWindow);    // the actions planned in a round
     int32_t* cand = nullptr;
     float* cdist = nullptr;
+    int32_t* starts = nullptr;
     long long cand_cap = 0;
     long long reached = 0;
     for (int round = 0; round < 16; ++round) {
-        reached = bfs(c, g, visited, fa, fb, counts);
+        reached = bfs(c, g, E, visited, fa, fb, counts);
         if (reached >= N) break;
         ck(launch_cc_init(visited, N, label, c.s));
         for (long long it = 0; it <= N; ++it) {
@@ -663,10 +717,13 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
         if (nr > cand_cap) {
             cand = c.alloc<int32_t>(nr * beam);
             cdist = c.alloc<float>(nr * beam);
+            if (E.ent) starts = c.alloc<int32_t>(nr);
             cand_cap = nr;
         }
+        // each representative searches from its merge's entry
+        if (E.ent) ck(launch_rep_starts(reps, nr, E.off, E.ent, E.nm, starts, c.s));
         ck(launch_search(P.X, P.X8, P.inv, N, P.d, P.metric, g->ids, R, g->entry, nullptr, nullptr, reps, nr, beam, beam,
-                         cand, cdist, c.ctr + 0, c.status, c.s, P.Xh));
+                         cand, cdist, c.ctr + 0, c.status, c.s, P.Xh, E.ent ? starts : nullptr));
         ck(launch_bfs_parents(g->ids, R, N, visited, npar, c.s));
         // rounds run in batches between host reads of the progress; ff[0] = 0 starts round 1
         ck(cudaMemsetAsync(owner, 0xff, sizeof(unsigned long long) * N, c.s));
@@ -684,7 +741,7 @@ static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph
             start = next;
         }
     }
-    reached = bfs(c, g, visited, fa, fb, counts);
+    reached = bfs(c, g, E, visited, fa, fb, counts);
     if (st) st->unreached = N - reached;
 }
 
@@ -896,6 +953,123 @@ fgim_status fgim_merge(const fgim_shard* shards, int32_t h, const fgim_params* p
     return r;
 }
 
+// A batch of independent merges as ONE problem over the disjoint union of their vertices: the
+// shards of every merge get consecutive global ids (merge after merge), the shard table groups
+// each merge's shards (the cross query of a vertex searches only its own merge's other shards,
+// with its merge's L), and each stage's kernels run once for the whole batch instead of once
+// per merge. The outputs are those of the merges run one by one: no list ever holds an id of
+// another merge (stage a draws candidates from the vertex's own merge, Update pairs candidates of
+// one list, prune and reverse edges stay inside lists), and the sequential loops that are run in
+// rounds (indegree repair, reachability fix) commit exactly the sequential result, whose steps
+// for one merge never read another merge's vertices; the reachability fix starts its BFS from
+// every merge's entry and each representative's search from its own merge's entry.
+static bool union_batch_ok(const fgim_shard* const* shards, const int32_t* h, int n) {
+    long long shard_count = 0, N = 0;
+    for (int m = 0; m < n; ++m) {
+        if (has_valid(shards[m], h[m])) return false;
+        shard_count += h[m];
+        N += total_n(shards[m], h[m]);
+    }
+    return n > 1 && shard_count <= kMaxTableShards && N < 0x7fffffffLL;
+}
+
+static void merge_union(Ctx& c, const fgim_shard* const* shards, const int32_t* h, int nm, const fgim_params* p,
+                        fgim_graph* outs) {
+    const int d = p->dim, k = p->k, R = p->R;
+    std::vector<long long> moff(nm + 1, 0);
+    Problem P;
+    std::memset(&P.t, 0, sizeof(P.t));
+    P.t.dim = d;
+    int H = 0, Lmax = 1;
+    long long o = 0;
+    for (int m = 0; m < nm; ++m) {
+        const int L = resolve_L(p, h[m]);
+        need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
+        Lmax = std::max(Lmax, L);
+        const int first = H;
+        for (int i = 0; i < h[m]; ++i, ++H) {
+            const fgim_shard& sh = shards[m][i];
+            P.t.off[H] = o;
+            P.t.adj[H] = sh.adj;
+            P.t.M[H] = sh.max_degree;
+            P.t.entry[H] = sh.entry;
+            P.t.grp[H] = first;
+            P.t.gend[H] = first + h[m];
+            P.t.gL[H] = L;
+            o += sh.n;
+        }
+        moff[m + 1] = o;
+    }
+    P.t.h = H;
+    P.t.off[H] = o;
+    const long long N = o;
+    P.N = N;
+    P.d = d;
+    P.metric = p->metric;
+    // the vectors of every shard in one buffer (FP32 working copy; BF16 rows kept beside it)
+    float* X = c.alloc<float>(N * d);
+    uint16_t* Xh = p->dtype == FGIM_BF16 ? c.alloc<uint16_t>(N * d) : nullptr;
+    for (int m = 0, q = 0; m < nm; ++m)
+        for (int i = 0; i < h[m]; ++i, ++q) {
+            const fgim_shard& sh = shards[m][i];
+            const long long at = P.t.off[q] * d, cnt = (long long)sh.n * d;
+            if (Xh) {
+                ck(launch_bf16_to_f32(static_cast<const uint16_t*>(sh.vectors), cnt, X + at, c.s));
+                ck(cudaMemcpyAsync(Xh + at, sh.vectors, (size_t)cnt * 2, cudaMemcpyDeviceToDevice, c.s));
+            } else {
+                ck(cudaMemcpyAsync(X + at, sh.vectors, (size_t)cnt * 4, cudaMemcpyDeviceToDevice, c.s));
+            }
+        }
+    P.X = X;
+    P.Xh = Xh;
+    finish_problem(c, P, p);
+    fgim_knng g;
+    g.ids = c.alloc<int32_t>(N * k);
+    g.dist = c.alloc<float>(N * k);
+    g.flags = c.alloc<uint8_t>(N * k);
+    g.n = N;
+    g.k = k;
+    ck(launch_cross_query(P.t, P.X, P.X8, P.inv, N, P.metric, k, Lmax, &g, c.ctr + 0, c.status, c.s, nullptr, nullptr,
+                          N, P.Xh));
+    int32_t* T = c.alloc<int32_t>(N);
+    for (int it = 0; it < p->iters; ++it) {
+        refine_pass(c, P, p, &g, &t_stats);
+        repair(c, P, &g, T, &t_stats);
+    }
+    if (p->iters == 0) ck(launch_indegree(g.ids, N, k, T, false, nullptr, c.s));
+    int32_t* e_ids = c.alloc<int32_t>(N * R);
+    float* e_dist = c.alloc<float>(N * R);
+    int32_t* e_cnt = c.alloc<int32_t>(N);
+    prune(c, P, p, &g, T, e_ids, e_dist, e_cnt);
+    fgim_graph U;
+    U.ids = c.alloc<int32_t>(N * R);
+    U.dist = c.alloc<float>(N * R);
+    U.deg = c.alloc<int32_t>(N);
+    U.n = N;
+    U.R = R;
+    reverse_insert(c, N, R, e_ids, e_dist, e_cnt, &U);
+    std::vector<int32_t> ent(nm);
+    for (int m = 0; m < nm; ++m) ent[m] = (int32_t)(moff[m] + merged_entry(shards[m], h[m]));
+    U.entry = ent[0];
+    if (p->ensure_reachable) {
+        Entries E;
+        int32_t* ent_d = c.alloc<int32_t>(nm);
+        long long* off_d = c.alloc<long long>(nm + 1);
+        ck(cudaMemcpyAsync(ent_d, ent.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, c.s));
+        ck(cudaMemcpyAsync(off_d, moff.data(), sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, c.s));
+        E.ent = ent_d;
+        E.off = off_d;
+        E.nm = nm;
+        reach_fix(c, P, p, &U, &t_stats, E);
+    }
+    for (int m = 0; m < nm; ++m) {
+        ck(launch_split_rows(U.ids + moff[m] * R, U.dist + moff[m] * R, U.deg + moff[m], moff[m + 1] - moff[m], R,
+                             (int32_t)moff[m], outs[m].ids, outs[m].dist, outs[m].deg, c.s));
+        outs[m].entry = ent[m] - (int32_t)moff[m];
+    }
+    c.finish(&t_stats);
+}
+
 fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, int32_t n_merges,
                              const fgim_params* params, fgim_graph* outs, void* stream) {
     begin_call();
@@ -908,6 +1082,11 @@ fgim_status fgim_merge_batch(const fgim_shard* const* shards, const int32_t* h, 
             need(outs[m].ids && outs[m].dist && outs[m].deg, FGIM_EINVAL, "graph buffers are NULL");
             need((has_valid(shards[m], h[m]) || outs[m].n == total_n(shards[m], h[m])) && outs[m].R == params->R,
                  FGIM_EINVAL, "graph shape mismatch");
+        }
+        if (g_test_batch_union.load(std::memory_order_relaxed) && union_batch_ok(shards, h, n_merges)) {
+            Ctx c((cudaStream_t)stream);
+            merge_union(c, shards, h, n_merges, params, outs);
+            return;
         }
         for (int m = 0; m < n_merges; ++m) {
             Ctx c((cudaStream_t)stream);
@@ -1109,29 +1288,111 @@ fgim_status fgim_hnsw_layer(const void* vectors, int64_t n, int32_t dim, int32_t
     return r;
 }
 fgim_status fgim_build_pg(const void* vectors, int64_t n, int32_t dim, int32_t dtype, int32_t metric, int32_t M,
-                          int32_t ef, int32_t* adj, int32_t* deg, void* stream) {
+                          int32_t ef, int32_t* adj, int32_t* deg, int32_t* entry_out, void* stream) {
     begin_call();
     fgim_status r = guarded([&] {
-        need(vectors && adj && deg, FGIM_EINVAL, "NULL buffer");
+        need(vectors && adj && deg && entry_out, FGIM_EINVAL, "NULL buffer");
         need(n >= 1 && n < 0x7fffffffLL, FGIM_EINVAL, "bad n");
         need(dim >= 4 && dim <= FGIM_MAX_DIM && dim % 4 == 0, FGIM_EINVAL, "dim must be a multiple of 4 in [4, 2048]");
         need(dtype == FGIM_F32 || dtype == FGIM_BF16, FGIM_EINVAL, "dtype must be FGIM_F32 or FGIM_BF16");
         need(metric == FGIM_L2SQ || metric == FGIM_IP || metric == FGIM_COSINE, FGIM_EINVAL, "unknown metric");
-        need(M >= 1 && M <= 64, FGIM_EINVAL, "M must be in [1, 64]");
-        need(ef >= 1 && ef <= FGIM_MAX_K, FGIM_EINVAL, "ef must be in [1, 128]");
+        need(M >= 1 && M <= FGIM_MAX_DEGREE, FGIM_EINVAL, "M must be in [1, 128]");
+        need(ef >= 1 && ef <= FGIM_MAX_L, FGIM_EINVAL, "ef must be in [1, 128]");
         need(((uintptr_t)vectors & (dtype == FGIM_F32 ? 15u : 1u)) == 0, FGIM_EINVAL, "vectors misaligned");
         Ctx c((cudaStream_t)stream);
-        // every vertex is a member: ids 0 .. n - 1
-        int32_t* flag = c.alloc<int32_t>(n);
+        Problem P;
+        std::memset(&P.t, 0, sizeof(P.t));
+        P.N = n;
+        P.d = dim;
+        P.metric = metric;
+        P.X = f32_rows(c, vectors, n, dim, dtype);
+        P.Xh = dtype == FGIM_BF16 ? static_cast<const uint16_t*>(vectors) : nullptr;
+        fgim_params lp;
+        std::memset(&lp, 0, sizeof(lp));
+        lp.metric = metric;
+        finish_problem(c, P, &lp);   // byte rows when the data allow, cosine norms
+        // the medoid and the insertion order
+        double* mean = c.alloc<double>(dim);
+        unsigned long long* dbits = c.alloc<unsigned long long>(n);
+        unsigned long long* best = c.alloc<unsigned long long>(1);
+        int* medoid_d = c.alloc<int>(1);
+        ck(launch_pg_medoid(P.X, n, dim, mean, dbits, best, medoid_d, c.s));
+        int32_t* order = c.alloc<int32_t>(n);
+        float* nd = c.alloc<float>(n * M);
+        int32_t* zeros = c.alloc<int32_t>(n);
+        ck(launch_pg_init(n, M, medoid_d, order, adj, nd, deg, zeros, c.s));
+        const int medoid = c.read_i32(medoid_d);
+        need(medoid >= 0 && medoid < n, FGIM_EINTERNAL, "medoid out of range");
+        // per-batch scratch
+        const long long bmax = std::min<long long>(1024, n);
+        const int W = M + (int)bmax;   // a target's list and the batch's reverse edges to it
+        int32_t* res_ids = c.alloc<int32_t>(bmax * ef);
+        float* res_d = c.alloc<float>(bmax * ef);
+        int32_t* e_ids = c.alloc<int32_t>(bmax * M);
+        float* e_dist = c.alloc<float>(bmax * M);
+        int32_t* e_cnt = c.alloc<int32_t>(bmax);
+        int32_t* cin = c.alloc<int32_t>(n);
+        int32_t* fill = c.alloc<int32_t>(n);
         long long* off = c.alloc<long long>(n + 1);
+        uint64_t* rev = c.alloc<uint64_t>(bmax * M);
+        int32_t* flag = c.alloc<int32_t>(n);
+        int32_t* targets = c.alloc<int32_t>(n);
+        long long* toff = c.alloc<long long>(n + 1);
         const size_t sb = scan_scratch_bytes(n);
-        void* tmp = c.alloc<unsigned char>((long long)sb);
-        int32_t* all = c.alloc<int32_t>(n);
-        ck(launch_valid_flags(nullptr, n, flag, c.s));
-        ck(compact_flags(flag, n, all, off, tmp, sb, c.s));
-        const float* X = f32_rows(c, vectors, n, dim, dtype);
-        build_layer_graph(c, X, dim, metric, all, n, M, ef, adj, deg);
+        unsigned char* tmp = c.alloc<unsigned char>((long long)sb);
+        const long long tmax = std::min<long long>(n, bmax * M);
+        int32_t* ov_ids = c.alloc<int32_t>(tmax * W);
+        float* ov_dist = c.alloc<float>(tmax * W);
+        int32_t* ov_tgt = c.alloc<int32_t>(tmax);
+        int* n_ov = c.alloc<int>(1);
+        int32_t* o_ids = c.alloc<int32_t>(tmax * M);
+        float* o_dist = c.alloc<float>(tmax * M);
+        int32_t* o_cnt = c.alloc<int32_t>(tmax);
+        PruneRule heur;   // HNSW's heuristic: MRNG's rule, no indegree clause (T = 0 everywhere)
+        heur.kind = FGIM_PRUNE_MRNG;
+        heur.alpha2 = 1.f;
+        heur.tau3 = 0.f;
+        for (long long done = 1; done < n;) {
+            const long long b = std::min(std::min(std::max(done / 2, 1LL), bmax), n - done);
+            // 1. every row of the batch searches the graph as it stands (Alg. 1 from the medoid)
+            ck(launch_search(P.X, P.X8, P.inv, n, dim, metric, adj, M, medoid, nullptr, nullptr, order + done, b, ef,
+                             ef, res_ids, res_d, c.ctr + 0, c.status, c.s, P.Xh));
+            fgim_knng g1;
+            std::memset(&g1, 0, sizeof(g1));
+            g1.ids = res_ids;
+            g1.dist = res_d;
+            g1.n = b;
+            g1.k = ef;
+            ck(launch_prune(P.X, P.X8, P.inv, n, dim, metric, g1, zeros, M, heur, e_ids, e_dist, e_cnt, c.status, c.s));
+            // 2. the batch's lists go in, their entries are reverse edges of their targets
+            ck(cudaMemsetAsync(cin, 0, sizeof(int32_t) * n, c.s));
+            ck(cudaMemsetAsync(fill, 0, sizeof(int32_t) * n, c.s));
+            ck(launch_pg_install(order + done, b, M, e_ids, e_dist, e_cnt, adj, nd, deg, cin, c.s));
+            ck(scan_counts(cin, n, off, tmp, sb, c.s));
+            ck(launch_pg_rev_fill(order + done, b, M, e_ids, e_dist, e_cnt, off, fill, rev, c.s));
+            ck(launch_pos_flags(cin, n, flag, c.s));
+            ck(compact_flags(flag, n, targets, toff, tmp, sb, c.s));
+            const long long nt = c.read_ll(toff + n);
+            // 3. every target keeps its list and its new edges, or the heuristic's M of them
+            ck(cudaMemsetAsync(n_ov, 0, sizeof(int), c.s));
+            ck(launch_pg_rev_merge(targets, nt, off, rev, M, M + (int)b, adj, nd, deg, ov_ids, ov_dist, ov_tgt, n_ov,
+                                   c.s));
+            const long long nov = c.read_i32(n_ov);
+            if (nov > 0) {
+                fgim_knng g2;
+                std::memset(&g2, 0, sizeof(g2));
+                g2.ids = ov_ids;
+                g2.dist = ov_dist;
+                g2.n = nov;
+                g2.k = M + (int)b;
+                ck(launch_prune(P.X, P.X8, P.inv, n, dim, metric, g2, zeros, M, heur, o_ids, o_dist, o_cnt, c.status,
+                                c.s));
+                ck(launch_pg_write_back(ov_tgt, nov, M, o_ids, o_dist, o_cnt, adj, nd, deg, c.s));
+            }
+            done += b;
+        }
         c.finish(&t_stats);
+        *entry_out = medoid;
     });
     end_call();
     return r;
@@ -1287,6 +1548,118 @@ void fgim_graph_free(fgim_graph* g) {
     std::memset(g, 0, sizeof(*g));
 }
 
+fgim_status fgim_autotune(const fgim_shard* shards, int32_t h, const fgim_params* params, const char* cache_path,
+                          int32_t* out_wpb, int32_t* out_ht_bits, float* out_ms, void* stream) {
+    begin_call();
+    fgim_status r = guarded([&] {
+        check_params(params, true);
+        check_shards(shards, h, params);
+        need(!has_valid(shards, h), FGIM_EUNSUPPORTED, "tune on a merge without validity masks");
+        Ctx c((cudaStream_t)stream);
+        Problem P = make_problem(c, shards, h, params);
+        const int L = resolve_L(params, h);
+        need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
+        const bool bytes = P.X8 && byte_rows_ok(P.d);
+        const bool bf16 = !bytes && P.Xh && P.d > 128 && (reinterpret_cast<uintptr_t>(P.Xh) & 7u) == 0;
+        const unsigned long long key = beam_shape_key(P.metric, bytes ? 1 : bf16 ? 2 : 4, P.d, L);
+        fgim_knng g;
+        g.ids = c.alloc<int32_t>(P.N * params->k);
+        g.dist = c.alloc<float>(P.N * params->k);
+        g.flags = c.alloc<uint8_t>(P.N * params->k);
+        g.n = P.N;
+        g.k = params->k;
+        cudaEvent_t e0, e1;
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        const int ht0 = ht_bits_for(L);
+        BeamShape best = {4, ht0};
+        float best_ms = -1.f;
+        bool had = false;
+        BeamShape before = best;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                had = true;
+                before = it->second;
+            }
+        }
+        const int wpbs[2] = {2, 4};
+        for (int wi = 0; wi < 2; ++wi)
+            for (int dh = -1; dh <= 1; ++dh) {
+                const BeamShape cand = {wpbs[wi], std::min(13, std::max(6, ht0 + dh))};
+                if ((size_t)warp_layout(P.d, L, cand.htbits, params->k, !bytes).bytes * cand.wpb > 227 * 1024) continue;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tuned[key] = cand;
+                }
+                stage_a(c, P, params, h, &g);   // warm-up of this shape
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    ck(cudaEventRecord(e0, c.s));
+                    stage_a(c, P, params, h, &g);
+                    ck(cudaEventRecord(e1, c.s));
+                    ck(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    ck(cudaEventElapsedTime(&t, e0, e1));
+                    ms = rep == 0 ? t : std::min(ms, t);
+                }
+                if (best_ms < 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (best_ms >= 0.f) g_tuned[key] = best;
+            else if (had) g_tuned[key] = before;
+            else g_tuned.erase(key);
+        }
+        c.finish(&t_stats);
+        if (cache_path && best_ms >= 0.f) {
+            FILE* f = std::fopen(cache_path, "a");
+            need(f != nullptr, FGIM_EINVAL, "cannot open the autotune cache file");
+            std::fprintf(f,
+                         "{\"key\": %llu, \"wpb\": %d, \"ht_bits\": %d, \"ms\": %.4f, \"dim\": %d, \"L\": %d, "
+                         "\"row_bytes\": %d, \"metric\": %d}\n",
+                         key, best.wpb, best.htbits, best_ms, P.d, L, bytes ? 1 : bf16 ? 2 : 4, P.metric);
+            std::fclose(f);
+        }
+        if (out_wpb) *out_wpb = best.wpb;
+        if (out_ht_bits) *out_ht_bits = best.htbits;
+        if (out_ms) *out_ms = best_ms;
+    });
+    end_call();
+    return r;
+}
+
+fgim_status fgim_autotune_load(const char* cache_path) {
+    if (!cache_path) return FGIM_EINVAL;
+    FILE* f = std::fopen(cache_path, "r");
+    if (!f) return FGIM_EINVAL;
+    char line[512];
+    int loaded = 0;
+    while (std::fgets(line, sizeof(line), f)) {
+        unsigned long long key = 0;
+        int wpb = 0, hb = 0;
+        if (std::sscanf(line, "{\"key\": %llu, \"wpb\": %d, \"ht_bits\": %d", &key, &wpb, &hb) == 3 &&
+            (wpb == 1 || wpb == 2 || wpb == 4) && hb >= 6 && hb <= 13) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = BeamShape{wpb, hb};   // a later line for the same key wins
+            ++loaded;
+        }
+    }
+    std::fclose(f);
+    return loaded > 0 ? FGIM_OK : FGIM_EINVAL;
+}
+
+void fgim_autotune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
+
 int32_t fgim_test_set(const char* knob, int64_t value) {
     if (!knob) return 0;
     const std::string k(knob);
@@ -1296,6 +1669,10 @@ int32_t fgim_test_set(const char* knob, int64_t value) {
     }
     if (k == "hop_budget") {
         g_test_hop_budget.store(value > 0 ? (int)std::min<int64_t>(value, 0x7fffffff) : 0);
+        return 1;
+    }
+    if (k == "batch_union") {
+        g_test_batch_union.store(value != 0 ? 1 : 0);
         return 1;
     }
     if (k == "fail_alloc_after") {

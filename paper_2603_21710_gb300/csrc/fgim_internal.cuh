@@ -37,13 +37,21 @@ constexpr int kErrOverflow = 1;   // a bounded buffer overflowed (handled by the
 constexpr int kErrBounds = 2;     // an index failed a bounds check (the access was skipped)
 constexpr int kErrTimeout = 4;    // a bounded wait ran out
 
+// The input shards of one merge, or of a batch of independent merges run as one problem over
+// the disjoint union of their vertices (fgim_merge_batch): the shards of merge m are the
+// consecutive range grp[i] .. gend[i] - 1 of every shard i of m, and the cross query of a vertex
+// of shard i searches the other shards of that range with the pool gL[i] (its merge's L).
+constexpr int kMaxTableShards = 512;
 struct ShardTable {
-    int h;
+    int h;                               // shards in the table
     int dim;
-    long long off[kMaxShards + 1];
-    const int32_t* adj[kMaxShards];
-    int M[kMaxShards];
-    int entry[kMaxShards];
+    long long off[kMaxTableShards + 1];  // first global id of every shard
+    const int32_t* adj[kMaxTableShards];
+    int M[kMaxTableShards];
+    int entry[kMaxTableShards];          // local entry of every input PG
+    int grp[kMaxTableShards];            // first shard of the shard's merge
+    int gend[kMaxTableShards];           // one past the last shard of the shard's merge
+    int gL[kMaxTableShards];             // cross-query pool of the shard's merge
 };
 
 __host__ __device__ inline uint32_t f2ord(float f) {

@@ -87,6 +87,7 @@ struct RefineBuffers {
     int32_t* max_nc;
     int32_t* host_i32;
     long long class_count[4];   // out of refine_join: vertices per form (TC <= 64, <= 128, > 128; FP32 tile)
+    bool fp8;                   // Xb holds E4M3 rows with per-vector scales (tcm.w) instead of BF16 rows
     int32_t* blist;
     long long blist_cap;
     // tensor-core filter inputs: BF16 copy of the vectors and per row (|x|^2, bound on |x|,
@@ -103,6 +104,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         unsigned long long* cands, int* status, cudaStream_t s);
 cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
+cudaError_t launch_prep_fp8(const float* X, long long N, int d, uint8_t* Xq, float4* tcm, cudaStream_t s);
 cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
                             cudaStream_t s);
@@ -116,6 +118,7 @@ cudaError_t launch_zero_flags(const int32_t* T, long long N, int32_t* flag, cuda
 cudaError_t launch_nonzero_flags(const uint8_t* v, long long N, int32_t* flag, cudaStream_t s);
 
 // ---- k_prune.cu
+// Alg. 5 neighbour selection of the g.n lists of g (ids in 0 .. N - 1, rows of X) with `rule`
 cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
                          const fgim_knng& g, const int32_t* T, int R, PruneRule rule, int32_t* e_ids, float* e_dist,
                          int32_t* e_cnt, int* status, cudaStream_t s);
@@ -133,6 +136,15 @@ cudaError_t launch_reverse_insert(long long N, int R, const int32_t* e_ids, cons
 // reachability fix helpers
 cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, int32_t* st, int entry,
                             cudaStream_t s);
+// the same from the ne sources entries[] (device)
+cudaError_t launch_bfs_init_multi(int32_t* visited, long long N, int32_t* frontier, int32_t* st,
+                                  const int32_t* entries, int ne, int* status, cudaStream_t s);
+// batches run as one problem: start[r] = entries[m] of the merge m (id range off[m] .. off[m+1]-1)
+// holding reps[r]; the rows of one merge copied out of the union graph, ids minus base
+cudaError_t launch_rep_starts(const int32_t* reps, long long nr, const long long* off, const int32_t* entries, int nm,
+                              int32_t* start, cudaStream_t s);
+cudaError_t launch_split_rows(const int32_t* ids, const float* dist, const int32_t* deg, long long n, int R,
+                              int32_t base, int32_t* out_ids, float* out_dist, int32_t* out_deg, cudaStream_t s);
 // BFS levels level0 .. level0 + levels - 1 (state st: 8 ints, see k_prune.cu; level 1 reads fa)
 cudaError_t launch_bfs_levels(const int32_t* graph, int R, long long N, int32_t* visited, int32_t* fa, int32_t* fb,
                               int32_t* st, int level0, int levels, cudaStream_t s);
@@ -174,5 +186,30 @@ cudaError_t launch_layer_knn(const float* Xl, const uint8_t* X8l, const float* i
 cudaError_t launch_hnsw_next(const int32_t* best, const int32_t* mem, long long nmem, const int32_t* next,
                              long long nnext, long long nq, int first, int entry, int32_t* qpos, int32_t* start,
                              int* status, cudaStream_t s);
+
+// ---- k_pgbuild.cu: input PGs by batch-incremental insertion (see the file comment)
+cudaError_t launch_pg_medoid(const float* X, long long n, int d, double* mean, unsigned long long* dist_bits,
+                             unsigned long long* best, int* medoid, cudaStream_t s);
+cudaError_t launch_pg_init(long long n, int M, const int* medoid, int32_t* order, int32_t* nbr, float* nd, int32_t* cnt,
+                           int32_t* zeros, cudaStream_t s);
+cudaError_t launch_pg_install(const int32_t* rows, long long b, int M, const int32_t* e_ids, const float* e_dist,
+                              const int32_t* e_cnt, int32_t* nbr, float* nd, int32_t* cnt, int32_t* cin,
+                              cudaStream_t s);
+cudaError_t launch_pg_rev_fill(const int32_t* rows, long long b, int M, const int32_t* e_ids, const float* e_dist,
+                               const int32_t* e_cnt, const long long* off, int32_t* fill, uint64_t* rev,
+                               cudaStream_t s);
+cudaError_t launch_pg_rev_merge(const int32_t* targets, long long nt, const long long* off, const uint64_t* rev, int M,
+                                int W, int32_t* nbr, float* nd, int32_t* cnt, int32_t* ov_ids, float* ov_dist,
+                                int32_t* ov_tgt, int* n_ov, cudaStream_t s);
+cudaError_t launch_pg_write_back(const int32_t* ov_tgt, long long nov, int M, const int32_t* e_ids, const float* e_dist,
+                                 const int32_t* e_cnt, int32_t* nbr, float* nd, int32_t* cnt, cudaStream_t s);
+cudaError_t launch_pos_flags(const int32_t* c, long long n, int32_t* flag, cudaStream_t s);
+
+// ---- fgim_abi.cu: launch shapes chosen by the autotuner (fgim_autotune)
+// Beam-search kernels (cross query, searches): warps per block and visited-table bits, keyed by
+// (metric, bytes per coordinate read, dim, pool L) on the current device; untuned keys keep the
+// defaults passed in. Neither changes a result (the visited table may only forget ids).
+unsigned long long beam_shape_key(int metric, int row_bytes, int dim, int L);
+void tuned_beam_shape(unsigned long long key, int* wpb, int* htbits);
 
 }  // namespace fgim

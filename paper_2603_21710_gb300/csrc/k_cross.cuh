@@ -7,7 +7,8 @@
 namespace fgim {
 
 // Stage (a), Alg. 2: for every global vertex g (warp per vertex) collect C_i^+(u) from its
-// own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j, keep the top-k by
+// own PG and KNNSearch(x_u, G_j, L, L, ep_j) for every other shard j of its merge (L: the
+// merge's pool, at most the launch's L, which sizes shared memory), keep the top-k by
 // (delta, id), write ids / distances / new flags. With the ID mapping phi (Sec. 4.1.3) of
 // invalid vertices, warp r serves input row rows_of[r]; local candidates and search results are
 // renamed by phi and the invalid ones (phi = -1) dropped before the top-k (phi keeps the
@@ -85,13 +86,14 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
         __syncwarp();
         nres = warp_merge<true>(res, nullptr, nres, k, cand, 0);
     }
-    // Alg. 2, cross querying of every other index
-    for (int j = 0; j < t.h; ++j) {
+    // Alg. 2, cross querying of every other index of this vertex's merge, with its pool size
+    const int Lq = t.gL[i];
+    for (int j = t.grp[i]; j < t.gend[i]; ++j) {
         if (j == i) continue;
         const long long nj = t.off[j + 1] - t.off[j];
         const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr + t.off[j] * d,
                                                              inv_norm ? inv_norm + t.off[j] : nullptr, t.adj[j], t.M[j],
-                                                             nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d, L, pool,
+                                                             nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d, Lq, pool,
                                                              pflag, ht, htbits, scratch, P, ctr, status);
         for (int c0 = 0; c0 < np; c0 += 32) {
             uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
@@ -123,9 +125,10 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
                                  long long N, int metric, int k, int L, fgim_knng* out,
                                  unsigned long long* counters, int* status, cudaStream_t s, const int32_t* phi,
                                  const int32_t* src, long long nq, const uint16_t* Xh) {
-    const int htbits = ht_bits_for(L);
-    const int wpb = 4;
     const bool bytes = X8 && byte_rows_ok(t.dim);
+    const bool bf16 = !bytes && Xh && t.dim > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0;
+    int htbits = ht_bits_for(L), wpb = 4;   // the autotuner's choice for this workload, if any
+    tuned_beam_shape(beam_shape_key(metric, bytes ? 1 : bf16 ? 2 : 4, t.dim, L), &wpb, &htbits);
     const WarpLayout lay = warp_layout(t.dim, L, htbits, k, !bytes);
     const size_t smem = (size_t)lay.bytes * wpb;
     if (nq < 0) nq = N;
@@ -148,7 +151,7 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
     if (bytes) {
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, t.dim, L, FGIM_LAUNCH_CQ, uint8_t);
-    } else if (Xh && t.dim > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0) {   // BF16 storage: same values, half the bytes
+    } else if (bf16) {   // BF16 storage: same values, half the bytes
         const void* rows = Xh;
         FGIM_DISPATCH_ALL_WIDE(metric, L, FGIM_LAUNCH_CQ, uint16_t);
     } else {

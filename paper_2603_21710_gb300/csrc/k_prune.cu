@@ -29,7 +29,7 @@ static inline long long cdivl(long long a, long long b) { return (a + b - 1) / b
 
 template <int METRIC, bool STAGE>
 __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const float* __restrict__ inv_norm,
-                                              long long N, int d, int k, const int32_t* __restrict__ ids,
+                                              long long N, long long nrows, int d, int k, const int32_t* __restrict__ ids,
                                               const float* __restrict__ dist, const int32_t* __restrict__ T, int R,
                                               PruneRule rule, int32_t* __restrict__ e_ids, float* __restrict__ e_dist,
                                               int32_t* __restrict__ e_cnt, int* status) {
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
     const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (u >= N) return;
+    if (u >= nrows) return;
     const int stride = d + 4;
     const int nc4 = d >> 2;
     const size_t per_warp = ((size_t)(STAGE ? k * stride * 4 : 0) + (size_t)k * 12 + 16 + 15) & ~(size_t)15;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(64) k_prune(const float* __restrict__ X, const
 // distances instead of one per kept neighbour.
 template <int METRIC>
 __global__ void __launch_bounds__(128) k_prune_wide(const float* __restrict__ X, const float* __restrict__ inv_norm,
-                                                    long long N, int d, int k, const int32_t* __restrict__ ids,
+                                                    long long N, long long nrows, int d, int k, const int32_t* __restrict__ ids,
                                                     const float* __restrict__ dist, const int32_t* __restrict__ T,
                                                     int R, PruneRule rule, int32_t* __restrict__ e_ids,
                                                     float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) k_prune_wide(const float* __restrict__ X,
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
     const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (u >= N) return;
+    if (u >= nrows) return;
     const int nc4 = d >> 2;
     int32_t* cidv = reinterpret_cast<int32_t*>(smem) + (size_t)warp * 2 * k;
     int32_t* kept = cidv + k;
@@ -230,7 +230,7 @@ __host__ __device__ inline size_t prune_bytes_per_warp(int k, int d) {
 // which spreads the lanes' rows over the banks), with their squared norms.
 template <int METRIC>
 __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__ X8, const float* __restrict__ inv_norm,
-                                                     long long N, int d, int k, const int32_t* __restrict__ ids,
+                                                     long long N, long long nrows, int d, int k, const int32_t* __restrict__ ids,
                                                      const float* __restrict__ dist, const int32_t* __restrict__ T,
                                                      int R, PruneRule rule, int32_t* __restrict__ e_ids,
                                                      float* __restrict__ e_dist, int32_t* __restrict__ e_cnt,
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
     const long long u = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (u >= N) return;
+    if (u >= nrows) return;
     const int stride = d + 16;
     const size_t per_warp = prune_bytes_per_warp(k, d);
     unsigned char* base = smem + per_warp * warp;
@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
 cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_norm, long long N, int d, int metric,
                          const fgim_knng& g, const int32_t* T, int R, PruneRule rule, int32_t* e_ids, float* e_dist,
                          int32_t* e_cnt, int* status, cudaStream_t s) {
-    if (N <= 0) return cudaSuccess;
+    const long long nrows = g.n;   // lists to prune (ids range over 0 .. N - 1)
+    if (nrows <= 0) return cudaSuccess;
     const int k = g.k;
     if (X8 && byte_rows_ok(d) && k <= 64) {
         const int wpb = 4;
@@ -368,7 +369,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
         e = cudaFuncSetAttribute(k_prune_bytes<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_prune", s);                                                                             \
-        k_prune_bytes<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X8, inv_norm, N, d, k, g.ids, g.dist, T, \
+        k_prune_bytes<MT><<<(unsigned)cdivl(nrows, wpb), wpb * 32, smem, s>>>(X8, inv_norm, N, nrows, d, k, g.ids, g.dist, T, \
                                                                           R, rule, e_ids, e_dist, e_cnt, status);\
         e = cudaGetLastError();                                                                                   \
     } while (0)
@@ -385,7 +386,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
 #define FGIM_LAUNCH_PW(MT)                                                                                        \
     do {                                                                                                          \
         LaunchScope ls("k_prune", s);                                                                             \
-        k_prune_wide<MT><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R,  \
+        k_prune_wide<MT><<<(unsigned)cdivl(nrows, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, nrows, d, k, g.ids, g.dist, T, R,  \
                                                                          rule, e_ids, e_dist, e_cnt, status);   \
         e = cudaGetLastError();                                                                                   \
     } while (0)
@@ -406,7 +407,7 @@ cudaError_t launch_prune(const float* X, const uint8_t* X8, const float* inv_nor
         e = cudaFuncSetAttribute(k_prune<MT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_prune", s);                                                                             \
-        k_prune<MT, ST><<<(unsigned)cdivl(N, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, d, k, g.ids, g.dist, T, R, \
+        k_prune<MT, ST><<<(unsigned)cdivl(nrows, wpb), wpb * 32, smem, s>>>(X, inv_norm, N, nrows, d, k, g.ids, g.dist, T, R, \
                                                                         rule, e_ids, e_dist, e_cnt, status);    \
         e = cudaGetLastError();                                                                                   \
     } while (0)
@@ -519,6 +520,46 @@ cudaError_t launch_bfs_init(int32_t* visited, long long N, int32_t* frontier, in
                             cudaStream_t s) {
     LaunchScope ls("k_bfs_init", s);
     k_bfs_init<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, frontier, st, entry);
+    return cudaGetLastError();
+}
+
+// BFS from several sources at once (the entries of the merges of a batch, each in its own
+// component of the union graph): every entry is at level 1 and in the first frontier
+__global__ void k_bfs_init_multi(int32_t* visited, long long N, int32_t* frontier, int32_t* st,
+                                 const int32_t* __restrict__ entries, int ne) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) visited[i] = 0;
+    if (i == 0) {
+        st[1] = ne;
+        st[2] = 0;
+        st[0] = 0;
+        *reinterpret_cast<long long*>(st + 4) = ne;
+    }
+}
+__global__ void k_bfs_seed(int32_t* visited, long long N, int32_t* frontier, const int32_t* __restrict__ entries,
+                           int ne, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int32_t e = entries[i];
+    if (e < 0 || e >= N) {
+        atomicOr(status, kErrBounds);
+        frontier[i] = 0;
+        return;
+    }
+    visited[e] = 1;
+    frontier[i] = e;
+}
+
+cudaError_t launch_bfs_init_multi(int32_t* visited, long long N, int32_t* frontier, int32_t* st,
+                                  const int32_t* entries, int ne, int* status, cudaStream_t s) {
+    {
+        LaunchScope ls("k_bfs_init", s);
+        k_bfs_init_multi<<<(unsigned)cdivl(N, 256), 256, 0, s>>>(visited, N, frontier, st, entries, ne);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    LaunchScope ls("k_bfs_init", s);
+    k_bfs_seed<<<(unsigned)cdivl(ne, 256), 256, 0, s>>>(visited, N, frontier, entries, ne, status);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@
 // the host merges what fits and re-runs those vertices (their pairs are re-evaluated
 // against the updated lists), which yields the same final lists.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "fgim_launch.h"
 #include "tc_sm100.cuh"
@@ -593,6 +595,47 @@ __global__ void k_prep_bf16(const float* __restrict__ X, long long N, int d, __n
     }
 }
 
+// FP8 E4M3 rows with one scale per vector: s = amax |x| / 448 (1 for an all-zero row),
+// q = saturating round-to-nearest E4M3 of x / s; the MMA forms sum q_a q_b and the filter takes
+// s_a s_b times it. tcm = (|x|^2, bound on |x|, bound on |x - s q|, s); the conversion error is
+// what the filter's bound is built from (every row counts as inexact).
+__global__ void k_prep_fp8(const float* __restrict__ X, long long N, int d, __nv_fp8_storage_t* __restrict__ Xq,
+                           float4* __restrict__ tcm) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const float* x = X + row * d;
+    float amax = 0.f;
+    for (int c = lane; c < d; c += 32) amax = fmaxf(amax, fabsf(x[c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
+    const float sc = amax > 0.f ? amax / 448.f : 1.f;
+    __nv_fp8_storage_t* xq = Xq + row * d;
+    float s = 0.f, se = 0.f;
+    for (int c = lane; c < d; c += 32) {
+        const float v = x[c];
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(v / sc, __NV_SATFINITE, __NV_E4M3);
+        xq[c] = q;
+        const float dq = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+        const float e = fmaf(-sc, dq, v);   // v - s q, one rounding
+        s = fmaf(v, v, s);
+        se = fmaf(e, e, se);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(kFull, s, o);
+        se += __shfl_xor_sync(kFull, se, o);
+    }
+    if (lane == 0) tcm[row] = make_float4(s, sqrtf(s) * 1.0001f, fmaxf(sqrtf(se) * 1.001f, 1e-18f), sc);
+}
+
+cudaError_t launch_prep_fp8(const float* X, long long N, int d, uint8_t* Xq, float4* tcm, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    LaunchScope ls("k_prep_fp8", s);
+    k_prep_fp8<<<(unsigned)cdivll(N * 32, 256), 256, 0, s>>>(X, N, d, reinterpret_cast<__nv_fp8_storage_t*>(Xq), tcm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     LaunchScope ls("k_prep_bf16", s);
@@ -661,7 +704,10 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
 }
 
 // One CTA per vertex v (vlist[blockIdx.x]); C_n = the first nn candidates, C = all nc.
-template <int METRIC, bool BYTES, bool LARGE>
+// FP8: the staged operand holds E4M3 rows with one scale per vector (k_prep_fp8) instead of BF16
+// rows; each Gram entry is then scaled by the two vectors' scales, the filter's bound takes their
+// conversion errors, and the re-rank always reads the FP32 rows.
+template <int METRIC, bool BYTES, bool LARGE, bool FP8>
 __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
     const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
@@ -689,7 +735,8 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         return;
     }
     const int d = t.dim;
-    const TCLayout L = tc_layout(cm, d);
+    const int du = FP8 ? d / 2 : d;   // row length in 2-byte staging units (an E4M3 pair per unit)
+    const TCLayout L = tc_layout(cm, du);
     unsigned char* op = smem + L.op;
     float4* meta = reinterpret_cast<float4*>(smem + L.meta);   // n2, |x| bound, |e| bound, cosine 1/|x|
     float4* colf = reinterpret_cast<float4*>(smem + L.colf);   // P, worst distance, shard (bits), -
@@ -708,7 +755,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc + 48);
     const int W = L.words, hs = L.hs, rows = L.rows_alloc;
     const int vq = d >> 2;           // float4 chunks per FP32 row
-    const int kc = d >> 3;           // 16-byte chunks per BF16 row
+    const int kc = du >> 3;          // 16-byte chunks per staged (BF16 or E4M3) row
     const int kcp = L.dpad >> 3;     // 16-byte chunks per staged row
     const int npad = ((nc + 15) / 16) * 16;   // MMA N
     const int kcp_sh = (kcp & (kcp - 1)) == 0 ? __ffs(kcp) - 1 : -1;   // shift for / kcp when a power of two
@@ -738,7 +785,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             const int c = item - r * kcp;
             const int gc = ch * kcp + c;
             unsigned char* dst = op + tc::sw_offset(LARGE ? r : tc_row(r), c, rows);
-            if (gc < kc) cp_async16(dst, Xb + (long long)cid[r] * d + gc * 8, true);
+            if (gc < kc) cp_async16(dst, Xb + (long long)cid[r] * du + gc * 8, true);
             else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
         }
         cp_async_commit();
@@ -797,7 +844,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         thr[i] = wi < 0 ? kEmptyKey : mkkey(dk, wi);
         if (m.z != 0.f) atomicOr(misc + 2, 1);
         colf[i] = make_float4((1.f - Cf) * m.x, wi < 0 ? __int_as_float(0x7f800000) : dk,
-                              __int_as_float(shard_of(t, c)), 0.f);
+                              __int_as_float(shard_of(t, c)), FP8 ? m.w : 0.f);   // w: the E4M3 scale
         m.w = inv;
         meta[i] = m;
     };
@@ -865,8 +912,8 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const uint32_t tmem = *tmem_slot;
     // every row converted exactly to BF16 and the whole row fits one staged chunk: the re-rank
     // may read the staged tile instead of the FP32 rows
-    const bool exact = misc[2] == 0 && nch == 1;
-    const bool exact_rows = misc[2] == 0;
+    const bool exact = !FP8 && misc[2] == 0 && nch == 1;
+    const bool exact_rows = !FP8 && misc[2] == 0;
     bool ok_mma = true;
     for (int ch = 0; ch < nch && ok_mma; ++ch) {
         if (ch > 0) {
@@ -880,11 +927,12 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             tc::fence_after_sync();
         }
         if (tid == 0) {
-            const uint32_t idesc = tc::idesc_bf16(128, LARGE ? npad : 128);
+            const uint32_t idesc = FP8 ? tc::idesc_e4m3(128, LARGE ? npad : 128) : tc::idesc_bf16(128, LARGE ? npad : 128);
             const uint32_t base = tc::smem_u32(op);
-            for (int s = 0; s < L.dpad / 16; ++s) {
+            for (int s = 0; s < L.dpad / 16; ++s) {   // 32 bytes of every row per MMA
                 const uint64_t desc = tc::smem_desc_sw128(base + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32));
-                tc::mma_bf16(tmem, desc, desc, idesc, (ch > 0 || s > 0) ? 1u : 0u);
+                if (FP8) tc::mma_e4m3(tmem, desc, desc, idesc, (ch > 0 || s > 0) ? 1u : 0u);
+                else tc::mma_bf16(tmem, desc, desc, idesc, (ch > 0 || s > 0) ? 1u : 0u);
             }
             tc::commit_to(mbar);
         }
@@ -922,7 +970,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     const int a = LARGE ? r : tc_cand(r);    // this lane's candidate
     const bool r_ok = a < nc;
     const float4 fr = r_ok ? colf[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float Pr = fr.x, tdr = fr.y;
+    const float Pr = fr.x, tdr = fr.y, sr = fr.w;
     const int shr = r_ok ? __float_as_int(fr.z) : -1;
     const float4 mr = r_ok ? meta[a] : make_float4(0.f, 0.f, 0.f, 1.f);
     const float n2r = mr.x, xr = mr.y, er = mr.z, cr = mr.w;
@@ -934,6 +982,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     auto trow_of = [&](int w) -> uint32_t { return tmem + ((uint32_t)(32 * (w & 3)) << 16); };
     // lo, a lower bound of the exact value of pair {a, b}, from its Gram entry
     auto lower = [&](int b, float dot, const float4& cc) -> float {
+        if (FP8) dot = dot * (sr * cc.w);   // sum q_a q_b -> s_a s_b sum q_a q_b (two roundings, in the bound)
         if (fast) return fmaf(-2.f, dot, Pr + cc.x);
         const float4 mc = meta[b];
         const float cs = er * mc.y + mc.z * xer + g * xer * (mc.y + mc.z);
@@ -1289,47 +1338,61 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
     for (int q = 0; q < 8; ++q) hb[q] = b.host_i32[q];
     const int32_t cm = hb[0], cmn = hb[1];
     if (cm < 2) return cudaSuccess;
-    bool use_tc = b.join_filter == 0 && b.Xb && t.dim % 16 == 0 && cmn <= 128 && cm <= 256;
+    const int du = b.fp8 ? t.dim / 2 : t.dim;   // staged row length in 2-byte units
+    bool use_tc = b.join_filter != 1 && b.Xb && du % 16 == 0 && cmn <= 128 && cm <= 256;
     if (use_tc)
         for (int q = 0; q < kTCLists; ++q)
-            if (hb[2 + q] > 0 && tc_layout(hb[5 + q], t.dim).bytes > 227 * 1024) use_tc = false;
+            if (hb[2 + q] > 0 && tc_layout(hb[5 + q], du).bytes > 227 * 1024) use_tc = false;
     if (use_tc) {
         for (int q = 0; q < kTCLists; ++q) {
             const int32_t count = hb[2 + q], cmq = hb[5 + q];
             if (count <= 0) continue;
             b.class_count[q] += count;
-            const TCLayout TL = tc_layout(cmq, t.dim);
+            const TCLayout TL = tc_layout(cmq, du);
             const int ncols = cmq <= 128 ? 128 : ((cmq + 15) / 16) * 16;   // MMA N (interleaved order: 128)
             uint32_t cols = 32;
             while ((int)cols < ncols) cols <<= 1;
             const size_t smem = tc_launch_smem(TL, cols);
             const int32_t* list = b.blist + (long long)q * b.blist_cap;
-#define FGIM_LAUNCH_TC3(MT, BY, LG)                                                                               \
+#define FGIM_LAUNCH_TC4(MT, BY, LG, F8)                                                                           \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(k_join_tc<MT, BY, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        e = cudaFuncSetAttribute(k_join_tc<MT, BY, LG, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                 (int)smem);                                                                      \
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
-        k_join_tc<MT, BY, LG><<<(unsigned)count, (BY) ? 256 : kTCThreads, smem, s>>>(                               \
+        k_join_tc<MT, BY, LG, F8><<<(unsigned)count, (BY) ? 256 : kTCThreads, smem, s>>>(                           \
             t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, cands, status);                                                                                \
         e = cudaGetLastError();                                                                                   \
     } while (0)
+#define FGIM_LAUNCH_TC3(MT, BY, LG) FGIM_LAUNCH_TC4(MT, BY, LG, false)
 #define FGIM_LAUNCH_TC(MT, BY)                                                                                    \
     do {                                                                                                          \
         if (cmq > 128) FGIM_LAUNCH_TC3(MT, BY, true);                                                             \
         else FGIM_LAUNCH_TC3(MT, BY, false);                                                                      \
     } while (0)
-            const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim);
-            if (metric == FGIM_L2SQ) {
+#define FGIM_LAUNCH_TC8(MT)                                                                                       \
+    do {                                                                                                          \
+        if (cmq > 128) FGIM_LAUNCH_TC4(MT, false, true, true);                                                    \
+        else FGIM_LAUNCH_TC4(MT, false, false, true);                                                             \
+    } while (0)
+            const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim) && !b.fp8;
+            if (b.fp8) {
+                if (metric == FGIM_L2SQ) FGIM_LAUNCH_TC8(FGIM_L2SQ);
+                else if (metric == FGIM_IP) FGIM_LAUNCH_TC8(FGIM_IP);
+                else FGIM_LAUNCH_TC8(FGIM_COSINE);
+            } else if (metric == FGIM_L2SQ) {
                 if (bytes) FGIM_LAUNCH_TC(FGIM_L2SQ, true); else FGIM_LAUNCH_TC(FGIM_L2SQ, false);
             } else if (metric == FGIM_IP) {
                 if (bytes) FGIM_LAUNCH_TC(FGIM_IP, true); else FGIM_LAUNCH_TC(FGIM_IP, false);
             } else {
                 if (bytes) FGIM_LAUNCH_TC(FGIM_COSINE, true); else FGIM_LAUNCH_TC(FGIM_COSINE, false);
             }
+#undef FGIM_LAUNCH_TC8
 #undef FGIM_LAUNCH_TC
 #undef FGIM_LAUNCH_TC3
+#undef FGIM_LAUNCH_TC4
             if (e != cudaSuccess) return e;
         }
         return e;

@@ -61,9 +61,10 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
                           const int32_t* qids, long long nq, int topk, int L, int32_t* out_ids, float* out_dist,
                           unsigned long long* counters, int* status, cudaStream_t s, const uint16_t* Xh,
                           const int32_t* qentry) {
-    const int htbits = ht_bits_for(L);
-    const int wpb = 4;
     const bool bytes = X8 && qids && byte_rows_ok(d);
+    const bool bf16 = !bytes && Xh && d > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0;
+    int htbits = ht_bits_for(L), wpb = 4;   // the autotuner's choice for this workload, if any
+    tuned_beam_shape(beam_shape_key(metric, bytes ? 1 : bf16 ? 2 : 4, d, L), &wpb, &htbits);
     const WarpLayout lay = warp_layout(d, L, htbits, 0, !bytes);
     const size_t smem = (size_t)lay.bytes * wpb;
     const long long blocks = (nq + wpb - 1) / wpb;
@@ -82,7 +83,7 @@ cudaError_t launch_search(const float* X, const uint8_t* X8, const float* inv_no
     if (bytes) {   // byte rows need integer queries: rows of X
         const void* rows = X8;
         FGIM_DISPATCH_ALL(metric, d, L, FGIM_LAUNCH_S, uint8_t);
-    } else if (Xh && d > 128 && (reinterpret_cast<uintptr_t>(Xh) & 7u) == 0) {   // BF16 storage: same values, half the bytes
+    } else if (bf16) {   // BF16 storage: same values, half the bytes
         const void* rows = Xh;
         FGIM_DISPATCH_ALL_WIDE(metric, L, FGIM_LAUNCH_S, uint16_t);
     } else {

@@ -211,4 +211,50 @@ cudaError_t launch_bf16_to_f32(const uint16_t* in, long long n, float* out, cuda
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------- batches as one problem
+// start[r] = entries[m] for the merge m whose id range off[m] .. off[m + 1] - 1 holds reps[r]
+__global__ void k_rep_starts(const int32_t* __restrict__ reps, long long nr, const long long* __restrict__ off,
+                             const int32_t* __restrict__ entries, int nm, int32_t* __restrict__ start) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    const long long x = reps[r];
+    int lo = 0, hi = nm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (x >= off[mid]) lo = mid;
+        else hi = mid - 1;
+    }
+    start[r] = entries[lo];
+}
+
+cudaError_t launch_rep_starts(const int32_t* reps, long long nr, const long long* off, const int32_t* entries, int nm,
+                              int32_t* start, cudaStream_t s) {
+    if (nr <= 0) return cudaSuccess;
+    LaunchScope ls("k_rep_starts", s);
+    k_rep_starts<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(reps, nr, off, entries, nm, start);
+    return cudaGetLastError();
+}
+
+// rows of one merge out of the union graph: ids renumbered to the merge (id - base), dist, deg
+__global__ void k_split_rows(const int32_t* __restrict__ ids, const float* __restrict__ dist,
+                             const int32_t* __restrict__ deg, long long n, int R, int32_t base,
+                             int32_t* __restrict__ out_ids, float* __restrict__ out_dist, int32_t* __restrict__ out_deg) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n * R) {
+        const int32_t v = ids[i];
+        out_ids[i] = v >= 0 ? v - base : -1;
+        out_dist[i] = dist[i];
+    }
+    if (i < n) out_deg[i] = deg[i];
+}
+
+cudaError_t launch_split_rows(const int32_t* ids, const float* dist, const int32_t* deg, long long n, int R,
+                              int32_t base, int32_t* out_ids, float* out_dist, int32_t* out_deg, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    LaunchScope ls("k_split_rows", s);
+    k_split_rows<<<(unsigned)((n * R + 255) / 256), 256, 0, s>>>(ids, dist, deg, n, R, base, out_ids, out_dist,
+                                                                 out_deg);
+    return cudaGetLastError();
+}
+
 }  // namespace fgim

@@ -10,7 +10,9 @@
 // of every row): step s starts (s / 4) panels and (s % 4) * 32 bytes further. A row read by
 // a warp touches 128 contiguous bytes of each panel, so neither the staging writes nor the
 // row reads conflict on shared-memory banks. The accumulator D (M = 128 rows) occupies
-// TMEM lanes 0..127, one row per lane, one FP32 column per output column.
+// TMEM lanes 0..127, one row per lane, one FP32 column per output column. E4M3 operands use the
+// same byte layout (a 128-byte panel line holds 128 of them) and one kind::f8f6f4 MMA consumes
+// K = 32, again 32 bytes of every row.
 #pragma once
 
 #include <cstdint>
@@ -42,6 +44,12 @@ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0), D FP32, both
+// K-major, M x N; one MMA consumes K = 32 (the same 32 bytes of every row as kind::f16)
+__device__ __forceinline__ uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)), "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -56,6 +64,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 

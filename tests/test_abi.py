@@ -120,8 +120,10 @@ def test_newer_entry_points_reject_bad_arguments_on_host(lib):
                                 None) == _lib.FGIM_EINVAL
     assert ctypes.sizeof(_lib.Layer) == 32
     # the input-PG builder: M and ef out of range
-    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 0, 16, base, base, None) == _lib.FGIM_EINVAL
-    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 8, 129, base, base, None) == _lib.FGIM_EINVAL
+    ent = ctypes.c_int32(0)
+    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 0, 16, base, base, ctypes.byref(ent), None) == _lib.FGIM_EINVAL
+    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 8, 129, base, base, ctypes.byref(ent), None) == _lib.FGIM_EINVAL
+    assert lib.fgim_build_pg(base, 64, 16, 0, 0, 8, 16, base, base, None, None) == _lib.FGIM_EINVAL
 
 
 def test_test_hooks_named_and_unknown(lib):
@@ -149,3 +151,15 @@ def test_graph_alloc_rejects_bad_shapes_on_host(lib):
     assert lib.fgim_graph_alloc(10, 32, None) == -1
     assert not g.ids and g.n == 0
     lib.fgim_graph_free(ctypes.byref(g))   # a zeroed graph is a no-op
+
+
+def test_autotune_cache_parsing_on_host(lib, tmp_path):
+    """fgim_autotune_load reads the cache's JSON lines without a device; unreadable input is refused."""
+    assert lib.fgim_autotune_load(str(tmp_path / "missing.jsonl").encode()) == -1
+    bad = tmp_path / "bad.jsonl"
+    bad.write_text("not json\n")
+    assert lib.fgim_autotune_load(str(bad).encode()) == -1
+    good = tmp_path / "good.jsonl"
+    good.write_text('{"key": 12345, "wpb": 2, "ht_bits": 9, "ms": 1.0}\n{"key": 12345, "wpb": 8, "ht_bits": 9}\n')
+    assert lib.fgim_autotune_load(str(good).encode()) == 0   # the second line (wpb 8) is refused
+    lib.fgim_autotune_clear()

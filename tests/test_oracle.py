@@ -824,3 +824,58 @@ def test_parallel_layers_match_the_sequential_insertion_in_quality(small_problem
     rp = O.recall_at(O.hnsw_search(w.X, w.metric, r.ids, [(m, a) for m, a, _ in par], O.hnsw_entry(levels), Q, 32,
                                    10, 8)[0], gt, 10)
     assert rp >= rs - 0.01, (rp, rs)
+
+
+# --------------------------------------------------------------------------- reachability fix, plain form
+def test_reach_fix_rounds_against_the_plain_sequential_rule(small_problem):
+    """The round-based reachability fix (the form the kernels follow) against the plain sequential
+    rule (each unreached vertex in ascending id attached to the first reached vertex of its k-NNG
+    list or search results with room, else with a neighbour of indegree > 1): both leave every
+    vertex reachable from the entry and both lift the flat search's recall far above the graph
+    without the fix (the two attach differently, so their recalls are reported, not equated)."""
+    w, graphs, P = small_problem
+    r = O.merge(P, w.k, w.R, w.alpha, iters=1, ensure_reachable=False)
+    assert not _bfs_all(r.ids, r.entry)
+    a_ids, a_dist, a_deg = r.ids.copy(), r.dist.copy(), r.deg.copy()
+    b_ids, b_dist, b_deg = r.ids.copy(), r.dist.copy(), r.deg.copy()
+    sa = O.reach_fix(P, a_ids, a_dist, a_deg, r.entry, 64)
+    sb = O.reach_fix_seq(P, b_ids, b_dist, b_deg, r.entry, 64, knn_ids=r.knn_ids)
+    assert sa["unreached"] == 0 and sb["unreached"] == 0
+    assert _bfs_all(a_ids, r.entry) and _bfs_all(b_ids, r.entry)
+    assert sa["attached"] > 0 and sb["attached"] > 0
+    Q = w.Q[:1000]
+    gt, _ = O.knn_exact(w.X, Q, 10, w.metric)
+    r0 = O.recall_at(O.search(w.X, r.ids, r.entry, Q, 64, 10, w.metric)[0], gt, 10)
+    ra = O.recall_at(O.search(w.X, a_ids, r.entry, Q, 64, 10, w.metric)[0], gt, 10)
+    rb = O.recall_at(O.search(w.X, b_ids, r.entry, Q, 64, 10, w.metric)[0], gt, 10)
+    assert ra > r0 + 0.2 and rb > r0 + 0.2, (r0, ra, rb)
+
+
+def test_plain_reach_fix_can_cut_off_vertices_the_round_form_keeps():
+    """Why the round-based form replaces only a neighbour that keeps another BFS parent: on the
+    Sift-like recipe (12,000 points) the plain rule's 'indegree > 1' victim can lose its only
+    reached in-edge, and vertices stay unreachable; the round-based form reaches every vertex
+    with as many attachments."""
+    from synth import gen, pgbuild
+    w = gen.make("medium", N=12000, nq=10, n_centers=12)
+    P = O.Problem.from_workload(w, pgbuild.build_all(w))
+    r = O.merge(P, w.k, w.R, w.alpha, iters=2, ensure_reachable=False)
+    a = (r.ids.copy(), r.dist.copy(), r.deg.copy())
+    b = (r.ids.copy(), r.dist.copy(), r.deg.copy())
+    sa = O.reach_fix(P, *a, r.entry, 64)
+    sb = O.reach_fix_seq(P, *b, r.entry, 64, knn_ids=r.knn_ids)
+    assert sa["unreached"] == 0 and _bfs_all(a[0], r.entry)
+    assert sb["unreached"] > 0 and not _bfs_all(b[0], r.entry)
+
+
+def _bfs_all(ids, entry):
+    seen = np.zeros(ids.shape[0], bool)
+    seen[entry] = True
+    stack = [entry]
+    while stack:
+        x = stack.pop()
+        for y in ids[x]:
+            if y >= 0 and not seen[y]:
+                seen[y] = True
+                stack.append(int(y))
+    return bool(seen.all())

@@ -59,10 +59,11 @@ def parse():
                          "the plain FP32 form of the same merges; prints its own JSON line")
     ap.add_argument("--batched-lo", type=int, default=10_000)
     ap.add_argument("--batched-hi", type=int, default=200_000)
-    ap.add_argument("--configs", default="precision,fp8,batched",
+    ap.add_argument("--configs", default="small,precision,fp8,batched",
                     help="other workloads timed after the headline one, each in its own sub-record: "
                          "'precision' (1M d=96 IP, BF16 filter against plain FP32), 'fp8' (1M d=960, 8 uneven "
-                         "shards), 'batched' (64 merges, ~4M points, d=768 BF16 cosine, one call); '' = none")
+                         "shards), 'batched' (64 merges, ~4M points, d=768 BF16 cosine, one call), 'small' (20k, "
+                         "d=32, with the single-thread oracle); '' = none")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip comparing the GPU merge with the oracle's (100k sample and the largest N the "
                          "oracle finishes in about two minutes)")
@@ -423,10 +424,10 @@ def gpu_graphs(fg, w, X_dev):
 
 # the other workloads of the measurement plan, timed after the headline one (one sub-record each)
 CONFIGS = {
-    "precision": dict(recipe="precision", metric="ip", filter="tc", others=(),
+    "precision": dict(recipe="precision", metric="ip", filter="tc", others=(), oracle_n=100_000,
                       workload="Deep-like merge: N=1,000,000 (2 x 500,000), d=96 unit-norm, inner product, "
                                "input PGs M=32 ef=128, k=48, R=32, alpha=1.0, I_max=3"),
-    "fp8": dict(recipe="fp8", metric="l2", filter="fp8", others=("tc",),
+    "fp8": dict(recipe="fp8", metric="l2", filter="fp8", others=("tc",), oracle_n=36_000,
                 workload="Gist-like merge: N=1,000,000 (8 shards sized i*N/36), d=960 non-negative, squared L2, "
                          "input PGs M=32 ef=128, k=64, R=48, alpha=1.0, I_max=3"),
 }
@@ -462,6 +463,75 @@ def timed_merges(fg, inp, kw, steps, warmup, profile=False):
             "launches": fg.launch_count() - launches0}
 
 
+def oracle_sample_check(fg, recipe, n, kw, metric_name, dev, filter_, nq=1000, host_graphs=False):
+    """The recall delta against the FP64 oracle on a bounded sample of a workload: the same
+    recipe at n points, merged by the GPU (chosen form) and by the oracle (all host cores), each
+    graph searched by its own side (recall@10, beam 64, exact truth); plus the share of identical
+    merged rows."""
+    import torch
+    import oracle as O
+    from synth import gen, pgbuild
+    w = gen.make(recipe, N=n, nq=nq)
+    X = torch.from_numpy(w.X).to(dev)
+    graphs = pgbuild.build_all(w) if host_graphs else gpu_graphs(fg, w, X)[0]
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs], metric=metric_name)
+    o = fg.merge(inp, **kw, join_filter=filter_)
+    P = O.Problem.from_workload(w, graphs)
+    t0 = time.perf_counter()
+    r = O.merge(P, kw["k"], kw["R"], kw["alpha"], iters=kw["iters"])
+    dt = time.perf_counter() - t0
+    Q = torch.from_numpy(np.ascontiguousarray(w.Q)).to(dev)
+    gt = exact_top10(X, Q, w.metric)
+    sid, _ = fg.search(X, o["ids"], o["entry"], Q, topk=10, beam=64, metric=metric_name)
+    oid, _, _ = O.search(w.X, r.ids, r.entry, np.ascontiguousarray(w.Q), 64, 10, w.metric)
+    rg, ro = recall10(sid.cpu().numpy(), gt), recall10(oid, gt)
+    gi = o["ids"].cpu().numpy()
+    return {"N": n, "oracle_seconds": dt, "cores": os.cpu_count() or 1, "recall@10_gpu": rg,
+            "recall@10_oracle": ro, "recall_delta_pt": 100 * (rg - ro), "queries": nq, "beam": 64,
+            "rows_identical": float(np.mean(np.all(gi == r.ids, 1))), "entry_equal": o["entry"] == r.entry,
+            "input_pgs": "host builder" if host_graphs else "GPU builder (the same recipe)"}
+
+
+def measure_small(fg, dev, peaks):
+    """The small parity workload (20,000 points, d = 32, 2 shards): the GPU forms, the oracle on
+    one host thread and on all of them, and the recall of both merged graphs."""
+    import torch
+    import oracle as O
+    from synth import gen, pgbuild
+    w = gen.make("small")
+    graphs = pgbuild.build_all(w)
+    X = torch.from_numpy(w.X).to(dev)
+    adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
+    inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs])
+    kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=3)
+    ch = timed_merges(fg, inp, dict(kw, join_filter="tc"), 5, 3)
+    pl = timed_merges(fg, inp, dict(kw, join_filter="fp32", rows="fp32"), 5, 3)
+    times = {}
+    for threads in (1, 0):
+        P = O.Problem.from_workload(w, graphs, nthreads=threads)
+        t0 = time.perf_counter()
+        r = O.merge(P, w.k, w.R, w.alpha, iters=3)
+        times[threads] = time.perf_counter() - t0
+    Q = torch.from_numpy(w.Q).to(dev)
+    gt = exact_top10(X, Q, 0)
+    sid, _ = fg.search(X, ch["out"]["ids"], ch["out"]["entry"], Q, topk=10, beam=64)
+    oid, _, _ = O.search(w.X, r.ids, r.entry, w.Q, 64, 10, 0)
+    ms_c, ms_p = float(np.mean(ch["step_ms"])), float(np.mean(pl["step_ms"]))
+    gi = ch["out"]["ids"].cpu().numpy()
+    return {"workload": "small: N=20,000 (2 x 10,000), d=32, 50-cluster Gaussian mixture, squared L2, input PGs "
+                        "M=16 ef=64, k=16, R=32, alpha=1.2, I_max=3",
+            "value": w.N / (ms_c * 1e-3), "unit": UNIT, "ms_per_step": ms_c, "steps": 5, "warmup": 3,
+            "form": "BF16 tensor-core join filter", "l2_policy": "L2-resident (2.6 MB of vectors): a parity workload",
+            "plain_fp32": {"value": w.N / (ms_p * 1e-3), "unit": UNIT, "ms_per_step": ms_p,
+                           "same_graph": bool(torch.equal(pl["out"]["ids"], ch["out"]["ids"]))},
+            "oracle": {"seconds_1_thread": times[1], "seconds_all_threads": times[0], "cores": os.cpu_count() or 1,
+                       "value_1_thread": w.N / times[1], "value_all_threads": w.N / times[0]},
+            "recall@10_gpu": recall10(sid.cpu().numpy(), gt), "recall@10_oracle": recall10(oid, gt),
+            "rows_identical_to_oracle": float(np.mean(np.all(gi == r.ids, 1))),
+            "entry_equal": ch["out"]["entry"] == r.entry}
+
+
 def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
     """One sub-record: the chosen form (BF16 tensor-core join filter) and the plain FP32 form
     (FP32 rows, FP32 SIMT join filter) of one workload at full size, the roofline of the chosen
@@ -470,6 +540,8 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
     from synth import gen, pgbuild
     if name == "batched":
         return measure_batched(fg, dev, peaks, 64, 10_000, 200_000, steps, warmup)
+    if name == "small":
+        return measure_small(fg, dev, peaks)
     c = CONFIGS[name]
     t0 = time.perf_counter()
     w = gen.make(c["recipe"])
@@ -519,6 +591,8 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
     del inp, X, adj, ch, pl
     torch.cuda.empty_cache()
     fg.trim_memory()
+    if c.get("oracle_n"):   # the recall delta against the FP64 oracle, on a bounded sample
+        rec["oracle_sample"] = oracle_sample_check(fg, c["recipe"], c["oracle_n"], kw, c["metric"], dev, c["filter"])
     return rec
 
 
@@ -727,7 +801,7 @@ def measure_batched(fg, dev, peaks, n_merges, lo, hi, steps, warmup):
     import torch
     from synth import gen
     t0 = time.perf_counter()
-    ws_ = gen.batched(n_merges=n_merges, n_lo=lo, n_hi=hi, nq=10)
+    ws_ = gen.batched(n_merges=n_merges, n_lo=lo, n_hi=hi, nq=200)
     chosen, plain, pg_ms = [], [], 0.0
     for w in ws_:
         xb = torch.from_numpy(w.bits().view(np.int16)).to(dev).view(torch.bfloat16)
@@ -774,6 +848,24 @@ def measure_batched(fg, dev, peaks, n_merges, lo, hi, steps, warmup):
         fg._lib.test_set("batch_union", 1)
     ms_p, out_p, _ = timed(plain, 1, join_filter="fp32")
     N = sum(w.N for w in ws_)
+    # the recall delta against the FP64 oracle on the two smallest merges of the batch (each
+    # merged alone by the oracle; GPU graphs from the batch call)
+    import oracle as O
+    osamp = []
+    for m in sorted(range(len(ws_)), key=lambda i: ws_[i].N)[:2]:
+        w = ws_[m]
+        graphs = [(a.cpu().numpy(), e) for a, e in zip(chosen[m].adjs, chosen[m].entries)]
+        r = O.merge(O.Problem.from_workload(w, graphs), w.k, w.R, w.alpha, iters=3)
+        Xm = torch.from_numpy(w.X).to(dev)
+        Qm = torch.from_numpy(np.ascontiguousarray(w.Q)).to(dev)
+        gt = exact_top10(Xm, Qm, w.metric)
+        sid, _ = fg.search(Xm, out_c[m]["ids"], out_c[m]["entry"], Qm, topk=10, beam=64, metric="cos")
+        oid, _, _ = O.search(w.X, r.ids, r.entry, np.ascontiguousarray(w.Q), 64, 10, w.metric)
+        rg, ro = recall10(sid.cpu().numpy(), gt), recall10(oid, gt)
+        osamp.append({"merge": m, "N": w.N, "h": w.h, "recall@10_gpu": rg, "recall@10_oracle": ro,
+                      "recall_delta_pt": 100 * (rg - ro), "queries": len(w.Q),
+                      "rows_identical": float(np.mean(np.all(out_c[m]["ids"].cpu().numpy() == r.ids, 1)))})
+        del Xm, Qm
     dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])[0] if kernels else None
     roof = None
     if dom in ("k_join", "k_prune"):
@@ -797,6 +889,7 @@ def measure_batched(fg, dev, peaks, n_merges, lo, hi, steps, warmup):
                           "form": "FP32 storage of the same values, FP32 SIMT join filter",
                           "same_graphs": all(torch.equal(a["ids"], b["ids"]) for a, b in zip(out_c, out_p))},
            "roofline": roof, "kernels": kernels, "merge_stats": stats, "inputs_seconds": t_inputs,
+           "oracle_sample": osamp,
            "inputs": f"vectors drawn on the host; input PGs built on the GPU by fgim_build_pg in {pg_ms:.0f} ms",
            "l2_policy": f"inputs larger than L2 ({N * w0.d * 2 / 1e9:.2f} GB of BF16 vectors)"}
     del chosen, plain, out_c, out_s, out_p

@@ -131,26 +131,48 @@ __device__ __forceinline__ float rows_delta(const RT* __restrict__ base, const i
                 w[t] = make_uint4(0u, 0u, 0u, 0u);
                 if (r < U && has) w[t] = *reinterpret_cast<const uint4*>(base + (long long)rid[r] * d + 16 * part);
             }
+            uint32_t sv[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                if ((t0 + t) * rpi < U) {
-                    uint32_t sq = __dp4a(qb.w.x, w[t].x, 0u);
-                    sq = __dp4a(qb.w.y, w[t].y, sq);
-                    sq = __dp4a(qb.w.z, w[t].z, sq);
-                    sq = __dp4a(qb.w.w, w[t].w, sq);
-                    uint32_t sv;
-                    if (METRIC == FGIM_L2SQ) {
-                        uint32_t sx = __dp4a(w[t].x, w[t].x, 0u);
-                        sx = __dp4a(w[t].y, w[t].y, sx);
-                        sx = __dp4a(w[t].z, w[t].z, sx);
-                        sx = __dp4a(w[t].w, w[t].w, sx);
-                        sv = sx - 2u * sq;   // modulo 2^32; the row total is exact
-                    } else {
-                        sv = sq;
+                uint32_t sq = __dp4a(qb.w.x, w[t].x, 0u);
+                sq = __dp4a(qb.w.y, w[t].y, sq);
+                sq = __dp4a(qb.w.z, w[t].z, sq);
+                sq = __dp4a(qb.w.w, w[t].w, sq);
+                if (METRIC == FGIM_L2SQ) {
+                    uint32_t sx = __dp4a(w[t].x, w[t].x, 0u);
+                    sx = __dp4a(w[t].y, w[t].y, sx);
+                    sx = __dp4a(w[t].z, w[t].z, sx);
+                    sx = __dp4a(w[t].w, w[t].w, sx);
+                    sv[t] = sx - 2u * sq;   // modulo 2^32; the row total is exact
+                } else {
+                    sv[t] = sq;
+                }
+            }
+            if (lsh == 3) {
+                // eight lanes per row: the four loads' partials are summed over the eight lanes
+                // together (each exchange step halves the values a lane keeps), so lane part p of
+                // row group s ends with the total of load p / 2, row 4 (p / 2) + s of the batch;
+                // unsigned additions in any order give the same (exact) totals
+                const int p = lane & 7;
+                const bool b2 = (p & 4) != 0, b1 = (p & 2) != 0;
+                const uint32_t keep0 = b2 ? sv[2] : sv[0], keep1 = b2 ? sv[3] : sv[1];
+                const uint32_t send0 = b2 ? sv[0] : sv[2], send1 = b2 ? sv[1] : sv[3];
+                const uint32_t h0 = keep0 + __shfl_xor_sync(kFull, send0, 4);
+                const uint32_t h1 = keep1 + __shfl_xor_sync(kFull, send1, 4);
+                uint32_t x = (b1 ? h1 : h0) + __shfl_xor_sync(kFull, b1 ? h0 : h1, 2);
+                x += __shfl_xor_sync(kFull, x, 1);
+                // lane r of the batch (rows 4 t0 .. 4 t0 + 15) takes row r: load r / 4 - t0, group r % 4
+                const int tn = (lane >> 2) - t0;
+                const uint32_t got = __shfl_sync(kFull, x, 8 * (lane & 3) + 2 * (tn & 3));
+                if (tn >= 0 && tn < 4) mine = got;
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if ((t0 + t) * rpi < U) {
+                        const uint32_t tot = row_group_sum(sv[t], lsh);
+                        const uint32_t got = __shfl_sync(kFull, tot, (lane & (rpi - 1)) << lsh);
+                        if ((lane >> rsh) == t0 + t) mine = got;
                     }
-                    sv = row_group_sum(sv, lsh);
-                    const uint32_t got = __shfl_sync(kFull, sv, (lane & (rpi - 1)) << lsh);
-                    if ((lane >> rsh) == t0 + t) mine = got;
                 }
             }
         }

@@ -63,7 +63,9 @@ def parse():
                     help="other workloads timed after the headline one, each in its own sub-record: "
                          "'precision' (1M d=96 IP, BF16 filter against plain FP32), 'fp8' (1M d=960, 8 uneven "
                          "shards), 'batched' (64 merges, ~4M points, d=768 BF16 cosine, one call), 'small' (20k, "
-                         "d=32, with the single-thread oracle); '' = none")
+                         "d=32, with the single-thread oracle); '' or 'none' = none")
+    ap.add_argument("--no-pg-build", action="store_true",
+                    help="skip building the headline's input PGs a second time on the GPU (timed, compared)")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip comparing the GPU merge with the oracle's (100k sample and the largest N the "
                          "oracle finishes in about two minutes)")
@@ -613,11 +615,13 @@ def run_fgim(args):
     t_pg_host = time.perf_counter() - t0
     X = torch.from_numpy(w.X).to(dev)
     # the same input PGs built on the GPU (outside every timed region): equal on these integer data
-    g_gpu, pg_gpu_ms = gpu_graphs(fg, w, X)
-    pg_build = {"gpu_ms": pg_gpu_ms, "host_seconds": t_pg_host, "host_threads": os.cpu_count() or 1,
-                "equal": all(np.array_equal(a[0], b[0]) and a[1] == b[1] for a, b in zip(g_gpu, graphs)),
-                "recipe": f"batch-incremental insertion from the medoid, M={w.M}, ef={w.ef}, {w.h} shards"}
-    del g_gpu
+    pg_build = None
+    if not args.no_pg_build:
+        g_gpu, pg_gpu_ms = gpu_graphs(fg, w, X)
+        pg_build = {"gpu_ms": pg_gpu_ms, "host_seconds": t_pg_host, "host_threads": os.cpu_count() or 1,
+                    "equal": all(np.array_equal(a[0], b[0]) and a[1] == b[1] for a, b in zip(g_gpu, graphs)),
+                    "recipe": f"batch-incremental insertion from the medoid, M={w.M}, ef={w.ef}, {w.h} shards"}
+        del g_gpu
     adj_np = np.concatenate([g[0] for g in graphs])
     adj = torch.from_numpy(adj_np).to(dev)
     entries = [g[1] for g in graphs]
@@ -778,7 +782,7 @@ def run_fgim(args):
             "input_pg_build": pg_build,
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms,
             "ms_median": float(np.median(step_ms))}
-    if ws == 1 and args.configs:
+    if ws == 1 and args.configs and args.configs != "none":
         # the other workloads, each outside the headline's timed region, in its own sub-record
         del X, adj, inp, out
         torch.cuda.empty_cache()

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fgim_launch.h"
 #include "k_beam.cuh"   // launch-shape helpers of the beam-search kernels (the autotuner)
 
@@ -258,6 +260,15 @@ struct Ctx {
     }
 };
 
+// NVTX range over one stage of a call on the host timeline (a profiler shows the stages; without
+// one attached the calls do nothing)
+struct StageRange {
+    explicit StageRange(const char* name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange&) = delete;
+    StageRange& operator=(const StageRange&) = delete;
+};
+
 // ---------------------------------------------------------------------------- validation
 static long long total_n(const fgim_shard* sh, int h) {
     long long n = 0;
@@ -497,6 +508,7 @@ static Problem compact_problem(Ctx& c, const Problem& P, const PhiMap& F, const 
 }
 
 static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_knng* g, const PhiMap* F = nullptr) {
+    StageRange range("fgim stage a: cross query (Alg. 1, Alg. 2)");
     const int L = resolve_L(p, h);
     need(L >= 1 && L <= FGIM_MAX_L, FGIM_EINVAL, "resolved L out of range");
     ck(launch_cross_query(P.t, P.X, P.X8, P.inv, P.N, P.metric, g->k, L, g, c.ctr + 0, c.status, c.s,
@@ -504,6 +516,7 @@ static void stage_a(Ctx& c, const Problem& P, const fgim_params* p, int h, fgim_
 }
 
 static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knng* g, fgim_stats* st) {
+    StageRange range("fgim stage b: Visit + Update (Alg. 3)");
     const long long N = P.N;
     const int k = g->k;
     const int rev_cap = resolve_rev_cap(p);
@@ -603,6 +616,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
 }
 
 static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stats* st) {
+    StageRange range("fgim stage b: indegree repair (Alg. 4)");
     const long long N = P.N;
     ck(launch_indegree(g->ids, N, g->k, T, true, g->flags, c.s));
     int32_t* flag = c.alloc<int32_t>(N);
@@ -634,6 +648,7 @@ static void repair(Ctx& c, const Problem& P, fgim_knng* g, int32_t* T, fgim_stat
 
 static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knng* g, const int32_t* T, int32_t* e_ids,
                   float* e_dist, int32_t* e_cnt) {
+    StageRange range("fgim stage c: neighbour selection (Alg. 5)");
     PruneRule rule;
     rule.kind = p->prune_rule;
     rule.alpha2 = (float)((double)p->alpha * (double)p->alpha);   // alpha^2 and 3 tau rounded once to FP32
@@ -643,6 +658,7 @@ static void prune(Ctx& c, const Problem& P, const fgim_params* p, const fgim_knn
 
 static void reverse_insert(Ctx& c, long long N, int R, const int32_t* e_ids, const float* e_dist, const int32_t* e_cnt,
                            fgim_graph* out) {
+    StageRange range("fgim stage c: reverse edges (Alg. 5)");
     ReverseBuffers b;
     b.cnt = c.alloc<int32_t>(N);
     b.off = c.alloc<long long>(N + 1);
@@ -678,6 +694,7 @@ static long long bfs(Ctx& c, const fgim_graph* g, const Entries& E, int32_t* vis
 
 static void reach_fix(Ctx& c, const Problem& P, const fgim_params* p, fgim_graph* g, fgim_stats* st,
                       const Entries& E = Entries()) {
+    StageRange range("fgim reachability fix");
     const long long N = g->n;
     const int R = g->R;
     const int beam = p->reach_beam > 0 ? p->reach_beam : 64;

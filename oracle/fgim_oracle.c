@@ -93,9 +93,13 @@ static int shard_of(const or_input* in, int64_t g) {
     return s;
 }
 
+// n > 0: that many threads; n <= 0: the OpenMP default seen at the first call (an earlier
+// call's count does not stick)
 static void set_threads(int32_t n) {
 #ifdef _OPENMP
-    if (n > 0) omp_set_num_threads(n);
+    static int dflt = 0;
+    if (dflt == 0) dflt = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : dflt);
 #else
     (void)n;
 #endif

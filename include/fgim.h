@@ -181,8 +181,9 @@ typedef struct {
     int64_t unreached;       /* vertices still unreached after the fix */
     int64_t join_reruns;     /* Update passes re-run after a proposal-buffer overflow */
     int64_t join_cands;      /* candidate-set sizes |C_n| + |C_o| summed over the vertices joined */
-    int64_t join_class[4];   /* vertices joined per Update form: tensor-core tile for |C| <= 64, <= 128,
-                                > 128, and the FP32 SIMT tile */
+    int64_t join_class[5];   /* vertices joined per Update form: tensor-core tile for |C| <= 64, <= 128,
+                                > 128, the FP32 SIMT tile, and one warp per vertex (few new
+                                candidates, byte rows) */
 } fgim_stats;
 
 /*
@@ -367,6 +368,10 @@ void fgim_trim_memory(void);
  *                       stops and the call returns FGIM_ETIMEOUT; 0 = unbounded (default).
  *   "batch_union"       0: fgim_merge_batch runs its merges one after another instead of as
  *                       one problem (same results; for comparing the two); 1 = default.
+ *   "join_sparse_nn"    >= 0: Update joins the vertices with at most this many new candidates
+ *                       (and at most 128 candidates) one warp per vertex on byte rows, the
+ *                       rest in the tensor-core tile (same results; 0 = never, a large value =
+ *                       every eligible vertex); -1 = the default cut-off (10).
  *   "fail_alloc_after"  >= 0: the scratch allocation of a call that comes after this many
  *                       successful ones fails as if the device were out of memory (the call
  *                       returns FGIM_ENOMEM); -1 = off (default).

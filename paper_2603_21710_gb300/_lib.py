@@ -51,7 +51,7 @@ class Graph(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("ndc", "hops", "join_pairs", "proposals", "zero_indegree",
                                               "repaired", "attached", "unreached", "join_reruns", "join_cands")] + [
-        ("join_class", ctypes.c_int64 * 4)]
+        ("join_class", ctypes.c_int64 * 5)]
 
     def as_dict(self):
         d = {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "join_class"}

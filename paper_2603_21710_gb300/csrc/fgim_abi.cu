@@ -109,6 +109,7 @@ static std::atomic<long long> g_test_prop_cap{0};
 static std::atomic<int> g_test_hop_budget{0};
 static std::atomic<long long> g_test_fail_after{-1};
 static std::atomic<int> g_test_batch_union{1};
+static std::atomic<int> g_test_sparse_nn{-1};   // >= 0: the cut-off of the warp-per-vertex Update form
 static thread_local long long t_allocs = 0;   // scratch allocations of the current call
 
 static cudaMemPool_t lib_pool() {
@@ -214,7 +215,7 @@ struct Ctx {
         const int hop_budget = g_test_hop_budget.load(std::memory_order_relaxed);
         if (hop_budget > 0)   // status[1]: the beam searches' expansion budget (test hook)
             ck(cudaMemcpyAsync(status + 1, &hop_budget, sizeof(int), cudaMemcpyHostToDevice, s));
-        ck(cudaMallocHost(&host, 64));
+        ck(cudaMallocHost(&host, 128));
     }
     ~Ctx() {
         if (host) cudaFreeHost(host);
@@ -561,11 +562,18 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.pend_off = c.alloc<long long>(N + 1);
     b.scan_bytes = scan_scratch_bytes(N);
     b.scan_tmp = c.alloc<unsigned char>((long long)b.scan_bytes);
-    b.max_nc = c.alloc<int32_t>(8);
-    b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);   // 8 ints of the 64-byte pinned slot
-    b.blist = c.alloc<int32_t>(3 * N);
+    b.max_nc = c.alloc<int32_t>(12);
+    b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);   // 24 ints of the 128-byte pinned slot
+    b.blist = c.alloc<int32_t>(4 * N);
     b.blist_cap = N;
     b.join_filter = p->join_filter;
+    {
+        // vertices with at most this many new candidates join one warp each on byte rows (their
+        // pairs are few; the tile form's per-candidate costs dominate there)
+        constexpr int kSparseNNDefault = 10;
+        const int o = g_test_sparse_nn.load(std::memory_order_relaxed);
+        b.sparse_nn = o >= 0 ? o : kSparseNNDefault;
+    }
     b.X8 = P.X8;
     b.Xb = nullptr;
     b.fp8 = false;
@@ -586,7 +594,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     ck(cudaMemsetAsync(b.pending, 0, N, c.s));
     ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
     ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, nullptr, N, c.ctr + 2, c.ctr + 5, c.status, c.s));
-    for (int q = 0; q < 4; ++q) st->join_class[q] += b.class_count[q];
+    for (int q = 0; q < 5; ++q) st->join_class[q] += b.class_count[q];
     unsigned long long cnt = c.read_u64(b.prop_count);
     long long total = (long long)cnt;
     ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
@@ -607,7 +615,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
         ck(cudaMemsetAsync(b.pending, 0, N, c.s));
         ck(cudaMemsetAsync(b.prop_count, 0, sizeof(unsigned long long), c.s));
         ck(refine_join(P.t, P.X, P.inv, P.metric, *g, b, b.pend_list, np, c.ctr + 2, c.ctr + 5, c.status, c.s));
-        for (int q = 0; q < 4; ++q) st->join_class[q] += b.class_count[q];
+        for (int q = 0; q < 5; ++q) st->join_class[q] += b.class_count[q];
         cnt = c.read_u64(b.prop_count);
         total += (long long)cnt;
         ck(refine_merge(*g, b, cnt < (unsigned long long)cap ? (long long)cnt : cap, c.s));
@@ -1690,6 +1698,10 @@ int32_t fgim_test_set(const char* knob, int64_t value) {
     }
     if (k == "batch_union") {
         g_test_batch_union.store(value != 0 ? 1 : 0);
+        return 1;
+    }
+    if (k == "join_sparse_nn") {
+        g_test_sparse_nn.store(value >= 0 ? (int)std::min<int64_t>(value, 1 << 20) : -1);
         return 1;
     }
     if (k == "fail_alloc_after") {

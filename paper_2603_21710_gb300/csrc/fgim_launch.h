@@ -86,7 +86,10 @@ struct RefineBuffers {
     // sets (device, 8 ints), a pinned host slot to read them, and the launch lists (3 x cap)
     int32_t* max_nc;
     int32_t* host_i32;
-    long long class_count[4];   // out of refine_join: vertices per form (TC <= 64, <= 128, > 128; FP32 tile)
+    long long class_count[5];   // out of refine_join: vertices per form (TC <= 64, <= 128, > 128; FP32 tile;
+                                // warp per vertex)
+    int sparse_nn;              // vertices with |C_n| <= sparse_nn (and |C| <= 128) join one warp each
+                                // (byte rows; 0: never)
     bool fp8;                   // Xb holds E4M3 rows with per-vector scales (tcm.w) instead of BF16 rows
     int32_t* blist;
     long long blist_cap;

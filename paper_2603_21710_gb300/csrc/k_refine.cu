@@ -16,6 +16,8 @@
 // A proposal buffer that overflows marks the vertices whose proposals were dropped;
 // the host merges what fits and re-runs those vertices (their pairs are re-evaluated
 // against the updated lists), which yields the same final lists.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -1035,14 +1037,16 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
                     const uint32_t e = wq[q0 + lane];
                     const uint4* pa = reinterpret_cast<const uint4*>(op + (e & 1023u) * brs);
                     const uint4* pb = reinterpret_cast<const uint4*>(op + ((e >> 10) & 1023u) * brs);
-                    uint32_t dot = 0u;
+                    // four independent chains (integer sums: any order gives the same total)
+                    uint32_t d0 = 0u, d1 = 0u, d2 = 0u, d3 = 0u;
                     for (int c = 0; c < (d >> 4); ++c) {
                         const uint4 x = pa[c], y = pb[c];
-                        dot = __dp4a(x.x, y.x, dot);
-                        dot = __dp4a(x.y, y.y, dot);
-                        dot = __dp4a(x.z, y.z, dot);
-                        dot = __dp4a(x.w, y.w, dot);
+                        d0 = __dp4a(x.x, y.x, d0);
+                        d1 = __dp4a(x.y, y.y, d1);
+                        d2 = __dp4a(x.z, y.z, d2);
+                        d3 = __dp4a(x.w, y.w, d3);
                     }
+                    const uint32_t dot = (d0 + d1) + (d2 + d3);
                     if (METRIC == FGIM_L2SQ) {
                         const uint32_t na = __float2uint_rn(meta[e & 1023u].x);
                         const uint32_t nb = __float2uint_rn(meta[(e >> 10) & 1023u].x);
@@ -1262,16 +1266,384 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     if (tid == 0) atomicAdd(cands_count, (unsigned long long)nc);
 }
 
+// ---------------------------------------------------------------------------- Update, few new candidates
+// A vertex whose C_n is small has few pairs to join (about |C_n| x |C|), while the tile form
+// above pays for every candidate's list (the membership bits) and the staging regardless. Such
+// vertices join one warp per vertex on byte rows, one lane per pair: lane j holds the row of
+// C[j] in registers, the rows of C_n sit in shared memory (every lane reads the same one at a
+// time), and every cross-graph pair {C[i], C[j]} (i < |C_n|, i < j < |C|) gets its exact
+// distance straight away (no filter). A direction proposes when its key beats the list's
+// worst key and the list does not hold the other vertex yet; both membership tests are bits
+// per (i, j), found from the new candidates' own lists:
+//   A (C[j] in list(C[i])): the entries of list(C[i]) looked up in a hash of C;
+//   B (C[i] in list(C[j])): the reverse list of C[i] (the Visit step's, every u whose list
+//      holds C[i]) looked up the same way. The lists have not changed since Visit in the first
+//      run of a pass, so this form joins only there (a re-run after a proposal overflow reads
+//      merged lists and goes to the tile form).
+// The pairs, their distances (the exact integer values of the canonical FP32 sums, as in the
+// tile form's re-rank) and the proposal rule are the tile form's, so the proposals are the same.
+// A warp's global reads come in a few rounds whose loads are all issued before any is used
+// (candidates; their worst keys and rows; list entries and reverse-list bounds; reverse-list
+// entries; the rows of each chunk of 32 candidates): one vertex is a chain of dependent reads.
+constexpr int kSparseWarps = 4;
+constexpr int kSparseBatch = 8;   // loads a lane keeps in flight in the list rounds
+
+// Shared memory of one warp of k_join_sparse (byte offsets; cm = largest |C|, nnm = largest
+// |C_n| of the launch, d = row bytes).
+struct SparseLayout {
+    int cthr, rbN, rbO, hkv, qrows, cid, csh, cinv, q2, rmN, rpre, memA, memB, bytes, hs, W;
+};
+
+__host__ __device__ inline SparseLayout sparse_layout(int cm, int nnm, int d) {
+    SparseLayout l;
+    int hs = 64;   // id -> index table, at most half full
+    while (hs < 2 * cm) hs <<= 1;
+    l.hs = hs;
+    l.W = (cm + 31) >> 5;   // bit words per membership row
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    int o = 0;
+    l.cthr = o;    // worst key of list(C[j])
+    o += a16(cm * 8);
+    l.rbN = o;     // start of the new / old reverse segment of C[i]
+    o += a16(nnm * 8);
+    l.rbO = o;
+    o += a16(nnm * 8);
+    l.hkv = o;     // (candidate id or -1, its index)
+    o += hs * 8;
+    l.qrows = o;   // byte rows of C_n (d is a multiple of 16)
+    o += nnm * d;
+    l.cid = o;
+    o += a16(cm * 4);
+    l.csh = o;     // graph of C[j]
+    o += a16(cm * 4);
+    l.cinv = o;    // 1 / |C[j]| (cosine)
+    o += a16(cm * 4);
+    l.q2 = o;      // |C[i]|^2 of the new candidates
+    o += a16(nnm * 4);
+    l.rmN = o;     // length of the new reverse segment of C[i]
+    o += a16(nnm * 4);
+    l.rpre = o;    // reverse entries of C[0 .. i) (new and old), nn + 1 of them
+    o += a16((nnm + 1) * 4);
+    l.memA = o;    // bit (i, j): C[j] in list(C[i])
+    o += nnm * l.W * 4;
+    l.memB = o;    // bit (i, j): C[i] in list(C[j])
+    o += nnm * l.W * 4;
+    l.bytes = a16(o);
+    return l;
+}
+
+template <int METRIC>
+__global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
+    ShardTable t, const uint8_t* __restrict__ X8, const float* __restrict__ inv_norm, int k,
+    const int32_t* __restrict__ ids, const float* __restrict__ dist, const uint64_t* __restrict__ revN,
+    const long long* __restrict__ offN, const uint64_t* __restrict__ revO, const long long* __restrict__ offO,
+    const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr,
+    int cmax, int cm, int nnm, const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ prop_tgt,
+    uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap,
+    uint8_t* __restrict__ pending, unsigned long long* pairs_count, unsigned long long* cands_count, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_sp[];
+    const int lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const long long w = (long long)blockIdx.x * kSparseWarps + warp;
+    if (w >= nv) return;
+    const long long v = vlist[w];
+    // round 1: the candidate row (read up to cm <= cmax entries before |C| is known) and the sizes
+    const long long crow = v * (long long)cmax;
+    int32_t cl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cl[u] = 32 * u + lane < cm ? cand[crow + 32 * u + lane] : -1;
+    const int nn = nn_arr[v];
+    const int nc = nn + no_arr[v];
+    if (nn == 0 || nc < 2) return;
+    const int d = t.dim;
+    if (nc > cm || nn > nnm || cm > 128 || (d & 15) != 0 || d > 128) {   // the host sized the launch
+        if (lane == 0) atomicOr(status, kErrBounds);
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (32 * u + lane >= nc) cl[u] = -1;
+    const SparseLayout L = sparse_layout(cm, nnm, d);
+    unsigned char* base = smem_sp + (size_t)warp * L.bytes;
+    uint64_t* cthr = reinterpret_cast<uint64_t*>(base + L.cthr);
+    long long* rbN = reinterpret_cast<long long*>(base + L.rbN);
+    long long* rbO = reinterpret_cast<long long*>(base + L.rbO);
+    int2* hkv = reinterpret_cast<int2*>(base + L.hkv);
+    unsigned char* qrows = base + L.qrows;
+    int32_t* cid = reinterpret_cast<int32_t*>(base + L.cid);
+    int32_t* csh = reinterpret_cast<int32_t*>(base + L.csh);
+    float* cinv = reinterpret_cast<float*>(base + L.cinv);
+    uint32_t* q2s = reinterpret_cast<uint32_t*>(base + L.q2);
+    int32_t* rmN = reinterpret_cast<int32_t*>(base + L.rmN);
+    int32_t* rpre = reinterpret_cast<int32_t*>(base + L.rpre);
+    uint32_t* memA = reinterpret_cast<uint32_t*>(base + L.memA);
+    uint32_t* memB = reinterpret_cast<uint32_t*>(base + L.memB);
+    const int hs = L.hs, W = L.W;
+    const int c16 = d >> 4;   // 16-byte chunks per row
+    // shifts for / c16 and / k when they are powers of two (the usual case), else -1
+    const int c16_sh = (c16 & (c16 - 1)) == 0 ? __ffs(c16) - 1 : -1;
+    const int k_sh = (k & (k - 1)) == 0 ? __ffs(k) - 1 : -1;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = lane; s < hs; s += 32) hkv[s] = make_int2(-1, -1);
+    for (int s = lane; s < 2 * nnm * W; s += 32) memA[s] = 0u;   // memB follows memA
+    __syncwarp();
+    // round 2: the candidates' worst keys
+    int32_t wl[4];
+    float dl[4], il[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        wl[u] = -1;
+        dl[u] = 0.f;
+        il[u] = 1.f;
+        if (cl[u] >= 0) {
+            wl[u] = ids[(long long)cl[u] * k + k - 1];
+            dl[u] = dist[(long long)cl[u] * k + k - 1];
+            if (METRIC == FGIM_COSINE) il[u] = inv_norm[cl[u]];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int j = 32 * u + lane;
+        if (j >= nc) continue;
+        const int32_t c = cl[u];
+        cid[j] = c;
+        csh[j] = shard_of(t, c);
+        cthr[j] = wl[u] < 0 ? kEmptyKey : mkkey(dl[u], wl[u]);
+        cinv[j] = il[u];
+        int slot = jhash(c, hs);
+        for (int p = 0; p < hs; ++p) {
+            if (atomicCAS(&hkv[slot].x, -1, c) == -1) {
+                hkv[slot].y = j;
+                break;
+            }
+            slot = (slot + 1) & (hs - 1);
+        }
+    }
+    __syncwarp();
+    auto lookup = [&](int32_t x) -> int {   // index of x in C, or -1
+        int slot = jhash(x, hs);
+        for (int p = 0; p < hs; ++p) {
+            const int2 kv = hkv[slot];
+            if (kv.x == x) return kv.y;
+            if (kv.x == -1) return -1;
+            slot = (slot + 1) & (hs - 1);
+        }
+        return -1;
+    };
+    // round 3, all issued before any is used: the rows of C_n (copied to shared memory
+    // asynchronously), the reverse-segment bounds of C_n, and the entries of the lists of C_n
+    for (int it = lane; it < nn * c16; it += 32) {
+        const int i = c16_sh >= 0 ? it >> c16_sh : it / c16, c = it - i * c16;
+        cp_async16(qrows + i * d + 16 * c, X8 + (long long)cid[i] * d + 16 * c, true);
+    }
+    cp_async_commit();
+    long long obn = 0, oen = 0, obo = 0, oeo = 0;   // bounds of C[lane] (the first 32 of C_n)
+    if (lane < nn) {
+        const int32_t ci = cid[lane];
+        obn = offN[ci];
+        oen = offN[ci + 1];
+        obo = offO[ci];
+        oeo = offO[ci + 1];
+    }
+    {
+        const int total = nn * k;
+        for (int b0 = 0; b0 < total; b0 += 32 * kSparseBatch) {
+            int32_t x[kSparseBatch];
+            int xi[kSparseBatch];
+#pragma unroll
+            for (int u = 0; u < kSparseBatch; ++u) {
+                const int it = b0 + 32 * u + lane;
+                x[u] = -1;
+                xi[u] = 0;
+                if (it < total) {
+                    const int i = k_sh >= 0 ? it >> k_sh : it / k;
+                    x[u] = ids[(long long)cid[i] * k + (it - i * k)];
+                    xi[u] = i;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSparseBatch; ++u) {
+                if (x[u] < 0) continue;
+                const int j = lookup(x[u]);
+                if (j >= 0) atomicOr(memA + xi[u] * W + (j >> 5), 1u << (j & 31));   // A bits
+            }
+        }
+    }
+    {
+        int carry = 0;
+        for (int i0 = 0; i0 < nn; i0 += 32) {
+            const int i = i0 + lane;
+            int cnt = 0;
+            if (i < nn) {
+                if (i0 > 0) {
+                    const int32_t ci = cid[i];
+                    obn = offN[ci];
+                    oen = offN[ci + 1];
+                    obo = offO[ci];
+                    oeo = offO[ci + 1];
+                }
+                rbN[i] = obn;
+                rbO[i] = obo;
+                rmN[i] = (int)(oen - obn);
+                cnt = (int)(oen - obn + oeo - obo);
+            }
+            int inc = cnt;   // inclusive prefix over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (i < nn) rpre[i] = carry + inc - cnt;
+            carry += __shfl_sync(kFull, inc, 31);
+        }
+        if (lane == 0) rpre[nn] = carry;
+    }
+    __syncwarp();
+    // round 4: the reverse-list entries of C_n, all at once (B bits)
+    {
+        const int total = rpre[nn];
+        for (int b0 = 0; b0 < total; b0 += 32 * kSparseBatch) {
+            int32_t x[kSparseBatch];
+            int xi[kSparseBatch];
+#pragma unroll
+            for (int u = 0; u < kSparseBatch; ++u) {
+                const int f = b0 + 32 * u + lane;
+                x[u] = -1;
+                xi[u] = 0;
+                if (f < total) {
+                    int lo = 0, hi = nn - 1;   // the i with rpre[i] <= f < rpre[i + 1]
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (rpre[mid] <= f) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int s = f - rpre[lo];
+                    const uint64_t key = s < rmN[lo] ? revN[rbN[lo] + s] : revO[rbO[lo] + (s - rmN[lo])];
+                    x[u] = key_id(key);
+                    xi[u] = lo;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSparseBatch; ++u) {
+                if (x[u] < 0) continue;
+                const int j = lookup(x[u]);
+                if (j >= 0) atomicOr(memB + xi[u] * W + (j >> 5), 1u << (j & 31));
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    if (METRIC == FGIM_L2SQ) {
+        for (int i = lane; i < nn; i += 32) {
+            const uint4* q = reinterpret_cast<const uint4*>(qrows + i * d);
+            uint32_t s = 0u;
+            for (int c = 0; c < c16; ++c) {
+                const uint4 x = q[c];
+                s = __dp4a(x.x, x.x, s);
+                s = __dp4a(x.y, x.y, s);
+                s = __dp4a(x.z, x.z, s);
+                s = __dp4a(x.w, x.w, s);
+            }
+            q2s[i] = s;
+        }
+        __syncwarp();
+    }
+    uint32_t my_pairs = 0;
+    for (int j0 = 0; j0 < nc; j0 += 32) {
+        const int j = j0 + lane;
+        const bool hj = j < nc;
+        // this lane's row C[j] in registers, and |C[j]|^2
+        uint4 xr[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            xr[c] = (hj && c < c16) ? *reinterpret_cast<const uint4*>(X8 + (long long)cid[j] * d + 16 * c)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t x2 = 0u;
+        if (METRIC == FGIM_L2SQ) {
+            uint32_t e0 = 0u, e1 = 0u, e2 = 0u, e3 = 0u;   // integer sums: any order, the same total
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                e0 = __dp4a(xr[c].x, xr[c].x, e0);
+                e1 = __dp4a(xr[c].y, xr[c].y, e1);
+                e2 = __dp4a(xr[c].z, xr[c].z, e2);
+                e3 = __dp4a(xr[c].w, xr[c].w, e3);
+            }
+            x2 = (e0 + e1) + (e2 + e3);
+        }
+        const int32_t cj = hj ? cid[j] : -1;
+        const int shj = hj ? csh[j] : -1;
+        const uint64_t thrj = hj ? cthr[j] : 0ull;
+        const float invj = (METRIC == FGIM_COSINE && hj) ? cinv[j] : 1.f;
+        const int wj = j0 >> 5;
+        const int ilim = min(nn, j0 + 31);   // a pair needs i < j <= j0 + 31
+        for (int i = 0; i < ilim; ++i) {
+            const bool valid = hj && i < j && csh[i] != shj;   // cross-graph pairs only
+            if (!__any_sync(kFull, valid)) continue;
+            my_pairs += valid ? 1u : 0u;
+            const uint4* q = reinterpret_cast<const uint4*>(qrows + i * d);
+            uint32_t e0 = 0u, e1 = 0u, e2 = 0u, e3 = 0u;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (c < c16) {
+                    const uint4 y = q[c];
+                    e0 = __dp4a(y.x, xr[c].x, e0);
+                    e1 = __dp4a(y.y, xr[c].y, e1);
+                    e2 = __dp4a(y.z, xr[c].z, e2);
+                    e3 = __dp4a(y.w, xr[c].w, e3);
+                }
+            }
+            const uint32_t dot = (e0 + e1) + (e2 + e3);
+            float dd;
+            if (METRIC == FGIM_L2SQ) {
+                dd = (float)(q2s[i] + x2 - 2u * dot);   // |a|^2 + |b|^2 - 2 a.b, an integer below 2^24
+            } else {
+                const float inv = METRIC == FGIM_COSINE ? __fmul_rn(cinv[i], invj) : 1.f;
+                dd = delta_finish<METRIC>((float)dot, inv);
+            }
+            const int32_t ci = cid[i];
+            const uint64_t kA = mkkey(dd, cj), kB = mkkey(dd, ci);
+            const bool pA = valid && kA < cthr[i] && !((memA[i * W + wj] >> lane) & 1u);
+            const bool pB = valid && kB < thrj && !((memB[i * W + wj] >> lane) & 1u);
+            const unsigned va = __ballot_sync(kFull, pA), vb = __ballot_sync(kFull, pB);
+            if ((va | vb) == 0u) continue;
+            const int na = __popc(va);
+            unsigned long long pos0 = 0;
+            if (lane == 0) pos0 = atomicAdd(prop_count, (unsigned long long)(na + __popc(vb)));
+            pos0 = __shfl_sync(kFull, pos0, 0);
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                if (!(dir == 0 ? pA : pB)) continue;
+                const unsigned long long pos = pos0 + (dir == 0 ? __popc(va & lt) : na + __popc(vb & lt));
+                if (pos < (unsigned long long)prop_cap) {
+                    prop_tgt[pos] = dir == 0 ? ci : cj;
+                    prop_key[pos] = dir == 0 ? kA : kB;
+                } else {
+                    pending[v] = 1;
+                    atomicOr(status, kErrOverflow);
+                }
+            }
+        }
+    }
+    const uint32_t tot = __reduce_add_sync(kFull, my_pairs);
+    if (lane == 0) {
+        if (tot) atomicAdd(pairs_count, (unsigned long long)tot);
+        atomicAdd(cands_count, (unsigned long long)nc);
+    }
+}
+
 // Largest candidate set and C_n of the vertices in vlist (all when null), and the vertices
-// split by candidate-set size into kTCLists lists (blist[q * cap ..]) for the tensor-core
-// launches: |C| <= 64, <= 128, > 128. out: [0] max |C|, [1] max |C_n|, [2 + q] list sizes,
-// [5 + q] max |C| per list.
+// split into kJoinLists lists (blist[q * cap ..]): the tensor-core launches by candidate-set
+// size (|C| <= 64, <= 128, > 128), and the warp-per-vertex form (list 3) for the vertices with
+// |C_n| <= sparse_nn and |C| <= kSparseMaxC. out: [0] max |C|, [1] max |C_n|, [2 + q] list sizes,
+// [6 + q] max |C| per list.
 constexpr int kTCLists = 3;
+constexpr int kJoinLists = 4;
+constexpr int kSparseMaxC = 128;
 __device__ __forceinline__ int tc_list_of(int m) { return m <= 64 ? 0 : m <= 128 ? 1 : 2; }
 
 __global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __restrict__ no,
-                               const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ out,
-                               int32_t* __restrict__ blist, long long cap) {
+                               const int32_t* __restrict__ vlist, long long nv, int sparse_nn,
+                               int32_t* __restrict__ out, int32_t* __restrict__ blist, long long cap) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int m = 0, mn = 0;
@@ -1283,10 +1655,10 @@ __global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __
         m = mn > 0 ? mn + no[v] : 0;
         act = mn > 0 && m >= 2;
     }
-    const int q = tc_list_of(m);
+    const int q = (mn <= sparse_nn && m <= kSparseMaxC) ? 3 : tc_list_of(m);
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int b = 0; b < kTCLists; ++b) {
+    for (int b = 0; b < kJoinLists; ++b) {
         const bool mine = act && q == b;
         const unsigned vote = __ballot_sync(kFull, mine);
         int base = 0;
@@ -1296,7 +1668,7 @@ __global__ void k_join_buckets(const int32_t* __restrict__ nn, const int32_t* __
         int mb = mine ? m : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(kFull, mb, o));
-        if (lane == 0 && mb > 0) atomicMax(out + 5 + b, mb);
+        if (lane == 0 && mb > 0) atomicMax(out + 2 + kJoinLists + b, mb);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1321,31 +1693,36 @@ static size_t tc_launch_smem(const TCLayout& TL, uint32_t cols) {
 cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_norm, int metric, const fgim_knng& g,
                         RefineBuffers& b, const int32_t* vlist, long long nv, unsigned long long* pairs,
                         unsigned long long* cands, int* status, cudaStream_t s) {
-    for (int q = 0; q < 4; ++q) b.class_count[q] = 0;
+    for (int q = 0; q < 5; ++q) b.class_count[q] = 0;
     if (nv <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMemsetAsync(b.max_nc, 0, 8 * sizeof(int32_t), s)) != cudaSuccess) return e;
+    // the warp-per-vertex form works on byte rows, in the first run of a pass only (its
+    // membership bits come from the reverse lists of Visit; a re-run reads merged lists)
+    const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim) && !b.fp8;
+    const int sparse_nn = bytes && vlist == nullptr ? std::min(b.sparse_nn, kSparseMaxC) : 0;
+    constexpr int kOut = 2 + 2 * kJoinLists;
+    if ((e = cudaMemsetAsync(b.max_nc, 0, kOut * sizeof(int32_t), s)) != cudaSuccess) return e;
     {
         LaunchScope ls("k_join_buckets", s);
-        k_join_buckets<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, b.max_nc, b.blist,
-                                                                  b.blist_cap);
+        k_join_buckets<<<(unsigned)cdivll(nv, 256), 256, 0, s>>>(b.nn, b.no, vlist, nv, sparse_nn, b.max_nc,
+                                                                  b.blist, b.blist_cap);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(b.host_i32, b.max_nc, kOut * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    int32_t hb[8];
-    for (int q = 0; q < 8; ++q) hb[q] = b.host_i32[q];
+    int32_t hb[kOut];
+    for (int q = 0; q < kOut; ++q) hb[q] = b.host_i32[q];
     const int32_t cm = hb[0], cmn = hb[1];
     if (cm < 2) return cudaSuccess;
     const int du = b.fp8 ? t.dim / 2 : t.dim;   // staged row length in 2-byte units
     bool use_tc = b.join_filter != 1 && b.Xb && du % 16 == 0 && cmn <= 128 && cm <= 256;
     if (use_tc)
         for (int q = 0; q < kTCLists; ++q)
-            if (hb[2 + q] > 0 && tc_layout(hb[5 + q], du).bytes > 227 * 1024) use_tc = false;
+            if (hb[2 + q] > 0 && tc_layout(hb[2 + kJoinLists + q], du).bytes > 227 * 1024) use_tc = false;
     if (use_tc) {
         for (int q = 0; q < kTCLists; ++q) {
-            const int32_t count = hb[2 + q], cmq = hb[5 + q];
+            const int32_t count = hb[2 + q], cmq = hb[2 + kJoinLists + q];
             if (count <= 0) continue;
             b.class_count[q] += count;
             const TCLayout TL = tc_layout(cmq, du);
@@ -1377,7 +1754,6 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         if (cmq > 128) FGIM_LAUNCH_TC4(MT, false, true, true);                                                    \
         else FGIM_LAUNCH_TC4(MT, false, false, true);                                                             \
     } while (0)
-            const bool bytes = b.X8 != nullptr && byte_rows_ok(t.dim) && !b.fp8;
             if (b.fp8) {
                 if (metric == FGIM_L2SQ) FGIM_LAUNCH_TC8(FGIM_L2SQ);
                 else if (metric == FGIM_IP) FGIM_LAUNCH_TC8(FGIM_IP);
@@ -1395,13 +1771,36 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
 #undef FGIM_LAUNCH_TC4
             if (e != cudaSuccess) return e;
         }
+        const int32_t count = hb[2 + 3], cms = hb[2 + kJoinLists + 3];
+        if (count > 0) {   // the vertices with few new candidates, one warp each
+            b.class_count[4] += count;
+            const int nnm = std::min(sparse_nn, (int)cms);
+            const size_t smem = (size_t)kSparseWarps * sparse_layout(cms, nnm, t.dim).bytes;
+            const int32_t* list = b.blist + 3LL * b.blist_cap;
+            const unsigned grid = (unsigned)cdivll(count, kSparseWarps);
+#define FGIM_LAUNCH_SP(MT)                                                                                        \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(k_join_sparse<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+        if (e != cudaSuccess) break;                                                                              \
+        LaunchScope ls("k_join_sparse", s);                                                                       \
+        k_join_sparse<MT><<<grid, kSparseWarps * 32, smem, s>>>(                                                  \
+            t, b.X8, inv_norm, g.k, g.ids, g.dist, b.revN, b.offN, b.revO, b.offO, b.cand, b.nn, b.no, b.cmax,    \
+            cms, nnm, list, count, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending, pairs, cands,     \
+            status);                                                                                              \
+        e = cudaGetLastError();                                                                                   \
+    } while (0)
+            if (metric == FGIM_L2SQ) FGIM_LAUNCH_SP(FGIM_L2SQ);
+            else if (metric == FGIM_IP) FGIM_LAUNCH_SP(FGIM_IP);
+            else FGIM_LAUNCH_SP(FGIM_COSINE);
+#undef FGIM_LAUNCH_SP
+        }
         return e;
     }
     // the rows are staged when they fit the shared memory of a CTA, otherwise read from global memory
     const bool stage = staged_layout(cm, g.k, t.dim).bytes <= 227 * 1024;
     const StagedLayout SL = staged_layout(cm, g.k, stage ? t.dim : 0);
     if (SL.bytes > 227 * 1024) return cudaErrorNotSupported;
-    b.class_count[3] += (long long)hb[2] + hb[3] + hb[4];   // the vertices with a pair to join
+    b.class_count[3] += (long long)hb[2] + hb[3] + hb[4] + hb[5];   // the vertices with a pair to join
     const size_t smem = SL.bytes;
 #define FGIM_LAUNCH_JS(MT, ST)                                                                                    \
     do {                                                                                                          \

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.Params) == 64
     assert ctypes.sizeof(_lib.KNNG) == 40
     assert ctypes.sizeof(_lib.Graph) == 40
-    assert ctypes.sizeof(_lib.Stats) == 112
+    assert ctypes.sizeof(_lib.Stats) == 120
 
 
 def _params(**kw):
@@ -128,7 +128,7 @@ def test_newer_entry_points_reject_bad_arguments_on_host(lib):
 
 def test_test_hooks_named_and_unknown(lib):
     """The test hooks exist by name, unknown names are refused; none touches the device."""
-    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1)):
+    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1), ("join_sparse_nn", -1)):
         assert lib.fgim_test_set(knob.encode(), off) == 1
     assert lib.fgim_test_set(b"no_such_knob", 1) == 0
     assert lib.fgim_test_get(b"no_such_counter") == -1

@@ -774,19 +774,19 @@ def test_precision_recipe_refine_pass_and_merge(deep_like):
 # --------------------------------------------------------------------------- join forms reached
 def test_parity_inputs_reach_every_join_form(sift_like, small):
     """Update's forms on the parity inputs: the Sift-like merge passes reach the two smaller
-    tensor-core size classes; a k-NNG with mixed flags reaches the third (|C| > 128); k = 96
+    tensor-core size classes and the warp-per-vertex form (few new candidates); a k-NNG with mixed flags reaches the third (|C| > 128); k = 96
     (candidate sets above the tile's limits) takes the FP32 tile; every one keeps the oracle's
     lists."""
     import paper_2603_21710_gb300 as fg
     w, graphs, P, inp = sift_like
     o, _, _ = O.stage_a(P, w.k)
     g = _to_dev(o)
-    seen = [0, 0, 0, 0]
+    seen = [0, 0, 0, 0, 0]
     for _ in range(3):
         st = fg.refine_pass(inp, g)
         seen = [a + b for a, b in zip(seen, st["join_class"])]
         fg.indegree_repair(inp, g)
-    assert seen[0] > 0 and seen[1] > 0, seen
+    assert seen[0] > 0 and seen[1] > 0 and seen[4] > 0, seen
     # a k-NNG with half of its entries old (the state of a later pass on larger data) gives sets
     # of new and old candidates above 128: the third class, bit for bit against the oracle
     o, _, _ = O.stage_a(P, w.k)
@@ -812,7 +812,8 @@ def hooks():
     import paper_2603_21710_gb300 as fg
     fg.load()
     yield fg._lib
-    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1), ("batch_union", 1)):
+    for knob, off in (("prop_cap", 0), ("hop_budget", 0), ("fail_alloc_after", -1), ("batch_union", 1),
+                      ("join_sparse_nn", -1)):
         fg._lib.test_set(knob, off)
 
 
@@ -1058,3 +1059,86 @@ def test_autotune_changes_no_result(sift_like, tmp_path):
     fg.autotune_clear()
     assert torch.equal(b["ids"], ref["ids"]) and torch.equal(b["dist"], ref["dist"])
     assert b["stats"]["ndc"] >= ref["stats"]["ndc"]   # a smaller table may only re-evaluate
+
+
+# --------------------------------------------------------------------------- warp-per-vertex Update
+def test_sparse_join_form_overflow_rerun(sift_like, hooks):
+    """The warp-per-vertex form with a proposal buffer far too small: its vertices whose
+    proposals did not fit are re-run by the tile form against the merged lists, and the pass
+    still equals the oracle's bit for bit."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, _, _ = O.stage_a(P, w.k)
+    g = _to_dev(o)
+    hooks.test_set("join_sparse_nn", 1 << 20)   # every vertex with |C| <= 128
+    hooks.test_set("prop_cap", 1)
+    st = fg.refine_pass(inp, g)
+    O.refine_iter(P, o)
+    assert st["join_reruns"] > 0 and st["join_class"][4] > 0, st
+    for key, ref in (("ids", o.ids), ("dist", o.dist), ("flags", o.flags)):
+        assert np.array_equal(_np(g[key]), ref), key
+
+
+@pytest.mark.parametrize("cut", [0, 1 << 20])
+def test_sparse_join_form_bit_exact(sift_like, hooks, cut):
+    """Update with every eligible vertex (|C| <= 128) joined one warp per vertex, and with none:
+    three passes from the oracle's state (the later ones have few new candidates per vertex)
+    each equal the oracle's pass bit for bit, pair count included."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    o, _, _ = O.stage_a(P, w.k)
+    hooks.test_set("join_sparse_nn", cut)
+    sparse = 0
+    for _ in range(3):
+        g = _to_dev(o)
+        st = fg.refine_pass(inp, g)
+        ost = O.refine_iter(P, o)
+        sparse += st["join_class"][4]
+        assert np.array_equal(_np(g["ids"]), o.ids)
+        assert np.array_equal(_np(g["dist"]), o.dist)
+        assert np.array_equal(_np(g["flags"]), o.flags)
+        assert st["join_pairs"] == ost["pairs"]
+    assert (sparse > 0) == (cut > 0), sparse
+
+
+def _int_tiny(seed, sizes, d, M, metric):
+    from synth import pgbuild
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(0, 255, (20, d))
+    X = np.rint(np.clip(centers[rng.integers(0, 20, sum(sizes))] + rng.normal(0, 25, (sum(sizes), d)), 0, 255))
+    X = X.astype(np.float32)
+    gs, o = [], 0
+    for n in sizes:
+        gs.append(pgbuild.build_pg(X[o:o + n], M, 32, metric))
+        o += n
+    return X, gs
+
+
+@pytest.mark.parametrize("metric", [0, 1, 2])
+def test_sparse_join_form_metrics(hooks, metric):
+    """Integer rows under each metric (squared L2, inner product, cosine): the warp-per-vertex
+    form and the tensor-core tile give the same lists, flags and pair counts, and both keep
+    the oracle's lists."""
+    import paper_2603_21710_gb300 as fg
+    sizes, d, M, k = [700, 500, 300], 48, 16, 16
+    X, gs = _int_tiny(40 + metric, sizes, d, M, metric)
+    P = O.Problem(X, sizes, np.concatenate([g[0] for g in gs]), np.array([g[1] for g in gs], np.int32), metric)
+    dev = _dev()
+    inp = fg.MergeInput.from_flat(torch.from_numpy(X).to(dev), sizes,
+                                  torch.from_numpy(np.concatenate([g[0] for g in gs])).to(dev),
+                                  [g[1] for g in gs], metric=metric)
+    o, _, _ = O.stage_a(P, k)
+    for _ in range(2):
+        outs = []
+        for cut in (0, 1 << 20):
+            hooks.test_set("join_sparse_nn", cut)
+            g = _to_dev(o)
+            st = fg.refine_pass(inp, g)
+            outs.append((g, st))
+        (a, sa), (b, sb) = outs
+        assert sa["join_class"][4] == 0 and sb["join_class"][4] > 0, (sa["join_class"], sb["join_class"])
+        for key in ("ids", "dist", "flags"):
+            assert torch.equal(a[key], b[key]), key
+        assert sa["join_pairs"] == sb["join_pairs"]
+        O.refine_iter(P, o)
+        assert len(PR.lists_match(_np(b["ids"]), _np(b["dist"]), o.ids, o.dist)) == 0

@@ -16,8 +16,10 @@ def test_join_roofline_arithmetic():
     stats = {"join_cands": 2000, "join_pairs": 10_000}
     out = bench.roofline_for("k_join", 10.0, 2, w, [], None, {"hbm_gbs": 1000.0, "bf16_tflops_sustained": 100.0},
                              stats, 1)
-    per_launch = 1000 * (2 * 128 + 4 * 64)          # candidates per launch x (BF16 row + list)
+    per_launch = 1000 * (1 * 128 + 4 * 64)          # candidates per launch x (byte row + list)
     assert out["algorithmic_bytes"] == per_launch
+    out4 = bench.roofline_for("k_join", 10.0, 2, w, [], None, {"hbm_gbs": 1000.0}, stats, 4)
+    assert out4["algorithmic_bytes"] == 1000 * (4 * 128 + 4 * 64)   # FP32 rows
     assert out["achieved"] == pytest.approx(per_launch / 0.01 / 1e9)
     assert out["frac"] == pytest.approx(out["achieved"] / 1000.0)
     assert out["algorithmic_flops"] == 5000 * 2 * 128
@@ -45,3 +47,15 @@ def test_row_bytes():
     assert bench.row_bytes(types.SimpleNamespace(X=(row + 0.5)[None], d=16)) == 4   # not integers
     assert bench.row_bytes(types.SimpleNamespace(X=(row + 1)[None], d=16)) == 4     # 256 out of range
     assert bench.row_bytes(types.SimpleNamespace(X=row[None, :12], d=12)) == 4      # d % 16 != 0
+
+
+def test_update_launches_fold_into_one_family():
+    """The Update's tile and warp-per-vertex launches are one roofline family: times and launch
+    counts add, the other kernels pass through."""
+    import bench
+    k = {"k_join": {"launches": 4, "ms": 40.0}, "k_join_sparse": {"launches": 2, "ms": 10.0},
+         "k_prune": {"launches": 1, "ms": 5.0}}
+    f = bench.roofline_kernels(k)
+    assert f == {"k_join": {"launches": 6, "ms": 50.0}, "k_prune": {"launches": 1, "ms": 5.0}}
+    assert bench.roofline_kernels({"k_join_sparse": {"launches": 2, "ms": 3.0}}) == {
+        "k_join": {"launches": 2, "ms": 3.0}}

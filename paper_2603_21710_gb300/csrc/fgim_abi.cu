@@ -565,6 +565,7 @@ static void refine_pass(Ctx& c, const Problem& P, const fgim_params* p, fgim_knn
     b.max_nc = c.alloc<int32_t>(12);
     b.host_i32 = reinterpret_cast<int32_t*>(c.host + 4);   // 24 ints of the 128-byte pinned slot
     b.blist = c.alloc<int32_t>(4 * N);
+    b.wk = c.alloc<uint64_t>(N);
     b.blist_cap = N;
     b.join_filter = p->join_filter;
     {

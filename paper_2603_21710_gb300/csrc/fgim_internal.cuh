@@ -31,7 +31,7 @@ constexpr int kMaxShards = FGIM_MAX_SHARDS;
 
 // Every call passes its kernels a device status array int[4]: status[0] collects the error
 // bits below; status[1] is the beam searches' expansion budget (0 = unbounded), set only by
-// the "hop_budget" test hook.
+// the "hop_budget" test hook; status[2] is scratch for one host read (the adjacency check).
 // device status word bits
 constexpr int kErrOverflow = 1;   // a bounded buffer overflowed (handled by the host)
 constexpr int kErrBounds = 2;     // an index failed a bounds check (the access was skipped)

@@ -88,6 +88,7 @@ struct RefineBuffers {
     int32_t* host_i32;
     long long class_count[5];   // out of refine_join: vertices per form (TC <= 64, <= 128, > 128; FP32 tile;
                                 // warp per vertex)
+    uint64_t* wk;               // worst key of every list (filled by refine_join for the Update launches)
     int sparse_nn;              // vertices with |C_n| <= sparse_nn (and |C| <= 128) join one warp each
                                 // (byte rows; 0: never)
     bool fp8;                   // Xb holds E4M3 rows with per-vector scales (tcm.w) instead of BF16 rows
@@ -108,6 +109,9 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
                         unsigned long long* cands, int* status, cudaStream_t s);
 cudaError_t refine_merge(const fgim_knng& g, RefineBuffers& b, long long nprop, cudaStream_t s);
 cudaError_t launch_prep_fp8(const float* X, long long N, int d, uint8_t* Xq, float4* tcm, cudaStream_t s);
+// *out = some adjacency row of the input graphs repeats an id within a 32-entry chunk (uses
+// status[2] as scratch; synchronizes the stream)
+cudaError_t adjacency_has_repeats(const ShardTable& t, long long N, int* status, cudaStream_t s, bool* out);
 cudaError_t launch_prep_bf16(const float* X, long long N, int d, __nv_bfloat16* Xb, float4* tcm, cudaStream_t s);
 cudaError_t launch_indegree(const int32_t* ids, long long N, int k, int32_t* T, bool clear_replaced, uint8_t* flags,
                             cudaStream_t s);

@@ -267,7 +267,8 @@ template <int METRIC, bool SMALLD, typename RT, int MAXS>
 __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ invt, const int32_t* __restrict__ adj,
                            int M, long long nt, int ep, long long id_off, const float* q, float4 qreg,
                            const QBytes& qb, float qinv, int d, int L, uint64_t* pool, uint8_t* pflag, int32_t* ht,
-                           int htbits, int32_t* scratch, float* P, WarpCounters& ctr, int* status) {
+                           int htbits, int32_t* scratch, float* P, WarpCounters& ctr, int* status,
+                           bool dedupe = true) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const int H = 1 << htbits;
@@ -331,8 +332,12 @@ __device__ int beam_search(const RT* __restrict__ Xt, const float* __restrict__ 
                 atomicOr(status, kErrBounds);
                 v = -1;
             }
-            // a neighbour listed twice is evaluated once (the lowest lane keeps it)
-            if ((__match_any_sync(kFull, v) & lt) != 0u) v = -1;
+            // a neighbour listed twice is evaluated once (the lowest lane keeps it); skipped
+            // (dedupe false) when the caller knows that no 32-entry chunk of a row repeats an id
+            if (dedupe) {   // warp-uniform: every lane takes the match
+                const unsigned same = __match_any_sync(kFull, v);
+                if ((same & lt) != 0u) v = -1;
+            }
             if (v >= 0) {
                 const int s = ht_slot(v, htbits);
                 if (ht[s] == v) v = -1;

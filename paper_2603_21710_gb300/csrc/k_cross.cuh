@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
                                                      float* __restrict__ out_dist, uint8_t* __restrict__ out_flags,
                                                      unsigned long long* counters, int* status,
                                                      const int32_t* __restrict__ phi, const int32_t* __restrict__ rows_of,
-                                                     long long nq) {
+                                                     long long nq, bool dedupe) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = lane_id();
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 1 ? 8 : 5) k_cross_query(Sh
         const int np = beam_search<METRIC, SMALLD, RT, MAXS>(Xr + t.off[j] * d,
                                                              inv_norm ? inv_norm + t.off[j] : nullptr, t.adj[j], t.M[j],
                                                              nj, t.entry[j], t.off[j], q, qreg, qb, qinv, d, Lq, pool,
-                                                             pflag, ht, htbits, scratch, P, ctr, status);
+                                                             pflag, ht, htbits, scratch, P, ctr, status, dedupe);
         for (int c0 = 0; c0 < np; c0 += 32) {
             uint64_t cand = (c0 + lane < np) ? pool[c0 + lane] : kEmptyKey;
             if (PHI && cand != kEmptyKey) {
@@ -135,7 +135,11 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
     if ((phi == nullptr) != (src == nullptr)) return cudaErrorInvalidValue;
     const long long blocks = (nq + wpb - 1) / wpb;
     if (blocks <= 0) return cudaSuccess;
-    cudaError_t e = cudaSuccess;
+    // the searches skip their per-expansion duplicate check when no adjacency row repeats an id
+    // within a 32-entry chunk (one pass over the input graphs; the usual case)
+    bool dedupe = true;
+    cudaError_t e = adjacency_has_repeats(t, N, status, s, &dedupe);
+    if (e != cudaSuccess) return e;
 #define FGIM_LAUNCH_CQ2(MT, SD, RT, MS, PH)                                                                          \
     do {                                                                                                           \
         e = cudaFuncSetAttribute(k_cross_query<MT, SD, RT, MS, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
@@ -144,7 +148,7 @@ cudaError_t launch_cross_query_t(const ShardTable& t, const float* X, const uint
         LaunchScope ls("k_cross_query", s);                                                                        \
         k_cross_query<MT, SD, RT, MS, PH><<<(unsigned)blocks, wpb * 32, smem, s>>>(                                    \
             t, X, reinterpret_cast<const RT*>(rows), inv_norm, N, k, L, htbits, out->ids, out->dist, out->flags,   \
-            counters, status, phi, src, nq);                                                                       \
+            counters, status, phi, src, nq, dedupe);                                                               \
         e = cudaGetLastError();                                                                                    \
     } while (0)
 #define FGIM_LAUNCH_CQ(MT, SD, RT, MS) FGIM_LAUNCH_CQ2(MT, SD, RT, MS, PHI)

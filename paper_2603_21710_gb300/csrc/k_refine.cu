@@ -223,6 +223,16 @@ cudaError_t refine_visit(const fgim_knng& g, int rev_cap, RefineBuffers& b, cuda
     return cudaSuccess;
 }
 
+// The worst key of every list, (delta, id) of entry k - 1 or the empty key (8 bytes per vertex:
+// the Update kernels read one per candidate, and the array stays in L2)
+__global__ void k_worst_keys(const int32_t* __restrict__ ids, const float* __restrict__ dist, long long N, int k,
+                             uint64_t* __restrict__ wk) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int32_t w = ids[v * k + k - 1];
+    wk[v] = w < 0 ? kEmptyKey : mkkey(dist[v * k + k - 1], w);
+}
+
 // ---------------------------------------------------------------------------- Update
 constexpr int kJThreads = 256;
 
@@ -712,8 +722,8 @@ __host__ __device__ inline TCLayout tc_layout(int cm, int d) {
 template <int METRIC, bool BYTES, bool LARGE, bool FP8>
 __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     ShardTable t, const float* __restrict__ X, const __nv_bfloat16* __restrict__ Xb, const uint8_t* __restrict__ X8,
-    const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids, const float* __restrict__ dist,
-    const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
+    const float4* __restrict__ tcm, const float* __restrict__ inv_norm, int k, const int32_t* __restrict__ ids,
+    const uint64_t* __restrict__ wk, const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr, int cmax,
     int cm, uint32_t tmem_cols, const int32_t* __restrict__ vlist, int32_t* __restrict__ prop_tgt,
     uint64_t* __restrict__ prop_key, unsigned long long* prop_count, long long prop_cap, uint8_t* __restrict__ pending,
     unsigned long long* pairs_count, unsigned long long* cands_count, int* status) {
@@ -793,18 +803,16 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         cp_async_commit();
     };
     stage(0);
-    int32_t wiA = -1, wiB = -1;
-    float dkA = 0.f, dkB = 0.f, invA = 1.f, invB = 1.f;
+    uint64_t wkA = kEmptyKey, wkB = kEmptyKey;
+    float invA = 1.f, invB = 1.f;
     float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), mB = mA;
     if (tid < nc) {
-        wiA = ids[(long long)cA * k + k - 1];
-        dkA = dist[(long long)cA * k + k - 1];
+        wkA = wk[cA];
         mA = tcm[cA];
         if (METRIC == FGIM_COSINE) invA = inv_norm[cA];
     }
     if (tid + NT < nc) {
-        wiB = ids[(long long)cB * k + k - 1];
-        dkB = dist[(long long)cB * k + k - 1];
+        wkB = wk[cB];
         mB = tcm[cB];
         if (METRIC == FGIM_COSINE) invB = inv_norm[cB];
     }
@@ -842,16 +850,16 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     if (tid < nc) insert(cA, tid);
     if (tid + NT < nc) insert(cB, tid + NT);
     __syncthreads();
-    auto put_meta = [&](int i, int32_t c, int32_t wi, float dk, float4 m, float inv) {
-        thr[i] = wi < 0 ? kEmptyKey : mkkey(dk, wi);
+    auto put_meta = [&](int i, int32_t c, uint64_t wkey, float4 m, float inv) {
+        thr[i] = wkey;
         if (m.z != 0.f) atomicOr(misc + 2, 1);
-        colf[i] = make_float4((1.f - Cf) * m.x, wi < 0 ? __int_as_float(0x7f800000) : dk,
+        colf[i] = make_float4((1.f - Cf) * m.x, wkey == kEmptyKey ? __int_as_float(0x7f800000) : key_dist(wkey),
                               __int_as_float(shard_of(t, c)), FP8 ? m.w : 0.f);   // w: the E4M3 scale
         m.w = inv;
         meta[i] = m;
     };
-    if (tid < nc) put_meta(tid, cA, wiA, dkA, mA, invA);
-    if (tid + NT < nc) put_meta(tid + NT, cB, wiB, dkB, mB, invB);
+    if (tid < nc) put_meta(tid, cA, wkA, mA, invA);
+    if (tid + NT < nc) put_meta(tid + NT, cB, wkB, mB, invB);
     // membership bits, per TMEM lane row a and TMEM column c of candidate b (col(b)):
     //   A (mask):  bit (a, col(b)) = C[b] in N(C[a])  (a's list already holds b)
     //   B (maskB): bit (a, col(b)) = C[a] in N(C[b])  (b's list already holds a)
@@ -1335,7 +1343,7 @@ __host__ __device__ inline SparseLayout sparse_layout(int cm, int nnm, int d) {
 template <int METRIC>
 __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
     ShardTable t, const uint8_t* __restrict__ X8, const float* __restrict__ inv_norm, int k,
-    const int32_t* __restrict__ ids, const float* __restrict__ dist, const uint64_t* __restrict__ revN,
+    const int32_t* __restrict__ ids, const uint64_t* __restrict__ wk, const uint64_t* __restrict__ revN,
     const long long* __restrict__ offN, const uint64_t* __restrict__ revO, const long long* __restrict__ offO,
     const int32_t* __restrict__ cand, const int32_t* __restrict__ nn_arr, const int32_t* __restrict__ no_arr,
     int cmax, int cm, int nnm, const int32_t* __restrict__ vlist, long long nv, int32_t* __restrict__ prop_tgt,
@@ -1388,16 +1396,14 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
     for (int s = lane; s < 2 * nnm * W; s += 32) memA[s] = 0u;   // memB follows memA
     __syncwarp();
     // round 2: the candidates' worst keys
-    int32_t wl[4];
-    float dl[4], il[4];
+    uint64_t wl[4];
+    float il[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        wl[u] = -1;
-        dl[u] = 0.f;
+        wl[u] = kEmptyKey;
         il[u] = 1.f;
         if (cl[u] >= 0) {
-            wl[u] = ids[(long long)cl[u] * k + k - 1];
-            dl[u] = dist[(long long)cl[u] * k + k - 1];
+            wl[u] = wk[cl[u]];
             if (METRIC == FGIM_COSINE) il[u] = inv_norm[cl[u]];
         }
     }
@@ -1408,7 +1414,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
         const int32_t c = cl[u];
         cid[j] = c;
         csh[j] = shard_of(t, c);
-        cthr[j] = wl[u] < 0 ? kEmptyKey : mkkey(dl[u], wl[u]);
+        cthr[j] = wl[u];
         cinv[j] = il[u];
         int slot = jhash(c, hs);
         for (int p = 0; p < hs; ++p) {
@@ -1721,6 +1727,11 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         for (int q = 0; q < kTCLists; ++q)
             if (hb[2 + q] > 0 && tc_layout(hb[2 + kJoinLists + q], du).bytes > 227 * 1024) use_tc = false;
     if (use_tc) {
+        {
+            LaunchScope ls("k_worst_keys", s);
+            k_worst_keys<<<(unsigned)cdivll(g.n, 256), 256, 0, s>>>(g.ids, g.dist, g.n, g.k, b.wk);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         for (int q = 0; q < kTCLists; ++q) {
             const int32_t count = hb[2 + q], cmq = hb[2 + kJoinLists + q];
             if (count <= 0) continue;
@@ -1738,7 +1749,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join", s);                                                                              \
         k_join_tc<MT, BY, LG, F8><<<(unsigned)count, (BY) ? 256 : kTCThreads, smem, s>>>(                           \
-            t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, g.dist, b.cand,\
+            t, X, reinterpret_cast<const __nv_bfloat16*>(b.Xb), b.X8, b.tcm, inv_norm, g.k, g.ids, b.wk, b.cand,  \
             b.nn, b.no, b.cmax, cmq, cols, list, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending,     \
             pairs, cands, status);                                                                                \
         e = cudaGetLastError();                                                                                   \
@@ -1784,7 +1795,7 @@ cudaError_t refine_join(const ShardTable& t, const float* X, const float* inv_no
         if (e != cudaSuccess) break;                                                                              \
         LaunchScope ls("k_join_sparse", s);                                                                       \
         k_join_sparse<MT><<<grid, kSparseWarps * 32, smem, s>>>(                                                  \
-            t, b.X8, inv_norm, g.k, g.ids, g.dist, b.revN, b.offN, b.revO, b.offO, b.cand, b.nn, b.no, b.cmax,    \
+            t, b.X8, inv_norm, g.k, g.ids, b.wk, b.revN, b.offN, b.revO, b.offO, b.cand, b.nn, b.no, b.cmax,      \
             cms, nnm, list, count, b.prop_tgt, b.prop_key, b.prop_count, b.prop_cap, b.pending, pairs, cands,     \
             status);                                                                                              \
         e = cudaGetLastError();                                                                                   \

@@ -257,4 +257,43 @@ cudaError_t launch_split_rows(const int32_t* ids, const float* dist, const int32
     return cudaGetLastError();
 }
 
+// Does any adjacency row of the input graphs repeat an id within a 32-entry chunk? (warp per
+// vertex; the beam searches check each chunk for repeats unless this says there are none)
+__global__ void k_adj_repeats(ShardTable t, long long N, int* flag) {
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= N) return;
+    const int i = shard_of(t, g);
+    const int M = t.M[i];
+    const int32_t* row = t.adj[i] + (g - t.off[i]) * M;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < M; c0 += 32) {
+        const int v = c0 + lane < M ? row[c0 + lane] : -1;
+        const unsigned same = __match_any_sync(kFull, v);   // every lane takes part
+        const bool rep = v >= 0 && (same & lt) != 0u;
+        if (__any_sync(kFull, rep)) {
+            if (lane == 0) atomicOr(flag, 1);
+            return;
+        }
+    }
+}
+
+cudaError_t adjacency_has_repeats(const ShardTable& t, long long N, int* status, cudaStream_t s, bool* out) {
+    *out = true;
+    if (N <= 0) return cudaSuccess;
+    int* flag = status + 2;   // a free word of the call's status array
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls("k_adj_repeats", s);
+        k_adj_repeats<<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(t, N, flag);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int h = 1;
+    if ((e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *out = h != 0;
+    return cudaSuccess;
+}
+
 }  // namespace fgim

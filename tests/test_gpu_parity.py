@@ -1142,3 +1142,29 @@ def test_sparse_join_form_metrics(hooks, metric):
         assert sa["join_pairs"] == sb["join_pairs"]
         O.refine_iter(P, o)
         assert len(PR.lists_match(_np(b["ids"]), _np(b["dist"]), o.ids, o.dist)) == 0
+
+
+def test_cross_query_adjacency_with_repeated_ids(sift_like):
+    """Input graphs whose rows list a neighbour twice (within one 32-entry chunk): the searches
+    evaluate each neighbour once, as Alg. 1's visited set does, so stage a still equals the
+    oracle's bit for bit; the same graphs without repeats give the same result."""
+    import paper_2603_21710_gb300 as fg
+    w, graphs, P, inp = sift_like
+    rng = np.random.default_rng(21)
+    gs = []
+    for adj, ent in graphs:
+        a = adj.copy()
+        rows = rng.choice(a.shape[0], a.shape[0] // 3, replace=False)
+        for r in rows:   # replace the last valid entry by a copy of the first (same chunk)
+            nv = int((a[r] >= 0).sum())
+            if nv >= 2 and nv <= 32:
+                a[r, nv - 1] = a[r, 0]
+        gs.append((a, ent))
+    Pd = O.Problem.from_workload(w, gs)
+    dev = _dev()
+    inpd = fg.MergeInput.from_flat(inp.X, w.shard_sizes, torch.from_numpy(np.concatenate([g[0] for g in gs])).to(dev),
+                                   [g[1] for g in gs])
+    ga = fg.cross_query(inpd, w.k)
+    oa, _, _ = O.stage_a(Pd, w.k)
+    assert np.array_equal(_np(ga["ids"]), oa.ids)
+    assert np.array_equal(_np(ga["dist"]), oa.dist)

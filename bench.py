@@ -64,6 +64,8 @@ def parse():
                          "'precision' (1M d=96 IP, BF16 filter against plain FP32), 'fp8' (1M d=960, 8 uneven "
                          "shards), 'batched' (64 merges, ~4M points, d=768 BF16 cosine, one call), 'small' (20k, "
                          "d=32, with the single-thread oracle); '' or 'none' = none")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default beam-search launch shape (no fgim_autotune before the timed steps)")
     ap.add_argument("--no-pg-build", action="store_true",
                     help="skip building the headline's input PGs a second time on the GPU (timed, compared)")
     ap.add_argument("--no-oracle-check", action="store_true",
@@ -440,7 +442,7 @@ def gpu_graphs(fg, w, X_dev):
 
 # the other workloads of the measurement plan, timed after the headline one (one sub-record each)
 CONFIGS = {
-    "precision": dict(recipe="precision", metric="ip", filter="tc", others=(), oracle_n=100_000,
+    "precision": dict(recipe="precision", metric="ip", filter="tc", others=(), oracle_n=100_000, tune=True,
                       workload="Deep-like merge: N=1,000,000 (2 x 500,000), d=96 unit-norm, inner product, "
                                "input PGs M=32 ef=128, k=48, R=32, alpha=1.0, I_max=3"),
     "fp8": dict(recipe="fp8", metric="l2", filter="fp8", others=("tc",), oracle_n=36_000,
@@ -567,6 +569,8 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
     adj = torch.from_numpy(np.concatenate([g[0] for g in graphs])).to(dev)
     inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, [g[1] for g in graphs], metric=c["metric"])
     kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=3)
+    # tuned beam-search shape where a tuning run is short (a few seconds of cross queries)
+    tune = fg.autotune(inp, k=w.k) if c.get("tune") else None
     ch = timed_merges(fg, inp, dict(kw, join_filter=c["filter"]), steps, warmup, profile=True)
     stats = ch["out"]["stats"]
     pl = timed_merges(fg, inp, dict(kw, join_filter="fp32", rows="fp32"), 1, 0)
@@ -601,6 +605,8 @@ def measure_config(fg, name, dev, peaks, steps=2, warmup=1, nq_eval=1000):
                           "same_graph": bool(torch.equal(pl["out"]["ids"], ch["out"]["ids"]))},
            "recall@10": recall10(sid.cpu().numpy(), gt), "recall_eval": {"queries": nq_eval, "beam": 64},
            "gpu_launches_per_step": ch["launches"] / steps, "roofline": roof, "roofline_by_kernel": roof_all,
+           "beam_shape": ({"warps_per_block": tune["wpb"], "table_bits": tune["ht_bits"], "by": "fgim_autotune"}
+                          if tune else "default"),
            "kernels": kernels, "merge_stats": stats, "inputs_seconds": t_inputs,
            "inputs": f"vectors drawn on the host; input PGs (M={w.M}, ef={w.ef}) built on the GPU by "
                      f"fgim_build_pg in {pg_ms:.0f} ms",
@@ -642,6 +648,9 @@ def run_fgim(args):
     entries = [g[1] for g in graphs]
     inp = fg.MergeInput.from_flat(X, w.shard_sizes, adj, entries, metric="l2")
     kw = dict(k=w.k, R=w.R, alpha=w.alpha, iters=WORKLOAD["iters"], join_filter=args.join_filter)
+    # the beam-search launch shape tuned on this merge's cross query (fgim_autotune; outside every
+    # timed region, as a user would run it once per workload)
+    tune = None if args.no_autotune else fg.autotune(inp, k=w.k)
     stream = torch.cuda.current_stream()
     out = None
     for _ in range(args.warmup):
@@ -796,6 +805,8 @@ def run_fgim(args):
             "hnsw": hnsw,
             "oracle_check": ocheck,
             "input_pg_build": pg_build,
+            "beam_shape": ({"warps_per_block": tune["wpb"], "table_bits": tune["ht_bits"],
+                            "cross_query_ms": tune["ms"], "by": "fgim_autotune"} if tune else "default"),
             "roofline_by_kernel": roof_all, "kernels": kernels, "merge_stats": stats, "step_ms": step_ms,
             "ms_median": float(np.median(step_ms))}
     if ws == 1 and args.configs and args.configs != "none":

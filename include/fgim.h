@@ -386,8 +386,8 @@ int64_t fgim_test_get(const char* what);
  * Autotuner of the launch shapes that change no result: the warps per block of the beam-search
  * kernels (the cross query of stage (a), the evaluation and reachability searches) and the size
  * of their visited table (a bigger table costs shared memory per warp, and so resident warps,
- * and saves re-evaluations of forgotten ids). fgim_autotune times every candidate shape (2 or 4
- * warps per block; the default table size and one step either way) on this merge's cross query
+ * and saves re-evaluations of forgotten ids). fgim_autotune times every candidate shape (1, 2 or
+ * 4 warps per block; the default table size, two steps smaller and one larger) on this merge's cross query
  * with CUDA events (one warm-up, best of two), keeps the fastest for this workload's key (metric,
  * bytes per coordinate read, dim, pool L, SM count of the current device) for the rest of the
  * process, appends it as a JSON line to cache_path (NULL: no file), and returns it (out pointers

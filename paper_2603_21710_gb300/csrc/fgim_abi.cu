@@ -1610,9 +1610,9 @@ fgim_status fgim_autotune(const fgim_shard* shards, int32_t h, const fgim_params
                 before = it->second;
             }
         }
-        const int wpbs[2] = {2, 4};
-        for (int wi = 0; wi < 2; ++wi)
-            for (int dh = -1; dh <= 1; ++dh) {
+        const int wpbs[3] = {1, 2, 4};
+        for (int wi = 0; wi < 3; ++wi)
+            for (int dh = -2; dh <= 1; ++dh) {
                 const BeamShape cand = {wpbs[wi], std::min(13, std::max(6, ht0 + dh))};
                 if ((size_t)warp_layout(P.d, L, cand.htbits, params->k, !bytes).bytes * cand.wpb > 227 * 1024) continue;
                 {

@@ -80,7 +80,8 @@ __global__ void k_rev_fill(const int32_t* __restrict__ ids, const float* __restr
     }
 }
 
-// the `cap` smallest (delta, source) keys of every reverse segment (warp per vertex)
+// the `cap` smallest (delta, source) keys of every reverse segment (warp per vertex), as a set:
+// in segment order when the segment has at most `cap` entries, else ascending
 __global__ void __launch_bounds__(128) k_rev_select(const long long* __restrict__ off, const uint64_t* __restrict__ rev,
                                                     long long N, int cap, int32_t* __restrict__ top,
                                                     int32_t* __restrict__ ntop) {
@@ -91,6 +92,11 @@ __global__ void __launch_bounds__(128) k_rev_select(const long long* __restrict_
     if (v >= N) return;
     uint64_t* list = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * cap;
     const long long b = off[v], m = off[v + 1] - off[v];
+    if (m <= cap) {   // the whole segment is the selection: the candidate sets are sets, so no order is needed
+        for (long long s = lane; s < m; s += 32) top[v * cap + s] = key_id(rev[b + s]);
+        if (lane == 0) ntop[v] = (int)m;
+        return;
+    }
     if (m <= 32) {   // one sort: the keys of a segment are distinct (one entry per source)
         const uint64_t sorted = warp_sort32(lane < m ? rev[b + lane] : kEmptyKey);
         const int nk = (int)(m < cap ? m : cap);

@@ -756,14 +756,21 @@ def run_fgim(args):
         fg.merge_host(Xh, Ah, w.shard_sizes, entries, out_ids=oi, out_deg=od, **kw)
         torch.cuda.synchronize()
         barrier(ws)
+        eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        walls = []
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for q in range(args.steps):
+            tq = time.perf_counter()
+            eev[q][0].record(stream)
             fg.merge_host(Xh, Ah, w.shard_sizes, entries, out_ids=oi, out_deg=od, **kw)
+            eev[q][1].record(stream)
+            walls.append(1e3 * (time.perf_counter() - tq))
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
         e2e = {"value": ws * w.N * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Ah.numel() * 4),
-               "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4 + 4)}
+               "d2h_bytes_per_step": int(oi.numel() * 4 + od.numel() * 4 + 4),
+               "step_wall_ms": walls, "step_device_ms": [a.elapsed_time(b) for a, b in eev]}
     if rank != 0:
         return
     cpu = None

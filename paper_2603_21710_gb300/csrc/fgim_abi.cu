@@ -215,10 +215,21 @@ struct Ctx {
         const int hop_budget = g_test_hop_budget.load(std::memory_order_relaxed);
         if (hop_budget > 0)   // status[1]: the beam searches' expansion budget (test hook)
             ck(cudaMemcpyAsync(status + 1, &hop_budget, sizeof(int), cudaMemcpyHostToDevice, s));
-        ck(cudaMallocHost(&host, 128));
+        host = pinned_slot();
     }
-    ~Ctx() {
-        if (host) cudaFreeHost(host);
+    // One pinned 128-byte readback slot per host thread, made once and kept for the thread's
+    // life: pinning and releasing host memory on every call costs milliseconds now and then
+    // (and the release synchronizes the device).
+    static long long* pinned_slot() {
+        struct Slot {
+            long long* p = nullptr;
+            ~Slot() {
+                if (p) cudaFreeHost(p);
+            }
+        };
+        thread_local Slot slot;
+        if (!slot.p) ck(cudaMallocHost(&slot.p, 128));
+        return slot.p;
     }
     template <typename T>
     T* alloc(long long n) {

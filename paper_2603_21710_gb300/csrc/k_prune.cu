@@ -318,15 +318,17 @@ __global__ void __launch_bounds__(128) k_prune_bytes(const uint8_t* __restrict__
                 if (s < nk) {
                     const int wi = kept[s];
                     const unsigned char* rw = rows + (size_t)wi * stride;
-                    uint32_t dot = 0u;
+                    // four independent chains (integer sums: any order gives the same total)
+                    uint32_t d0 = 0u, d1 = 0u, d2 = 0u, d3 = 0u;
                     for (int c = 0; c < c16n; ++c) {
                         const uint4 a = *reinterpret_cast<const uint4*>(rw + 16 * c);
                         const uint4 b = *reinterpret_cast<const uint4*>(rv + 16 * c);
-                        dot = __dp4a(a.x, b.x, dot);
-                        dot = __dp4a(a.y, b.y, dot);
-                        dot = __dp4a(a.z, b.z, dot);
-                        dot = __dp4a(a.w, b.w, dot);
+                        d0 = __dp4a(a.x, b.x, d0);
+                        d1 = __dp4a(a.y, b.y, d1);
+                        d2 = __dp4a(a.z, b.z, d2);
+                        d3 = __dp4a(a.w, b.w, d3);
                     }
+                    const uint32_t dot = (d0 + d1) + (d2 + d3);
                     float dc;
                     if (METRIC == FGIM_L2SQ) dc = (float)(n2[wi] + n2[t] - 2u * dot);
                     else if (METRIC == FGIM_IP) dc = delta_finish<FGIM_IP>((float)dot, 1.f);

@@ -767,10 +767,12 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     uint64_t* pb_key = reinterpret_cast<uint64_t*>(smem + L.pb_key);
     // misc: [0] proposals buffered, [2] rows whose BF16 copy is inexact,
     // [4..5] base of this CTA's proposals in the global buffer; mbarrier at byte 32, TMEM
-    // address at byte 48
+    // address at byte 48, the byte rows' mbarrier at byte 56
     int* misc = reinterpret_cast<int*>(smem + L.misc);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L.misc + 32);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc + 48);
+    // byte rows of the re-rank: completes when every thread's copies of them have landed
+    uint64_t* rows_bar = reinterpret_cast<uint64_t*>(smem + L.misc + 56);
     const int W = L.words, hs = L.hs, rows = L.rows_alloc;
     const int vq = d >> 2;           // float4 chunks per FP32 row
     const int kc = du >> 3;          // 16-byte chunks per staged (BF16 or E4M3) row
@@ -790,7 +792,10 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     uint32_t* maskB = mask + mrows * W;
     for (int i = tid; i < 2 * mrows * W; i += NT) mask[i] = 0u;
     if (tid < 8) misc[tid] = 0;
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_init(rows_bar, NT);
+    }
     if (warp == 0) tc::tmem_alloc(tmem_slot, tmem_cols);
     __syncthreads();
     // One round trip for everything the candidate ids address: the BF16 rows (cp.async; rows
@@ -958,6 +963,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     if (!ok_mma && tid == 0) atomicOr(status, kErrTimeout);
     // byte rows: the MMAs have read the BF16 tile, so its space takes the byte rows of the
     // candidates for the exact re-rank
+    // (the copies run under the filter: each warp waits on rows_bar before its first re-rank)
     const int brs = d + 16;
     if (BYTES && ok_mma) {
         const int c16 = d >> 4;
@@ -966,9 +972,9 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
             cp_async16(op + r * brs + c * 16, X8 + (long long)cid[r] * d + c * 16, true);
         }
         cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(tc::smem_u32(rows_bar)) : "memory");
     }
+    bool rows_ready = !BYTES;
 
     // Filter. A pair survives when lo, a lower bound of its exact value, can still beat the
     // worst key of a list it is not already in. General test: lo = value - bound with the
@@ -1042,6 +1048,10 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
     //    exact (the same values), else from the FP32 rows in global memory.
     constexpr int kStep = BYTES ? 32 : 8;
     auto rerank = [&](int nq) {
+        if (BYTES && !rows_ready && nq > 0) {   // bounded wait for the byte rows (every lane)
+            if (!tc::mbar_wait(rows_bar, 0u, 1 << 24)) atomicOr(status, kErrTimeout);
+            rows_ready = true;
+        }
         for (int q0 = 0; q0 < nq; q0 += kStep) {
             const int U = min(kStep, nq - q0);
             float sc = 0.f;
@@ -1254,6 +1264,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
         rerank(qn);
         qn = 0;
     }
+    cp_async_wait<0>();   // no copy of this thread may still be writing shared memory at exit
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);

@@ -356,12 +356,36 @@ def roofline_kernels(kernels):
     return out
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines (string and character literals kept),
+    so that a hash of it changes with the code only."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":   # a literal: copy it whole, escapes included
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def kernel_sources_sha256(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
     for f in sorted(TRAFFIC_SOURCES[kernel] + ["fgim_internal.cuh"]):
         h.update(f.encode())
-        h.update(open(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", f), "rb").read())
+        h.update(strip_comments(open(os.path.join(ROOT, "paper_2603_21710_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()
 
 

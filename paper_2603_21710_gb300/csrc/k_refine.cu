@@ -1307,7 +1307,7 @@ __global__ void __launch_bounds__(BYTES ? 256 : 128, 4) k_join_tc(
 //      merged lists and goes to the tile form).
 // The pairs, their distances (the exact integer values of the canonical FP32 sums, as in the
 // tile form's re-rank) and the proposal rule are the tile form's, so the proposals are the same.
-// A warp's global reads come in a few rounds whose loads are all issued before any is used
+// A warp's global reads come in a few batches whose loads are all issued before any is used
 // (candidates; their worst keys and rows; list entries and reverse-list bounds; reverse-list
 // entries; the rows of each chunk of 32 candidates): one vertex is a chain of dependent reads.
 constexpr int kSparseWarps = 4;
@@ -1372,7 +1372,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
     const long long w = (long long)blockIdx.x * kSparseWarps + warp;
     if (w >= nv) return;
     const long long v = vlist[w];
-    // round 1: the candidate row (read up to cm <= cmax entries before |C| is known) and the sizes
+    // read batch 1: the candidate row (read up to cm <= cmax entries before |C| is known) and the sizes
     const long long crow = v * (long long)cmax;
     int32_t cl[4];
 #pragma unroll
@@ -1412,7 +1412,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
     for (int s = lane; s < hs; s += 32) hkv[s] = make_int2(-1, -1);
     for (int s = lane; s < 2 * nnm * W; s += 32) memA[s] = 0u;   // memB follows memA
     __syncwarp();
-    // round 2: the candidates' worst keys
+    // read batch 2: the candidates' worst keys
     uint64_t wl[4];
     float il[4];
 #pragma unroll
@@ -1453,7 +1453,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
         }
         return -1;
     };
-    // round 3, all issued before any is used: the rows of C_n (copied to shared memory
+    // read batch 3, all issued before any is used: the rows of C_n (copied to shared memory
     // asynchronously), the reverse-segment bounds of C_n, and the entries of the lists of C_n
     for (int it = lane; it < nn * c16; it += 32) {
         const int i = c16_sh >= 0 ? it >> c16_sh : it / c16, c = it - i * c16;
@@ -1522,7 +1522,7 @@ __global__ void __launch_bounds__(kSparseWarps * 32, 8) k_join_sparse(
         if (lane == 0) rpre[nn] = carry;
     }
     __syncwarp();
-    // round 4: the reverse-list entries of C_n, all at once (B bits)
+    // read batch 4: the reverse-list entries of C_n, all at once (B bits)
     {
         const int total = rpre[nn];
         for (int b0 = 0; b0 < total; b0 += 32 * kSparseBatch) {

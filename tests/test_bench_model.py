@@ -59,3 +59,15 @@ def test_update_launches_fold_into_one_family():
     assert f == {"k_join": {"launches": 6, "ms": 50.0}, "k_prune": {"launches": 1, "ms": 5.0}}
     assert bench.roofline_kernels({"k_join_sparse": {"launches": 2, "ms": 3.0}}) == {
         "k_join": {"launches": 2, "ms": 3.0}}
+
+
+def test_source_hash_ignores_comments_only():
+    """The traffic figures are keyed by the kernels' code: comments and blank lines do not change
+    the hash, any code change does, and literals containing comment markers are kept."""
+    import bench
+    a = 'int f(int x) { return x + 1; }  // one\n/* two\n lines */\nconst char* s = "a//b/*c*/";\n'
+    b = '// header\nint f(int x) { return x + 1; }\n\nconst char* s = "a//b/*c*/";  /* tail */\n'
+    c = 'int f(int x) { return x + 2; }\nconst char* s = "a//b/*c*/";\n'
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments(a) != bench.strip_comments(c)
+    assert '"a//b/*c*/"' in bench.strip_comments(a)
